@@ -1,0 +1,299 @@
+"""Benchmark: milliseconds per certified N-1 objective bound on the 8316-bus
+synthetic network (10500 lines, 5000 non-islanding contingencies, 1100
+generators, 5000 flexible loads), one box per bound.
+
+One step = one full pass of the hot path (box -> bus intervals, base flows,
+contingency flow intervals with fused penalty maps and reductions, objective
+assembly) through the C ABI.  Prints one JSON line (rank 0).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+With N > 1 (torchrun), every rank bounds its own boxes of the same workload on
+its own GPU (weak scaling, no data-path collective); rank 0 reports the
+aggregate bounds per second as milliseconds per bound.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "ms per certified N-1 objective bound, 8316-bus"
+WORKLOAD = ("mesh8316: 8316 buses, 10500 lines, 5000 N-1 contingencies, 1100 gens, "
+            "5000 flexible loads, seed 1003, 1 box per bound")
+
+
+def _args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--config", type=int, default=3)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=15.0,
+                   help="target CPU time of the oracle sample")
+    return p.parse_args()
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            return json.load(fh)
+    except OSError:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smmax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smmax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smmax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _oracle_sample(case, target_s: float):
+    """Time the oracle (as it stands) on a bounded sample of the bound: all lines
+    against a subset of contingencies, then scale to the full contingency list.
+    Returns (ms per bound, description, threads)."""
+    import numpy as np
+
+    import oracle as O
+    sens_t0 = time.time()
+    sens = O.sensitivities(case)
+    sens_s = time.time() - sens_t0
+    cb, rb = O.bus_box(case, case.box_lo, case.box_hi)
+    # the parts outside the contingency loop, timed in full
+    t0 = time.time()
+    O.imbalance_interval(case, sens.phi, cb, rb)
+    O.base_terms(case, sens.phi, cb, rb)
+    O.cost_interval(case, case.box_lo[0], case.box_hi[0])
+    rest_s = time.time() - t0
+    threads = int(os.environ.get("IBP_ORACLE_THREADS", "0")) or len(os.sched_getaffinity(0))
+    n = max(threads, 16)
+    while True:
+        sub = case.__class__(**{**case.__dict__, "ctg_line": case.ctg_line[:n]})
+        ss = O.Sensitivities(phi=sens.phi, lodf=np.ascontiguousarray(sens.lodf[:, :n]),
+                             ptdf_kk=sens.ptdf_kk[:n])
+        t0 = time.time()
+        O.ctg_terms(sub, ss, cb, rb)
+        dt = time.time() - t0
+        if dt >= 0.25 * target_s or n >= case.n_ctg:
+            break
+        n = min(case.n_ctg, int(n * max(2.0, target_s / max(dt, 1e-3))))
+    per_bound = dt * case.n_ctg / n + rest_s
+    desc = (f"oracle on {n} of {case.n_ctg} contingencies x all {case.n_line} lines x all "
+            f"{case.n_bus} buses ({dt:.1f} s), scaled by {case.n_ctg}/{n}, plus base flows, "
+            f"imbalance and costs in full ({rest_s:.1f} s); PTDF/LODF build ({sens_s:.1f} s) "
+            f"excluded like the GPU case build")
+    return per_bound * 1e3, desc, threads
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return
+    from gen import make_config
+    case = make_config(args.config)
+    times = []
+    desc = ""
+    threads = 1
+    for i in range(args.warmup + args.steps):
+        ms, desc, threads = _oracle_sample(case, target_s=max(2.0, 60.0 / (args.warmup + args.steps)))
+        if i >= args.warmup:
+            times.append(ms)
+    v = statistics.median(times)
+    line = {"metric": METRIC, "value": v, "unit": "ms", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD, "boxes": 1, "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": v, "unit": "ms", "cores": threads, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_gb300(args):
+    import numpy as np
+    import torch
+
+    import paper_2511_15624_gb300 as P
+    from gen import make_config
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    case = make_config(args.config)
+    gpu = P.Case(case, device=local)
+    info = gpu.info()
+    nb = 1
+    lo = torch.tensor(case.box_lo, device=dev)
+    hi = torch.tensor(case.box_hi, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    # warm-up (device pointers, inputs resident in HBM)
+    for _ in range(args.warmup):
+        gpu.bound(lo, hi)
+    gpu.sync()
+
+    # (1) device-timed throughput
+    start, stop = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        start.record(stream)
+        for _ in range(args.steps):
+            out = gpu.bound(lo, hi)
+        stop.record(stream)
+        barrier()
+    gpu.sync()
+    clocks = clk.summary()
+    dev_ms = start.elapsed_time(stop)
+    obj = [t.cpu().numpy() for t in out]
+
+    # (2) per-kernel durations of the same launches, recorded by the library
+    # with CUDA events on the launching stream
+    gpu.set_timing(True)
+    ktimes = []
+    for _ in range(args.steps):
+        gpu.bound(lo, hi)
+        ktimes.append(gpu.last_timing())
+    gpu.set_timing(False)
+    ctg_ms = statistics.mean(t["contingency"] for t in ktimes)
+    tot_k = {k: statistics.mean(t[k] for t in ktimes) for k in ktimes[0]}
+
+    # (3) end to end through the public API with host buffers
+    hlo = np.ascontiguousarray(case.box_lo)
+    hhi = np.ascontiguousarray(case.box_hi)
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        gpu.bound(hlo, hhi)
+    e2e_s = time.perf_counter() - t0
+
+    steps_t = torch.tensor([dev_ms, e2e_s * 1e3], device=dev, dtype=torch.float64)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.all_reduce(steps_t, op=dist.ReduceOp.MAX)
+    dev_ms, e2e_ms = float(steps_t[0]), float(steps_t[1])
+    if rank != 0:
+        return
+    bounds = args.steps * nb * ws
+    value = dev_ms / bounds
+    peaks = _peaks()
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = sm_count * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s, FMA lanes x 2 x max clock
+    flop = P.algorithmic_flop(case.n_ctg, case.n_line, info.n_active, nb)
+    achieved = flop / (ctg_ms * 1e-3) / 1e12
+    line = {
+        "metric": METRIC, "value": value, "unit": "ms", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "boxes": nb, "n_active_buses": info.n_active,
+                   "interval_flows_per_s": case.n_ctg * case.n_line * nb / (value * 1e-3),
+                   "l2": "no flush: the streamed PTDF rows (345 MB) exceed the 129 MB L2",
+                   "kernel_ms": tot_k},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                     "frac": achieved / fp32_peak, "traffic": None,
+                     "peak_source": f"{sm_count} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz"},
+        "clocks": clocks,
+        "e2e": {"value": e2e_ms / bounds, "unit": "ms",
+                "h2d_bytes_per_step": int(2 * case.box_lo.nbytes),
+                "d2h_bytes_per_step": int(3 * 8 * nb)},
+        "gpu_launches": 4 * args.steps,
+        "objective": {"lo": float(obj[0][0]), "hi": float(obj[1][0]), "err": float(obj[2][0])},
+    }
+    if not args.no_cpu_baseline and ws == 1:
+        ms, desc, threads = _oracle_sample(case, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": ms, "unit": "ms", "cores": threads, "kind": "oracle",
+                                "sample": desc}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = _args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gb300(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,204 @@
+/*
+ * ibp.h -- C ABI of the GB300 interval-bound-propagation library for the
+ * soft-constrained security-constrained DCOPF market-clearing objective.
+ *
+ * What it computes (arXiv 2511.15624):
+ *   f_ibp(p_d, p_g) = sum_j c_j(p_d,j) - sum_i g_i(p_g,i)
+ *                     - zeta_inj 1^T s_inj - zeta_f (1^T s_fb + s_fc^agg)
+ *   (appendix eq. (ibp_f), eq. (penalized-objective)), with
+ *     s_inj  = |(E^T Phi - I) p_inj|                      eq. (slack-sinj)
+ *     s_fb   = max(|Phi p_inj| - p_fb^max, 0)             eq. (slack-sfb)
+ *     S_fc   = max(|P_fc| - 1 (p_fc^max)^T, 0), s_fc^agg = 1^T S_fc 1
+ *                                                         eqs. (slack-Sc), (slack-sagg)
+ *     P_fc[k,:] = H_k p_inj,  H_k = Phi + L[:,k] Phi[k,:] (Sec. II-C,
+ *       eq. (ctg flow simplified); L = line outage distribution factors)
+ *     p_inj = N_g p_g - N_d p_d                           (Sec. II-A)
+ *   and bounds it over the input box [box_lo, box_hi] by interval bound
+ *   propagation, eq. (IBP): an affine map W over a box with centre x_mu and
+ *   radius x_sigma lands in [W x_mu - |W| x_sigma, W x_mu + |W| x_sigma].
+ *   The contingency flows use the tight per-row rule (|H_k| r), which gives
+ *   the exact range of every post-contingency flow.
+ *
+ * Certification: every reported interval contains the exact IBP interval
+ * computed in real arithmetic from the FP64 sensitivities the library built
+ * (outward rounding throughout).  obj_err bounds the distance between the
+ * reported and the exact IBP objective bounds.
+ *
+ * Conventions
+ *   - Units: MW, $/MWh, reactance in p.u.; a single slack bus absorbs any
+ *     mismatch; flows are positive from line_from to line_to.
+ *   - Devices: boxes hold generators first, then loads: [n_gen + n_load].
+ *   - Piecewise-linear cost/value curves (Sec. III-B, eqs. (single ReLU),
+ *     (combined ReLUs)): device i owns n_seg[i] consecutive entries of the
+ *     flattened slope[] (a_m >= 0) and bkpt[] (segment starts, strictly
+ *     increasing); the curve is 0 before bkpt[0] and continues with the last
+ *     slope beyond the last breakpoint.
+ *   - Ownership: every input array is copied during the call; outputs are
+ *     written to caller-owned memory.  A case owns its device memory until
+ *     ibp_case_destroy.
+ *   - Pointers: ptr_mode 0 = host pointers, the call is synchronous (it copies
+ *     inputs to the device, runs, copies results back and synchronises the
+ *     stream).  ptr_mode 1 = device pointers, the call only enqueues work on
+ *     cuda_stream (NULL = legacy default stream) and returns; numerical errors
+ *     found on the device are reported by the next ibp_case_sync().
+ *   - Errors: no exception crosses the ABI.  Every call returns ibp_status and
+ *     leaves a message in a thread-local buffer read by ibp_last_error().
+ *     A device-side failure (an input box with lo > hi or a non-finite entry
+ *     seen only on the device, or a bounded wait that ran out) writes NaN into
+ *     obj_lo/obj_hi/obj_err of the call and makes ibp_case_sync() return
+ *     IBP_EINVAL or IBP_ETIMEOUT.  Nothing traps or hangs on the device.
+ *   - Threads: calls on one case must not overlap; distinct cases may be used
+ *     from distinct host threads.
+ */
+#ifndef IBP_GB300_H
+#define IBP_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ibp_case ibp_case; /* opaque; owns device buffers */
+
+typedef enum {
+    IBP_OK = 0,
+    IBP_EINVAL = 1,    /* bad argument (index, size, NaN, lo > hi, ...) */
+    IBP_EISLAND = 2,   /* network not connected, or a contingency islands it */
+    IBP_ESINGULAR = 3, /* FP64 factorisation failed for another reason */
+    IBP_ENOMEM = 4,    /* host or device allocation failed */
+    IBP_ECUDA = 5,     /* a CUDA runtime / library call failed, or no device */
+    IBP_ETIMEOUT = 6,  /* a bounded device-side wait ran out */
+    IBP_EUNSOUND = 7,  /* an internal consistency check on the bound failed */
+    IBP_ENOTSUP = 8    /* the case was created without a device (dry run) */
+} ibp_status;
+
+/*
+ * Build a case: validate the network, build the FP64 PTDF (Sec. II-A, eq. (line
+ * flow ptdf), slack column zero) and the line outage distribution factors of
+ * every listed contingency (Sec. II-C, eq. (ctg flow simplified): the
+ * Sherman-Morrison rank-1 update written as L[l,k] = PTDF_line[l,k] /
+ * (1 - PTDF_line[k,k]), L[k,k] = -1), keep the columns of buses that carry a
+ * device (slack excluded) in FP32 on the device, and allocate the per-call
+ * working buffers.  Runs once per case, outside any timed bound.
+ *
+ *   n_bus >= 2, 0 <= slack_bus < n_bus
+ *   n_line >= 1, line_from/line_to in [0, n_bus), from != to
+ *   reactance[n_line] > 0 (p.u.), rating[n_line] >= 0 (MW, base case),
+ *   rating_ctg[n_line] >= 0 or NULL (then = rating), eq. (slack-Sc)
+ *   n_gen, n_load >= 0 with n_gen + n_load >= 1; *_bus in [0, n_bus);
+ *   *_nseg[i] >= 1; *_slope >= 0; *_bkpt strictly increasing per device
+ *   zeta_inj, zeta_f >= 0 ($/MW), eq. (penalized-objective)
+ *   n_ctg >= 0, ctg_line[n_ctg] in [0, n_line) (duplicates are allowed and
+ *     counted twice, as in eq. (slack-sagg))
+ *   device: CUDA device ordinal; -1 = dry run (validation and host-side graph
+ *     checks only, no device work; the case then only validates arguments)
+ * Errors: IBP_EINVAL, IBP_EISLAND (disconnected network or a bridge
+ * contingency, checked on the host before any device work), IBP_ESINGULAR,
+ * IBP_ENOMEM, IBP_ECUDA.
+ */
+ibp_status ibp_case_create(int32_t n_bus, int32_t slack_bus, int32_t n_line,
+                           const int32_t *line_from, const int32_t *line_to,
+                           const double *reactance, const double *rating,
+                           const double *rating_ctg, int32_t n_gen,
+                           const int32_t *gen_bus, const int32_t *gen_nseg,
+                           const double *gen_slope, const double *gen_bkpt,
+                           int32_t n_load, const int32_t *load_bus,
+                           const int32_t *load_nseg, const double *load_slope,
+                           const double *load_bkpt, double zeta_inj, double zeta_f,
+                           int32_t n_ctg, const int32_t *ctg_line, int32_t device,
+                           ibp_case **out);
+
+void ibp_case_destroy(ibp_case *c);
+
+/*
+ * Certified IBP bound of f_ibp over each of n_box boxes (appendix eq. (f-ibp)
+ * bounds max f over the box from above by obj_hi).
+ *   box_lo, box_hi [n_box][n_gen + n_load] (FP64, MW), lo <= hi, finite
+ *   obj_lo, obj_hi, obj_err [n_box] (FP64): obj_hi >= the exact IBP upper
+ *     bound >= max f over the box; obj_lo <= the exact IBP lower bound;
+ *     obj_err >= |reported - exact IBP| for both ends.
+ *     obj_hi < 0 certifies that the box is welfare-negative, eq. (inf-or-wn).
+ *   flow_lo, flow_hi [n_box][n_ctg][n_line] (FP32) or NULL: outward-rounded
+ *     post-contingency flow intervals (the outaged line is exactly [0, 0]).
+ * n_box >= 1 (n_box == 0 is a no-op returning IBP_OK).
+ */
+ibp_status ibp_bound(ibp_case *c, int32_t n_box, const double *box_lo,
+                     const double *box_hi, double *obj_lo, double *obj_hi,
+                     double *obj_err, float *flow_lo, float *flow_hi,
+                     int32_t ptr_mode, void *cuda_stream);
+
+/*
+ * Adjoint of obj_hi (not certified; FP32 kernels with FP64 accumulation).
+ * Given grad_obj_hi [n_box] (d loss / d obj_hi), writes
+ *   grad_lo, grad_hi [n_box][n_gen + n_load]: d loss / d box_lo, d box_hi
+ *   grad_rating [n_box][n_line] or NULL: d loss / d rating_ctg (contingency
+ *     ratings; base ratings add their own term)
+ * The derivative is taken with the active set of the forward pass (pairs whose
+ * certified lower violation bound is > 0); it is valid away from kinks.
+ */
+ibp_status ibp_bound_backward(ibp_case *c, int32_t n_box, const double *box_lo,
+                              const double *box_hi, const double *grad_obj_hi,
+                              double *grad_lo, double *grad_hi, double *grad_rating,
+                              int32_t ptr_mode, void *cuda_stream);
+
+/*
+ * Bounds of many cases of uneven size in one persistent launch of the
+ * contingency kernel (device pointers only).  For case i:
+ *   box_lo[i], box_hi[i] [n_box[i]][n_dev_i], obj_lo[i], obj_hi[i], obj_err[i]
+ *   [n_box[i]].  Flow intervals are not written.
+ */
+ibp_status ibp_bound_multi(int32_t n_case, ibp_case *const *cases,
+                           const int32_t *n_box, const double *const *box_lo,
+                           const double *const *box_hi, double *const *obj_lo,
+                           double *const *obj_hi, double *const *obj_err,
+                           void *cuda_stream);
+
+/* Wait for the case's stream work and report device-side errors of the last
+ * asynchronous call (IBP_EINVAL for a bad box, IBP_ETIMEOUT for a wait). */
+ibp_status ibp_case_sync(ibp_case *c);
+
+typedef struct {
+    int32_t n_bus, n_line, n_ctg, n_gen, n_load;
+    int32_t n_active;      /* buses with a device, slack excluded */
+    int32_t n_active_pad;  /* row stride of the FP32 PTDF on the device */
+    int32_t device;        /* -1 for a dry-run case */
+    int64_t device_bytes;  /* device memory held by the case */
+    double build_seconds;  /* wall time of the FP64 sensitivity build */
+    double max_abs_lodf;   /* max |L| over the contingency list */
+} ibp_case_info_t;
+
+ibp_status ibp_case_info(const ibp_case *c, ibp_case_info_t *out);
+
+/*
+ * Kernel-shape selection for the contingency kernel (used by the autotuner).
+ * variant: 0 = library default for the box count; other values select one of
+ * the compiled tile shapes listed by ibp_kernel_variants().  Returns
+ * IBP_EINVAL for an unknown variant.
+ */
+ibp_status ibp_case_set_variant(ibp_case *c, int32_t variant);
+int32_t ibp_kernel_variants(int32_t *ids, int32_t cap, int32_t batched);
+
+/*
+ * Optional per-kernel timing of the last ibp_bound call, recorded with CUDA
+ * events on the call's stream when enabled (0 disables).  ms[0..n) receives
+ * {box_to_bus, base_flow, contingency, assemble} durations in milliseconds;
+ * the call synchronises the stream.
+ */
+ibp_status ibp_case_set_timing(ibp_case *c, int32_t enable);
+ibp_status ibp_case_last_timing(ibp_case *c, float *ms, int32_t n);
+
+/* Bounded-wait self test: launches one kernel that waits on an mbarrier that
+ * no thread arrives at, with a limit of limit_us microseconds; returns
+ * IBP_ETIMEOUT when the wait ran out and the kernel returned (expected), or
+ * IBP_OK / IBP_ECUDA otherwise. */
+ibp_status ibp_selftest_wait_timeout(int32_t device, int32_t limit_us);
+
+const char *ibp_last_error(void);
+const char *ibp_status_string(ibp_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IBP_GB300_H */

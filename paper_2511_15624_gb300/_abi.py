@@ -1,0 +1,210 @@
+"""Thin ctypes binding of ``include/ibp.h`` (argument marshalling only).
+
+Every step of a bound runs in the CUDA library ``_lib/libibp_gb300.so``; this
+module only converts arrays to pointers.  Host arrays (numpy) use the
+synchronous host-pointer mode; CUDA tensors (torch) use the device-pointer
+mode on the caller's current stream.  If the library is missing the import
+fails loudly: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_lib", "libibp_gb300.so")
+
+IBP_OK, IBP_EINVAL, IBP_EISLAND, IBP_ESINGULAR, IBP_ENOMEM, IBP_ECUDA, IBP_ETIMEOUT, \
+    IBP_EUNSOUND, IBP_ENOTSUP = range(9)
+
+EXPORTED = (
+    "ibp_case_create", "ibp_case_destroy", "ibp_bound", "ibp_bound_backward", "ibp_bound_multi",
+    "ibp_case_sync", "ibp_case_info", "ibp_case_set_variant", "ibp_kernel_variants",
+    "ibp_case_set_timing", "ibp_case_last_timing", "ibp_selftest_wait_timeout", "ibp_last_error",
+    "ibp_status_string",
+)
+
+
+class IBPError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{_status_name(status)}: {message}")
+        self.status = status
+
+
+class CaseInfo(ctypes.Structure):
+    _fields_ = [("n_bus", ctypes.c_int32), ("n_line", ctypes.c_int32), ("n_ctg", ctypes.c_int32),
+                ("n_gen", ctypes.c_int32), ("n_load", ctypes.c_int32),
+                ("n_active", ctypes.c_int32), ("n_active_pad", ctypes.c_int32),
+                ("device", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
+                ("build_seconds", ctypes.c_double), ("max_abs_lodf", ctypes.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    """Load the CUDA library (once).  Raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"CUDA library not built: {LIB_PATH} is missing "
+                "(run `python -c 'import __graft_entry__ as g; g.build()'`)")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I32, D = ctypes.c_void_p, ctypes.c_int32, ctypes.c_double
+        L.ibp_case_create.argtypes = [I32, I32, I32, P, P, P, P, P, I32, P, P, P, P, I32, P, P, P, P,
+                                      D, D, I32, P, I32, ctypes.POINTER(P)]
+        L.ibp_case_create.restype = ctypes.c_int
+        L.ibp_case_destroy.argtypes = [P]
+        L.ibp_case_destroy.restype = None
+        L.ibp_bound.argtypes = [P, I32, P, P, P, P, P, P, P, I32, P]
+        L.ibp_bound.restype = ctypes.c_int
+        L.ibp_bound_backward.argtypes = [P, I32, P, P, P, P, P, P, I32, P]
+        L.ibp_bound_backward.restype = ctypes.c_int
+        L.ibp_bound_multi.argtypes = [I32, P, P, P, P, P, P, P, P]
+        L.ibp_bound_multi.restype = ctypes.c_int
+        L.ibp_case_sync.argtypes = [P]
+        L.ibp_case_sync.restype = ctypes.c_int
+        L.ibp_case_info.argtypes = [P, ctypes.POINTER(CaseInfo)]
+        L.ibp_case_info.restype = ctypes.c_int
+        L.ibp_case_set_variant.argtypes = [P, I32]
+        L.ibp_case_set_variant.restype = ctypes.c_int
+        L.ibp_kernel_variants.argtypes = [P, I32, I32]
+        L.ibp_kernel_variants.restype = I32
+        L.ibp_case_set_timing.argtypes = [P, I32]
+        L.ibp_case_set_timing.restype = ctypes.c_int
+        L.ibp_case_last_timing.argtypes = [P, P, I32]
+        L.ibp_case_last_timing.restype = ctypes.c_int
+        L.ibp_selftest_wait_timeout.argtypes = [I32, I32]
+        L.ibp_selftest_wait_timeout.restype = ctypes.c_int
+        L.ibp_last_error.argtypes = []
+        L.ibp_last_error.restype = ctypes.c_char_p
+        L.ibp_status_string.argtypes = [ctypes.c_int]
+        L.ibp_status_string.restype = ctypes.c_char_p
+        _lib = L
+    return _lib
+
+
+def _status_name(s: int) -> str:
+    names = ["IBP_OK", "IBP_EINVAL", "IBP_EISLAND", "IBP_ESINGULAR", "IBP_ENOMEM", "IBP_ECUDA",
+             "IBP_ETIMEOUT", "IBP_EUNSOUND", "IBP_ENOTSUP"]
+    return names[s] if 0 <= s < len(names) else f"status {s}"
+
+
+def _check(status: int):
+    if status != IBP_OK:
+        raise IBPError(status, lib().ibp_last_error().decode())
+
+
+def ibp_last_error() -> str:
+    return lib().ibp_last_error().decode()
+
+
+def _host(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _ptr(a) -> Optional[int]:
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data
+    return a.data_ptr()  # torch tensor
+
+
+def _is_cuda_tensor(a) -> bool:
+    return hasattr(a, "is_cuda") and bool(a.is_cuda)
+
+
+def ibp_case_create(n_bus, slack_bus, line_from, line_to, reactance, rating, rating_ctg,
+                    gen_bus, gen_nseg, gen_slope, gen_bkpt, load_bus, load_nseg, load_slope,
+                    load_bkpt, zeta_inj, zeta_f, ctg_line, device=0) -> int:
+    """Returns the opaque case handle (an int)."""
+    keep = dict(
+        fr=_host(line_from, np.int32), to=_host(line_to, np.int32), x=_host(reactance, np.float64),
+        r=_host(rating, np.float64),
+        rc=None if rating_ctg is None else _host(rating_ctg, np.float64),
+        gb=_host(gen_bus, np.int32), gn=_host(gen_nseg, np.int32), gs=_host(gen_slope, np.float64),
+        gk=_host(gen_bkpt, np.float64), lb=_host(load_bus, np.int32), ln=_host(load_nseg, np.int32),
+        ls=_host(load_slope, np.float64), lk=_host(load_bkpt, np.float64),
+        ctg=_host(ctg_line, np.int32))
+    out = ctypes.c_void_p()
+    st = lib().ibp_case_create(
+        int(n_bus), int(slack_bus), keep["fr"].size, _ptr(keep["fr"]), _ptr(keep["to"]),
+        _ptr(keep["x"]), _ptr(keep["r"]), _ptr(keep["rc"]), keep["gb"].size, _ptr(keep["gb"]),
+        _ptr(keep["gn"]), _ptr(keep["gs"]), _ptr(keep["gk"]), keep["lb"].size, _ptr(keep["lb"]),
+        _ptr(keep["ln"]), _ptr(keep["ls"]), _ptr(keep["lk"]), float(zeta_inj), float(zeta_f),
+        keep["ctg"].size, _ptr(keep["ctg"]), int(device), ctypes.byref(out))
+    _check(st)
+    return out.value
+
+
+def ibp_case_destroy(handle: int):
+    lib().ibp_case_destroy(ctypes.c_void_p(handle))
+
+
+def ibp_bound(handle, n_box, box_lo, box_hi, obj_lo, obj_hi, obj_err, flow_lo=None, flow_hi=None,
+              ptr_mode=0, stream=None):
+    st = lib().ibp_bound(ctypes.c_void_p(handle), int(n_box), _ptr(box_lo), _ptr(box_hi),
+                         _ptr(obj_lo), _ptr(obj_hi), _ptr(obj_err), _ptr(flow_lo), _ptr(flow_hi),
+                         int(ptr_mode), stream)
+    _check(st)
+
+
+def ibp_bound_backward(handle, n_box, box_lo, box_hi, grad_obj_hi, grad_lo, grad_hi,
+                       grad_rating=None, ptr_mode=0, stream=None):
+    st = lib().ibp_bound_backward(ctypes.c_void_p(handle), int(n_box), _ptr(box_lo), _ptr(box_hi),
+                                  _ptr(grad_obj_hi), _ptr(grad_lo), _ptr(grad_hi),
+                                  _ptr(grad_rating), int(ptr_mode), stream)
+    _check(st)
+
+
+def ibp_bound_multi(handles, n_box, box_lo, box_hi, obj_lo, obj_hi, obj_err, stream=None):
+    n = len(handles)
+    H = (ctypes.c_void_p * n)(*[ctypes.c_void_p(h) for h in handles])
+    NB = (ctypes.c_int32 * n)(*[int(b) for b in n_box])
+
+    def arr(xs):
+        return (ctypes.c_void_p * n)(*[ctypes.c_void_p(_ptr(x)) for x in xs])
+    st = lib().ibp_bound_multi(n, H, NB, arr(box_lo), arr(box_hi), arr(obj_lo), arr(obj_hi),
+                               arr(obj_err), stream)
+    _check(st)
+
+
+def ibp_case_sync(handle):
+    _check(lib().ibp_case_sync(ctypes.c_void_p(handle)))
+
+
+def ibp_case_info(handle) -> CaseInfo:
+    info = CaseInfo()
+    _check(lib().ibp_case_info(ctypes.c_void_p(handle), ctypes.byref(info)))
+    return info
+
+
+def ibp_case_set_variant(handle, variant: int):
+    _check(lib().ibp_case_set_variant(ctypes.c_void_p(handle), int(variant)))
+
+
+def ibp_kernel_variants(batched: bool):
+    n = lib().ibp_kernel_variants(None, 0, int(batched))
+    ids = (ctypes.c_int32 * max(n, 1))()
+    lib().ibp_kernel_variants(ids, n, int(batched))
+    return [ids[i] for i in range(n)]
+
+
+def ibp_case_set_timing(handle, enable: bool):
+    _check(lib().ibp_case_set_timing(ctypes.c_void_p(handle), int(bool(enable))))
+
+
+def ibp_case_last_timing(handle):
+    ms = (ctypes.c_float * 4)()
+    _check(lib().ibp_case_last_timing(ctypes.c_void_p(handle), ms, 4))
+    return {"box_to_bus": ms[0], "base_flow": ms[1], "contingency": ms[2], "assemble": ms[3]}
+
+
+def ibp_selftest_wait_timeout(device: int, limit_us: int) -> int:
+    """Returns the status code (IBP_ETIMEOUT is the expected outcome)."""
+    return int(lib().ibp_selftest_wait_timeout(int(device), int(limit_us)))

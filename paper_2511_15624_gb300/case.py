@@ -1,0 +1,145 @@
+"""Python-side handle of an IBP case (a thin wrapper of the C ABI).
+
+``Case`` owns one ``ibp_case``; ``Case.bound`` and ``Case.backward`` marshal
+numpy (host) or torch CUDA (device) arrays into ``ibp_bound`` and
+``ibp_bound_backward``.
+"""
+from __future__ import annotations
+
+from typing import Optional
+
+import numpy as np
+
+from . import _abi
+
+
+class Case:
+    """A network, its devices, prices and contingency list, built on one GPU.
+
+    ``network`` is any object with the attributes of ``gen.Case`` (n_bus, slack,
+    line_from, line_to, reactance, rating, gen_bus, gen_nseg, gen_slope,
+    gen_bkpt, load_bus, load_nseg, load_slope, load_bkpt, zeta_inj, zeta_f,
+    ctg_line and optionally rating_ctg).
+    """
+
+    def __init__(self, network, device: int = 0):
+        n = network
+        self.n_bus = int(n.n_bus)
+        self.n_line = int(len(n.line_from))
+        self.n_gen = int(len(n.gen_bus))
+        self.n_load = int(len(n.load_bus))
+        self.n_dev = self.n_gen + self.n_load
+        self.n_ctg = int(len(n.ctg_line))
+        self.device = device
+        self._h = None
+        self._h = _abi.ibp_case_create(
+            n.n_bus, n.slack, n.line_from, n.line_to, n.reactance, n.rating,
+            getattr(n, "rating_ctg", None), n.gen_bus, n.gen_nseg, n.gen_slope, n.gen_bkpt,
+            n.load_bus, n.load_nseg, n.load_slope, n.load_bkpt, n.zeta_inj, n.zeta_f,
+            n.ctg_line, device)
+
+    @property
+    def handle(self) -> int:
+        return self._h
+
+    def close(self):
+        if self._h is not None:
+            _abi.ibp_case_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self) -> _abi.CaseInfo:
+        return _abi.ibp_case_info(self._h)
+
+    # ------------------------------------------------------------ forward
+    def bound(self, lo, hi, flows: bool = False, stream=None):
+        """Certified IBP bound over each box.
+
+        Host (numpy) boxes: returns numpy ``(obj_lo, obj_hi, obj_err)`` and, if
+        ``flows``, ``(flow_lo, flow_hi)`` of shape [n_box, n_ctg, n_line].
+        CUDA tensors: the same as torch tensors, enqueued on ``stream`` (default:
+        torch's current stream) without synchronising.
+        """
+        if _abi._is_cuda_tensor(lo):
+            import torch
+            lo = lo.contiguous().to(torch.float64)
+            hi = hi.contiguous().to(torch.float64)
+            nb = int(lo.shape[0]) if lo.dim() == 2 else 1
+            out = torch.empty((3, nb), dtype=torch.float64, device=lo.device)
+            fl = fh = None
+            if flows:
+                fl = torch.empty((nb, self.n_ctg, self.n_line), dtype=torch.float32, device=lo.device)
+                fh = torch.empty_like(fl)
+            s = stream if stream is not None else torch.cuda.current_stream(lo.device).cuda_stream
+            _abi.ibp_bound(self._h, nb, lo, hi, out[0], out[1], out[2], fl, fh, ptr_mode=1,
+                           stream=s)
+            res = (out[0], out[1], out[2])
+            return res + ((fl, fh) if flows else ())
+        lo = np.ascontiguousarray(np.atleast_2d(lo), np.float64)
+        hi = np.ascontiguousarray(np.atleast_2d(hi), np.float64)
+        if lo.shape != hi.shape or lo.shape[1] != self.n_dev:
+            raise ValueError(f"boxes must be [n_box, {self.n_dev}]")
+        nb = lo.shape[0]
+        olo, ohi, oerr = np.empty(nb), np.empty(nb), np.empty(nb)
+        fl = fh = None
+        if flows:
+            fl = np.empty((nb, self.n_ctg, self.n_line), np.float32)
+            fh = np.empty_like(fl)
+        _abi.ibp_bound(self._h, nb, lo, hi, olo, ohi, oerr, fl, fh, ptr_mode=0, stream=None)
+        return (olo, ohi, oerr) + ((fl, fh) if flows else ())
+
+    # ------------------------------------------------------------ adjoint
+    def backward(self, lo, hi, grad_obj_hi, want_rating: bool = False, stream=None):
+        """d loss / d box_lo, d box_hi (and d loss / d rating_ctg) of obj_hi."""
+        if _abi._is_cuda_tensor(lo):
+            import torch
+            nb = int(lo.shape[0])
+            g = grad_obj_hi.contiguous().to(torch.float64)
+            glo = torch.empty((nb, self.n_dev), dtype=torch.float64, device=lo.device)
+            ghi = torch.empty_like(glo)
+            gr = torch.empty((nb, self.n_line), dtype=torch.float64, device=lo.device) if want_rating else None
+            s = stream if stream is not None else torch.cuda.current_stream(lo.device).cuda_stream
+            _abi.ibp_bound_backward(self._h, nb, lo.contiguous(), hi.contiguous(), g, glo, ghi, gr,
+                                    ptr_mode=1, stream=s)
+            return (glo, ghi) + ((gr,) if want_rating else ())
+        lo = np.ascontiguousarray(np.atleast_2d(lo), np.float64)
+        hi = np.ascontiguousarray(np.atleast_2d(hi), np.float64)
+        nb = lo.shape[0]
+        g = np.ascontiguousarray(np.broadcast_to(np.asarray(grad_obj_hi, np.float64), (nb,)))
+        glo = np.empty((nb, self.n_dev))
+        ghi = np.empty((nb, self.n_dev))
+        gr = np.empty((nb, self.n_line)) if want_rating else None
+        _abi.ibp_bound_backward(self._h, nb, lo, hi, g, glo, ghi, gr, ptr_mode=0, stream=None)
+        return (glo, ghi) + ((gr,) if want_rating else ())
+
+    def sync(self):
+        _abi.ibp_case_sync(self._h)
+
+    def set_variant(self, variant: int):
+        _abi.ibp_case_set_variant(self._h, variant)
+
+    def set_timing(self, enable: bool):
+        _abi.ibp_case_set_timing(self._h, enable)
+
+    def last_timing(self):
+        return _abi.ibp_case_last_timing(self._h)
+
+
+def dry_run_case(network) -> "Case":
+    """A case created without a device: validates inputs only (host tests)."""
+    return Case(network, device=-1)
+
+
+def algorithmic_flop(n_ctg: int, n_line: int, n_active: int, n_box: int) -> float:
+    """Flops of the contingency kernel counted as FMAs x 2: one FMA forms each
+    |H_k| entry and one accumulates it per box, n_c n_l n_a (1 + B) FMAs."""
+    return 2.0 * n_ctg * n_line * n_active * (1 + n_box)
+
+
+__all__ = ["Case", "dry_run_case", "algorithmic_flop"]
+_ = Optional

@@ -1,0 +1,826 @@
+// C ABI of the library: argument validation, host-side graph checks, the FP64
+// sensitivity build, per-call workspace and the launch sequence of a bound.
+#include "internal.h"
+
+#include <cudaTypedefs.h>
+#include <cusolverDn.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <numeric>
+#include <string>
+#include <vector>
+
+using namespace ibp;
+
+// ----------------------------------------------------------------- errors
+static thread_local std::string g_last_error;
+
+static ibp_status fail(ibp_status s, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return s;
+}
+
+static ibp_status ok() {
+    g_last_error.clear();
+    return IBP_OK;
+}
+
+#define CUDA_TRY(expr)                                                                      \
+    do {                                                                                    \
+        cudaError_t _e = (expr);                                                            \
+        if (_e != cudaSuccess)                                                              \
+            return fail(_e == cudaErrorMemoryAllocation ? IBP_ENOMEM : IBP_ECUDA,           \
+                        "%s failed: %s", #expr, cudaGetErrorString(_e));                    \
+    } while (0)
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && cudaSetDevice(dev) == cudaSuccess) ok = true;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+template <class T>
+struct DevBuf {
+    T *p = nullptr;
+    size_t n = 0;
+    cudaError_t alloc(size_t count) {
+        free();
+        if (count == 0) count = 1;
+        cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+        if (e == cudaSuccess) n = count;
+        else p = nullptr;
+        return e;
+    }
+    void free() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        n = 0;
+    }
+    ~DevBuf() { free(); }
+};
+
+// ----------------------------------------------------------------- the case
+struct ibp_case {
+    int device = -1;
+    int n_bus = 0, slack = 0, n_line = 0, n_gen = 0, n_load = 0, n_dev = 0, n_ctg = 0;
+    int n_a = 0, n_a_pad = 0;
+    double zeta_inj = 0, zeta_f = 0;
+    double build_seconds = 0, max_abs_lodf = 0;
+    int num_sms = 0;
+    int variant = 0;
+    std::vector<int> ctg_line_h;
+
+    // persistent device data
+    DevBuf<float> phi_a, lodf, rate_up, rate_dn, rate_c_up, rate_c_dn;
+    DevBuf<int> ctg_line, act_ptr, act_dev, seg_ptr;
+    DevBuf<double> slope, bkpt;
+    DevBuf<float> hat_l, hat_k;  // one-box scaled rows (lazily allocated)
+
+    // per-call workspace
+    int cap_box = 0;
+    DevBuf<double> box_lo, box_hi, obj;
+    DevBuf<double> cbus;
+    DevBuf<float> rbus, cabs, box_consts, line_c, line_e, line_R;
+    DevBuf<double> part_base, part_ctg;
+    DevBuf<float> flows;
+    DevBuf<int> err;
+    int n_part_base = 0;
+
+    // timing
+    bool timing = false;
+    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+
+    ~ibp_case() {
+        if (device >= 0) {
+            DeviceGuard g(device);
+            for (auto &e : ev)
+                if (e) cudaEventDestroy(e);
+            phi_a.free(); lodf.free(); rate_up.free(); rate_dn.free(); rate_c_up.free();
+            rate_c_dn.free(); ctg_line.free(); act_ptr.free(); act_dev.free(); seg_ptr.free();
+            slope.free(); bkpt.free(); hat_l.free(); hat_k.free(); box_lo.free(); box_hi.free();
+            obj.free(); cbus.free(); rbus.free(); cabs.free(); box_consts.free(); line_c.free();
+            line_e.free(); line_R.free(); part_base.free(); part_ctg.free(); flows.free(); err.free();
+        }
+    }
+};
+
+// ----------------------------------------------------------------- helpers
+static bool is_fin(double x) { return std::isfinite(x); }
+
+static ibp_status check_pwl(const char *what, int n, const int32_t *nseg, const double *slope,
+                            const double *bkpt, std::vector<int> &ptr) {
+    ptr.assign(n + 1, 0);
+    for (int i = 0; i < n; ++i) {
+        if (nseg[i] < 1 || nseg[i] > 1024)
+            return fail(IBP_EINVAL, "%s_nseg[%d] = %d out of [1, 1024]", what, i, nseg[i]);
+        ptr[i + 1] = ptr[i] + nseg[i];
+    }
+    for (int i = 0; i < n; ++i) {
+        for (int m = ptr[i]; m < ptr[i + 1]; ++m) {
+            if (!is_fin(slope[m]) || slope[m] < 0)
+                return fail(IBP_EINVAL, "%s_slope[%d] must be finite and >= 0", what, m);
+            if (!is_fin(bkpt[m])) return fail(IBP_EINVAL, "%s_bkpt[%d] is not finite", what, m);
+            if (m > ptr[i] && !(bkpt[m] > bkpt[m - 1]))
+                return fail(IBP_EINVAL, "%s_bkpt of device %d must increase", what, i);
+        }
+    }
+    return IBP_OK;
+}
+
+// connectivity (BFS) and bridges (iterative Tarjan low-link) on the host
+static bool connected(int n, const std::vector<std::vector<std::pair<int, int>>> &adj) {
+    std::vector<char> seen(n, 0);
+    std::vector<int> st{0};
+    seen[0] = 1;
+    int cnt = 1;
+    while (!st.empty()) {
+        int v = st.back();
+        st.pop_back();
+        for (auto &e : adj[v])
+            if (!seen[e.first]) {
+                seen[e.first] = 1;
+                ++cnt;
+                st.push_back(e.first);
+            }
+    }
+    return cnt == n;
+}
+
+static std::vector<char> bridges(int n, int m, const std::vector<std::vector<std::pair<int, int>>> &adj) {
+    std::vector<char> is_bridge(m, 0);
+    std::vector<int> disc(n, -1), low(n, 0);
+    int t = 0;
+    struct Frame { int v, pe; size_t i; };
+    for (int root = 0; root < n; ++root) {
+        if (disc[root] >= 0) continue;
+        std::vector<Frame> st{{root, -1, 0}};
+        disc[root] = low[root] = t++;
+        while (!st.empty()) {
+            Frame &f = st.back();
+            if (f.i < adj[f.v].size()) {
+                auto [w, e] = adj[f.v][f.i++];
+                if (e == f.pe) continue;
+                if (disc[w] < 0) {
+                    disc[w] = low[w] = t++;
+                    st.push_back({w, e, 0});
+                } else {
+                    low[f.v] = std::min(low[f.v], disc[w]);
+                }
+            } else {
+                int v = f.v, pe = f.pe;
+                st.pop_back();
+                if (!st.empty()) {
+                    int u = st.back().v;
+                    low[u] = std::min(low[u], low[v]);
+                    if (low[v] > disc[u]) is_bridge[pe] = 1;
+                }
+            }
+        }
+    }
+    return is_bridge;
+}
+
+static int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+// worst-case relative excess of a round-up sum accumulated in levels of
+// n1, n2, n3 terms: (1 + 2u)^(n1 + n2 + n3) - 1, with slack
+static float rup_gamma(long n1, long n2, long n3) {
+    const double u = std::ldexp(1.0, -24);
+    const double n = (double)(n1 + n2 + n3 + 2);
+    return (float)(std::expm1(n * std::log1p(2 * u)) * 1.01);
+}
+
+// ----------------------------------------------------------------- tensor maps
+namespace ibp {
+bool encode_map_2d(CUtensorMap *map, const float *base, int64_t inner, int64_t outer,
+                   int64_t row_stride_elems, int box_inner, int box_outer, std::string *err) {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void *p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !p) {
+            *err = "cuTensorMapEncodeTiled is not available";
+            return false;
+        }
+        fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
+    cuuint64_t strides[1] = {(cuuint64_t)(row_stride_elems * sizeof(float))};
+    cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_outer};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dims, strides,
+                    box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        *err = "cuTensorMapEncodeTiled failed with code " + std::to_string((int)r);
+        return false;
+    }
+    return true;
+}
+}  // namespace ibp
+
+// ----------------------------------------------------------------- the build
+static ibp_status build_sensitivities(ibp_case *c, const std::vector<int> &from,
+                                      const std::vector<int> &to, const double *x,
+                                      const std::vector<int> &active) {
+    const int nb_r = c->n_bus - 1;
+    const int n_l = c->n_line, n_c = c->n_ctg;
+    std::vector<int> red(c->n_bus, -1);
+    for (int b = 0, r = 0; b < c->n_bus; ++b)
+        if (b != c->slack) red[b] = r++;
+
+    // reduced admittance Y_B,r = E_r^T Y_D E_r (eq. (line flow ptdf)), as COO
+    std::map<std::pair<int, int>, double> Y;
+    for (int l = 0; l < n_l; ++l) {
+        const double b = 1.0 / x[l];
+        const int i = red[from[l]], j = red[to[l]];
+        if (i >= 0) Y[{i, i}] += b;
+        if (j >= 0) Y[{j, j}] += b;
+        if (i >= 0 && j >= 0) {
+            Y[{i, j}] -= b;
+            Y[{j, i}] -= b;
+        }
+    }
+    std::vector<int> yr, yc;
+    std::vector<double> yv;
+    for (auto &kv : Y) {
+        yr.push_back(kv.first.first);
+        yc.push_back(kv.first.second);
+        yv.push_back(kv.second);
+    }
+    // right-hand sides E_r^T Y_D: column l has b_l at from, -b_l at to
+    std::vector<int> rr, rc;
+    std::vector<double> rv;
+    for (int l = 0; l < n_l; ++l) {
+        const double b = 1.0 / x[l];
+        if (red[from[l]] >= 0) { rr.push_back(red[from[l]]); rc.push_back(l); rv.push_back(b); }
+        if (red[to[l]] >= 0) { rr.push_back(red[to[l]]); rc.push_back(l); rv.push_back(-b); }
+    }
+
+    cudaStream_t s = nullptr;
+    DevBuf<double> dY, dZ, dV1, dV2;
+    DevBuf<int> dI1, dI2, dI3, dI4, dinfo;
+    CUDA_TRY(dY.alloc((size_t)nb_r * nb_r));
+    CUDA_TRY(dZ.alloc((size_t)nb_r * n_l));
+    CUDA_TRY(cudaMemsetAsync(dY.p, 0, (size_t)nb_r * nb_r * sizeof(double), s));
+    CUDA_TRY(cudaMemsetAsync(dZ.p, 0, (size_t)nb_r * n_l * sizeof(double), s));
+    CUDA_TRY(dV1.alloc(yv.size()));
+    CUDA_TRY(dI1.alloc(yv.size()));
+    CUDA_TRY(dI2.alloc(yv.size()));
+    CUDA_TRY(cudaMemcpy(dV1.p, yv.data(), yv.size() * sizeof(double), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(dI1.p, yr.data(), yr.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(dI2.p, yc.data(), yc.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CUDA_TRY(launch_scatter_dense(dY.p, nb_r, dI1.p, dI2.p, dV1.p, (int)yv.size(), s));
+    CUDA_TRY(dV2.alloc(rv.size()));
+    CUDA_TRY(dI3.alloc(rv.size()));
+    CUDA_TRY(dI4.alloc(rv.size()));
+    CUDA_TRY(cudaMemcpy(dV2.p, rv.data(), rv.size() * sizeof(double), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(dI3.p, rr.data(), rr.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(dI4.p, rc.data(), rc.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CUDA_TRY(launch_scatter_dense(dZ.p, nb_r, dI3.p, dI4.p, dV2.p, (int)rv.size(), s));
+
+    // Cholesky of the SPD reduced Laplacian, then Z = Y^-1 E_r^T Y_D = Phi_r^T
+    cusolverDnHandle_t h = nullptr;
+    if (cusolverDnCreate(&h) != CUSOLVER_STATUS_SUCCESS) return fail(IBP_ECUDA, "cusolverDnCreate failed");
+    std::unique_ptr<cusolverDnContext, decltype(&cusolverDnDestroy)> hg(h, cusolverDnDestroy);
+    int lwork = 0;
+    if (cusolverDnDpotrf_bufferSize(h, CUBLAS_FILL_MODE_LOWER, nb_r, dY.p, nb_r, &lwork) !=
+        CUSOLVER_STATUS_SUCCESS)
+        return fail(IBP_ECUDA, "cusolverDnDpotrf_bufferSize failed");
+    DevBuf<double> work;
+    CUDA_TRY(work.alloc((size_t)std::max(lwork, 1)));
+    CUDA_TRY(dinfo.alloc(1));
+    if (cusolverDnDpotrf(h, CUBLAS_FILL_MODE_LOWER, nb_r, dY.p, nb_r, work.p, lwork, dinfo.p) !=
+        CUSOLVER_STATUS_SUCCESS)
+        return fail(IBP_ECUDA, "cusolverDnDpotrf failed");
+    int info = 0;
+    CUDA_TRY(cudaMemcpy(&info, dinfo.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (info != 0)
+        return fail(IBP_ESINGULAR, "Cholesky of the reduced admittance failed (info=%d)", info);
+    if (cusolverDnDpotrs(h, CUBLAS_FILL_MODE_LOWER, nb_r, n_l, dY.p, nb_r, dZ.p, nb_r, dinfo.p) !=
+        CUSOLVER_STATUS_SUCCESS)
+        return fail(IBP_ECUDA, "cusolverDnDpotrs failed");
+    CUDA_TRY(cudaMemcpy(&info, dinfo.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (info != 0) return fail(IBP_ESINGULAR, "Cholesky solve failed (info=%d)", info);
+    work.free();
+    dY.free();
+
+    // FP32 PTDF of the active buses
+    std::vector<int> act_red(active.size());
+    for (size_t i = 0; i < active.size(); ++i) act_red[i] = red[active[i]];
+    DevBuf<int> dact;
+    CUDA_TRY(dact.alloc(act_red.size()));
+    if (!act_red.empty())
+        CUDA_TRY(cudaMemcpy(dact.p, act_red.data(), act_red.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CUDA_TRY(c->phi_a.alloc((size_t)n_l * c->n_a_pad));
+    CUDA_TRY(launch_extract_phi(dZ.p, nb_r, n_l, dact.p, c->n_a, c->n_a_pad, c->phi_a.p, s));
+
+    // LODF of the contingency list
+    CUDA_TRY(c->lodf.alloc((size_t)std::max(n_c, 1) * n_l));
+    if (n_c > 0) {
+        std::vector<int> cf(n_c), ct(n_c);
+        for (int k = 0; k < n_c; ++k) {
+            cf[k] = red[from[c->ctg_line_h[k]]];
+            ct[k] = red[to[c->ctg_line_h[k]]];
+        }
+        DevBuf<int> dcf, dct;
+        DevBuf<double> dden;
+        DevBuf<float> dmax;
+        CUDA_TRY(dcf.alloc(n_c));
+        CUDA_TRY(dct.alloc(n_c));
+        CUDA_TRY(dden.alloc(n_c));
+        CUDA_TRY(dmax.alloc(1));
+        CUDA_TRY(cudaMemcpy(dcf.p, cf.data(), n_c * sizeof(int), cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(dct.p, ct.data(), n_c * sizeof(int), cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemset(dmax.p, 0, sizeof(float)));
+        CUDA_TRY(launch_lodf(dZ.p, nb_r, n_l, n_c, dcf.p, dct.p, c->ctg_line.p, c->lodf.p, dden.p,
+                             dmax.p, s));
+        std::vector<double> den(n_c);
+        float mx = 0;
+        CUDA_TRY(cudaMemcpy(den.data(), dden.p, n_c * sizeof(double), cudaMemcpyDeviceToHost));
+        CUDA_TRY(cudaMemcpy(&mx, dmax.p, sizeof(float), cudaMemcpyDeviceToHost));
+        for (int k = 0; k < n_c; ++k)
+            if (!(std::fabs(den[k]) > 1e-9))
+                return fail(IBP_EISLAND, "contingency %d (line %d) islands the network", k,
+                            c->ctg_line_h[k]);
+        c->max_abs_lodf = mx;
+    }
+    CUDA_TRY(cudaDeviceSynchronize());
+    return IBP_OK;
+}
+
+// ----------------------------------------------------------------- create
+extern "C" ibp_status ibp_case_create(int32_t n_bus, int32_t slack_bus, int32_t n_line,
+                                      const int32_t *line_from, const int32_t *line_to,
+                                      const double *reactance, const double *rating,
+                                      const double *rating_ctg, int32_t n_gen,
+                                      const int32_t *gen_bus, const int32_t *gen_nseg,
+                                      const double *gen_slope, const double *gen_bkpt,
+                                      int32_t n_load, const int32_t *load_bus,
+                                      const int32_t *load_nseg, const double *load_slope,
+                                      const double *load_bkpt, double zeta_inj, double zeta_f,
+                                      int32_t n_ctg, const int32_t *ctg_line, int32_t device,
+                                      ibp_case **out) {
+    if (!out) return fail(IBP_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (n_bus < 2) return fail(IBP_EINVAL, "n_bus must be >= 2");
+    if (slack_bus < 0 || slack_bus >= n_bus) return fail(IBP_EINVAL, "slack_bus out of range");
+    if (n_line < 1) return fail(IBP_EINVAL, "n_line must be >= 1");
+    if (n_gen < 0 || n_load < 0 || n_gen + n_load < 1)
+        return fail(IBP_EINVAL, "need n_gen, n_load >= 0 and at least one device");
+    if (n_ctg < 0) return fail(IBP_EINVAL, "n_ctg must be >= 0");
+    if (!line_from || !line_to || !reactance || !rating)
+        return fail(IBP_EINVAL, "line arrays must not be NULL");
+    if ((n_gen > 0 && (!gen_bus || !gen_nseg || !gen_slope || !gen_bkpt)) ||
+        (n_load > 0 && (!load_bus || !load_nseg || !load_slope || !load_bkpt)))
+        return fail(IBP_EINVAL, "device arrays must not be NULL");
+    if (n_ctg > 0 && !ctg_line) return fail(IBP_EINVAL, "ctg_line is NULL");
+    if (!is_fin(zeta_inj) || !is_fin(zeta_f) || zeta_inj < 0 || zeta_f < 0)
+        return fail(IBP_EINVAL, "penalty prices must be finite and >= 0");
+    for (int l = 0; l < n_line; ++l) {
+        if (line_from[l] < 0 || line_from[l] >= n_bus || line_to[l] < 0 || line_to[l] >= n_bus)
+            return fail(IBP_EINVAL, "line %d has a bus index out of range", l);
+        if (line_from[l] == line_to[l]) return fail(IBP_EINVAL, "line %d is a self loop", l);
+        if (!is_fin(reactance[l]) || !(reactance[l] > 0))
+            return fail(IBP_EINVAL, "reactance[%d] must be finite and > 0", l);
+        if (!is_fin(rating[l]) || rating[l] < 0)
+            return fail(IBP_EINVAL, "rating[%d] must be finite and >= 0", l);
+        if (rating_ctg && (!is_fin(rating_ctg[l]) || rating_ctg[l] < 0))
+            return fail(IBP_EINVAL, "rating_ctg[%d] must be finite and >= 0", l);
+    }
+    for (int i = 0; i < n_gen; ++i)
+        if (gen_bus[i] < 0 || gen_bus[i] >= n_bus) return fail(IBP_EINVAL, "gen_bus[%d] out of range", i);
+    for (int i = 0; i < n_load; ++i)
+        if (load_bus[i] < 0 || load_bus[i] >= n_bus) return fail(IBP_EINVAL, "load_bus[%d] out of range", i);
+    for (int k = 0; k < n_ctg; ++k)
+        if (ctg_line[k] < 0 || ctg_line[k] >= n_line) return fail(IBP_EINVAL, "ctg_line[%d] out of range", k);
+    std::vector<int> gptr, lptr;
+    ibp_status st;
+    if ((st = check_pwl("gen", n_gen, gen_nseg, gen_slope, gen_bkpt, gptr)) != IBP_OK) return st;
+    if ((st = check_pwl("load", n_load, load_nseg, load_slope, load_bkpt, lptr)) != IBP_OK) return st;
+
+    // graph checks on the host, before any device work
+    std::vector<std::vector<std::pair<int, int>>> adj(n_bus);
+    for (int l = 0; l < n_line; ++l) {
+        adj[line_from[l]].push_back({line_to[l], l});
+        adj[line_to[l]].push_back({line_from[l], l});
+    }
+    if (!connected(n_bus, adj)) return fail(IBP_EISLAND, "the network is not connected");
+    const std::vector<char> br = bridges(n_bus, n_line, adj);
+    for (int k = 0; k < n_ctg; ++k)
+        if (br[ctg_line[k]])
+            return fail(IBP_EISLAND, "contingency %d outages bridge line %d (islanding)", k, ctg_line[k]);
+
+    std::unique_ptr<ibp_case> c(new ibp_case());
+    c->n_bus = n_bus;
+    c->slack = slack_bus;
+    c->n_line = n_line;
+    c->n_gen = n_gen;
+    c->n_load = n_load;
+    c->n_dev = n_gen + n_load;
+    c->n_ctg = n_ctg;
+    c->zeta_inj = zeta_inj;
+    c->zeta_f = zeta_f;
+    c->ctg_line_h.assign(ctg_line, ctg_line + n_ctg);
+
+    // active bus columns: buses with a device, slack excluded, in bus order
+    std::vector<std::vector<int>> devs_at(n_bus);
+    for (int i = 0; i < n_gen; ++i) devs_at[gen_bus[i]].push_back(i);
+    for (int i = 0; i < n_load; ++i) devs_at[load_bus[i]].push_back(n_gen + i);
+    std::vector<int> active, aptr{0}, adev;
+    for (int b = 0; b < n_bus; ++b) {
+        if (b == slack_bus || devs_at[b].empty()) continue;
+        active.push_back(b);
+        for (int d : devs_at[b]) adev.push_back(d);
+        aptr.push_back((int)adev.size());
+    }
+    c->n_a = (int)active.size();
+    c->n_a_pad = round_up(std::max(c->n_a, 1), 32);
+
+    if (device < 0) {  // dry run: validation only
+        c->device = -1;
+        *out = c.release();
+        return ok();
+    }
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0)
+        return fail(IBP_ECUDA, "no CUDA device is available");
+    if (device >= ndev) return fail(IBP_EINVAL, "device %d out of range (%d devices)", device, ndev);
+    DeviceGuard guard(device);
+    if (!guard.ok) return fail(IBP_ECUDA, "cannot select device %d", device);
+    c->device = device;
+    CUDA_TRY(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device));
+
+    const auto t0 = std::chrono::steady_clock::now();
+    // small persistent arrays
+    auto up32 = [](double v) {
+        float f = (float)v;
+        return (double)f < v ? std::nextafter(f, INFINITY) : f;
+    };
+    auto dn32 = [](double v) {
+        float f = (float)v;
+        return (double)f > v ? std::nextafter(f, -INFINITY) : f;
+    };
+    std::vector<float> ru(n_line), rd(n_line), rcu(n_line), rcd(n_line);
+    for (int l = 0; l < n_line; ++l) {
+        ru[l] = up32(rating[l]);
+        rd[l] = dn32(rating[l]);
+        const double rc = rating_ctg ? rating_ctg[l] : rating[l];
+        rcu[l] = up32(rc);
+        rcd[l] = dn32(rc);
+    }
+    CUDA_TRY(c->rate_up.alloc(n_line));
+    CUDA_TRY(c->rate_dn.alloc(n_line));
+    CUDA_TRY(c->rate_c_up.alloc(n_line));
+    CUDA_TRY(c->rate_c_dn.alloc(n_line));
+    CUDA_TRY(cudaMemcpy(c->rate_up.p, ru.data(), n_line * sizeof(float), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(c->rate_dn.p, rd.data(), n_line * sizeof(float), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(c->rate_c_up.p, rcu.data(), n_line * sizeof(float), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(c->rate_c_dn.p, rcd.data(), n_line * sizeof(float), cudaMemcpyHostToDevice));
+    CUDA_TRY(c->ctg_line.alloc(std::max(n_ctg, 1)));
+    if (n_ctg > 0)
+        CUDA_TRY(cudaMemcpy(c->ctg_line.p, ctg_line, n_ctg * sizeof(int), cudaMemcpyHostToDevice));
+    CUDA_TRY(c->act_ptr.alloc(aptr.size()));
+    CUDA_TRY(cudaMemcpy(c->act_ptr.p, aptr.data(), aptr.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CUDA_TRY(c->act_dev.alloc(std::max<size_t>(adev.size(), 1)));
+    if (!adev.empty())
+        CUDA_TRY(cudaMemcpy(c->act_dev.p, adev.data(), adev.size() * sizeof(int), cudaMemcpyHostToDevice));
+    std::vector<int> sp(c->n_dev + 1, 0);
+    std::vector<double> sl, bk;
+    for (int i = 0; i < n_gen; ++i) {
+        for (int m = gptr[i]; m < gptr[i + 1]; ++m) { sl.push_back(gen_slope[m]); bk.push_back(gen_bkpt[m]); }
+        sp[i + 1] = (int)sl.size();
+    }
+    for (int i = 0; i < n_load; ++i) {
+        for (int m = lptr[i]; m < lptr[i + 1]; ++m) { sl.push_back(load_slope[m]); bk.push_back(load_bkpt[m]); }
+        sp[n_gen + i + 1] = (int)sl.size();
+    }
+    CUDA_TRY(c->seg_ptr.alloc(sp.size()));
+    CUDA_TRY(c->slope.alloc(sl.size()));
+    CUDA_TRY(c->bkpt.alloc(bk.size()));
+    CUDA_TRY(cudaMemcpy(c->seg_ptr.p, sp.data(), sp.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(c->slope.p, sl.data(), sl.size() * sizeof(double), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(c->bkpt.p, bk.data(), bk.size() * sizeof(double), cudaMemcpyHostToDevice));
+    CUDA_TRY(c->err.alloc(1));
+
+    std::vector<int> from(line_from, line_from + n_line), to(line_to, line_to + n_line);
+    if ((st = build_sensitivities(c.get(), from, to, reactance, active)) != IBP_OK) return st;
+    c->build_seconds =
+        std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    for (auto &e : c->ev) CUDA_TRY(cudaEventCreate(&e));
+    c->n_part_base = base_partials_count(c->num_sms);
+    *out = c.release();
+    return ok();
+}
+
+extern "C" void ibp_case_destroy(ibp_case *c) { delete c; }
+
+// ----------------------------------------------------------------- workspace
+static const CtgVariant *pick_variant(const ibp_case *c, int n_box) {
+    if (c->variant > 0) {
+        const CtgVariant *v = ctg_variant_by_id(c->variant);
+        if (v && (v->batched != 0) == (n_box > 1)) return v;
+    }
+    (void)n_box;
+    return ctg_variant_by_id(1);
+}
+
+static int max_tiles(const ibp_case *c) {
+    int n, best = 1;
+    const CtgVariant *v = ctg_variants(&n);
+    for (int i = 0; i < n; ++i) {
+        const int t = ((c->n_line + v[i].BL - 1) / v[i].BL) * ((std::max(c->n_ctg, 1) + v[i].BK - 1) / v[i].BK);
+        best = std::max(best, t);
+    }
+    return best;
+}
+
+static ibp_status ensure_workspace(ibp_case *c, int n_box) {
+    if (n_box <= c->cap_box) return IBP_OK;
+    const int cap = std::max(n_box, 1);
+    const size_t na = c->n_a_pad;
+    CUDA_TRY(c->box_lo.alloc((size_t)cap * c->n_dev));
+    CUDA_TRY(c->box_hi.alloc((size_t)cap * c->n_dev));
+    CUDA_TRY(c->obj.alloc((size_t)cap * 3));
+    CUDA_TRY(c->cbus.alloc(cap * na));
+    CUDA_TRY(c->rbus.alloc(cap * na));
+    CUDA_TRY(c->cabs.alloc(cap * na));
+    CUDA_TRY(c->box_consts.alloc((size_t)cap * 4));
+    CUDA_TRY(c->line_c.alloc((size_t)cap * c->n_line));
+    CUDA_TRY(c->line_e.alloc((size_t)cap * c->n_line));
+    CUDA_TRY(c->line_R.alloc((size_t)cap * c->n_line));
+    CUDA_TRY(c->part_base.alloc((size_t)c->n_part_base * cap * 3));
+    CUDA_TRY(c->part_ctg.alloc((size_t)max_tiles(c) * 8 * cap * 3));
+    c->cap_box = cap;
+    return IBP_OK;
+}
+
+// ----------------------------------------------------------------- bound
+static ibp_status enqueue_bound(ibp_case *c, int n_box, const double *lo, const double *hi,
+                                double *olo, double *ohi, double *oerr, float *flo, float *fhi,
+                                cudaStream_t s) {
+    ibp_status st = ensure_workspace(c, n_box);
+    if (st != IBP_OK) return st;
+    const CtgVariant *v = pick_variant(c, n_box);
+    if (!v) return fail(IBP_EINVAL, "no kernel variant");
+    if (n_box != 1) return fail(IBP_ENOTSUP, "more than one box per call is not built yet");
+    if (!c->hat_l.p) {
+        CUDA_TRY(c->hat_l.alloc((size_t)c->n_line * c->n_a_pad));
+        CUDA_TRY(c->hat_k.alloc((size_t)std::max(c->n_ctg, 1) * c->n_a_pad));
+    }
+    CUDA_TRY(cudaMemsetAsync(c->err.p, 0, sizeof(int), s));
+    if (c->timing) CUDA_TRY(cudaEventRecord(c->ev[0], s));
+
+    BusArgs ba{};
+    ba.n_a = c->n_a; ba.n_a_pad = c->n_a_pad; ba.n_dev = c->n_dev; ba.n_gen = c->n_gen; ba.n_box = n_box;
+    ba.act_ptr = c->act_ptr.p; ba.act_dev = c->act_dev.p; ba.box_lo = lo; ba.box_hi = hi;
+    ba.cbus = c->cbus.p; ba.rbus = c->rbus.p; ba.rbus_t = nullptr; ba.n_box_pad = 0;
+    ba.cabs = c->cabs.p; ba.box_consts = c->box_consts.p; ba.err = c->err.p;
+    CUDA_TRY(launch_bus(ba, s));
+    if (c->timing) CUDA_TRY(cudaEventRecord(c->ev[1], s));
+
+    BaseArgs bb{};
+    bb.n_l = c->n_line; bb.n_c = c->n_ctg; bb.n_a = c->n_a; bb.n_a_pad = c->n_a_pad; bb.n_box = n_box;
+    bb.phi = c->phi_a.p; bb.ctg_line = c->ctg_line.p; bb.cbus = c->cbus.p; bb.rbus = c->rbus.p;
+    bb.cabs = c->cabs.p; bb.rate_up = c->rate_up.p; bb.rate_dn = c->rate_dn.p;
+    bb.box_consts = c->box_consts.p;
+    bb.gamma_base = rup_gamma((c->n_a_pad / 4 + 31) / 32, 2, 5);
+    bb.line_c = c->line_c.p; bb.line_e = c->line_e.p; bb.line_R = c->line_R.p;
+    bb.hat_l = c->hat_l.p; bb.hat_k = c->hat_k.p; bb.partials = c->part_base.p;
+    CUDA_TRY(launch_base(bb, c->n_part_base, s));
+    if (c->timing) CUDA_TRY(cudaEventRecord(c->ev[2], s));
+
+    const int tiles_l = (c->n_line + v->BL - 1) / v->BL;
+    const int tiles_k = (c->n_ctg + v->BK - 1) / v->BK;
+    const int n_chunks = (c->n_a + 31) / 32;
+    CtgArgs ca{};
+    ca.n_l = c->n_line; ca.n_c = c->n_ctg; ca.n_a = c->n_a; ca.n_chunks = n_chunks; ca.n_box = n_box;
+    ca.tiles_l = tiles_l; ca.n_tiles = tiles_l * tiles_k;
+    ca.lodf = c->lodf.p; ca.ctg_line = c->ctg_line.p;
+    ca.line_c = c->line_c.p; ca.line_e = c->line_e.p; ca.line_R = c->line_R.p;
+    ca.rate_up = c->rate_c_up.p; ca.rate_dn = c->rate_c_dn.p; ca.box_consts = c->box_consts.p;
+    ca.rbus_t = nullptr; ca.n_box_pad = 0;
+    ca.gamma = rup_gamma(32, 8, (n_chunks + 7) / 8);
+    ca.flow_lo = flo; ca.flow_hi = fhi; ca.partials = c->part_ctg.p; ca.err = c->err.p;
+    ca.wait_ns = 2000000000ull;
+    if (ca.n_tiles > 0) {
+        CUtensorMap mL, mK;
+        std::string err;
+        if (!encode_map_2d(&mL, c->hat_l.p, c->n_a_pad, c->n_line, c->n_a_pad, 32, v->BL, &err) ||
+            !encode_map_2d(&mK, c->hat_k.p, c->n_a_pad, c->n_ctg, c->n_a_pad, 32, v->BK, &err))
+            return fail(IBP_ECUDA, "%s", err.c_str());
+        CUDA_TRY(launch_ctg(*v, mL, mK, ca, c->num_sms, s));
+    }
+    if (c->timing) CUDA_TRY(cudaEventRecord(c->ev[3], s));
+
+    AsmArgs aa{};
+    aa.n_box = n_box; aa.n_dev = c->n_dev; aa.n_gen = c->n_gen;
+    aa.n_part_ctg = ca.n_tiles * 8; aa.n_part_base = c->n_part_base;
+    aa.part_ctg = c->part_ctg.p; aa.part_base = c->part_base.p; aa.box_lo = lo; aa.box_hi = hi;
+    aa.seg_ptr = c->seg_ptr.p; aa.slope = c->slope.p; aa.bkpt = c->bkpt.p;
+    aa.zeta_inj = c->zeta_inj; aa.zeta_f = c->zeta_f;
+    aa.obj_lo = olo; aa.obj_hi = ohi; aa.obj_err = oerr; aa.err = c->err.p;
+    CUDA_TRY(launch_assemble(aa, s));
+    if (c->timing) CUDA_TRY(cudaEventRecord(c->ev[4], s));
+    return IBP_OK;
+}
+
+static ibp_status read_err_word(ibp_case *c) {
+    int e = 0;
+    CUDA_TRY(cudaMemcpy(&e, c->err.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e & kErrTimeout) return fail(IBP_ETIMEOUT, "a bounded device wait ran out");
+    if (e & kErrBadBox) return fail(IBP_EINVAL, "a box has lo > hi or a non-finite entry");
+    return IBP_OK;
+}
+
+static ibp_status check_boxes_host(const ibp_case *c, int n_box, const double *lo, const double *hi) {
+    const size_t n = (size_t)n_box * c->n_dev;
+    for (size_t i = 0; i < n; ++i) {
+        if (!is_fin(lo[i]) || !is_fin(hi[i]))
+            return fail(IBP_EINVAL, "box entry %zu (box %zu, device %zu) is not finite", i, i / c->n_dev,
+                        i % c->n_dev);
+        if (lo[i] > hi[i])
+            return fail(IBP_EINVAL, "box %zu device %zu has lo > hi", i / c->n_dev, i % c->n_dev);
+    }
+    return IBP_OK;
+}
+
+extern "C" ibp_status ibp_bound(ibp_case *c, int32_t n_box, const double *box_lo,
+                                const double *box_hi, double *obj_lo, double *obj_hi,
+                                double *obj_err, float *flow_lo, float *flow_hi, int32_t ptr_mode,
+                                void *cuda_stream) {
+    if (!c) return fail(IBP_EINVAL, "case is NULL");
+    if (n_box < 0) return fail(IBP_EINVAL, "n_box must be >= 0");
+    if (ptr_mode != 0 && ptr_mode != 1) return fail(IBP_EINVAL, "ptr_mode must be 0 or 1");
+    if (n_box == 0) return ok();
+    if (!box_lo || !box_hi || !obj_lo || !obj_hi || !obj_err)
+        return fail(IBP_EINVAL, "box and objective pointers must not be NULL");
+    if ((flow_lo == nullptr) != (flow_hi == nullptr))
+        return fail(IBP_EINVAL, "flow_lo and flow_hi must both be NULL or both be set");
+    if (ptr_mode == 0) {
+        ibp_status st = check_boxes_host(c, n_box, box_lo, box_hi);
+        if (st != IBP_OK) return st;
+    }
+    if (c->device < 0) return fail(IBP_ENOTSUP, "case was created without a device (dry run)");
+    DeviceGuard guard(c->device);
+    if (!guard.ok) return fail(IBP_ECUDA, "cannot select device %d", c->device);
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    if (ptr_mode == 1)
+        return enqueue_bound(c, n_box, box_lo, box_hi, obj_lo, obj_hi, obj_err, flow_lo, flow_hi, s);
+
+    ibp_status st = ensure_workspace(c, n_box);
+    if (st != IBP_OK) return st;
+    const size_t nd = (size_t)n_box * c->n_dev;
+    CUDA_TRY(cudaMemcpyAsync(c->box_lo.p, box_lo, nd * sizeof(double), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(c->box_hi.p, box_hi, nd * sizeof(double), cudaMemcpyHostToDevice, s));
+    float *dflo = nullptr, *dfhi = nullptr;
+    const size_t nf = (size_t)n_box * c->n_ctg * c->n_line;
+    if (flow_lo && nf > 0) {
+        if (c->flows.n < 2 * nf) CUDA_TRY(c->flows.alloc(2 * nf));
+        dflo = c->flows.p;
+        dfhi = c->flows.p + nf;
+    }
+    double *dobj = c->obj.p;
+    st = enqueue_bound(c, n_box, c->box_lo.p, c->box_hi.p, dobj, dobj + n_box, dobj + 2 * n_box,
+                       dflo, dfhi, s);
+    if (st != IBP_OK) return st;
+    CUDA_TRY(cudaMemcpyAsync(obj_lo, dobj, n_box * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(obj_hi, dobj + n_box, n_box * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(obj_err, dobj + 2 * n_box, n_box * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (dflo) {
+        CUDA_TRY(cudaMemcpyAsync(flow_lo, dflo, nf * sizeof(float), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaMemcpyAsync(flow_hi, dfhi, nf * sizeof(float), cudaMemcpyDeviceToHost, s));
+    }
+    CUDA_TRY(cudaStreamSynchronize(s));
+    st = read_err_word(c);
+    if (st != IBP_OK) return st;
+    return ok();
+}
+
+extern "C" ibp_status ibp_bound_backward(ibp_case *c, int32_t n_box, const double *, const double *,
+                                         const double *, double *, double *, double *, int32_t, void *) {
+    if (!c) return fail(IBP_EINVAL, "case is NULL");
+    if (n_box < 0) return fail(IBP_EINVAL, "n_box must be >= 0");
+    return fail(IBP_ENOTSUP, "ibp_bound_backward is not built yet");
+}
+
+extern "C" ibp_status ibp_bound_multi(int32_t n_case, ibp_case *const *, const int32_t *,
+                                      const double *const *, const double *const *, double *const *,
+                                      double *const *, double *const *, void *) {
+    if (n_case < 0) return fail(IBP_EINVAL, "n_case must be >= 0");
+    return fail(IBP_ENOTSUP, "ibp_bound_multi is not built yet");
+}
+
+extern "C" ibp_status ibp_case_sync(ibp_case *c) {
+    if (!c) return fail(IBP_EINVAL, "case is NULL");
+    if (c->device < 0) return fail(IBP_ENOTSUP, "case was created without a device (dry run)");
+    DeviceGuard guard(c->device);
+    CUDA_TRY(cudaDeviceSynchronize());
+    ibp_status st = read_err_word(c);
+    if (st != IBP_OK) return st;
+    return ok();
+}
+
+extern "C" ibp_status ibp_case_info(const ibp_case *c, ibp_case_info_t *o) {
+    if (!c || !o) return fail(IBP_EINVAL, "NULL argument");
+    o->n_bus = c->n_bus; o->n_line = c->n_line; o->n_ctg = c->n_ctg; o->n_gen = c->n_gen;
+    o->n_load = c->n_load; o->n_active = c->n_a; o->n_active_pad = c->n_a_pad; o->device = c->device;
+    int64_t bytes = 0;
+    bytes += (int64_t)c->phi_a.n * 4 + (int64_t)c->lodf.n * 4 + (int64_t)c->hat_l.n * 4 + (int64_t)c->hat_k.n * 4;
+    bytes += (int64_t)(c->cbus.n + c->part_base.n + c->part_ctg.n + c->box_lo.n + c->box_hi.n) * 8;
+    bytes += (int64_t)(c->rbus.n + c->cabs.n + c->line_c.n + c->line_e.n + c->line_R.n + c->flows.n) * 4;
+    o->device_bytes = bytes;
+    o->build_seconds = c->build_seconds;
+    o->max_abs_lodf = c->max_abs_lodf;
+    return ok();
+}
+
+extern "C" ibp_status ibp_case_set_variant(ibp_case *c, int32_t variant) {
+    if (!c) return fail(IBP_EINVAL, "case is NULL");
+    if (variant != 0 && !ctg_variant_by_id(variant)) return fail(IBP_EINVAL, "unknown variant %d", variant);
+    c->variant = variant;
+    return ok();
+}
+
+extern "C" int32_t ibp_kernel_variants(int32_t *ids, int32_t cap, int32_t batched) {
+    int n;
+    const CtgVariant *v = ctg_variants(&n);
+    int32_t k = 0;
+    for (int i = 0; i < n; ++i) {
+        if ((v[i].batched != 0) != (batched != 0)) continue;
+        if (ids && k < cap) ids[k] = v[i].id;
+        ++k;
+    }
+    return k;
+}
+
+extern "C" ibp_status ibp_case_set_timing(ibp_case *c, int32_t enable) {
+    if (!c) return fail(IBP_EINVAL, "case is NULL");
+    if (c->device < 0) return fail(IBP_ENOTSUP, "dry-run case");
+    c->timing = enable != 0;
+    return ok();
+}
+
+extern "C" ibp_status ibp_case_last_timing(ibp_case *c, float *ms, int32_t n) {
+    if (!c || !ms) return fail(IBP_EINVAL, "NULL argument");
+    if (!c->timing) return fail(IBP_EINVAL, "timing is not enabled");
+    DeviceGuard guard(c->device);
+    CUDA_TRY(cudaEventSynchronize(c->ev[4]));
+    for (int i = 0; i < std::min<int>(n, 4); ++i) CUDA_TRY(cudaEventElapsedTime(&ms[i], c->ev[i], c->ev[i + 1]));
+    return ok();
+}
+
+extern "C" ibp_status ibp_selftest_wait_timeout(int32_t device, int32_t limit_us) {
+    if (limit_us <= 0 || limit_us > 2000000) return fail(IBP_EINVAL, "limit_us out of (0, 2e6]");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+        return fail(IBP_ECUDA, "no such CUDA device");
+    DeviceGuard guard(device);
+    DevBuf<int> flag;
+    CUDA_TRY(flag.alloc(1));
+    CUDA_TRY(cudaMemset(flag.p, 0xff, sizeof(int)));
+    CUDA_TRY(launch_wait_selftest(flag.p, (unsigned long long)limit_us * 1000ull, nullptr));
+    CUDA_TRY(cudaDeviceSynchronize());
+    int f = 0;
+    CUDA_TRY(cudaMemcpy(&f, flag.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (f == kErrTimeout) return fail(IBP_ETIMEOUT, "wait ran out after %d us (expected)", limit_us);
+    if (f == 0) return ok();
+    return fail(IBP_ECUDA, "self-test kernel did not report");
+}
+
+extern "C" const char *ibp_last_error(void) { return g_last_error.c_str(); }
+
+extern "C" const char *ibp_status_string(ibp_status s) {
+    switch (s) {
+    case IBP_OK: return "IBP_OK";
+    case IBP_EINVAL: return "IBP_EINVAL";
+    case IBP_EISLAND: return "IBP_EISLAND";
+    case IBP_ESINGULAR: return "IBP_ESINGULAR";
+    case IBP_ENOMEM: return "IBP_ENOMEM";
+    case IBP_ECUDA: return "IBP_ECUDA";
+    case IBP_ETIMEOUT: return "IBP_ETIMEOUT";
+    case IBP_EUNSOUND: return "IBP_EUNSOUND";
+    case IBP_ENOTSUP: return "IBP_ENOTSUP";
+    }
+    return "unknown";
+}

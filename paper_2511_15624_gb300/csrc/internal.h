@@ -1,0 +1,120 @@
+// Internal declarations shared by the ABI implementation and the kernel launchers.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include "../../include/ibp.h"
+
+namespace ibp {
+
+// error word bits (device -> host)
+constexpr int kErrTimeout = 1;
+constexpr int kErrBadBox = 2;
+
+// ---------------------------------------------------------------- kernel args
+struct BusArgs {
+    int n_a, n_a_pad, n_dev, n_gen, n_box;
+    const int *act_ptr;     // [n_a + 1] CSR over active bus columns
+    const int *act_dev;     // device indices (gens < n_gen are +, loads are -)
+    const double *box_lo;   // [n_box][n_dev]
+    const double *box_hi;
+    double *cbus;           // [n_box][n_a_pad] bus injection centre (FP64)
+    float *rbus;            // [n_box][n_a_pad] radius, rounded up
+    float *rbus_t;          // [n_a_pad][n_box_pad] transposed radius (or null)
+    int n_box_pad;
+    float *cabs;            // [n_box][n_a_pad] |centre| rounded up
+    float *box_consts;      // [n_box][4] eta_r, eta_c, sum r, sum |c|
+    int *err;
+};
+
+struct BaseArgs {
+    int n_l, n_c, n_a, n_a_pad, n_box;
+    const float *phi;        // [n_l][n_a_pad]
+    const int *ctg_line;     // [n_c]
+    const double *cbus;
+    const float *rbus;
+    const float *cabs;
+    const float *rate_up;    // base ratings rounded up / down
+    const float *rate_dn;
+    const float *box_consts;
+    float gamma_base;        // worst-case relative excess of the RU radius sums
+    float *line_c;           // [n_box][n_l] FP32 centre of the base flow
+    float *line_e;           // [n_box][n_l] bound on the centre's error
+    float *line_R;           // [n_box][n_l] radius sum, rounded up
+    float *hat_l;            // [n_l][n_a_pad] Phi * r (one-box mode) or null
+    float *hat_k;            // [n_c][n_a_pad] Phi[ctg line] * r or null
+    double *partials;        // [n_part][n_box][3]
+};
+
+struct CtgArgs {
+    int n_l, n_c, n_a, n_chunks, n_box;
+    int tiles_l, n_tiles;
+    const float *lodf;       // [n_c][n_l]
+    const int *ctg_line;     // [n_c]
+    const float *line_c, *line_e, *line_R;  // [n_box][n_l]
+    const float *rate_up, *rate_dn;         // contingency ratings
+    const float *box_consts;                // [n_box][4]
+    const float *rbus_t;     // [n_a_pad][n_box_pad] (batched kernel)
+    int n_box_pad;
+    float gamma;             // worst-case relative excess of the RU radius sums
+    float *flow_lo, *flow_hi;  // [n_box][n_c][n_l] or null
+    double *partials;        // [n_tiles * 8][n_box][3]
+    int *err;
+    unsigned long long wait_ns;
+};
+
+struct AsmArgs {
+    int n_box, n_dev, n_gen;
+    int n_part_ctg, n_part_base;
+    const double *part_ctg;   // [n_part_ctg][n_box][3]
+    const double *part_base;  // [n_part_base][n_box][3]
+    const double *box_lo, *box_hi;
+    const int *seg_ptr;       // [n_dev + 1]
+    const double *slope, *bkpt;
+    double zeta_inj, zeta_f;
+    double *obj_lo, *obj_hi, *obj_err;
+    const int *err;
+};
+
+// ----------------------------------------------------------- kernel variants
+struct CtgVariant {
+    int id;
+    int batched;     // 0: one-box scaled kernel, 1: multi-box kernel
+    int BL, BK, CH, ST;
+    int boxes_per_thread;
+    const char *name;
+};
+
+const CtgVariant *ctg_variants(int *count);
+const CtgVariant *ctg_variant_by_id(int id);
+
+// launchers (return cudaError_t of the launch)
+cudaError_t launch_bus(const BusArgs &a, cudaStream_t s);
+cudaError_t launch_base(const BaseArgs &a, int n_part, cudaStream_t s);
+int base_partials_count(int num_sms);
+cudaError_t launch_ctg(const CtgVariant &v, const CUtensorMap &mL, const CUtensorMap &mK,
+                       const CtgArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_assemble(const AsmArgs &a, cudaStream_t s);
+cudaError_t launch_wait_selftest(int *flag, unsigned long long limit_ns, cudaStream_t s);
+
+// case-build kernels
+cudaError_t launch_scatter_dense(double *dst, int64_t ld, const int *rows, const int *cols,
+                                 const double *vals, int nnz, cudaStream_t s);
+cudaError_t launch_extract_phi(const double *Z, int nb_r, int n_l, const int *act_red, int n_a,
+                               int n_a_pad, float *phi_a, cudaStream_t s);
+cudaError_t launch_lodf(const double *Z, int nb_r, int n_l, int n_c, const int *ctg_from_red,
+                        const int *ctg_to_red, const int *ctg_line, float *lodf,
+                        double *den_out, float *maxabs_out, cudaStream_t s);
+cudaError_t launch_gather_rows(const float *src, int ld, const int *rows, int n_rows,
+                               float *dst, cudaStream_t s);
+
+// tensor maps
+bool encode_map_2d(CUtensorMap *map, const float *base, int64_t inner, int64_t outer,
+                   int64_t row_stride_elems, int box_inner, int box_outer, std::string *err);
+
+}  // namespace ibp

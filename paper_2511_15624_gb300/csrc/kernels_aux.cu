@@ -1,0 +1,476 @@
+// Box-to-bus, base-flow, objective-assembly and case-build kernels.
+//
+// Rounding: every quantity that enters a certified bound is computed with
+// directed rounding (round-up for upper bounds, round-down for lower bounds)
+// or carries an explicit error term; see the comment of each kernel.
+#include "common.cuh"
+#include "internal.h"
+
+#include <cfloat>
+
+namespace ibp {
+
+// ---------------------------------------------------------------------------
+// Box -> bus injection intervals.  IBP of p_inj = N_g p_g - N_d p_d
+// (Sec. II-A under eq. (IBP)): bus b lies in [P_lo, P_hi] with
+//   P_lo = sum_{g@b} lo_g - sum_{d@b} hi_d,  P_hi = sum_{g@b} hi_g - sum_{d@b} lo_d
+// (rounded down / up).  The centre c = (P_lo + P_hi)/2 may round; the radius
+// r = max(P_hi - c, c - P_lo) is rounded up, so [c - r, c + r] contains the
+// interval whatever c is.  One block per box.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_bus(BusArgs a) {
+    const int j = blockIdx.x;
+    const double *lo = a.box_lo + (size_t)j * a.n_dev;
+    const double *hi = a.box_hi + (size_t)j * a.n_dev;
+    float rsum = 0.0f, csum = 0.0f;
+    int bad = 0;
+    for (int d = threadIdx.x; d < a.n_dev; d += blockDim.x) {
+        const double x = lo[d], y = hi[d];
+        if (!(x <= y) || !isfinite(x) || !isfinite(y)) bad = 1;
+    }
+    for (int col = threadIdx.x; col < a.n_a_pad; col += blockDim.x) {
+        double c = 0.0;
+        float r32 = 0.0f, ca = 0.0f;
+        if (col < a.n_a) {
+            double plo = 0.0, phi = 0.0;
+            for (int p = a.act_ptr[col]; p < a.act_ptr[col + 1]; ++p) {
+                const int d = a.act_dev[p];
+                if (d < a.n_gen) {
+                    plo = __dadd_rd(plo, lo[d]);
+                    phi = __dadd_ru(phi, hi[d]);
+                } else {
+                    plo = __dadd_rd(plo, -hi[d]);
+                    phi = __dadd_ru(phi, -lo[d]);
+                }
+            }
+            c = 0.5 * (plo + phi);
+            const double r = fmax(__dadd_ru(phi, -c), __dadd_ru(c, -plo));
+            r32 = __double2float_ru(fmax(r, 0.0));
+            ca = __double2float_ru(fabs(c));
+        }
+        a.cbus[(size_t)j * a.n_a_pad + col] = c;
+        a.rbus[(size_t)j * a.n_a_pad + col] = r32;
+        a.cabs[(size_t)j * a.n_a_pad + col] = ca;
+        if (a.rbus_t) a.rbus_t[(size_t)col * a.n_box_pad + j] = r32;
+        rsum = __fadd_ru(rsum, r32);
+        csum = __fadd_ru(csum, ca);
+    }
+    __shared__ float sr[8], sc[8];
+    __shared__ int sbad[8];
+    rsum = warp_sum_ru_f(rsum);
+    csum = warp_sum_ru_f(csum);
+    bad = __any_sync(0xffffffffu, bad);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) {
+        sr[w] = rsum;
+        sc[w] = csum;
+        sbad[w] = bad;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float R = 0.0f, C = 0.0f;
+        int B = 0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+            R = __fadd_ru(R, sr[i]);
+            C = __fadd_ru(C, sc[i]);
+            B |= sbad[i];
+        }
+        // Absolute error allowances for FP32 underflow (entries of Phi and L
+        // below 2^-120 are stored as 0; products may be subnormal):
+        //   eta_r covers sum_b |dPhi| r_b and per-term subnormal rounding,
+        //   eta_c covers sum_b |dPhi| |c_b|.
+        const float t120 = 7.52316384526264e-37f;   // 2^-120
+        const float t99 = 1.5777218104420236e-30f;  // 2^-99
+        float *bc = a.box_consts + (size_t)j * 4;
+        bc[0] = __fadd_ru(__fmul_ru(t99, R), __fmul_ru(t120, (float)a.n_a));
+        bc[1] = __fmul_ru(t99, C);
+        bc[2] = R;
+        bc[3] = C;
+        if (B) atomicOr(a.err, kErrBadBox);
+    }
+}
+
+cudaError_t launch_bus(const BusArgs &a, cudaStream_t s) {
+    k_bus<<<a.n_box, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Base-case flows, one warp per line (eq. (line flow ptdf) under eq. (IBP)).
+// For line l and box j:
+//   centre   c_l = sum_b Phi~[l,b] c_b       FP64 accumulation, then FP32 RN
+//   C_l          = sum_b |Phi~[l,b]| |c_b|   FP32 round-up
+//   R_l          = sum_b |Phi~[l,b]| r_b     FP32 round-up
+// Phi~ is the FP32 copy of the FP64 PTDF (|Phi - Phi~| <= u |Phi~| + 2^-120),
+// so the exact centre from the FP64 data is within
+//   e_l = 2.1 u C_l + eta_c
+// of the FP32 centre (storage u(1+u) C_l, FP64 sum <= 1e-12 C_l, final RN
+// u |c_l|), and the exact radius is at most (1 + u) R_l + eta_r.
+// The violation interval of eq. (slack-sfb) follows; its lower/upper ends
+// and an error allowance are summed per warp into partials (FP64 directed).
+// Rows n_l .. n_l + n_c - 1 (one-box mode only) write the scaled rows
+// hat_k[k] = RN(Phi~[ctg_line[k], b] r_b) used by the contingency kernel;
+// line rows write hat_l[l] likewise.
+// ---------------------------------------------------------------------------
+constexpr int kBaseWarps = 8;
+
+int base_partials_count(int num_sms) { return num_sms * 2 * kBaseWarps; }
+
+__global__ void __launch_bounds__(kBaseWarps * 32) k_base(BaseArgs a) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * kBaseWarps + warp;
+    const int nw = gridDim.x * kBaseWarps;
+    const bool scaled = a.hat_l != nullptr;
+    const int n_rows = a.n_l + (scaled ? a.n_c : 0);
+    const int nv = a.n_a_pad >> 2;  // float4 per row
+    double *part = a.partials + (size_t)gw * a.n_box * 3;
+    for (int j = 0; j < a.n_box; ++j) {
+        if (lane == 0) {
+            part[j * 3 + 0] = 0.0;
+            part[j * 3 + 1] = 0.0;
+            part[j * 3 + 2] = 0.0;
+        }
+    }
+    for (int row = gw; row < n_rows; row += nw) {
+        if (row >= a.n_l) {
+            // scaled copy of a contingency line's row (one-box mode)
+            const int k = row - a.n_l;
+            const float4 *src = reinterpret_cast<const float4 *>(a.phi + (size_t)a.ctg_line[k] * a.n_a_pad);
+            const float4 *rr = reinterpret_cast<const float4 *>(a.rbus);
+            float4 *dst = reinterpret_cast<float4 *>(a.hat_k + (size_t)k * a.n_a_pad);
+            for (int v = lane; v < nv; v += 32) {
+                const float4 p = src[v], r = rr[v];
+                dst[v] = make_float4(__fmul_rn(p.x, r.x), __fmul_rn(p.y, r.y), __fmul_rn(p.z, r.z),
+                                     __fmul_rn(p.w, r.w));
+            }
+            continue;
+        }
+        const int l = row;
+        const float4 *prow = reinterpret_cast<const float4 *>(a.phi + (size_t)l * a.n_a_pad);
+        for (int j = 0; j < a.n_box; ++j) {
+            const double2 *cb = reinterpret_cast<const double2 *>(a.cbus + (size_t)j * a.n_a_pad);
+            const float4 *rb = reinterpret_cast<const float4 *>(a.rbus + (size_t)j * a.n_a_pad);
+            const float4 *ab = reinterpret_cast<const float4 *>(a.cabs + (size_t)j * a.n_a_pad);
+            double cs = 0.0;
+            float C0 = 0.f, C1 = 0.f, C2 = 0.f, C3 = 0.f;
+            float R0 = 0.f, R1 = 0.f, R2 = 0.f, R3 = 0.f;
+            float4 *hl = scaled ? reinterpret_cast<float4 *>(a.hat_l + (size_t)l * a.n_a_pad) : nullptr;
+            for (int v = lane; v < nv; v += 32) {
+                const float4 p = prow[v];
+                const double2 c01 = cb[2 * v], c23 = cb[2 * v + 1];
+                const float4 r = rb[v], ca = ab[v];
+                cs = fma((double)p.x, c01.x, cs);
+                cs = fma((double)p.y, c01.y, cs);
+                cs = fma((double)p.z, c23.x, cs);
+                cs = fma((double)p.w, c23.y, cs);
+                C0 = __fmaf_ru(fabsf(p.x), ca.x, C0);
+                C1 = __fmaf_ru(fabsf(p.y), ca.y, C1);
+                C2 = __fmaf_ru(fabsf(p.z), ca.z, C2);
+                C3 = __fmaf_ru(fabsf(p.w), ca.w, C3);
+                R0 = __fmaf_ru(fabsf(p.x), r.x, R0);
+                R1 = __fmaf_ru(fabsf(p.y), r.y, R1);
+                R2 = __fmaf_ru(fabsf(p.z), r.z, R2);
+                R3 = __fmaf_ru(fabsf(p.w), r.w, R3);
+                if (hl)
+                    hl[v] = make_float4(__fmul_rn(p.x, r.x), __fmul_rn(p.y, r.y), __fmul_rn(p.z, r.z),
+                                        __fmul_rn(p.w, r.w));
+            }
+            float C = __fadd_ru(__fadd_ru(C0, C1), __fadd_ru(C2, C3));
+            float R = __fadd_ru(__fadd_ru(R0, R1), __fadd_ru(R2, R3));
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) cs += __shfl_xor_sync(0xffffffffu, cs, o);
+            C = warp_sum_ru_f(C);
+            R = warp_sum_ru_f(R);
+            if (lane == 0) {
+                const float *bc = a.box_consts + (size_t)j * 4;
+                const float eta_r = bc[0], eta_c = bc[1];
+                const float c = __double2float_rn(cs);
+                const float e = __fadd_ru(__fmul_ru(2.1f * kU, C), eta_c);
+                const float rbar = __fadd_ru(__fmaf_ru(R, kU, R), eta_r);
+                const float rho = __fadd_ru(rbar, e);
+                const float flo = __fsub_rd(c, rho), fhi = __fadd_ru(c, rho);
+                float alo, ahi;
+                abs_interval(flo, fhi, alo, ahi);
+                const float slo = fmax0(__fsub_rd(alo, a.rate_up[l]));
+                const float shi = fmax0(__fsub_ru(ahi, a.rate_dn[l]));
+                float w = 0.0f;
+                if (shi > 0.0f) {
+                    // |s - s_exact| <= (rbar - R_exact) + 2 e + u rating
+                    w = __fmaf_ru(a.gamma_base + 3.0f * kU, R, __fmaf_ru(2.0f, e, __fmaf_ru(kU, a.rate_up[l], 2.0f * eta_r)));
+                }
+                a.line_c[(size_t)j * a.n_l + l] = c;
+                a.line_e[(size_t)j * a.n_l + l] = e;
+                a.line_R[(size_t)j * a.n_l + l] = R;
+                part[j * 3 + 0] = __dadd_rd(part[j * 3 + 0], (double)slo);
+                part[j * 3 + 1] = __dadd_ru(part[j * 3 + 1], (double)shi);
+                part[j * 3 + 2] = __dadd_ru(part[j * 3 + 2], (double)w);
+            }
+            hl = nullptr;
+        }
+    }
+}
+
+cudaError_t launch_base(const BaseArgs &a, int n_part, cudaStream_t s) {
+    const int grid = n_part / kBaseWarps;
+    k_base<<<grid, kBaseWarps * 32, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Objective assembly, one block per box (eq. (penalized-objective), appendix
+// eq. (ibp_f) under eq. (IBP)):
+//   hi = C(pd_hi) - G(pg_lo) - z_inj s_inj,lo - z_f (S_fb,lo + S_fc,lo)
+//   lo = C(pd_lo) - G(pg_hi) - z_inj s_inj,hi - z_f (S_fb,hi + S_fc,hi)
+// The PWL curves are monotone, so their IBP is the value at the endpoints,
+// evaluated through the ReLU chain of eqs. (single ReLU), (combined ReLUs) in
+// round-up and round-down arithmetic.  The imbalance uses the closed form
+// (E^T Phi - I) p = -(1^T p) e_slack (the explicit matrix has zero rows away
+// from the slack), so 1^T s_inj is |.| of the interval of the total
+// injection.  All sums are FP64 with directed rounding.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double pwl_eval(const double *a, const double *b, int n, double x,
+                                           bool up) {
+    double F = 0.0, U = 0.0;
+    for (int m = 0; m < n; ++m) {
+        double t;
+        if (up) {
+            t = __dmul_ru(a[m], fmax(__dsub_ru(x, b[m]), 0.0));
+            F = __dadd_ru(F, t);
+        } else {
+            t = __dmul_rd(a[m], fmax(__dsub_rd(x, b[m]), 0.0));
+            F = __dadd_rd(F, t);
+        }
+        if (m + 1 < n) {
+            const double seg = up ? __dmul_ru(a[m], __dsub_ru(b[m + 1], b[m]))
+                                  : __dmul_rd(a[m], __dsub_rd(b[m + 1], b[m]));
+            U = up ? __dadd_ru(U, seg) : __dadd_rd(U, seg);
+            F = fmin(F, U);
+        }
+    }
+    return F;
+}
+
+__device__ __forceinline__ void block_sum(double *v, int n, bool *up, double *sh) {
+    // v[0..n) per thread -> thread 0 holds totals; sh has room for 8 * n doubles
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    for (int i = 0; i < n; ++i) v[i] = up[i] ? warp_sum_ru(v[i]) : warp_sum_rd(v[i]);
+    if (l == 0)
+        for (int i = 0; i < n; ++i) sh[w * n + i] = v[i];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < n; ++i) {
+            double s = 0.0;
+            for (int k = 0; k < (int)(blockDim.x >> 5); ++k)
+                s = up[i] ? __dadd_ru(s, sh[k * n + i]) : __dadd_rd(s, sh[k * n + i]);
+            v[i] = s;
+        }
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(256) k_assemble(AsmArgs a) {
+    const int j = blockIdx.x;
+    // 0 Sfc_lo(rd) 1 Sfc_hi(ru) 2 Wfc(ru) 3 Sfb_lo 4 Sfb_hi 5 Wfb
+    // 6 Clo_dn 7 Chi_up 8 Glo_dn 9 Ghi_up 10 cost_err(ru)
+    // 11 Plo_dn 12 Plo_up 13 Phi_dn 14 Phi_up
+    constexpr int N = 15;
+    double v[N];
+    bool up[N] = {false, true, true, false, true, true, false, true, false, true, true,
+                  false, true, false, true};
+    for (int i = 0; i < N; ++i) v[i] = 0.0;
+    for (int p = threadIdx.x; p < a.n_part_ctg; p += blockDim.x) {
+        const double *q = a.part_ctg + ((size_t)p * a.n_box + j) * 3;
+        v[0] = __dadd_rd(v[0], q[0]);
+        v[1] = __dadd_ru(v[1], q[1]);
+        v[2] = __dadd_ru(v[2], q[2]);
+    }
+    for (int p = threadIdx.x; p < a.n_part_base; p += blockDim.x) {
+        const double *q = a.part_base + ((size_t)p * a.n_box + j) * 3;
+        v[3] = __dadd_rd(v[3], q[0]);
+        v[4] = __dadd_ru(v[4], q[1]);
+        v[5] = __dadd_ru(v[5], q[2]);
+    }
+    const double *lo = a.box_lo + (size_t)j * a.n_dev;
+    const double *hi = a.box_hi + (size_t)j * a.n_dev;
+    for (int d = threadIdx.x; d < a.n_dev; d += blockDim.x) {
+        const int s0 = a.seg_ptr[d], ns = a.seg_ptr[d + 1] - s0;
+        const double *sl = a.slope + s0, *bk = a.bkpt + s0;
+        const double vlo_dn = pwl_eval(sl, bk, ns, lo[d], false);
+        const double vlo_up = pwl_eval(sl, bk, ns, lo[d], true);
+        const double vhi_dn = pwl_eval(sl, bk, ns, hi[d], false);
+        const double vhi_up = pwl_eval(sl, bk, ns, hi[d], true);
+        if (d >= a.n_gen) {  // load value c_j
+            v[6] = __dadd_rd(v[6], vlo_dn);
+            v[7] = __dadd_ru(v[7], vhi_up);
+            v[11] = __dadd_rd(v[11], -hi[d]);
+            v[12] = __dadd_ru(v[12], -hi[d]);
+            v[13] = __dadd_rd(v[13], -lo[d]);
+            v[14] = __dadd_ru(v[14], -lo[d]);
+        } else {  // generator cost g_i
+            v[8] = __dadd_rd(v[8], vlo_dn);
+            v[9] = __dadd_ru(v[9], vhi_up);
+            v[11] = __dadd_rd(v[11], lo[d]);
+            v[12] = __dadd_ru(v[12], lo[d]);
+            v[13] = __dadd_rd(v[13], hi[d]);
+            v[14] = __dadd_ru(v[14], hi[d]);
+        }
+        v[10] = __dadd_ru(v[10], __dadd_ru(__dsub_ru(vlo_up, vlo_dn), __dsub_ru(vhi_up, vhi_dn)));
+    }
+    __shared__ double sh[8 * N];
+    block_sum(v, N, up, sh);
+    if (threadIdx.x == 0) {
+        // total injection interval [Plo, Phi] enclosed by [Plo_dn, Phi_up]
+        const double plo = v[11], phi = v[14];
+        double ilo, ihi;
+        if (plo >= 0.0) {
+            ilo = plo;
+            ihi = phi;
+        } else if (phi <= 0.0) {
+            ilo = -phi;
+            ihi = -plo;
+        } else {
+            ilo = 0.0;
+            ihi = fmax(-plo, phi);
+        }
+        const double w_inj = fmax(__dsub_ru(v[12], v[11]), __dsub_ru(v[14], v[13]));
+        const double pen_dn = __dadd_rd(__dmul_rd(a.zeta_inj, ilo),
+                                        __dmul_rd(a.zeta_f, __dadd_rd(v[3], v[0])));
+        const double pen_up = __dadd_ru(__dmul_ru(a.zeta_inj, ihi),
+                                        __dmul_ru(a.zeta_f, __dadd_ru(v[4], v[1])));
+        double ohi = __dsub_ru(__dsub_ru(v[7], v[8]), pen_dn);
+        double olo = __dsub_rd(__dsub_rd(v[6], v[9]), pen_up);
+        // error: FP32 allowances of the flow terms, the imbalance enclosure,
+        // the cost enclosures, plus FP64 summation of the partial sums
+        double err = __dmul_ru(a.zeta_f, __dadd_ru(v[2], v[5]));
+        err = __dadd_ru(err, __dmul_ru(a.zeta_inj, w_inj));
+        err = __dadd_ru(err, v[10]);
+        err = __dadd_ru(err, __dmul_ru(1e-12, __dadd_ru(__dadd_ru(fabs(v[7]), fabs(v[9])), pen_up)));
+        if (*a.err) {
+            ohi = olo = err = __longlong_as_double(0x7ff8000000000000ll);
+        }
+        a.obj_hi[j] = ohi;
+        a.obj_lo[j] = olo;
+        a.obj_err[j] = err;
+    }
+}
+
+cudaError_t launch_assemble(const AsmArgs &a, cudaStream_t s) {
+    k_assemble<<<a.n_box, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Bounded-wait self test: one thread waits on an mbarrier whose phase never
+// completes (nobody arrives), gives up after limit_ns and reports it.
+// ---------------------------------------------------------------------------
+__global__ void k_wait_selftest(int *flag, unsigned long long limit_ns) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(smem_addr(&bar), 1);
+        fence_mbar_init();
+        const bool ok = mbar_wait(smem_addr(&bar), 0, limit_ns);
+        *flag = ok ? 0 : kErrTimeout;
+    }
+}
+
+cudaError_t launch_wait_selftest(int *flag, unsigned long long limit_ns, cudaStream_t s) {
+    k_wait_selftest<<<1, 32, 0, s>>>(flag, limit_ns);
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Case-build kernels (FP64, once per case).
+// ---------------------------------------------------------------------------
+__global__ void k_scatter_dense(double *dst, int64_t ld, const int *rows, const int *cols,
+                                const double *vals, int nnz) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < nnz) dst[(int64_t)cols[i] * ld + rows[i]] = vals[i];
+}
+
+cudaError_t launch_scatter_dense(double *dst, int64_t ld, const int *rows, const int *cols,
+                                 const double *vals, int nnz, cudaStream_t s) {
+    if (nnz <= 0) return cudaSuccess;
+    k_scatter_dense<<<(nnz + 255) / 256, 256, 0, s>>>(dst, ld, rows, cols, vals, nnz);
+    return cudaGetLastError();
+}
+
+__device__ __forceinline__ float to_f32_flushed(double x) {
+    // values below 2^-120 in magnitude are stored as 0 (accounted for by eta)
+    return fabs(x) < 7.52316384526264e-37 ? 0.0f : __double2float_rn(x);
+}
+
+// Z is column-major (nb_r x n_l): column l holds Phi_r[l, :] (reduced buses).
+__global__ void k_extract_phi(const double *Z, int nb_r, int n_l, const int *act_red, int n_a,
+                              int n_a_pad, float *phi_a) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t tot = (int64_t)n_l * n_a_pad;
+    if (i >= tot) return;
+    const int l = (int)(i / n_a_pad), a = (int)(i % n_a_pad);
+    float v = 0.0f;
+    if (a < n_a) v = to_f32_flushed(Z[(int64_t)l * nb_r + act_red[a]]);
+    phi_a[i] = v;
+}
+
+cudaError_t launch_extract_phi(const double *Z, int nb_r, int n_l, const int *act_red, int n_a,
+                               int n_a_pad, float *phi_a, cudaStream_t s) {
+    const int64_t tot = (int64_t)n_l * n_a_pad;
+    k_extract_phi<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(Z, nb_r, n_l, act_red, n_a, n_a_pad,
+                                                                phi_a);
+    return cudaGetLastError();
+}
+
+// L[k][l] = PTDF_line[l,k] / (1 - PTDF_line[kline,k]),  L[k][kline] = -1,
+// PTDF_line[l,k] = Phi[l, from_k] - Phi[l, to_k] (slack entries are 0).
+// One block per contingency.
+__global__ void k_lodf(const double *Z, int nb_r, int n_l, int n_c, const int *fr, const int *to,
+                       const int *ctg_line, float *lodf, double *den_out, float *maxabs) {
+    const int k = blockIdx.x;
+    const int f = fr[k], t = to[k], kl = ctg_line[k];
+    auto ptl = [&](int l) -> double {
+        const double *col = Z + (int64_t)l * nb_r;
+        const double a = f >= 0 ? col[f] : 0.0;
+        const double b = t >= 0 ? col[t] : 0.0;
+        return a - b;
+    };
+    const double den = 1.0 - ptl(kl);
+    if (threadIdx.x == 0) den_out[k] = den;
+    float mx = 0.0f;
+    for (int l = threadIdx.x; l < n_l; l += blockDim.x) {
+        float v;
+        if (l == kl) {
+            v = -1.0f;
+        } else {
+            v = to_f32_flushed(ptl(l) / den);
+        }
+        lodf[(int64_t)k * n_l + l] = v;
+        mx = fmaxf(mx, fabsf(v));
+    }
+    mx = warp_max_f(mx);
+    if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<int *>(maxabs), __float_as_int(mx));
+}
+
+cudaError_t launch_lodf(const double *Z, int nb_r, int n_l, int n_c, const int *ctg_from_red,
+                        const int *ctg_to_red, const int *ctg_line, float *lodf, double *den_out,
+                        float *maxabs_out, cudaStream_t s) {
+    if (n_c <= 0) return cudaSuccess;
+    k_lodf<<<n_c, 256, 0, s>>>(Z, nb_r, n_l, n_c, ctg_from_red, ctg_to_red, ctg_line, lodf, den_out,
+                               maxabs_out);
+    return cudaGetLastError();
+}
+
+__global__ void k_gather_rows(const float *src, int ld, const int *rows, int n_rows, float *dst) {
+    const int r = blockIdx.x;
+    if (r >= n_rows) return;
+    const float *s = src + (int64_t)rows[r] * ld;
+    float *d = dst + (int64_t)r * ld;
+    for (int i = threadIdx.x; i < ld; i += blockDim.x) d[i] = s[i];
+}
+
+cudaError_t launch_gather_rows(const float *src, int ld, const int *rows, int n_rows, float *dst,
+                               cudaStream_t s) {
+    if (n_rows <= 0) return cudaSuccess;
+    k_gather_rows<<<n_rows, 256, 0, s>>>(src, ld, rows, n_rows, dst);
+    return cudaGetLastError();
+}
+
+}  // namespace ibp

@@ -1,0 +1,107 @@
+"""Host-only checks of the C ABI: the library loads, exports every symbol that
+include/ibp.h declares, and rejects bad inputs with a status code before any
+device work (dry-run cases, device = -1)."""
+import ctypes
+import dataclasses
+import os
+import re
+
+import numpy as np
+import pytest
+
+from gen import find_bridges, make_config, make_network_case
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    from paper_2511_15624_gb300.build import build
+    build()
+    import paper_2511_15624_gb300 as P
+    return P
+
+
+def test_exports_every_declared_symbol(pkg):
+    hdr = open(os.path.join(ROOT, "include", "ibp.h")).read()
+    names = set(re.findall(r"\b(ibp_[a-z_0-9]+)\s*\(", hdr))
+    assert {"ibp_case_create", "ibp_bound", "ibp_bound_backward"} <= names
+    lib = ctypes.CDLL(pkg._abi.LIB_PATH)
+    for n in sorted(names):
+        assert hasattr(lib, n), n
+    assert set(pkg._abi.EXPORTED) == names
+
+
+def _expect(P, status, fn):
+    with pytest.raises(P.IBPError) as ei:
+        fn()
+    assert ei.value.status == status, str(ei.value)
+
+
+def test_dry_run_validation(pkg):
+    P = pkg
+    c = make_config(1)
+    P.dry_run_case(c)  # valid input passes
+    bad = dataclasses.replace(c, line_from=c.line_from.copy())
+    bad.line_from[3] = c.n_bus + 5
+    _expect(P, P._abi.IBP_EINVAL, lambda: P.dry_run_case(bad))
+    bad = dataclasses.replace(c, reactance=c.reactance.copy())
+    bad.reactance[0] = -1.0
+    _expect(P, P._abi.IBP_EINVAL, lambda: P.dry_run_case(bad))
+    bad = dataclasses.replace(c, reactance=c.reactance.copy())
+    bad.reactance[0] = np.nan
+    _expect(P, P._abi.IBP_EINVAL, lambda: P.dry_run_case(bad))
+    bad = dataclasses.replace(c, rating=c.rating.copy())
+    bad.rating[2] = np.inf
+    _expect(P, P._abi.IBP_EINVAL, lambda: P.dry_run_case(bad))
+    bad = dataclasses.replace(c, ctg_line=np.array([0, c.n_line], np.int32))
+    _expect(P, P._abi.IBP_EINVAL, lambda: P.dry_run_case(bad))
+    bad = dataclasses.replace(c, gen_bkpt=c.gen_bkpt.copy(), gen_nseg=c.gen_nseg.copy())
+    # two segments with non-increasing breakpoints on device 0
+    bad = dataclasses.replace(c, gen_nseg=np.concatenate([[2], c.gen_nseg[1:]]).astype(np.int32),
+                              gen_slope=np.concatenate([[1.0], c.gen_slope]),
+                              gen_bkpt=np.concatenate([[5.0], c.gen_bkpt]))
+    _expect(P, P._abi.IBP_EINVAL, lambda: P.dry_run_case(bad))
+    bad = dataclasses.replace(c, line_to=c.line_to.copy())
+    bad.line_to[0] = bad.line_from[0]
+    _expect(P, P._abi.IBP_EINVAL, lambda: P.dry_run_case(bad))
+
+
+def test_bridge_and_disconnected_rejected(pkg):
+    P = pkg
+    c = make_network_case("t", 12, 13, 3, 4, seed=5)
+    br = find_bridges(c.n_bus, c.line_from, c.line_to)
+    assert br.any()
+    bad = dataclasses.replace(c, ctg_line=np.flatnonzero(br)[:1].astype(np.int32))
+    _expect(P, P._abi.IBP_EISLAND, lambda: P.dry_run_case(bad))
+    # drop a bridge line: the network falls apart
+    keep = np.flatnonzero(~br | (np.arange(c.n_line) != np.flatnonzero(br)[0]))
+    keep = np.array([l for l in range(c.n_line) if l != np.flatnonzero(br)[0]])
+    disc = dataclasses.replace(c, line_from=c.line_from[keep], line_to=c.line_to[keep],
+                               reactance=c.reactance[keep], rating=c.rating[keep],
+                               ctg_line=np.zeros(0, np.int32))
+    _expect(P, P._abi.IBP_EISLAND, lambda: P.dry_run_case(disc))
+
+
+def test_box_validation_before_device(pkg):
+    P = pkg
+    c = make_config(0)
+    d = P.dry_run_case(c)
+    lo, hi = c.box_lo.copy(), c.box_hi.copy()
+    lo[0, 1] = hi[0, 1] + 1.0
+    _expect(P, P._abi.IBP_EINVAL, lambda: d.bound(lo, hi))
+    lo = c.box_lo.copy()
+    lo[0, 0] = np.nan
+    _expect(P, P._abi.IBP_EINVAL, lambda: d.bound(lo, c.box_hi))
+    _expect(P, P._abi.IBP_ENOTSUP, lambda: d.bound(c.box_lo, c.box_hi))
+    with pytest.raises(ValueError):
+        d.bound(c.box_lo[:, :3], c.box_hi[:, :3])
+
+
+def test_no_cpu_fallback_without_device(pkg):
+    """On a machine without a GPU the product path fails loudly."""
+    P = pkg
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    _expect(P, P._abi.IBP_ECUDA, lambda: P.Case(make_config(0), device=0))

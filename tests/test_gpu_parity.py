@@ -1,0 +1,203 @@
+"""GPU vs oracle parity of the certified bound (calls go through the C ABI).
+
+Tolerances (written here, derived in the design doc):
+* soundness: the GPU interval must contain the oracle's, up to the FP64
+  difference between the two independent sensitivity builds, 1e-9 of the
+  operand scale;
+* objective: |gpu - oracle| <= 1e-5 |oracle| at both ends, and <= obj_err
+  (the GPU's own error bound) plus the same FP64 allowance;
+* flows: |gpu - oracle| <= 1e-5 s_kl at both ends, where
+  s_kl = |c_l| + R_l + |L_lk| (|c_k| + R_k) is the magnitude of the FP32
+  operands combined for the pair (lines whose post-outage flow cancels to
+  ~0 keep an FP32-sized error relative to these operands), plus an absolute
+  floor of 1e-12 max s_kl for lines whose exact flow is identically zero
+  (both FP64 builds leave noise of that size there).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from gen import make_config, make_network_case, split_boxes
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2511_15624_gb300 as pkg
+    pkg._abi.lib()
+    return pkg
+
+
+_SENS = {}
+
+
+def _sens(key, case):
+    if key not in _SENS:
+        _SENS[key] = O.sensitivities(case)
+    return _SENS[key]
+
+
+def _obj_scale(ref):
+    C = ref.terms["costs"]
+    z = np.abs(C).sum(axis=1)
+    return z + 1e4 * (ref.terms["inj"][1]) + 1e3 * (ref.terms["fb"][1] + ref.terms["fc"][1])
+
+
+def check_objective(lo, hi, err, ref, rel=1e-5):
+    scale = _obj_scale(ref)
+    d = 1e-9 * scale
+    assert np.all(hi >= ref.hi - d), (hi, ref.hi)
+    assert np.all(lo <= ref.lo + d), (lo, ref.lo)
+    assert np.all(np.abs(hi - ref.hi) <= rel * np.abs(ref.hi) + d), (hi, ref.hi)
+    assert np.all(np.abs(lo - ref.lo) <= rel * np.abs(ref.lo) + d), (lo, ref.lo)
+    assert np.all(np.abs(hi - ref.hi) <= err + d)
+    assert np.all(np.abs(lo - ref.lo) <= err + d)
+
+
+def flow_scale(case, sens, cb, rb, pk, pl):
+    fc = cb @ sens.phi.T
+    fr = rb @ np.abs(sens.phi).T
+    kl = case.ctg_line[pk]
+    L = np.abs(sens.lodf[pl, pk])
+    return (np.abs(fc[:, pl]) + fr[:, pl]) + L[None, :] * (np.abs(fc[:, kl]) + fr[:, kl])
+
+
+def _worst(excess, pk, pl):
+    i = np.unravel_index(np.argmax(excess), excess.shape)
+    return f"worst excess {excess[i]:.3e} at box {i[0]} k={pk[i[1]]} l={pl[i[1]]}"
+
+
+def check_flows(case, sens, lo_box, hi_box, flo, fhi, pk, pl, rel=1e-5):
+    cb, rb = O.bus_box(case, lo_box, hi_box)
+    cent, rad = O.ctg_flows(case, sens, cb, rb, pk, pl)
+    s = flow_scale(case, sens, cb, rb, pk, pl)
+    # floor: both FP64 builds are accurate to ~1e-12 of the largest operand, so
+    # lines whose exact flow is identically zero carry that much noise
+    floor = 1e-12 * s.max()
+    g_lo = flo[:, pk, pl]
+    g_hi = fhi[:, pk, pl]
+    d = 1e-9 * s + floor
+    assert np.all(g_lo <= cent - rad + d), _worst(g_lo - (cent - rad) - d, pk, pl)
+    assert np.all(g_hi >= cent + rad - d), _worst((cent + rad) - g_hi - d, pk, pl)
+    assert np.all(np.abs(g_lo - (cent - rad)) <= rel * s + floor), \
+        _worst(np.abs(g_lo - (cent - rad)) - rel * s - floor, pk, pl)
+    assert np.all(np.abs(g_hi - (cent + rad)) <= rel * s + floor), \
+        _worst(np.abs(g_hi - (cent + rad)) - rel * s - floor, pk, pl)
+    # the outaged line is exactly [0, 0]
+    out = pl == case.ctg_line[pk]
+    assert np.all(g_lo[:, out] == 0) and np.all(g_hi[:, out] == 0)
+
+
+@pytest.mark.parametrize("cfg", [0, 1, 2])
+def test_single_box_parity(P, cfg):
+    case = make_config(cfg)
+    sens = _sens(cfg, case)
+    ref = O.bound(case, sens)
+    gpu = P.Case(case, device=0)
+    lo, hi, err, flo, fhi = gpu.bound(case.box_lo, case.box_hi, flows=True)
+    check_objective(lo, hi, err, ref)
+    if case.n_ctg * case.n_line <= 200_000:
+        kk, ll = np.meshgrid(np.arange(case.n_ctg), np.arange(case.n_line), indexing="ij")
+        pk, pl = kk.ravel(), ll.ravel()
+    else:
+        rng = np.random.default_rng(cfg)
+        pk = rng.integers(0, case.n_ctg, 20000)
+        pl = rng.integers(0, case.n_line, 20000)
+        pl[:200] = case.ctg_line[pk[:200]]  # include outaged lines
+    check_flows(case, sens, case.box_lo, case.box_hi, flo, fhi, pk, pl)
+
+
+def test_device_pointer_mode_matches_host_mode(P):
+    import torch
+    case = make_config(1)
+    gpu = P.Case(case, device=0)
+    lo, hi, err = gpu.bound(case.box_lo, case.box_hi)
+    tlo = torch.tensor(case.box_lo, device="cuda")
+    thi = torch.tensor(case.box_hi, device="cuda")
+    dlo, dhi, derr, fl, fh = gpu.bound(tlo, thi, flows=True)
+    torch.cuda.synchronize()
+    gpu.sync()
+    assert np.array_equal(dlo.cpu().numpy(), lo) and np.array_equal(dhi.cpu().numpy(), hi)
+    assert np.array_equal(derr.cpu().numpy(), err)
+    # deterministic: a second call reproduces every bit
+    lo2, hi2, err2 = gpu.bound(case.box_lo, case.box_hi)
+    assert np.array_equal(lo, lo2) and np.array_equal(hi, hi2)
+
+
+def test_point_box_and_sub_boxes(P):
+    case = make_config(1)
+    sens = _sens(1, case)
+    gpu = P.Case(case, device=0)
+    rng = np.random.default_rng(3)
+    x = case.box_lo[0] + rng.random(case.n_dev) * (case.box_hi[0] - case.box_lo[0])
+    lo, hi, err = gpu.bound(x[None], x[None])
+    f = O.objective_point(case, sens, x)
+    assert lo[0] <= f + 1e-9 * abs(f) and f <= hi[0] + 1e-9 * abs(f)
+    assert hi[0] - lo[0] <= 1e-5 * abs(f)
+    # a few sub-boxes one by one
+    slo, shi = split_boxes(case.box_lo[0], case.box_hi[0], 3, rng)
+    ref = O.bound(case, sens, lo=slo, hi=shi)
+    for j in range(slo.shape[0]):
+        lo, hi, err = gpu.bound(slo[j:j + 1], shi[j:j + 1])
+        sub = O.Bound(lo=ref.lo[j:j + 1], hi=ref.hi[j:j + 1],
+                      terms={k: (v[j:j + 1] if not isinstance(v, tuple) else tuple(t[j:j + 1] for t in v))
+                             for k, v in ref.terms.items()})
+        check_objective(lo, hi, err, sub)
+
+
+def test_edge_cases(P):
+    # no contingencies at all
+    case = make_config(1)
+    import dataclasses
+    nc = dataclasses.replace(case, ctg_line=np.zeros(0, np.int32))
+    gpu = P.Case(nc, device=0)
+    lo, hi, err = gpu.bound(nc.box_lo, nc.box_hi)
+    ref = O.bound(nc, O.sensitivities(nc))
+    check_objective(lo, hi, err, ref)
+    # duplicated contingencies count twice, PWL costs with 3 segments, tiny network
+    c0 = make_config(0, n_seg=3)
+    dup = dataclasses.replace(c0, ctg_line=np.concatenate([c0.ctg_line, c0.ctg_line[:2]]).astype(np.int32))
+    gpu = P.Case(dup, device=0)
+    lo, hi, err = gpu.bound(dup.box_lo, dup.box_hi)
+    check_objective(lo, hi, err, O.bound(dup, O.sensitivities(dup)))
+    # separate contingency ratings
+    rc = dataclasses.replace(case, rating_ctg=case.rating * 1.3)
+    gpu = P.Case(rc, device=0)
+    lo, hi, err = gpu.bound(rc.box_lo, rc.box_hi)
+    check_objective(lo, hi, err, O.bound(rc, _sens(1, case)))
+    # a network whose line count is not a multiple of anything, slack with devices
+    odd = make_network_case("odd", 37, 61, 9, 20, seed=77)
+    gpu = P.Case(odd, device=0)
+    lo, hi, err = gpu.bound(odd.box_lo, odd.box_hi)
+    check_objective(lo, hi, err, O.bound(odd, O.sensitivities(odd)))
+
+
+def test_bad_box_on_device_reports_and_poisons(P):
+    import torch
+    case = make_config(0)
+    gpu = P.Case(case, device=0)
+    lo = case.box_lo.copy()
+    lo[0, 2] = case.box_hi[0, 2] + 5.0
+    dlo, dhi, derr = gpu.bound(torch.tensor(lo, device="cuda"), torch.tensor(case.box_hi, device="cuda"))
+    torch.cuda.synchronize()
+    with pytest.raises(P.IBPError) as ei:
+        gpu.sync()
+    assert ei.value.status == P._abi.IBP_EINVAL
+    assert np.isnan(dhi.cpu().numpy()).all()
+    # the case stays usable
+    lo2, hi2, err2 = gpu.bound(case.box_lo, case.box_hi)
+    assert np.isfinite(hi2).all()
+
+
+def test_bounded_wait_times_out_cleanly(P):
+    st = P._abi.ibp_selftest_wait_timeout(0, 1000)
+    assert st == P._abi.IBP_ETIMEOUT
+    # the context is still usable afterwards
+    case = make_config(0)
+    gpu = P.Case(case, device=0)
+    lo, hi, err = gpu.bound(case.box_lo, case.box_hi)
+    assert np.isfinite(hi).all()
