@@ -28,8 +28,12 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "ms per certified N-1 objective bound, 8316-bus"
-WORKLOAD = ("mesh8316: 8316 buses, 10500 lines, 5000 N-1 contingencies, 1100 gens, "
-            "5000 flexible loads, seed 1003, 1 box per bound")
+
+
+def workload(case, cfg, nb):
+    return (f"{case.name}: {case.n_bus} buses, {case.n_line} lines, {case.n_ctg} N-1 "
+            f"contingencies, {case.n_gen} gens, {case.n_load} flexible loads, seed {1000 + cfg}, "
+            f"{nb} box per bound")
 
 
 def _args():
@@ -174,7 +178,7 @@ def run_reference(args):
             "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": WORKLOAD, "boxes": 1, "l2": "n/a (CPU)"},
+            "config": {"workload": workload(case, args.config, 1), "boxes": 1, "l2": "n/a (CPU)"},
             "cpu_baseline": {"value": v, "unit": "ms", "cores": threads, "kind": "oracle",
                              "sample": desc},
             "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -266,7 +270,8 @@ def run_gb300(args):
         "metric": METRIC, "value": value, "unit": "ms", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "boxes": nb, "n_active_buses": info.n_active,
+        "config": {"workload": workload(case, args.config, nb), "boxes": nb,
+                   "n_active_buses": info.n_active,
                    "interval_flows_per_s": case.n_ctg * case.n_line * nb / (value * 1e-3),
                    "l2": "no flush: the streamed PTDF rows (345 MB) exceed the 129 MB L2",
                    "kernel_ms": tot_k},

@@ -37,6 +37,8 @@ CONFIG_SIZES = {
     1: (118, 186, 54, 99, None),
     2: (2000, 3200, 500, 1200, 2500),
     3: (8316, 10500, 1100, 5000, 5000),
+    # profiling size: PTDF rows larger than the 129 MB L2, a few ms per bound
+    5: (5000, 7000, 660, 3000, 4000),
 }
 RAGGED_SIZES = (73, 300, 500, 1000, 2000)
 
@@ -320,9 +322,9 @@ def split_boxes(lo: np.ndarray, hi: np.ndarray, levels: int, rng: np.random.Gene
 
 
 def make_config(cfg: int, n_box: int = 1, n_seg: int = 1) -> Case:
-    """The seeded case of synthetic workload ``cfg`` (0..3); seed 1000 + cfg."""
+    """The seeded case of synthetic workload ``cfg`` (0..3, 5); seed 1000 + cfg."""
     n_bus, n_line, n_gen, n_load, n_ctg = CONFIG_SIZES[cfg]
-    names = {0: "ring5", 1: "mesh118", 2: "mesh2000", 3: "mesh8316"}
+    names = {0: "ring5", 1: "mesh118", 2: "mesh2000", 3: "mesh8316", 5: "mesh5000"}
     c = make_network_case(names[cfg], n_bus, n_line, n_gen, n_load, seed=1000 + cfg,
                           n_ctg=n_ctg, n_seg=n_seg, ring5=(cfg == 0))
     if n_box > 1:
