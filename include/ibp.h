@@ -154,6 +154,38 @@ ibp_status ibp_bound_multi(int32_t n_case, ibp_case *const *cases,
                            double *const *obj_hi, double *const *obj_err,
                            void *cuda_stream);
 
+/*
+ * One-box bound that allocates no device memory (the paper has no counterpart:
+ * this is a deployment aid).  Some callers cannot call cudaMalloc while they
+ * compute a bound: code that runs while a CUDA stream is being captured into a
+ * graph, host threads with latency limits (cudaMalloc/cudaFree may synchronise
+ * the whole device), and programs whose own allocator owns all device memory.
+ * ibp_bound may allocate its per-call workspace on first use; this entry point
+ * never does.  Its per-call buffers live in one file-scope __device__ array of
+ * 8 MiB that every GPU which loads the library holds until the process exits.
+ *
+ *   c: a case from ibp_case_create (its sensitivities were allocated there)
+ *   box_lo, box_hi [n_gen + n_load], obj_lo, obj_hi, obj_err [1]: DEVICE
+ *     pointers; the work is only enqueued on cuda_stream (NULL = legacy
+ *     default stream).  Same results as ibp_bound up to FP32 rounding order
+ *     (same certified arithmetic, unscaled PTDF rows); flows are not written.
+ * Limits and behaviour:
+ *   - returns IBP_EINVAL, touching nothing, when the case needs more scratch
+ *     than the array holds (about 1.5 MiB for 8316 buses, 10500 lines and
+ *     5000 contingencies);
+ *   - the first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress), so make that first call before any stream
+ *     capture;
+ *   - every call, on every case, shares the one array (it keeps the last
+ *     call's contents; the error word is cleared at the start of each call):
+ *     calls whose work overlaps on the GPU race and must be serialised by the
+ *     caller, e.g. by issuing them on one stream;
+ *   - a device-side error (a box with lo > hi, a non-finite entry) writes NaN
+ *     into obj_lo, obj_hi and obj_err.
+ */
+ibp_status ibp_bound_noalloc(ibp_case *c, const double *box_lo, const double *box_hi,
+                             double *obj_lo, double *obj_hi, double *obj_err, void *cuda_stream);
+
 /* Wait for the case's stream work and report device-side errors of the last
  * asynchronous call (IBP_EINVAL for a bad box, IBP_ETIMEOUT for a wait). */
 ibp_status ibp_case_sync(ibp_case *c);

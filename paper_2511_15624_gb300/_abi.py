@@ -24,7 +24,7 @@ EXPORTED = (
     "ibp_case_create", "ibp_case_destroy", "ibp_bound", "ibp_bound_backward", "ibp_bound_multi",
     "ibp_case_sync", "ibp_case_info", "ibp_case_set_variant", "ibp_kernel_variants",
     "ibp_case_set_timing", "ibp_case_last_timing", "ibp_selftest_wait_timeout", "ibp_last_error",
-    "ibp_status_string",
+    "ibp_status_string", "ibp_bound_noalloc",
 )
 
 
@@ -66,6 +66,8 @@ def lib():
         L.ibp_bound_backward.restype = ctypes.c_int
         L.ibp_bound_multi.argtypes = [I32, P, P, P, P, P, P, P, P]
         L.ibp_bound_multi.restype = ctypes.c_int
+        L.ibp_bound_noalloc.argtypes = [P, P, P, P, P, P, P]
+        L.ibp_bound_noalloc.restype = ctypes.c_int
         L.ibp_case_sync.argtypes = [P]
         L.ibp_case_sync.restype = ctypes.c_int
         L.ibp_case_info.argtypes = [P, ctypes.POINTER(CaseInfo)]
@@ -171,6 +173,13 @@ def ibp_bound_multi(handles, n_box, box_lo, box_hi, obj_lo, obj_hi, obj_err, str
         return (ctypes.c_void_p * n)(*[ctypes.c_void_p(_ptr(x)) for x in xs])
     st = lib().ibp_bound_multi(n, H, NB, arr(box_lo), arr(box_hi), arr(obj_lo), arr(obj_hi),
                                arr(obj_err), stream)
+    _check(st)
+
+
+def ibp_bound_noalloc(handle, box_lo, box_hi, obj_lo, obj_hi, obj_err, stream=None):
+    """One-box bound with no device allocation; all pointers are device pointers."""
+    st = lib().ibp_bound_noalloc(ctypes.c_void_p(handle), _ptr(box_lo), _ptr(box_hi), _ptr(obj_lo),
+                                 _ptr(obj_hi), _ptr(obj_err), stream)
     _check(st)
 
 

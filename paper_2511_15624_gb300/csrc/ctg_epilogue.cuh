@@ -1,0 +1,85 @@
+// Per-pair epilogue of the contingency kernels: the certified flow interval
+// of one (k, l) pair from its round-up radius sum, the violation interval of
+// eq. (slack-Sc), and the per-warp FP64 partial sums of eq. (slack-sagg).
+#pragma once
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace ibp {
+
+constexpr int kConsumerWarps = 8;
+
+// Epilogue for one (k, l) pair: flow interval, violation interval, error term.
+__device__ __forceinline__ void pair_epilogue(const CtgArgs &a, int box, int l, int k, float Lt,
+                                              float A, float &slo_acc, float &shi_acc,
+                                              float &w_acc) {
+    const int kl = __ldg(&a.ctg_line[k]);
+    const size_t ob = (size_t)box * a.n_l;
+    const float cl = __ldg(&a.line_c[ob + l]), ck = __ldg(&a.line_c[ob + kl]);
+    const float el = __ldg(&a.line_e[ob + l]), ek = __ldg(&a.line_e[ob + kl]);
+    const float Rl = __ldg(&a.line_R[ob + l]), Rk = __ldg(&a.line_R[ob + kl]);
+    const float *bc = a.box_consts + (size_t)box * 4;
+    const float eta_r = __ldg(&bc[0]), eta_c = __ldg(&bc[1]);
+    const float aL = fabsf(Lt);
+    float flo, fhi, slo, shi, w;
+    if (l == kl) {
+        // the outaged line carries exactly nothing (L[k,k] = -1, like M_k)
+        flo = fhi = 0.0f;
+        slo = shi = w = 0.0f;
+    } else {
+        const float one_l = __fadd_ru(1.0f, aL);
+        const float eta = __fmul_ru(eta_r, one_l);
+        const float m = __fmaf_ru(aL, Rk, Rl);
+        float rbar = __fmaf_ru(A, kU, A);
+        rbar = __fmaf_ru(4.0f * kU, m, rbar);
+        rbar = __fadd_ru(rbar, eta);
+        const float c = __fmaf_rn(Lt, ck, cl);
+        // centre error: e_l + |L|(e_k + u|c_k|) + u|c|, with (1+u) slack on |L|
+        float ec = __fmaf_ru(2.0f * kU, fabsf(ck), __fmul_ru(ek, 1.0000002f));
+        ec = __fmaf_ru(aL, ec, el);
+        ec = __fmaf_ru(2.0f * kU, fabsf(c), ec);
+        ec = __fmaf_ru(eta_c, one_l, ec);
+        const float rho = __fadd_ru(rbar, ec);
+        flo = __fsub_rd(c, rho);
+        fhi = __fadd_ru(c, rho);
+        float alo, ahi;
+        abs_interval(flo, fhi, alo, ahi);
+        const float rup = __ldg(&a.rate_up[l]), rdn = __ldg(&a.rate_dn[l]);
+        slo = fmax0(__fsub_rd(alo, rup));
+        shi = fmax0(__fsub_ru(ahi, rdn));
+        w = 0.0f;
+        if (shi > 0.0f) {
+            // |s - s_exact| <= (rbar - r_exact) + 2 ec + u rating
+            w = __fmaf_ru(a.gamma + 3.0f * kU, A, __fmaf_ru(8.0f * kU, m, 0.0f));
+            w = __fmaf_ru(2.0f, ec, w);
+            w = __fmaf_ru(kU, rup, w);
+            w = __fmaf_ru(2.0f, eta, w);
+        }
+    }
+    if (a.flow_lo) {
+        const size_t o = ((size_t)box * a.n_c + k) * a.n_l + l;
+        a.flow_lo[o] = flo;
+        a.flow_hi[o] = fhi;
+    }
+    slo_acc = __fadd_rd(slo_acc, slo);
+    shi_acc = __fadd_ru(shi_acc, shi);
+    w_acc = __fadd_ru(w_acc, w);
+}
+
+// Per-warp FP64 partial sums (deterministic tree, directed rounding).
+__device__ __forceinline__ void write_warp_partials(const CtgArgs &a, int tile, int warp, int box,
+                                                    float slo, float shi, float w) {
+    const int lane = threadIdx.x & 31;
+    const double dlo = warp_sum_rd((double)slo);
+    const double dhi = warp_sum_ru((double)shi);
+    const double dw = warp_sum_ru((double)w);
+    if (lane == 0) {
+        double *p = a.partials + (((size_t)tile * kConsumerWarps + warp) * a.n_box + box) * 3;
+        p[0] = dlo;
+        p[1] = dhi;
+        p[2] = dw;
+    }
+}
+
+}  // namespace ibp

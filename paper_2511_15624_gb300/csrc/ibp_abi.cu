@@ -535,6 +535,25 @@ extern "C" ibp_status ibp_case_create(int32_t n_bus, int32_t slack_bus, int32_t 
 
 extern "C" void ibp_case_destroy(ibp_case *c) { delete c; }
 
+namespace ibp {
+bool case_view(const ibp_case *c, CaseView *v) {
+    if (!c || !v || c->device < 0) return false;
+    v->device = c->device; v->n_line = c->n_line; v->n_ctg = c->n_ctg; v->n_gen = c->n_gen;
+    v->n_dev = c->n_dev; v->n_a = c->n_a; v->n_a_pad = c->n_a_pad; v->num_sms = c->num_sms;
+    v->zeta_inj = c->zeta_inj; v->zeta_f = c->zeta_f;
+    v->phi_a = c->phi_a.p; v->lodf = c->lodf.p; v->rate_up = c->rate_up.p; v->rate_dn = c->rate_dn.p;
+    v->rate_c_up = c->rate_c_up.p; v->rate_c_dn = c->rate_c_dn.p; v->ctg_line = c->ctg_line.p;
+    v->act_ptr = c->act_ptr.p; v->act_dev = c->act_dev.p; v->seg_ptr = c->seg_ptr.p;
+    v->slope = c->slope.p; v->bkpt = c->bkpt.p; v->n_part_base = c->n_part_base;
+    return true;
+}
+
+ibp_status set_error(ibp_status s, const char *msg) {
+    if (s == IBP_OK) return ok();
+    return fail(s, "%s", msg);
+}
+}  // namespace ibp
+
 // ----------------------------------------------------------------- workspace
 static const CtgVariant *pick_variant(const ibp_case *c, int n_box) {
     if (c->variant > 0) {

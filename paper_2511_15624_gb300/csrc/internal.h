@@ -113,6 +113,19 @@ cudaError_t launch_lodf(const double *Z, int nb_r, int n_l, int n_c, const int *
 cudaError_t launch_gather_rows(const float *src, int ld, const int *rows, int n_rows,
                                float *dst, cudaStream_t s);
 
+// read-only view of a case's device data and sizes (for entry points that
+// live in other translation units)
+struct CaseView {
+    int device, n_line, n_ctg, n_gen, n_dev, n_a, n_a_pad, num_sms;
+    double zeta_inj, zeta_f;
+    const float *phi_a, *lodf, *rate_up, *rate_dn, *rate_c_up, *rate_c_dn;
+    const int *ctg_line, *act_ptr, *act_dev, *seg_ptr;
+    const double *slope, *bkpt;
+    int n_part_base;
+};
+bool case_view(const ibp_case *c, CaseView *v);
+ibp_status set_error(ibp_status s, const char *msg);
+
 // tensor maps
 bool encode_map_2d(CUtensorMap *map, const float *base, int64_t inner, int64_t outer,
                    int64_t row_stride_elems, int box_inner, int box_outer, std::string *err);
