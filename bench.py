@@ -44,6 +44,8 @@ def _args():
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--config", type=int, default=3)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--variant", type=int, default=0,
+                   help="contingency-kernel tile shape (0 = library default)")
     p.add_argument("--cpu-seconds", type=float, default=15.0,
                    help="target CPU time of the oracle sample")
     return p.parse_args()
@@ -200,6 +202,8 @@ def run_gb300(args):
     dev = torch.device("cuda", local)
     case = make_config(args.config)
     gpu = P.Case(case, device=local)
+    if args.variant:
+        gpu.set_variant(args.variant)
     info = gpu.info()
     nb = 1
     lo = torch.tensor(case.box_lo, device=dev)
@@ -283,7 +287,8 @@ def run_gb300(args):
                 "h2d_bytes_per_step": int(2 * case.box_lo.nbytes),
                 "d2h_bytes_per_step": int(3 * 8 * nb)},
         "gpu_launches": 4 * args.steps,
-        "objective": {"lo": float(obj[0][0]), "hi": float(obj[1][0]), "err": float(obj[2][0])},
+        "objective": {"lo": float(obj[0][0]), "hi": float(obj[1][0]),
+                      "err_hi": float(obj[2][0][0]), "err_lo": float(obj[2][0][1])},
     }
     if not args.no_cpu_baseline and ws == 1:
         ms, desc, threads = _oracle_sample(case, args.cpu_seconds)

@@ -21,8 +21,8 @@
  *
  * Certification: every reported interval contains the exact IBP interval
  * computed in real arithmetic from the FP64 sensitivities the library built
- * (outward rounding throughout).  obj_err bounds the distance between the
- * reported and the exact IBP objective bounds.
+ * (outward rounding throughout).  obj_err bounds the distance between each
+ * reported and exact IBP objective bound.
  *
  * Conventions
  *   - Units: MW, $/MWh, reactance in p.u.; a single slack bus absorbs any
@@ -115,9 +115,11 @@ void ibp_case_destroy(ibp_case *c);
  * Certified IBP bound of f_ibp over each of n_box boxes (appendix eq. (f-ibp)
  * bounds max f over the box from above by obj_hi).
  *   box_lo, box_hi [n_box][n_gen + n_load] (FP64, MW), lo <= hi, finite
- *   obj_lo, obj_hi, obj_err [n_box] (FP64): obj_hi >= the exact IBP upper
- *     bound >= max f over the box; obj_lo <= the exact IBP lower bound;
- *     obj_err >= |reported - exact IBP| for both ends.
+ *   obj_lo, obj_hi [n_box] (FP64): obj_hi >= the exact IBP upper bound >=
+ *     max f over the box; obj_lo <= the exact IBP lower bound.
+ *   obj_err [n_box][2] (FP64): {e_hi, e_lo} with |obj_hi - exact IBP upper
+ *     bound| <= e_hi and |obj_lo - exact IBP lower bound| <= e_lo (a-priori
+ *     bounds of the FP32 outward rounding, stated per result).
  *     obj_hi < 0 certifies that the box is welfare-negative, eq. (inf-or-wn).
  *   flow_lo, flow_hi [n_box][n_ctg][n_line] (FP32) or NULL: outward-rounded
  *     post-contingency flow intervals (the outaged line is exactly [0, 0]).
@@ -165,7 +167,7 @@ ibp_status ibp_bound_multi(int32_t n_case, ibp_case *const *cases,
  * 8 MiB that every GPU which loads the library holds until the process exits.
  *
  *   c: a case from ibp_case_create (its sensitivities were allocated there)
- *   box_lo, box_hi [n_gen + n_load], obj_lo, obj_hi, obj_err [1]: DEVICE
+ *   box_lo, box_hi [n_gen + n_load], obj_lo, obj_hi [1], obj_err [2]: DEVICE
  *     pointers; the work is only enqueued on cuda_stream (NULL = legacy
  *     default stream).  Same results as ibp_bound up to FP32 rounding order
  *     (same certified arithmetic, unscaled PTDF rows); flows are not written.

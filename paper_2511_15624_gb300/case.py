@@ -60,7 +60,9 @@ class Case:
     def bound(self, lo, hi, flows: bool = False, stream=None):
         """Certified IBP bound over each box.
 
-        Host (numpy) boxes: returns numpy ``(obj_lo, obj_hi, obj_err)`` and, if
+        Host (numpy) boxes: returns numpy ``(obj_lo, obj_hi, obj_err)`` with
+        ``obj_err[:, 0]`` bounding the error of obj_hi and ``obj_err[:, 1]`` that
+        of obj_lo, and, if
         ``flows``, ``(flow_lo, flow_hi)`` of shape [n_box, n_ctg, n_line].
         CUDA tensors: the same as torch tensors, enqueued on ``stream`` (default:
         torch's current stream) without synchronising.
@@ -70,22 +72,23 @@ class Case:
             lo = lo.contiguous().to(torch.float64)
             hi = hi.contiguous().to(torch.float64)
             nb = int(lo.shape[0]) if lo.dim() == 2 else 1
-            out = torch.empty((3, nb), dtype=torch.float64, device=lo.device)
+            out = torch.empty((2, nb), dtype=torch.float64, device=lo.device)
+            err = torch.empty((nb, 2), dtype=torch.float64, device=lo.device)
             fl = fh = None
             if flows:
                 fl = torch.empty((nb, self.n_ctg, self.n_line), dtype=torch.float32, device=lo.device)
                 fh = torch.empty_like(fl)
             s = stream if stream is not None else torch.cuda.current_stream(lo.device).cuda_stream
-            _abi.ibp_bound(self._h, nb, lo, hi, out[0], out[1], out[2], fl, fh, ptr_mode=1,
+            _abi.ibp_bound(self._h, nb, lo, hi, out[0], out[1], err, fl, fh, ptr_mode=1,
                            stream=s)
-            res = (out[0], out[1], out[2])
+            res = (out[0], out[1], err)
             return res + ((fl, fh) if flows else ())
         lo = np.ascontiguousarray(np.atleast_2d(lo), np.float64)
         hi = np.ascontiguousarray(np.atleast_2d(hi), np.float64)
         if lo.shape != hi.shape or lo.shape[1] != self.n_dev:
             raise ValueError(f"boxes must be [n_box, {self.n_dev}]")
         nb = lo.shape[0]
-        olo, ohi, oerr = np.empty(nb), np.empty(nb), np.empty(nb)
+        olo, ohi, oerr = np.empty(nb), np.empty(nb), np.empty((nb, 2))
         fl = fh = None
         if flows:
             fl = np.empty((nb, self.n_ctg, self.n_line), np.float32)

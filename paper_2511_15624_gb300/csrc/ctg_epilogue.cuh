@@ -13,7 +13,7 @@ constexpr int kConsumerWarps = 8;
 // Epilogue for one (k, l) pair: flow interval, violation interval, error term.
 __device__ __forceinline__ void pair_epilogue(const CtgArgs &a, int box, int l, int k, float Lt,
                                               float A, float &slo_acc, float &shi_acc,
-                                              float &w_acc) {
+                                              float &whi_acc, float &wlo_acc) {
     const int kl = __ldg(&a.ctg_line[k]);
     const size_t ob = (size_t)box * a.n_l;
     const float cl = __ldg(&a.line_c[ob + l]), ck = __ldg(&a.line_c[ob + kl]);
@@ -22,11 +22,11 @@ __device__ __forceinline__ void pair_epilogue(const CtgArgs &a, int box, int l, 
     const float *bc = a.box_consts + (size_t)box * 4;
     const float eta_r = __ldg(&bc[0]), eta_c = __ldg(&bc[1]);
     const float aL = fabsf(Lt);
-    float flo, fhi, slo, shi, w;
+    float flo, fhi, slo, shi, whi, wlo;
     if (l == kl) {
         // the outaged line carries exactly nothing (L[k,k] = -1, like M_k)
         flo = fhi = 0.0f;
-        slo = shi = w = 0.0f;
+        slo = shi = whi = wlo = 0.0f;
     } else {
         const float one_l = __fadd_ru(1.0f, aL);
         const float eta = __fmul_ru(eta_r, one_l);
@@ -48,13 +48,16 @@ __device__ __forceinline__ void pair_epilogue(const CtgArgs &a, int box, int l, 
         const float rup = __ldg(&a.rate_up[l]), rdn = __ldg(&a.rate_dn[l]);
         slo = fmax0(__fsub_rd(alo, rup));
         shi = fmax0(__fsub_ru(ahi, rdn));
-        w = 0.0f;
+        whi = wlo = 0.0f;
         if (shi > 0.0f) {
-            // |s - s_exact| <= (rbar - r_exact) + 2 ec + u rating
-            w = __fmaf_ru(a.gamma + 3.0f * kU, A, __fmaf_ru(8.0f * kU, m, 0.0f));
+            // |s - s_exact| <= w = (rbar - r_exact) + 2 ec + u rating for both
+            // ends; s_hi is exact where it is 0, s_lo where alo - rating + w <= 0
+            float w = __fmaf_ru(a.gamma + 3.0f * kU, A, __fmaf_ru(8.0f * kU, m, 0.0f));
             w = __fmaf_ru(2.0f, ec, w);
             w = __fmaf_ru(kU, rup, w);
             w = __fmaf_ru(2.0f, eta, w);
+            wlo = w;
+            if (__fadd_ru(__fsub_ru(alo, rdn), w) > 0.0f) whi = w;
         }
     }
     if (a.flow_lo) {
@@ -64,21 +67,28 @@ __device__ __forceinline__ void pair_epilogue(const CtgArgs &a, int box, int l, 
     }
     slo_acc = __fadd_rd(slo_acc, slo);
     shi_acc = __fadd_ru(shi_acc, shi);
-    w_acc = __fadd_ru(w_acc, w);
+    whi_acc = __fadd_ru(whi_acc, whi);
+    wlo_acc = __fadd_ru(wlo_acc, wlo);
 }
 
-// Per-warp FP64 partial sums (deterministic tree, directed rounding).
+// Per-warp FP64 partial sums (deterministic tree, directed rounding):
+// {sum s_lo (down), sum s_hi (up), error allowance of obj_hi, of obj_lo}.
+// partial-sum rows per tile: at most the largest warp count of any kernel
+constexpr int kPartRowsPerTile = 16;
+
 __device__ __forceinline__ void write_warp_partials(const CtgArgs &a, int tile, int warp, int box,
-                                                    float slo, float shi, float w) {
+                                                    float slo, float shi, float whi, float wlo) {
     const int lane = threadIdx.x & 31;
     const double dlo = warp_sum_rd((double)slo);
     const double dhi = warp_sum_ru((double)shi);
-    const double dw = warp_sum_ru((double)w);
+    const double dwh = warp_sum_ru((double)whi);
+    const double dwl = warp_sum_ru((double)wlo);
     if (lane == 0) {
-        double *p = a.partials + (((size_t)tile * kConsumerWarps + warp) * a.n_box + box) * 3;
+        double *p = a.partials + (((size_t)tile * a.warps_per_tile + warp) * a.n_box + box) * kPartVals;
         p[0] = dlo;
         p[1] = dhi;
-        p[2] = dw;
+        p[2] = dwh;
+        p[3] = dwl;
     }
 }
 

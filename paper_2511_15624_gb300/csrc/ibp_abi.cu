@@ -555,13 +555,17 @@ ibp_status set_error(ibp_status s, const char *msg) {
 }  // namespace ibp
 
 // ----------------------------------------------------------------- workspace
+// fastest one-box shape measured on GB300 (16 warps, 4x4 pairs per thread,
+// 64-bus chunks, 4-bus round-up add tree)
+constexpr int kDefaultOneBoxVariant = 9;
+
 static const CtgVariant *pick_variant(const ibp_case *c, int n_box) {
     if (c->variant > 0) {
         const CtgVariant *v = ctg_variant_by_id(c->variant);
         if (v && (v->batched != 0) == (n_box > 1)) return v;
     }
     (void)n_box;
-    return ctg_variant_by_id(1);
+    return ctg_variant_by_id(kDefaultOneBoxVariant);
 }
 
 static int max_tiles(const ibp_case *c) {
@@ -580,7 +584,7 @@ static ibp_status ensure_workspace(ibp_case *c, int n_box) {
     const size_t na = c->n_a_pad;
     CUDA_TRY(c->box_lo.alloc((size_t)cap * c->n_dev));
     CUDA_TRY(c->box_hi.alloc((size_t)cap * c->n_dev));
-    CUDA_TRY(c->obj.alloc((size_t)cap * 3));
+    CUDA_TRY(c->obj.alloc((size_t)cap * 4));
     CUDA_TRY(c->cbus.alloc(cap * na));
     CUDA_TRY(c->rbus.alloc(cap * na));
     CUDA_TRY(c->cabs.alloc(cap * na));
@@ -588,8 +592,8 @@ static ibp_status ensure_workspace(ibp_case *c, int n_box) {
     CUDA_TRY(c->line_c.alloc((size_t)cap * c->n_line));
     CUDA_TRY(c->line_e.alloc((size_t)cap * c->n_line));
     CUDA_TRY(c->line_R.alloc((size_t)cap * c->n_line));
-    CUDA_TRY(c->part_base.alloc((size_t)c->n_part_base * cap * 3));
-    CUDA_TRY(c->part_ctg.alloc((size_t)max_tiles(c) * 8 * cap * 3));
+    CUDA_TRY(c->part_base.alloc((size_t)c->n_part_base * cap * kPartVals));
+    CUDA_TRY(c->part_ctg.alloc((size_t)max_tiles(c) * 16 * cap * kPartVals));
     c->cap_box = cap;
     return IBP_OK;
 }
@@ -631,7 +635,7 @@ static ibp_status enqueue_bound(ibp_case *c, int n_box, const double *lo, const 
 
     const int tiles_l = (c->n_line + v->BL - 1) / v->BL;
     const int tiles_k = (c->n_ctg + v->BK - 1) / v->BK;
-    const int n_chunks = (c->n_a + 31) / 32;
+    const int n_chunks = (c->n_a_pad + v->CH - 1) / v->CH;
     CtgArgs ca{};
     ca.n_l = c->n_line; ca.n_c = c->n_ctg; ca.n_a = c->n_a; ca.n_chunks = n_chunks; ca.n_box = n_box;
     ca.tiles_l = tiles_l; ca.n_tiles = tiles_l * tiles_k;
@@ -639,9 +643,17 @@ static ibp_status enqueue_bound(ibp_case *c, int n_box, const double *lo, const 
     ca.line_c = c->line_c.p; ca.line_e = c->line_e.p; ca.line_R = c->line_R.p;
     ca.rate_up = c->rate_c_up.p; ca.rate_dn = c->rate_c_dn.p; ca.box_consts = c->box_consts.p;
     ca.rbus_t = nullptr; ca.n_box_pad = 0;
-    ca.gamma = rup_gamma(32, 8, (n_chunks + 7) / 8);
+    // round-up adds per radius sum: level 1 within a chunk (one per bus, or a
+    // depth-2 tree per 4 buses plus one add), level 2 over 256/CH chunks, level 3
+    {
+        const bool tree = v->id >= 6;
+        const long n1 = tree ? v->CH / 4 + 2 : v->CH;
+        const long n2 = 256 / v->CH;
+        ca.gamma = rup_gamma(n1, n2, (n_chunks + n2 - 1) / n2);
+    }
     ca.flow_lo = flo; ca.flow_hi = fhi; ca.partials = c->part_ctg.p; ca.err = c->err.p;
     ca.wait_ns = 2000000000ull;
+    ca.warps_per_tile = ctg_warps(*v);
     if (ca.n_tiles > 0) {
         CUtensorMap mL, mK;
         std::string err;
@@ -654,7 +666,7 @@ static ibp_status enqueue_bound(ibp_case *c, int n_box, const double *lo, const 
 
     AsmArgs aa{};
     aa.n_box = n_box; aa.n_dev = c->n_dev; aa.n_gen = c->n_gen;
-    aa.n_part_ctg = ca.n_tiles * 8; aa.n_part_base = c->n_part_base;
+    aa.n_part_ctg = ca.n_tiles * ca.warps_per_tile; aa.n_part_base = c->n_part_base;
     aa.part_ctg = c->part_ctg.p; aa.part_base = c->part_base.p; aa.box_lo = lo; aa.box_hi = hi;
     aa.seg_ptr = c->seg_ptr.p; aa.slope = c->slope.p; aa.bkpt = c->bkpt.p;
     aa.zeta_inj = c->zeta_inj; aa.zeta_f = c->zeta_f;
@@ -725,7 +737,7 @@ extern "C" ibp_status ibp_bound(ibp_case *c, int32_t n_box, const double *box_lo
     if (st != IBP_OK) return st;
     CUDA_TRY(cudaMemcpyAsync(obj_lo, dobj, n_box * sizeof(double), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaMemcpyAsync(obj_hi, dobj + n_box, n_box * sizeof(double), cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(cudaMemcpyAsync(obj_err, dobj + 2 * n_box, n_box * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(obj_err, dobj + 2 * n_box, 2 * n_box * sizeof(double), cudaMemcpyDeviceToHost, s));
     if (dflo) {
         CUDA_TRY(cudaMemcpyAsync(flow_lo, dflo, nf * sizeof(float), cudaMemcpyDeviceToHost, s));
         CUDA_TRY(cudaMemcpyAsync(flow_hi, dfhi, nf * sizeof(float), cudaMemcpyDeviceToHost, s));

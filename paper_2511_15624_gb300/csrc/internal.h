@@ -15,6 +15,8 @@ namespace ibp {
 // error word bits (device -> host)
 constexpr int kErrTimeout = 1;
 constexpr int kErrBadBox = 2;
+// values per partial-sum row: sum s_lo, sum s_hi, error of obj_hi, error of obj_lo
+constexpr int kPartVals = 4;
 
 // ---------------------------------------------------------------- kernel args
 struct BusArgs {
@@ -48,7 +50,7 @@ struct BaseArgs {
     float *line_R;           // [n_box][n_l] radius sum, rounded up
     float *hat_l;            // [n_l][n_a_pad] Phi * r (one-box mode) or null
     float *hat_k;            // [n_c][n_a_pad] Phi[ctg line] * r or null
-    double *partials;        // [n_part][n_box][3]
+    double *partials;        // [n_part][n_box][kPartVals]
 };
 
 struct CtgArgs {
@@ -63,7 +65,8 @@ struct CtgArgs {
     int n_box_pad;
     float gamma;             // worst-case relative excess of the RU radius sums
     float *flow_lo, *flow_hi;  // [n_box][n_c][n_l] or null
-    double *partials;        // [n_tiles * 8][n_box][3]
+    double *partials;        // [n_tiles * warps_per_tile][n_box][kPartVals]
+    int warps_per_tile;      // partial-sum rows written per tile
     int *err;
     unsigned long long wait_ns;
 };
@@ -71,13 +74,13 @@ struct CtgArgs {
 struct AsmArgs {
     int n_box, n_dev, n_gen;
     int n_part_ctg, n_part_base;
-    const double *part_ctg;   // [n_part_ctg][n_box][3]
-    const double *part_base;  // [n_part_base][n_box][3]
+    const double *part_ctg;   // [n_part_ctg][n_box][kPartVals]
+    const double *part_base;  // [n_part_base][n_box][kPartVals]
     const double *box_lo, *box_hi;
     const int *seg_ptr;       // [n_dev + 1]
     const double *slope, *bkpt;
     double zeta_inj, zeta_f;
-    double *obj_lo, *obj_hi, *obj_err;
+    double *obj_lo, *obj_hi, *obj_err;  // obj_err [n_box][2]: error of hi, of lo
     const int *err;
 };
 
@@ -92,6 +95,7 @@ struct CtgVariant {
 
 const CtgVariant *ctg_variants(int *count);
 const CtgVariant *ctg_variant_by_id(int id);
+int ctg_warps(const CtgVariant &v);
 
 // launchers (return cudaError_t of the launch)
 cudaError_t launch_bus(const BusArgs &a, cudaStream_t s);

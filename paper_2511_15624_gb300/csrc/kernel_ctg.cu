@@ -37,59 +37,91 @@
 
 namespace ibp {
 
-constexpr int kThreads = kConsumerWarps * 32;
+// Tile order: bands of kBand line tiles; inside a band the contingency tiles
+// run slowest, so the tiles in flight at one time (one per SM) touch about
+// kBand line-row blocks and 152/kBand contingency-row blocks, which stay in L2.
+constexpr int kBand = 8;
 
-template <int BL, int BK, int ST>
-struct SmemLayout {
-    static constexpr int CH = 32;  // buses per chunk: one 128-byte swizzled row
+__device__ __forceinline__ void tile_origin(int tile, int tiles_l, int tiles_k, int BL, int BK,
+                                            int &l0, int &k0) {
+    const int per_band = kBand * tiles_k;
+    const int band = tile / per_band, r = tile % per_band;
+    const int g = min(kBand, tiles_l - band * kBand);
+    l0 = (band * kBand + r % g) * BL;
+    k0 = (r / g) * BK;
+}
+
+template <int WL, int WK, int ML, int MK, int ST, bool S3 = false, int CH_ = 32>
+struct Shape {
+    static constexpr int kWarps = WL * WK;
+    static constexpr int kThreads = kWarps * 32;
+    static constexpr int TL = WL * 4, TK = WK * 8;  // threads along lines / contingencies
+    static constexpr int BL = TL * ML, BK = TK * MK;
+    static constexpr int CH = CH_;                  // buses per chunk
+    static constexpr int NSUB = CH / 32;            // 128-byte swizzled sub-blocks per row
     static constexpr int kStageFloats = (BL + BK) * CH;
     static constexpr size_t kRing = (size_t)ST * kStageFloats * sizeof(float);
+    // level-3 radius sums in shared memory when S3: [slot][thread]
+    static constexpr size_t kAcc3 = S3 ? (size_t)ML * MK * kThreads * sizeof(float) : 0;
     // full[ST] mbarriers, arrival counters[ST], last issued chunk[ST], abort flag
     static constexpr size_t kCtl = ST * sizeof(uint64_t) + 2 * ST * sizeof(int) + 16;
-    static constexpr size_t kBytes = kRing + kCtl + 1024;
+    static constexpr size_t kBytes = kRing + kAcc3 + kCtl + 1024;
+    static_assert(TL % 8 == 0 && TK % 8 == 0, "swizzle phase must be per-thread constant");
+    static_assert(CH == 32 || CH == 64, "chunk of one or two 128-byte rows");
+    static_assert(BL <= 256 && BK <= 256, "TMA box rows");
 };
 
 // Issue the TMA copies of chunk c (global index within this CTA's tile list).
-template <int BL, int BK, int ST>
+template <class S, int ST>
 __device__ __forceinline__ void issue_chunk(const CUtensorMap *mL, const CUtensorMap *mK,
                                             const CtgArgs &a, float *ring, uint64_t *full,
-                                            int *last_issued, uint32_t c) {
-    using S = SmemLayout<BL, BK, ST>;
+                                            int *last_issued, uint32_t c, int tiles_k) {
     constexpr uint32_t kBytes = (uint32_t)S::kStageFloats * sizeof(float);
     const int s = (int)(c % ST);
     const int ti = (int)(c / (uint32_t)a.n_chunks), ch = (int)(c % (uint32_t)a.n_chunks);
     const int tile = blockIdx.x + ti * gridDim.x;
-    const int l0 = (tile % a.tiles_l) * BL, k0 = (tile / a.tiles_l) * BK;
+    int l0, k0;
+    tile_origin(tile, a.tiles_l, tiles_k, S::BL, S::BK, l0, k0);
+    // stage layout: [sub][BL rows][32] line block, then [sub][BK rows][32]
     float *sL = ring + (size_t)s * S::kStageFloats;
-    float *sK = sL + BL * S::CH;
+    float *sK = sL + S::BL * S::CH;
     last_issued[s] = (int)c;
     mbar_arrive_expect_tx(smem_addr(&full[s]), kBytes);
-    tma_load_2d(smem_addr(sL), mL, smem_addr(&full[s]), ch * S::CH, l0);
-    tma_load_2d(smem_addr(sK), mK, smem_addr(&full[s]), ch * S::CH, k0);
+#pragma unroll
+    for (int sub = 0; sub < S::NSUB; ++sub) {
+        tma_load_2d(smem_addr(sL + sub * S::BL * 32), mL, smem_addr(&full[s]), ch * S::CH + 32 * sub, l0);
+        tma_load_2d(smem_addr(sK + sub * S::BK * 32), mK, smem_addr(&full[s]), ch * S::CH + 32 * sub, k0);
+    }
 }
 
 // ---------------------------------------------------------------------------
-// One-box kernel (scaled rows).  Tile BL x BK, thread micro-tile ML x MK with
-// lines tl + 16 i and contingencies tk + 16 j.  No dedicated producer warp:
-// the warp that releases a stage last (cumulative shared counter) refills it
-// with the chunk ST ahead, so no warp waits for "stage empty".
+// One-box kernel (scaled rows).  WL x WK warps; a warp is 4 line-lanes x 8
+// contingency-lanes; thread (tl, tk) owns lines tl + TL i (i < ML) and
+// contingencies tk + TK j (j < MK).  No dedicated producer warp: the warp
+// that releases a stage last (cumulative shared counter) refills it with the
+// chunk ST ahead, so no warp waits for "stage empty".
 // ---------------------------------------------------------------------------
-template <int BL, int BK, int ST>
-__global__ void __launch_bounds__(kThreads, 1)
+template <int WL, int WK, int ML, int MK, int ST, bool S3, int CH_, int BODY, int MINB>
+__global__ void __launch_bounds__(WL * WK * 32, MINB)
     k_ctg_one(const __grid_constant__ CUtensorMap mL, const __grid_constant__ CUtensorMap mK,
               const CtgArgs a) {
-    using S = SmemLayout<BL, BK, ST>;
-    constexpr int ML = BL / 16, MK = BK / 16;
-    constexpr int CH = S::CH;
+    using S = Shape<WL, WK, ML, MK, ST, S3, CH_>;
+    constexpr int CH = S::CH, TL = S::TL, TK = S::TK, BL = S::BL;
     extern __shared__ unsigned char smem_raw[];
     float *ring = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                             ~uintptr_t(1023));
-    uint64_t *full = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(ring) + S::kRing);
+    float *acc3s = reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(ring) + S::kRing) +
+                   threadIdx.x;  // slot (i, j) at acc3s[(i * MK + j) * kThreads]
+    uint64_t *full = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(ring) + S::kRing +
+                                                  S::kAcc3);
     int *arrivals = reinterpret_cast<int *>(full + ST);
     int *last_issued = arrivals + ST;
     volatile int *abort_flag = last_issued + ST;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // level-2 sums are folded into level 3 every kFold3 chunks (256 buses)
+    constexpr int kFold3 = 256 / CH;
+    const int tiles_k = (a.n_c + S::BK - 1) / S::BK;
     const int my_tiles = (a.n_tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
     const uint32_t total = (uint32_t)my_tiles * (uint32_t)a.n_chunks;
     if (threadIdx.x == 0) {
@@ -106,28 +138,33 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     if (threadIdx.x == 0)
         for (uint32_t c = 0; c < total && c < (uint32_t)ST; ++c)
-            issue_chunk<BL, BK, ST>(&mL, &mK, a, ring, full, last_issued, c);
+            issue_chunk<S, ST>(&mL, &mK, a, ring, full, last_issued, c, tiles_k);
 
-    const int tl = (warp >> 1) * 4 + (lane >> 3);
-    const int tk = (warp & 1) * 8 + (lane & 7);
+    const int tl = (warp / WK) * 4 + (lane >> 3);
+    const int tk = (warp % WK) * 8 + (lane & 7);
     const int xl = tl & 7, xk = tk & 7;  // SWIZZLE_128B: chunk q of row r sits at q ^ (r & 7)
     uint32_t it = 0;
     bool stop = false;
     for (int tile = blockIdx.x; tile < a.n_tiles && !stop; tile += gridDim.x) {
-        const int l0 = (tile % a.tiles_l) * BL, k0 = (tile / a.tiles_l) * BK;
+        int l0, k0;
+        tile_origin(tile, a.tiles_l, tiles_k, S::BL, S::BK, l0, k0);
         float Lr[ML][MK];
 #pragma unroll
         for (int i = 0; i < ML; ++i)
 #pragma unroll
             for (int j = 0; j < MK; ++j) {
-                const int l = l0 + tl + 16 * i, k = k0 + tk + 16 * j;
+                const int l = l0 + tl + TL * i, k = k0 + tk + TK * j;
                 Lr[i][j] = (l < a.n_l && k < a.n_c) ? __ldg(&a.lodf[(size_t)k * a.n_l + l]) : 0.0f;
             }
-        float acc1[ML][MK], acc2[ML][MK], acc3[ML][MK];
+        float acc1[ML][MK], acc2[ML][MK], acc3[S3 ? 1 : ML][S3 ? 1 : MK];
 #pragma unroll
         for (int i = 0; i < ML; ++i)
 #pragma unroll
-            for (int j = 0; j < MK; ++j) acc1[i][j] = acc2[i][j] = acc3[i][j] = 0.0f;
+            for (int j = 0; j < MK; ++j) {
+                acc1[i][j] = acc2[i][j] = 0.0f;
+                if constexpr (S3) acc3s[(i * MK + j) * S::kThreads] = 0.0f;
+                else acc3[i][j] = 0.0f;
+            }
 
         for (int ch = 0; ch < a.n_chunks; ++ch, ++it) {
             const int s = (int)(it % ST);
@@ -146,39 +183,53 @@ __global__ void __launch_bounds__(kThreads, 1)
             const float *sK = sL + BL * CH;
 #pragma unroll
             for (int q = 0; q < CH / 4; ++q) {
+                // 16-byte group q of the chunk: sub-block q / 8, swizzled slot (q % 8) ^ (row & 7)
+                const int sub = q >> 3, qq = q & 7;
+                const float *bL = sL + sub * BL * 32, *bK = sK + sub * S::BK * 32;
                 float4 fk[MK];
-                const int ok4 = (q ^ xk) << 2, ol4 = (q ^ xl) << 2;
+                const int ok4 = (qq ^ xk) << 2, ol4 = (qq ^ xl) << 2;
 #pragma unroll
                 for (int j = 0; j < MK; ++j)
-                    fk[j] = *reinterpret_cast<const float4 *>(sK + (tk + 16 * j) * CH + ok4);
+                    fk[j] = *reinterpret_cast<const float4 *>(bK + (tk + TK * j) * 32 + ok4);
 #pragma unroll
                 for (int i = 0; i < ML; ++i) {
-                    const float4 fl = *reinterpret_cast<const float4 *>(sL + (tl + 16 * i) * CH + ol4);
+                    const float4 fl = *reinterpret_cast<const float4 *>(bL + (tl + TL * i) * 32 + ol4);
 #pragma unroll
                     for (int j = 0; j < MK; ++j) {
                         const float L = Lr[i][j];
-                        float h;
-                        h = __fmaf_rn(L, fk[j].x, fl.x);
-                        acc1[i][j] = __fadd_ru(acc1[i][j], fabsf(h));
-                        h = __fmaf_rn(L, fk[j].y, fl.y);
-                        acc1[i][j] = __fadd_ru(acc1[i][j], fabsf(h));
-                        h = __fmaf_rn(L, fk[j].z, fl.z);
-                        acc1[i][j] = __fadd_ru(acc1[i][j], fabsf(h));
-                        h = __fmaf_rn(L, fk[j].w, fl.w);
-                        acc1[i][j] = __fadd_ru(acc1[i][j], fabsf(h));
+                        if constexpr (BODY == 0) {
+                            float h;
+                            h = __fmaf_rn(L, fk[j].x, fl.x);
+                            acc1[i][j] = __fadd_ru(acc1[i][j], fabsf(h));
+                            h = __fmaf_rn(L, fk[j].y, fl.y);
+                            acc1[i][j] = __fadd_ru(acc1[i][j], fabsf(h));
+                            h = __fmaf_rn(L, fk[j].z, fl.z);
+                            acc1[i][j] = __fadd_ru(acc1[i][j], fabsf(h));
+                            h = __fmaf_rn(L, fk[j].w, fl.w);
+                            acc1[i][j] = __fadd_ru(acc1[i][j], fabsf(h));
+                        } else {
+                            // four buses summed as a round-up tree, then accumulated
+                            const float h0 = __fmaf_rn(L, fk[j].x, fl.x);
+                            const float h1 = __fmaf_rn(L, fk[j].y, fl.y);
+                            const float h2 = __fmaf_rn(L, fk[j].z, fl.z);
+                            const float h3 = __fmaf_rn(L, fk[j].w, fl.w);
+                            const float s01 = __fadd_ru(fabsf(h0), fabsf(h1));
+                            const float s23 = __fadd_ru(fabsf(h2), fabsf(h3));
+                            acc1[i][j] = __fadd_ru(acc1[i][j], __fadd_ru(s01, s23));
+                        }
                     }
                 }
             }
             __syncwarp();
             if (lane == 0) {
-                // release the stage; the last of the 8 warps refills it
+                // release the stage; the last of the warps refills it
                 __threadfence_block();
                 const int old = atomicAdd(&arrivals[s], 1);
-                if (old == (int)(it / ST) * kConsumerWarps + kConsumerWarps - 1) {
+                if (old == (int)(it / ST) * S::kWarps + S::kWarps - 1) {
                     const uint32_t nxt = it + ST;
                     if (nxt < total && !*abort_flag) {
                         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                        issue_chunk<BL, BK, ST>(&mL, &mK, a, ring, full, last_issued, nxt);
+                        issue_chunk<S, ST>(&mL, &mK, a, ring, full, last_issued, nxt, tiles_k);
                     }
                 }
             }
@@ -189,29 +240,36 @@ __global__ void __launch_bounds__(kThreads, 1)
                     acc2[i][j] = __fadd_ru(acc2[i][j], acc1[i][j]);
                     acc1[i][j] = 0.0f;
                 }
-            if ((ch & 7) == 7) {
+            if ((ch & (kFold3 - 1)) == kFold3 - 1) {
 #pragma unroll
                 for (int i = 0; i < ML; ++i)
 #pragma unroll
                     for (int j = 0; j < MK; ++j) {
-                        acc3[i][j] = __fadd_ru(acc3[i][j], acc2[i][j]);
+                        if constexpr (S3) {
+                            float &a3 = acc3s[(i * MK + j) * S::kThreads];
+                            a3 = __fadd_ru(a3, acc2[i][j]);
+                        } else {
+                            acc3[i][j] = __fadd_ru(acc3[i][j], acc2[i][j]);
+                        }
                         acc2[i][j] = 0.0f;
                     }
             }
         }
         if (stop) break;
-        float slo = 0.0f, shi = 0.0f, w = 0.0f;
+        float slo = 0.0f, shi = 0.0f, whi = 0.0f, wlo = 0.0f;
 #pragma unroll
         for (int i = 0; i < ML; ++i)
 #pragma unroll
             for (int j = 0; j < MK; ++j) {
-                const int l = l0 + tl + 16 * i, k = k0 + tk + 16 * j;
+                const int l = l0 + tl + TL * i, k = k0 + tk + TK * j;
                 if (l < a.n_l && k < a.n_c) {
-                    const float A = __fadd_ru(acc3[i][j], acc2[i][j]);
-                    pair_epilogue(a, 0, l, k, Lr[i][j], A, slo, shi, w);
+                    float a3;
+                    if constexpr (S3) a3 = acc3s[(i * MK + j) * S::kThreads];
+                    else a3 = acc3[i][j];
+                    pair_epilogue(a, 0, l, k, Lr[i][j], __fadd_ru(a3, acc2[i][j]), slo, shi, whi, wlo);
                 }
             }
-        write_warp_partials(a, tile, warp, 0, slo, shi, w);
+        write_warp_partials(a, tile, warp, 0, slo, shi, whi, wlo);
     }
     // Every warp gets here (all waits are bounded).  After an abort, copies
     // may still be in flight: wait (bounded) for the last one of each stage.
@@ -227,9 +285,17 @@ __global__ void __launch_bounds__(kThreads, 1)
 // ---------------------------------------------------------------------------
 // Variant table and launcher
 // ---------------------------------------------------------------------------
+// {id, batched, BL, BK, CH, ST, boxes per thread, name}; warps and the loop
+// body are fixed per id in launch_ctg / ctg_warps.
 static const CtgVariant kVariants[] = {
-    {1, 0, 128, 64, 32, 4, 1, "one-box 128x64 st4"},
-    {2, 0, 128, 64, 32, 6, 1, "one-box 128x64 st6"},
+    {1, 0, 128, 64, 32, 4, 1, "8 warps, 8x4/thread, 32-bus chunks, 4 stages, 1 add per bus"},
+    {3, 0, 128, 64, 32, 4, 1, "16 warps, 4x4/thread, 32-bus chunks, 4 stages, 1 add per bus"},
+    {6, 0, 128, 64, 32, 4, 1, "8 warps, 8x4/thread, 32-bus chunks, 4 stages, 4-bus add tree"},
+    {7, 0, 128, 64, 64, 3, 1, "8 warps, 8x4/thread, 64-bus chunks, 3 stages, 4-bus add tree"},
+    {8, 0, 128, 64, 32, 4, 1, "16 warps, 4x4/thread, 32-bus chunks, 4 stages, 4-bus add tree"},
+    {9, 0, 128, 64, 64, 3, 1, "16 warps, 4x4/thread, 64-bus chunks, 3 stages, 4-bus add tree"},
+    {10, 0, 64, 64, 32, 4, 1, "2 CTAs/SM x 8 warps, 4x4/thread, 32-bus chunks, 4 stages, tree"},
+    {11, 0, 64, 64, 64, 2, 1, "2 CTAs/SM x 8 warps, 4x4/thread, 64-bus chunks, 2 stages, tree"},
 };
 
 const CtgVariant *ctg_variants(int *count) {
@@ -245,33 +311,47 @@ const CtgVariant *ctg_variant_by_id(int id) {
     return nullptr;
 }
 
-template <int BL, int BK, int ST>
+template <int WL, int WK, int ML, int MK, int ST, bool S3, int CH, int BODY, int MINB = 1>
 static cudaError_t launch_one(const CUtensorMap &mL, const CUtensorMap &mK, const CtgArgs &a,
                               int grid, cudaStream_t s) {
-    using S = SmemLayout<BL, BK, ST>;
-    auto kern = k_ctg_one<BL, BK, ST>;
+    using S = Shape<WL, WK, ML, MK, ST, S3, CH>;
+    auto kern = k_ctg_one<WL, WK, ML, MK, ST, S3, CH, BODY, MINB>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)S::kBytes);
     if (e != cudaSuccess) return e;
     cudaFuncAttributes fa;
     e = cudaFuncGetAttributes(&fa, kern);
     if (e != cudaSuccess) return e;
-    if (fa.maxThreadsPerBlock < kThreads) {
+    if (fa.maxThreadsPerBlock < S::kThreads) {
         fprintf(stderr, "k_ctg_one: %d registers allow only %d threads per block (need %d)\n",
-                fa.numRegs, fa.maxThreadsPerBlock, kThreads);
+                fa.numRegs, fa.maxThreadsPerBlock, S::kThreads);
         return cudaErrorLaunchOutOfResources;
     }
-    kern<<<grid, kThreads, S::kBytes, s>>>(mL, mK, a);
+    // persistent grid: as many CTAs as fit on the SMs at once
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, S::kThreads, S::kBytes);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorLaunchOutOfResources;
+    grid = std::min(grid * per_sm, a.n_tiles);
+    kern<<<grid, S::kThreads, S::kBytes, s>>>(mL, mK, a);
     return cudaGetLastError();
 }
+
+int ctg_warps(const CtgVariant &v) { return (v.id == 3 || v.id == 8 || v.id == 9) ? 16 : 8; }
 
 cudaError_t launch_ctg(const CtgVariant &v, const CUtensorMap &mL, const CUtensorMap &mK,
                        const CtgArgs &a, int grid, cudaStream_t s) {
     if (a.n_tiles <= 0) return cudaSuccess;
     grid = std::min(grid, a.n_tiles);
     switch (v.id) {
-    case 1: return launch_one<128, 64, 4>(mL, mK, a, grid, s);
-    case 2: return launch_one<128, 64, 6>(mL, mK, a, grid, s);
+    case 1: return launch_one<4, 2, 8, 4, 4, false, 32, 0>(mL, mK, a, grid, s);
+    case 3: return launch_one<8, 2, 4, 4, 4, true, 32, 0>(mL, mK, a, grid, s);
+    case 6: return launch_one<4, 2, 8, 4, 4, false, 32, 1>(mL, mK, a, grid, s);
+    case 7: return launch_one<4, 2, 8, 4, 3, false, 64, 1>(mL, mK, a, grid, s);
+    case 8: return launch_one<8, 2, 4, 4, 4, true, 32, 1>(mL, mK, a, grid, s);
+    case 9: return launch_one<8, 2, 4, 4, 3, true, 64, 1>(mL, mK, a, grid, s);
+    case 10: return launch_one<4, 2, 4, 4, 4, true, 32, 1, 2>(mL, mK, a, grid, s);
+    case 11: return launch_one<4, 2, 4, 4, 2, true, 64, 1, 2>(mL, mK, a, grid, s);
     default: return cudaErrorInvalidValue;
     }
 }

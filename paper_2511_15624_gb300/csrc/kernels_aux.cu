@@ -123,14 +123,10 @@ __global__ void __launch_bounds__(kBaseWarps * 32) k_base(BaseArgs a) {
     const bool scaled = a.hat_l != nullptr;
     const int n_rows = a.n_l + (scaled ? a.n_c : 0);
     const int nv = a.n_a_pad >> 2;  // float4 per row
-    double *part = a.partials + (size_t)gw * a.n_box * 3;
-    for (int j = 0; j < a.n_box; ++j) {
-        if (lane == 0) {
-            part[j * 3 + 0] = 0.0;
-            part[j * 3 + 1] = 0.0;
-            part[j * 3 + 2] = 0.0;
-        }
-    }
+    double *part = a.partials + (size_t)gw * a.n_box * kPartVals;
+    for (int j = 0; j < a.n_box; ++j)
+        if (lane == 0)
+            for (int v = 0; v < kPartVals; ++v) part[j * kPartVals + v] = 0.0;
     for (int row = gw; row < n_rows; row += nw) {
         if (row >= a.n_l) {
             // scaled copy of a contingency line's row (one-box mode)
@@ -193,17 +189,23 @@ __global__ void __launch_bounds__(kBaseWarps * 32) k_base(BaseArgs a) {
                 abs_interval(flo, fhi, alo, ahi);
                 const float slo = fmax0(__fsub_rd(alo, a.rate_up[l]));
                 const float shi = fmax0(__fsub_ru(ahi, a.rate_dn[l]));
-                float w = 0.0f;
+                float whi = 0.0f, wlo = 0.0f;
                 if (shi > 0.0f) {
-                    // |s - s_exact| <= (rbar - R_exact) + 2 e + u rating
-                    w = __fmaf_ru(a.gamma_base + 3.0f * kU, R, __fmaf_ru(2.0f, e, __fmaf_ru(kU, a.rate_up[l], 2.0f * eta_r)));
+                    // |s - s_exact| <= w = (rbar - R_exact) + 2 e + u rating; s_lo is
+                    // exact where alo - rating + w <= 0
+                    const float w = __fmaf_ru(a.gamma_base + 3.0f * kU, R,
+                                              __fmaf_ru(2.0f, e, __fmaf_ru(kU, a.rate_up[l], 2.0f * eta_r)));
+                    wlo = w;
+                    if (__fadd_ru(__fsub_ru(alo, a.rate_dn[l]), w) > 0.0f) whi = w;
                 }
                 a.line_c[(size_t)j * a.n_l + l] = c;
                 a.line_e[(size_t)j * a.n_l + l] = e;
                 a.line_R[(size_t)j * a.n_l + l] = R;
-                part[j * 3 + 0] = __dadd_rd(part[j * 3 + 0], (double)slo);
-                part[j * 3 + 1] = __dadd_ru(part[j * 3 + 1], (double)shi);
-                part[j * 3 + 2] = __dadd_ru(part[j * 3 + 2], (double)w);
+                double *q = part + j * kPartVals;
+                q[0] = __dadd_rd(q[0], (double)slo);
+                q[1] = __dadd_ru(q[1], (double)shi);
+                q[2] = __dadd_ru(q[2], (double)whi);
+                q[3] = __dadd_ru(q[3], (double)wlo);
             }
             hl = nullptr;
         }
@@ -270,25 +272,27 @@ __device__ __forceinline__ void block_sum(double *v, int n, bool *up, double *sh
 
 __global__ void __launch_bounds__(256) k_assemble(AsmArgs a) {
     const int j = blockIdx.x;
-    // 0 Sfc_lo(rd) 1 Sfc_hi(ru) 2 Wfc(ru) 3 Sfb_lo 4 Sfb_hi 5 Wfb
-    // 6 Clo_dn 7 Chi_up 8 Glo_dn 9 Ghi_up 10 cost_err(ru)
-    // 11 Plo_dn 12 Plo_up 13 Phi_dn 14 Phi_up
-    constexpr int N = 15;
+    // 0 Sfc_lo(rd) 1 Sfc_hi(ru) 2 Wfc_hi(ru) 3 Wfc_lo(ru) 4 Sfb_lo 5 Sfb_hi 6 Wfb_hi 7 Wfb_lo
+    // 8 Clo_dn 9 Chi_up 10 Glo_dn 11 Ghi_up 12 cost_err_hi(ru) 13 cost_err_lo(ru)
+    // 14 Plo_dn 15 Plo_up 16 Phi_dn 17 Phi_up
+    constexpr int N = 18;
     double v[N];
-    bool up[N] = {false, true, true, false, true, true, false, true, false, true, true,
-                  false, true, false, true};
+    bool up[N] = {false, true, true, true, false, true, true, true, false, true, false, true,
+                  true, true, false, true, false, true};
     for (int i = 0; i < N; ++i) v[i] = 0.0;
     for (int p = threadIdx.x; p < a.n_part_ctg; p += blockDim.x) {
-        const double *q = a.part_ctg + ((size_t)p * a.n_box + j) * 3;
+        const double *q = a.part_ctg + ((size_t)p * a.n_box + j) * kPartVals;
         v[0] = __dadd_rd(v[0], q[0]);
         v[1] = __dadd_ru(v[1], q[1]);
         v[2] = __dadd_ru(v[2], q[2]);
+        v[3] = __dadd_ru(v[3], q[3]);
     }
     for (int p = threadIdx.x; p < a.n_part_base; p += blockDim.x) {
-        const double *q = a.part_base + ((size_t)p * a.n_box + j) * 3;
-        v[3] = __dadd_rd(v[3], q[0]);
-        v[4] = __dadd_ru(v[4], q[1]);
-        v[5] = __dadd_ru(v[5], q[2]);
+        const double *q = a.part_base + ((size_t)p * a.n_box + j) * kPartVals;
+        v[4] = __dadd_rd(v[4], q[0]);
+        v[5] = __dadd_ru(v[5], q[1]);
+        v[6] = __dadd_ru(v[6], q[2]);
+        v[7] = __dadd_ru(v[7], q[3]);
     }
     const double *lo = a.box_lo + (size_t)j * a.n_dev;
     const double *hi = a.box_hi + (size_t)j * a.n_dev;
@@ -299,28 +303,31 @@ __global__ void __launch_bounds__(256) k_assemble(AsmArgs a) {
         const double vlo_up = pwl_eval(sl, bk, ns, lo[d], true);
         const double vhi_dn = pwl_eval(sl, bk, ns, hi[d], false);
         const double vhi_up = pwl_eval(sl, bk, ns, hi[d], true);
-        if (d >= a.n_gen) {  // load value c_j
-            v[6] = __dadd_rd(v[6], vlo_dn);
-            v[7] = __dadd_ru(v[7], vhi_up);
-            v[11] = __dadd_rd(v[11], -hi[d]);
-            v[12] = __dadd_ru(v[12], -hi[d]);
-            v[13] = __dadd_rd(v[13], -lo[d]);
-            v[14] = __dadd_ru(v[14], -lo[d]);
-        } else {  // generator cost g_i
+        if (d >= a.n_gen) {  // load value c_j: C(hi) enters obj_hi, C(lo) enters obj_lo
             v[8] = __dadd_rd(v[8], vlo_dn);
             v[9] = __dadd_ru(v[9], vhi_up);
-            v[11] = __dadd_rd(v[11], lo[d]);
-            v[12] = __dadd_ru(v[12], lo[d]);
-            v[13] = __dadd_rd(v[13], hi[d]);
-            v[14] = __dadd_ru(v[14], hi[d]);
+            v[12] = __dadd_ru(v[12], __dsub_ru(vhi_up, vhi_dn));
+            v[13] = __dadd_ru(v[13], __dsub_ru(vlo_up, vlo_dn));
+            v[14] = __dadd_rd(v[14], -hi[d]);
+            v[15] = __dadd_ru(v[15], -hi[d]);
+            v[16] = __dadd_rd(v[16], -lo[d]);
+            v[17] = __dadd_ru(v[17], -lo[d]);
+        } else {  // generator cost g_i: G(lo) enters obj_hi, G(hi) enters obj_lo
+            v[10] = __dadd_rd(v[10], vlo_dn);
+            v[11] = __dadd_ru(v[11], vhi_up);
+            v[12] = __dadd_ru(v[12], __dsub_ru(vlo_up, vlo_dn));
+            v[13] = __dadd_ru(v[13], __dsub_ru(vhi_up, vhi_dn));
+            v[14] = __dadd_rd(v[14], lo[d]);
+            v[15] = __dadd_ru(v[15], lo[d]);
+            v[16] = __dadd_rd(v[16], hi[d]);
+            v[17] = __dadd_ru(v[17], hi[d]);
         }
-        v[10] = __dadd_ru(v[10], __dadd_ru(__dsub_ru(vlo_up, vlo_dn), __dsub_ru(vhi_up, vhi_dn)));
     }
     __shared__ double sh[8 * N];
     block_sum(v, N, up, sh);
     if (threadIdx.x == 0) {
         // total injection interval [Plo, Phi] enclosed by [Plo_dn, Phi_up]
-        const double plo = v[11], phi = v[14];
+        const double plo = v[14], phi = v[17];
         double ilo, ihi;
         if (plo >= 0.0) {
             ilo = plo;
@@ -332,25 +339,30 @@ __global__ void __launch_bounds__(256) k_assemble(AsmArgs a) {
             ilo = 0.0;
             ihi = fmax(-plo, phi);
         }
-        const double w_inj = fmax(__dsub_ru(v[12], v[11]), __dsub_ru(v[14], v[13]));
+        const double w_inj = fmax(__dsub_ru(v[15], v[14]), __dsub_ru(v[17], v[16]));
         const double pen_dn = __dadd_rd(__dmul_rd(a.zeta_inj, ilo),
-                                        __dmul_rd(a.zeta_f, __dadd_rd(v[3], v[0])));
+                                        __dmul_rd(a.zeta_f, __dadd_rd(v[4], v[0])));
         const double pen_up = __dadd_ru(__dmul_ru(a.zeta_inj, ihi),
-                                        __dmul_ru(a.zeta_f, __dadd_ru(v[4], v[1])));
-        double ohi = __dsub_ru(__dsub_ru(v[7], v[8]), pen_dn);
-        double olo = __dsub_rd(__dsub_rd(v[6], v[9]), pen_up);
-        // error: FP32 allowances of the flow terms, the imbalance enclosure,
-        // the cost enclosures, plus FP64 summation of the partial sums
-        double err = __dmul_ru(a.zeta_f, __dadd_ru(v[2], v[5]));
-        err = __dadd_ru(err, __dmul_ru(a.zeta_inj, w_inj));
-        err = __dadd_ru(err, v[10]);
-        err = __dadd_ru(err, __dmul_ru(1e-12, __dadd_ru(__dadd_ru(fabs(v[7]), fabs(v[9])), pen_up)));
+                                        __dmul_ru(a.zeta_f, __dadd_ru(v[5], v[1])));
+        double ohi = __dsub_ru(__dsub_ru(v[9], v[10]), pen_dn);
+        double olo = __dsub_rd(__dsub_rd(v[8], v[11]), pen_up);
+        // error bounds: FP32 allowances of the flow terms, the imbalance
+        // enclosure, the cost enclosures, plus FP64 summation of the partial sums
+        double ehi = __dmul_ru(a.zeta_f, __dadd_ru(v[2], v[6]));
+        ehi = __dadd_ru(ehi, __dmul_ru(a.zeta_inj, w_inj));
+        ehi = __dadd_ru(ehi, v[12]);
+        ehi = __dadd_ru(ehi, __dmul_ru(1e-12, __dadd_ru(__dadd_ru(fabs(v[9]), fabs(v[10])), pen_dn)));
+        double elo = __dmul_ru(a.zeta_f, __dadd_ru(v[3], v[7]));
+        elo = __dadd_ru(elo, __dmul_ru(a.zeta_inj, w_inj));
+        elo = __dadd_ru(elo, v[13]);
+        elo = __dadd_ru(elo, __dmul_ru(1e-12, __dadd_ru(__dadd_ru(fabs(v[8]), fabs(v[11])), pen_up)));
         if (*a.err) {
-            ohi = olo = err = __longlong_as_double(0x7ff8000000000000ll);
+            ohi = olo = ehi = elo = __longlong_as_double(0x7ff8000000000000ll);
         }
         a.obj_hi[j] = ohi;
         a.obj_lo[j] = olo;
-        a.obj_err[j] = err;
+        a.obj_err[2 * j] = ehi;
+        a.obj_err[2 * j + 1] = elo;
     }
 }
 

@@ -121,16 +121,16 @@ __global__ void __launch_bounds__(256, 1)
                     }
             }
         }
-        float slo = 0.0f, shi = 0.0f, w = 0.0f;
+        float slo = 0.0f, shi = 0.0f, whi = 0.0f, wlo = 0.0f;
 #pragma unroll
         for (int i = 0; i < ML; ++i)
 #pragma unroll
             for (int j = 0; j < MK; ++j) {
                 const int l = l0 + tl + 16 * i, k = k0 + tk + 16 * j;
                 if (l < a.n_l && k < a.n_c)
-                    pair_epilogue(a, 0, l, k, Lr[i][j], __fadd_ru(acc3[i][j], acc2[i][j]), slo, shi, w);
+                    pair_epilogue(a, 0, l, k, Lr[i][j], __fadd_ru(acc3[i][j], acc2[i][j]), slo, shi, whi, wlo);
             }
-        write_warp_partials(a, tile, warp, 0, slo, shi, w);
+        write_warp_partials(a, tile, warp, 0, slo, shi, whi, wlo);
     }
 }
 
@@ -159,8 +159,8 @@ static NoAllocLayout noalloc_layout(const CaseView &v, int n_tiles) {
     L.line_c = take((size_t)v.n_line * sizeof(float));
     L.line_e = take((size_t)v.n_line * sizeof(float));
     L.line_R = take((size_t)v.n_line * sizeof(float));
-    L.part_base = take((size_t)v.n_part_base * 3 * sizeof(double));
-    L.part_ctg = take((size_t)std::max(n_tiles, 1) * kConsumerWarps * 3 * sizeof(double));
+    L.part_base = take((size_t)v.n_part_base * kPartVals * sizeof(double));
+    L.part_ctg = take((size_t)std::max(n_tiles, 1) * kConsumerWarps * kPartVals * sizeof(double));
     L.total = off;
     return L;
 }
@@ -253,6 +253,7 @@ extern "C" ibp_status ibp_bound_noalloc(ibp_case *c, const double *box_lo, const
     ca.gamma = noalloc_gamma(kPlainCH, 8, (n_chunks + 7) / 8);
     ca.flow_lo = nullptr; ca.flow_hi = nullptr; ca.partials = part_ctg; ca.err = err;
     ca.wait_ns = 0;
+    ca.warps_per_tile = kConsumerWarps;
     if (e == cudaSuccess && n_tiles > 0) {
         const int grid = std::min(v.num_sms, n_tiles);
         k_ctg_plain<kPlainBL, kPlainBK><<<grid, 256, 0, s>>>(ca, v.phi_a, v.n_a_pad, rbus);

@@ -54,8 +54,8 @@ def check_objective(lo, hi, err, ref, rel=1e-5):
     assert np.all(lo <= ref.lo + d), (lo, ref.lo)
     assert np.all(np.abs(hi - ref.hi) <= rel * np.abs(ref.hi) + d), (hi, ref.hi)
     assert np.all(np.abs(lo - ref.lo) <= rel * np.abs(ref.lo) + d), (lo, ref.lo)
-    assert np.all(np.abs(hi - ref.hi) <= err + d)
-    assert np.all(np.abs(lo - ref.lo) <= err + d)
+    assert np.all(np.abs(hi - ref.hi) <= err[:, 0] + d), (hi - ref.hi, err[:, 0])
+    assert np.all(np.abs(lo - ref.lo) <= err[:, 1] + d), (lo - ref.lo, err[:, 1])
 
 
 def flow_scale(case, sens, cb, rb, pk, pl):
@@ -201,3 +201,23 @@ def test_bounded_wait_times_out_cleanly(P):
     gpu = P.Case(case, device=0)
     lo, hi, err = gpu.bound(case.box_lo, case.box_hi)
     assert np.isfinite(hi).all()
+
+
+@pytest.mark.parametrize("cfg", [1, 2])
+def test_every_kernel_variant_parity(P, cfg):
+    """Each compiled tile shape of the contingency kernel meets the same bar."""
+    case = make_config(cfg)
+    sens = _sens(cfg, case)
+    ref = O.bound(case, sens)
+    gpu = P.Case(case, device=0)
+    rng = np.random.default_rng(10 + cfg)
+    pk = rng.integers(0, case.n_ctg, 5000)
+    pl = rng.integers(0, case.n_line, 5000)
+    pl[:50] = case.ctg_line[pk[:50]]
+    variants = P._abi.ibp_kernel_variants(False)
+    assert len(variants) >= 2
+    for vid in variants:
+        gpu.set_variant(vid)
+        lo, hi, err, flo, fhi = gpu.bound(case.box_lo, case.box_hi, flows=True)
+        check_objective(lo, hi, err, ref)
+        check_flows(case, sens, case.box_lo, case.box_hi, flo, fhi, pk, pl)
