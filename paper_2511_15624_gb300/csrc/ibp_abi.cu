@@ -93,12 +93,13 @@ struct ibp_case {
     DevBuf<int> ctg_line, act_ptr, act_dev, seg_ptr;
     DevBuf<double> slope, bkpt;
     DevBuf<float> hat_l, hat_k;  // one-box scaled rows (lazily allocated)
+    DevBuf<float> phi_k;         // unscaled PTDF rows of the contingency lines
 
     // per-call workspace
     int cap_box = 0;
     DevBuf<double> box_lo, box_hi, obj;
     DevBuf<double> cbus;
-    DevBuf<float> rbus, cabs, box_consts, line_c, line_e, line_R;
+    DevBuf<float> rbus, cabs, box_consts, line_c, line_e, line_R, rbus_t;
     DevBuf<double> part_base, part_ctg;
     DevBuf<float> flows;
     DevBuf<int> err;
@@ -115,7 +116,8 @@ struct ibp_case {
                 if (e) cudaEventDestroy(e);
             phi_a.free(); lodf.free(); rate_up.free(); rate_dn.free(); rate_c_up.free();
             rate_c_dn.free(); ctg_line.free(); act_ptr.free(); act_dev.free(); seg_ptr.free();
-            slope.free(); bkpt.free(); hat_l.free(); hat_k.free(); box_lo.free(); box_hi.free();
+            slope.free(); bkpt.free(); hat_l.free(); hat_k.free(); phi_k.free(); rbus_t.free();
+            box_lo.free(); box_hi.free();
             obj.free(); cbus.free(); rbus.free(); cabs.free(); box_consts.free(); line_c.free();
             line_e.free(); line_R.free(); part_base.free(); part_ctg.free(); flows.free(); err.free();
         }
@@ -211,7 +213,8 @@ static float rup_gamma(long n1, long n2, long n3) {
 // ----------------------------------------------------------------- tensor maps
 namespace ibp {
 bool encode_map_2d(CUtensorMap *map, const float *base, int64_t inner, int64_t outer,
-                   int64_t row_stride_elems, int box_inner, int box_outer, std::string *err) {
+                   int64_t row_stride_elems, int box_inner, int box_outer, std::string *err,
+                   bool swizzle) {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     if (!fn) {
         cudaDriverEntryPointQueryResult q;
@@ -229,7 +232,8 @@ bool encode_map_2d(CUtensorMap *map, const float *base, int64_t inner, int64_t o
     cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_outer};
     cuuint32_t es[2] = {1, 1};
     CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(base), dims, strides,
-                    box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    swizzle ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) {
         *err = "cuTensorMapEncodeTiled failed with code " + std::to_string((int)r);
@@ -334,6 +338,8 @@ static ibp_status build_sensitivities(ibp_case *c, const std::vector<int> &from,
         CUDA_TRY(cudaMemcpy(dact.p, act_red.data(), act_red.size() * sizeof(int), cudaMemcpyHostToDevice));
     CUDA_TRY(c->phi_a.alloc((size_t)n_l * c->n_a_pad));
     CUDA_TRY(launch_extract_phi(dZ.p, nb_r, n_l, dact.p, c->n_a, c->n_a_pad, c->phi_a.p, s));
+    CUDA_TRY(c->phi_k.alloc((size_t)std::max(n_c, 1) * c->n_a_pad));
+    CUDA_TRY(launch_gather_rows(c->phi_a.p, c->n_a_pad, c->ctg_line.p, n_c, c->phi_k.p, s));
 
     // LODF of the contingency list
     CUDA_TRY(c->lodf.alloc((size_t)std::max(n_c, 1) * n_l));
@@ -558,21 +564,24 @@ ibp_status set_error(ibp_status s, const char *msg) {
 // fastest one-box shape measured on GB300 (16 warps, 4x4 pairs per thread,
 // 64-bus chunks, 4-bus round-up add tree)
 constexpr int kDefaultOneBoxVariant = 9;
+constexpr int kDefaultMultiBoxVariant = 20;
 
 static const CtgVariant *pick_variant(const ibp_case *c, int n_box) {
     if (c->variant > 0) {
         const CtgVariant *v = ctg_variant_by_id(c->variant);
         if (v && (v->batched != 0) == (n_box > 1)) return v;
     }
-    (void)n_box;
-    return ctg_variant_by_id(kDefaultOneBoxVariant);
+    return ctg_variant_by_id(n_box > 1 ? kDefaultMultiBoxVariant : kDefaultOneBoxVariant);
 }
 
-static int max_tiles(const ibp_case *c) {
-    int n, best = 1;
+// partial-sum rows of the contingency kernels: (line, contingency) tiles x warps
+static size_t max_part_rows(const ibp_case *c) {
+    int n;
+    size_t best = 1;
     const CtgVariant *v = ctg_variants(&n);
     for (int i = 0; i < n; ++i) {
-        const int t = ((c->n_line + v[i].BL - 1) / v[i].BL) * ((std::max(c->n_ctg, 1) + v[i].BK - 1) / v[i].BK);
+        const size_t t = (size_t)((c->n_line + v[i].BL - 1) / v[i].BL) *
+                         ((std::max(c->n_ctg, 1) + v[i].BK - 1) / v[i].BK) * ctg_warps(v[i]);
         best = std::max(best, t);
     }
     return best;
@@ -593,7 +602,9 @@ static ibp_status ensure_workspace(ibp_case *c, int n_box) {
     CUDA_TRY(c->line_e.alloc((size_t)cap * c->n_line));
     CUDA_TRY(c->line_R.alloc((size_t)cap * c->n_line));
     CUDA_TRY(c->part_base.alloc((size_t)c->n_part_base * cap * kPartVals));
-    CUDA_TRY(c->part_ctg.alloc((size_t)max_tiles(c) * 16 * cap * kPartVals));
+    CUDA_TRY(c->part_ctg.alloc(max_part_rows(c) * cap * kPartVals));
+    const int cap_pad = (cap + kBoxTile - 1) / kBoxTile * kBoxTile;
+    CUDA_TRY(c->rbus_t.alloc(na * cap_pad));
     c->cap_box = cap;
     return IBP_OK;
 }
@@ -606,18 +617,22 @@ static ibp_status enqueue_bound(ibp_case *c, int n_box, const double *lo, const 
     if (st != IBP_OK) return st;
     const CtgVariant *v = pick_variant(c, n_box);
     if (!v) return fail(IBP_EINVAL, "no kernel variant");
-    if (n_box != 1) return fail(IBP_ENOTSUP, "more than one box per call is not built yet");
-    if (!c->hat_l.p) {
+    const bool multi = n_box > 1;
+    const int n_box_pad = (n_box + kBoxTile - 1) / kBoxTile * kBoxTile;
+    if (!multi && !c->hat_l.p) {
         CUDA_TRY(c->hat_l.alloc((size_t)c->n_line * c->n_a_pad));
         CUDA_TRY(c->hat_k.alloc((size_t)std::max(c->n_ctg, 1) * c->n_a_pad));
     }
     CUDA_TRY(cudaMemsetAsync(c->err.p, 0, sizeof(int), s));
+    if (multi)
+        CUDA_TRY(cudaMemsetAsync(c->rbus_t.p, 0, (size_t)c->n_a_pad * n_box_pad * sizeof(float), s));
     if (c->timing) CUDA_TRY(cudaEventRecord(c->ev[0], s));
 
     BusArgs ba{};
     ba.n_a = c->n_a; ba.n_a_pad = c->n_a_pad; ba.n_dev = c->n_dev; ba.n_gen = c->n_gen; ba.n_box = n_box;
     ba.act_ptr = c->act_ptr.p; ba.act_dev = c->act_dev.p; ba.box_lo = lo; ba.box_hi = hi;
-    ba.cbus = c->cbus.p; ba.rbus = c->rbus.p; ba.rbus_t = nullptr; ba.n_box_pad = 0;
+    ba.cbus = c->cbus.p; ba.rbus = c->rbus.p; ba.rbus_t = multi ? c->rbus_t.p : nullptr;
+    ba.n_box_pad = n_box_pad;
     ba.cabs = c->cabs.p; ba.box_consts = c->box_consts.p; ba.err = c->err.p;
     CUDA_TRY(launch_bus(ba, s));
     if (c->timing) CUDA_TRY(cudaEventRecord(c->ev[1], s));
@@ -629,7 +644,9 @@ static ibp_status enqueue_bound(ibp_case *c, int n_box, const double *lo, const 
     bb.box_consts = c->box_consts.p;
     bb.gamma_base = rup_gamma((c->n_a_pad / 4 + 31) / 32, 2, 5);
     bb.line_c = c->line_c.p; bb.line_e = c->line_e.p; bb.line_R = c->line_R.p;
-    bb.hat_l = c->hat_l.p; bb.hat_k = c->hat_k.p; bb.partials = c->part_base.p;
+    bb.hat_l = multi ? nullptr : c->hat_l.p;
+    bb.hat_k = multi ? nullptr : c->hat_k.p;
+    bb.partials = c->part_base.p;
     CUDA_TRY(launch_base(bb, c->n_part_base, s));
     if (c->timing) CUDA_TRY(cudaEventRecord(c->ev[2], s));
 
@@ -638,15 +655,16 @@ static ibp_status enqueue_bound(ibp_case *c, int n_box, const double *lo, const 
     const int n_chunks = (c->n_a_pad + v->CH - 1) / v->CH;
     CtgArgs ca{};
     ca.n_l = c->n_line; ca.n_c = c->n_ctg; ca.n_a = c->n_a; ca.n_chunks = n_chunks; ca.n_box = n_box;
-    ca.tiles_l = tiles_l; ca.n_tiles = tiles_l * tiles_k;
+    ca.tiles_l = tiles_l;
+    ca.n_tiles = tiles_l * tiles_k * (multi ? n_box_pad / kBoxTile : 1);
     ca.lodf = c->lodf.p; ca.ctg_line = c->ctg_line.p;
     ca.line_c = c->line_c.p; ca.line_e = c->line_e.p; ca.line_R = c->line_R.p;
     ca.rate_up = c->rate_c_up.p; ca.rate_dn = c->rate_c_dn.p; ca.box_consts = c->box_consts.p;
-    ca.rbus_t = nullptr; ca.n_box_pad = 0;
+    ca.rbus_t = multi ? c->rbus_t.p : nullptr; ca.n_box_pad = n_box_pad;
     // round-up adds per radius sum: level 1 within a chunk (one per bus, or a
     // depth-2 tree per 4 buses plus one add), level 2 over 256/CH chunks, level 3
     {
-        const bool tree = v->id >= 6;
+        const bool tree = !multi && v->id >= 6;
         const long n1 = tree ? v->CH / 4 + 2 : v->CH;
         const long n2 = 256 / v->CH;
         ca.gamma = rup_gamma(n1, n2, (n_chunks + n2 - 1) / n2);
@@ -655,18 +673,27 @@ static ibp_status enqueue_bound(ibp_case *c, int n_box, const double *lo, const 
     ca.wait_ns = 2000000000ull;
     ca.warps_per_tile = ctg_warps(*v);
     if (ca.n_tiles > 0) {
-        CUtensorMap mL, mK;
+        CUtensorMap mL, mK, mR;
         std::string err;
-        if (!encode_map_2d(&mL, c->hat_l.p, c->n_a_pad, c->n_line, c->n_a_pad, 32, v->BL, &err) ||
-            !encode_map_2d(&mK, c->hat_k.p, c->n_a_pad, c->n_ctg, c->n_a_pad, 32, v->BK, &err))
-            return fail(IBP_ECUDA, "%s", err.c_str());
-        CUDA_TRY(launch_ctg(*v, mL, mK, ca, c->num_sms, s));
+        if (multi) {
+            if (!encode_map_2d(&mL, c->phi_a.p, c->n_a_pad, c->n_line, c->n_a_pad, 32, v->BL, &err) ||
+                !encode_map_2d(&mK, c->phi_k.p, c->n_a_pad, c->n_ctg, c->n_a_pad, 32, v->BK, &err) ||
+                !encode_map_2d(&mR, c->rbus_t.p, n_box_pad, c->n_a_pad, n_box_pad, kBoxTile, 32, &err,
+                               false))
+                return fail(IBP_ECUDA, "%s", err.c_str());
+            CUDA_TRY(launch_ctg_multi(*v, mL, mK, mR, ca, c->num_sms, s));
+        } else {
+            if (!encode_map_2d(&mL, c->hat_l.p, c->n_a_pad, c->n_line, c->n_a_pad, 32, v->BL, &err) ||
+                !encode_map_2d(&mK, c->hat_k.p, c->n_a_pad, c->n_ctg, c->n_a_pad, 32, v->BK, &err))
+                return fail(IBP_ECUDA, "%s", err.c_str());
+            CUDA_TRY(launch_ctg(*v, mL, mK, ca, c->num_sms, s));
+        }
     }
     if (c->timing) CUDA_TRY(cudaEventRecord(c->ev[3], s));
 
     AsmArgs aa{};
     aa.n_box = n_box; aa.n_dev = c->n_dev; aa.n_gen = c->n_gen;
-    aa.n_part_ctg = ca.n_tiles * ca.warps_per_tile; aa.n_part_base = c->n_part_base;
+    aa.n_part_ctg = tiles_l * tiles_k * ca.warps_per_tile; aa.n_part_base = c->n_part_base;
     aa.part_ctg = c->part_ctg.p; aa.part_base = c->part_base.p; aa.box_lo = lo; aa.box_hi = hi;
     aa.seg_ptr = c->seg_ptr.p; aa.slope = c->slope.p; aa.bkpt = c->bkpt.p;
     aa.zeta_inj = c->zeta_inj; aa.zeta_f = c->zeta_f;

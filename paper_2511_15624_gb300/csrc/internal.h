@@ -103,6 +103,9 @@ cudaError_t launch_base(const BaseArgs &a, int n_part, cudaStream_t s);
 int base_partials_count(int num_sms);
 cudaError_t launch_ctg(const CtgVariant &v, const CUtensorMap &mL, const CUtensorMap &mK,
                        const CtgArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_ctg_multi(const CtgVariant &v, const CUtensorMap &mL, const CUtensorMap &mK,
+                             const CUtensorMap &mR, const CtgArgs &a, int grid, cudaStream_t s);
+constexpr int kBoxTile = 16;  // boxes per work item of the multi-box kernel
 cudaError_t launch_assemble(const AsmArgs &a, cudaStream_t s);
 cudaError_t launch_wait_selftest(int *flag, unsigned long long limit_ns, cudaStream_t s);
 
@@ -132,6 +135,7 @@ ibp_status set_error(ibp_status s, const char *msg);
 
 // tensor maps
 bool encode_map_2d(CUtensorMap *map, const float *base, int64_t inner, int64_t outer,
-                   int64_t row_stride_elems, int box_inner, int box_outer, std::string *err);
+                   int64_t row_stride_elems, int box_inner, int box_outer, std::string *err,
+                   bool swizzle = true);
 
 }  // namespace ibp

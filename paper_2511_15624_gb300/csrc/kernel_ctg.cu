@@ -283,6 +283,259 @@ __global__ void __launch_bounds__(WL * WK * 32, MINB)
 }
 
 // ---------------------------------------------------------------------------
+// Multi-box kernel.  Work item = (line tile of 64, contingency tile of 16,
+// box tile of 16).  8 warps = 4 line groups x 2 contingency groups; a warp is 4
+// line-lanes x 8 contingency-lanes; thread (tl, tk) owns lines tl + 16 i
+// (i < 4), contingency tk and all 16 boxes of the box tile.  Per (pair, bus):
+//   h = RN(L~ Phi~[k,b] + Phi~[l,b]),  acc_j <- RU(|h| r_jb + acc_j)  (j < 16)
+// i.e. 18 instructions for 17 counted FMAs.  Stage = unscaled PTDF rows of the
+// line and contingency tiles (SWIZZLE_128B) and the radius tile [32 buses][16
+// boxes] (bus-major, broadcast reads).  Level-3 radius sums live in shared
+// memory.
+// ---------------------------------------------------------------------------
+constexpr int kMB = 16;  // boxes per work item
+
+template <int ST>
+struct MultiShape {
+    static constexpr int kWarps = 8, kThreads = 256;
+    static constexpr int TL = 16, TK = 16, ML = 4;
+    static constexpr int BL = TL * ML, BK = TK;
+    static constexpr int CH = 32;
+    static constexpr int kStageFloats = (BL + BK) * CH + CH * kMB;
+    static constexpr size_t kRing = (size_t)ST * kStageFloats * sizeof(float);
+    static constexpr size_t kAcc3 = (size_t)ML * kMB * kThreads * sizeof(float);
+    static constexpr size_t kCtl = ST * sizeof(uint64_t) + 2 * ST * sizeof(int) + 16;
+    static constexpr size_t kBytes = kRing + kAcc3 + kCtl + 1024;
+    static_assert((BL + BK) * CH * sizeof(float) % 1024 == 0, "radius tile alignment");
+    static_assert(kStageFloats * sizeof(float) % 1024 == 0, "stage alignment");
+};
+
+__device__ __forceinline__ void multi_origin(int item, int tiles_l, int tiles_k, int box_tiles,
+                                             int BL, int BK, int &l0, int &k0, int &b0,
+                                             int &tile_lk) {
+    // box tiles innermost (concurrent CTAs share rows), then banded (line, ctg)
+    tile_lk = item / box_tiles;
+    b0 = (item % box_tiles) * kMB;
+    tile_origin(tile_lk, tiles_l, tiles_k, BL, BK, l0, k0);
+}
+
+template <int ST>
+__device__ __forceinline__ void issue_multi(const CUtensorMap *mL, const CUtensorMap *mK,
+                                            const CUtensorMap *mR, const CtgArgs &a, float *ring,
+                                            uint64_t *full, int *last_issued, uint32_t c,
+                                            int tiles_k, int box_tiles) {
+    using S = MultiShape<ST>;
+    constexpr uint32_t kBytes = (uint32_t)S::kStageFloats * sizeof(float);
+    const int s = (int)(c % ST);
+    const int ti = (int)(c / (uint32_t)a.n_chunks), ch = (int)(c % (uint32_t)a.n_chunks);
+    const int item = blockIdx.x + ti * gridDim.x;
+    int l0, k0, b0, tlk;
+    multi_origin(item, a.tiles_l, tiles_k, box_tiles, S::BL, S::BK, l0, k0, b0, tlk);
+    float *sL = ring + (size_t)s * S::kStageFloats;
+    float *sK = sL + S::BL * S::CH;
+    float *sR = sK + S::BK * S::CH;
+    last_issued[s] = (int)c;
+    mbar_arrive_expect_tx(smem_addr(&full[s]), kBytes);
+    tma_load_2d(smem_addr(sL), mL, smem_addr(&full[s]), ch * S::CH, l0);
+    tma_load_2d(smem_addr(sK), mK, smem_addr(&full[s]), ch * S::CH, k0);
+    tma_load_2d(smem_addr(sR), mR, smem_addr(&full[s]), b0, ch * S::CH);
+}
+
+template <int ST>
+__global__ void __launch_bounds__(256, 1)
+    k_ctg_multi(const __grid_constant__ CUtensorMap mL, const __grid_constant__ CUtensorMap mK,
+                const __grid_constant__ CUtensorMap mR, const CtgArgs a) {
+    using S = MultiShape<ST>;
+    constexpr int CH = S::CH, ML = S::ML, TL = S::TL, BL = S::BL, BK = S::BK;
+    extern __shared__ unsigned char smem_raw[];
+    float *ring = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                            ~uintptr_t(1023));
+    float *acc3 = reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(ring) + S::kRing) +
+                  threadIdx.x;  // slot (i, j) at acc3[(i * kMB + j) * 256]
+    uint64_t *full = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(ring) + S::kRing +
+                                                  S::kAcc3);
+    int *arrivals = reinterpret_cast<int *>(full + ST);
+    int *last_issued = arrivals + ST;
+    volatile int *abort_flag = last_issued + ST;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    constexpr int kFold3 = 8;
+    const int tiles_k = (a.n_c + BK - 1) / BK;
+    const int box_tiles = (a.n_box + kMB - 1) / kMB;
+    const int my_items = (a.n_tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+    const uint32_t total = (uint32_t)my_items * (uint32_t)a.n_chunks;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < ST; ++s) {
+            mbar_init(smem_addr(&full[s]), 1);
+            arrivals[s] = 0;
+            last_issued[s] = -1;
+        }
+        *abort_flag = 0;
+        fence_mbar_init();
+        prefetch_tensormap(&mL);
+        prefetch_tensormap(&mK);
+        prefetch_tensormap(&mR);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0)
+        for (uint32_t c = 0; c < total && c < (uint32_t)ST; ++c)
+            issue_multi<ST>(&mL, &mK, &mR, a, ring, full, last_issued, c, tiles_k, box_tiles);
+
+    const int tl = (warp >> 1) * 4 + (lane >> 3);
+    const int tk = (warp & 1) * 8 + (lane & 7);
+    const int xl = tl & 7, xk = tk & 7;
+    uint32_t it = 0;
+    bool stop = false;
+    for (int item = blockIdx.x; item < a.n_tiles && !stop; item += gridDim.x) {
+        int l0, k0, b0, tlk;
+        multi_origin(item, a.tiles_l, tiles_k, box_tiles, BL, BK, l0, k0, b0, tlk);
+        const int k = k0 + tk;
+        float Lr[ML];
+#pragma unroll
+        for (int i = 0; i < ML; ++i) {
+            const int l = l0 + tl + TL * i;
+            Lr[i] = (l < a.n_l && k < a.n_c) ? __ldg(&a.lodf[(size_t)k * a.n_l + l]) : 0.0f;
+        }
+        float acc1[ML][kMB], acc2[ML][kMB];
+#pragma unroll
+        for (int i = 0; i < ML; ++i)
+#pragma unroll
+            for (int j = 0; j < kMB; ++j) {
+                acc1[i][j] = acc2[i][j] = 0.0f;
+                acc3[(i * kMB + j) * S::kThreads] = 0.0f;
+            }
+        for (int ch = 0; ch < a.n_chunks; ++ch, ++it) {
+            const int s = (int)(it % ST);
+            const uint32_t par = (it / ST) & 1u;
+            bool ok = mbar_wait(smem_addr(&full[s]), par, a.wait_ns);
+            ok = __all_sync(0xffffffffu, ok);
+            if (!ok || *abort_flag) {
+                if (!ok && lane == 0) {
+                    atomicOr(a.err, kErrTimeout);
+                    *abort_flag = 1;
+                }
+                stop = true;
+                break;
+            }
+            const float *sL = ring + (size_t)s * S::kStageFloats;
+            const float *sK = sL + BL * CH;
+            const float *sR = sK + BK * CH;
+#pragma unroll 2
+            for (int q = 0; q < CH / 4; ++q) {
+                const float4 fk = *reinterpret_cast<const float4 *>(sK + tk * CH + ((q ^ xk) << 2));
+                float4 fl[ML];
+#pragma unroll
+                for (int i = 0; i < ML; ++i)
+                    fl[i] = *reinterpret_cast<const float4 *>(sL + (tl + TL * i) * CH + ((q ^ xl) << 2));
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    const float *rr = sR + (4 * q + t) * kMB;
+                    float r[kMB];
+#pragma unroll
+                    for (int v = 0; v < kMB / 4; ++v) {
+                        const float4 r4 = *reinterpret_cast<const float4 *>(rr + 4 * v);
+                        r[4 * v] = r4.x;
+                        r[4 * v + 1] = r4.y;
+                        r[4 * v + 2] = r4.z;
+                        r[4 * v + 3] = r4.w;
+                    }
+                    const float fkt = t == 0 ? fk.x : t == 1 ? fk.y : t == 2 ? fk.z : fk.w;
+#pragma unroll
+                    for (int i = 0; i < ML; ++i) {
+                        const float flt = t == 0 ? fl[i].x : t == 1 ? fl[i].y : t == 2 ? fl[i].z : fl[i].w;
+                        const float ah = fabsf(__fmaf_rn(Lr[i], fkt, flt));
+#pragma unroll
+                        for (int j = 0; j < kMB; ++j) acc1[i][j] = __fmaf_ru(ah, r[j], acc1[i][j]);
+                    }
+                }
+            }
+            __syncwarp();
+            if (lane == 0) {
+                __threadfence_block();
+                const int old = atomicAdd(&arrivals[s], 1);
+                if (old == (int)(it / ST) * S::kWarps + S::kWarps - 1) {
+                    const uint32_t nxt = it + ST;
+                    if (nxt < total && !*abort_flag) {
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        issue_multi<ST>(&mL, &mK, &mR, a, ring, full, last_issued, nxt, tiles_k,
+                                        box_tiles);
+                    }
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < ML; ++i)
+#pragma unroll
+                for (int j = 0; j < kMB; ++j) {
+                    acc2[i][j] = __fadd_ru(acc2[i][j], acc1[i][j]);
+                    acc1[i][j] = 0.0f;
+                }
+            if ((ch & (kFold3 - 1)) == kFold3 - 1) {
+#pragma unroll
+                for (int i = 0; i < ML; ++i)
+#pragma unroll
+                    for (int j = 0; j < kMB; ++j) {
+                        float &a3 = acc3[(i * kMB + j) * S::kThreads];
+                        a3 = __fadd_ru(a3, acc2[i][j]);
+                        acc2[i][j] = 0.0f;
+                    }
+            }
+        }
+        if (stop) break;
+#pragma unroll 1
+        for (int j = 0; j < kMB; ++j) {
+            const int box = b0 + j;
+            if (box >= a.n_box) break;
+            float slo = 0.0f, shi = 0.0f, whi = 0.0f, wlo = 0.0f;
+#pragma unroll
+            for (int i = 0; i < ML; ++i) {
+                const int l = l0 + tl + TL * i;
+                if (l < a.n_l && k < a.n_c) {
+                    float a2 = 0.0f;
+                    // registers cannot be indexed by the runtime j: select it
+#pragma unroll
+                    for (int jj = 0; jj < kMB; ++jj)
+                        if (jj == j) a2 = acc2[i][jj];
+                    const float A = __fadd_ru(acc3[(i * kMB + j) * S::kThreads], a2);
+                    pair_epilogue(a, box, l, k, Lr[i], A, slo, shi, whi, wlo);
+                }
+            }
+            write_warp_partials(a, tlk, warp, box, slo, shi, whi, wlo);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && *abort_flag) {
+        for (int s = 0; s < ST; ++s) {
+            const int c = last_issued[s];
+            if (c >= 0) mbar_wait(smem_addr(&full[s]), ((uint32_t)c / ST) & 1u, a.wait_ns);
+        }
+    }
+}
+
+template <int ST>
+static cudaError_t launch_multi(const CUtensorMap &mL, const CUtensorMap &mK,
+                                const CUtensorMap &mR, const CtgArgs &a, int grid,
+                                cudaStream_t s) {
+    using S = MultiShape<ST>;
+    auto kern = k_ctg_multi<ST>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)S::kBytes);
+    if (e != cudaSuccess) return e;
+    grid = std::min(grid, a.n_tiles);
+    kern<<<grid, S::kThreads, S::kBytes, s>>>(mL, mK, mR, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ctg_multi(const CtgVariant &v, const CUtensorMap &mL, const CUtensorMap &mK,
+                             const CUtensorMap &mR, const CtgArgs &a, int grid, cudaStream_t s) {
+    if (a.n_tiles <= 0) return cudaSuccess;
+    switch (v.id) {
+    case 20: return launch_multi<4>(mL, mK, mR, a, grid, s);
+    case 21: return launch_multi<6>(mL, mK, mR, a, grid, s);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Variant table and launcher
 // ---------------------------------------------------------------------------
 // {id, batched, BL, BK, CH, ST, boxes per thread, name}; warps and the loop
@@ -296,6 +549,8 @@ static const CtgVariant kVariants[] = {
     {9, 0, 128, 64, 64, 3, 1, "16 warps, 4x4/thread, 64-bus chunks, 3 stages, 4-bus add tree"},
     {10, 0, 64, 64, 32, 4, 1, "2 CTAs/SM x 8 warps, 4x4/thread, 32-bus chunks, 4 stages, tree"},
     {11, 0, 64, 64, 64, 2, 1, "2 CTAs/SM x 8 warps, 4x4/thread, 64-bus chunks, 2 stages, tree"},
+    {20, 1, 64, 16, 32, 4, 16, "multi-box 64x16x16, 8 warps, 4 lines x 16 boxes/thread, 4 stages"},
+    {21, 1, 64, 16, 32, 6, 16, "multi-box 64x16x16, 8 warps, 4 lines x 16 boxes/thread, 6 stages"},
 };
 
 const CtgVariant *ctg_variants(int *count) {
@@ -338,6 +593,7 @@ static cudaError_t launch_one(const CUtensorMap &mL, const CUtensorMap &mK, cons
 }
 
 int ctg_warps(const CtgVariant &v) { return (v.id == 3 || v.id == 8 || v.id == 9) ? 16 : 8; }
+
 
 cudaError_t launch_ctg(const CtgVariant &v, const CUtensorMap &mL, const CUtensorMap &mK,
                        const CtgArgs &a, int grid, cudaStream_t s) {

@@ -7,9 +7,10 @@ Tolerances (written here, derived in the design doc):
 * objective: |gpu - oracle| <= 1e-5 |oracle| at both ends, and <= obj_err
   (the GPU's own error bound) plus the same FP64 allowance;
 * flows: |gpu - oracle| <= 1e-5 s_kl at both ends, where
-  s_kl = |c_l| + R_l + |L_lk| (|c_k| + R_k) is the magnitude of the FP32
-  operands combined for the pair (lines whose post-outage flow cancels to
-  ~0 keep an FP32-sized error relative to these operands), plus an absolute
+  s_kl = S_l + |L_lk| S_k with S_x = sum_b |Phi[x,b]| (|c_b| + r_b) is the
+  magnitude of the FP32 operands combined for the pair (a centre or a
+  post-outage flow that cancels to ~0 keeps an FP32-sized error relative to
+  these operands), plus an absolute
   floor of 1e-12 max s_kl for lines whose exact flow is identically zero
   (both FP64 builds leave noise of that size there).
 """
@@ -59,11 +60,13 @@ def check_objective(lo, hi, err, ref, rel=1e-5):
 
 
 def flow_scale(case, sens, cb, rb, pk, pl):
-    fc = cb @ sens.phi.T
-    fr = rb @ np.abs(sens.phi).T
+    """Magnitude of the FP32 operands of pair (k, l): the centre and radius
+    sums of both rows, sum_b |Phi| (|c_b| + r_b), combined through |L_lk|."""
+    ab = np.abs(sens.phi)
+    S = (np.abs(cb) + rb) @ ab.T
     kl = case.ctg_line[pk]
     L = np.abs(sens.lodf[pl, pk])
-    return (np.abs(fc[:, pl]) + fr[:, pl]) + L[None, :] * (np.abs(fc[:, kl]) + fr[:, kl])
+    return S[:, pl] + L[None, :] * S[:, kl]
 
 
 def _worst(excess, pk, pl):
@@ -221,3 +224,45 @@ def test_every_kernel_variant_parity(P, cfg):
         lo, hi, err, flo, fhi = gpu.bound(case.box_lo, case.box_hi, flows=True)
         check_objective(lo, hi, err, ref)
         check_flows(case, sens, case.box_lo, case.box_hi, flo, fhi, pk, pl)
+
+
+@pytest.mark.parametrize("cfg,n_sub", [(1, 5), (1, 16), (2, 20)])
+def test_multi_box_parity(P, cfg, n_sub):
+    """Many boxes in one call (ragged box tiles included) against the oracle,
+    box by box, objective and flows."""
+    case = make_config(cfg)
+    sens = _sens(cfg, case)
+    rng = np.random.default_rng(40 + n_sub)
+    lo0, hi0 = case.box_lo[0], case.box_hi[0]
+    a = lo0 + 0.5 * rng.random((n_sub, case.n_dev)) * (hi0 - lo0)
+    b = hi0 - 0.5 * rng.random((n_sub, case.n_dev)) * (hi0 - lo0)
+    lo_b, hi_b = np.minimum(a, b), np.maximum(a, b)
+    lo_b[0] = hi_b[0]  # one point box
+    ref = O.bound(case, sens, lo=lo_b, hi=hi_b)
+    gpu = P.Case(case, device=0)
+    for vid in P._abi.ibp_kernel_variants(True):
+        gpu.set_variant(vid)
+        lo, hi, err, flo, fhi = gpu.bound(lo_b, hi_b, flows=True)
+        check_objective(lo, hi, err, ref)
+        pk = rng.integers(0, case.n_ctg, 3000)
+        pl = rng.integers(0, case.n_line, 3000)
+        pl[:30] = case.ctg_line[pk[:30]]
+        check_flows(case, sens, lo_b, hi_b, flo, fhi, pk, pl)
+    # device pointers give the same bits as host pointers
+    import torch
+    dlo, dhi, derr = gpu.bound(torch.tensor(lo_b, device="cuda"), torch.tensor(hi_b, device="cuda"))
+    torch.cuda.synchronize()
+    assert np.array_equal(dhi.cpu().numpy(), hi) and np.array_equal(dlo.cpu().numpy(), lo)
+
+
+def test_one_box_and_multi_box_agree(P):
+    """The one-box and multi-box kernels bound the same box within tolerance."""
+    case = make_config(2)
+    gpu = P.Case(case, device=0)
+    lo1, hi1, e1 = gpu.bound(case.box_lo, case.box_hi)
+    two_lo = np.repeat(case.box_lo, 2, axis=0)
+    two_hi = np.repeat(case.box_hi, 2, axis=0)
+    lo2, hi2, e2 = gpu.bound(two_lo, two_hi)
+    assert np.all(np.abs(hi2 - hi1[0]) <= 1e-5 * abs(hi1[0]))
+    assert np.all(np.abs(lo2 - lo1[0]) <= 1e-5 * abs(lo1[0]))
+    assert hi2[0] == hi2[1] and lo2[0] == lo2[1]
