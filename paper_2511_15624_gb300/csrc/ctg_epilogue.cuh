@@ -59,6 +59,15 @@ __device__ __forceinline__ void pair_epilogue(const CtgArgs &a, int box, int l, 
             wlo = w;
             if (__fadd_ru(__fsub_ru(alo, rdn), w) > 0.0f) whi = w;
         }
+        if (a.act_list && slo > 0.0f) {
+            // certified active: record for the adjoint
+            const int idx = atomicAdd(&a.act_count[box], 1);
+            if (idx < a.act_cap)
+                a.act_list[(size_t)box * a.act_cap + idx] =
+                    make_int4(l, kl, __float_as_int(Lt), __float_as_int(c > 0.0f ? 1.0f : -1.0f));
+            else
+                atomicOr(a.err, kErrOverflow);
+        }
     }
     if (a.flow_lo) {
         const size_t o = ((size_t)box * a.n_c + k) * a.n_l + l;

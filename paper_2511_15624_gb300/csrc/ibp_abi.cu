@@ -90,7 +90,7 @@ struct ibp_case {
 
     // persistent device data
     DevBuf<float> phi_a, lodf, rate_up, rate_dn, rate_c_up, rate_c_dn;
-    DevBuf<int> ctg_line, act_ptr, act_dev, seg_ptr;
+    DevBuf<int> ctg_line, act_ptr, act_dev, seg_ptr, dev_col;
     DevBuf<double> slope, bkpt;
     DevBuf<float> hat_l, hat_k;  // one-box scaled rows (lazily allocated)
     DevBuf<float> phi_k;         // unscaled PTDF rows of the contingency lines
@@ -103,6 +103,11 @@ struct ibp_case {
     DevBuf<double> part_base, part_ctg;
     DevBuf<float> flows;
     DevBuf<int> err;
+    // adjoint workspace
+    int bwd_cap_box = 0, act_cap = 0;
+    DevBuf<int> act_count, cnt;
+    DevBuf<int4> act_list;
+    DevBuf<double> W, dc, dr, grads;
     int n_part_base = 0;
 
     // timing
@@ -120,6 +125,8 @@ struct ibp_case {
             box_lo.free(); box_hi.free();
             obj.free(); cbus.free(); rbus.free(); cabs.free(); box_consts.free(); line_c.free();
             line_e.free(); line_R.free(); part_base.free(); part_ctg.free(); flows.free(); err.free();
+            dev_col.free(); act_count.free(); cnt.free(); act_list.free(); W.free(); dc.free(); dr.free();
+            grads.free();
         }
     }
 };
@@ -528,6 +535,14 @@ extern "C" ibp_status ibp_case_create(int32_t n_bus, int32_t slack_bus, int32_t 
     CUDA_TRY(cudaMemcpy(c->slope.p, sl.data(), sl.size() * sizeof(double), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(c->bkpt.p, bk.data(), bk.size() * sizeof(double), cudaMemcpyHostToDevice));
     CUDA_TRY(c->err.alloc(1));
+    {
+        std::vector<int> col_of_bus(n_bus, -1), dcol(c->n_dev);
+        for (size_t i = 0; i < active.size(); ++i) col_of_bus[active[i]] = (int)i;
+        for (int i = 0; i < n_gen; ++i) dcol[i] = col_of_bus[gen_bus[i]];
+        for (int i = 0; i < n_load; ++i) dcol[n_gen + i] = col_of_bus[load_bus[i]];
+        CUDA_TRY(c->dev_col.alloc(c->n_dev));
+        CUDA_TRY(cudaMemcpy(c->dev_col.p, dcol.data(), c->n_dev * sizeof(int), cudaMemcpyHostToDevice));
+    }
 
     std::vector<int> from(line_from, line_from + n_line), to(line_to, line_to + n_line);
     if ((st = build_sensitivities(c.get(), from, to, reactance, active)) != IBP_OK) return st;
@@ -612,7 +627,7 @@ static ibp_status ensure_workspace(ibp_case *c, int n_box) {
 // ----------------------------------------------------------------- bound
 static ibp_status enqueue_bound(ibp_case *c, int n_box, const double *lo, const double *hi,
                                 double *olo, double *ohi, double *oerr, float *flo, float *fhi,
-                                cudaStream_t s) {
+                                cudaStream_t s, bool record = false) {
     ibp_status st = ensure_workspace(c, n_box);
     if (st != IBP_OK) return st;
     const CtgVariant *v = pick_variant(c, n_box);
@@ -647,6 +662,12 @@ static ibp_status enqueue_bound(ibp_case *c, int n_box, const double *lo, const 
     bb.hat_l = multi ? nullptr : c->hat_l.p;
     bb.hat_k = multi ? nullptr : c->hat_k.p;
     bb.partials = c->part_base.p;
+    bb.err = c->err.p;
+    if (record) {
+        bb.act_count = c->act_count.p;
+        bb.act_list = c->act_list.p;
+        bb.act_cap = c->act_cap;
+    }
     CUDA_TRY(launch_base(bb, c->n_part_base, s));
     if (c->timing) CUDA_TRY(cudaEventRecord(c->ev[2], s));
 
@@ -672,6 +693,11 @@ static ibp_status enqueue_bound(ibp_case *c, int n_box, const double *lo, const 
     ca.flow_lo = flo; ca.flow_hi = fhi; ca.partials = c->part_ctg.p; ca.err = c->err.p;
     ca.wait_ns = 2000000000ull;
     ca.warps_per_tile = ctg_warps(*v);
+    if (record) {
+        ca.act_count = c->act_count.p;
+        ca.act_list = c->act_list.p;
+        ca.act_cap = c->act_cap;
+    }
     if (ca.n_tiles > 0) {
         CUtensorMap mL, mK, mR;
         std::string err;
@@ -708,6 +734,8 @@ static ibp_status read_err_word(ibp_case *c) {
     CUDA_TRY(cudaMemcpy(&e, c->err.p, sizeof(int), cudaMemcpyDeviceToHost));
     if (e & kErrTimeout) return fail(IBP_ETIMEOUT, "a bounded device wait ran out");
     if (e & kErrBadBox) return fail(IBP_EINVAL, "a box has lo > hi or a non-finite entry");
+    if (e & kErrOverflow)
+        return fail(IBP_ENOMEM, "too many active pairs for the adjoint's list; call with fewer boxes");
     return IBP_OK;
 }
 
@@ -775,11 +803,91 @@ extern "C" ibp_status ibp_bound(ibp_case *c, int32_t n_box, const double *box_lo
     return ok();
 }
 
-extern "C" ibp_status ibp_bound_backward(ibp_case *c, int32_t n_box, const double *, const double *,
-                                         const double *, double *, double *, double *, int32_t, void *) {
+static ibp_status ensure_bwd_workspace(ibp_case *c, int n_box) {
+    if (n_box <= c->bwd_cap_box) return IBP_OK;
+    const int cap = std::max(n_box, 1);
+    // active-pair list: about 16M entries (256 MB) shared by the boxes
+    const long long pairs = (long long)c->n_ctg * c->n_line + c->n_line;
+    c->act_cap = (int)std::max<long long>(4096, std::min<long long>(pairs, (16ll << 20) / cap));
+    CUDA_TRY(c->act_count.alloc(cap));
+    CUDA_TRY(c->act_list.alloc((size_t)cap * c->act_cap));
+    CUDA_TRY(c->W.alloc((size_t)cap * c->n_line));
+    CUDA_TRY(c->cnt.alloc((size_t)cap * c->n_line));
+    CUDA_TRY(c->dc.alloc((size_t)cap * c->n_a_pad));
+    CUDA_TRY(c->dr.alloc((size_t)cap * c->n_a_pad));
+    CUDA_TRY(c->grads.alloc((size_t)cap * (2 * c->n_dev + c->n_line + 1)));
+    c->bwd_cap_box = cap;
+    return IBP_OK;
+}
+
+static ibp_status enqueue_backward(ibp_case *c, int n_box, const double *lo, const double *hi,
+                                   const double *gobj, double *glo, double *ghi, double *grat,
+                                   cudaStream_t s) {
+    ibp_status st = ensure_bwd_workspace(c, n_box);
+    if (st != IBP_OK) return st;
+    CUDA_TRY(cudaMemsetAsync(c->act_count.p, 0, n_box * sizeof(int), s));
+    // forward pass with recording of the certified active pairs
+    double *dobj = c->obj.p;
+    if ((st = enqueue_bound(c, n_box, lo, hi, dobj, dobj + n_box, dobj + 2 * n_box, nullptr,
+                            nullptr, s, true)) != IBP_OK)
+        return st;
+    CUDA_TRY(cudaMemsetAsync(c->W.p, 0, (size_t)n_box * c->n_line * sizeof(double), s));
+    CUDA_TRY(cudaMemsetAsync(c->cnt.p, 0, (size_t)n_box * c->n_line * sizeof(int), s));
+    CUDA_TRY(cudaMemsetAsync(c->dr.p, 0, (size_t)n_box * c->n_a_pad * sizeof(double), s));
+    BwdArgs b{};
+    b.n_l = c->n_line; b.n_a = c->n_a; b.n_a_pad = c->n_a_pad; b.n_dev = c->n_dev; b.n_gen = c->n_gen;
+    b.n_box = n_box; b.act_cap = c->act_cap; b.phi = c->phi_a.p; b.act_count = c->act_count.p;
+    b.act_list = c->act_list.p; b.W = c->W.p; b.cnt = c->cnt.p; b.dc = c->dc.p; b.dr = c->dr.p;
+    b.dev_col = c->dev_col.p; b.box_lo = lo; b.box_hi = hi; b.seg_ptr = c->seg_ptr.p;
+    b.slope = c->slope.p; b.bkpt = c->bkpt.p; b.zeta_inj = c->zeta_inj; b.zeta_f = c->zeta_f;
+    b.grad_obj_hi = gobj; b.grad_lo = glo; b.grad_hi = ghi; b.grad_rating = grat;
+    CUDA_TRY(launch_backward(b, s));
+    return IBP_OK;
+}
+
+extern "C" ibp_status ibp_bound_backward(ibp_case *c, int32_t n_box, const double *box_lo,
+                                         const double *box_hi, const double *grad_obj_hi,
+                                         double *grad_lo, double *grad_hi, double *grad_rating,
+                                         int32_t ptr_mode, void *cuda_stream) {
     if (!c) return fail(IBP_EINVAL, "case is NULL");
     if (n_box < 0) return fail(IBP_EINVAL, "n_box must be >= 0");
-    return fail(IBP_ENOTSUP, "ibp_bound_backward is not built yet");
+    if (ptr_mode != 0 && ptr_mode != 1) return fail(IBP_EINVAL, "ptr_mode must be 0 or 1");
+    if (n_box == 0) return ok();
+    if (!box_lo || !box_hi || !grad_obj_hi || !grad_lo || !grad_hi)
+        return fail(IBP_EINVAL, "box and gradient pointers must not be NULL");
+    if (ptr_mode == 0) {
+        ibp_status st = check_boxes_host(c, n_box, box_lo, box_hi);
+        if (st != IBP_OK) return st;
+        for (int j = 0; j < n_box; ++j)
+            if (!is_fin(grad_obj_hi[j])) return fail(IBP_EINVAL, "grad_obj_hi[%d] is not finite", j);
+    }
+    if (c->device < 0) return fail(IBP_ENOTSUP, "case was created without a device (dry run)");
+    DeviceGuard guard(c->device);
+    if (!guard.ok) return fail(IBP_ECUDA, "cannot select device %d", c->device);
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    ibp_status st = ensure_workspace(c, n_box);
+    if (st != IBP_OK) return st;
+    if (ptr_mode == 1)
+        return enqueue_backward(c, n_box, box_lo, box_hi, grad_obj_hi, grad_lo, grad_hi, grad_rating, s);
+    if ((st = ensure_bwd_workspace(c, n_box)) != IBP_OK) return st;
+    const size_t nd = (size_t)n_box * c->n_dev;
+    CUDA_TRY(cudaMemcpyAsync(c->box_lo.p, box_lo, nd * sizeof(double), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(c->box_hi.p, box_hi, nd * sizeof(double), cudaMemcpyHostToDevice, s));
+    double *dg = c->grads.p;                 // [n_box] grad_obj_hi
+    double *dglo = dg + n_box;               // [n_box][n_dev]
+    double *dghi = dglo + nd;                // [n_box][n_dev]
+    double *dgr = dghi + nd;                 // [n_box][n_line]
+    CUDA_TRY(cudaMemcpyAsync(dg, grad_obj_hi, n_box * sizeof(double), cudaMemcpyHostToDevice, s));
+    st = enqueue_backward(c, n_box, c->box_lo.p, c->box_hi.p, dg, dglo, dghi,
+                          grad_rating ? dgr : nullptr, s);
+    if (st != IBP_OK) return st;
+    CUDA_TRY(cudaMemcpyAsync(grad_lo, dglo, nd * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(grad_hi, dghi, nd * sizeof(double), cudaMemcpyDeviceToHost, s));
+    if (grad_rating)
+        CUDA_TRY(cudaMemcpyAsync(grad_rating, dgr, (size_t)n_box * c->n_line * sizeof(double),
+                                 cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return read_err_word(c);
 }
 
 extern "C" ibp_status ibp_bound_multi(int32_t n_case, ibp_case *const *, const int32_t *,

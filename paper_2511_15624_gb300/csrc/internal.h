@@ -15,6 +15,7 @@ namespace ibp {
 // error word bits (device -> host)
 constexpr int kErrTimeout = 1;
 constexpr int kErrBadBox = 2;
+constexpr int kErrOverflow = 4;  // active-pair list of the adjoint ran out of room
 // values per partial-sum row: sum s_lo, sum s_hi, error of obj_hi, error of obj_lo
 constexpr int kPartVals = 4;
 
@@ -51,6 +52,12 @@ struct BaseArgs {
     float *hat_l;            // [n_l][n_a_pad] Phi * r (one-box mode) or null
     float *hat_k;            // [n_c][n_a_pad] Phi[ctg line] * r or null
     double *partials;        // [n_part][n_box][kPartVals]
+    // adjoint support (null when not recording): active base lines are
+    // appended to act_list[box][act_cap] as (l, l, 0, sign)
+    int *act_count;
+    int4 *act_list;
+    int act_cap;
+    int *err;
 };
 
 struct CtgArgs {
@@ -69,6 +76,29 @@ struct CtgArgs {
     int warps_per_tile;      // partial-sum rows written per tile
     int *err;
     unsigned long long wait_ns;
+    // adjoint support (null when not recording): pairs whose certified lower
+    // violation bound is > 0 are appended as (l, ctg line, L bits, sign bits)
+    int *act_count;
+    int4 *act_list;
+    int act_cap;
+};
+
+struct BwdArgs {
+    int n_l, n_a, n_a_pad, n_dev, n_gen, n_box, act_cap;
+    const float *phi;          // [n_l][n_a_pad]
+    const int *act_count;      // [n_box]
+    const int4 *act_list;      // [n_box][act_cap]
+    double *W;                 // [n_box][n_l] line weights of the centre gradient
+    int *cnt;                  // [n_box][n_l] active count per line (rating gradient)
+    double *dc, *dr;           // [n_box][n_a_pad] d(sum s_lo)/dc, d(sum s_lo)/dr (sign: see kernels)
+    const int *dev_col;        // [n_dev] active column of the device's bus or -1
+    const double *box_lo, *box_hi;
+    const int *seg_ptr;
+    const double *slope, *bkpt;
+    double zeta_inj, zeta_f;
+    const double *grad_obj_hi; // [n_box]
+    double *grad_lo, *grad_hi; // [n_box][n_dev]
+    double *grad_rating;       // [n_box][n_l] or null
 };
 
 struct AsmArgs {
@@ -107,6 +137,7 @@ cudaError_t launch_ctg_multi(const CtgVariant &v, const CUtensorMap &mL, const C
                              const CUtensorMap &mR, const CtgArgs &a, int grid, cudaStream_t s);
 constexpr int kBoxTile = 16;  // boxes per work item of the multi-box kernel
 cudaError_t launch_assemble(const AsmArgs &a, cudaStream_t s);
+cudaError_t launch_backward(const BwdArgs &a, cudaStream_t s);
 cudaError_t launch_wait_selftest(int *flag, unsigned long long limit_ns, cudaStream_t s);
 
 // case-build kernels

@@ -201,6 +201,14 @@ __global__ void __launch_bounds__(kBaseWarps * 32) k_base(BaseArgs a) {
                 a.line_c[(size_t)j * a.n_l + l] = c;
                 a.line_e[(size_t)j * a.n_l + l] = e;
                 a.line_R[(size_t)j * a.n_l + l] = R;
+                if (a.act_list && slo > 0.0f) {
+                    const int idx = atomicAdd(&a.act_count[j], 1);
+                    if (idx < a.act_cap)
+                        a.act_list[(size_t)j * a.act_cap + idx] =
+                            make_int4(l, l, __float_as_int(0.0f), __float_as_int(c > 0.0f ? 1.0f : -1.0f));
+                    else
+                        atomicOr(a.err, kErrOverflow);
+                }
                 double *q = part + j * kPartVals;
                 q[0] = __dadd_rd(q[0], (double)slo);
                 q[1] = __dadd_ru(q[1], (double)shi);

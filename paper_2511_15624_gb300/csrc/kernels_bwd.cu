@@ -1,0 +1,162 @@
+// Adjoint of the certified upper bound obj_hi with respect to the box
+// endpoints and the line ratings (not certified: FP32 products, FP64 sums).
+//
+// obj_hi = C(pd_hi) - G(pg_lo) - z_inj s_inj,lo - z_f (sum_l s_fb,lo + sum_{k,l} s_fc,lo)
+// (eq. (penalized-objective) under eq. (IBP)).  With A the set of certified
+// active pairs, s_lo = |c_kl| - r_kl - rating_l > 0 (base lines included with
+// H = Phi), the derivative is
+//   d obj_hi / d c_b = -z_f sum_A sgn(c_kl) H_k[l,b],
+//   d obj_hi / d r_b = +z_f sum_A |H_k[l,b]|,
+//   d obj_hi / d rating_l = +z_f #{pairs of A on line l},
+// and sum_A sgn H_k[l,b] = sum_x W_x Phi[x,b] with line weights
+//   W_l += sgn, W_{line of k} += sgn L[l,k]  (H_k = Phi + L[:,k] Phi[k,:]).
+// The imbalance term and the monotone cost curves act on the device
+// endpoints directly.  Kernels, in order: weights, centre GEMV, radius pass,
+// chain rule to the box endpoints.
+#include "common.cuh"
+#include "internal.h"
+
+namespace ibp {
+
+constexpr int kEntryChunk = 128;
+constexpr int kEntryBlocks = 64;
+
+__global__ void k_bwd_weights(BwdArgs a) {
+    const int box = blockIdx.y;
+    const int n = min(a.act_count[box], a.act_cap);
+    const int4 *list = a.act_list + (size_t)box * a.act_cap;
+    double *W = a.W + (size_t)box * a.n_l;
+    int *cnt = a.cnt + (size_t)box * a.n_l;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int4 e = list[i];
+        const float L = __int_as_float(e.z), sg = __int_as_float(e.w);
+        atomicAdd(&W[e.x], (double)sg);
+        if (L != 0.0f) atomicAdd(&W[e.y], (double)sg * (double)L);
+        atomicAdd(&cnt[e.x], 1);
+    }
+}
+
+// dc[box][col] = sum_l W[box][l] Phi[l][col]  (lines with W = 0 are skipped)
+__global__ void k_bwd_center(BwdArgs a) {
+    const int box = blockIdx.y;
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    const double *W = a.W + (size_t)box * a.n_l;
+    double acc = 0.0;
+    if (col < a.n_a_pad) {
+        for (int l = 0; l < a.n_l; ++l) {
+            const double w = W[l];
+            if (w != 0.0) acc = fma(w, (double)__ldg(&a.phi[(size_t)l * a.n_a_pad + col]), acc);
+        }
+        a.dc[(size_t)box * a.n_a_pad + col] = acc;
+    }
+}
+
+// dr[box][col] += sum over a chunk of entries of |Phi[l][col] + L Phi[kline][col]|
+__global__ void k_bwd_radius(BwdArgs a) {
+    const int box = blockIdx.z;
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    const int n = min(a.act_count[box], a.act_cap);
+    const int4 *list = a.act_list + (size_t)box * a.act_cap;
+    if (col >= a.n_a_pad) return;
+    // FP64 sums: the list order depends on the forward pass's atomics, so the
+    // result must not depend on how the entries are grouped
+    double tot = 0.0;
+    for (int c0 = blockIdx.y * kEntryChunk; c0 < n; c0 += gridDim.y * kEntryChunk) {
+        const int c1 = min(c0 + kEntryChunk, n);
+        for (int i = c0; i < c1; ++i) {
+            const int4 e = list[i];
+            const float L = __int_as_float(e.z);
+            const float h = __fmaf_rn(L, __ldg(&a.phi[(size_t)e.y * a.n_a_pad + col]),
+                                      __ldg(&a.phi[(size_t)e.x * a.n_a_pad + col]));
+            tot += (double)fabsf(h);
+        }
+    }
+    if (tot != 0.0) atomicAdd(&a.dr[(size_t)box * a.n_a_pad + col], tot);
+}
+
+__device__ __forceinline__ double pwl_slope(const double *s, const double *b, int n, double x) {
+    // slope of the segment that contains x (the right one at a breakpoint)
+    if (x < b[0]) return 0.0;
+    int i = 0;
+    while (i + 1 < n && b[i + 1] <= x) ++i;
+    return s[i];
+}
+
+// one block per box: chain rule to the device endpoints, costs, imbalance
+__global__ void __launch_bounds__(256) k_bwd_chain(BwdArgs a) {
+    const int box = blockIdx.x;
+    const double *lo = a.box_lo + (size_t)box * a.n_dev;
+    const double *hi = a.box_hi + (size_t)box * a.n_dev;
+    const double g = a.grad_obj_hi[box];
+    // total injection interval [plo, phi] (imbalance at the slack)
+    double plo = 0.0, phi = 0.0;
+    for (int d = threadIdx.x; d < a.n_dev; d += blockDim.x) {
+        if (d < a.n_gen) {
+            plo += lo[d];
+            phi += hi[d];
+        } else {
+            plo -= hi[d];
+            phi -= lo[d];
+        }
+    }
+    __shared__ double sp[2][8];
+    for (int o = 16; o > 0; o >>= 1) {
+        plo += __shfl_xor_sync(0xffffffffu, plo, o);
+        phi += __shfl_xor_sync(0xffffffffu, phi, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        sp[0][threadIdx.x >> 5] = plo;
+        sp[1][threadIdx.x >> 5] = phi;
+    }
+    __syncthreads();
+    plo = phi = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        plo += sp[0][w];
+        phi += sp[1][w];
+    }
+    const int inj = plo > 0.0 ? 1 : (phi < 0.0 ? -1 : 0);
+    for (int d = threadIdx.x; d < a.n_dev; d += blockDim.x) {
+        const bool gen = d < a.n_gen;
+        const double sgn = gen ? 1.0 : -1.0;
+        const int col = a.dev_col[d];
+        double gc = 0.0, gr = 0.0;
+        if (col >= 0) {
+            gc = -a.zeta_f * a.dc[(size_t)box * a.n_a_pad + col];
+            gr = a.zeta_f * a.dr[(size_t)box * a.n_a_pad + col];
+        }
+        double glo = 0.5 * sgn * gc - 0.5 * gr;
+        double ghi = 0.5 * sgn * gc + 0.5 * gr;
+        const int s0 = a.seg_ptr[d], ns = a.seg_ptr[d + 1] - s0;
+        if (gen) glo -= pwl_slope(a.slope + s0, a.bkpt + s0, ns, lo[d]);
+        else ghi += pwl_slope(a.slope + s0, a.bkpt + s0, ns, hi[d]);
+        if (inj > 0) {  // s_inj,lo = plo = sum lo_g - sum hi_d
+            if (gen) glo -= a.zeta_inj;
+            else ghi += a.zeta_inj;
+        } else if (inj < 0) {  // s_inj,lo = -phi = sum lo_d - sum hi_g
+            if (gen) ghi += a.zeta_inj;
+            else glo -= a.zeta_inj;
+        }
+        a.grad_lo[(size_t)box * a.n_dev + d] = g * glo;
+        a.grad_hi[(size_t)box * a.n_dev + d] = g * ghi;
+    }
+    if (a.grad_rating)
+        for (int l = threadIdx.x; l < a.n_l; l += blockDim.x)
+            a.grad_rating[(size_t)box * a.n_l + l] = g * a.zeta_f * (double)a.cnt[(size_t)box * a.n_l + l];
+}
+
+cudaError_t launch_backward(const BwdArgs &a, cudaStream_t s) {
+    const dim3 gw(kEntryBlocks, a.n_box);
+    k_bwd_weights<<<gw, 256, 0, s>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const dim3 gc((a.n_a_pad + 127) / 128, a.n_box);
+    k_bwd_center<<<gc, 128, 0, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const dim3 gr((a.n_a_pad + 127) / 128, kEntryBlocks / 4, a.n_box);
+    k_bwd_radius<<<gr, 128, 0, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_bwd_chain<<<a.n_box, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace ibp

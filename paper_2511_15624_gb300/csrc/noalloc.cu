@@ -241,7 +241,7 @@ extern "C" ibp_status ibp_bound_noalloc(ibp_case *c, const double *box_lo, const
     bb.rate_up = v.rate_up; bb.rate_dn = v.rate_dn; bb.box_consts = consts;
     bb.gamma_base = noalloc_gamma((v.n_a_pad / 4 + 31) / 32, 2, 5);
     bb.line_c = line_c; bb.line_e = line_e; bb.line_R = line_R;
-    bb.hat_l = nullptr; bb.hat_k = nullptr; bb.partials = part_base;
+    bb.hat_l = nullptr; bb.hat_k = nullptr; bb.partials = part_base; bb.err = err;
     if (e == cudaSuccess) e = launch_base(bb, v.n_part_base, s);
 
     const int n_chunks = (v.n_a + kPlainCH - 1) / kPlainCH;
