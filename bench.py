@@ -46,6 +46,11 @@ def _args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--variant", type=int, default=0,
                    help="contingency-kernel tile shape (0 = library default)")
+    p.add_argument("--boxes", type=int, default=32,
+                   help="box count of the batched measurement on the same network (0 = skip)")
+    p.add_argument("--study", default="", choices=["", "bisection"],
+                   help="bisection: batched vs per-box gradient-guided bisection on mesh2000")
+    p.add_argument("--rounds", type=int, default=20)
     p.add_argument("--cpu-seconds", type=float, default=15.0,
                    help="target CPU time of the oracle sample")
     return p.parse_args()
@@ -255,6 +260,33 @@ def run_gb300(args):
         gpu.bound(hlo, hhi)
     e2e_s = time.perf_counter() - t0
 
+    # (4) batched: args.boxes time-index boxes of the same network in one call
+    batched = None
+    if args.boxes > 1:
+        from gen.cases import time_index_boxes
+        bcase = time_index_boxes(case, args.boxes, seed=2000 + args.config)
+        blo = torch.tensor(bcase.box_lo, device=dev)
+        bhi = torch.tensor(bcase.box_hi, device=dev)
+        for _ in range(2):
+            gpu.bound(blo, bhi)
+        gpu.sync()
+        bsteps = max(2, args.steps // 5)
+        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        for _ in range(bsteps):
+            gpu.bound(blo, bhi)
+        b1.record(stream)
+        torch.cuda.synchronize(dev)
+        bms = b0.elapsed_time(b1) / bsteps
+        gpu.set_timing(True)
+        gpu.bound(blo, bhi)
+        bk = gpu.last_timing()
+        gpu.set_timing(False)
+        bflop = P.algorithmic_flop(case.n_ctg, case.n_line, info.n_active, args.boxes)
+        batched = {"boxes": args.boxes, "ms_per_call": bms, "ms_per_bound": bms / args.boxes,
+                   "contingency_kernel_ms": bk["contingency"],
+                   "achieved_tflops": bflop / (bk["contingency"] * 1e-3) / 1e12}
+
     steps_t = torch.tensor([dev_ms, e2e_s * 1e3], device=dev, dtype=torch.float64)
     if ws > 1:
         import torch.distributed as dist
@@ -287,6 +319,9 @@ def run_gb300(args):
                 "h2d_bytes_per_step": int(2 * case.box_lo.nbytes),
                 "d2h_bytes_per_step": int(3 * 8 * nb)},
         "gpu_launches": 4 * args.steps,
+        "batched": None if batched is None else {
+            **batched, "frac": batched["achieved_tflops"] / fp32_peak,
+            "interval_flows_per_s": case.n_ctg * case.n_line * batched["boxes"] / (batched["ms_per_call"] * 1e-3)},
         "objective": {"lo": float(obj[0][0]), "hi": float(obj[1][0]),
                       "err_hi": float(obj[2][0][0]), "err_lo": float(obj[2][0][1])},
     }
@@ -297,8 +332,35 @@ def run_gb300(args):
     print(json.dumps(line), flush=True)
 
 
+def run_bisection_study(args):
+    """Gap (UB - LB)/|LB| against wall seconds, batched vs one box per call."""
+    import torch
+
+    import paper_2511_15624_gb300 as P
+    from gen import make_config
+    from paper_2511_15624_gb300.bisect import Bisection
+
+    case = make_config(2)
+    gpu = P.Case(case, device=0)
+    out = {"study": "bisection", "workload": workload(case, 2, 1) + " (root box)",
+           "rounds": args.rounds, "max_leaves": 256}
+    for batched in (True, False):
+        b = Bisection(gpu, case.box_lo, case.box_hi, max_leaves=256, batched=batched)
+        b.step()  # warm-up round, not reported
+        b = Bisection(gpu, case.box_lo, case.box_hi, max_leaves=256, batched=batched)
+        hist = b.run(args.rounds)
+        out["batched" if batched else "single"] = [
+            {"round": r.round, "s": round(r.seconds, 4), "ub": r.ub, "lb": r.lb, "gap": r.gap,
+             "leaves": r.n_leaves} for r in hist]
+    torch.cuda.synchronize()
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = _args()
+    if args.study == "bisection":
+        run_bisection_study(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
