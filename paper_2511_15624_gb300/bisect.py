@@ -7,8 +7,11 @@ may still hold the maximiser:
 
 * UB = max over leaves of obj_hi is a certified upper bound of max f over the
   root box (leaves dropped below hold max f <= their obj_hi < LB <= max f);
-* LB = max over leaf centres of obj_lo of the zero-width box at the centre, a
-  certified lower bound of f(centre) <= max f;
+* LB = max over candidate points x of obj_lo of the zero-width box at x, a
+  certified lower bound of f(x) <= max f.  Each leaf carries one candidate
+  (its centre at first); every round moves it by a projected sign-gradient
+  step inside the leaf, with the gradient of f at x taken from the adjoint of
+  the zero-width box (f is concave, so the ascent heads for the maximiser);
 * each round bounds every leaf and its centre, takes the adjoint of obj_hi,
   drops leaves with obj_hi < LB, and splits up to ``split_per_round`` leaves
   with the largest obj_hi at the midpoint of the coordinate with the largest
@@ -52,6 +55,8 @@ class Bisection:
         self.max_leaves = int(max_leaves)
         self.split_per_round = int(split_per_round or max(1, self.max_leaves // 16))
         self.batched = bool(batched)
+        self.x = 0.5 * (self.lo + self.hi)  # candidate point per leaf
+        self.step_frac = 0.25               # ascent step, fraction of the leaf width
         self.ub = float("inf")
         self.lb = -float("inf")
         self.round = 0
@@ -87,15 +92,21 @@ class Bisection:
         torch.cuda.synchronize(self.device)
         t0 = time.perf_counter()
         n = self.lo.shape[0]
-        mid = 0.5 * (self.lo + self.hi)
-        both_lo = torch.cat([self.lo, mid])
-        both_hi = torch.cat([self.hi, mid])
+        both_lo = torch.cat([self.lo, self.x])
+        both_hi = torch.cat([self.hi, self.x])
         obj_lo, obj_hi = self._bound(both_lo, both_hi)
         leaf_hi = obj_hi[:n]
-        centre_lo = obj_lo[n:]
-        self.lb = max(self.lb, float(centre_lo.max()))
+        point_lo = obj_lo[n:]
+        self.lb = max(self.lb, float(point_lo.max()))
+        # projected sign-gradient ascent of every candidate inside its leaf
+        gxl, gxh = self._grad(self.x, self.x)
+        gx = gxl + gxh
+        width = self.hi - self.lo
+        self.x = torch.minimum(torch.maximum(self.x + self.step_frac * width * torch.sign(gx), self.lo),
+                               self.hi)
+        self.step_frac *= 0.8
         keep = leaf_hi >= self.lb
-        lo, hi, leaf_hi = self.lo[keep], self.hi[keep], leaf_hi[keep]
+        lo, hi, leaf_hi, x = self.lo[keep], self.hi[keep], leaf_hi[keep], self.x[keep]
         self.ub = min(self.ub, float(leaf_hi.max()))
         # split the leaves with the largest upper bound
         room = max(0, self.max_leaves - lo.shape[0])
@@ -117,8 +128,11 @@ class Bisection:
             b_lo[rows, dim] = m
             self.lo = torch.cat([lo[rest], a_lo, b_lo])
             self.hi = torch.cat([hi[rest], a_hi, b_hi])
+            xs = x[sel]
+            self.x = torch.cat([x[rest], torch.minimum(torch.maximum(xs, a_lo), a_hi),
+                                torch.minimum(torch.maximum(xs, b_lo), b_hi)])
         else:
-            self.lo, self.hi = lo, hi
+            self.lo, self.hi, self.x = lo, hi, x
         torch.cuda.synchronize(self.device)
         self._elapsed += time.perf_counter() - t0
         self.round += 1
@@ -134,8 +148,9 @@ class Bisection:
 
     # -------------------------------------------------------------- checkpoint
     def save(self, path: str):
-        np.savez(path, lo=self.lo.cpu().numpy(), hi=self.hi.cpu().numpy(), ub=self.ub, lb=self.lb,
-                 round=self.round, elapsed=self._elapsed)
+        np.savez(path, lo=self.lo.cpu().numpy(), hi=self.hi.cpu().numpy(), x=self.x.cpu().numpy(),
+                 ub=self.ub, lb=self.lb, round=self.round, elapsed=self._elapsed,
+                 step_frac=self.step_frac)
 
     @classmethod
     def load(cls, case: Case, path: str, **kw) -> "Bisection":
@@ -144,6 +159,8 @@ class Bisection:
         b.ub, b.lb = float(z["ub"]), float(z["lb"])
         b.round = int(z["round"])
         b._elapsed = float(z["elapsed"])
+        b.x = torch.as_tensor(z["x"], dtype=torch.float64, device=b.device)
+        b.step_frac = float(z["step_frac"])
         return b
 
 

@@ -144,5 +144,31 @@ def algorithmic_flop(n_ctg: int, n_line: int, n_active: int, n_box: int) -> floa
     return 2.0 * n_ctg * n_line * n_active * (1 + n_box)
 
 
-__all__ = ["Case", "dry_run_case", "algorithmic_flop"]
+__all__ = ["Case", "dry_run_case", "algorithmic_flop", "bound_multi"]
 _ = Optional
+
+
+def bound_multi(cases, box_lo, box_hi, stream=None):
+    """Bounds of many cases (networks of uneven size) in one persistent launch
+    of the contingency kernel.  ``box_lo[i]``, ``box_hi[i]`` are CUDA tensors
+    [n_box_i, n_dev_i]; returns a list of (obj_lo, obj_hi, obj_err) per case,
+    enqueued on ``stream`` (default: torch's current stream).  The first call
+    with a given set of cases and box counts builds and uploads the work plan;
+    later calls only enqueue kernels and can be captured in a CUDA graph."""
+    import torch
+    outs = []
+    los, his = [], []
+    for c, lo, hi in zip(cases, box_lo, box_hi):
+        lo = lo.contiguous().to(torch.float64)
+        hi = hi.contiguous().to(torch.float64)
+        los.append(lo)
+        his.append(hi)
+        nb = int(lo.shape[0])
+        outs.append((torch.empty(nb, dtype=torch.float64, device=lo.device),
+                     torch.empty(nb, dtype=torch.float64, device=lo.device),
+                     torch.empty((nb, 2), dtype=torch.float64, device=lo.device)))
+    dev = los[0].device
+    s = stream if stream is not None else torch.cuda.current_stream(dev).cuda_stream
+    _abi.ibp_bound_multi([c.handle for c in cases], [int(x.shape[0]) for x in los], los, his,
+                         [o[0] for o in outs], [o[1] for o in outs], [o[2] for o in outs], stream=s)
+    return outs

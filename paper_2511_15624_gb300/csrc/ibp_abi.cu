@@ -12,6 +12,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <memory>
 #include <numeric>
 #include <string>
@@ -95,8 +96,8 @@ struct ibp_case {
     DevBuf<float> hat_l, hat_k;  // one-box scaled rows (lazily allocated)
     DevBuf<float> phi_k;         // unscaled PTDF rows of the contingency lines
 
-    // per-call workspace
-    int cap_box = 0;
+    // per-call workspace (ws_gen changes whenever its buffers move)
+    int cap_box = 0, ws_gen = 0;
     DevBuf<double> box_lo, box_hi, obj;
     DevBuf<double> cbus;
     DevBuf<float> rbus, cabs, box_consts, line_c, line_e, line_R, rbus_t;
@@ -554,7 +555,12 @@ extern "C" ibp_status ibp_case_create(int32_t n_bus, int32_t slack_bus, int32_t 
     return ok();
 }
 
-extern "C" void ibp_case_destroy(ibp_case *c) { delete c; }
+static void drop_plans_of(const ibp_case *c);
+extern "C" void ibp_case_destroy(ibp_case *c) {
+    if (!c) return;
+    drop_plans_of(c);
+    delete c;
+}
 
 namespace ibp {
 bool case_view(const ibp_case *c, CaseView *v) {
@@ -621,6 +627,7 @@ static ibp_status ensure_workspace(ibp_case *c, int n_box) {
     const int cap_pad = (cap + kBoxTile - 1) / kBoxTile * kBoxTile;
     CUDA_TRY(c->rbus_t.alloc(na * cap_pad));
     c->cap_box = cap;
+    ++c->ws_gen;
     return IBP_OK;
 }
 
@@ -890,11 +897,216 @@ extern "C" ibp_status ibp_bound_backward(ibp_case *c, int32_t n_box, const doubl
     return read_err_word(c);
 }
 
-extern "C" ibp_status ibp_bound_multi(int32_t n_case, ibp_case *const *, const int32_t *,
-                                      const double *const *, const double *const *, double *const *,
-                                      double *const *, double *const *, void *) {
+// ---------------------------------------------------------------- many cases
+// Work plan of one ibp_bound_multi configuration (cases, box counts and their
+// workspace generations), built and uploaded once, then reused.
+struct MultiPlan {
+    std::vector<const ibp_case *> cases;
+    std::vector<int> n_box, gens;
+    int device = -1, grid = 0;
+    DevBuf<MultiItem> items;
+    DevBuf<int> cta_start, err;
+    DevBuf<uint32_t> prefix;
+    DevBuf<CtgArgs> args;
+    DevBuf<CUtensorMap> maps;
+    ~MultiPlan() {
+        if (device >= 0) {
+            DeviceGuard g(device);
+            items.free(); cta_start.free(); err.free(); prefix.free(); args.free(); maps.free();
+        }
+    }
+};
+static std::mutex g_plan_mu;
+static std::vector<std::unique_ptr<MultiPlan>> g_plans;
+
+static void drop_plans_of(const ibp_case *c) {
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    g_plans.erase(std::remove_if(g_plans.begin(), g_plans.end(),
+                                 [c](const std::unique_ptr<MultiPlan> &p) {
+                                     return std::find(p->cases.begin(), p->cases.end(), c) !=
+                                            p->cases.end();
+                                 }),
+                  g_plans.end());
+}
+
+static CtgArgs multi_args(const ibp_case *c, int n_box, int BL, int BK, int CH) {
+    const int n_box_pad = (n_box + kBoxTile - 1) / kBoxTile * kBoxTile;
+    const int tiles_l = (c->n_line + BL - 1) / BL, tiles_k = (c->n_ctg + BK - 1) / BK;
+    const int n_chunks = (c->n_a_pad + CH - 1) / CH;
+    CtgArgs ca{};
+    ca.n_l = c->n_line; ca.n_c = c->n_ctg; ca.n_a = c->n_a; ca.n_chunks = n_chunks; ca.n_box = n_box;
+    ca.tiles_l = tiles_l; ca.n_tiles = tiles_l * tiles_k * (n_box_pad / kBoxTile);
+    ca.lodf = c->lodf.p; ca.ctg_line = c->ctg_line.p;
+    ca.line_c = c->line_c.p; ca.line_e = c->line_e.p; ca.line_R = c->line_R.p;
+    ca.rate_up = c->rate_c_up.p; ca.rate_dn = c->rate_c_dn.p; ca.box_consts = c->box_consts.p;
+    ca.rbus_t = c->rbus_t.p; ca.n_box_pad = n_box_pad;
+    ca.gamma = rup_gamma(CH, 256 / CH, (n_chunks + 256 / CH - 1) / (256 / CH));
+    ca.flow_lo = nullptr; ca.flow_hi = nullptr; ca.partials = c->part_ctg.p; ca.err = c->err.p;
+    ca.wait_ns = 2000000000ull;
+    ca.warps_per_tile = 8;
+    return ca;
+}
+
+static ibp_status build_plan(ibp_case *const *cases, const int32_t *n_box, int n_case, int num_sms,
+                             MultiPlan **out) {
+    int BL, BK, CH;
+    multi_tile_shape(&BL, &BK, &CH);
+    std::unique_ptr<MultiPlan> P(new MultiPlan());
+    P->device = cases[0]->device;
+    std::vector<CtgArgs> args(n_case);
+    std::vector<CUtensorMap> maps(3 * (size_t)n_case);
+    struct Item { MultiItem m; long long cost; int order; };
+    std::vector<Item> all;
+    for (int i = 0; i < n_case; ++i) {
+        const ibp_case *c = cases[i];
+        P->cases.push_back(c);
+        P->n_box.push_back(n_box[i]);
+        P->gens.push_back(c->ws_gen);
+        args[i] = multi_args(c, n_box[i], BL, BK, CH);
+        const int n_box_pad = args[i].n_box_pad;
+        std::string err;
+        if (!encode_map_2d(&maps[3 * i], c->phi_a.p, c->n_a_pad, c->n_line, c->n_a_pad, 32, BL, &err) ||
+            !encode_map_2d(&maps[3 * i + 1], c->phi_k.p, c->n_a_pad, std::max(c->n_ctg, 1), c->n_a_pad,
+                           32, BK, &err) ||
+            !encode_map_2d(&maps[3 * i + 2], c->rbus_t.p, n_box_pad, c->n_a_pad, n_box_pad, kBoxTile,
+                           32, &err, false))
+            return fail(IBP_ECUDA, "%s", err.c_str());
+        if (c->n_ctg == 0) continue;
+        const int tiles_l = args[i].tiles_l, tiles_k = (c->n_ctg + BK - 1) / BK;
+        const long long cost = (long long)args[i].n_chunks * BL * BK * kBoxTile;
+        for (int tl = 0; tl < tiles_l; ++tl)
+            for (int tk = 0; tk < tiles_k; ++tk)
+                for (int bt = 0; bt < n_box_pad / kBoxTile; ++bt) {
+                    Item it;
+                    it.m = MultiItem{i, tl * BL, tk * BK, bt * kBoxTile, tl * tiles_k + tk, args[i].n_chunks};
+                    it.cost = cost;
+                    it.order = (int)all.size();
+                    all.push_back(it);
+                }
+    }
+    // longest items first, dealt round-robin to the persistent CTAs
+    std::stable_sort(all.begin(), all.end(), [](const Item &a, const Item &b) { return a.cost > b.cost; });
+    const int G = std::max(1, std::min<int>(num_sms, (int)all.size()));
+    std::vector<std::vector<MultiItem>> per(G);
+    for (size_t k = 0; k < all.size(); ++k) per[k % G].push_back(all[k].m);
+    std::vector<MultiItem> items;
+    std::vector<int> start(G + 1, 0);
+    std::vector<uint32_t> prefix;
+    for (int b = 0; b < G; ++b) {
+        start[b] = (int)items.size();
+        uint32_t acc = 0;
+        for (const MultiItem &m : per[b]) {
+            items.push_back(m);
+            prefix.push_back(acc);
+            acc += (uint32_t)m.n_chunks;
+        }
+        prefix.push_back(acc);
+    }
+    start[G] = (int)items.size();
+    P->grid = all.empty() ? 0 : G;
+    CUDA_TRY(P->items.alloc(std::max<size_t>(items.size(), 1)));
+    CUDA_TRY(P->cta_start.alloc(start.size()));
+    CUDA_TRY(P->prefix.alloc(prefix.size() + 1));
+    CUDA_TRY(P->args.alloc(args.size()));
+    CUDA_TRY(P->maps.alloc(maps.size()));
+    CUDA_TRY(P->err.alloc(1));
+    if (!items.empty())
+        CUDA_TRY(cudaMemcpy(P->items.p, items.data(), items.size() * sizeof(MultiItem), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(P->cta_start.p, start.data(), start.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(P->prefix.p, prefix.data(), prefix.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(P->args.p, args.data(), args.size() * sizeof(CtgArgs), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(P->maps.p, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice));
+    *out = P.release();
+    return IBP_OK;
+}
+
+static MultiPlan *find_plan(ibp_case *const *cases, const int32_t *n_box, int n_case) {
+    for (auto &p : g_plans) {
+        if ((int)p->cases.size() != n_case) continue;
+        bool same = true;
+        for (int i = 0; i < n_case && same; ++i)
+            same = p->cases[i] == cases[i] && p->n_box[i] == n_box[i] && p->gens[i] == cases[i]->ws_gen;
+        if (same) return p.get();
+    }
+    return nullptr;
+}
+
+extern "C" ibp_status ibp_bound_multi(int32_t n_case, ibp_case *const *cases, const int32_t *n_box,
+                                      const double *const *box_lo, const double *const *box_hi,
+                                      double *const *obj_lo, double *const *obj_hi,
+                                      double *const *obj_err, void *cuda_stream) {
     if (n_case < 0) return fail(IBP_EINVAL, "n_case must be >= 0");
-    return fail(IBP_ENOTSUP, "ibp_bound_multi is not built yet");
+    if (n_case == 0) return ok();
+    if (!cases || !n_box || !box_lo || !box_hi || !obj_lo || !obj_hi || !obj_err)
+        return fail(IBP_EINVAL, "array arguments must not be NULL");
+    for (int i = 0; i < n_case; ++i) {
+        if (!cases[i]) return fail(IBP_EINVAL, "case %d is NULL", i);
+        if (cases[i]->device < 0) return fail(IBP_ENOTSUP, "case %d was created without a device", i);
+        if (cases[i]->device != cases[0]->device) return fail(IBP_EINVAL, "cases live on different devices");
+        if (n_box[i] < 1) return fail(IBP_EINVAL, "n_box[%d] must be >= 1", i);
+        if (!box_lo[i] || !box_hi[i] || !obj_lo[i] || !obj_hi[i] || !obj_err[i])
+            return fail(IBP_EINVAL, "pointers of case %d must not be NULL", i);
+        for (int j = 0; j < i; ++j)
+            if (cases[j] == cases[i]) return fail(IBP_EINVAL, "case %d appears twice", i);
+    }
+    DeviceGuard guard(cases[0]->device);
+    if (!guard.ok) return fail(IBP_ECUDA, "cannot select device %d", cases[0]->device);
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    ibp_status st;
+    for (int i = 0; i < n_case; ++i)
+        if ((st = ensure_workspace(cases[i], n_box[i])) != IBP_OK) return st;
+    MultiPlan *P = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_plan_mu);
+        P = find_plan(cases, n_box, n_case);
+        if (!P) {
+            if ((st = build_plan(cases, n_box, n_case, cases[0]->num_sms, &P)) != IBP_OK) return st;
+            g_plans.emplace_back(P);
+        }
+    }
+    CUDA_TRY(cudaMemsetAsync(P->err.p, 0, sizeof(int), s));
+    // per-case box intervals and base flows
+    for (int i = 0; i < n_case; ++i) {
+        ibp_case *c = cases[i];
+        const int nb = n_box[i];
+        const int n_box_pad = (nb + kBoxTile - 1) / kBoxTile * kBoxTile;
+        CUDA_TRY(cudaMemsetAsync(c->err.p, 0, sizeof(int), s));
+        CUDA_TRY(cudaMemsetAsync(c->rbus_t.p, 0, (size_t)c->n_a_pad * n_box_pad * sizeof(float), s));
+        BusArgs ba{};
+        ba.n_a = c->n_a; ba.n_a_pad = c->n_a_pad; ba.n_dev = c->n_dev; ba.n_gen = c->n_gen; ba.n_box = nb;
+        ba.act_ptr = c->act_ptr.p; ba.act_dev = c->act_dev.p; ba.box_lo = box_lo[i]; ba.box_hi = box_hi[i];
+        ba.cbus = c->cbus.p; ba.rbus = c->rbus.p; ba.rbus_t = c->rbus_t.p; ba.n_box_pad = n_box_pad;
+        ba.cabs = c->cabs.p; ba.box_consts = c->box_consts.p; ba.err = c->err.p;
+        CUDA_TRY(launch_bus(ba, s));
+        BaseArgs bb{};
+        bb.n_l = c->n_line; bb.n_c = c->n_ctg; bb.n_a = c->n_a; bb.n_a_pad = c->n_a_pad; bb.n_box = nb;
+        bb.phi = c->phi_a.p; bb.ctg_line = c->ctg_line.p; bb.cbus = c->cbus.p; bb.rbus = c->rbus.p;
+        bb.cabs = c->cabs.p; bb.rate_up = c->rate_up.p; bb.rate_dn = c->rate_dn.p;
+        bb.box_consts = c->box_consts.p;
+        bb.gamma_base = rup_gamma((c->n_a_pad / 4 + 31) / 32, 2, 5);
+        bb.line_c = c->line_c.p; bb.line_e = c->line_e.p; bb.line_R = c->line_R.p;
+        bb.partials = c->part_base.p; bb.err = c->err.p;
+        CUDA_TRY(launch_base(bb, c->n_part_base, s));
+    }
+    // one persistent launch over the contingency tiles of every case
+    CUDA_TRY(launch_ctg_cases(P->items.p, P->cta_start.p, P->prefix.p, P->args.p, P->maps.p, P->grid,
+                              2000000000ull, P->err.p, s));
+    int BL, BK, CH;
+    multi_tile_shape(&BL, &BK, &CH);
+    for (int i = 0; i < n_case; ++i) {
+        ibp_case *c = cases[i];
+        CUDA_TRY(launch_or_err(c->err.p, P->err.p, s));
+        AsmArgs aa{};
+        aa.n_box = n_box[i]; aa.n_dev = c->n_dev; aa.n_gen = c->n_gen;
+        aa.n_part_ctg = ((c->n_line + BL - 1) / BL) * ((c->n_ctg + BK - 1) / BK) * 8;
+        aa.n_part_base = c->n_part_base;
+        aa.part_ctg = c->part_ctg.p; aa.part_base = c->part_base.p; aa.box_lo = box_lo[i]; aa.box_hi = box_hi[i];
+        aa.seg_ptr = c->seg_ptr.p; aa.slope = c->slope.p; aa.bkpt = c->bkpt.p;
+        aa.zeta_inj = c->zeta_inj; aa.zeta_f = c->zeta_f;
+        aa.obj_lo = obj_lo[i]; aa.obj_hi = obj_hi[i]; aa.obj_err = obj_err[i]; aa.err = c->err.p;
+        CUDA_TRY(launch_assemble(aa, s));
+    }
+    return ok();
 }
 
 extern "C" ibp_status ibp_case_sync(ibp_case *c) {

@@ -136,9 +136,19 @@ cudaError_t launch_ctg(const CtgVariant &v, const CUtensorMap &mL, const CUtenso
 cudaError_t launch_ctg_multi(const CtgVariant &v, const CUtensorMap &mL, const CUtensorMap &mK,
                              const CUtensorMap &mR, const CtgArgs &a, int grid, cudaStream_t s);
 constexpr int kBoxTile = 16;  // boxes per work item of the multi-box kernel
+
+// one work item of the many-case launch
+struct MultiItem {
+    int case_id, l0, k0, b0, tile_lk, n_chunks;
+};
+cudaError_t launch_ctg_cases(const MultiItem *items, const int *cta_start, const uint32_t *prefix,
+                             const CtgArgs *args, const CUtensorMap *maps, int grid,
+                             unsigned long long wait_ns, int *err, cudaStream_t s);
+void multi_tile_shape(int *BL, int *BK, int *CH);
 cudaError_t launch_assemble(const AsmArgs &a, cudaStream_t s);
 cudaError_t launch_backward(const BwdArgs &a, cudaStream_t s);
 cudaError_t launch_wait_selftest(int *flag, unsigned long long limit_ns, cudaStream_t s);
+cudaError_t launch_or_err(int *dst, const int *src, cudaStream_t s);
 
 // case-build kernels
 cudaError_t launch_scatter_dense(double *dst, int64_t ld, const int *rows, const int *cols,

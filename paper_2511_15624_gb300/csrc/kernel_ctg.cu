@@ -319,34 +319,84 @@ __device__ __forceinline__ void multi_origin(int item, int tiles_l, int tiles_k,
     tile_origin(tile_lk, tiles_l, tiles_k, BL, BK, l0, k0);
 }
 
-template <int ST>
-__device__ __forceinline__ void issue_multi(const CUtensorMap *mL, const CUtensorMap *mK,
-                                            const CUtensorMap *mR, const CtgArgs &a, float *ring,
-                                            uint64_t *full, int *last_issued, uint32_t c,
-                                            int tiles_k, int box_tiles) {
+// One work item of the multi-box kernel: the case's arguments and TMA maps and
+// the tile origin.
+struct MultiItemView {
+    const CtgArgs *a;
+    const CUtensorMap *mL, *mK, *mR;
+    int l0, k0, b0, tlk, n_chunks;
+};
+
+// Work plan of one case: item i of this CTA is blockIdx.x + i * gridDim.x.
+struct SinglePlan {
+    const CtgArgs *a;
+    const CUtensorMap *mL, *mK, *mR;
+    int tiles_k, box_tiles, BL, BK;
+    __device__ int n_items() const {
+        return (a->n_tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+    }
+    __device__ MultiItemView item(int i) const {
+        MultiItemView v{a, mL, mK, mR, 0, 0, 0, 0, a->n_chunks};
+        multi_origin((int)blockIdx.x + i * (int)gridDim.x, a->tiles_l, tiles_k, box_tiles, BL, BK,
+                     v.l0, v.k0, v.b0, v.tlk);
+        return v;
+    }
+    __device__ void locate(uint32_t c, int &i, int &ch) const {
+        i = (int)(c / (uint32_t)a->n_chunks);
+        ch = (int)(c % (uint32_t)a->n_chunks);
+    }
+};
+
+// Work plan of many cases: a host-built table, sliced per CTA, with the
+// exclusive prefix of chunk counts for the chunk -> item lookup.
+struct CasesPlan {
+    const MultiItem *items;       // this CTA's items
+    const uint32_t *prefix;       // [count + 1] chunk prefix of this CTA's items
+    int count;
+    const CtgArgs *args;          // per case
+    const CUtensorMap *maps;      // per case: L rows, contingency rows, radius
+    __device__ int n_items() const { return count; }
+    __device__ MultiItemView item(int i) const {
+        const MultiItem m = items[i];
+        MultiItemView v{args + m.case_id, maps + 3 * m.case_id, maps + 3 * m.case_id + 1,
+                        maps + 3 * m.case_id + 2, m.l0, m.k0, m.b0, m.tile_lk, m.n_chunks};
+        return v;
+    }
+    __device__ void locate(uint32_t c, int &i, int &ch) const {
+        int lo = 0, hi = count - 1;  // last item with prefix <= c
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (prefix[mid] <= c) lo = mid;
+            else hi = mid - 1;
+        }
+        i = lo;
+        ch = (int)(c - prefix[lo]);
+    }
+};
+
+template <int ST, class Plan>
+__device__ __forceinline__ void issue_multi(const Plan &P, float *ring, uint64_t *full,
+                                            int *last_issued, uint32_t c) {
     using S = MultiShape<ST>;
     constexpr uint32_t kBytes = (uint32_t)S::kStageFloats * sizeof(float);
     const int s = (int)(c % ST);
-    const int ti = (int)(c / (uint32_t)a.n_chunks), ch = (int)(c % (uint32_t)a.n_chunks);
-    const int item = blockIdx.x + ti * gridDim.x;
-    int l0, k0, b0, tlk;
-    multi_origin(item, a.tiles_l, tiles_k, box_tiles, S::BL, S::BK, l0, k0, b0, tlk);
+    int i, ch;
+    P.locate(c, i, ch);
+    const MultiItemView v = P.item(i);
     float *sL = ring + (size_t)s * S::kStageFloats;
     float *sK = sL + S::BL * S::CH;
     float *sR = sK + S::BK * S::CH;
     last_issued[s] = (int)c;
     mbar_arrive_expect_tx(smem_addr(&full[s]), kBytes);
-    tma_load_2d(smem_addr(sL), mL, smem_addr(&full[s]), ch * S::CH, l0);
-    tma_load_2d(smem_addr(sK), mK, smem_addr(&full[s]), ch * S::CH, k0);
-    tma_load_2d(smem_addr(sR), mR, smem_addr(&full[s]), b0, ch * S::CH);
+    tma_load_2d(smem_addr(sL), v.mL, smem_addr(&full[s]), ch * S::CH, v.l0);
+    tma_load_2d(smem_addr(sK), v.mK, smem_addr(&full[s]), ch * S::CH, v.k0);
+    tma_load_2d(smem_addr(sR), v.mR, smem_addr(&full[s]), v.b0, ch * S::CH);
 }
 
-template <int ST>
-__global__ void __launch_bounds__(256, 1)
-    k_ctg_multi(const __grid_constant__ CUtensorMap mL, const __grid_constant__ CUtensorMap mK,
-                const __grid_constant__ CUtensorMap mR, const CtgArgs a) {
+template <int ST, class Plan>
+__device__ __forceinline__ void multi_body(const Plan &P, unsigned long long wait_ns, int *err) {
     using S = MultiShape<ST>;
-    constexpr int CH = S::CH, ML = S::ML, TL = S::TL, BL = S::BL, BK = S::BK;
+    constexpr int CH = S::CH, ML = S::ML, TL = S::TL, BL = S::BL;
     extern __shared__ unsigned char smem_raw[];
     float *ring = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                             ~uintptr_t(1023));
@@ -360,10 +410,9 @@ __global__ void __launch_bounds__(256, 1)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     constexpr int kFold3 = 8;
-    const int tiles_k = (a.n_c + BK - 1) / BK;
-    const int box_tiles = (a.n_box + kMB - 1) / kMB;
-    const int my_items = (a.n_tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
-    const uint32_t total = (uint32_t)my_items * (uint32_t)a.n_chunks;
+    const int my_items = P.n_items();
+    uint32_t total = 0;
+    for (int i = 0; i < my_items; ++i) total += (uint32_t)P.item(i).n_chunks;
     if (threadIdx.x == 0) {
         for (int s = 0; s < ST; ++s) {
             mbar_init(smem_addr(&full[s]), 1);
@@ -372,29 +421,28 @@ __global__ void __launch_bounds__(256, 1)
         }
         *abort_flag = 0;
         fence_mbar_init();
-        prefetch_tensormap(&mL);
-        prefetch_tensormap(&mK);
-        prefetch_tensormap(&mR);
     }
     __syncthreads();
     if (threadIdx.x == 0)
         for (uint32_t c = 0; c < total && c < (uint32_t)ST; ++c)
-            issue_multi<ST>(&mL, &mK, &mR, a, ring, full, last_issued, c, tiles_k, box_tiles);
+            issue_multi<ST>(P, ring, full, last_issued, c);
 
     const int tl = (warp >> 1) * 4 + (lane >> 3);
     const int tk = (warp & 1) * 8 + (lane & 7);
     const int xl = tl & 7, xk = tk & 7;
     uint32_t it = 0;
     bool stop = false;
-    for (int item = blockIdx.x; item < a.n_tiles && !stop; item += gridDim.x) {
-        int l0, k0, b0, tlk;
-        multi_origin(item, a.tiles_l, tiles_k, box_tiles, BL, BK, l0, k0, b0, tlk);
-        const int k = k0 + tk;
+    for (int ii = 0; ii < my_items && !stop; ++ii) {
+        const MultiItemView v = P.item(ii);
+        const CtgArgs &a = *v.a;
+        const int l0 = v.l0, b0 = v.b0, tlk = v.tlk;
+        const int k = v.k0 + tk;
+        const int n_l = a.n_l, n_c = a.n_c, n_box = a.n_box;
         float Lr[ML];
 #pragma unroll
         for (int i = 0; i < ML; ++i) {
             const int l = l0 + tl + TL * i;
-            Lr[i] = (l < a.n_l && k < a.n_c) ? __ldg(&a.lodf[(size_t)k * a.n_l + l]) : 0.0f;
+            Lr[i] = (l < n_l && k < n_c) ? __ldg(&a.lodf[(size_t)k * n_l + l]) : 0.0f;
         }
         float acc1[ML][kMB], acc2[ML][kMB];
 #pragma unroll
@@ -404,14 +452,14 @@ __global__ void __launch_bounds__(256, 1)
                 acc1[i][j] = acc2[i][j] = 0.0f;
                 acc3[(i * kMB + j) * S::kThreads] = 0.0f;
             }
-        for (int ch = 0; ch < a.n_chunks; ++ch, ++it) {
+        for (int ch = 0; ch < v.n_chunks; ++ch, ++it) {
             const int s = (int)(it % ST);
             const uint32_t par = (it / ST) & 1u;
-            bool ok = mbar_wait(smem_addr(&full[s]), par, a.wait_ns);
+            bool ok = mbar_wait(smem_addr(&full[s]), par, wait_ns);
             ok = __all_sync(0xffffffffu, ok);
             if (!ok || *abort_flag) {
                 if (!ok && lane == 0) {
-                    atomicOr(a.err, kErrTimeout);
+                    atomicOr(err, kErrTimeout);
                     *abort_flag = 1;
                 }
                 stop = true;
@@ -419,7 +467,7 @@ __global__ void __launch_bounds__(256, 1)
             }
             const float *sL = ring + (size_t)s * S::kStageFloats;
             const float *sK = sL + BL * CH;
-            const float *sR = sK + BK * CH;
+            const float *sR = sK + S::BK * CH;
 #pragma unroll 2
             for (int q = 0; q < CH / 4; ++q) {
                 const float4 fk = *reinterpret_cast<const float4 *>(sK + tk * CH + ((q ^ xk) << 2));
@@ -432,12 +480,12 @@ __global__ void __launch_bounds__(256, 1)
                     const float *rr = sR + (4 * q + t) * kMB;
                     float r[kMB];
 #pragma unroll
-                    for (int v = 0; v < kMB / 4; ++v) {
-                        const float4 r4 = *reinterpret_cast<const float4 *>(rr + 4 * v);
-                        r[4 * v] = r4.x;
-                        r[4 * v + 1] = r4.y;
-                        r[4 * v + 2] = r4.z;
-                        r[4 * v + 3] = r4.w;
+                    for (int u = 0; u < kMB / 4; ++u) {
+                        const float4 r4 = *reinterpret_cast<const float4 *>(rr + 4 * u);
+                        r[4 * u] = r4.x;
+                        r[4 * u + 1] = r4.y;
+                        r[4 * u + 2] = r4.z;
+                        r[4 * u + 3] = r4.w;
                     }
                     const float fkt = t == 0 ? fk.x : t == 1 ? fk.y : t == 2 ? fk.z : fk.w;
 #pragma unroll
@@ -457,8 +505,7 @@ __global__ void __launch_bounds__(256, 1)
                     const uint32_t nxt = it + ST;
                     if (nxt < total && !*abort_flag) {
                         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                        issue_multi<ST>(&mL, &mK, &mR, a, ring, full, last_issued, nxt, tiles_k,
-                                        box_tiles);
+                        issue_multi<ST>(P, ring, full, last_issued, nxt);
                     }
                 }
             }
@@ -484,12 +531,12 @@ __global__ void __launch_bounds__(256, 1)
 #pragma unroll 1
         for (int j = 0; j < kMB; ++j) {
             const int box = b0 + j;
-            if (box >= a.n_box) break;
+            if (box >= n_box) break;
             float slo = 0.0f, shi = 0.0f, whi = 0.0f, wlo = 0.0f;
 #pragma unroll
             for (int i = 0; i < ML; ++i) {
                 const int l = l0 + tl + TL * i;
-                if (l < a.n_l && k < a.n_c) {
+                if (l < n_l && k < n_c) {
                     float a2 = 0.0f;
                     // registers cannot be indexed by the runtime j: select it
 #pragma unroll
@@ -506,9 +553,36 @@ __global__ void __launch_bounds__(256, 1)
     if (threadIdx.x == 0 && *abort_flag) {
         for (int s = 0; s < ST; ++s) {
             const int c = last_issued[s];
-            if (c >= 0) mbar_wait(smem_addr(&full[s]), ((uint32_t)c / ST) & 1u, a.wait_ns);
+            if (c >= 0) mbar_wait(smem_addr(&full[s]), ((uint32_t)c / ST) & 1u, wait_ns);
         }
     }
+}
+
+template <int ST>
+__global__ void __launch_bounds__(256, 1)
+    k_ctg_multi(const __grid_constant__ CUtensorMap mL, const __grid_constant__ CUtensorMap mK,
+                const __grid_constant__ CUtensorMap mR, const CtgArgs a) {
+    using S = MultiShape<ST>;
+    if (threadIdx.x == 0) {
+        prefetch_tensormap(&mL);
+        prefetch_tensormap(&mK);
+        prefetch_tensormap(&mR);
+    }
+    const SinglePlan P{&a, &mL, &mK, &mR, (a.n_c + S::BK - 1) / S::BK, (a.n_box + kMB - 1) / kMB,
+                       S::BL, S::BK};
+    multi_body<ST>(P, a.wait_ns, a.err);
+}
+
+// Many cases in one persistent launch: CTA b walks items [start[b], start[b+1])
+// of the host-built table (longest items first, dealt round-robin).
+template <int ST>
+__global__ void __launch_bounds__(256, 1)
+    k_ctg_cases(const MultiItem *__restrict__ items, const int *__restrict__ cta_start,
+                const uint32_t *__restrict__ prefix, const CtgArgs *__restrict__ args,
+                const CUtensorMap *__restrict__ maps, unsigned long long wait_ns, int *err) {
+    const int s0 = cta_start[blockIdx.x], s1 = cta_start[blockIdx.x + 1];
+    const CasesPlan P{items + s0, prefix + s0 + blockIdx.x, s1 - s0, args, maps};
+    multi_body<ST>(P, wait_ns, err);
 }
 
 template <int ST>
@@ -533,6 +607,25 @@ cudaError_t launch_ctg_multi(const CtgVariant &v, const CUtensorMap &mL, const C
     case 21: return launch_multi<6>(mL, mK, mR, a, grid, s);
     default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_ctg_cases(const MultiItem *items, const int *cta_start, const uint32_t *prefix,
+                             const CtgArgs *args, const CUtensorMap *maps, int grid,
+                             unsigned long long wait_ns, int *err, cudaStream_t s) {
+    using S = MultiShape<4>;
+    if (grid <= 0) return cudaSuccess;
+    auto kern = k_ctg_cases<4>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)S::kBytes);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, S::kThreads, S::kBytes, s>>>(items, cta_start, prefix, args, maps, wait_ns, err);
+    return cudaGetLastError();
+}
+
+void multi_tile_shape(int *BL, int *BK, int *CH) {
+    *BL = MultiShape<4>::BL;
+    *BK = MultiShape<4>::BK;
+    *CH = MultiShape<4>::CH;
 }
 
 // ---------------------------------------------------------------------------

@@ -379,6 +379,16 @@ cudaError_t launch_assemble(const AsmArgs &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// error word of a shared launch -> each case's error word
+__global__ void k_or_err(int *dst, const int *src) {
+    if (threadIdx.x == 0 && *src) atomicOr(dst, *src);
+}
+
+cudaError_t launch_or_err(int *dst, const int *src, cudaStream_t s) {
+    k_or_err<<<1, 32, 0, s>>>(dst, src);
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // Bounded-wait self test: one thread waits on an mbarrier whose phase never
 // completes (nobody arrives), gives up after limit_ns and reports it.
