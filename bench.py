@@ -48,8 +48,9 @@ def _args():
                    help="contingency-kernel tile shape (0 = library default)")
     p.add_argument("--boxes", type=int, default=32,
                    help="box count of the batched measurement on the same network (0 = skip)")
-    p.add_argument("--study", default="", choices=["", "bisection"],
-                   help="bisection: batched vs per-box gradient-guided bisection on mesh2000")
+    p.add_argument("--study", default="", choices=["", "bisection", "ragged"],
+                   help="bisection: batched vs per-box gradient-guided bisection on mesh2000; "
+                        "ragged: 64 uneven networks x 16 sub-boxes in one persistent launch")
     p.add_argument("--rounds", type=int, default=20)
     p.add_argument("--cpu-seconds", type=float, default=15.0,
                    help="target CPU time of the oracle sample")
@@ -356,8 +357,71 @@ def run_bisection_study(args):
     print(json.dumps(out), flush=True)
 
 
+def run_ragged_study(args):
+    """64 networks of uneven size, 16 sub-boxes each: one persistent launch of
+    the contingency kernel replayed from a CUDA graph, against one call per case."""
+    import torch
+
+    import paper_2511_15624_gb300 as P
+    from gen import make_ragged_batch
+
+    nets = make_ragged_batch()
+    t0 = time.perf_counter()
+    cases = [P.Case(n, device=0) for n in nets]
+    build_s = time.perf_counter() - t0
+    los = [torch.tensor(n.box_lo, device="cuda") for n in nets]
+    his = [torch.tensor(n.box_hi, device="cuda") for n in nets]
+    P.bound_multi(cases, los, his)  # plan and workspaces, outside capture
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        P.bound_multi(cases, los, his, stream=s.cuda_stream)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        P.bound_multi(cases, los, his, stream=s.cuda_stream)
+    for _ in range(args.warmup):
+        g.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        g.replay()
+    e1.record()
+    torch.cuda.synchronize()
+    graph_ms = e0.elapsed_time(e1) / args.steps
+    # one call per case (multi-box kernel each), same boxes
+    for c, lo, hi in zip(cases, los, his):
+        c.bound(lo, hi)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(args.steps):
+        for c, lo, hi in zip(cases, los, his):
+            c.bound(lo, hi)
+    e1.record()
+    torch.cuda.synchronize()
+    seq_ms = e0.elapsed_time(e1) / args.steps
+    flows = sum(n.n_ctg * n.n_line * n.n_box for n in nets)
+    flop = sum(P.algorithmic_flop(n.n_ctg, n.n_line, c.info().n_active, n.n_box)
+               for n, c in zip(nets, cases))
+    sizes = {}
+    for n in nets:
+        sizes[n.n_bus] = sizes.get(n.n_bus, 0) + 1
+    out = {"study": "ragged", "networks": len(nets), "boxes_per_network": nets[0].n_box,
+           "bus_sizes": sizes, "case_build_s": build_s,
+           "graph_ms_per_batch": graph_ms, "per_case_calls_ms_per_batch": seq_ms,
+           "interval_flows_per_s": flows / (graph_ms * 1e-3),
+           "algorithmic_tflops": flop / (graph_ms * 1e-3) / 1e12, "steps": args.steps}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     args = _args()
+    if args.study == "ragged":
+        run_ragged_study(args)
+        return
     if args.study == "bisection":
         run_bisection_study(args)
         return

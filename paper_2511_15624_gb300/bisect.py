@@ -101,6 +101,9 @@ class Bisection:
         # projected sign-gradient ascent of every candidate inside its leaf
         gxl, gxh = self._grad(self.x, self.x)
         gx = gxl + gxh
+        # components at rounding-noise level count as zero (sign would amplify them)
+        gmax = gx.abs().amax(dim=1, keepdim=True)
+        gx = torch.where(gx.abs() > 1e-9 * gmax, gx, torch.zeros_like(gx))
         width = self.hi - self.lo
         self.x = torch.minimum(torch.maximum(self.x + self.step_frac * width * torch.sign(gx), self.lo),
                                self.hi)

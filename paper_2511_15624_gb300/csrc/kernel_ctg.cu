@@ -305,7 +305,9 @@ struct MultiShape {
     static constexpr size_t kRing = (size_t)ST * kStageFloats * sizeof(float);
     static constexpr size_t kAcc3 = (size_t)ML * kMB * kThreads * sizeof(float);
     static constexpr size_t kCtl = ST * sizeof(uint64_t) + 2 * ST * sizeof(int) + 16;
-    static constexpr size_t kBytes = kRing + kAcc3 + kCtl + 1024;
+    // per-warp copy of the current item's kernel arguments
+    static constexpr size_t kArgs = (size_t)kWarps * ((sizeof(CtgArgs) + 15) / 16 * 16);
+    static constexpr size_t kBytes = kRing + kAcc3 + kArgs + kCtl + 1024;
     static_assert((BL + BK) * CH * sizeof(float) % 1024 == 0, "radius tile alignment");
     static_assert(kStageFloats * sizeof(float) % 1024 == 0, "stage alignment");
 };
@@ -341,14 +343,9 @@ struct SinglePlan {
                      v.l0, v.k0, v.b0, v.tlk);
         return v;
     }
-    __device__ void locate(uint32_t c, int &i, int &ch) const {
-        i = (int)(c / (uint32_t)a->n_chunks);
-        ch = (int)(c % (uint32_t)a->n_chunks);
-    }
 };
 
-// Work plan of many cases: a host-built table, sliced per CTA, with the
-// exclusive prefix of chunk counts for the chunk -> item lookup.
+// Work plan of many cases: a host-built table, sliced per CTA.
 struct CasesPlan {
     const MultiItem *items;       // this CTA's items
     const uint32_t *prefix;       // [count + 1] chunk prefix of this CTA's items
@@ -362,26 +359,14 @@ struct CasesPlan {
                         maps + 3 * m.case_id + 2, m.l0, m.k0, m.b0, m.tile_lk, m.n_chunks};
         return v;
     }
-    __device__ void locate(uint32_t c, int &i, int &ch) const {
-        int lo = 0, hi = count - 1;  // last item with prefix <= c
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (prefix[mid] <= c) lo = mid;
-            else hi = mid - 1;
-        }
-        i = lo;
-        ch = (int)(c - prefix[lo]);
-    }
 };
 
 template <int ST, class Plan>
 __device__ __forceinline__ void issue_multi(const Plan &P, float *ring, uint64_t *full,
-                                            int *last_issued, uint32_t c) {
+                                            int *last_issued, uint32_t c, int i, int ch) {
     using S = MultiShape<ST>;
     constexpr uint32_t kBytes = (uint32_t)S::kStageFloats * sizeof(float);
     const int s = (int)(c % ST);
-    int i, ch;
-    P.locate(c, i, ch);
     const MultiItemView v = P.item(i);
     float *sL = ring + (size_t)s * S::kStageFloats;
     float *sK = sL + S::BL * S::CH;
@@ -402,13 +387,15 @@ __device__ __forceinline__ void multi_body(const Plan &P, unsigned long long wai
                                             ~uintptr_t(1023));
     float *acc3 = reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(ring) + S::kRing) +
                   threadIdx.x;  // slot (i, j) at acc3[(i * kMB + j) * 256]
-    uint64_t *full = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(ring) + S::kRing +
-                                                  S::kAcc3);
+    constexpr size_t kArgSlot = (sizeof(CtgArgs) + 15) / 16 * 16;
+    unsigned char *arg_base = reinterpret_cast<unsigned char *>(ring) + S::kRing + S::kAcc3;
+    uint64_t *full = reinterpret_cast<uint64_t *>(arg_base + S::kArgs);
     int *arrivals = reinterpret_cast<int *>(full + ST);
     int *last_issued = arrivals + ST;
     volatile int *abort_flag = last_issued + ST;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    CtgArgs *my_args = reinterpret_cast<CtgArgs *>(arg_base + warp * kArgSlot);
     constexpr int kFold3 = 8;
     const int my_items = P.n_items();
     uint32_t total = 0;
@@ -423,9 +410,17 @@ __device__ __forceinline__ void multi_body(const Plan &P, unsigned long long wai
         fence_mbar_init();
     }
     __syncthreads();
-    if (threadIdx.x == 0)
-        for (uint32_t c = 0; c < total && c < (uint32_t)ST; ++c)
-            issue_multi<ST>(P, ring, full, last_issued, c);
+    if (threadIdx.x == 0) {
+        int i = 0, ch = 0;
+        for (uint32_t c = 0; c < total && c < (uint32_t)ST; ++c) {
+            while (ch >= P.item(i).n_chunks) {
+                ch -= P.item(i).n_chunks;
+                ++i;
+            }
+            issue_multi<ST>(P, ring, full, last_issued, c, i, ch);
+            ++ch;
+        }
+    }
 
     const int tl = (warp >> 1) * 4 + (lane >> 3);
     const int tk = (warp & 1) * 8 + (lane & 7);
@@ -434,7 +429,14 @@ __device__ __forceinline__ void multi_body(const Plan &P, unsigned long long wai
     bool stop = false;
     for (int ii = 0; ii < my_items && !stop; ++ii) {
         const MultiItemView v = P.item(ii);
-        const CtgArgs &a = *v.a;
+        {
+            // this warp's shared copy of the item's arguments (read by the epilogue)
+            const int *src = reinterpret_cast<const int *>(v.a);
+            int *dst = reinterpret_cast<int *>(my_args);
+            for (int w = lane; w < (int)(sizeof(CtgArgs) / sizeof(int)); w += 32) dst[w] = src[w];
+            __syncwarp();
+        }
+        const CtgArgs &a = *my_args;
         const int l0 = v.l0, b0 = v.b0, tlk = v.tlk;
         const int k = v.k0 + tk;
         const int n_l = a.n_l, n_c = a.n_c, n_box = a.n_box;
@@ -504,8 +506,14 @@ __device__ __forceinline__ void multi_body(const Plan &P, unsigned long long wai
                 if (old == (int)(it / ST) * S::kWarps + S::kWarps - 1) {
                     const uint32_t nxt = it + ST;
                     if (nxt < total && !*abort_flag) {
+                        // advance ST chunks from this warp's own position
+                        int i2 = ii, ch2 = ch + ST;
+                        while (ch2 >= P.item(i2).n_chunks) {
+                            ch2 -= P.item(i2).n_chunks;
+                            ++i2;
+                        }
                         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                        issue_multi<ST>(P, ring, full, last_issued, nxt);
+                        issue_multi<ST>(P, ring, full, last_issued, nxt, i2, ch2);
                     }
                 }
             }
