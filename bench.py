@@ -199,6 +199,7 @@ def run_gb300(args):
 
     import paper_2511_15624_gb300 as P
     from gen import make_config
+    from paper_2511_15624_gb300.shard import max_over_ranks
 
     ws, rank, local = _dist()
     if ws > 1:
@@ -288,11 +289,8 @@ def run_gb300(args):
                    "contingency_kernel_ms": bk["contingency"],
                    "achieved_tflops": bflop / (bk["contingency"] * 1e-3) / 1e12}
 
-    steps_t = torch.tensor([dev_ms, e2e_s * 1e3], device=dev, dtype=torch.float64)
-    if ws > 1:
-        import torch.distributed as dist
-        dist.all_reduce(steps_t, op=dist.ReduceOp.MAX)
-    dev_ms, e2e_ms = float(steps_t[0]), float(steps_t[1])
+    # the slowest rank sets the job time (no other exchange: every rank owns its bounds)
+    dev_ms, e2e_ms = max_over_ranks([dev_ms, e2e_s * 1e3], device=dev)
     if rank != 0:
         return
     bounds = args.steps * nb * ws
