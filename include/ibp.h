@@ -214,10 +214,33 @@ ibp_status ibp_case_set_variant(ibp_case *c, int32_t variant);
 int32_t ibp_kernel_variants(int32_t *ids, int32_t cap, int32_t batched);
 
 /*
+ * Paper-mode line screen (Sec. II-C: the contingency flow of eq. (ctg flow
+ * matrix form) propagated as the two intervals [Phi p] and [U p], radius
+ * R_l + |L[l,k]| R_k, an upper bound of the tight radius).  When enabled (the
+ * default), ibp_bound and ibp_bound_backward first drop every line whose
+ * certified upper flow bound in that interval stays within its contingency
+ * rating for all contingencies and boxes of the call: those pairs have a
+ * violation interval of exactly [0, 0], so the result is unchanged up to the
+ * rounding order of the sums (and stays certified); only the remaining lines
+ * reach the contingency kernel.  Calls that ask for flow_lo/flow_hi and
+ * ibp_bound_multi never screen.  enable: 0 disables, other values enable.
+ *
+ * ibp_case_last_live: *n_live = number of lines the last ibp_bound /
+ * ibp_bound_backward call of this case kept, or -1 when that call did not
+ * screen; lines (nullable, host, room for n_line) receives their indices in
+ * ascending order.  Synchronises the device.  No counterpart in the paper
+ * beyond the interval it uses.
+ */
+ibp_status ibp_case_set_screen(ibp_case *c, int32_t enable);
+ibp_status ibp_case_last_live(ibp_case *c, int32_t *n_live, int32_t *lines);
+
+/*
  * Optional per-kernel timing of the last ibp_bound call, recorded with CUDA
  * events on the call's stream when enabled (0 disables).  ms[0..n) receives
- * {box_to_bus, base_flow, contingency, assemble} durations in milliseconds;
- * the call synchronises the stream.
+ * {box_to_bus, base_flow, screen, contingency, assemble} durations in
+ * milliseconds (screen is the paper-mode line screen and the gather of the
+ * kept rows, about 0 when the call does not screen); the call synchronises
+ * the stream.
  */
 ibp_status ibp_case_set_timing(ibp_case *c, int32_t enable);
 ibp_status ibp_case_last_timing(ibp_case *c, float *ms, int32_t n);

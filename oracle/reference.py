@@ -21,6 +21,7 @@ Every function names the passage of the paper it follows:
 * ``bound``               eq. (penalized-objective) / appendix eq. (ibp_f) under eq. (IBP)
 * ``grad_hi``             hand-derived adjoint of the upper bound (the paper has none)
 * ``paper_mode_flows``    IBP applied literally to eq. (ctg flow matrix form)
+* ``screen_lines``        lines whose paper-mode contingency interval can exceed the rating
 * ``objective_point``     f_ibp at a point, appendix eq. (ibp_f)
 
 Parity pins: every function above is checked in ``tests/test_oracle_*.py``
@@ -498,3 +499,15 @@ def paper_mode_flows(case, sens: Sensitivities, c, r):
     cent = M[None] * fc[:, None, :] - Bm[None] * uc[:, :, None]
     rad = M[None] * fr[:, None, :] + np.abs(Bm)[None] * ur[:, :, None]
     return cent, rad
+
+
+def screen_lines(case, sens: Sensitivities, c, r, rel: float = 0.0):
+    """Lines that the paper-mode interval (``paper_mode_flows``, eq. (ctg flow
+    matrix form)) cannot clear: True where |centre| + radius > rating * (1 - rel)
+    for some contingency and box.  The paper-mode radius bounds the tight one
+    from above, so every other line has the violation interval [0, 0] of
+    eq. (slack-Sc) for every contingency.  Returns a bool array [n_line]."""
+    cent, rad = paper_mode_flows(case, sens, c, r)
+    rating = case.rating if getattr(case, "rating_ctg", None) is None else case.rating_ctg
+    up = np.abs(cent) + rad
+    return np.any(up > rating[None, None, :] * (1.0 - rel), axis=(0, 1))

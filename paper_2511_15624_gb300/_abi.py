@@ -24,7 +24,7 @@ EXPORTED = (
     "ibp_case_create", "ibp_case_destroy", "ibp_bound", "ibp_bound_backward", "ibp_bound_multi",
     "ibp_case_sync", "ibp_case_info", "ibp_case_set_variant", "ibp_kernel_variants",
     "ibp_case_set_timing", "ibp_case_last_timing", "ibp_selftest_wait_timeout", "ibp_last_error",
-    "ibp_status_string", "ibp_bound_noalloc",
+    "ibp_status_string", "ibp_bound_noalloc", "ibp_case_set_screen", "ibp_case_last_live",
 )
 
 
@@ -80,6 +80,10 @@ def lib():
         L.ibp_case_set_timing.restype = ctypes.c_int
         L.ibp_case_last_timing.argtypes = [P, P, I32]
         L.ibp_case_last_timing.restype = ctypes.c_int
+        L.ibp_case_set_screen.argtypes = [P, I32]
+        L.ibp_case_set_screen.restype = ctypes.c_int
+        L.ibp_case_last_live.argtypes = [P, P, P]
+        L.ibp_case_last_live.restype = ctypes.c_int
         L.ibp_selftest_wait_timeout.argtypes = [I32, I32]
         L.ibp_selftest_wait_timeout.restype = ctypes.c_int
         L.ibp_last_error.argtypes = []
@@ -209,9 +213,25 @@ def ibp_case_set_timing(handle, enable: bool):
 
 
 def ibp_case_last_timing(handle):
-    ms = (ctypes.c_float * 4)()
-    _check(lib().ibp_case_last_timing(ctypes.c_void_p(handle), ms, 4))
-    return {"box_to_bus": ms[0], "base_flow": ms[1], "contingency": ms[2], "assemble": ms[3]}
+    ms = (ctypes.c_float * 5)()
+    _check(lib().ibp_case_last_timing(ctypes.c_void_p(handle), ms, 5))
+    return {"box_to_bus": ms[0], "base_flow": ms[1], "screen": ms[2], "contingency": ms[3],
+            "assemble": ms[4]}
+
+
+def ibp_case_set_screen(handle, enable: bool):
+    _check(lib().ibp_case_set_screen(ctypes.c_void_p(handle), int(bool(enable))))
+
+
+def ibp_case_last_live(handle, n_line: int):
+    """(count, ascending line indices) kept by the last screened call, or (-1, None)."""
+    n = ctypes.c_int32(0)
+    buf = np.empty(max(n_line, 1), np.int32)
+    _check(lib().ibp_case_last_live(ctypes.c_void_p(handle), ctypes.byref(n),
+                                    buf.ctypes.data_as(ctypes.c_void_p)))
+    if n.value < 0:
+        return -1, None
+    return int(n.value), buf[: n.value].copy()
 
 
 def ibp_selftest_wait_timeout(device: int, limit_us: int) -> int:

@@ -15,7 +15,8 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "libibp_gb300.so")
-SOURCES = ["ibp_abi.cu", "kernels_aux.cu", "kernel_ctg.cu", "kernels_bwd.cu", "noalloc.cu"]
+SOURCES = ["ibp_abi.cu", "kernels_aux.cu", "kernel_ctg.cu", "kernel_screen.cu", "kernels_bwd.cu",
+           "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -126,6 +126,15 @@ class Case:
     def set_variant(self, variant: int):
         _abi.ibp_case_set_variant(self._h, variant)
 
+    def set_screen(self, enable: bool):
+        """Paper-mode line screen ahead of the contingency kernel (default on)."""
+        _abi.ibp_case_set_screen(self._h, enable)
+
+    def last_live(self):
+        """(count, ascending indices) of the lines the screen kept in the last
+        bound, or (-1, None) when that call did not screen."""
+        return _abi.ibp_case_last_live(self._h, self.n_line)
+
     def set_timing(self, enable: bool):
         _abi.ibp_case_set_timing(self._h, enable)
 

@@ -10,6 +10,18 @@ namespace ibp {
 
 constexpr int kConsumerWarps = 8;
 
+// Centre of the post-contingency flow in FP32 and a bound on its distance from
+// the exact centre c_l + L[l,k] c_k of the FP64 data:
+//   e_c = e_l + |L|(e_k (1 + 3u) + 2u|c_k|) + 2u|c| + eta_c (1 + |L|).
+__device__ __forceinline__ void pair_centre(float Lt, float cl, float ck, float el, float ek,
+                                            float eta_c, float one_l, float &c, float &ec) {
+    c = __fmaf_rn(Lt, ck, cl);
+    ec = __fmaf_ru(2.0f * kU, fabsf(ck), __fmul_ru(ek, 1.0000002f));
+    ec = __fmaf_ru(fabsf(Lt), ec, el);
+    ec = __fmaf_ru(2.0f * kU, fabsf(c), ec);
+    ec = __fmaf_ru(eta_c, one_l, ec);
+}
+
 // Epilogue for one (k, l) pair: flow interval, violation interval, error term.
 __device__ __forceinline__ void pair_epilogue(const CtgArgs &a, int box, int l, int k, float Lt,
                                               float A, float &slo_acc, float &shi_acc,
@@ -34,12 +46,8 @@ __device__ __forceinline__ void pair_epilogue(const CtgArgs &a, int box, int l, 
         float rbar = __fmaf_ru(A, kU, A);
         rbar = __fmaf_ru(4.0f * kU, m, rbar);
         rbar = __fadd_ru(rbar, eta);
-        const float c = __fmaf_rn(Lt, ck, cl);
-        // centre error: e_l + |L|(e_k + u|c_k|) + u|c|, with (1+u) slack on |L|
-        float ec = __fmaf_ru(2.0f * kU, fabsf(ck), __fmul_ru(ek, 1.0000002f));
-        ec = __fmaf_ru(aL, ec, el);
-        ec = __fmaf_ru(2.0f * kU, fabsf(c), ec);
-        ec = __fmaf_ru(eta_c, one_l, ec);
+        float c, ec;
+        pair_centre(Lt, cl, ck, el, ek, eta_c, one_l, c, ec);
         const float rho = __fadd_ru(rbar, ec);
         flo = __fsub_rd(c, rho);
         fhi = __fadd_ru(c, rho);

@@ -87,6 +87,8 @@ struct ibp_case {
     double build_seconds = 0, max_abs_lodf = 0;
     int num_sms = 0;
     int variant = 0;
+    bool screen = true;      // paper-mode line screen ahead of the contingency kernel
+    int last_screened = 0;   // whether the last bound call ran the screen
     std::vector<int> ctg_line_h;
 
     // persistent device data
@@ -104,6 +106,7 @@ struct ibp_case {
     DevBuf<double> part_base, part_ctg;
     DevBuf<float> flows;
     DevBuf<int> err;
+    DevBuf<int> live_flag, live, n_live;  // line screen
     // adjoint workspace
     int bwd_cap_box = 0, act_cap = 0;
     DevBuf<int> act_count, cnt;
@@ -113,7 +116,8 @@ struct ibp_case {
 
     // timing
     bool timing = false;
-    cudaEvent_t ev[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    static constexpr int kEvents = 6;
+    cudaEvent_t ev[kEvents] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
 
     ~ibp_case() {
         if (device >= 0) {
@@ -126,6 +130,7 @@ struct ibp_case {
             box_lo.free(); box_hi.free();
             obj.free(); cbus.free(); rbus.free(); cabs.free(); box_consts.free(); line_c.free();
             line_e.free(); line_R.free(); part_base.free(); part_ctg.free(); flows.free(); err.free();
+            live_flag.free(); live.free(); n_live.free();
             dev_col.free(); act_count.free(); cnt.free(); act_list.free(); W.free(); dc.free(); dr.free();
             grads.free();
         }
@@ -626,6 +631,11 @@ static ibp_status ensure_workspace(ibp_case *c, int n_box) {
     CUDA_TRY(c->part_ctg.alloc(max_part_rows(c) * cap * kPartVals));
     const int cap_pad = (cap + kBoxTile - 1) / kBoxTile * kBoxTile;
     CUDA_TRY(c->rbus_t.alloc(na * cap_pad));
+    if (!c->live.p) {
+        CUDA_TRY(c->live_flag.alloc(std::max(c->n_line, 1)));
+        CUDA_TRY(c->live.alloc(std::max(c->n_line, 1)));
+        CUDA_TRY(c->n_live.alloc(1));
+    }
     c->cap_box = cap;
     ++c->ws_gen;
     return IBP_OK;
@@ -640,11 +650,12 @@ static ibp_status enqueue_bound(ibp_case *c, int n_box, const double *lo, const 
     const CtgVariant *v = pick_variant(c, n_box);
     if (!v) return fail(IBP_EINVAL, "no kernel variant");
     const bool multi = n_box > 1;
+    // the screen leaves the flows of the lines it drops unwritten
+    const bool screened = c->screen && !flo && c->n_ctg > 0;
+    c->last_screened = screened;
     const int n_box_pad = (n_box + kBoxTile - 1) / kBoxTile * kBoxTile;
-    if (!multi && !c->hat_l.p) {
-        CUDA_TRY(c->hat_l.alloc((size_t)c->n_line * c->n_a_pad));
-        CUDA_TRY(c->hat_k.alloc((size_t)std::max(c->n_ctg, 1) * c->n_a_pad));
-    }
+    if ((!multi || screened) && !c->hat_l.p) CUDA_TRY(c->hat_l.alloc((size_t)c->n_line * c->n_a_pad));
+    if (!multi && !c->hat_k.p) CUDA_TRY(c->hat_k.alloc((size_t)std::max(c->n_ctg, 1) * c->n_a_pad));
     CUDA_TRY(cudaMemsetAsync(c->err.p, 0, sizeof(int), s));
     if (multi)
         CUDA_TRY(cudaMemsetAsync(c->rbus_t.p, 0, (size_t)c->n_a_pad * n_box_pad * sizeof(float), s));
@@ -666,7 +677,7 @@ static ibp_status enqueue_bound(ibp_case *c, int n_box, const double *lo, const 
     bb.box_consts = c->box_consts.p;
     bb.gamma_base = rup_gamma((c->n_a_pad / 4 + 31) / 32, 2, 5);
     bb.line_c = c->line_c.p; bb.line_e = c->line_e.p; bb.line_R = c->line_R.p;
-    bb.hat_l = multi ? nullptr : c->hat_l.p;
+    bb.hat_l = (multi || screened) ? nullptr : c->hat_l.p;
     bb.hat_k = multi ? nullptr : c->hat_k.p;
     bb.partials = c->part_base.p;
     bb.err = c->err.p;
@@ -677,6 +688,19 @@ static ibp_status enqueue_bound(ibp_case *c, int n_box, const double *lo, const 
     }
     CUDA_TRY(launch_base(bb, c->n_part_base, s));
     if (c->timing) CUDA_TRY(cudaEventRecord(c->ev[2], s));
+
+    if (screened) {
+        ScreenArgs sa{};
+        sa.n_l = c->n_line; sa.n_c = c->n_ctg; sa.n_box = n_box;
+        sa.lodf = c->lodf.p; sa.ctg_line = c->ctg_line.p;
+        sa.line_c = c->line_c.p; sa.line_e = c->line_e.p; sa.line_R = c->line_R.p;
+        sa.box_consts = c->box_consts.p; sa.rate_dn = c->rate_c_dn.p;
+        sa.live_flag = c->live_flag.p; sa.live = c->live.p; sa.n_live = c->n_live.p;
+        sa.phi = c->phi_a.p; sa.rbus = multi ? nullptr : c->rbus.p; sa.rows = c->hat_l.p;
+        sa.n_a_pad = c->n_a_pad;
+        CUDA_TRY(launch_screen(sa, c->num_sms, s));
+    }
+    if (c->timing) CUDA_TRY(cudaEventRecord(c->ev[3], s));
 
     const int tiles_l = (c->n_line + v->BL - 1) / v->BL;
     const int tiles_k = (c->n_ctg + v->BK - 1) / v->BK;
@@ -705,11 +729,16 @@ static ibp_status enqueue_bound(ibp_case *c, int n_box, const double *lo, const 
         ca.act_list = c->act_list.p;
         ca.act_cap = c->act_cap;
     }
+    if (screened) {
+        ca.live = c->live.p;
+        ca.n_live = c->n_live.p;
+    }
     if (ca.n_tiles > 0) {
         CUtensorMap mL, mK, mR;
         std::string err;
         if (multi) {
-            if (!encode_map_2d(&mL, c->phi_a.p, c->n_a_pad, c->n_line, c->n_a_pad, 32, v->BL, &err) ||
+            const float *rows = screened ? c->hat_l.p : c->phi_a.p;
+            if (!encode_map_2d(&mL, rows, c->n_a_pad, c->n_line, c->n_a_pad, 32, v->BL, &err) ||
                 !encode_map_2d(&mK, c->phi_k.p, c->n_a_pad, c->n_ctg, c->n_a_pad, 32, v->BK, &err) ||
                 !encode_map_2d(&mR, c->rbus_t.p, n_box_pad, c->n_a_pad, n_box_pad, kBoxTile, 32, &err,
                                false))
@@ -722,7 +751,7 @@ static ibp_status enqueue_bound(ibp_case *c, int n_box, const double *lo, const 
             CUDA_TRY(launch_ctg(*v, mL, mK, ca, c->num_sms, s));
         }
     }
-    if (c->timing) CUDA_TRY(cudaEventRecord(c->ev[3], s));
+    if (c->timing) CUDA_TRY(cudaEventRecord(c->ev[4], s));
 
     AsmArgs aa{};
     aa.n_box = n_box; aa.n_dev = c->n_dev; aa.n_gen = c->n_gen;
@@ -731,8 +760,14 @@ static ibp_status enqueue_bound(ibp_case *c, int n_box, const double *lo, const 
     aa.seg_ptr = c->seg_ptr.p; aa.slope = c->slope.p; aa.bkpt = c->bkpt.p;
     aa.zeta_inj = c->zeta_inj; aa.zeta_f = c->zeta_f;
     aa.obj_lo = olo; aa.obj_hi = ohi; aa.obj_err = oerr; aa.err = c->err.p;
+    if (screened) {
+        aa.n_live = c->n_live.p;
+        aa.live_BL = v->BL;
+        aa.live_tiles_k = tiles_k;
+        aa.live_rows_per_tile = ca.warps_per_tile;
+    }
     CUDA_TRY(launch_assemble(aa, s));
-    if (c->timing) CUDA_TRY(cudaEventRecord(c->ev[4], s));
+    if (c->timing) CUDA_TRY(cudaEventRecord(c->ev[5], s));
     return IBP_OK;
 }
 
@@ -1140,6 +1175,28 @@ extern "C" ibp_status ibp_case_set_variant(ibp_case *c, int32_t variant) {
     return ok();
 }
 
+extern "C" ibp_status ibp_case_set_screen(ibp_case *c, int32_t enable) {
+    if (!c) return fail(IBP_EINVAL, "case is NULL");
+    c->screen = enable != 0;
+    return ok();
+}
+
+extern "C" ibp_status ibp_case_last_live(ibp_case *c, int32_t *n_live, int32_t *lines) {
+    if (!c || !n_live) return fail(IBP_EINVAL, "NULL argument");
+    if (c->device < 0) return fail(IBP_ENOTSUP, "dry-run case");
+    if (!c->last_screened || !c->n_live.p) {
+        *n_live = -1;
+        return ok();
+    }
+    DeviceGuard guard(c->device);
+    CUDA_TRY(cudaDeviceSynchronize());
+    CUDA_TRY(cudaMemcpy(n_live, c->n_live.p, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (*n_live < 0 || *n_live > c->n_line) return fail(IBP_ECUDA, "corrupt live-line count");
+    if (lines && *n_live > 0)
+        CUDA_TRY(cudaMemcpy(lines, c->live.p, (size_t)*n_live * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    return ok();
+}
+
 extern "C" int32_t ibp_kernel_variants(int32_t *ids, int32_t cap, int32_t batched) {
     int n;
     const CtgVariant *v = ctg_variants(&n);
@@ -1163,8 +1220,9 @@ extern "C" ibp_status ibp_case_last_timing(ibp_case *c, float *ms, int32_t n) {
     if (!c || !ms) return fail(IBP_EINVAL, "NULL argument");
     if (!c->timing) return fail(IBP_EINVAL, "timing is not enabled");
     DeviceGuard guard(c->device);
-    CUDA_TRY(cudaEventSynchronize(c->ev[4]));
-    for (int i = 0; i < std::min<int>(n, 4); ++i) CUDA_TRY(cudaEventElapsedTime(&ms[i], c->ev[i], c->ev[i + 1]));
+    CUDA_TRY(cudaEventSynchronize(c->ev[ibp_case::kEvents - 1]));
+    for (int i = 0; i < std::min<int>(n, ibp_case::kEvents - 1); ++i)
+        CUDA_TRY(cudaEventElapsedTime(&ms[i], c->ev[i], c->ev[i + 1]));
     return ok();
 }
 

@@ -81,6 +81,30 @@ struct CtgArgs {
     int *act_count;
     int4 *act_list;
     int act_cap;
+    // line screen (null: all n_l lines): line tile rows index the compacted
+    // list live[0 .. *n_live) of lines that can carry a violation
+    const int *live;
+    const int *n_live;
+};
+
+// Paper-mode line screen (Sec. II-C, the interval of eq. (ctg flow matrix
+// form) propagated in two parts): line l needs the tight radius only if, for
+// some contingency and box, |c_kl| + R_l + |L[l,k]| R_k can exceed its rating.
+struct ScreenArgs {
+    int n_l, n_c, n_box;
+    const float *lodf;       // [n_c][n_l]
+    const int *ctg_line;     // [n_c]
+    const float *line_c, *line_e, *line_R;  // [n_box][n_l]
+    const float *box_consts;                // [n_box][4]
+    const float *rate_dn;    // contingency ratings rounded down
+    int *live_flag;          // [n_l], zeroed before the launch
+    int *live;               // [n_l] compacted list (ascending)
+    int *n_live;             // [1]
+    // rows of the compacted list: dst[i] = phi[live[i]] (* rbus when scaled)
+    const float *phi;        // [n_l][n_a_pad]
+    const float *rbus;       // [n_a_pad] (one-box) or null (copy)
+    float *rows;             // [n_l][n_a_pad]
+    int n_a_pad;
 };
 
 struct BwdArgs {
@@ -104,6 +128,10 @@ struct BwdArgs {
 struct AsmArgs {
     int n_box, n_dev, n_gen;
     int n_part_ctg, n_part_base;
+    // screened calls: the contingency partials cover ceil(*n_live / BL) line
+    // tiles x tiles_k x rows_per_tile rows (n_part_ctg is ignored)
+    const int *n_live;
+    int live_BL, live_tiles_k, live_rows_per_tile;
     const double *part_ctg;   // [n_part_ctg][n_box][kPartVals]
     const double *part_base;  // [n_part_base][n_box][kPartVals]
     const double *box_lo, *box_hi;
@@ -146,6 +174,7 @@ cudaError_t launch_ctg_cases(const MultiItem *items, const int *cta_start, const
                              unsigned long long wait_ns, int *err, cudaStream_t s);
 void multi_tile_shape(int *BL, int *BK, int *CH);
 cudaError_t launch_assemble(const AsmArgs &a, cudaStream_t s);
+cudaError_t launch_screen(const ScreenArgs &a, int num_sms, cudaStream_t s);
 cudaError_t launch_backward(const BwdArgs &a, cudaStream_t s);
 cudaError_t launch_wait_selftest(int *flag, unsigned long long limit_ns, cudaStream_t s);
 cudaError_t launch_or_err(int *dst, const int *src, cudaStream_t s);

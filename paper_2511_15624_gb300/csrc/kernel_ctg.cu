@@ -75,13 +75,13 @@ struct Shape {
 template <class S, int ST>
 __device__ __forceinline__ void issue_chunk(const CUtensorMap *mL, const CUtensorMap *mK,
                                             const CtgArgs &a, float *ring, uint64_t *full,
-                                            int *last_issued, uint32_t c, int tiles_k) {
+                                            int *last_issued, uint32_t c, int tiles_l, int tiles_k) {
     constexpr uint32_t kBytes = (uint32_t)S::kStageFloats * sizeof(float);
     const int s = (int)(c % ST);
     const int ti = (int)(c / (uint32_t)a.n_chunks), ch = (int)(c % (uint32_t)a.n_chunks);
     const int tile = blockIdx.x + ti * gridDim.x;
     int l0, k0;
-    tile_origin(tile, a.tiles_l, tiles_k, S::BL, S::BK, l0, k0);
+    tile_origin(tile, tiles_l, tiles_k, S::BL, S::BK, l0, k0);
     // stage layout: [sub][BL rows][32] line block, then [sub][BK rows][32]
     float *sL = ring + (size_t)s * S::kStageFloats;
     float *sK = sL + S::BL * S::CH;
@@ -122,7 +122,11 @@ __global__ void __launch_bounds__(WL * WK * 32, MINB)
     // level-2 sums are folded into level 3 every kFold3 chunks (256 buses)
     constexpr int kFold3 = 256 / CH;
     const int tiles_k = (a.n_c + S::BK - 1) / S::BK;
-    const int my_tiles = (a.n_tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+    // screened calls walk the compacted line list live[0 .. n_ll)
+    const int n_ll = a.n_live ? *a.n_live : a.n_l;
+    const int tiles_l = (n_ll + BL - 1) / BL;
+    const int n_tiles = a.n_live ? tiles_l * tiles_k : a.n_tiles;
+    const int my_tiles = max(0, (n_tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x);
     const uint32_t total = (uint32_t)my_tiles * (uint32_t)a.n_chunks;
     if (threadIdx.x == 0) {
         for (int s = 0; s < ST; ++s) {
@@ -138,24 +142,27 @@ __global__ void __launch_bounds__(WL * WK * 32, MINB)
     __syncthreads();
     if (threadIdx.x == 0)
         for (uint32_t c = 0; c < total && c < (uint32_t)ST; ++c)
-            issue_chunk<S, ST>(&mL, &mK, a, ring, full, last_issued, c, tiles_k);
+            issue_chunk<S, ST>(&mL, &mK, a, ring, full, last_issued, c, tiles_l, tiles_k);
 
     const int tl = (warp / WK) * 4 + (lane >> 3);
     const int tk = (warp % WK) * 8 + (lane & 7);
     const int xl = tl & 7, xk = tk & 7;  // SWIZZLE_128B: chunk q of row r sits at q ^ (r & 7)
     uint32_t it = 0;
     bool stop = false;
-    for (int tile = blockIdx.x; tile < a.n_tiles && !stop; tile += gridDim.x) {
+    for (int tile = blockIdx.x; tile < n_tiles && !stop; tile += gridDim.x) {
         int l0, k0;
-        tile_origin(tile, a.tiles_l, tiles_k, S::BL, S::BK, l0, k0);
+        tile_origin(tile, tiles_l, tiles_k, S::BL, S::BK, l0, k0);
         float Lr[ML][MK];
 #pragma unroll
-        for (int i = 0; i < ML; ++i)
+        for (int i = 0; i < ML; ++i) {
+            const int lq = l0 + tl + TL * i;
+            const int l = lq < n_ll ? (a.live ? __ldg(&a.live[lq]) : lq) : -1;
 #pragma unroll
             for (int j = 0; j < MK; ++j) {
-                const int l = l0 + tl + TL * i, k = k0 + tk + TK * j;
-                Lr[i][j] = (l < a.n_l && k < a.n_c) ? __ldg(&a.lodf[(size_t)k * a.n_l + l]) : 0.0f;
+                const int k = k0 + tk + TK * j;
+                Lr[i][j] = (l >= 0 && k < a.n_c) ? __ldg(&a.lodf[(size_t)k * a.n_l + l]) : 0.0f;
             }
+        }
         float acc1[ML][MK], acc2[ML][MK], acc3[S3 ? 1 : ML][S3 ? 1 : MK];
 #pragma unroll
         for (int i = 0; i < ML; ++i)
@@ -229,7 +236,7 @@ __global__ void __launch_bounds__(WL * WK * 32, MINB)
                     const uint32_t nxt = it + ST;
                     if (nxt < total && !*abort_flag) {
                         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                        issue_chunk<S, ST>(&mL, &mK, a, ring, full, last_issued, nxt, tiles_k);
+                        issue_chunk<S, ST>(&mL, &mK, a, ring, full, last_issued, nxt, tiles_l, tiles_k);
                     }
                 }
             }
@@ -261,8 +268,9 @@ __global__ void __launch_bounds__(WL * WK * 32, MINB)
         for (int i = 0; i < ML; ++i)
 #pragma unroll
             for (int j = 0; j < MK; ++j) {
-                const int l = l0 + tl + TL * i, k = k0 + tk + TK * j;
-                if (l < a.n_l && k < a.n_c) {
+                const int lq = l0 + tl + TL * i, k = k0 + tk + TK * j;
+                if (lq < n_ll && k < a.n_c) {
+                    const int l = a.live ? __ldg(&a.live[lq]) : lq;
                     float a3;
                     if constexpr (S3) a3 = acc3s[(i * MK + j) * S::kThreads];
                     else a3 = acc3[i][j];
@@ -333,13 +341,13 @@ struct MultiItemView {
 struct SinglePlan {
     const CtgArgs *a;
     const CUtensorMap *mL, *mK, *mR;
-    int tiles_k, box_tiles, BL, BK;
+    int tiles_l, tiles_k, box_tiles, BL, BK, n_tiles;
     __device__ int n_items() const {
-        return (a->n_tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x;
+        return max(0, (n_tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x);
     }
     __device__ MultiItemView item(int i) const {
         MultiItemView v{a, mL, mK, mR, 0, 0, 0, 0, a->n_chunks};
-        multi_origin((int)blockIdx.x + i * (int)gridDim.x, a->tiles_l, tiles_k, box_tiles, BL, BK,
+        multi_origin((int)blockIdx.x + i * (int)gridDim.x, tiles_l, tiles_k, box_tiles, BL, BK,
                      v.l0, v.k0, v.b0, v.tlk);
         return v;
     }
@@ -440,11 +448,14 @@ __device__ __forceinline__ void multi_body(const Plan &P, unsigned long long wai
         const int l0 = v.l0, b0 = v.b0, tlk = v.tlk;
         const int k = v.k0 + tk;
         const int n_l = a.n_l, n_c = a.n_c, n_box = a.n_box;
+        // screened calls walk the compacted line list live[0 .. n_ll)
+        const int n_ll = a.n_live ? *a.n_live : n_l;
         float Lr[ML];
 #pragma unroll
         for (int i = 0; i < ML; ++i) {
-            const int l = l0 + tl + TL * i;
-            Lr[i] = (l < n_l && k < n_c) ? __ldg(&a.lodf[(size_t)k * n_l + l]) : 0.0f;
+            const int lq = l0 + tl + TL * i;
+            const int l = lq < n_ll ? (a.live ? __ldg(&a.live[lq]) : lq) : -1;
+            Lr[i] = (l >= 0 && k < n_c) ? __ldg(&a.lodf[(size_t)k * n_l + l]) : 0.0f;
         }
         float acc1[ML][kMB], acc2[ML][kMB];
 #pragma unroll
@@ -543,8 +554,9 @@ __device__ __forceinline__ void multi_body(const Plan &P, unsigned long long wai
             float slo = 0.0f, shi = 0.0f, whi = 0.0f, wlo = 0.0f;
 #pragma unroll
             for (int i = 0; i < ML; ++i) {
-                const int l = l0 + tl + TL * i;
-                if (l < n_l && k < n_c) {
+                const int lq = l0 + tl + TL * i;
+                if (lq < n_ll && k < n_c) {
+                    const int l = a.live ? __ldg(&a.live[lq]) : lq;
                     float a2 = 0.0f;
                     // registers cannot be indexed by the runtime j: select it
 #pragma unroll
@@ -576,8 +588,11 @@ __global__ void __launch_bounds__(256, 1)
         prefetch_tensormap(&mK);
         prefetch_tensormap(&mR);
     }
-    const SinglePlan P{&a, &mL, &mK, &mR, (a.n_c + S::BK - 1) / S::BK, (a.n_box + kMB - 1) / kMB,
-                       S::BL, S::BK};
+    const int tiles_k = (a.n_c + S::BK - 1) / S::BK, box_tiles = (a.n_box + kMB - 1) / kMB;
+    const int n_ll = a.n_live ? *a.n_live : a.n_l;
+    const int tiles_l = a.n_live ? (n_ll + S::BL - 1) / S::BL : a.tiles_l;
+    const int n_tiles = a.n_live ? tiles_l * tiles_k * box_tiles : a.n_tiles;
+    const SinglePlan P{&a, &mL, &mK, &mR, tiles_l, tiles_k, box_tiles, S::BL, S::BK, n_tiles};
     multi_body<ST>(P, a.wait_ns, a.err);
 }
 

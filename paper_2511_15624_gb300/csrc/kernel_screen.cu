@@ -1,0 +1,137 @@
+// Paper-mode line screen ahead of the contingency kernel.
+//
+// The paper propagates the contingency flow of eq. (ctg flow matrix form) as
+// two intervals, [Phi p] and [U p], combined with the LODF column; for a pair
+// (k, l) that gives the radius R_l + |L[l,k]| R_k, which is never smaller
+// than the tight radius sum_b |Phi[l,b] + L[l,k] Phi[k,b]| r_b (triangle
+// inequality).  A line whose upper flow bound in that two-part interval stays
+// within its contingency rating for every contingency and every box has a
+// violation interval of exactly [0, 0] in the tight interval as well, so it
+// adds nothing to eq. (slack-Sc) and its tight radii need not be computed.
+//
+// Certified test (u = 2^-24; R~, c~, e as written by the base-flow kernel):
+// the exact radius of line x is at most (1 + u) R~_x + eta_r and
+// |L - L~| <= u |L~| + 2^-120, so
+//   R_l + |L| R_k <= (1 + 4u)(R~_l + |L~| R~_k) + 2 eta_r (1 + |L~|),
+// the exact centre is within e_c of the FP32 centre (pair_centre), and the
+// line is dead when  RU(|c~| + e_c + that radius) <= rating rounded down.
+//
+// Kernels: screen (one thread per line and block of contingencies), compact
+// (one block: ascending list of live lines and its length), gather (one warp
+// per live row: the PTDF row, scaled by the bus radius in one-box mode).
+#include "common.cuh"
+#include "ctg_epilogue.cuh"
+#include "internal.h"
+
+namespace ibp {
+
+constexpr int kScreenThreads = 256;
+constexpr int kScreenK = 64;  // contingencies per thread
+
+__global__ void __launch_bounds__(kScreenThreads) k_screen(const ScreenArgs a) {
+    const int l = blockIdx.x * kScreenThreads + threadIdx.x;
+    if (l >= a.n_l) return;
+    const int k0 = blockIdx.y * kScreenK, k1 = min(k0 + kScreenK, a.n_c);
+    const float rdn = __ldg(&a.rate_dn[l]);
+    bool live = false;
+    for (int j = 0; j < a.n_box && !live; ++j) {
+        const size_t ob = (size_t)j * a.n_l;
+        const float cl = __ldg(&a.line_c[ob + l]), el = __ldg(&a.line_e[ob + l]);
+        const float Rl = __ldg(&a.line_R[ob + l]);
+        const float eta_r = __ldg(&a.box_consts[(size_t)j * 4]);
+        const float eta_c = __ldg(&a.box_consts[(size_t)j * 4 + 1]);
+        for (int k = k0; k < k1; ++k) {
+            const int kl = __ldg(&a.ctg_line[k]);
+            if (kl == l) continue;  // the outaged line carries exactly nothing
+            const float Lt = __ldg(&a.lodf[(size_t)k * a.n_l + l]);
+            const float ck = __ldg(&a.line_c[ob + kl]), ek = __ldg(&a.line_e[ob + kl]);
+            const float Rk = __ldg(&a.line_R[ob + kl]);
+            const float aL = fabsf(Lt);
+            const float one_l = __fadd_ru(1.0f, aL);
+            float c, ec;
+            pair_centre(Lt, cl, ck, el, ek, eta_c, one_l, c, ec);
+            const float m = __fmaf_ru(aL, Rk, Rl);
+            float rp = __fmaf_ru(4.0f * kU, m, m);
+            rp = __fmaf_ru(2.0f, __fmul_ru(eta_r, one_l), rp);
+            const float U = __fadd_ru(__fadd_ru(fabsf(c), ec), rp);
+            if (!(U <= rdn)) {  // NaN counts as live
+                live = true;
+                break;
+            }
+        }
+    }
+    if (live) a.live_flag[l] = 1;
+}
+
+// One block of 1024 threads: live[0 .. n_live) = ascending indices of the
+// flagged lines.
+__global__ void __launch_bounds__(1024) k_compact_live(const ScreenArgs a) {
+    __shared__ int warp_off[32];
+    __shared__ int chunk_total;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    int base = 0;
+    for (int l0 = 0; l0 < a.n_l; l0 += 1024) {
+        const int l = l0 + (int)threadIdx.x;
+        const bool f = l < a.n_l && a.live_flag[l] != 0;
+        const unsigned bal = __ballot_sync(0xffffffffu, f);
+        const int pre = __popc(bal & ((1u << lane) - 1u));
+        if (lane == 0) warp_off[w] = __popc(bal);
+        __syncthreads();
+        if (w == 0) {
+            const int t = warp_off[lane];
+            int incl = t;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += y;
+            }
+            warp_off[lane] = incl - t;
+            if (lane == 31) chunk_total = incl;
+        }
+        __syncthreads();
+        if (f) a.live[base + warp_off[w] + pre] = l;
+        base += chunk_total;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *a.n_live = base;
+}
+
+// rows[i] = phi[live[i]] (times rbus when scaled), one warp per row
+__global__ void __launch_bounds__(256) k_gather_live_rows(const ScreenArgs a) {
+    const int n = *a.n_live;
+    const int nv = a.n_a_pad >> 2;
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    const float4 *rr = reinterpret_cast<const float4 *>(a.rbus);
+    for (int i = gw; i < n; i += nw) {
+        const float4 *src = reinterpret_cast<const float4 *>(a.phi + (size_t)a.live[i] * a.n_a_pad);
+        float4 *dst = reinterpret_cast<float4 *>(a.rows + (size_t)i * a.n_a_pad);
+        for (int v = lane; v < nv; v += 32) {
+            const float4 p = src[v];
+            if (rr) {
+                const float4 r = rr[v];
+                dst[v] = make_float4(__fmul_rn(p.x, r.x), __fmul_rn(p.y, r.y), __fmul_rn(p.z, r.z),
+                                     __fmul_rn(p.w, r.w));
+            } else {
+                dst[v] = p;
+            }
+        }
+    }
+}
+
+cudaError_t launch_screen(const ScreenArgs &a, int num_sms, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(a.live_flag, 0, (size_t)a.n_l * sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    if (a.n_l > 0 && a.n_c > 0) {
+        const dim3 g((a.n_l + kScreenThreads - 1) / kScreenThreads, (a.n_c + kScreenK - 1) / kScreenK);
+        k_screen<<<g, kScreenThreads, 0, s>>>(a);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    k_compact_live<<<1, 1024, 0, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_gather_live_rows<<<num_sms * 4, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace ibp

@@ -110,7 +110,8 @@ cudaError_t launch_bus(const BusArgs &a, cudaStream_t s) {
 // and an error allowance are summed per warp into partials (FP64 directed).
 // Rows n_l .. n_l + n_c - 1 (one-box mode only) write the scaled rows
 // hat_k[k] = RN(Phi~[ctg_line[k], b] r_b) used by the contingency kernel;
-// line rows write hat_l[l] likewise.
+// line rows write hat_l[l] likewise when hat_l is given (unscreened calls; the
+// line screen writes the rows of the lines it keeps).
 // ---------------------------------------------------------------------------
 constexpr int kBaseWarps = 8;
 
@@ -120,8 +121,7 @@ __global__ void __launch_bounds__(kBaseWarps * 32) k_base(BaseArgs a) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gw = blockIdx.x * kBaseWarps + warp;
     const int nw = gridDim.x * kBaseWarps;
-    const bool scaled = a.hat_l != nullptr;
-    const int n_rows = a.n_l + (scaled ? a.n_c : 0);
+    const int n_rows = a.n_l + (a.hat_k ? a.n_c : 0);
     const int nv = a.n_a_pad >> 2;  // float4 per row
     double *part = a.partials + (size_t)gw * a.n_box * kPartVals;
     for (int j = 0; j < a.n_box; ++j)
@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(kBaseWarps * 32) k_base(BaseArgs a) {
             double cs = 0.0;
             float C0 = 0.f, C1 = 0.f, C2 = 0.f, C3 = 0.f;
             float R0 = 0.f, R1 = 0.f, R2 = 0.f, R3 = 0.f;
-            float4 *hl = scaled ? reinterpret_cast<float4 *>(a.hat_l + (size_t)l * a.n_a_pad) : nullptr;
+            float4 *hl = a.hat_l ? reinterpret_cast<float4 *>(a.hat_l + (size_t)l * a.n_a_pad) : nullptr;
             for (int v = lane; v < nv; v += 32) {
                 const float4 p = prow[v];
                 const double2 c01 = cb[2 * v], c23 = cb[2 * v + 1];
@@ -288,7 +288,10 @@ __global__ void __launch_bounds__(256) k_assemble(AsmArgs a) {
     bool up[N] = {false, true, true, true, false, true, true, true, false, true, false, true,
                   true, true, false, true, false, true};
     for (int i = 0; i < N; ++i) v[i] = 0.0;
-    for (int p = threadIdx.x; p < a.n_part_ctg; p += blockDim.x) {
+    int n_part_ctg = a.n_part_ctg;
+    if (a.n_live)
+        n_part_ctg = (*a.n_live + a.live_BL - 1) / a.live_BL * a.live_tiles_k * a.live_rows_per_tile;
+    for (int p = threadIdx.x; p < n_part_ctg; p += blockDim.x) {
         const double *q = a.part_ctg + ((size_t)p * a.n_box + j) * kPartVals;
         v[0] = __dadd_rd(v[0], q[0]);
         v[1] = __dadd_ru(v[1], q[1]);

@@ -281,6 +281,41 @@ def test_tight_inside_paper_mode(cases):
         np.testing.assert_allclose(cent, pc, atol=1e-9 * np.abs(pc).max())
 
 
+def test_screen_keeps_every_violating_line(cases):
+    """A line the paper-mode screen drops has the tight violation interval
+    [0, 0] for every contingency (checked against the tight flows summed by
+    the plain definition), and dropping those lines leaves the contingency
+    penalty sums of the bound unchanged."""
+    for cfg, nb in ((0, 1), (1, 1), (1, 4)):
+        c = cases(cfg)
+        s = O.sensitivities(c)
+        if nb > 1:
+            rng = np.random.default_rng(5)
+            lo, hi = split_boxes(c.box_lo[0], c.box_hi[0], 2, rng)
+        else:
+            lo, hi = c.box_lo, c.box_hi
+        cb, rb = O.bus_box(c, lo, hi)
+        live = O.screen_lines(c, s, cb, rb)
+        cent, rad = O.all_ctg_flows(c, s, cb, rb)
+        viol_hi = np.maximum(np.abs(cent) + rad - c.rating[None, None, :], 0.0)
+        assert np.all(viol_hi[:, :, ~live] == 0.0)
+        fc_lo, fc_hi = O.ctg_terms(c, s, cb, rb)[:2]
+        viol_lo = np.maximum(np.maximum(np.abs(cent) - rad, 0.0) - c.rating[None, None, :], 0.0)
+        np.testing.assert_allclose(viol_hi[:, :, live].sum(axis=(1, 2)), fc_hi, rtol=1e-9)
+        np.testing.assert_allclose(viol_lo[:, :, live].sum(axis=(1, 2)), fc_lo, rtol=1e-9,
+                                   atol=1e-9 * (1 + np.abs(fc_hi).max()))
+    # at a point box both radii vanish: the screen keeps exactly the lines
+    # with a post-contingency flow above the rating
+    c = cases(1)
+    s = O.sensitivities(c)
+    mid = 0.5 * (c.box_lo + c.box_hi)
+    cb, rb = O.bus_box(c, mid, mid)
+    cent, _ = O.all_ctg_flows(c, s, cb, rb)
+    want = np.any(np.abs(cent[0]) > c.rating[None, :], axis=0)
+    np.testing.assert_array_equal(O.screen_lines(c, s, cb, rb), want)
+    assert 0 < want.sum() < c.n_line
+
+
 def test_inclusion_monotone(cases):
     c = cases(1)
     s = O.sensitivities(c)
