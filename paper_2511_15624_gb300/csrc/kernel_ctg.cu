@@ -303,15 +303,18 @@ __global__ void __launch_bounds__(WL * WK * 32, MINB)
 // ---------------------------------------------------------------------------
 constexpr int kMB = 16;  // boxes per work item
 
-template <int ST>
+// BH = box halves: 1 -> 8 warps, each thread 16 boxes; 2 -> 16 warps, the
+// second 8 warps take boxes 8..15 of the item (h is formed by both halves).
+template <int ST, int BH = 1>
 struct MultiShape {
-    static constexpr int kWarps = 8, kThreads = 256;
+    static constexpr int kWarps = 8 * BH, kThreads = 256 * BH;
+    static constexpr int kMBT = kMB / BH;  // boxes per thread
     static constexpr int TL = 16, TK = 16, ML = 4;
     static constexpr int BL = TL * ML, BK = TK;
     static constexpr int CH = 32;
     static constexpr int kStageFloats = (BL + BK) * CH + CH * kMB;
     static constexpr size_t kRing = (size_t)ST * kStageFloats * sizeof(float);
-    static constexpr size_t kAcc3 = (size_t)ML * kMB * kThreads * sizeof(float);
+    static constexpr size_t kAcc3 = (size_t)ML * kMBT * kThreads * sizeof(float);
     static constexpr size_t kCtl = ST * sizeof(uint64_t) + 2 * ST * sizeof(int) + 16;
     // per-warp copy of the current item's kernel arguments
     static constexpr size_t kArgs = (size_t)kWarps * ((sizeof(CtgArgs) + 15) / 16 * 16);
@@ -369,10 +372,10 @@ struct CasesPlan {
     }
 };
 
-template <int ST, class Plan>
+template <int ST, int BH, class Plan>
 __device__ __forceinline__ void issue_multi(const Plan &P, float *ring, uint64_t *full,
                                             int *last_issued, uint32_t c, int i, int ch) {
-    using S = MultiShape<ST>;
+    using S = MultiShape<ST, BH>;
     constexpr uint32_t kBytes = (uint32_t)S::kStageFloats * sizeof(float);
     const int s = (int)(c % ST);
     const MultiItemView v = P.item(i);
@@ -386,15 +389,15 @@ __device__ __forceinline__ void issue_multi(const Plan &P, float *ring, uint64_t
     tma_load_2d(smem_addr(sR), v.mR, smem_addr(&full[s]), v.b0, ch * S::CH);
 }
 
-template <int ST, class Plan>
+template <int ST, int BH, class Plan>
 __device__ __forceinline__ void multi_body(const Plan &P, unsigned long long wait_ns, int *err) {
-    using S = MultiShape<ST>;
-    constexpr int CH = S::CH, ML = S::ML, TL = S::TL, BL = S::BL;
+    using S = MultiShape<ST, BH>;
+    constexpr int CH = S::CH, ML = S::ML, TL = S::TL, BL = S::BL, kMBT = S::kMBT;
     extern __shared__ unsigned char smem_raw[];
     float *ring = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                             ~uintptr_t(1023));
     float *acc3 = reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(ring) + S::kRing) +
-                  threadIdx.x;  // slot (i, j) at acc3[(i * kMB + j) * 256]
+                  threadIdx.x;  // slot (i, j) at acc3[(i * kMBT + j) * kThreads]
     constexpr size_t kArgSlot = (sizeof(CtgArgs) + 15) / 16 * 16;
     unsigned char *arg_base = reinterpret_cast<unsigned char *>(ring) + S::kRing + S::kAcc3;
     uint64_t *full = reinterpret_cast<uint64_t *>(arg_base + S::kArgs);
@@ -425,13 +428,15 @@ __device__ __forceinline__ void multi_body(const Plan &P, unsigned long long wai
                 ch -= P.item(i).n_chunks;
                 ++i;
             }
-            issue_multi<ST>(P, ring, full, last_issued, c, i, ch);
+            issue_multi<ST, BH>(P, ring, full, last_issued, c, i, ch);
             ++ch;
         }
     }
 
-    const int tl = (warp >> 1) * 4 + (lane >> 3);
-    const int tk = (warp & 1) * 8 + (lane & 7);
+    // box half of this warp (BH = 2) and its position inside the half
+    const int half = warp >> 3, wq = warp & 7;
+    const int tl = (wq >> 1) * 4 + (lane >> 3);
+    const int tk = (wq & 1) * 8 + (lane & 7);
     const int xl = tl & 7, xk = tk & 7;
     uint32_t it = 0;
     bool stop = false;
@@ -457,13 +462,13 @@ __device__ __forceinline__ void multi_body(const Plan &P, unsigned long long wai
             const int l = lq < n_ll ? (a.live ? __ldg(&a.live[lq]) : lq) : -1;
             Lr[i] = (l >= 0 && k < n_c) ? __ldg(&a.lodf[(size_t)k * n_l + l]) : 0.0f;
         }
-        float acc1[ML][kMB], acc2[ML][kMB];
+        float acc1[ML][kMBT], acc2[ML][kMBT];
 #pragma unroll
         for (int i = 0; i < ML; ++i)
 #pragma unroll
-            for (int j = 0; j < kMB; ++j) {
+            for (int j = 0; j < kMBT; ++j) {
                 acc1[i][j] = acc2[i][j] = 0.0f;
-                acc3[(i * kMB + j) * S::kThreads] = 0.0f;
+                acc3[(i * kMBT + j) * S::kThreads] = 0.0f;
             }
         for (int ch = 0; ch < v.n_chunks; ++ch, ++it) {
             const int s = (int)(it % ST);
@@ -490,10 +495,10 @@ __device__ __forceinline__ void multi_body(const Plan &P, unsigned long long wai
                     fl[i] = *reinterpret_cast<const float4 *>(sL + (tl + TL * i) * CH + ((q ^ xl) << 2));
 #pragma unroll
                 for (int t = 0; t < 4; ++t) {
-                    const float *rr = sR + (4 * q + t) * kMB;
-                    float r[kMB];
+                    const float *rr = sR + (4 * q + t) * kMB + half * kMBT;
+                    float r[kMBT];
 #pragma unroll
-                    for (int u = 0; u < kMB / 4; ++u) {
+                    for (int u = 0; u < kMBT / 4; ++u) {
                         const float4 r4 = *reinterpret_cast<const float4 *>(rr + 4 * u);
                         r[4 * u] = r4.x;
                         r[4 * u + 1] = r4.y;
@@ -506,7 +511,7 @@ __device__ __forceinline__ void multi_body(const Plan &P, unsigned long long wai
                         const float flt = t == 0 ? fl[i].x : t == 1 ? fl[i].y : t == 2 ? fl[i].z : fl[i].w;
                         const float ah = fabsf(__fmaf_rn(Lr[i], fkt, flt));
 #pragma unroll
-                        for (int j = 0; j < kMB; ++j) acc1[i][j] = __fmaf_ru(ah, r[j], acc1[i][j]);
+                        for (int j = 0; j < kMBT; ++j) acc1[i][j] = __fmaf_ru(ah, r[j], acc1[i][j]);
                     }
                 }
             }
@@ -524,14 +529,14 @@ __device__ __forceinline__ void multi_body(const Plan &P, unsigned long long wai
                             ++i2;
                         }
                         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                        issue_multi<ST>(P, ring, full, last_issued, nxt, i2, ch2);
+                        issue_multi<ST, BH>(P, ring, full, last_issued, nxt, i2, ch2);
                     }
                 }
             }
 #pragma unroll
             for (int i = 0; i < ML; ++i)
 #pragma unroll
-                for (int j = 0; j < kMB; ++j) {
+                for (int j = 0; j < kMBT; ++j) {
                     acc2[i][j] = __fadd_ru(acc2[i][j], acc1[i][j]);
                     acc1[i][j] = 0.0f;
                 }
@@ -539,8 +544,8 @@ __device__ __forceinline__ void multi_body(const Plan &P, unsigned long long wai
 #pragma unroll
                 for (int i = 0; i < ML; ++i)
 #pragma unroll
-                    for (int j = 0; j < kMB; ++j) {
-                        float &a3 = acc3[(i * kMB + j) * S::kThreads];
+                    for (int j = 0; j < kMBT; ++j) {
+                        float &a3 = acc3[(i * kMBT + j) * S::kThreads];
                         a3 = __fadd_ru(a3, acc2[i][j]);
                         acc2[i][j] = 0.0f;
                     }
@@ -548,8 +553,8 @@ __device__ __forceinline__ void multi_body(const Plan &P, unsigned long long wai
         }
         if (stop) break;
 #pragma unroll 1
-        for (int j = 0; j < kMB; ++j) {
-            const int box = b0 + j;
+        for (int j = 0; j < kMBT; ++j) {
+            const int box = b0 + half * kMBT + j;
             if (box >= n_box) break;
             float slo = 0.0f, shi = 0.0f, whi = 0.0f, wlo = 0.0f;
 #pragma unroll
@@ -560,13 +565,15 @@ __device__ __forceinline__ void multi_body(const Plan &P, unsigned long long wai
                     float a2 = 0.0f;
                     // registers cannot be indexed by the runtime j: select it
 #pragma unroll
-                    for (int jj = 0; jj < kMB; ++jj)
+                    for (int jj = 0; jj < kMBT; ++jj)
                         if (jj == j) a2 = acc2[i][jj];
-                    const float A = __fadd_ru(acc3[(i * kMB + j) * S::kThreads], a2);
+                    const float A = __fadd_ru(acc3[(i * kMBT + j) * S::kThreads], a2);
                     pair_epilogue(a, box, l, k, Lr[i], A, slo, shi, whi, wlo);
                 }
             }
-            write_warp_partials(a, tlk, warp, box, slo, shi, whi, wlo);
+            // partial rows per item: 8 (the warp's place in its half; each
+            // box belongs to exactly one half)
+            write_warp_partials(a, tlk, wq, box, slo, shi, whi, wlo);
         }
     }
     __syncthreads();
@@ -578,11 +585,11 @@ __device__ __forceinline__ void multi_body(const Plan &P, unsigned long long wai
     }
 }
 
-template <int ST>
-__global__ void __launch_bounds__(256, 1)
+template <int ST, int BH>
+__global__ void __launch_bounds__(256 * BH, 1)
     k_ctg_multi(const __grid_constant__ CUtensorMap mL, const __grid_constant__ CUtensorMap mK,
                 const __grid_constant__ CUtensorMap mR, const CtgArgs a) {
-    using S = MultiShape<ST>;
+    using S = MultiShape<ST, BH>;
     if (threadIdx.x == 0) {
         prefetch_tensormap(&mL);
         prefetch_tensormap(&mK);
@@ -593,27 +600,27 @@ __global__ void __launch_bounds__(256, 1)
     const int tiles_l = a.n_live ? (n_ll + S::BL - 1) / S::BL : a.tiles_l;
     const int n_tiles = a.n_live ? tiles_l * tiles_k * box_tiles : a.n_tiles;
     const SinglePlan P{&a, &mL, &mK, &mR, tiles_l, tiles_k, box_tiles, S::BL, S::BK, n_tiles};
-    multi_body<ST>(P, a.wait_ns, a.err);
+    multi_body<ST, BH>(P, a.wait_ns, a.err);
 }
 
 // Many cases in one persistent launch: CTA b walks items [start[b], start[b+1])
 // of the host-built table (longest items first, dealt round-robin).
-template <int ST>
-__global__ void __launch_bounds__(256, 1)
+template <int ST, int BH>
+__global__ void __launch_bounds__(256 * BH, 1)
     k_ctg_cases(const MultiItem *__restrict__ items, const int *__restrict__ cta_start,
                 const uint32_t *__restrict__ prefix, const CtgArgs *__restrict__ args,
                 const CUtensorMap *__restrict__ maps, unsigned long long wait_ns, int *err) {
     const int s0 = cta_start[blockIdx.x], s1 = cta_start[blockIdx.x + 1];
     const CasesPlan P{items + s0, prefix + s0 + blockIdx.x, s1 - s0, args, maps};
-    multi_body<ST>(P, wait_ns, err);
+    multi_body<ST, BH>(P, wait_ns, err);
 }
 
-template <int ST>
+template <int ST, int BH>
 static cudaError_t launch_multi(const CUtensorMap &mL, const CUtensorMap &mK,
                                 const CUtensorMap &mR, const CtgArgs &a, int grid,
                                 cudaStream_t s) {
-    using S = MultiShape<ST>;
-    auto kern = k_ctg_multi<ST>;
+    using S = MultiShape<ST, BH>;
+    auto kern = k_ctg_multi<ST, BH>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)S::kBytes);
     if (e != cudaSuccess) return e;
@@ -626,18 +633,23 @@ cudaError_t launch_ctg_multi(const CtgVariant &v, const CUtensorMap &mL, const C
                              const CUtensorMap &mR, const CtgArgs &a, int grid, cudaStream_t s) {
     if (a.n_tiles <= 0) return cudaSuccess;
     switch (v.id) {
-    case 20: return launch_multi<4>(mL, mK, mR, a, grid, s);
-    case 21: return launch_multi<6>(mL, mK, mR, a, grid, s);
+    case 20: return launch_multi<4, 1>(mL, mK, mR, a, grid, s);
+    case 21: return launch_multi<6, 1>(mL, mK, mR, a, grid, s);
+    case 22: return launch_multi<4, 2>(mL, mK, mR, a, grid, s);
+    case 23: return launch_multi<6, 2>(mL, mK, mR, a, grid, s);
     default: return cudaErrorInvalidValue;
     }
 }
 
+// box halves of the many-case launch (same work items either way)
+constexpr int kCasesBH = 2;
+
 cudaError_t launch_ctg_cases(const MultiItem *items, const int *cta_start, const uint32_t *prefix,
                              const CtgArgs *args, const CUtensorMap *maps, int grid,
                              unsigned long long wait_ns, int *err, cudaStream_t s) {
-    using S = MultiShape<4>;
+    using S = MultiShape<4, kCasesBH>;
     if (grid <= 0) return cudaSuccess;
-    auto kern = k_ctg_cases<4>;
+    auto kern = k_ctg_cases<4, kCasesBH>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)S::kBytes);
     if (e != cudaSuccess) return e;
@@ -667,6 +679,8 @@ static const CtgVariant kVariants[] = {
     {11, 0, 64, 64, 64, 2, 1, "2 CTAs/SM x 8 warps, 4x4/thread, 64-bus chunks, 2 stages, tree"},
     {20, 1, 64, 16, 32, 4, 16, "multi-box 64x16x16, 8 warps, 4 lines x 16 boxes/thread, 4 stages"},
     {21, 1, 64, 16, 32, 6, 16, "multi-box 64x16x16, 8 warps, 4 lines x 16 boxes/thread, 6 stages"},
+    {22, 1, 64, 16, 32, 4, 8, "multi-box 64x16x16, 16 warps, 4 lines x 8 boxes/thread, 4 stages"},
+    {23, 1, 64, 16, 32, 6, 8, "multi-box 64x16x16, 16 warps, 4 lines x 8 boxes/thread, 6 stages"},
 };
 
 const CtgVariant *ctg_variants(int *count) {
