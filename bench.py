@@ -31,9 +31,10 @@ METRIC = "ms per certified N-1 objective bound, 8316-bus"
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
 # contingency kernel, from a one-pass ncu capture of this same kernel build on
-# the same workload; keyed by (config, tile-shape variant, screen on).  Other
-# workloads, tile shapes or kernel builds report null.
-MEASURED_TRAFFIC = {(3, 0, True): 1.316e9}
+# the same workload; keyed by (config, tile-shape variant, screen on,
+# network reduction on).  Other workloads, tile shapes or kernel builds
+# report null.
+MEASURED_TRAFFIC = {(3, 0, True, False): 1.316e9}
 
 
 def workload(case, cfg, nb):
@@ -54,6 +55,8 @@ def _args():
                    help="contingency-kernel tile shape (0 = library default)")
     p.add_argument("--no-screen", action="store_true",
                    help="run every line through the contingency kernel (no paper-mode line screen)")
+    p.add_argument("--no-reduction", action="store_true",
+                   help="stream every active bus and line (no exact network reduction)")
     p.add_argument("--boxes", type=int, default=32,
                    help="box count of the batched measurement on the same network (0 = skip)")
     p.add_argument("--study", default="", choices=["", "bisection", "ragged"],
@@ -221,7 +224,12 @@ def run_gb300(args):
         gpu.set_variant(args.variant)
     if args.no_screen:
         gpu.set_screen(False)
+    if args.no_reduction:
+        gpu.set_reduction(False)
     info = gpu.info()
+    # columns the contingency kernel streams: bus classes under the reduction
+    reduced = (not args.no_reduction) and (info.n_bridges > 0 or info.n_bus_classes < info.n_active)
+    n_cols = info.n_bus_classes if reduced else info.n_active
     nb = 1
     lo = torch.tensor(case.box_lo, device=dev)
     hi = torch.tensor(case.box_hi, device=dev)
@@ -300,7 +308,7 @@ def run_gb300(args):
         gpu.set_timing(False)
         b_live = gpu.last_live()[0]
         b_live = case.n_line if b_live < 0 else b_live
-        bflop = P.algorithmic_flop(case.n_ctg, b_live, info.n_active, args.boxes)
+        bflop = P.algorithmic_flop(case.n_ctg, b_live, n_cols, args.boxes)
         batched = {"boxes": args.boxes, "ms_per_call": bms, "ms_per_bound": bms / args.boxes,
                    "lines_kept_by_screen": b_live,
                    "contingency_kernel_ms": bk["contingency"],
@@ -316,7 +324,7 @@ def run_gb300(args):
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak = sm_count * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s, FMA lanes x 2 x max clock
-    flop = P.algorithmic_flop(case.n_ctg, n_live, info.n_active, nb)
+    flop = P.algorithmic_flop(case.n_ctg, n_live, n_cols, nb)
     achieved = flop / (ctg_ms * 1e-3) / 1e12
     line = {
         "metric": METRIC, "value": value, "unit": "ms", "n_gpus": ws, "steps": args.steps,
@@ -324,18 +332,21 @@ def run_gb300(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": workload(case, args.config, nb), "boxes": nb,
                    "n_active_buses": info.n_active, "lines_kept_by_screen": n_live,
+                   "network_reduction": {"on": reduced, "bus_classes": info.n_bus_classes,
+                                         "bridges": info.n_bridges},
                    "interval_flows_per_s": case.n_ctg * case.n_line * nb / (value * 1e-3),
                    "l2": "no flush: the streamed PTDF rows (345 MB) exceed the 129 MB L2",
                    "kernel_ms": tot_k},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                      "frac": achieved / fp32_peak,
-                     "traffic": MEASURED_TRAFFIC.get((args.config, args.variant, not args.no_screen)),
+                     "traffic": MEASURED_TRAFFIC.get((args.config, args.variant, not args.no_screen,
+                                                      reduced)),
                      "peak_source": f"{sm_count} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz"},
         "clocks": clocks,
         "e2e": {"value": e2e_ms / bounds, "unit": "ms",
                 "h2d_bytes_per_step": int(2 * case.box_lo.nbytes),
                 "d2h_bytes_per_step": int(3 * 8 * nb)},
-        "gpu_launches": (4 + (3 if n_live_screened else 0)) * args.steps,
+        "gpu_launches": (4 + (3 if n_live_screened else 0) + (1 if reduced else 0)) * args.steps,
         "batched": None if batched is None else {
             **batched, "frac": batched["achieved_tflops"] / fp32_peak,
             "interval_flows_per_s": case.n_ctg * case.n_line * batched["boxes"] / (batched["ms_per_call"] * 1e-3)},

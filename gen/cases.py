@@ -242,11 +242,16 @@ def _pwl(rng, n_dev, pmax, lo_slope, hi_slope, nseg, convex):
 
 def make_network_case(name: str, n_bus: int, n_line: int, n_gen: int, n_load: int,
                       seed: int, n_ctg: Optional[int] = None, n_seg: int = 1,
-                      n_tighten: Optional[int] = None, ring5: bool = False) -> Case:
-    """Draw one network case with a single root box."""
+                      n_tighten: Optional[int] = None, ring5: bool = False,
+                      topology=None, slack: int = 0) -> Case:
+    """Draw one network case with a single root box.  ``topology`` = (from,
+    to) fixes the lines (reactances are still drawn)."""
     rng = np.random.default_rng(seed)
-    slack = 0
-    if ring5:
+    if topology is not None:
+        fr = np.asarray(topology[0], np.int32)
+        to = np.asarray(topology[1], np.int32)
+        x = np.exp(rng.normal(-2.3, 0.5, size=fr.size))
+    elif ring5:
         fr = np.array([0, 1, 2, 3, 4, 1], np.int32)
         to = np.array([1, 2, 3, 4, 0, 3], np.int32)
         x = rng.uniform(0.05, 0.5, size=6)
@@ -287,6 +292,23 @@ def make_network_case(name: str, n_bus: int, n_line: int, n_gen: int, n_load: in
                 load_nseg=load_nseg, load_slope=load_slope, load_bkpt=load_bkpt,
                 zeta_inj=ZETA_INJ, zeta_f=ZETA_F, ctg_line=ctg,
                 box_lo=lo[None, :].copy(), box_hi=hi[None, :].copy())
+
+
+def make_two_core_case(seed: int = 1200) -> Case:
+    """Two meshed cores joined by a path of bridges, radial feeders hanging off
+    both, and the slack at the end of a feeder: a small network whose
+    2-edge-connected structure has several parts with inner lines."""
+    core_a = [(0, 1), (1, 2), (2, 3), (3, 4), (4, 5), (5, 0), (1, 4), (2, 5)]
+    core_b = [(10, 11), (11, 12), (12, 13), (13, 14), (14, 10), (11, 13)]
+    core_c = [(20, 21), (21, 22), (22, 20)]
+    path = [(3, 6), (6, 7), (7, 10), (12, 18), (18, 20)]
+    feeders = [(0, 8), (8, 9), (9, 24), (5, 15), (15, 16), (16, 17), (14, 19), (19, 23),
+               (21, 25), (25, 26), (6, 27)]
+    lines = core_a + core_b + core_c + path + feeders
+    fr = np.array([a for a, _ in lines], np.int32)
+    to = np.array([b for _, b in lines], np.int32)
+    return make_network_case("two-core", 28, len(lines), 8, 14, seed=seed, topology=(fr, to),
+                             slack=24)
 
 
 def time_index_boxes(case: Case, n_box: int, seed: int) -> Case:

@@ -200,6 +200,8 @@ typedef struct {
     int64_t device_bytes;  /* device memory held by the case */
     double build_seconds;  /* wall time of the FP64 sensitivity build */
     double max_abs_lodf;   /* max |L| over the contingency list */
+    int32_t n_bus_classes; /* columns of the reduced rows (see ibp_case_reduction) */
+    int32_t n_bridges;     /* bridge lines (never contingencies) */
 } ibp_case_info_t;
 
 ibp_status ibp_case_info(const ibp_case *c, ibp_case_info_t *out);
@@ -233,6 +235,31 @@ int32_t ibp_kernel_variants(int32_t *ids, int32_t cap, int32_t batched);
  */
 ibp_status ibp_case_set_screen(ibp_case *c, int32_t enable);
 ibp_status ibp_case_last_live(ibp_case *c, int32_t *n_live, int32_t *lines);
+
+/*
+ * Exact network reduction of the contingency pass (enabled by default;
+ * enable = 0 disables).  Two identities of the DC network, both exact in
+ * exact arithmetic, shrink the n_c x n_l x n_a contraction behind
+ * eq. (ctg flow simplified):
+ *  - a bridge line carries the net injection of the side away from the slack,
+ *    which no non-islanding outage changes (L[l,k] = 0), so all n_c pairs of a
+ *    bridge share its base interval and are added in closed form;
+ *  - removing the bridges leaves 2-edge-connected components; an injection
+ *    enters each component through one vertex, so active buses that enter
+ *    every component with inner lines through the same vertices have equal
+ *    PTDF columns on every non-bridge line.  Such a class streams as one
+ *    column whose radius is the rounded-up sum of its members' radii; the
+ *    class of the slack has a zero column there and is dropped.
+ * The result stays certified against the FP64 data (the column equalities
+ * hold to the accuracy of the FP64 build); only the rounding of the sums
+ * moves.  Calls that ask for flow_lo/flow_hi and ibp_bound_multi do not use
+ * it.  ibp_case_reduction reports the partition: class_of_active[i] (host,
+ * [n_active], nullable) is the class of active column i or -1 for the
+ * slack's class; is_bridge[l] (host, [n_line], nullable) is 1 for bridges.
+ * Works on dry-run cases.  No counterpart in the paper.
+ */
+ibp_status ibp_case_set_reduction(ibp_case *c, int32_t enable);
+ibp_status ibp_case_reduction(const ibp_case *c, int32_t *class_of_active, int32_t *is_bridge);
 
 /*
  * Optional per-kernel timing of the last ibp_bound call, recorded with CUDA

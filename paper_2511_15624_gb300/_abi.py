@@ -25,6 +25,7 @@ EXPORTED = (
     "ibp_case_sync", "ibp_case_info", "ibp_case_set_variant", "ibp_kernel_variants",
     "ibp_case_set_timing", "ibp_case_last_timing", "ibp_selftest_wait_timeout", "ibp_last_error",
     "ibp_status_string", "ibp_bound_noalloc", "ibp_case_set_screen", "ibp_case_last_live",
+    "ibp_case_set_reduction", "ibp_case_reduction",
 )
 
 
@@ -39,7 +40,8 @@ class CaseInfo(ctypes.Structure):
                 ("n_gen", ctypes.c_int32), ("n_load", ctypes.c_int32),
                 ("n_active", ctypes.c_int32), ("n_active_pad", ctypes.c_int32),
                 ("device", ctypes.c_int32), ("device_bytes", ctypes.c_int64),
-                ("build_seconds", ctypes.c_double), ("max_abs_lodf", ctypes.c_double)]
+                ("build_seconds", ctypes.c_double), ("max_abs_lodf", ctypes.c_double),
+                ("n_bus_classes", ctypes.c_int32), ("n_bridges", ctypes.c_int32)]
 
 
 _lib = None
@@ -83,6 +85,10 @@ def lib():
         L.ibp_case_set_screen.argtypes = [P, I32]
         L.ibp_case_set_screen.restype = ctypes.c_int
         L.ibp_case_last_live.argtypes = [P, P, P]
+        L.ibp_case_set_reduction.argtypes = [P, I32]
+        L.ibp_case_set_reduction.restype = ctypes.c_int
+        L.ibp_case_reduction.argtypes = [P, P, P]
+        L.ibp_case_reduction.restype = ctypes.c_int
         L.ibp_case_last_live.restype = ctypes.c_int
         L.ibp_selftest_wait_timeout.argtypes = [I32, I32]
         L.ibp_selftest_wait_timeout.restype = ctypes.c_int
@@ -221,6 +227,19 @@ def ibp_case_last_timing(handle):
 
 def ibp_case_set_screen(handle, enable: bool):
     _check(lib().ibp_case_set_screen(ctypes.c_void_p(handle), int(bool(enable))))
+
+
+def ibp_case_set_reduction(handle, enable: bool):
+    _check(lib().ibp_case_set_reduction(ctypes.c_void_p(handle), int(bool(enable))))
+
+
+def ibp_case_reduction(handle, n_active: int, n_line: int):
+    """(class of each active column or -1, bridge flag of each line)."""
+    cls = np.empty(max(n_active, 1), np.int32)
+    br = np.empty(max(n_line, 1), np.int32)
+    _check(lib().ibp_case_reduction(ctypes.c_void_p(handle), cls.ctypes.data_as(ctypes.c_void_p),
+                                    br.ctypes.data_as(ctypes.c_void_p)))
+    return cls[:n_active].copy(), br[:n_line].copy()
 
 
 def ibp_case_last_live(handle, n_line: int):

@@ -130,6 +130,16 @@ class Case:
         """Paper-mode line screen ahead of the contingency kernel (default on)."""
         _abi.ibp_case_set_screen(self._h, enable)
 
+    def set_reduction(self, enable: bool):
+        """Exact network reduction of the contingency pass (default on)."""
+        _abi.ibp_case_set_reduction(self._h, enable)
+
+    def reduction(self):
+        """(class of each active bus column or -1 for the slack's class,
+        bridge flag of each line)."""
+        info = self.info()
+        return _abi.ibp_case_reduction(self._h, info.n_active, self.n_line)
+
     def last_live(self):
         """(count, ascending indices) of the lines the screen kept in the last
         bound, or (-1, None) when that call did not screen."""

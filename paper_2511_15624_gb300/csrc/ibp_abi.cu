@@ -88,6 +88,10 @@ struct ibp_case {
     int num_sms = 0;
     int variant = 0;
     bool screen = true;      // paper-mode line screen ahead of the contingency kernel
+    bool reduce = true;      // exact network reduction (bridges, bus classes)
+    bool has_reduction = false;
+    int n_r = 0, n_r_pad = 0, n_bridges = 0;  // bus classes, bridge lines
+    std::vector<int> cls_ptr_h, cls_col_h, is_bridge_h;
     int last_screened = 0;   // whether the last bound call ran the screen
     std::vector<int> ctg_line_h;
 
@@ -97,6 +101,11 @@ struct ibp_case {
     DevBuf<double> slope, bkpt;
     DevBuf<float> hat_l, hat_k;  // one-box scaled rows (lazily allocated)
     DevBuf<float> phi_k;         // unscaled PTDF rows of the contingency lines
+    // network reduction: bridge flags, bus classes (CSR over active columns)
+    // and the PTDF columns of one member per class, [n_l][n_r_pad] and the
+    // contingency rows [n_c][n_r_pad]
+    DevBuf<int> is_bridge, cls_ptr, cls_col;
+    DevBuf<float> phi_r, phi_kr;
 
     // per-call workspace (ws_gen changes whenever its buffers move)
     int cap_box = 0, ws_gen = 0;
@@ -107,6 +116,7 @@ struct ibp_case {
     DevBuf<float> flows;
     DevBuf<int> err;
     DevBuf<int> live_flag, live, n_live;  // line screen
+    DevBuf<float> rcls, rcls_t;           // class radii [box][n_r_pad], [n_r_pad][box_pad]
     // adjoint workspace
     int bwd_cap_box = 0, act_cap = 0;
     DevBuf<int> act_count, cnt;
@@ -130,7 +140,8 @@ struct ibp_case {
             box_lo.free(); box_hi.free();
             obj.free(); cbus.free(); rbus.free(); cabs.free(); box_consts.free(); line_c.free();
             line_e.free(); line_R.free(); part_base.free(); part_ctg.free(); flows.free(); err.free();
-            live_flag.free(); live.free(); n_live.free();
+            live_flag.free(); live.free(); n_live.free(); is_bridge.free(); cls_ptr.free();
+            cls_col.free(); phi_r.free(); phi_kr.free(); rcls.free(); rcls_t.free();
             dev_col.free(); act_count.free(); cnt.free(); act_list.free(); W.free(); dc.free(); dr.free();
             grads.free();
         }
@@ -214,6 +225,83 @@ static std::vector<char> bridges(int n, int m, const std::vector<std::vector<std
 }
 
 static int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+// Bus classes of the exact network reduction.  Removing the bridges leaves the
+// 2-edge-connected components; an injection at bus b, withdrawn at the slack,
+// enters a component C through one vertex e_C(b) (b itself when b is in C) and
+// leaves it through e_C(slack), so on a line inside C its flow depends on b
+// only through e_C(b).  Buses with the same e_C for every component that has
+// a line inside it therefore have equal PTDF columns on every non-bridge line,
+// and buses with e_C(b) = e_C(slack) for all those components have a zero
+// column there.  Returns the classes as CSR over active column indices
+// (ascending within a class, classes ordered by their first member) without
+// the slack's class.
+static void bus_classes(int n, const std::vector<std::vector<std::pair<int, int>>> &adj,
+                        const std::vector<char> &br, const std::vector<int> &active, int slack,
+                        std::vector<int> &cls_ptr, std::vector<int> &cls_col) {
+    std::vector<int> comp(n, -1), size;
+    for (int r = 0; r < n; ++r) {
+        if (comp[r] >= 0) continue;
+        const int id = (int)size.size();
+        size.push_back(0);
+        std::vector<int> st{r};
+        comp[r] = id;
+        while (!st.empty()) {
+            const int v = st.back();
+            st.pop_back();
+            ++size[id];
+            for (auto [w, e] : adj[v])
+                if (!br[e] && comp[w] < 0) {
+                    comp[w] = id;
+                    st.push_back(w);
+                }
+        }
+    }
+    std::vector<int> key(n, 0), label(n);
+    for (int C = 0; C < (int)size.size(); ++C) {
+        if (size[C] < 2) continue;  // no line inside
+        // multi-source search from the vertices of C that avoids C's own lines
+        std::fill(label.begin(), label.end(), -1);
+        std::vector<int> st;
+        for (int v = 0; v < n; ++v)
+            if (comp[v] == C) {
+                label[v] = v;
+                st.push_back(v);
+            }
+        while (!st.empty()) {
+            const int v = st.back();
+            st.pop_back();
+            for (auto [w, e] : adj[v]) {
+                if (comp[v] == C && comp[w] == C) continue;
+                if (label[w] < 0) {
+                    label[w] = label[v];
+                    st.push_back(w);
+                }
+            }
+        }
+        // refine the partition by the entry vertex
+        std::map<std::pair<int, int>, int> ids;
+        for (int v = 0; v < n; ++v) {
+            auto it = ids.emplace(std::make_pair(key[v], label[v]), (int)ids.size()).first;
+            key[v] = it->second;
+        }
+    }
+    std::map<int, int> cls_of_key;
+    std::vector<std::vector<int>> members;
+    for (size_t i = 0; i < active.size(); ++i) {
+        const int k = key[active[i]];
+        if (k == key[slack]) continue;
+        auto it = cls_of_key.emplace(k, (int)members.size()).first;
+        if (it->second == (int)members.size()) members.emplace_back();
+        members[it->second].push_back((int)i);
+    }
+    cls_ptr.assign(1, 0);
+    cls_col.clear();
+    for (auto &m : members) {
+        cls_col.insert(cls_col.end(), m.begin(), m.end());
+        cls_ptr.push_back((int)cls_col.size());
+    }
+}
 
 // worst-case relative excess of a round-up sum accumulated in levels of
 // n1, n2, n3 terms: (1 + 2u)^(n1 + n2 + n3) - 1, with slack
@@ -475,6 +563,14 @@ extern "C" ibp_status ibp_case_create(int32_t n_bus, int32_t slack_bus, int32_t 
     }
     c->n_a = (int)active.size();
     c->n_a_pad = round_up(std::max(c->n_a, 1), 32);
+    // exact network reduction for the contingency kernel (host part)
+    bus_classes(n_bus, adj, br, active, slack_bus, c->cls_ptr_h, c->cls_col_h);
+    c->is_bridge_h.resize(n_line);
+    for (int l = 0; l < n_line; ++l) c->is_bridge_h[l] = br[l] ? 1 : 0;
+    c->n_bridges = (int)std::count(c->is_bridge_h.begin(), c->is_bridge_h.end(), 1);
+    c->n_r = (int)c->cls_ptr_h.size() - 1;
+    c->n_r_pad = round_up(std::max(c->n_r, 1), 32);
+    c->has_reduction = c->n_bridges > 0 || c->n_r < c->n_a;
 
     if (device < 0) {  // dry run: validation only
         c->device = -1;
@@ -552,6 +648,30 @@ extern "C" ibp_status ibp_case_create(int32_t n_bus, int32_t slack_bus, int32_t 
 
     std::vector<int> from(line_from, line_from + n_line), to(line_to, line_to + n_line);
     if ((st = build_sensitivities(c.get(), from, to, reactance, active)) != IBP_OK) return st;
+    {
+        // exact network reduction for the contingency kernel (device part)
+        const std::vector<int> &cptr = c->cls_ptr_h, &ccol = c->cls_col_h, &isb = c->is_bridge_h;
+        if (c->has_reduction) {
+            std::vector<int> rep_col(std::max(c->n_r, 1), 0);
+            for (int j = 0; j < c->n_r; ++j) rep_col[j] = ccol[cptr[j]];
+            DevBuf<int> drep;
+            CUDA_TRY(drep.alloc(rep_col.size()));
+            CUDA_TRY(cudaMemcpy(drep.p, rep_col.data(), rep_col.size() * sizeof(int), cudaMemcpyHostToDevice));
+            CUDA_TRY(c->is_bridge.alloc(n_line));
+            CUDA_TRY(cudaMemcpy(c->is_bridge.p, isb.data(), n_line * sizeof(int), cudaMemcpyHostToDevice));
+            CUDA_TRY(c->cls_ptr.alloc(cptr.size()));
+            CUDA_TRY(cudaMemcpy(c->cls_ptr.p, cptr.data(), cptr.size() * sizeof(int), cudaMemcpyHostToDevice));
+            CUDA_TRY(c->cls_col.alloc(std::max<size_t>(ccol.size(), 1)));
+            if (!ccol.empty())
+                CUDA_TRY(cudaMemcpy(c->cls_col.p, ccol.data(), ccol.size() * sizeof(int), cudaMemcpyHostToDevice));
+            CUDA_TRY(c->phi_r.alloc((size_t)n_line * c->n_r_pad));
+            CUDA_TRY(launch_gather_cols(c->phi_a.p, c->n_a_pad, n_line, drep.p, c->n_r, c->phi_r.p,
+                                        c->n_r_pad, nullptr));
+            CUDA_TRY(c->phi_kr.alloc((size_t)std::max(n_ctg, 1) * c->n_r_pad));
+            CUDA_TRY(launch_gather_rows(c->phi_r.p, c->n_r_pad, c->ctg_line.p, n_ctg, c->phi_kr.p, nullptr));
+            CUDA_TRY(cudaDeviceSynchronize());
+        }
+    }
     c->build_seconds =
         std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     for (auto &e : c->ev) CUDA_TRY(cudaEventCreate(&e));
@@ -650,15 +770,26 @@ static ibp_status enqueue_bound(ibp_case *c, int n_box, const double *lo, const 
     const CtgVariant *v = pick_variant(c, n_box);
     if (!v) return fail(IBP_EINVAL, "no kernel variant");
     const bool multi = n_box > 1;
-    // the screen leaves the flows of the lines it drops unwritten
-    const bool screened = c->screen && !flo && c->n_ctg > 0;
+    // the screen and the reduction leave the flows of the lines they drop unwritten
+    const bool reduced = c->reduce && c->has_reduction && !flo && c->n_ctg > 0;
+    const bool screened = (c->screen || reduced) && !flo && c->n_ctg > 0;
     c->last_screened = screened;
+    // columns of the rows the contingency kernel streams
+    const int n_w = reduced ? c->n_r_pad : c->n_a_pad;
     const int n_box_pad = (n_box + kBoxTile - 1) / kBoxTile * kBoxTile;
     if ((!multi || screened) && !c->hat_l.p) CUDA_TRY(c->hat_l.alloc((size_t)c->n_line * c->n_a_pad));
     if (!multi && !c->hat_k.p) CUDA_TRY(c->hat_k.alloc((size_t)std::max(c->n_ctg, 1) * c->n_a_pad));
+    if (reduced && c->rcls.n < (size_t)c->cap_box * c->n_r_pad) {
+        const size_t cap_pad = (size_t)(c->cap_box + kBoxTile - 1) / kBoxTile * kBoxTile;
+        CUDA_TRY(c->rcls.alloc((size_t)c->cap_box * c->n_r_pad));
+        CUDA_TRY(c->rcls_t.alloc(cap_pad * c->n_r_pad));
+    }
     CUDA_TRY(cudaMemsetAsync(c->err.p, 0, sizeof(int), s));
-    if (multi)
+    if (multi) {
         CUDA_TRY(cudaMemsetAsync(c->rbus_t.p, 0, (size_t)c->n_a_pad * n_box_pad * sizeof(float), s));
+        if (reduced)
+            CUDA_TRY(cudaMemsetAsync(c->rcls_t.p, 0, (size_t)c->n_r_pad * n_box_pad * sizeof(float), s));
+    }
     if (c->timing) CUDA_TRY(cudaEventRecord(c->ev[0], s));
 
     BusArgs ba{};
@@ -668,6 +799,13 @@ static ibp_status enqueue_bound(ibp_case *c, int n_box, const double *lo, const 
     ba.n_box_pad = n_box_pad;
     ba.cabs = c->cabs.p; ba.box_consts = c->box_consts.p; ba.err = c->err.p;
     CUDA_TRY(launch_bus(ba, s));
+    if (reduced) {
+        ClsArgs ra{};
+        ra.n_box = n_box; ra.n_r = c->n_r; ra.n_r_pad = c->n_r_pad; ra.n_a_pad = c->n_a_pad;
+        ra.n_box_pad = n_box_pad; ra.cls_ptr = c->cls_ptr.p; ra.cls_col = c->cls_col.p;
+        ra.rbus = c->rbus.p; ra.rcls = c->rcls.p; ra.rcls_t = multi ? c->rcls_t.p : nullptr;
+        CUDA_TRY(launch_class_radius(ra, s));
+    }
     if (c->timing) CUDA_TRY(cudaEventRecord(c->ev[1], s));
 
     BaseArgs bb{};
@@ -678,9 +816,14 @@ static ibp_status enqueue_bound(ibp_case *c, int n_box, const double *lo, const 
     bb.gamma_base = rup_gamma((c->n_a_pad / 4 + 31) / 32, 2, 5);
     bb.line_c = c->line_c.p; bb.line_e = c->line_e.p; bb.line_R = c->line_R.p;
     bb.hat_l = (multi || screened) ? nullptr : c->hat_l.p;
-    bb.hat_k = multi ? nullptr : c->hat_k.p;
+    bb.hat_k = (multi || screened) ? nullptr : c->hat_k.p;
     bb.partials = c->part_base.p;
     bb.err = c->err.p;
+    if (reduced) {
+        bb.is_bridge = c->is_bridge.p;
+        bb.rate_c_up = c->rate_c_up.p;
+        bb.rate_c_dn = c->rate_c_dn.p;
+    }
     if (record) {
         bb.act_count = c->act_count.p;
         bb.act_list = c->act_list.p;
@@ -696,15 +839,20 @@ static ibp_status enqueue_bound(ibp_case *c, int n_box, const double *lo, const 
         sa.line_c = c->line_c.p; sa.line_e = c->line_e.p; sa.line_R = c->line_R.p;
         sa.box_consts = c->box_consts.p; sa.rate_dn = c->rate_c_dn.p;
         sa.live_flag = c->live_flag.p; sa.live = c->live.p; sa.n_live = c->n_live.p;
-        sa.phi = c->phi_a.p; sa.rbus = multi ? nullptr : c->rbus.p; sa.rows = c->hat_l.p;
-        sa.n_a_pad = c->n_a_pad;
+        sa.is_bridge = reduced ? c->is_bridge.p : nullptr;
+        sa.paper_test = c->screen ? 1 : 0;
+        sa.src = reduced ? c->phi_r.p : c->phi_a.p;
+        sa.radius = multi ? nullptr : (reduced ? c->rcls.p : c->rbus.p);
+        sa.rows = c->hat_l.p;
+        sa.hat_k = multi ? nullptr : c->hat_k.p;
+        sa.n_w = n_w;
         CUDA_TRY(launch_screen(sa, c->num_sms, s));
     }
     if (c->timing) CUDA_TRY(cudaEventRecord(c->ev[3], s));
 
     const int tiles_l = (c->n_line + v->BL - 1) / v->BL;
     const int tiles_k = (c->n_ctg + v->BK - 1) / v->BK;
-    const int n_chunks = (c->n_a_pad + v->CH - 1) / v->CH;
+    const int n_chunks = (n_w + v->CH - 1) / v->CH;
     CtgArgs ca{};
     ca.n_l = c->n_line; ca.n_c = c->n_ctg; ca.n_a = c->n_a; ca.n_chunks = n_chunks; ca.n_box = n_box;
     ca.tiles_l = tiles_l;
@@ -712,7 +860,7 @@ static ibp_status enqueue_bound(ibp_case *c, int n_box, const double *lo, const 
     ca.lodf = c->lodf.p; ca.ctg_line = c->ctg_line.p;
     ca.line_c = c->line_c.p; ca.line_e = c->line_e.p; ca.line_R = c->line_R.p;
     ca.rate_up = c->rate_c_up.p; ca.rate_dn = c->rate_c_dn.p; ca.box_consts = c->box_consts.p;
-    ca.rbus_t = multi ? c->rbus_t.p : nullptr; ca.n_box_pad = n_box_pad;
+    ca.rbus_t = multi ? (reduced ? c->rcls_t.p : c->rbus_t.p) : nullptr; ca.n_box_pad = n_box_pad;
     // round-up adds per radius sum: level 1 within a chunk (one per bus, or a
     // depth-2 tree per 4 buses plus one add), level 2 over 256/CH chunks, level 3
     {
@@ -736,17 +884,19 @@ static ibp_status enqueue_bound(ibp_case *c, int n_box, const double *lo, const 
     if (ca.n_tiles > 0) {
         CUtensorMap mL, mK, mR;
         std::string err;
+        // rows of n_w columns: bus classes (reduced) or active buses
         if (multi) {
             const float *rows = screened ? c->hat_l.p : c->phi_a.p;
-            if (!encode_map_2d(&mL, rows, c->n_a_pad, c->n_line, c->n_a_pad, 32, v->BL, &err) ||
-                !encode_map_2d(&mK, c->phi_k.p, c->n_a_pad, c->n_ctg, c->n_a_pad, 32, v->BK, &err) ||
-                !encode_map_2d(&mR, c->rbus_t.p, n_box_pad, c->n_a_pad, n_box_pad, kBoxTile, 32, &err,
-                               false))
+            const float *krows = reduced ? c->phi_kr.p : c->phi_k.p;
+            const float *rt = reduced ? c->rcls_t.p : c->rbus_t.p;
+            if (!encode_map_2d(&mL, rows, n_w, c->n_line, n_w, 32, v->BL, &err) ||
+                !encode_map_2d(&mK, krows, n_w, c->n_ctg, n_w, 32, v->BK, &err) ||
+                !encode_map_2d(&mR, rt, n_box_pad, n_w, n_box_pad, kBoxTile, 32, &err, false))
                 return fail(IBP_ECUDA, "%s", err.c_str());
             CUDA_TRY(launch_ctg_multi(*v, mL, mK, mR, ca, c->num_sms, s));
         } else {
-            if (!encode_map_2d(&mL, c->hat_l.p, c->n_a_pad, c->n_line, c->n_a_pad, 32, v->BL, &err) ||
-                !encode_map_2d(&mK, c->hat_k.p, c->n_a_pad, c->n_ctg, c->n_a_pad, 32, v->BK, &err))
+            if (!encode_map_2d(&mL, c->hat_l.p, n_w, c->n_line, n_w, 32, v->BL, &err) ||
+                !encode_map_2d(&mK, c->hat_k.p, n_w, c->n_ctg, n_w, 32, v->BK, &err))
                 return fail(IBP_ECUDA, "%s", err.c_str());
             CUDA_TRY(launch_ctg(*v, mL, mK, ca, c->num_sms, s));
         }
@@ -1165,6 +1315,20 @@ extern "C" ibp_status ibp_case_info(const ibp_case *c, ibp_case_info_t *o) {
     o->device_bytes = bytes;
     o->build_seconds = c->build_seconds;
     o->max_abs_lodf = c->max_abs_lodf;
+    o->n_bus_classes = c->n_r;
+    o->n_bridges = c->n_bridges;
+    return ok();
+}
+
+extern "C" ibp_status ibp_case_reduction(const ibp_case *c, int32_t *class_of_active, int32_t *is_bridge) {
+    if (!c) return fail(IBP_EINVAL, "case is NULL");
+    if (class_of_active) {
+        for (int i = 0; i < c->n_a; ++i) class_of_active[i] = -1;
+        for (int j = 0; j < c->n_r; ++j)
+            for (int m = c->cls_ptr_h[j]; m < c->cls_ptr_h[j + 1]; ++m) class_of_active[c->cls_col_h[m]] = j;
+    }
+    if (is_bridge)
+        for (int l = 0; l < c->n_line; ++l) is_bridge[l] = c->is_bridge_h[l];
     return ok();
 }
 
@@ -1178,6 +1342,12 @@ extern "C" ibp_status ibp_case_set_variant(ibp_case *c, int32_t variant) {
 extern "C" ibp_status ibp_case_set_screen(ibp_case *c, int32_t enable) {
     if (!c) return fail(IBP_EINVAL, "case is NULL");
     c->screen = enable != 0;
+    return ok();
+}
+
+extern "C" ibp_status ibp_case_set_reduction(ibp_case *c, int32_t enable) {
+    if (!c) return fail(IBP_EINVAL, "case is NULL");
+    c->reduce = enable != 0;
     return ok();
 }
 

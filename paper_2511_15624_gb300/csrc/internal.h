@@ -53,11 +53,17 @@ struct BaseArgs {
     float *hat_k;            // [n_c][n_a_pad] Phi[ctg line] * r or null
     double *partials;        // [n_part][n_box][kPartVals]
     // adjoint support (null when not recording): active base lines are
-    // appended to act_list[box][act_cap] as (l, l, 0, sign)
+    // appended to act_list[box][act_cap] as (l, l, 0, sign); active bridge
+    // lines under every contingency as (l, -1, multiplicity bits, sign)
     int *act_count;
     int4 *act_list;
     int act_cap;
     int *err;
+    // bridge lines in closed form (null: off): no contingency of the list
+    // moves the flow of a bridge, so its n_c contingency pairs share its base
+    // interval, judged against the contingency ratings
+    const int *is_bridge;    // [n_l]
+    const float *rate_c_up, *rate_c_dn;
 };
 
 struct CtgArgs {
@@ -100,11 +106,28 @@ struct ScreenArgs {
     int *live_flag;          // [n_l], zeroed before the launch
     int *live;               // [n_l] compacted list (ascending)
     int *n_live;             // [1]
-    // rows of the compacted list: dst[i] = phi[live[i]] (* rbus when scaled)
-    const float *phi;        // [n_l][n_a_pad]
-    const float *rbus;       // [n_a_pad] (one-box) or null (copy)
-    float *rows;             // [n_l][n_a_pad]
-    int n_a_pad;
+    // bridge lines never reach the contingency kernel (null: none); with
+    // paper_test == 0 every other line is kept
+    const int *is_bridge;
+    int paper_test;
+    // rows of the compacted list: rows[i] = src[live[i]] (* radius when
+    // scaled); one-box calls also write hat_k[k] = src[ctg_line[k]] * radius
+    const float *src;        // [n_l][n_w]: PTDF columns of the active buses or bus classes
+    const float *radius;     // [n_w] (one-box) or null (copy)
+    float *rows;             // [n_l][n_w]
+    float *hat_k;            // [n_c][n_w] or null
+    int n_w;                 // row width (a multiple of 32)
+};
+
+// Radius of each bus class (the active buses whose PTDF columns coincide on
+// every non-bridge line): rcls[j] = RU(sum of rbus over the class members).
+struct ClsArgs {
+    int n_box, n_r, n_r_pad, n_a_pad, n_box_pad;
+    const int *cls_ptr;      // [n_r + 1] CSR over active columns
+    const int *cls_col;
+    const float *rbus;       // [n_box][n_a_pad]
+    float *rcls;             // [n_box][n_r_pad]
+    float *rcls_t;           // [n_r_pad][n_box_pad] or null
 };
 
 struct BwdArgs {
@@ -175,6 +198,7 @@ cudaError_t launch_ctg_cases(const MultiItem *items, const int *cta_start, const
 void multi_tile_shape(int *BL, int *BK, int *CH);
 cudaError_t launch_assemble(const AsmArgs &a, cudaStream_t s);
 cudaError_t launch_screen(const ScreenArgs &a, int num_sms, cudaStream_t s);
+cudaError_t launch_class_radius(const ClsArgs &a, cudaStream_t s);
 cudaError_t launch_backward(const BwdArgs &a, cudaStream_t s);
 cudaError_t launch_wait_selftest(int *flag, unsigned long long limit_ns, cudaStream_t s);
 cudaError_t launch_or_err(int *dst, const int *src, cudaStream_t s);
@@ -189,6 +213,8 @@ cudaError_t launch_lodf(const double *Z, int nb_r, int n_l, int n_c, const int *
                         double *den_out, float *maxabs_out, cudaStream_t s);
 cudaError_t launch_gather_rows(const float *src, int ld, const int *rows, int n_rows,
                                float *dst, cudaStream_t s);
+cudaError_t launch_gather_cols(const float *src, int ld_src, int n_rows, const int *cols, int n_cols,
+                               float *dst, int ld_dst, cudaStream_t s);
 
 // read-only view of a case's device data and sizes (for entry points that
 // live in other translation units)

@@ -16,9 +16,14 @@
 // the exact centre is within e_c of the FP32 centre (pair_centre), and the
 // line is dead when  RU(|c~| + e_c + that radius) <= rating rounded down.
 //
+// Bridge lines never reach the contingency kernel when the network reduction
+// is on: no non-islanding outage moves their flow, and the base-flow kernel
+// adds their contingency terms in closed form.
+//
 // Kernels: screen (one thread per line and block of contingencies), compact
 // (one block: ascending list of live lines and its length), gather (one warp
-// per live row: the PTDF row, scaled by the bus radius in one-box mode).
+// per row: the kept lines' PTDF rows and, in one-box mode, the contingency
+// rows, scaled by the radius of each column), and the bus-class radii.
 #include "common.cuh"
 #include "ctg_epilogue.cuh"
 #include "internal.h"
@@ -31,6 +36,11 @@ constexpr int kScreenK = 64;  // contingencies per thread
 __global__ void __launch_bounds__(kScreenThreads) k_screen(const ScreenArgs a) {
     const int l = blockIdx.x * kScreenThreads + threadIdx.x;
     if (l >= a.n_l) return;
+    if (a.is_bridge && a.is_bridge[l]) return;
+    if (!a.paper_test) {
+        if (blockIdx.y == 0) a.live_flag[l] = 1;
+        return;
+    }
     const int k0 = blockIdx.y * kScreenK, k1 = min(k0 + kScreenK, a.n_c);
     const float rdn = __ldg(&a.rate_dn[l]);
     bool live = false;
@@ -96,17 +106,21 @@ __global__ void __launch_bounds__(1024) k_compact_live(const ScreenArgs a) {
     if (threadIdx.x == 0) *a.n_live = base;
 }
 
-// rows[i] = phi[live[i]] (times rbus when scaled), one warp per row
+// rows[i] = src[live[i]] and, with hat_k, hat_k[k] = src[ctg_line[k]]
+// (times the column radius when given), one warp per row
 __global__ void __launch_bounds__(256) k_gather_live_rows(const ScreenArgs a) {
     const int n = *a.n_live;
-    const int nv = a.n_a_pad >> 2;
+    const int n_rows = n + (a.hat_k ? a.n_c : 0);
+    const int nv = a.n_w >> 2;
     const int lane = threadIdx.x & 31;
     const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nw = (gridDim.x * blockDim.x) >> 5;
-    const float4 *rr = reinterpret_cast<const float4 *>(a.rbus);
-    for (int i = gw; i < n; i += nw) {
-        const float4 *src = reinterpret_cast<const float4 *>(a.phi + (size_t)a.live[i] * a.n_a_pad);
-        float4 *dst = reinterpret_cast<float4 *>(a.rows + (size_t)i * a.n_a_pad);
+    const float4 *rr = reinterpret_cast<const float4 *>(a.radius);
+    for (int i = gw; i < n_rows; i += nw) {
+        const int row = i < n ? a.live[i] : a.ctg_line[i - n];
+        const float4 *src = reinterpret_cast<const float4 *>(a.src + (size_t)row * a.n_w);
+        float *d = i < n ? a.rows + (size_t)i * a.n_w : a.hat_k + (size_t)(i - n) * a.n_w;
+        float4 *dst = reinterpret_cast<float4 *>(d);
         for (int v = lane; v < nv; v += 32) {
             const float4 p = src[v];
             if (rr) {
@@ -118,6 +132,28 @@ __global__ void __launch_bounds__(256) k_gather_live_rows(const ScreenArgs a) {
             }
         }
     }
+}
+
+// rcls[box][j] = RU(sum over the members b of class j of rbus[box][b]); the
+// classes partition a subset of the active columns (padding columns get 0)
+__global__ void __launch_bounds__(256) k_class_radius(const ClsArgs a) {
+    const int box = blockIdx.y;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= a.n_r_pad) return;
+    float r = 0.0f;
+    if (j < a.n_r) {
+        const float *rb = a.rbus + (size_t)box * a.n_a_pad;
+        for (int m = a.cls_ptr[j]; m < a.cls_ptr[j + 1]; ++m) r = __fadd_ru(r, rb[a.cls_col[m]]);
+    }
+    a.rcls[(size_t)box * a.n_r_pad + j] = r;
+    if (a.rcls_t) a.rcls_t[(size_t)j * a.n_box_pad + box] = r;
+}
+
+cudaError_t launch_class_radius(const ClsArgs &a, cudaStream_t s) {
+    if (a.n_box <= 0 || a.n_r_pad <= 0) return cudaSuccess;
+    const dim3 g((a.n_r_pad + 255) / 256, a.n_box);
+    k_class_radius<<<g, 256, 0, s>>>(a);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_screen(const ScreenArgs &a, int num_sms, cudaStream_t s) {

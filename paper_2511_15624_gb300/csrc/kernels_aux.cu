@@ -214,6 +214,37 @@ __global__ void __launch_bounds__(kBaseWarps * 32) k_base(BaseArgs a) {
                 q[1] = __dadd_ru(q[1], (double)shi);
                 q[2] = __dadd_ru(q[2], (double)whi);
                 q[3] = __dadd_ru(q[3], (double)wlo);
+                if (a.is_bridge && a.is_bridge[l] && a.n_c > 0) {
+                    // A bridge carries the net injection of the side away from
+                    // the slack; no non-islanding outage changes that, so
+                    // L[l,k] = 0 and every contingency pair of the line has the
+                    // base interval [c - rho, c + rho] (eq. (slack-Sc) with the
+                    // contingency rating), n_c times.
+                    const float rcu = a.rate_c_up[l], rcd = a.rate_c_dn[l];
+                    const float clo = fmax0(__fsub_rd(alo, rcu));
+                    const float chi = fmax0(__fsub_ru(ahi, rcd));
+                    float cwh = 0.0f, cwl = 0.0f;
+                    if (chi > 0.0f) {
+                        const float w = __fmaf_ru(a.gamma_base + 3.0f * kU, R,
+                                                  __fmaf_ru(2.0f, e, __fmaf_ru(kU, rcu, 2.0f * eta_r)));
+                        cwl = w;
+                        if (__fadd_ru(__fsub_ru(alo, rcd), w) > 0.0f) cwh = w;
+                    }
+                    const double nc = (double)a.n_c;
+                    q[0] = __dadd_rd(q[0], __dmul_rd(nc, (double)clo));
+                    q[1] = __dadd_ru(q[1], __dmul_ru(nc, (double)chi));
+                    q[2] = __dadd_ru(q[2], __dmul_ru(nc, (double)cwh));
+                    q[3] = __dadd_ru(q[3], __dmul_ru(nc, (double)cwl));
+                    if (a.act_list && clo > 0.0f) {
+                        const int idx = atomicAdd(&a.act_count[j], 1);
+                        if (idx < a.act_cap)
+                            a.act_list[(size_t)j * a.act_cap + idx] =
+                                make_int4(l, -1, __float_as_int((float)a.n_c),
+                                          __float_as_int(c > 0.0f ? 1.0f : -1.0f));
+                        else
+                            atomicOr(a.err, kErrOverflow);
+                    }
+                }
             }
             hl = nullptr;
         }
@@ -503,6 +534,22 @@ cudaError_t launch_gather_rows(const float *src, int ld, const int *rows, int n_
                                cudaStream_t s) {
     if (n_rows <= 0) return cudaSuccess;
     k_gather_rows<<<n_rows, 256, 0, s>>>(src, ld, rows, n_rows, dst);
+    return cudaGetLastError();
+}
+
+// dst[r][j] = src[r][cols[j]] for j < n_cols, 0 for n_cols <= j < ld_dst
+__global__ void k_gather_cols(const float *src, int ld_src, const int *cols, int n_cols, float *dst,
+                              int ld_dst) {
+    const int r = blockIdx.x;
+    const float *s = src + (int64_t)r * ld_src;
+    float *d = dst + (int64_t)r * ld_dst;
+    for (int j = threadIdx.x; j < ld_dst; j += blockDim.x) d[j] = j < n_cols ? s[cols[j]] : 0.0f;
+}
+
+cudaError_t launch_gather_cols(const float *src, int ld_src, int n_rows, const int *cols, int n_cols,
+                               float *dst, int ld_dst, cudaStream_t s) {
+    if (n_rows <= 0) return cudaSuccess;
+    k_gather_cols<<<n_rows, 256, 0, s>>>(src, ld_src, cols, n_cols, dst, ld_dst);
     return cudaGetLastError();
 }
 

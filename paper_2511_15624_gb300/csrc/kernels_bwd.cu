@@ -10,6 +10,8 @@
 //   d obj_hi / d rating_l = +z_f #{pairs of A on line l},
 // and sum_A sgn H_k[l,b] = sum_x W_x Phi[x,b] with line weights
 //   W_l += sgn, W_{line of k} += sgn L[l,k]  (H_k = Phi + L[:,k] Phi[k,:]).
+// An entry (l, -1, m, sgn) stands for m pairs of a bridge line, whose
+// contingency flows all equal its base flow (H_k[l,:] = Phi[l,:]).
 // The imbalance term and the monotone cost curves act on the device
 // endpoints directly.  Kernels, in order: weights, centre GEMV, radius pass,
 // chain rule to the box endpoints.
@@ -29,7 +31,14 @@ __global__ void k_bwd_weights(BwdArgs a) {
     int *cnt = a.cnt + (size_t)box * a.n_l;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const int4 e = list[i];
-        const float L = __int_as_float(e.z), sg = __int_as_float(e.w);
+        const float sg = __int_as_float(e.w);
+        if (e.y < 0) {  // a bridge line, m contingency pairs at once
+            const float m = __int_as_float(e.z);
+            atomicAdd(&W[e.x], (double)sg * (double)m);
+            atomicAdd(&cnt[e.x], (int)m);
+            continue;
+        }
+        const float L = __int_as_float(e.z);
         atomicAdd(&W[e.x], (double)sg);
         if (L != 0.0f) atomicAdd(&W[e.y], (double)sg * (double)L);
         atomicAdd(&cnt[e.x], 1);
@@ -65,6 +74,11 @@ __global__ void k_bwd_radius(BwdArgs a) {
         const int c1 = min(c0 + kEntryChunk, n);
         for (int i = c0; i < c1; ++i) {
             const int4 e = list[i];
+            if (e.y < 0) {  // a bridge line, m contingency pairs at once
+                tot += (double)__int_as_float(e.z) *
+                       (double)fabsf(__ldg(&a.phi[(size_t)e.x * a.n_a_pad + col]));
+                continue;
+            }
             const float L = __int_as_float(e.z);
             const float h = __fmaf_rn(L, __ldg(&a.phi[(size_t)e.y * a.n_a_pad + col]),
                                       __ldg(&a.phi[(size_t)e.x * a.n_a_pad + col]));

@@ -105,3 +105,52 @@ def test_no_cpu_fallback_without_device(pkg):
     if torch.cuda.is_available():
         pytest.skip("a GPU is present")
     _expect(P, P._abi.IBP_ECUDA, lambda: P.Case(make_config(0), device=0))
+
+
+@pytest.mark.parametrize("which", ["cfg1", "cfg2", "sparse", "odd", "two-core"])
+def test_network_reduction_partition(pkg, which):
+    """The bus classes and bridge flags of the exact network reduction, checked
+    against the oracle's FP64 PTDF and LODF (dry-run case, no GPU): bridges are
+    the lines with PTDF_line[l,l] = 1 and have L[l,k] = 0 for every
+    contingency; members of a class have equal PTDF columns on every non-bridge
+    line, and the buses dropped with the slack's class have zero columns there."""
+    import oracle as O
+    P = pkg
+    if which == "cfg1":
+        c = make_config(1)
+    elif which == "cfg2":
+        c = make_config(2)
+    elif which == "sparse":
+        # few extra edges: many bridges and several small 2-edge-connected parts
+        c = make_network_case("sparse", 160, 175, 30, 70, seed=91)
+    elif which == "odd":
+        c = make_network_case("odd", 37, 61, 9, 20, seed=77)
+    else:
+        # three meshed parts joined by bridges, slack at the end of a feeder
+        from gen.cases import make_two_core_case
+        c = make_two_core_case()
+    case = P.dry_run_case(c)
+    info = case.info()
+    cls, br = case.reduction()
+    phi = O.ptdf(c)
+    fr, to = c.line_from, c.line_to
+    diag = phi[np.arange(c.n_line), fr] - phi[np.arange(c.n_line), to]
+    np.testing.assert_array_equal(br.astype(bool), np.abs(1.0 - diag) < 1e-9)
+    assert info.n_bridges == int(br.sum())
+    active = np.array(sorted((set(c.gen_bus.tolist()) | set(c.load_bus.tolist())) - {c.slack}))
+    assert cls.shape == (active.size,) and info.n_active == active.size
+    nb = ~br.astype(bool)
+    scale = np.abs(phi).max()
+    for j in range(info.n_bus_classes):
+        cols = active[cls == j]
+        assert cols.size >= 1
+        d = np.abs(phi[nb][:, cols] - phi[nb][:, cols[:1]]).max()
+        assert d <= 1e-12 * scale, (j, d)
+    if np.any(cls < 0):
+        assert np.abs(phi[nb][:, active[cls < 0]]).max() <= 1e-12 * scale
+    assert set(np.unique(cls[cls >= 0]).tolist()) == set(range(info.n_bus_classes))
+    if br.any() and c.n_ctg > 0:
+        s = O.sensitivities(c)
+        assert np.abs(s.lodf[br.astype(bool)]).max() <= 1e-9
+    if which in ("sparse", "two-core"):
+        assert info.n_bus_classes < info.n_active

@@ -29,11 +29,14 @@ def test_multi_matches_per_case_and_oracle(env):
     torch.cuda.synchronize()
     for i, (n, c) in enumerate(zip(nets, cases)):
         c.sync()
-        # the many-case launch does not screen lines: the per-case call without
-        # the screen has the same work items, so only FP64 reduction order differs
+        # the many-case launch neither screens lines nor reduces the network:
+        # the per-case call without both has the same work items, so only the
+        # FP64 reduction order differs
         c.set_screen(False)
+        c.set_reduction(False)
         lo1, hi1, e1 = c.bound(n.box_lo, n.box_hi)
         c.set_screen(True)
+        c.set_reduction(True)
         lo, hi, err = (t.cpu().numpy() for t in outs[i])
         np.testing.assert_allclose(hi, hi1, rtol=1e-12, atol=0)
         np.testing.assert_allclose(lo, lo1, rtol=1e-12, atol=0)
@@ -70,5 +73,10 @@ def test_multi_in_cuda_graph(env):
     his[0].copy_(his[0] - 0.1 * (his[0] - los[0]))
     g.replay()
     torch.cuda.synchronize()
+    # (per-case call on the many-case launch's path: no screen, no reduction)
+    cases[0].set_screen(False)
+    cases[0].set_reduction(False)
     lo1, hi1, _ = cases[0].bound(nets[0].box_lo, his[0].cpu().numpy())
+    cases[0].set_screen(True)
+    cases[0].set_reduction(True)
     np.testing.assert_allclose(outs[0][1].cpu().numpy(), hi1, rtol=1e-12)

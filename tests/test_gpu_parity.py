@@ -48,13 +48,18 @@ def _obj_scale(ref):
     return z + 1e4 * (ref.terms["inj"][1]) + 1e3 * (ref.terms["fb"][1] + ref.terms["fc"][1])
 
 
-def check_objective(lo, hi, err, ref, rel=1e-5):
+def check_objective(lo, hi, err, ref, rel=1e-5, rel_scale=None):
+    """rel_scale (default |oracle value|) is what the 1e-5 relative bar is
+    taken of; small networks whose objective cancels far below its cost terms
+    pass the cost scale instead."""
     scale = _obj_scale(ref)
     d = 1e-9 * scale
+    rs_hi = np.abs(ref.hi) if rel_scale is None else rel_scale
+    rs_lo = np.abs(ref.lo) if rel_scale is None else np.maximum(rel_scale, np.abs(ref.lo))
     assert np.all(hi >= ref.hi - d), (hi, ref.hi)
     assert np.all(lo <= ref.lo + d), (lo, ref.lo)
-    assert np.all(np.abs(hi - ref.hi) <= rel * np.abs(ref.hi) + d), (hi, ref.hi)
-    assert np.all(np.abs(lo - ref.lo) <= rel * np.abs(ref.lo) + d), (lo, ref.lo)
+    assert np.all(np.abs(hi - ref.hi) <= rel * rs_hi + d), (hi, ref.hi)
+    assert np.all(np.abs(lo - ref.lo) <= rel * rs_lo + d), (lo, ref.lo)
     assert np.all(np.abs(hi - ref.hi) <= err[:, 0] + d), (hi - ref.hi, err[:, 0])
     assert np.all(np.abs(lo - ref.lo) <= err[:, 1] + d), (lo - ref.lo, err[:, 1])
 

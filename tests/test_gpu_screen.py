@@ -37,26 +37,37 @@ def _tight_live(case, sens, cb, rb):
     return np.any(np.abs(cent) + rad > rating[None, None, :], axis=(0, 1))
 
 
-def _check_live_set(case, sens, lo, hi, n, lines):
+def _check_live_set(case, sens, lo, hi, n, lines, bridges=None):
+    """bridges: lines the network reduction handles in closed form (never kept)."""
     cb, rb = O.bus_box(case, lo, hi)
     assert n == len(lines) and np.all(np.diff(lines) > 0)
     kept = np.zeros(case.n_line, bool)
     kept[lines] = True
     must = _tight_live(case, sens, cb, rb)
+    if bridges is not None:
+        assert not np.any(kept & bridges)
+        must &= ~bridges
     assert np.all(kept[must]), np.flatnonzero(must & ~kept)[:10]
     may = O.screen_lines(case, sens, cb, rb, rel=1e-4)
     assert np.all(may[kept]), np.flatnonzero(kept & ~may)[:10]
 
 
 def _screened_and_plain(P, gpu, lo, hi):
+    """The default call (screen and network reduction on) and the plain one."""
     gpu.set_screen(True)
     s = gpu.bound(lo, hi)
     n, lines = gpu.last_live()
     gpu.set_screen(False)
+    gpu.set_reduction(False)
     p = gpu.bound(lo, hi)
     assert gpu.last_live() == (-1, None)
     gpu.set_screen(True)
+    gpu.set_reduction(True)
     return s, p, n, lines
+
+
+def _bridges(gpu):
+    return gpu.reduction()[1].astype(bool)
 
 
 @pytest.mark.parametrize("cfg", [1, 2])
@@ -66,7 +77,7 @@ def test_screen_one_box(P, cfg):
     gpu = P.Case(case, device=0)
     (lo, hi, err), (plo, phi, perr), n, lines = _screened_and_plain(P, gpu, case.box_lo, case.box_hi)
     assert 0 < n <= case.n_line
-    _check_live_set(case, sens, case.box_lo, case.box_hi, n, lines)
+    _check_live_set(case, sens, case.box_lo, case.box_hi, n, lines, _bridges(gpu))
     ref = O.bound(case, sens)
     check_objective(lo, hi, err, ref)
     check_objective(plo, phi, perr, ref)
@@ -84,7 +95,7 @@ def test_screen_small_boxes_drop_many_lines(P):
     w = 0.02 * (case.box_hi[0] - case.box_lo[0])
     lo, hi = (mid - w)[None], (mid + w)[None]
     (slo, shi, serr), _, n, lines = _screened_and_plain(P, gpu, lo, hi)
-    _check_live_set(case, sens, lo, hi, n, lines)
+    _check_live_set(case, sens, lo, hi, n, lines, _bridges(gpu))
     assert n < case.n_line
     check_objective(slo, shi, serr, O.bound(case, sens, lo=lo, hi=hi))
 
@@ -94,7 +105,7 @@ def test_screen_multi_box(P):
     sens = _sens(1, make_config(1))
     gpu = P.Case(case, device=0)
     (lo, hi, err), (plo, phi, perr), n, lines = _screened_and_plain(P, gpu, case.box_lo, case.box_hi)
-    _check_live_set(case, sens, case.box_lo, case.box_hi, n, lines)
+    _check_live_set(case, sens, case.box_lo, case.box_hi, n, lines, _bridges(gpu))
     ref = O.bound(case, sens)
     check_objective(lo, hi, err, ref)
     assert np.all(np.abs(hi - phi) <= err[:, 0] + perr[:, 0])
@@ -130,3 +141,89 @@ def test_screen_adjoint_unchanged(P):
     np.testing.assert_allclose(a_lo, b_lo, rtol=0, atol=scale)
     np.testing.assert_allclose(a_hi, b_hi, rtol=0, atol=scale)
     np.testing.assert_array_equal(a_r, b_r)
+
+
+def _modes(P, gpu, lo, hi):
+    """Bounds with (screen, reduction) on/off."""
+    out = {}
+    for screen, reduce in ((True, True), (False, True), (True, False), (False, False)):
+        gpu.set_screen(screen)
+        gpu.set_reduction(reduce)
+        out[(screen, reduce)] = gpu.bound(lo, hi)
+    gpu.set_screen(True)
+    gpu.set_reduction(True)
+    return out
+
+
+@pytest.mark.parametrize("which", ["cfg2", "two-core", "sparse"])
+def test_reduction_one_box(P, which):
+    """Exact network reduction (bridges in closed form, bus classes): every
+    combination with the line screen contains the oracle's bound and agrees
+    with the plain path within the two error bounds."""
+    from gen import make_network_case
+    from gen.cases import make_two_core_case
+    if which == "cfg2":
+        case = make_config(2)
+        sens = _sens(2, case)
+    elif which == "two-core":
+        case = make_two_core_case()
+        sens = O.sensitivities(case)
+    else:
+        case = make_network_case("sparse", 160, 175, 30, 70, seed=91)
+        sens = O.sensitivities(case)
+    gpu = P.Case(case, device=0)
+    info = gpu.info()
+    assert info.n_bus_classes < info.n_active and info.n_bridges > 0
+    ref = O.bound(case, sens)
+    out = _modes(P, gpu, case.box_lo, case.box_hi)
+    plo, phi, perr = out[(False, False)]
+    # the small networks' objectives cancel to ~10% of their cost terms: the
+    # 1e-5 relative bar is taken of the cost scale there
+    rs = None if which == "cfg2" else np.abs(ref.terms["costs"]).sum(axis=1)
+    for key, (lo, hi, err) in out.items():
+        check_objective(lo, hi, err, ref, rel_scale=rs)
+        assert np.all(np.abs(hi - phi) <= err[:, 0] + perr[:, 0]), key
+        assert np.all(np.abs(lo - plo) <= err[:, 1] + perr[:, 1]), key
+    # the reduced call keeps no bridge line for the contingency kernel
+    gpu.bound(case.box_lo, case.box_hi)
+    n, lines = gpu.last_live()
+    _, br = gpu.reduction()
+    assert not np.any(br[lines])
+
+
+def test_reduction_multi_box_and_adjoint(P):
+    from gen.cases import make_two_core_case
+    base = make_two_core_case()
+    sens = O.sensitivities(base)
+    rng = np.random.default_rng(12)
+    lo, hi = split_boxes(base.box_lo[0], base.box_hi[0], 4, rng)
+    case = base.with_boxes(lo, hi)
+    gpu = P.Case(case, device=0)
+    ref = O.bound(case, sens)
+    out = _modes(P, gpu, lo, hi)
+    rs = np.abs(ref.terms["costs"]).sum(axis=1)
+    for key, (blo, bhi, berr) in out.items():
+        check_objective(blo, bhi, berr, ref, rel_scale=rs)
+    # the adjoints compare only where no active-set decision sits at its kink
+    from tests.test_gpu_adjoint import _kink_free
+    keep = [j for j in range(lo.shape[0]) if _kink_free(case, sens, lo[j], hi[j])[0]]
+    assert len(keep) >= 4
+    lo, hi = lo[keep], hi[keep]
+    case = case.with_boxes(lo, hi)
+    g = np.ones(lo.shape[0])
+    grads = {}
+    for reduce in (True, False):
+        gpu.set_reduction(reduce)
+        grads[reduce] = gpu.backward(lo, hi, g, want_rating=True)
+    gpu.set_reduction(True)
+    a_lo, a_hi, a_r = grads[True]
+    b_lo, b_hi, b_r = grads[False]
+    scale = 1e-9 * (1 + np.abs(b_lo).max() + np.abs(b_hi).max())
+    np.testing.assert_allclose(a_lo, b_lo, rtol=0, atol=scale)
+    np.testing.assert_allclose(a_hi, b_hi, rtol=0, atol=scale)
+    np.testing.assert_array_equal(a_r, b_r)
+    # and the hand adjoint of the oracle on the same boxes
+    o_lo, o_hi, o_r = O.grad_hi(case, sens, lo, hi)
+    tol = 1e-6 * (1 + np.abs(o_lo).max() + np.abs(o_hi).max())
+    np.testing.assert_allclose(a_lo, o_lo, rtol=0, atol=tol)
+    np.testing.assert_allclose(a_hi, o_hi, rtol=0, atol=tol)

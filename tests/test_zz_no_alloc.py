@@ -25,9 +25,11 @@ def test_noalloc_matches_bound_on_two_calls(cfg):
     # the existing entry point with the tile shape whose round-up summation
     # layout (one add per bus, 32-bus chunks) matches this entry point's, so
     # that the a-priori error bounds are comparable too; this entry point has
-    # no line screen, so the reference call runs without it as well
+    # no line screen or network reduction, so the reference call runs without
+    # them as well
     gpu.set_variant(1)
     gpu.set_screen(False)
+    gpu.set_reduction(False)
     ref_lo, ref_hi, ref_err = gpu.bound(case.box_lo, case.box_hi)
     lo = torch.tensor(case.box_lo[0], device="cuda")
     hi = torch.tensor(case.box_hi[0], device="cuda")
