@@ -396,6 +396,9 @@ def run_ragged_study(args):
     t0 = time.perf_counter()
     cases = [P.Case(n, device=0) for n in nets]
     build_s = time.perf_counter() - t0
+    if args.variant:
+        for c in cases:
+            c.set_variant(args.variant)
     los = [torch.tensor(n.box_lo, device="cuda") for n in nets]
     his = [torch.tensor(n.box_hi, device="cuda") for n in nets]
     P.bound_multi(cases, los, his)  # plan and workspaces, outside capture
@@ -431,8 +434,14 @@ def run_ragged_study(args):
     torch.cuda.synchronize()
     seq_ms = e0.elapsed_time(e1) / args.steps
     flows = sum(n.n_ctg * n.n_line * n.n_box for n in nets)
-    flop = sum(P.algorithmic_flop(n.n_ctg, n.n_line, c.info().n_active, n.n_box)
-               for n, c in zip(nets, cases))
+    # work the launch does: non-bridge lines x bus classes under the reduction
+    flop = 0.0
+    for n, c in zip(nets, cases):
+        inf = c.info()
+        red = inf.n_bridges > 0 or inf.n_bus_classes < inf.n_active
+        lines = n.n_line - inf.n_bridges if red else n.n_line
+        cols = inf.n_bus_classes if red else inf.n_active
+        flop += P.algorithmic_flop(n.n_ctg, lines, cols, n.n_box)
     sizes = {}
     for n in nets:
         sizes[n.n_bus] = sizes.get(n.n_bus, 0) + 1

@@ -106,6 +106,11 @@ struct ibp_case {
     // contingency rows [n_c][n_r_pad]
     DevBuf<int> is_bridge, cls_ptr, cls_col;
     DevBuf<float> phi_r, phi_kr;
+    // many-case launch: the non-bridge lines (list, count on the device) and
+    // their reduced rows [n_nb][n_r_pad], built on first use
+    int n_nb = -1;
+    DevBuf<int> nb_list, nb_count;
+    DevBuf<float> phi_nb;
 
     // per-call workspace (ws_gen changes whenever its buffers move)
     int cap_box = 0, ws_gen = 0;
@@ -141,7 +146,8 @@ struct ibp_case {
             obj.free(); cbus.free(); rbus.free(); cabs.free(); box_consts.free(); line_c.free();
             line_e.free(); line_R.free(); part_base.free(); part_ctg.free(); flows.free(); err.free();
             live_flag.free(); live.free(); n_live.free(); is_bridge.free(); cls_ptr.free();
-            cls_col.free(); phi_r.free(); phi_kr.free(); rcls.free(); rcls_t.free();
+            cls_col.free(); phi_r.free(); phi_kr.free(); rcls.free(); rcls_t.free(); nb_list.free();
+            nb_count.free(); phi_nb.free();
             dev_col.free(); act_count.free(); cnt.free(); act_list.free(); W.free(); dc.free(); dr.free();
             grads.free();
         }
@@ -707,10 +713,11 @@ ibp_status set_error(ibp_status s, const char *msg) {
 }  // namespace ibp
 
 // ----------------------------------------------------------------- workspace
-// fastest one-box shape measured on GB300 (16 warps, 4x4 pairs per thread,
-// 64-bus chunks, 4-bus round-up add tree)
-constexpr int kDefaultOneBoxVariant = 9;
-constexpr int kDefaultMultiBoxVariant = 20;
+// fastest shapes measured on GB300: one box, 16 warps, 4x4 pairs per thread,
+// 64-bus chunks, packed two-lane sums; many boxes, 8 warps, 4 lines x 16
+// boxes per thread, packed FMA
+constexpr int kDefaultOneBoxVariant = 12;
+constexpr int kDefaultMultiBoxVariant = 26;
 
 static const CtgVariant *pick_variant(const ibp_case *c, int n_box) {
     if (c->variant > 0) {
@@ -761,6 +768,16 @@ static ibp_status ensure_workspace(ibp_case *c, int n_box) {
     return IBP_OK;
 }
 
+// class radii of the reduction, sized like the other per-box buffers
+static ibp_status ensure_class_ws(ibp_case *c) {
+    if (c->rcls.n >= (size_t)c->cap_box * c->n_r_pad) return IBP_OK;
+    const size_t cap_pad = (size_t)(c->cap_box + kBoxTile - 1) / kBoxTile * kBoxTile;
+    CUDA_TRY(c->rcls.alloc((size_t)c->cap_box * c->n_r_pad));
+    CUDA_TRY(c->rcls_t.alloc(cap_pad * c->n_r_pad));
+    ++c->ws_gen;
+    return IBP_OK;
+}
+
 // ----------------------------------------------------------------- bound
 static ibp_status enqueue_bound(ibp_case *c, int n_box, const double *lo, const double *hi,
                                 double *olo, double *ohi, double *oerr, float *flo, float *fhi,
@@ -779,11 +796,7 @@ static ibp_status enqueue_bound(ibp_case *c, int n_box, const double *lo, const 
     const int n_box_pad = (n_box + kBoxTile - 1) / kBoxTile * kBoxTile;
     if ((!multi || screened) && !c->hat_l.p) CUDA_TRY(c->hat_l.alloc((size_t)c->n_line * c->n_a_pad));
     if (!multi && !c->hat_k.p) CUDA_TRY(c->hat_k.alloc((size_t)std::max(c->n_ctg, 1) * c->n_a_pad));
-    if (reduced && c->rcls.n < (size_t)c->cap_box * c->n_r_pad) {
-        const size_t cap_pad = (size_t)(c->cap_box + kBoxTile - 1) / kBoxTile * kBoxTile;
-        CUDA_TRY(c->rcls.alloc((size_t)c->cap_box * c->n_r_pad));
-        CUDA_TRY(c->rcls_t.alloc(cap_pad * c->n_r_pad));
-    }
+    if (reduced && (st = ensure_class_ws(c)) != IBP_OK) return st;
     CUDA_TRY(cudaMemsetAsync(c->err.p, 0, sizeof(int), s));
     if (multi) {
         CUDA_TRY(cudaMemsetAsync(c->rbus_t.p, 0, (size_t)c->n_a_pad * n_box_pad * sizeof(float), s));
@@ -865,7 +878,9 @@ static ibp_status enqueue_bound(ibp_case *c, int n_box, const double *lo, const 
     // depth-2 tree per 4 buses plus one add), level 2 over 256/CH chunks, level 3
     {
         const bool tree = !multi && v->id >= 6;
-        const long n1 = tree ? v->CH / 4 + 2 : v->CH;
+        // packed two-lane sums (12, 13): one more add to join the lanes
+        const bool packed = !multi && (v->id == 12 || v->id == 13);
+        const long n1 = tree ? v->CH / 4 + 2 + (packed ? 1 : 0) : v->CH;
         const long n2 = 256 / v->CH;
         ca.gamma = rup_gamma(n1, n2, (n_chunks + n2 - 1) / n2);
     }
@@ -1087,7 +1102,7 @@ extern "C" ibp_status ibp_bound_backward(ibp_case *c, int32_t n_box, const doubl
 // workspace generations), built and uploaded once, then reused.
 struct MultiPlan {
     std::vector<const ibp_case *> cases;
-    std::vector<int> n_box, gens;
+    std::vector<int> n_box, gens, reduced;
     int device = -1, grid = 0;
     DevBuf<MultiItem> items;
     DevBuf<int> cta_start, err;
@@ -1114,22 +1129,50 @@ static void drop_plans_of(const ibp_case *c) {
                   g_plans.end());
 }
 
-static CtgArgs multi_args(const ibp_case *c, int n_box, int BL, int BK, int CH) {
+static CtgArgs multi_args(const ibp_case *c, int n_box, int BL, int BK, int CH, bool reduced) {
     const int n_box_pad = (n_box + kBoxTile - 1) / kBoxTile * kBoxTile;
-    const int tiles_l = (c->n_line + BL - 1) / BL, tiles_k = (c->n_ctg + BK - 1) / BK;
-    const int n_chunks = (c->n_a_pad + CH - 1) / CH;
+    const int n_rows = reduced ? c->n_nb : c->n_line;
+    const int tiles_l = (n_rows + BL - 1) / BL, tiles_k = (c->n_ctg + BK - 1) / BK;
+    const int n_chunks = ((reduced ? c->n_r_pad : c->n_a_pad) + CH - 1) / CH;
     CtgArgs ca{};
     ca.n_l = c->n_line; ca.n_c = c->n_ctg; ca.n_a = c->n_a; ca.n_chunks = n_chunks; ca.n_box = n_box;
     ca.tiles_l = tiles_l; ca.n_tiles = tiles_l * tiles_k * (n_box_pad / kBoxTile);
     ca.lodf = c->lodf.p; ca.ctg_line = c->ctg_line.p;
     ca.line_c = c->line_c.p; ca.line_e = c->line_e.p; ca.line_R = c->line_R.p;
     ca.rate_up = c->rate_c_up.p; ca.rate_dn = c->rate_c_dn.p; ca.box_consts = c->box_consts.p;
-    ca.rbus_t = c->rbus_t.p; ca.n_box_pad = n_box_pad;
+    ca.rbus_t = reduced ? c->rcls_t.p : c->rbus_t.p; ca.n_box_pad = n_box_pad;
     ca.gamma = rup_gamma(CH, 256 / CH, (n_chunks + 256 / CH - 1) / (256 / CH));
     ca.flow_lo = nullptr; ca.flow_hi = nullptr; ca.partials = c->part_ctg.p; ca.err = c->err.p;
     ca.wait_ns = 2000000000ull;
     ca.warps_per_tile = 8;
+    if (reduced) {
+        ca.live = c->nb_list.p;
+        ca.n_live = c->nb_count.p;
+    }
     return ca;
+}
+
+// the many-case launch uses the static part of the network reduction: every
+// non-bridge line, with its reduced row
+static bool multi_reduced(const ibp_case *c) { return c->reduce && c->has_reduction && c->n_ctg > 0; }
+
+static ibp_status ensure_nonbridge_rows(ibp_case *c) {
+    if (c->n_nb >= 0) return IBP_OK;
+    std::vector<int> nb;
+    for (int l = 0; l < c->n_line; ++l)
+        if (!c->is_bridge_h[l]) nb.push_back(l);
+    const int n = (int)nb.size();
+    CUDA_TRY(c->nb_list.alloc(std::max(n, 1)));
+    CUDA_TRY(c->nb_count.alloc(1));
+    CUDA_TRY(c->phi_nb.alloc((size_t)std::max(n, 1) * c->n_r_pad));
+    if (n > 0) {
+        CUDA_TRY(cudaMemcpy(c->nb_list.p, nb.data(), n * sizeof(int), cudaMemcpyHostToDevice));
+        CUDA_TRY(launch_gather_rows(c->phi_r.p, c->n_r_pad, c->nb_list.p, n, c->phi_nb.p, nullptr));
+    }
+    CUDA_TRY(cudaMemcpy(c->nb_count.p, &n, sizeof(int), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaDeviceSynchronize());
+    c->n_nb = n;
+    return IBP_OK;
 }
 
 static ibp_status build_plan(ibp_case *const *cases, const int32_t *n_box, int n_case, int num_sms,
@@ -1147,14 +1190,19 @@ static ibp_status build_plan(ibp_case *const *cases, const int32_t *n_box, int n
         P->cases.push_back(c);
         P->n_box.push_back(n_box[i]);
         P->gens.push_back(c->ws_gen);
-        args[i] = multi_args(c, n_box[i], BL, BK, CH);
+        const bool red = multi_reduced(c);
+        P->reduced.push_back(red ? 1 : 0);
+        args[i] = multi_args(c, n_box[i], BL, BK, CH, red);
         const int n_box_pad = args[i].n_box_pad;
+        const int w = red ? c->n_r_pad : c->n_a_pad;
+        const float *rows = red ? c->phi_nb.p : c->phi_a.p;
+        const int n_rows = std::max(red ? c->n_nb : c->n_line, 1);
         std::string err;
-        if (!encode_map_2d(&maps[3 * i], c->phi_a.p, c->n_a_pad, c->n_line, c->n_a_pad, 32, BL, &err) ||
-            !encode_map_2d(&maps[3 * i + 1], c->phi_k.p, c->n_a_pad, std::max(c->n_ctg, 1), c->n_a_pad,
+        if (!encode_map_2d(&maps[3 * i], rows, w, n_rows, w, 32, BL, &err) ||
+            !encode_map_2d(&maps[3 * i + 1], red ? c->phi_kr.p : c->phi_k.p, w, std::max(c->n_ctg, 1), w,
                            32, BK, &err) ||
-            !encode_map_2d(&maps[3 * i + 2], c->rbus_t.p, n_box_pad, c->n_a_pad, n_box_pad, kBoxTile,
-                           32, &err, false))
+            !encode_map_2d(&maps[3 * i + 2], red ? c->rcls_t.p : c->rbus_t.p, n_box_pad, w, n_box_pad,
+                           kBoxTile, 32, &err, false))
             return fail(IBP_ECUDA, "%s", err.c_str());
         if (c->n_ctg == 0) continue;
         const int tiles_l = args[i].tiles_l, tiles_k = (c->n_ctg + BK - 1) / BK;
@@ -1210,7 +1258,8 @@ static MultiPlan *find_plan(ibp_case *const *cases, const int32_t *n_box, int n_
         if ((int)p->cases.size() != n_case) continue;
         bool same = true;
         for (int i = 0; i < n_case && same; ++i)
-            same = p->cases[i] == cases[i] && p->n_box[i] == n_box[i] && p->gens[i] == cases[i]->ws_gen;
+            same = p->cases[i] == cases[i] && p->n_box[i] == n_box[i] && p->gens[i] == cases[i]->ws_gen &&
+                   p->reduced[i] == (int)multi_reduced(cases[i]);
         if (same) return p.get();
     }
     return nullptr;
@@ -1238,8 +1287,12 @@ extern "C" ibp_status ibp_bound_multi(int32_t n_case, ibp_case *const *cases, co
     if (!guard.ok) return fail(IBP_ECUDA, "cannot select device %d", cases[0]->device);
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     ibp_status st;
-    for (int i = 0; i < n_case; ++i)
+    for (int i = 0; i < n_case; ++i) {
         if ((st = ensure_workspace(cases[i], n_box[i])) != IBP_OK) return st;
+        if (multi_reduced(cases[i]) &&
+            ((st = ensure_class_ws(cases[i])) != IBP_OK || (st = ensure_nonbridge_rows(cases[i])) != IBP_OK))
+            return st;
+    }
     MultiPlan *P = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_plan_mu);
@@ -1257,12 +1310,22 @@ extern "C" ibp_status ibp_bound_multi(int32_t n_case, ibp_case *const *cases, co
         const int n_box_pad = (nb + kBoxTile - 1) / kBoxTile * kBoxTile;
         CUDA_TRY(cudaMemsetAsync(c->err.p, 0, sizeof(int), s));
         CUDA_TRY(cudaMemsetAsync(c->rbus_t.p, 0, (size_t)c->n_a_pad * n_box_pad * sizeof(float), s));
+        const bool red = P->reduced[i] != 0;
+        if (red)
+            CUDA_TRY(cudaMemsetAsync(c->rcls_t.p, 0, (size_t)c->n_r_pad * n_box_pad * sizeof(float), s));
         BusArgs ba{};
         ba.n_a = c->n_a; ba.n_a_pad = c->n_a_pad; ba.n_dev = c->n_dev; ba.n_gen = c->n_gen; ba.n_box = nb;
         ba.act_ptr = c->act_ptr.p; ba.act_dev = c->act_dev.p; ba.box_lo = box_lo[i]; ba.box_hi = box_hi[i];
         ba.cbus = c->cbus.p; ba.rbus = c->rbus.p; ba.rbus_t = c->rbus_t.p; ba.n_box_pad = n_box_pad;
         ba.cabs = c->cabs.p; ba.box_consts = c->box_consts.p; ba.err = c->err.p;
         CUDA_TRY(launch_bus(ba, s));
+        if (red) {
+            ClsArgs ra{};
+            ra.n_box = nb; ra.n_r = c->n_r; ra.n_r_pad = c->n_r_pad; ra.n_a_pad = c->n_a_pad;
+            ra.n_box_pad = n_box_pad; ra.cls_ptr = c->cls_ptr.p; ra.cls_col = c->cls_col.p;
+            ra.rbus = c->rbus.p; ra.rcls = c->rcls.p; ra.rcls_t = c->rcls_t.p;
+            CUDA_TRY(launch_class_radius(ra, s));
+        }
         BaseArgs bb{};
         bb.n_l = c->n_line; bb.n_c = c->n_ctg; bb.n_a = c->n_a; bb.n_a_pad = c->n_a_pad; bb.n_box = nb;
         bb.phi = c->phi_a.p; bb.ctg_line = c->ctg_line.p; bb.cbus = c->cbus.p; bb.rbus = c->rbus.p;
@@ -1271,11 +1334,16 @@ extern "C" ibp_status ibp_bound_multi(int32_t n_case, ibp_case *const *cases, co
         bb.gamma_base = rup_gamma((c->n_a_pad / 4 + 31) / 32, 2, 5);
         bb.line_c = c->line_c.p; bb.line_e = c->line_e.p; bb.line_R = c->line_R.p;
         bb.partials = c->part_base.p; bb.err = c->err.p;
+        if (red) {
+            bb.is_bridge = c->is_bridge.p;
+            bb.rate_c_up = c->rate_c_up.p;
+            bb.rate_c_dn = c->rate_c_dn.p;
+        }
         CUDA_TRY(launch_base(bb, c->n_part_base, s));
     }
     // one persistent launch over the contingency tiles of every case
-    CUDA_TRY(launch_ctg_cases(P->items.p, P->cta_start.p, P->prefix.p, P->args.p, P->maps.p, P->grid,
-                              2000000000ull, P->err.p, s));
+    CUDA_TRY(launch_ctg_cases(cases[0]->variant, P->items.p, P->cta_start.p, P->prefix.p, P->args.p,
+                              P->maps.p, P->grid, 2000000000ull, P->err.p, s));
     int BL, BK, CH;
     multi_tile_shape(&BL, &BK, &CH);
     for (int i = 0; i < n_case; ++i) {
@@ -1283,7 +1351,8 @@ extern "C" ibp_status ibp_bound_multi(int32_t n_case, ibp_case *const *cases, co
         CUDA_TRY(launch_or_err(c->err.p, P->err.p, s));
         AsmArgs aa{};
         aa.n_box = n_box[i]; aa.n_dev = c->n_dev; aa.n_gen = c->n_gen;
-        aa.n_part_ctg = ((c->n_line + BL - 1) / BL) * ((c->n_ctg + BK - 1) / BK) * 8;
+        const int rows = P->reduced[i] ? c->n_nb : c->n_line;
+        aa.n_part_ctg = ((rows + BL - 1) / BL) * ((c->n_ctg + BK - 1) / BK) * 8;
         aa.n_part_base = c->n_part_base;
         aa.part_ctg = c->part_ctg.p; aa.part_base = c->part_base.p; aa.box_lo = box_lo[i]; aa.box_hi = box_hi[i];
         aa.seg_ptr = c->seg_ptr.p; aa.slope = c->slope.p; aa.bkpt = c->bkpt.p;

@@ -192,9 +192,9 @@ constexpr int kBoxTile = 16;  // boxes per work item of the multi-box kernel
 struct MultiItem {
     int case_id, l0, k0, b0, tile_lk, n_chunks;
 };
-cudaError_t launch_ctg_cases(const MultiItem *items, const int *cta_start, const uint32_t *prefix,
-                             const CtgArgs *args, const CUtensorMap *maps, int grid,
-                             unsigned long long wait_ns, int *err, cudaStream_t s);
+cudaError_t launch_ctg_cases(int variant, const MultiItem *items, const int *cta_start,
+                             const uint32_t *prefix, const CtgArgs *args, const CUtensorMap *maps,
+                             int grid, unsigned long long wait_ns, int *err, cudaStream_t s);
 void multi_tile_shape(int *BL, int *BK, int *CH);
 cudaError_t launch_assemble(const AsmArgs &a, cudaStream_t s);
 cudaError_t launch_screen(const ScreenArgs &a, int num_sms, cudaStream_t s);

@@ -164,11 +164,14 @@ __global__ void __launch_bounds__(WL * WK * 32, MINB)
             }
         }
         float acc1[ML][MK], acc2[ML][MK], acc3[S3 ? 1 : ML][S3 ? 1 : MK];
+        // BODY 2: level-1 sums in two lanes (even / odd buses), packed adds
+        float2 acc1p[BODY == 2 ? ML : 1][BODY == 2 ? MK : 1];
 #pragma unroll
         for (int i = 0; i < ML; ++i)
 #pragma unroll
             for (int j = 0; j < MK; ++j) {
                 acc1[i][j] = acc2[i][j] = 0.0f;
+                if constexpr (BODY == 2) acc1p[i][j] = make_float2(0.0f, 0.0f);
                 if constexpr (S3) acc3s[(i * MK + j) * S::kThreads] = 0.0f;
                 else acc3[i][j] = 0.0f;
             }
@@ -188,7 +191,7 @@ __global__ void __launch_bounds__(WL * WK * 32, MINB)
             }
             const float *sL = ring + (size_t)s * S::kStageFloats;
             const float *sK = sL + BL * CH;
-#pragma unroll
+#pragma unroll (BODY == 2 ? 8 : CH / 4)
             for (int q = 0; q < CH / 4; ++q) {
                 // 16-byte group q of the chunk: sub-block q / 8, swizzled slot (q % 8) ^ (row & 7)
                 const int sub = q >> 3, qq = q & 7;
@@ -214,6 +217,16 @@ __global__ void __launch_bounds__(WL * WK * 32, MINB)
                             acc1[i][j] = __fadd_ru(acc1[i][j], fabsf(h));
                             h = __fmaf_rn(L, fk[j].w, fl.w);
                             acc1[i][j] = __fadd_ru(acc1[i][j], fabsf(h));
+                        } else if constexpr (BODY == 2) {
+                            // two buses per packed FMA / add: h = RN(L hat_k + hat_l)
+                            // per lane, |h| of buses (0,2) and (1,3) summed RU per
+                            // lane, then accumulated per lane
+                            const float2 L2 = make_float2(L, L);
+                            float2 h01 = __ffma2_rn(L2, make_float2(fk[j].x, fk[j].y), make_float2(fl.x, fl.y));
+                            float2 h23 = __ffma2_rn(L2, make_float2(fk[j].z, fk[j].w), make_float2(fl.z, fl.w));
+                            h01 = make_float2(fabsf(h01.x), fabsf(h01.y));
+                            h23 = make_float2(fabsf(h23.x), fabsf(h23.y));
+                            acc1p[i][j] = __fadd2_ru(acc1p[i][j], __fadd2_ru(h01, h23));
                         } else {
                             // four buses summed as a round-up tree, then accumulated
                             const float h0 = __fmaf_rn(L, fk[j].x, fl.x);
@@ -244,8 +257,13 @@ __global__ void __launch_bounds__(WL * WK * 32, MINB)
             for (int i = 0; i < ML; ++i)
 #pragma unroll
                 for (int j = 0; j < MK; ++j) {
-                    acc2[i][j] = __fadd_ru(acc2[i][j], acc1[i][j]);
-                    acc1[i][j] = 0.0f;
+                    if constexpr (BODY == 2) {
+                        acc2[i][j] = __fadd_ru(acc2[i][j], __fadd_ru(acc1p[i][j].x, acc1p[i][j].y));
+                        acc1p[i][j] = make_float2(0.0f, 0.0f);
+                    } else {
+                        acc2[i][j] = __fadd_ru(acc2[i][j], acc1[i][j]);
+                        acc1[i][j] = 0.0f;
+                    }
                 }
             if ((ch & (kFold3 - 1)) == kFold3 - 1) {
 #pragma unroll
@@ -303,13 +321,16 @@ __global__ void __launch_bounds__(WL * WK * 32, MINB)
 // ---------------------------------------------------------------------------
 constexpr int kMB = 16;  // boxes per work item
 
-// BH = box halves: 1 -> 8 warps, each thread 16 boxes; 2 -> 16 warps, the
-// second 8 warps take boxes 8..15 of the item (h is formed by both halves).
-template <int ST, int BH = 1>
+// BH = box halves: 1 -> each thread 16 boxes; 2 -> the second set of warps
+// takes boxes 8..15 of the item (h is formed by both halves).  ML = lines per
+// thread: 4 -> 8 warps per half, 2 -> 16 warps per half (64 lines per item).
+template <int ST, int BH = 1, int ML_ = 4>
 struct MultiShape {
-    static constexpr int kWarps = 8 * BH, kThreads = 256 * BH;
+    static constexpr int ML = ML_;
+    static constexpr int TL = 64 / ML, TK = 16;
+    static constexpr int kWarpsHalf = TL / 4 * 2;  // warps of one box half
+    static constexpr int kWarps = kWarpsHalf * BH, kThreads = 32 * kWarps;
     static constexpr int kMBT = kMB / BH;  // boxes per thread
-    static constexpr int TL = 16, TK = 16, ML = 4;
     static constexpr int BL = TL * ML, BK = TK;
     static constexpr int CH = 32;
     static constexpr int kStageFloats = (BL + BK) * CH + CH * kMB;
@@ -372,10 +393,10 @@ struct CasesPlan {
     }
 };
 
-template <int ST, int BH, class Plan>
+template <int ST, int BH, int ML, class Plan>
 __device__ __forceinline__ void issue_multi(const Plan &P, float *ring, uint64_t *full,
                                             int *last_issued, uint32_t c, int i, int ch) {
-    using S = MultiShape<ST, BH>;
+    using S = MultiShape<ST, BH, ML>;
     constexpr uint32_t kBytes = (uint32_t)S::kStageFloats * sizeof(float);
     const int s = (int)(c % ST);
     const MultiItemView v = P.item(i);
@@ -389,9 +410,10 @@ __device__ __forceinline__ void issue_multi(const Plan &P, float *ring, uint64_t
     tma_load_2d(smem_addr(sR), v.mR, smem_addr(&full[s]), v.b0, ch * S::CH);
 }
 
-template <int ST, int BH, class Plan>
+// PK: accumulate box pairs with the packed two-lane FMA (same rounding per lane)
+template <int ST, int BH, int ML_, class Plan, bool PK = false>
 __device__ __forceinline__ void multi_body(const Plan &P, unsigned long long wait_ns, int *err) {
-    using S = MultiShape<ST, BH>;
+    using S = MultiShape<ST, BH, ML_>;
     constexpr int CH = S::CH, ML = S::ML, TL = S::TL, BL = S::BL, kMBT = S::kMBT;
     extern __shared__ unsigned char smem_raw[];
     float *ring = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -428,13 +450,13 @@ __device__ __forceinline__ void multi_body(const Plan &P, unsigned long long wai
                 ch -= P.item(i).n_chunks;
                 ++i;
             }
-            issue_multi<ST, BH>(P, ring, full, last_issued, c, i, ch);
+            issue_multi<ST, BH, ML_>(P, ring, full, last_issued, c, i, ch);
             ++ch;
         }
     }
 
     // box half of this warp (BH = 2) and its position inside the half
-    const int half = warp >> 3, wq = warp & 7;
+    const int half = warp / S::kWarpsHalf, wq = warp % S::kWarpsHalf;
     const int tl = (wq >> 1) * 4 + (lane >> 3);
     const int tk = (wq & 1) * 8 + (lane & 7);
     const int xl = tl & 7, xk = tk & 7;
@@ -510,8 +532,19 @@ __device__ __forceinline__ void multi_body(const Plan &P, unsigned long long wai
                     for (int i = 0; i < ML; ++i) {
                         const float flt = t == 0 ? fl[i].x : t == 1 ? fl[i].y : t == 2 ? fl[i].z : fl[i].w;
                         const float ah = fabsf(__fmaf_rn(Lr[i], fkt, flt));
+                        if constexpr (PK) {
+                            const float2 ah2 = make_float2(ah, ah);
 #pragma unroll
-                        for (int j = 0; j < kMBT; ++j) acc1[i][j] = __fmaf_ru(ah, r[j], acc1[i][j]);
+                            for (int j = 0; j < kMBT; j += 2) {
+                                const float2 v = __ffma2_ru(ah2, make_float2(r[j], r[j + 1]),
+                                                            make_float2(acc1[i][j], acc1[i][j + 1]));
+                                acc1[i][j] = v.x;
+                                acc1[i][j + 1] = v.y;
+                            }
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < kMBT; ++j) acc1[i][j] = __fmaf_ru(ah, r[j], acc1[i][j]);
+                        }
                     }
                 }
             }
@@ -529,7 +562,7 @@ __device__ __forceinline__ void multi_body(const Plan &P, unsigned long long wai
                             ++i2;
                         }
                         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                        issue_multi<ST, BH>(P, ring, full, last_issued, nxt, i2, ch2);
+                        issue_multi<ST, BH, ML_>(P, ring, full, last_issued, nxt, i2, ch2);
                     }
                 }
             }
@@ -571,8 +604,8 @@ __device__ __forceinline__ void multi_body(const Plan &P, unsigned long long wai
                     pair_epilogue(a, box, l, k, Lr[i], A, slo, shi, whi, wlo);
                 }
             }
-            // partial rows per item: 8 (the warp's place in its half; each
-            // box belongs to exactly one half)
+            // partial rows per item: kWarpsHalf (the warp's place in its
+            // half; each box belongs to exactly one half)
             write_warp_partials(a, tlk, wq, box, slo, shi, whi, wlo);
         }
     }
@@ -585,11 +618,11 @@ __device__ __forceinline__ void multi_body(const Plan &P, unsigned long long wai
     }
 }
 
-template <int ST, int BH>
-__global__ void __launch_bounds__(256 * BH, 1)
+template <int ST, int BH, int ML, bool PK>
+__global__ void __launch_bounds__(MultiShape<ST, BH, ML>::kThreads, 1)
     k_ctg_multi(const __grid_constant__ CUtensorMap mL, const __grid_constant__ CUtensorMap mK,
                 const __grid_constant__ CUtensorMap mR, const CtgArgs a) {
-    using S = MultiShape<ST, BH>;
+    using S = MultiShape<ST, BH, ML>;
     if (threadIdx.x == 0) {
         prefetch_tensormap(&mL);
         prefetch_tensormap(&mK);
@@ -600,27 +633,27 @@ __global__ void __launch_bounds__(256 * BH, 1)
     const int tiles_l = a.n_live ? (n_ll + S::BL - 1) / S::BL : a.tiles_l;
     const int n_tiles = a.n_live ? tiles_l * tiles_k * box_tiles : a.n_tiles;
     const SinglePlan P{&a, &mL, &mK, &mR, tiles_l, tiles_k, box_tiles, S::BL, S::BK, n_tiles};
-    multi_body<ST, BH>(P, a.wait_ns, a.err);
+    multi_body<ST, BH, ML, SinglePlan, PK>(P, a.wait_ns, a.err);
 }
 
 // Many cases in one persistent launch: CTA b walks items [start[b], start[b+1])
 // of the host-built table (longest items first, dealt round-robin).
-template <int ST, int BH>
-__global__ void __launch_bounds__(256 * BH, 1)
+template <int ST, int BH, bool PK>
+__global__ void __launch_bounds__(MultiShape<ST, BH>::kThreads, 1)
     k_ctg_cases(const MultiItem *__restrict__ items, const int *__restrict__ cta_start,
                 const uint32_t *__restrict__ prefix, const CtgArgs *__restrict__ args,
                 const CUtensorMap *__restrict__ maps, unsigned long long wait_ns, int *err) {
     const int s0 = cta_start[blockIdx.x], s1 = cta_start[blockIdx.x + 1];
     const CasesPlan P{items + s0, prefix + s0 + blockIdx.x, s1 - s0, args, maps};
-    multi_body<ST, BH>(P, wait_ns, err);
+    multi_body<ST, BH, 4, CasesPlan, PK>(P, wait_ns, err);
 }
 
-template <int ST, int BH>
+template <int ST, int BH, int ML = 4, bool PK = false>
 static cudaError_t launch_multi(const CUtensorMap &mL, const CUtensorMap &mK,
                                 const CUtensorMap &mR, const CtgArgs &a, int grid,
                                 cudaStream_t s) {
-    using S = MultiShape<ST, BH>;
-    auto kern = k_ctg_multi<ST, BH>;
+    using S = MultiShape<ST, BH, ML>;
+    auto kern = k_ctg_multi<ST, BH, ML, PK>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)S::kBytes);
     if (e != cudaSuccess) return e;
@@ -637,24 +670,41 @@ cudaError_t launch_ctg_multi(const CtgVariant &v, const CUtensorMap &mL, const C
     case 21: return launch_multi<6, 1>(mL, mK, mR, a, grid, s);
     case 22: return launch_multi<4, 2>(mL, mK, mR, a, grid, s);
     case 23: return launch_multi<6, 2>(mL, mK, mR, a, grid, s);
+    case 24: return launch_multi<4, 1, 2>(mL, mK, mR, a, grid, s);
+    case 25: return launch_multi<6, 1, 2>(mL, mK, mR, a, grid, s);
+    case 26: return launch_multi<4, 1, 4, true>(mL, mK, mR, a, grid, s);
+    case 27: return launch_multi<4, 2, 4, true>(mL, mK, mR, a, grid, s);
     default: return cudaErrorInvalidValue;
     }
 }
 
-// box halves of the many-case launch (same work items either way)
-constexpr int kCasesBH = 2;
-
-cudaError_t launch_ctg_cases(const MultiItem *items, const int *cta_start, const uint32_t *prefix,
-                             const CtgArgs *args, const CUtensorMap *maps, int grid,
-                             unsigned long long wait_ns, int *err, cudaStream_t s) {
-    using S = MultiShape<4, kCasesBH>;
-    if (grid <= 0) return cudaSuccess;
-    auto kern = k_ctg_cases<4, kCasesBH>;
+template <int BH, bool PK>
+static cudaError_t launch_cases(const MultiItem *items, const int *cta_start, const uint32_t *prefix,
+                                const CtgArgs *args, const CUtensorMap *maps, int grid,
+                                unsigned long long wait_ns, int *err, cudaStream_t s) {
+    using S = MultiShape<4, BH>;
+    auto kern = k_ctg_cases<4, BH, PK>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)S::kBytes);
     if (e != cudaSuccess) return e;
     kern<<<grid, S::kThreads, S::kBytes, s>>>(items, cta_start, prefix, args, maps, wait_ns, err);
     return cudaGetLastError();
+}
+
+// The many-case launch runs the 4-stage body of multi-box variant `variant`
+// (20/21: 8 warps, 22/23: box halves, 27: box halves and packed FMA; 26 and
+// any other value: the default, 8 warps with packed FMA).  All write 8
+// partial rows per work item.
+cudaError_t launch_ctg_cases(int variant, const MultiItem *items, const int *cta_start,
+                             const uint32_t *prefix, const CtgArgs *args, const CUtensorMap *maps,
+                             int grid, unsigned long long wait_ns, int *err, cudaStream_t s) {
+    if (grid <= 0) return cudaSuccess;
+    switch (variant) {
+    case 20: case 21: return launch_cases<1, false>(items, cta_start, prefix, args, maps, grid, wait_ns, err, s);
+    case 22: case 23: return launch_cases<2, false>(items, cta_start, prefix, args, maps, grid, wait_ns, err, s);
+    case 27: return launch_cases<2, true>(items, cta_start, prefix, args, maps, grid, wait_ns, err, s);
+    default: return launch_cases<1, true>(items, cta_start, prefix, args, maps, grid, wait_ns, err, s);
+    }
 }
 
 void multi_tile_shape(int *BL, int *BK, int *CH) {
@@ -677,10 +727,16 @@ static const CtgVariant kVariants[] = {
     {9, 0, 128, 64, 64, 3, 1, "16 warps, 4x4/thread, 64-bus chunks, 3 stages, 4-bus add tree"},
     {10, 0, 64, 64, 32, 4, 1, "2 CTAs/SM x 8 warps, 4x4/thread, 32-bus chunks, 4 stages, tree"},
     {11, 0, 64, 64, 64, 2, 1, "2 CTAs/SM x 8 warps, 4x4/thread, 64-bus chunks, 2 stages, tree"},
+    {12, 0, 128, 64, 64, 3, 1, "16 warps, 4x4/thread, 64-bus chunks, 3 stages, packed two-lane sums"},
+    {13, 0, 128, 64, 32, 4, 1, "16 warps, 4x4/thread, 32-bus chunks, 4 stages, packed two-lane sums"},
     {20, 1, 64, 16, 32, 4, 16, "multi-box 64x16x16, 8 warps, 4 lines x 16 boxes/thread, 4 stages"},
     {21, 1, 64, 16, 32, 6, 16, "multi-box 64x16x16, 8 warps, 4 lines x 16 boxes/thread, 6 stages"},
     {22, 1, 64, 16, 32, 4, 8, "multi-box 64x16x16, 16 warps, 4 lines x 8 boxes/thread, 4 stages"},
     {23, 1, 64, 16, 32, 6, 8, "multi-box 64x16x16, 16 warps, 4 lines x 8 boxes/thread, 6 stages"},
+    {24, 1, 64, 16, 32, 4, 16, "multi-box 64x16x16, 16 warps, 2 lines x 16 boxes/thread, 4 stages"},
+    {25, 1, 64, 16, 32, 6, 16, "multi-box 64x16x16, 16 warps, 2 lines x 16 boxes/thread, 6 stages"},
+    {26, 1, 64, 16, 32, 4, 16, "multi-box 64x16x16, 8 warps, 4 lines x 16 boxes/thread, packed FMA"},
+    {27, 1, 64, 16, 32, 4, 8, "multi-box 64x16x16, 16 warps, 4 lines x 8 boxes/thread, packed FMA"},
 };
 
 const CtgVariant *ctg_variants(int *count) {
@@ -722,7 +778,13 @@ static cudaError_t launch_one(const CUtensorMap &mL, const CUtensorMap &mK, cons
     return cudaGetLastError();
 }
 
-int ctg_warps(const CtgVariant &v) { return (v.id == 3 || v.id == 8 || v.id == 9) ? 16 : 8; }
+// partial-sum rows written per tile (per work item for the multi-box kernels)
+int ctg_warps(const CtgVariant &v) {
+    switch (v.id) {
+    case 3: case 8: case 9: case 12: case 13: case 24: case 25: return 16;
+    default: return 8;
+    }
+}
 
 
 cudaError_t launch_ctg(const CtgVariant &v, const CUtensorMap &mL, const CUtensorMap &mK,
@@ -738,6 +800,8 @@ cudaError_t launch_ctg(const CtgVariant &v, const CUtensorMap &mL, const CUtenso
     case 9: return launch_one<8, 2, 4, 4, 3, true, 64, 1>(mL, mK, a, grid, s);
     case 10: return launch_one<4, 2, 4, 4, 4, true, 32, 1, 2>(mL, mK, a, grid, s);
     case 11: return launch_one<4, 2, 4, 4, 2, true, 64, 1, 2>(mL, mK, a, grid, s);
+    case 12: return launch_one<8, 2, 4, 4, 3, true, 64, 2>(mL, mK, a, grid, s);
+    case 13: return launch_one<8, 2, 4, 4, 4, true, 32, 2>(mL, mK, a, grid, s);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -29,14 +29,12 @@ def test_multi_matches_per_case_and_oracle(env):
     torch.cuda.synchronize()
     for i, (n, c) in enumerate(zip(nets, cases)):
         c.sync()
-        # the many-case launch neither screens lines nor reduces the network:
-        # the per-case call without both has the same work items, so only the
-        # FP64 reduction order differs
+        # the many-case launch reduces the network but does not screen lines:
+        # the per-case call without the screen has the same work items, so only
+        # the FP64 reduction order differs
         c.set_screen(False)
-        c.set_reduction(False)
         lo1, hi1, e1 = c.bound(n.box_lo, n.box_hi)
         c.set_screen(True)
-        c.set_reduction(True)
         lo, hi, err = (t.cpu().numpy() for t in outs[i])
         np.testing.assert_allclose(hi, hi1, rtol=1e-12, atol=0)
         np.testing.assert_allclose(lo, lo1, rtol=1e-12, atol=0)
@@ -49,6 +47,27 @@ def test_multi_matches_per_case_and_oracle(env):
             scale = np.abs(ref.terms["costs"]).sum(axis=1)
             assert np.all(hi >= ref.hi - 1e-9 * scale) and np.all(lo <= ref.lo + 1e-9 * scale)
             assert np.all(np.abs(hi - ref.hi) <= 1e-5 * np.abs(ref.hi) + 1e-9 * scale)
+
+
+def test_multi_without_reduction(env):
+    """With the reduction off, the many-case launch streams every line and
+    active bus; it agrees with the per-case plain call the same way."""
+    P, torch, nets, cases, los, his = env
+    for c in cases:
+        c.set_reduction(False)
+    try:
+        outs = P.bound_multi(cases, los, his)
+        torch.cuda.synchronize()
+        for i, (n, c) in enumerate(zip(nets, cases)):
+            c.set_screen(False)
+            lo1, hi1, e1 = c.bound(n.box_lo, n.box_hi)
+            c.set_screen(True)
+            lo, hi, err = (t.cpu().numpy() for t in outs[i])
+            np.testing.assert_allclose(hi, hi1, rtol=1e-12, atol=0)
+            np.testing.assert_allclose(lo, lo1, rtol=1e-12, atol=0)
+    finally:
+        for c in cases:
+            c.set_reduction(True)
 
 
 def test_multi_in_cuda_graph(env):
@@ -73,10 +92,8 @@ def test_multi_in_cuda_graph(env):
     his[0].copy_(his[0] - 0.1 * (his[0] - los[0]))
     g.replay()
     torch.cuda.synchronize()
-    # (per-case call on the many-case launch's path: no screen, no reduction)
+    # (per-case call on the many-case launch's path: no screen)
     cases[0].set_screen(False)
-    cases[0].set_reduction(False)
     lo1, hi1, _ = cases[0].bound(nets[0].box_lo, his[0].cpu().numpy())
     cases[0].set_screen(True)
-    cases[0].set_reduction(True)
     np.testing.assert_allclose(outs[0][1].cpu().numpy(), hi1, rtol=1e-12)
