@@ -117,7 +117,7 @@ struct ibp_case {
     DevBuf<double> box_lo, box_hi, obj;
     DevBuf<double> cbus;
     DevBuf<float> rbus, cabs, box_consts, line_c, line_e, line_R, rbus_t;
-    DevBuf<double> part_base, part_ctg;
+    DevBuf<double> part_base, part_ctg, part_stage;
     DevBuf<float> flows;
     DevBuf<int> err;
     DevBuf<int> live_flag, live, n_live;  // line screen
@@ -144,7 +144,7 @@ struct ibp_case {
             slope.free(); bkpt.free(); hat_l.free(); hat_k.free(); phi_k.free(); rbus_t.free();
             box_lo.free(); box_hi.free();
             obj.free(); cbus.free(); rbus.free(); cabs.free(); box_consts.free(); line_c.free();
-            line_e.free(); line_R.free(); part_base.free(); part_ctg.free(); flows.free(); err.free();
+            line_e.free(); line_R.free(); part_base.free(); part_ctg.free(); part_stage.free(); flows.free(); err.free();
             live_flag.free(); live.free(); n_live.free(); is_bridge.free(); cls_ptr.free();
             cls_col.free(); phi_r.free(); phi_kr.free(); rcls.free(); rcls_t.free(); nb_list.free();
             nb_count.free(); phi_nb.free();
@@ -740,6 +740,9 @@ static size_t max_part_rows(const ibp_case *c) {
     return best;
 }
 
+// blocks per box of the first stage of the contingency partial sums
+constexpr int kPartStages = 64;
+
 static ibp_status ensure_workspace(ibp_case *c, int n_box) {
     if (n_box <= c->cap_box) return IBP_OK;
     const int cap = std::max(n_box, 1);
@@ -756,6 +759,7 @@ static ibp_status ensure_workspace(ibp_case *c, int n_box) {
     CUDA_TRY(c->line_R.alloc((size_t)cap * c->n_line));
     CUDA_TRY(c->part_base.alloc((size_t)c->n_part_base * cap * kPartVals));
     CUDA_TRY(c->part_ctg.alloc(max_part_rows(c) * cap * kPartVals));
+    CUDA_TRY(c->part_stage.alloc((size_t)kPartStages * cap * kPartVals));
     const int cap_pad = (cap + kBoxTile - 1) / kBoxTile * kBoxTile;
     CUDA_TRY(c->rbus_t.alloc(na * cap_pad));
     if (!c->live.p) {
@@ -921,6 +925,7 @@ static ibp_status enqueue_bound(ibp_case *c, int n_box, const double *lo, const 
     AsmArgs aa{};
     aa.n_box = n_box; aa.n_dev = c->n_dev; aa.n_gen = c->n_gen;
     aa.n_part_ctg = tiles_l * tiles_k * ca.warps_per_tile; aa.n_part_base = c->n_part_base;
+    aa.part_stage = c->part_stage.p; aa.n_stage = kPartStages;
     aa.part_ctg = c->part_ctg.p; aa.part_base = c->part_base.p; aa.box_lo = lo; aa.box_hi = hi;
     aa.seg_ptr = c->seg_ptr.p; aa.slope = c->slope.p; aa.bkpt = c->bkpt.p;
     aa.zeta_inj = c->zeta_inj; aa.zeta_f = c->zeta_f;
@@ -1353,6 +1358,7 @@ extern "C" ibp_status ibp_bound_multi(int32_t n_case, ibp_case *const *cases, co
         aa.n_box = n_box[i]; aa.n_dev = c->n_dev; aa.n_gen = c->n_gen;
         const int rows = P->reduced[i] ? c->n_nb : c->n_line;
         aa.n_part_ctg = ((rows + BL - 1) / BL) * ((c->n_ctg + BK - 1) / BK) * 8;
+        aa.part_stage = c->part_stage.p; aa.n_stage = kPartStages;
         aa.n_part_base = c->n_part_base;
         aa.part_ctg = c->part_ctg.p; aa.part_base = c->part_base.p; aa.box_lo = box_lo[i]; aa.box_hi = box_hi[i];
         aa.seg_ptr = c->seg_ptr.p; aa.slope = c->slope.p; aa.bkpt = c->bkpt.p;

@@ -155,6 +155,10 @@ struct AsmArgs {
     // tiles x tiles_k x rows_per_tile rows (n_part_ctg is ignored)
     const int *n_live;
     int live_BL, live_tiles_k, live_rows_per_tile;
+    // two-stage reduction of the contingency partials (null: one block per
+    // box reads them all): stage 1 writes [n_box][n_stage][kPartVals]
+    double *part_stage;
+    int n_stage;
     const double *part_ctg;   // [n_part_ctg][n_box][kPartVals]
     const double *part_base;  // [n_part_base][n_box][kPartVals]
     const double *box_lo, *box_hi;

@@ -309,6 +309,55 @@ __device__ __forceinline__ void block_sum(double *v, int n, bool *up, double *sh
     __syncthreads();
 }
 
+__device__ __forceinline__ int ctg_partial_rows(const AsmArgs &a) {
+    if (a.n_live)
+        return (*a.n_live + a.live_BL - 1) / a.live_BL * a.live_tiles_k * a.live_rows_per_tile;
+    return a.n_part_ctg;
+}
+
+// Stage 1 of the contingency partial sums: block (g, box) sums the rows
+// g*128 + t + k*(n_stage*128) of its box (directed FP64), then reduces its
+// 128 threads in a fixed tree; the result does not depend on timing.
+__global__ void __launch_bounds__(128) k_partials(AsmArgs a) {
+    const int g = blockIdx.x, j = blockIdx.y;
+    const int n = ctg_partial_rows(a);
+    double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+    for (int p = g * 128 + threadIdx.x; p < n; p += a.n_stage * 128) {
+        const double4 q = *reinterpret_cast<const double4 *>(a.part_ctg + ((size_t)p * a.n_box + j) * kPartVals);
+        v0 = __dadd_rd(v0, q.x);
+        v1 = __dadd_ru(v1, q.y);
+        v2 = __dadd_ru(v2, q.z);
+        v3 = __dadd_ru(v3, q.w);
+    }
+    v0 = warp_sum_rd(v0);
+    v1 = warp_sum_ru(v1);
+    v2 = warp_sum_ru(v2);
+    v3 = warp_sum_ru(v3);
+    __shared__ double sh[4][4];
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        sh[w][0] = v0;
+        sh[w][1] = v1;
+        sh[w][2] = v2;
+        sh[w][3] = v3;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double r0 = 0.0, r1 = 0.0, r2 = 0.0, r3 = 0.0;
+        for (int i = 0; i < 4; ++i) {
+            r0 = __dadd_rd(r0, sh[i][0]);
+            r1 = __dadd_ru(r1, sh[i][1]);
+            r2 = __dadd_ru(r2, sh[i][2]);
+            r3 = __dadd_ru(r3, sh[i][3]);
+        }
+        double *o = a.part_stage + ((size_t)j * a.n_stage + g) * kPartVals;
+        o[0] = r0;
+        o[1] = r1;
+        o[2] = r2;
+        o[3] = r3;
+    }
+}
+
 __global__ void __launch_bounds__(256) k_assemble(AsmArgs a) {
     const int j = blockIdx.x;
     // 0 Sfc_lo(rd) 1 Sfc_hi(ru) 2 Wfc_hi(ru) 3 Wfc_lo(ru) 4 Sfb_lo 5 Sfb_hi 6 Wfb_hi 7 Wfb_lo
@@ -319,15 +368,23 @@ __global__ void __launch_bounds__(256) k_assemble(AsmArgs a) {
     bool up[N] = {false, true, true, true, false, true, true, true, false, true, false, true,
                   true, true, false, true, false, true};
     for (int i = 0; i < N; ++i) v[i] = 0.0;
-    int n_part_ctg = a.n_part_ctg;
-    if (a.n_live)
-        n_part_ctg = (*a.n_live + a.live_BL - 1) / a.live_BL * a.live_tiles_k * a.live_rows_per_tile;
-    for (int p = threadIdx.x; p < n_part_ctg; p += blockDim.x) {
-        const double *q = a.part_ctg + ((size_t)p * a.n_box + j) * kPartVals;
-        v[0] = __dadd_rd(v[0], q[0]);
-        v[1] = __dadd_ru(v[1], q[1]);
-        v[2] = __dadd_ru(v[2], q[2]);
-        v[3] = __dadd_ru(v[3], q[3]);
+    if (a.part_stage) {
+        for (int p = threadIdx.x; p < a.n_stage; p += blockDim.x) {
+            const double *q = a.part_stage + ((size_t)j * a.n_stage + p) * kPartVals;
+            v[0] = __dadd_rd(v[0], q[0]);
+            v[1] = __dadd_ru(v[1], q[1]);
+            v[2] = __dadd_ru(v[2], q[2]);
+            v[3] = __dadd_ru(v[3], q[3]);
+        }
+    } else {
+        const int n_part_ctg = ctg_partial_rows(a);
+        for (int p = threadIdx.x; p < n_part_ctg; p += blockDim.x) {
+            const double *q = a.part_ctg + ((size_t)p * a.n_box + j) * kPartVals;
+            v[0] = __dadd_rd(v[0], q[0]);
+            v[1] = __dadd_ru(v[1], q[1]);
+            v[2] = __dadd_ru(v[2], q[2]);
+            v[3] = __dadd_ru(v[3], q[3]);
+        }
     }
     for (int p = threadIdx.x; p < a.n_part_base; p += blockDim.x) {
         const double *q = a.part_base + ((size_t)p * a.n_box + j) * kPartVals;
@@ -409,6 +466,11 @@ __global__ void __launch_bounds__(256) k_assemble(AsmArgs a) {
 }
 
 cudaError_t launch_assemble(const AsmArgs &a, cudaStream_t s) {
+    if (a.part_stage) {
+        k_partials<<<dim3(a.n_stage, a.n_box), 128, 0, s>>>(a);
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
     k_assemble<<<a.n_box, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
