@@ -7,11 +7,15 @@ may still hold the maximiser:
 
 * UB = max over leaves of obj_hi is a certified upper bound of max f over the
   root box (leaves dropped below hold max f <= their obj_hi < LB <= max f);
-* LB = max over candidate points x of obj_lo of the zero-width box at x, a
-  certified lower bound of f(x) <= max f.  Each leaf carries one candidate
-  (its centre at first); every round moves it by a projected sign-gradient
-  step inside the leaf, with the gradient of f at x taken from the adjoint of
-  the zero-width box (f is concave, so the ascent heads for the maximiser);
+* LB = max over evaluated points y of obj_lo of the zero-width box at y, a
+  certified lower bound of f(y) <= max f.  Each leaf carries an accepted
+  point x (its centre at first), the certified value at x and a step s in
+  (0, 1].  Every round evaluates the proposal y made in the round before; y
+  replaces x when its value is higher (s grows by 1.5, else s halves).  The
+  next proposal is a conditional-gradient step inside the leaf: with g the
+  gradient of f at x (the adjoint of the zero-width box), the leaf vertex v
+  that maximises g.v, and y = x + s (v - x).  f is concave, so the accepted
+  points climb;
 * each round bounds every leaf and its centre, takes the adjoint of obj_hi,
   drops leaves with obj_hi < LB, and splits up to ``split_per_round`` leaves
   with the largest obj_hi at the midpoint of the coordinate with the largest
@@ -55,8 +59,11 @@ class Bisection:
         self.max_leaves = int(max_leaves)
         self.split_per_round = int(split_per_round or max(1, self.max_leaves // 16))
         self.batched = bool(batched)
-        self.x = 0.5 * (self.lo + self.hi)  # candidate point per leaf
-        self.step_frac = 0.25               # ascent step, fraction of the leaf width
+        n = self.lo.shape[0]
+        self.x = 0.5 * (self.lo + self.hi)  # accepted point per leaf
+        self.fx = torch.full((n,), -float("inf"), dtype=torch.float64, device=self.device)
+        self.y = self.x.clone()             # proposal, evaluated in the next round
+        self.s = torch.full((n,), 0.5, dtype=torch.float64, device=self.device)
         self.ub = float("inf")
         self.lb = -float("inf")
         self.round = 0
@@ -92,24 +99,25 @@ class Bisection:
         torch.cuda.synchronize(self.device)
         t0 = time.perf_counter()
         n = self.lo.shape[0]
-        both_lo = torch.cat([self.lo, self.x])
-        both_hi = torch.cat([self.hi, self.x])
+        both_lo = torch.cat([self.lo, self.y])
+        both_hi = torch.cat([self.hi, self.y])
         obj_lo, obj_hi = self._bound(both_lo, both_hi)
         leaf_hi = obj_hi[:n]
-        point_lo = obj_lo[n:]
-        self.lb = max(self.lb, float(point_lo.max()))
-        # projected sign-gradient ascent of every candidate inside its leaf
+        fy = obj_lo[n:]
+        self.lb = max(self.lb, float(fy.max()))
+        # accept the proposals that improved their leaf's point
+        better = fy > self.fx
+        self.x = torch.where(better[:, None], self.y, self.x)
+        self.fx = torch.where(better, fy, self.fx)
+        self.s = torch.where(better, torch.clamp(1.5 * self.s, max=1.0), 0.5 * self.s)
+        # next proposals: conditional-gradient step towards the best vertex
         gxl, gxh = self._grad(self.x, self.x)
-        gx = gxl + gxh
-        # components at rounding-noise level count as zero (sign would amplify them)
-        gmax = gx.abs().amax(dim=1, keepdim=True)
-        gx = torch.where(gx.abs() > 1e-9 * gmax, gx, torch.zeros_like(gx))
-        width = self.hi - self.lo
-        self.x = torch.minimum(torch.maximum(self.x + self.step_frac * width * torch.sign(gx), self.lo),
-                               self.hi)
-        self.step_frac *= 0.8
+        g = gxl + gxh
+        v = torch.where(g > 0, self.hi, torch.where(g < 0, self.lo, self.x))
+        self.y = self.x + self.s[:, None] * (v - self.x)
         keep = leaf_hi >= self.lb
-        lo, hi, leaf_hi, x = self.lo[keep], self.hi[keep], leaf_hi[keep], self.x[keep]
+        lo, hi, leaf_hi = self.lo[keep], self.hi[keep], leaf_hi[keep]
+        x, fx, y, sv = self.x[keep], self.fx[keep], self.y[keep], self.s[keep]
         self.ub = min(self.ub, float(leaf_hi.max()))
         # split the leaves with the largest upper bound
         room = max(0, self.max_leaves - lo.shape[0])
@@ -131,11 +139,22 @@ class Bisection:
             b_lo[rows, dim] = m
             self.lo = torch.cat([lo[rest], a_lo, b_lo])
             self.hi = torch.cat([hi[rest], a_hi, b_hi])
-            xs = x[sel]
-            self.x = torch.cat([x[rest], torch.minimum(torch.maximum(xs, a_lo), a_hi),
-                                torch.minimum(torch.maximum(xs, b_lo), b_hi)])
+
+            def clamp(v, l, h):
+                return torch.minimum(torch.maximum(v, l), h)
+
+            xs, ys, fs, ss = x[sel], y[sel], fx[sel], sv[sel]
+            xa, xb = clamp(xs, a_lo, a_hi), clamp(xs, b_lo, b_hi)
+            # the child that does not hold x gets the projection, not yet evaluated
+            ninf = torch.full_like(fs, -float("inf"))
+            fa = torch.where((xa == xs).all(dim=1), fs, ninf)
+            fb = torch.where((xb == xs).all(dim=1), fs, ninf)
+            self.x = torch.cat([x[rest], xa, xb])
+            self.fx = torch.cat([fx[rest], fa, fb])
+            self.y = torch.cat([y[rest], clamp(ys, a_lo, a_hi), clamp(ys, b_lo, b_hi)])
+            self.s = torch.cat([sv[rest], ss, ss])
         else:
-            self.lo, self.hi, self.x = lo, hi, x
+            self.lo, self.hi, self.x, self.fx, self.y, self.s = lo, hi, x, fx, y, sv
         torch.cuda.synchronize(self.device)
         self._elapsed += time.perf_counter() - t0
         self.round += 1
@@ -152,8 +171,8 @@ class Bisection:
     # -------------------------------------------------------------- checkpoint
     def save(self, path: str):
         np.savez(path, lo=self.lo.cpu().numpy(), hi=self.hi.cpu().numpy(), x=self.x.cpu().numpy(),
-                 ub=self.ub, lb=self.lb, round=self.round, elapsed=self._elapsed,
-                 step_frac=self.step_frac)
+                 fx=self.fx.cpu().numpy(), y=self.y.cpu().numpy(), s=self.s.cpu().numpy(),
+                 ub=self.ub, lb=self.lb, round=self.round, elapsed=self._elapsed)
 
     @classmethod
     def load(cls, case: Case, path: str, **kw) -> "Bisection":
@@ -162,8 +181,8 @@ class Bisection:
         b.ub, b.lb = float(z["ub"]), float(z["lb"])
         b.round = int(z["round"])
         b._elapsed = float(z["elapsed"])
-        b.x = torch.as_tensor(z["x"], dtype=torch.float64, device=b.device)
-        b.step_frac = float(z["step_frac"])
+        for name in ("x", "fx", "y", "s"):
+            setattr(b, name, torch.as_tensor(z[name], dtype=torch.float64, device=b.device))
         return b
 
 
