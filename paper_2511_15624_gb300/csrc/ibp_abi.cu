@@ -116,6 +116,7 @@ struct ibp_case {
     int cap_box = 0, ws_gen = 0;
     DevBuf<double> box_lo, box_hi, obj;
     DevBuf<double> cbus;
+    DevBuf<float2> cbus2;
     DevBuf<float> rbus, cabs, box_consts, line_c, line_e, line_R, rbus_t;
     DevBuf<double> part_base, part_ctg, part_stage;
     DevBuf<float> flows;
@@ -143,7 +144,7 @@ struct ibp_case {
             rate_c_dn.free(); ctg_line.free(); act_ptr.free(); act_dev.free(); seg_ptr.free();
             slope.free(); bkpt.free(); hat_l.free(); hat_k.free(); phi_k.free(); rbus_t.free();
             box_lo.free(); box_hi.free();
-            obj.free(); cbus.free(); rbus.free(); cabs.free(); box_consts.free(); line_c.free();
+            obj.free(); cbus.free(); cbus2.free(); rbus.free(); cabs.free(); box_consts.free(); line_c.free();
             line_e.free(); line_R.free(); part_base.free(); part_ctg.free(); part_stage.free(); flows.free(); err.free();
             live_flag.free(); live.free(); n_live.free(); is_bridge.free(); cls_ptr.free();
             cls_col.free(); phi_r.free(); phi_kr.free(); rcls.free(); rcls_t.free(); nb_list.free();
@@ -751,6 +752,7 @@ static ibp_status ensure_workspace(ibp_case *c, int n_box) {
     CUDA_TRY(c->box_hi.alloc((size_t)cap * c->n_dev));
     CUDA_TRY(c->obj.alloc((size_t)cap * 4));
     CUDA_TRY(c->cbus.alloc(cap * na));
+    CUDA_TRY(c->cbus2.alloc(cap * na));
     CUDA_TRY(c->rbus.alloc(cap * na));
     CUDA_TRY(c->cabs.alloc(cap * na));
     CUDA_TRY(c->box_consts.alloc((size_t)cap * 4));
@@ -812,7 +814,7 @@ static ibp_status enqueue_bound(ibp_case *c, int n_box, const double *lo, const 
     BusArgs ba{};
     ba.n_a = c->n_a; ba.n_a_pad = c->n_a_pad; ba.n_dev = c->n_dev; ba.n_gen = c->n_gen; ba.n_box = n_box;
     ba.act_ptr = c->act_ptr.p; ba.act_dev = c->act_dev.p; ba.box_lo = lo; ba.box_hi = hi;
-    ba.cbus = c->cbus.p; ba.rbus = c->rbus.p; ba.rbus_t = multi ? c->rbus_t.p : nullptr;
+    ba.cbus = c->cbus.p; ba.cbus2 = c->cbus2.p; ba.rbus = c->rbus.p; ba.rbus_t = multi ? c->rbus_t.p : nullptr;
     ba.n_box_pad = n_box_pad;
     ba.cabs = c->cabs.p; ba.box_consts = c->box_consts.p; ba.err = c->err.p;
     CUDA_TRY(launch_bus(ba, s));
@@ -827,7 +829,7 @@ static ibp_status enqueue_bound(ibp_case *c, int n_box, const double *lo, const 
 
     BaseArgs bb{};
     bb.n_l = c->n_line; bb.n_c = c->n_ctg; bb.n_a = c->n_a; bb.n_a_pad = c->n_a_pad; bb.n_box = n_box;
-    bb.phi = c->phi_a.p; bb.ctg_line = c->ctg_line.p; bb.cbus = c->cbus.p; bb.rbus = c->rbus.p;
+    bb.phi = c->phi_a.p; bb.ctg_line = c->ctg_line.p; bb.cbus = c->cbus.p; bb.cbus2 = c->cbus2.p; bb.rbus = c->rbus.p;
     bb.cabs = c->cabs.p; bb.rate_up = c->rate_up.p; bb.rate_dn = c->rate_dn.p;
     bb.box_consts = c->box_consts.p;
     bb.gamma_base = rup_gamma((c->n_a_pad / 4 + 31) / 32, 2, 5);
@@ -1321,7 +1323,8 @@ extern "C" ibp_status ibp_bound_multi(int32_t n_case, ibp_case *const *cases, co
         BusArgs ba{};
         ba.n_a = c->n_a; ba.n_a_pad = c->n_a_pad; ba.n_dev = c->n_dev; ba.n_gen = c->n_gen; ba.n_box = nb;
         ba.act_ptr = c->act_ptr.p; ba.act_dev = c->act_dev.p; ba.box_lo = box_lo[i]; ba.box_hi = box_hi[i];
-        ba.cbus = c->cbus.p; ba.rbus = c->rbus.p; ba.rbus_t = c->rbus_t.p; ba.n_box_pad = n_box_pad;
+        ba.cbus = c->cbus.p; ba.cbus2 = c->cbus2.p; ba.rbus = c->rbus.p; ba.rbus_t = c->rbus_t.p;
+        ba.n_box_pad = n_box_pad;
         ba.cabs = c->cabs.p; ba.box_consts = c->box_consts.p; ba.err = c->err.p;
         CUDA_TRY(launch_bus(ba, s));
         if (red) {
@@ -1333,7 +1336,7 @@ extern "C" ibp_status ibp_bound_multi(int32_t n_case, ibp_case *const *cases, co
         }
         BaseArgs bb{};
         bb.n_l = c->n_line; bb.n_c = c->n_ctg; bb.n_a = c->n_a; bb.n_a_pad = c->n_a_pad; bb.n_box = nb;
-        bb.phi = c->phi_a.p; bb.ctg_line = c->ctg_line.p; bb.cbus = c->cbus.p; bb.rbus = c->rbus.p;
+        bb.phi = c->phi_a.p; bb.ctg_line = c->ctg_line.p; bb.cbus = c->cbus.p; bb.cbus2 = c->cbus2.p; bb.rbus = c->rbus.p;
         bb.cabs = c->cabs.p; bb.rate_up = c->rate_up.p; bb.rate_dn = c->rate_dn.p;
         bb.box_consts = c->box_consts.p;
         bb.gamma_base = rup_gamma((c->n_a_pad / 4 + 31) / 32, 2, 5);

@@ -27,6 +27,7 @@ struct BusArgs {
     const double *box_lo;   // [n_box][n_dev]
     const double *box_hi;
     double *cbus;           // [n_box][n_a_pad] bus injection centre (FP64)
+    float2 *cbus2;          // [n_box][n_a_pad] the same as hi + lo FP32 pair, or null
     float *rbus;            // [n_box][n_a_pad] radius, rounded up
     float *rbus_t;          // [n_a_pad][n_box_pad] transposed radius (or null)
     int n_box_pad;
@@ -40,6 +41,7 @@ struct BaseArgs {
     const float *phi;        // [n_l][n_a_pad]
     const int *ctg_line;     // [n_c]
     const double *cbus;
+    const float2 *cbus2;     // hi + lo split of cbus; given -> compensated FP32 centre sums
     const float *rbus;
     const float *cabs;
     const float *rate_up;    // base ratings rounded up / down

@@ -49,6 +49,10 @@ __global__ void __launch_bounds__(256) k_bus(BusArgs a) {
             ca = __double2float_ru(fabs(c));
         }
         a.cbus[(size_t)j * a.n_a_pad + col] = c;
+        if (a.cbus2) {
+            const float ch = __double2float_rn(c);
+            a.cbus2[(size_t)j * a.n_a_pad + col] = make_float2(ch, __double2float_rn(c - (double)ch));
+        }
         a.rbus[(size_t)j * a.n_a_pad + col] = r32;
         a.cabs[(size_t)j * a.n_a_pad + col] = ca;
         if (a.rbus_t) a.rbus_t[(size_t)col * a.n_box_pad + j] = r32;
@@ -98,7 +102,9 @@ cudaError_t launch_bus(const BusArgs &a, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 // Base-case flows, one warp per line (eq. (line flow ptdf) under eq. (IBP)).
 // For line l and box j:
-//   centre   c_l = sum_b Phi~[l,b] c_b       FP64 accumulation, then FP32 RN
+//   centre   c_l = sum_b Phi~[l,b] c_b       FP64 accumulation (or the
+//                                            compensated FP32 sums of
+//                                            k_base_ff), then FP32 RN
 //   C_l          = sum_b |Phi~[l,b]| |c_b|   FP32 round-up
 //   R_l          = sum_b |Phi~[l,b]| r_b     FP32 round-up
 // Phi~ is the FP32 copy of the FP64 PTDF (|Phi - Phi~| <= u |Phi~| + 2^-120),
@@ -116,6 +122,186 @@ cudaError_t launch_bus(const BusArgs &a, cudaStream_t s) {
 constexpr int kBaseWarps = 8;
 
 int base_partials_count(int num_sms) { return num_sms * 2 * kBaseWarps; }
+
+// Per (line, box) epilogue of the base flows: certified interval, violation
+// interval of eq. (slack-sfb), error allowance, active-set recording and, for
+// bridge lines, their n_c contingency pairs in closed form.  c = FP32 centre,
+// C, R = round-up sums of |Phi~||c_b| and |Phi~| r_b.
+__device__ __forceinline__ void base_epilogue(const BaseArgs &a, int l, int j, float c, float C,
+                                              float R, double *part) {
+    const float *bc = a.box_consts + (size_t)j * 4;
+    const float eta_r = bc[0], eta_c = bc[1];
+    const float e = __fadd_ru(__fmul_ru(2.1f * kU, C), eta_c);
+    const float rbar = __fadd_ru(__fmaf_ru(R, kU, R), eta_r);
+    const float rho = __fadd_ru(rbar, e);
+    const float flo = __fsub_rd(c, rho), fhi = __fadd_ru(c, rho);
+    float alo, ahi;
+    abs_interval(flo, fhi, alo, ahi);
+    const float slo = fmax0(__fsub_rd(alo, a.rate_up[l]));
+    const float shi = fmax0(__fsub_ru(ahi, a.rate_dn[l]));
+    float whi = 0.0f, wlo = 0.0f;
+    if (shi > 0.0f) {
+        // |s - s_exact| <= w = (rbar - R_exact) + 2 e + u rating; s_lo is
+        // exact where alo - rating + w <= 0
+        const float w = __fmaf_ru(a.gamma_base + 3.0f * kU, R,
+                                  __fmaf_ru(2.0f, e, __fmaf_ru(kU, a.rate_up[l], 2.0f * eta_r)));
+        wlo = w;
+        if (__fadd_ru(__fsub_ru(alo, a.rate_dn[l]), w) > 0.0f) whi = w;
+    }
+    a.line_c[(size_t)j * a.n_l + l] = c;
+    a.line_e[(size_t)j * a.n_l + l] = e;
+    a.line_R[(size_t)j * a.n_l + l] = R;
+    if (a.act_list && slo > 0.0f) {
+        const int idx = atomicAdd(&a.act_count[j], 1);
+        if (idx < a.act_cap)
+            a.act_list[(size_t)j * a.act_cap + idx] =
+                make_int4(l, l, __float_as_int(0.0f), __float_as_int(c > 0.0f ? 1.0f : -1.0f));
+        else
+            atomicOr(a.err, kErrOverflow);
+    }
+    double *q = part + j * kPartVals;
+    q[0] = __dadd_rd(q[0], (double)slo);
+    q[1] = __dadd_ru(q[1], (double)shi);
+    q[2] = __dadd_ru(q[2], (double)whi);
+    q[3] = __dadd_ru(q[3], (double)wlo);
+    if (a.is_bridge && a.is_bridge[l] && a.n_c > 0) {
+        // A bridge carries the net injection of the side away from
+        // the slack; no non-islanding outage changes that, so
+        // L[l,k] = 0 and every contingency pair of the line has the
+        // base interval [c - rho, c + rho] (eq. (slack-Sc) with the
+        // contingency rating), n_c times.
+        const float rcu = a.rate_c_up[l], rcd = a.rate_c_dn[l];
+        const float clo = fmax0(__fsub_rd(alo, rcu));
+        const float chi = fmax0(__fsub_ru(ahi, rcd));
+        float cwh = 0.0f, cwl = 0.0f;
+        if (chi > 0.0f) {
+            const float w = __fmaf_ru(a.gamma_base + 3.0f * kU, R,
+                                      __fmaf_ru(2.0f, e, __fmaf_ru(kU, rcu, 2.0f * eta_r)));
+            cwl = w;
+            if (__fadd_ru(__fsub_ru(alo, rcd), w) > 0.0f) cwh = w;
+        }
+        const double nc = (double)a.n_c;
+        q[0] = __dadd_rd(q[0], __dmul_rd(nc, (double)clo));
+        q[1] = __dadd_ru(q[1], __dmul_ru(nc, (double)chi));
+        q[2] = __dadd_ru(q[2], __dmul_ru(nc, (double)cwh));
+        q[3] = __dadd_ru(q[3], __dmul_ru(nc, (double)cwl));
+        if (a.act_list && clo > 0.0f) {
+            const int idx = atomicAdd(&a.act_count[j], 1);
+            if (idx < a.act_cap)
+                a.act_list[(size_t)j * a.act_cap + idx] =
+                    make_int4(l, -1, __float_as_int((float)a.n_c),
+                              __float_as_int(c > 0.0f ? 1.0f : -1.0f));
+            else
+                atomicOr(a.err, kErrOverflow);
+        }
+    }
+}
+
+// Compensated FP32 accumulation of sum_b Phi~[l,b] c_b with c_b = hi + lo:
+// each product Phi~ hi is split exactly (FMA remainder), the running sum uses
+// TwoSum, and Phi~ lo goes to the compensation term.  The error is below
+// n u^2 sum_b |Phi~[l,b] c_b| plus the representation of c_b (u^2 |c_b|), far
+// inside the 0.1 u C_l left in e_l = 2.1 u C_l for the summation.
+struct FF {
+    float s, e;
+};
+// (intrinsics throughout: a contracted multiply-add would break TwoSum)
+__device__ __forceinline__ void ff_add_prod(FF &acc, float p, float2 c) {
+    const float m = __fmul_rn(p, c.x);
+    const float me = __fmaf_rn(p, c.x, -m);
+    const float t = __fadd_rn(acc.s, m);
+    const float z = __fsub_rn(t, acc.s);
+    const float err = __fadd_rn(__fsub_rn(acc.s, __fsub_rn(t, z)), __fsub_rn(m, z));
+    acc.s = t;
+    acc.e = __fmaf_rn(p, c.y, __fadd_rn(acc.e, __fadd_rn(err, me)));
+}
+
+// Box-grouped base flows: a warp takes one line and up to kBaseGroup boxes,
+// reads the PTDF row once and keeps the sums of every box of the group.
+constexpr int kBaseGroup = 8;
+
+__global__ void __launch_bounds__(kBaseWarps * 32) k_base_ff(BaseArgs a) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * kBaseWarps + warp;
+    const int nw = gridDim.x * kBaseWarps;
+    const int n_groups = (a.n_box + kBaseGroup - 1) / kBaseGroup;
+    const int n_items = a.n_l * n_groups + (a.hat_k ? a.n_c : 0);
+    const int nv = a.n_a_pad >> 2;  // float4 per row
+    double *part = a.partials + (size_t)gw * a.n_box * kPartVals;
+    for (int j = 0; j < a.n_box; ++j)
+        if (lane == 0)
+            for (int v = 0; v < kPartVals; ++v) part[j * kPartVals + v] = 0.0;
+    for (int item = gw; item < n_items; item += nw) {
+        if (item >= a.n_l * n_groups) {
+            // scaled copy of a contingency line's row (one-box mode)
+            const int k = item - a.n_l * n_groups;
+            const float4 *src = reinterpret_cast<const float4 *>(a.phi + (size_t)a.ctg_line[k] * a.n_a_pad);
+            const float4 *rr = reinterpret_cast<const float4 *>(a.rbus);
+            float4 *dst = reinterpret_cast<float4 *>(a.hat_k + (size_t)k * a.n_a_pad);
+            for (int v = lane; v < nv; v += 32) {
+                const float4 p = src[v], r = rr[v];
+                dst[v] = make_float4(__fmul_rn(p.x, r.x), __fmul_rn(p.y, r.y), __fmul_rn(p.z, r.z),
+                                     __fmul_rn(p.w, r.w));
+            }
+            continue;
+        }
+        const int l = item / n_groups, j0 = (item % n_groups) * kBaseGroup;
+        const int bg = min(kBaseGroup, a.n_box - j0);
+        const float4 *prow = reinterpret_cast<const float4 *>(a.phi + (size_t)l * a.n_a_pad);
+        float4 *hl = a.hat_l ? reinterpret_cast<float4 *>(a.hat_l + (size_t)l * a.n_a_pad) : nullptr;
+        // C and R keep one round-up sum per bus of the float4 (the same
+        // summation tree as the FP64 kernel, so gamma_base holds for both)
+        FF cs[kBaseGroup];
+        float4 C[kBaseGroup], R[kBaseGroup];
+#pragma unroll
+        for (int jj = 0; jj < kBaseGroup; ++jj) {
+            cs[jj] = FF{0.0f, 0.0f};
+            C[jj] = R[jj] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        }
+        for (int v = lane; v < nv; v += 32) {
+            const float4 p = prow[v];
+            const float4 ap = make_float4(fabsf(p.x), fabsf(p.y), fabsf(p.z), fabsf(p.w));
+#pragma unroll
+            for (int jj = 0; jj < kBaseGroup; ++jj) {
+                if (jj >= bg) break;
+                const size_t o = (size_t)(j0 + jj) * a.n_a_pad;
+                const float4 *c2 = reinterpret_cast<const float4 *>(a.cbus2 + o) + 2 * v;
+                const float4 c01 = c2[0], c23 = c2[1];
+                const float4 r = reinterpret_cast<const float4 *>(a.rbus + o)[v];
+                const float4 ca = reinterpret_cast<const float4 *>(a.cabs + o)[v];
+                ff_add_prod(cs[jj], p.x, make_float2(c01.x, c01.y));
+                ff_add_prod(cs[jj], p.y, make_float2(c01.z, c01.w));
+                ff_add_prod(cs[jj], p.z, make_float2(c23.x, c23.y));
+                ff_add_prod(cs[jj], p.w, make_float2(c23.z, c23.w));
+                C[jj].x = __fmaf_ru(ap.x, ca.x, C[jj].x);
+                C[jj].y = __fmaf_ru(ap.y, ca.y, C[jj].y);
+                C[jj].z = __fmaf_ru(ap.z, ca.z, C[jj].z);
+                C[jj].w = __fmaf_ru(ap.w, ca.w, C[jj].w);
+                R[jj].x = __fmaf_ru(ap.x, r.x, R[jj].x);
+                R[jj].y = __fmaf_ru(ap.y, r.y, R[jj].y);
+                R[jj].z = __fmaf_ru(ap.z, r.z, R[jj].z);
+                R[jj].w = __fmaf_ru(ap.w, r.w, R[jj].w);
+                if (hl && jj == 0)
+                    hl[v] = make_float4(__fmul_rn(p.x, r.x), __fmul_rn(p.y, r.y), __fmul_rn(p.z, r.z),
+                                        __fmul_rn(p.w, r.w));
+            }
+        }
+#pragma unroll
+        for (int jj = 0; jj < kBaseGroup; ++jj) {
+            if (jj >= bg) break;
+            // lanes' compensated sums are exact in FP64; the 5-level FP64 tree
+            // adds about 5 * 2^-53 relative
+            double d = (double)cs[jj].s + (double)cs[jj].e;
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+            const float Cs = warp_sum_ru_f(
+                __fadd_ru(__fadd_ru(C[jj].x, C[jj].y), __fadd_ru(C[jj].z, C[jj].w)));
+            const float Rs = warp_sum_ru_f(
+                __fadd_ru(__fadd_ru(R[jj].x, R[jj].y), __fadd_ru(R[jj].z, R[jj].w)));
+            if (lane == 0) base_epilogue(a, l, j0 + jj, __double2float_rn(d), Cs, Rs, part);
+        }
+    }
+}
 
 __global__ void __launch_bounds__(kBaseWarps * 32) k_base(BaseArgs a) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -177,75 +363,7 @@ __global__ void __launch_bounds__(kBaseWarps * 32) k_base(BaseArgs a) {
             for (int o = 16; o > 0; o >>= 1) cs += __shfl_xor_sync(0xffffffffu, cs, o);
             C = warp_sum_ru_f(C);
             R = warp_sum_ru_f(R);
-            if (lane == 0) {
-                const float *bc = a.box_consts + (size_t)j * 4;
-                const float eta_r = bc[0], eta_c = bc[1];
-                const float c = __double2float_rn(cs);
-                const float e = __fadd_ru(__fmul_ru(2.1f * kU, C), eta_c);
-                const float rbar = __fadd_ru(__fmaf_ru(R, kU, R), eta_r);
-                const float rho = __fadd_ru(rbar, e);
-                const float flo = __fsub_rd(c, rho), fhi = __fadd_ru(c, rho);
-                float alo, ahi;
-                abs_interval(flo, fhi, alo, ahi);
-                const float slo = fmax0(__fsub_rd(alo, a.rate_up[l]));
-                const float shi = fmax0(__fsub_ru(ahi, a.rate_dn[l]));
-                float whi = 0.0f, wlo = 0.0f;
-                if (shi > 0.0f) {
-                    // |s - s_exact| <= w = (rbar - R_exact) + 2 e + u rating; s_lo is
-                    // exact where alo - rating + w <= 0
-                    const float w = __fmaf_ru(a.gamma_base + 3.0f * kU, R,
-                                              __fmaf_ru(2.0f, e, __fmaf_ru(kU, a.rate_up[l], 2.0f * eta_r)));
-                    wlo = w;
-                    if (__fadd_ru(__fsub_ru(alo, a.rate_dn[l]), w) > 0.0f) whi = w;
-                }
-                a.line_c[(size_t)j * a.n_l + l] = c;
-                a.line_e[(size_t)j * a.n_l + l] = e;
-                a.line_R[(size_t)j * a.n_l + l] = R;
-                if (a.act_list && slo > 0.0f) {
-                    const int idx = atomicAdd(&a.act_count[j], 1);
-                    if (idx < a.act_cap)
-                        a.act_list[(size_t)j * a.act_cap + idx] =
-                            make_int4(l, l, __float_as_int(0.0f), __float_as_int(c > 0.0f ? 1.0f : -1.0f));
-                    else
-                        atomicOr(a.err, kErrOverflow);
-                }
-                double *q = part + j * kPartVals;
-                q[0] = __dadd_rd(q[0], (double)slo);
-                q[1] = __dadd_ru(q[1], (double)shi);
-                q[2] = __dadd_ru(q[2], (double)whi);
-                q[3] = __dadd_ru(q[3], (double)wlo);
-                if (a.is_bridge && a.is_bridge[l] && a.n_c > 0) {
-                    // A bridge carries the net injection of the side away from
-                    // the slack; no non-islanding outage changes that, so
-                    // L[l,k] = 0 and every contingency pair of the line has the
-                    // base interval [c - rho, c + rho] (eq. (slack-Sc) with the
-                    // contingency rating), n_c times.
-                    const float rcu = a.rate_c_up[l], rcd = a.rate_c_dn[l];
-                    const float clo = fmax0(__fsub_rd(alo, rcu));
-                    const float chi = fmax0(__fsub_ru(ahi, rcd));
-                    float cwh = 0.0f, cwl = 0.0f;
-                    if (chi > 0.0f) {
-                        const float w = __fmaf_ru(a.gamma_base + 3.0f * kU, R,
-                                                  __fmaf_ru(2.0f, e, __fmaf_ru(kU, rcu, 2.0f * eta_r)));
-                        cwl = w;
-                        if (__fadd_ru(__fsub_ru(alo, rcd), w) > 0.0f) cwh = w;
-                    }
-                    const double nc = (double)a.n_c;
-                    q[0] = __dadd_rd(q[0], __dmul_rd(nc, (double)clo));
-                    q[1] = __dadd_ru(q[1], __dmul_ru(nc, (double)chi));
-                    q[2] = __dadd_ru(q[2], __dmul_ru(nc, (double)cwh));
-                    q[3] = __dadd_ru(q[3], __dmul_ru(nc, (double)cwl));
-                    if (a.act_list && clo > 0.0f) {
-                        const int idx = atomicAdd(&a.act_count[j], 1);
-                        if (idx < a.act_cap)
-                            a.act_list[(size_t)j * a.act_cap + idx] =
-                                make_int4(l, -1, __float_as_int((float)a.n_c),
-                                          __float_as_int(c > 0.0f ? 1.0f : -1.0f));
-                        else
-                            atomicOr(a.err, kErrOverflow);
-                    }
-                }
-            }
+            if (lane == 0) base_epilogue(a, l, j, __double2float_rn(cs), C, R, part);
             hl = nullptr;
         }
     }
@@ -253,7 +371,8 @@ __global__ void __launch_bounds__(kBaseWarps * 32) k_base(BaseArgs a) {
 
 cudaError_t launch_base(const BaseArgs &a, int n_part, cudaStream_t s) {
     const int grid = n_part / kBaseWarps;
-    k_base<<<grid, kBaseWarps * 32, 0, s>>>(a);
+    if (a.cbus2) k_base_ff<<<grid, kBaseWarps * 32, 0, s>>>(a);
+    else k_base<<<grid, kBaseWarps * 32, 0, s>>>(a);
     return cudaGetLastError();
 }
 
