@@ -1,0 +1,58 @@
+"""Parity at the full 8316-bus size, in the launch configurations bench.py
+times: one box with the library defaults (line screen and network reduction
+on), and one box out of a 32-box call (multi-box kernel).  The oracle bounds
+the same boxes in full (all contingencies x all lines x all buses, about half
+a minute on the host cores per box); flow intervals are compared on a sample
+of pairs that the oracle computes one by one."""
+import numpy as np
+import pytest
+
+import oracle as O
+from gen import make_config
+from gen.cases import time_index_boxes
+from tests.test_gpu_parity import check_flows, check_objective
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2511_15624_gb300 as P
+    case = make_config(3)
+    sens = O.sensitivities(case)
+    gpu = P.Case(case, device=0)
+    return P, torch, case, sens, gpu
+
+
+def test_fullsize_one_box_default_launch(env):
+    P, torch, case, sens, gpu = env
+    lo = torch.tensor(case.box_lo, device="cuda")
+    hi = torch.tensor(case.box_hi, device="cuda")
+    olo, ohi, err = (t.cpu().numpy() for t in gpu.bound(lo, hi))
+    n, _ = gpu.last_live()
+    assert 0 < n < case.n_line  # the screen and the reduction were in the path
+    check_objective(olo, ohi, err, O.bound(case, sens))
+
+
+def test_fullsize_box_of_32_box_call(env):
+    P, torch, case, sens, gpu = env
+    bcase = time_index_boxes(case, 32, seed=2003)
+    lo = torch.tensor(bcase.box_lo, device="cuda")
+    hi = torch.tensor(bcase.box_hi, device="cuda")
+    olo, ohi, err = (t.cpu().numpy() for t in gpu.bound(lo, hi))
+    j = 17
+    ref = O.bound(case, sens, lo=bcase.box_lo[j:j + 1], hi=bcase.box_hi[j:j + 1])
+    check_objective(olo[j:j + 1], ohi[j:j + 1], err[j:j + 1], ref)
+
+
+def test_fullsize_sampled_flows(env):
+    P, torch, case, sens, gpu = env
+    lo, hi, err, flo, fhi = gpu.bound(case.box_lo, case.box_hi, flows=True)
+    rng = np.random.default_rng(83)
+    pk = rng.integers(0, case.n_ctg, 20000)
+    pl = rng.integers(0, case.n_line, 20000)
+    pl[:200] = case.ctg_line[pk[:200]]  # include outaged lines
+    check_flows(case, sens, case.box_lo, case.box_hi, flo, fhi, pk, pl)
