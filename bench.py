@@ -63,6 +63,8 @@ def _args():
                    help="bisection: batched vs per-box gradient-guided bisection on mesh2000; "
                         "ragged: 64 uneven networks x 16 sub-boxes in one persistent launch")
     p.add_argument("--rounds", type=int, default=20)
+    p.add_argument("--adjoint", action="store_true",
+                   help="also time the adjoint of the upper bound (1 box and the batch)")
     p.add_argument("--cpu-seconds", type=float, default=20.0,
                    help="target CPU time of the oracle sample")
     return p.parse_args()
@@ -323,6 +325,25 @@ def run_gb300(args):
                    "contingency_kernel_ms": bk["contingency"],
                    "achieved_tflops": bflop / (bk["contingency"] * 1e-3) / 1e12}
 
+    # (5) adjoint of obj_hi (forward with active-pair recording + backward
+    # kernels), one box and, when measured, the batch
+    adjoint = None
+    if args.adjoint:
+        def time_bwd(blo, bhi, reps):
+            g = torch.ones(blo.shape[0], dtype=torch.float64, device=dev)
+            gpu.backward(blo, bhi, g)
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                gpu.backward(blo, bhi, g)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            return e0.elapsed_time(e1) / reps
+        adjoint = {"ms_per_call_1_box": time_bwd(lo, hi, max(2, args.steps // 4))}
+        if batched is not None:
+            adjoint["ms_per_call_%d_boxes" % args.boxes] = time_bwd(blo, bhi, 2)
+
     # the slowest rank sets the job time (no other exchange: every rank owns its bounds)
     dev_ms, e2e_ms = max_over_ranks([dev_ms, e2e_s * 1e3], device=dev)
     if rank != 0:
@@ -361,6 +382,7 @@ def run_gb300(args):
         "batched": None if batched is None else {
             **batched, "frac": batched["achieved_tflops"] / fp32_peak,
             "interval_flows_per_s": case.n_ctg * case.n_line * batched["boxes"] / (batched["ms_per_call"] * 1e-3)},
+        "adjoint": adjoint,
         "objective": {"lo": float(obj[0][0]), "hi": float(obj[1][0]),
                       "err_hi": float(obj[2][0][0]), "err_lo": float(obj[2][0][1])},
     }

@@ -1048,6 +1048,7 @@ static ibp_status enqueue_backward(ibp_case *c, int n_box, const double *lo, con
     CUDA_TRY(cudaMemsetAsync(c->W.p, 0, (size_t)n_box * c->n_line * sizeof(double), s));
     CUDA_TRY(cudaMemsetAsync(c->cnt.p, 0, (size_t)n_box * c->n_line * sizeof(int), s));
     CUDA_TRY(cudaMemsetAsync(c->dr.p, 0, (size_t)n_box * c->n_a_pad * sizeof(double), s));
+    CUDA_TRY(cudaMemsetAsync(c->dc.p, 0, (size_t)n_box * c->n_a_pad * sizeof(double), s));
     BwdArgs b{};
     b.n_l = c->n_line; b.n_a = c->n_a; b.n_a_pad = c->n_a_pad; b.n_dev = c->n_dev; b.n_gen = c->n_gen;
     b.n_box = n_box; b.act_cap = c->act_cap; b.phi = c->phi_a.p; b.act_count = c->act_count.p;

@@ -45,18 +45,24 @@ __global__ void k_bwd_weights(BwdArgs a) {
     }
 }
 
-// dc[box][col] = sum_l W[box][l] Phi[l][col]  (lines with W = 0 are skipped)
+// dc[box][col] = sum_l W[box][l] Phi[l][col]  (lines with W = 0 are skipped);
+// block row y takes lines [y n_l / kCenterSplit, (y + 1) n_l / kCenterSplit)
+// and adds its sum into dc (zeroed by the caller)
+constexpr int kCenterSplit = 32;
+
 __global__ void k_bwd_center(BwdArgs a) {
-    const int box = blockIdx.y;
+    const int box = blockIdx.z;
     const int col = blockIdx.x * blockDim.x + threadIdx.x;
     const double *W = a.W + (size_t)box * a.n_l;
+    const int l0 = (int)((long long)blockIdx.y * a.n_l / kCenterSplit);
+    const int l1 = (int)((long long)(blockIdx.y + 1) * a.n_l / kCenterSplit);
     double acc = 0.0;
     if (col < a.n_a_pad) {
-        for (int l = 0; l < a.n_l; ++l) {
+        for (int l = l0; l < l1; ++l) {
             const double w = W[l];
             if (w != 0.0) acc = fma(w, (double)__ldg(&a.phi[(size_t)l * a.n_a_pad + col]), acc);
         }
-        a.dc[(size_t)box * a.n_a_pad + col] = acc;
+        if (acc != 0.0) atomicAdd(&a.dc[(size_t)box * a.n_a_pad + col], acc);
     }
 }
 
@@ -163,7 +169,7 @@ cudaError_t launch_backward(const BwdArgs &a, cudaStream_t s) {
     k_bwd_weights<<<gw, 256, 0, s>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    const dim3 gc((a.n_a_pad + 127) / 128, a.n_box);
+    const dim3 gc((a.n_a_pad + 127) / 128, kCenterSplit, a.n_box);
     k_bwd_center<<<gc, 128, 0, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     const dim3 gr((a.n_a_pad + 127) / 128, kEntryBlocks / 4, a.n_box);
