@@ -714,10 +714,10 @@ ibp_status set_error(ibp_status s, const char *msg) {
 }  // namespace ibp
 
 // ----------------------------------------------------------------- workspace
-// fastest shapes measured on GB300: one box, 16 warps, 4x4 pairs per thread,
-// 64-bus chunks, packed two-lane sums; many boxes, 8 warps, 4 lines x 16
-// boxes per thread, packed FMA
-constexpr int kDefaultOneBoxVariant = 12;
+// fastest shapes measured on GB300: one box, 2 CTAs per SM of 8 warps, 4x4
+// pairs per thread, 64-bus chunks in 2 stages, packed two-lane sums; many
+// boxes, 8 warps, 4 lines x 16 boxes per thread, packed FMA
+constexpr int kDefaultOneBoxVariant = 16;
 constexpr int kDefaultMultiBoxVariant = 26;
 
 static const CtgVariant *pick_variant(const ibp_case *c, int n_box) {
@@ -885,7 +885,7 @@ static ibp_status enqueue_bound(ibp_case *c, int n_box, const double *lo, const 
     {
         const bool tree = !multi && v->id >= 6;
         // packed two-lane sums (12, 13): one more add to join the lanes
-        const bool packed = !multi && (v->id == 12 || v->id == 13);
+        const bool packed = !multi && (v->id == 12 || v->id == 13 || v->id == 15 || v->id == 16);
         const long n1 = tree ? v->CH / 4 + 2 + (packed ? 1 : 0) : v->CH;
         const long n2 = 256 / v->CH;
         ca.gamma = rup_gamma(n1, n2, (n_chunks + n2 - 1) / n2);

@@ -729,6 +729,8 @@ static const CtgVariant kVariants[] = {
     {11, 0, 64, 64, 64, 2, 1, "2 CTAs/SM x 8 warps, 4x4/thread, 64-bus chunks, 2 stages, tree"},
     {12, 0, 128, 64, 64, 3, 1, "16 warps, 4x4/thread, 64-bus chunks, 3 stages, packed two-lane sums"},
     {13, 0, 128, 64, 32, 4, 1, "16 warps, 4x4/thread, 32-bus chunks, 4 stages, packed two-lane sums"},
+    {15, 0, 64, 64, 32, 4, 1, "2 CTAs/SM x 8 warps, 4x4/thread, 32-bus chunks, 4 stages, packed"},
+    {16, 0, 64, 64, 64, 2, 1, "2 CTAs/SM x 8 warps, 4x4/thread, 64-bus chunks, 2 stages, packed"},
     {20, 1, 64, 16, 32, 4, 16, "multi-box 64x16x16, 8 warps, 4 lines x 16 boxes/thread, 4 stages"},
     {21, 1, 64, 16, 32, 6, 16, "multi-box 64x16x16, 8 warps, 4 lines x 16 boxes/thread, 6 stages"},
     {22, 1, 64, 16, 32, 4, 8, "multi-box 64x16x16, 16 warps, 4 lines x 8 boxes/thread, 4 stages"},
@@ -802,6 +804,8 @@ cudaError_t launch_ctg(const CtgVariant &v, const CUtensorMap &mL, const CUtenso
     case 11: return launch_one<4, 2, 4, 4, 2, true, 64, 1, 2>(mL, mK, a, grid, s);
     case 12: return launch_one<8, 2, 4, 4, 3, true, 64, 2>(mL, mK, a, grid, s);
     case 13: return launch_one<8, 2, 4, 4, 4, true, 32, 2>(mL, mK, a, grid, s);
+    case 15: return launch_one<4, 2, 4, 4, 4, true, 32, 2, 2>(mL, mK, a, grid, s);
+    case 16: return launch_one<4, 2, 4, 4, 2, true, 64, 2, 2>(mL, mK, a, grid, s);
     default: return cudaErrorInvalidValue;
     }
 }
