@@ -325,7 +325,19 @@ def run_gb300(args):
                    "contingency_kernel_ms": bk["contingency"],
                    "achieved_tflops": bflop / (bk["contingency"] * 1e-3) / 1e12}
 
-    # (5) adjoint of obj_hi (forward with active-pair recording + backward
+    # (5) the paper's own bound (two-part contingency intervals) on the same box
+    gpu.bound_paper(lo, hi)
+    torch.cuda.synchronize(dev)
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0.record(stream)
+    for _ in range(args.steps):
+        pout = gpu.bound_paper(lo, hi)
+    p1.record(stream)
+    torch.cuda.synchronize(dev)
+    paper = {"ms_per_bound": p0.elapsed_time(p1) / args.steps,
+             "obj_hi": float(pout[1][0]), "obj_lo": float(pout[0][0])}
+
+    # (6) adjoint of obj_hi (forward with active-pair recording + backward
     # kernels), one box and, when measured, the batch
     adjoint = None
     if args.adjoint:
@@ -382,6 +394,7 @@ def run_gb300(args):
         "batched": None if batched is None else {
             **batched, "frac": batched["achieved_tflops"] / fp32_peak,
             "interval_flows_per_s": case.n_ctg * case.n_line * batched["boxes"] / (batched["ms_per_call"] * 1e-3)},
+        "paper_mode": paper,
         "adjoint": adjoint,
         "objective": {"lo": float(obj[0][0]), "hi": float(obj[1][0]),
                       "err_hi": float(obj[2][0][0]), "err_lo": float(obj[2][0][1])},

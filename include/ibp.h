@@ -216,6 +216,21 @@ ibp_status ibp_case_set_variant(ibp_case *c, int32_t variant);
 int32_t ibp_kernel_variants(int32_t *ids, int32_t cap, int32_t batched);
 
 /*
+ * The objective interval with the paper's own contingency intervals (Sec.
+ * II-C, eq. (ctg flow matrix form): [Phi p] and [U p] propagated separately,
+ * so every contingency flow takes the radius R_l + |L[l,k]| R_k) in place of
+ * the tight per-row radius of ibp_bound.  The result encloses ibp_bound's (it
+ * is the bound of the paper's graph), costs O(n_ctg * n_line) instead of
+ * O(n_ctg * n_line * n_active), and is certified the same way (outward FP32,
+ * FP64 sums, obj_err as in ibp_bound).  A box whose paper-mode obj_hi is
+ * already negative is certified welfare-negative without the tight pass.
+ * Arguments, layouts, ptr_mode, stream and errors as in ibp_bound (no flows).
+ */
+ibp_status ibp_bound_paper(ibp_case *c, int32_t n_box, const double *box_lo,
+                           const double *box_hi, double *obj_lo, double *obj_hi,
+                           double *obj_err, int32_t ptr_mode, void *cuda_stream);
+
+/*
  * Paper-mode line screen (Sec. II-C: the contingency flow of eq. (ctg flow
  * matrix form) propagated as the two intervals [Phi p] and [U p], radius
  * R_l + |L[l,k]| R_k, an upper bound of the tight radius).  When enabled (the

@@ -22,6 +22,7 @@ Every function names the passage of the paper it follows:
 * ``grad_hi``             hand-derived adjoint of the upper bound (the paper has none)
 * ``paper_mode_flows``    IBP applied literally to eq. (ctg flow matrix form)
 * ``screen_lines``        lines whose paper-mode contingency interval can exceed the rating
+* ``paper_ctg_terms``     eq. (slack-Sc) sums over the paper-mode intervals (``bound(mode="paper")``)
 * ``objective_point``     f_ibp at a point, appendix eq. (ibp_f)
 
 Parity pins: every function above is checked in ``tests/test_oracle_*.py``
@@ -367,12 +368,24 @@ class Bound:
     terms: dict
 
 
+def paper_ctg_terms(case, sens: Sensitivities, c, r):
+    """Sums of the contingency violation intervals of eq. (slack-Sc) when the
+    contingency flows take the paper-mode interval (``paper_mode_flows``)."""
+    rating = case.rating if case.rating_ctg is None else case.rating_ctg
+    cent, rad = paper_mode_flows(case, sens, c, r)
+    v_lo, v_hi = viol_interval(cent - rad, cent + rad, rating[None, None, :])
+    return v_lo.sum(axis=(1, 2)), v_hi.sum(axis=(1, 2))
+
+
 def bound(case, sens: Optional[Sensitivities] = None, lo=None, hi=None, nthreads=None,
-          W=None) -> Bound:
+          W=None, mode: str = "tight") -> Bound:
     """IBP bound of f_ibp over each box (appendix eq. (ibp_f), eq. (penalized-objective)).
 
     hi = C_hi - G_lo - z_inj S_inj,lo - z_f (S_fb,lo + S_fc,lo)
     lo = C_lo - G_hi - z_inj S_inj,hi - z_f (S_fb,hi + S_fc,hi)
+
+    mode "tight": every contingency flow by the per-row rule (reading C9);
+    mode "paper": the paper's two-part interval of eq. (ctg flow matrix form).
     """
     if sens is None:
         sens = sensitivities(case)
@@ -381,7 +394,10 @@ def bound(case, sens: Optional[Sensitivities] = None, lo=None, hi=None, nthreads
     c, r = bus_box(case, lo, hi)
     inj_lo, inj_hi = imbalance_interval(case, sens.phi, c, r, W)
     fb_lo, fb_hi, _, _ = base_terms(case, sens.phi, c, r)
-    fc_lo, fc_hi, _, _, _ = ctg_terms(case, sens, c, r, nthreads=nthreads)
+    if mode == "paper":
+        fc_lo, fc_hi = paper_ctg_terms(case, sens, c, r)
+    else:
+        fc_lo, fc_hi, _, _, _ = ctg_terms(case, sens, c, r, nthreads=nthreads)
     nbox = lo.shape[0]
     out_lo = np.empty(nbox)
     out_hi = np.empty(nbox)

@@ -25,7 +25,7 @@ EXPORTED = (
     "ibp_case_sync", "ibp_case_info", "ibp_case_set_variant", "ibp_kernel_variants",
     "ibp_case_set_timing", "ibp_case_last_timing", "ibp_selftest_wait_timeout", "ibp_last_error",
     "ibp_status_string", "ibp_bound_noalloc", "ibp_case_set_screen", "ibp_case_last_live",
-    "ibp_case_set_reduction", "ibp_case_reduction",
+    "ibp_case_set_reduction", "ibp_case_reduction", "ibp_bound_paper",
 )
 
 
@@ -64,6 +64,8 @@ def lib():
         L.ibp_case_destroy.restype = None
         L.ibp_bound.argtypes = [P, I32, P, P, P, P, P, P, P, I32, P]
         L.ibp_bound.restype = ctypes.c_int
+        L.ibp_bound_paper.argtypes = [P, I32, P, P, P, P, P, I32, P]
+        L.ibp_bound_paper.restype = ctypes.c_int
         L.ibp_bound_backward.argtypes = [P, I32, P, P, P, P, P, P, I32, P]
         L.ibp_bound_backward.restype = ctypes.c_int
         L.ibp_bound_multi.argtypes = [I32, P, P, P, P, P, P, P, P]
@@ -163,6 +165,12 @@ def ibp_bound(handle, n_box, box_lo, box_hi, obj_lo, obj_hi, obj_err, flow_lo=No
     st = lib().ibp_bound(ctypes.c_void_p(handle), int(n_box), _ptr(box_lo), _ptr(box_hi),
                          _ptr(obj_lo), _ptr(obj_hi), _ptr(obj_err), _ptr(flow_lo), _ptr(flow_hi),
                          int(ptr_mode), stream)
+    _check(st)
+
+
+def ibp_bound_paper(handle, n_box, box_lo, box_hi, obj_lo, obj_hi, obj_err, ptr_mode=0, stream=None):
+    st = lib().ibp_bound_paper(ctypes.c_void_p(handle), int(n_box), _ptr(box_lo), _ptr(box_hi),
+                               _ptr(obj_lo), _ptr(obj_hi), _ptr(obj_err), int(ptr_mode), stream)
     _check(st)
 
 

@@ -96,6 +96,29 @@ class Case:
         _abi.ibp_bound(self._h, nb, lo, hi, olo, ohi, oerr, fl, fh, ptr_mode=0, stream=None)
         return (olo, ohi, oerr) + ((fl, fh) if flows else ())
 
+    def bound_paper(self, lo, hi, stream=None):
+        """The objective interval with the paper's two-part contingency
+        intervals (looser than ``bound``, O(n_ctg * n_line)); same argument
+        and return conventions as ``bound`` without flows."""
+        if _abi._is_cuda_tensor(lo):
+            import torch
+            lo = lo.contiguous().to(torch.float64)
+            hi = hi.contiguous().to(torch.float64)
+            nb = int(lo.shape[0]) if lo.dim() == 2 else 1
+            out = torch.empty((2, nb), dtype=torch.float64, device=lo.device)
+            err = torch.empty((nb, 2), dtype=torch.float64, device=lo.device)
+            s = stream if stream is not None else torch.cuda.current_stream(lo.device).cuda_stream
+            _abi.ibp_bound_paper(self._h, nb, lo, hi, out[0], out[1], err, ptr_mode=1, stream=s)
+            return out[0], out[1], err
+        lo = np.ascontiguousarray(np.atleast_2d(lo), np.float64)
+        hi = np.ascontiguousarray(np.atleast_2d(hi), np.float64)
+        if lo.shape != hi.shape or lo.shape[1] != self.n_dev:
+            raise ValueError(f"boxes must be [n_box, {self.n_dev}]")
+        nb = lo.shape[0]
+        olo, ohi, oerr = np.empty(nb), np.empty(nb), np.empty((nb, 2))
+        _abi.ibp_bound_paper(self._h, nb, lo, hi, olo, ohi, oerr, ptr_mode=0, stream=None)
+        return olo, ohi, oerr
+
     # ------------------------------------------------------------ adjoint
     def backward(self, lo, hi, grad_obj_hi, want_rating: bool = False, stream=None):
         """d loss / d box_lo, d box_hi (and d loss / d rating_ctg) of obj_hi."""

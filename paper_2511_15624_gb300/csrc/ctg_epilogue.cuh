@@ -93,9 +93,16 @@ __device__ __forceinline__ void pair_epilogue(const CtgArgs &a, int box, int l, 
 // partial-sum rows per tile: at most the largest warp count of any kernel
 constexpr int kPartRowsPerTile = 16;
 
+// n_terms: violations the thread summed into slo / shi in FP32 (directed);
+// those sums are within 2u n_terms of the exact sums, which the error
+// allowances take on here.
 __device__ __forceinline__ void write_warp_partials(const CtgArgs &a, int tile, int warp, int box,
-                                                    float slo, float shi, float whi, float wlo) {
+                                                    float slo, float shi, float whi, float wlo,
+                                                    int n_terms) {
     const int lane = threadIdx.x & 31;
+    const float g = 2.02f * kU * (float)n_terms;
+    whi = __fmaf_ru(g, slo, whi);  // obj_hi takes sum s_lo
+    wlo = __fmaf_ru(g, shi, wlo);  // obj_lo takes sum s_hi
     const double dlo = warp_sum_rd((double)slo);
     const double dhi = warp_sum_ru((double)shi);
     const double dwh = warp_sum_ru((double)whi);

@@ -787,21 +787,24 @@ static ibp_status ensure_class_ws(ibp_case *c) {
 // ----------------------------------------------------------------- bound
 static ibp_status enqueue_bound(ibp_case *c, int n_box, const double *lo, const double *hi,
                                 double *olo, double *ohi, double *oerr, float *flo, float *fhi,
-                                cudaStream_t s, bool record = false) {
+                                cudaStream_t s, bool record = false, bool paper = false) {
     ibp_status st = ensure_workspace(c, n_box);
     if (st != IBP_OK) return st;
     const CtgVariant *v = pick_variant(c, n_box);
     if (!v) return fail(IBP_EINVAL, "no kernel variant");
     const bool multi = n_box > 1;
     // the screen and the reduction leave the flows of the lines they drop unwritten
-    const bool reduced = c->reduce && c->has_reduction && !flo && c->n_ctg > 0;
-    const bool screened = (c->screen || reduced) && !flo && c->n_ctg > 0;
+    // paper mode: the two-part contingency intervals, no tight kernel
+    const bool reduced = !paper && c->reduce && c->has_reduction && !flo && c->n_ctg > 0;
+    const bool screened = !paper && (c->screen || reduced) && !flo && c->n_ctg > 0;
     c->last_screened = screened;
     // columns of the rows the contingency kernel streams
     const int n_w = reduced ? c->n_r_pad : c->n_a_pad;
     const int n_box_pad = (n_box + kBoxTile - 1) / kBoxTile * kBoxTile;
-    if ((!multi || screened) && !c->hat_l.p) CUDA_TRY(c->hat_l.alloc((size_t)c->n_line * c->n_a_pad));
-    if (!multi && !c->hat_k.p) CUDA_TRY(c->hat_k.alloc((size_t)std::max(c->n_ctg, 1) * c->n_a_pad));
+    if (!paper && (!multi || screened) && !c->hat_l.p)
+        CUDA_TRY(c->hat_l.alloc((size_t)c->n_line * c->n_a_pad));
+    if (!paper && !multi && !c->hat_k.p)
+        CUDA_TRY(c->hat_k.alloc((size_t)std::max(c->n_ctg, 1) * c->n_a_pad));
     if (reduced && (st = ensure_class_ws(c)) != IBP_OK) return st;
     CUDA_TRY(cudaMemsetAsync(c->err.p, 0, sizeof(int), s));
     if (multi) {
@@ -834,8 +837,8 @@ static ibp_status enqueue_bound(ibp_case *c, int n_box, const double *lo, const 
     bb.box_consts = c->box_consts.p;
     bb.gamma_base = rup_gamma((c->n_a_pad / 4 + 31) / 32, 2, 5);
     bb.line_c = c->line_c.p; bb.line_e = c->line_e.p; bb.line_R = c->line_R.p;
-    bb.hat_l = (multi || screened) ? nullptr : c->hat_l.p;
-    bb.hat_k = (multi || screened) ? nullptr : c->hat_k.p;
+    bb.hat_l = (multi || screened || paper) ? nullptr : c->hat_l.p;
+    bb.hat_k = (multi || screened || paper) ? nullptr : c->hat_k.p;
     bb.partials = c->part_base.p;
     bb.err = c->err.p;
     if (reduced) {
@@ -902,7 +905,15 @@ static ibp_status enqueue_bound(ibp_case *c, int n_box, const double *lo, const 
         ca.live = c->live.p;
         ca.n_live = c->n_live.p;
     }
-    if (ca.n_tiles > 0) {
+    if (paper) {
+        PaperArgs pa{};
+        pa.n_l = c->n_line; pa.n_c = c->n_ctg; pa.n_box = n_box;
+        pa.lodf = c->lodf.p; pa.ctg_line = c->ctg_line.p;
+        pa.line_c = c->line_c.p; pa.line_e = c->line_e.p; pa.line_R = c->line_R.p;
+        pa.box_consts = c->box_consts.p; pa.rate_up = c->rate_c_up.p; pa.rate_dn = c->rate_c_dn.p;
+        pa.gamma_base = bb.gamma_base; pa.partials = c->part_ctg.p;
+        CUDA_TRY(launch_paper(pa, s));
+    } else if (ca.n_tiles > 0) {
         CUtensorMap mL, mK, mR;
         std::string err;
         // rows of n_w columns: bus classes (reduced) or active buses
@@ -926,7 +937,8 @@ static ibp_status enqueue_bound(ibp_case *c, int n_box, const double *lo, const 
 
     AsmArgs aa{};
     aa.n_box = n_box; aa.n_dev = c->n_dev; aa.n_gen = c->n_gen;
-    aa.n_part_ctg = tiles_l * tiles_k * ca.warps_per_tile; aa.n_part_base = c->n_part_base;
+    aa.n_part_ctg = paper ? paper_partials_count(c->n_line, c->n_ctg) : tiles_l * tiles_k * ca.warps_per_tile;
+    aa.n_part_base = c->n_part_base;
     aa.part_stage = c->part_stage.p; aa.n_stage = kPartStages;
     aa.part_ctg = c->part_ctg.p; aa.part_base = c->part_base.p; aa.box_lo = lo; aa.box_hi = hi;
     aa.seg_ptr = c->seg_ptr.p; aa.slope = c->slope.p; aa.bkpt = c->bkpt.p;
@@ -965,10 +977,10 @@ static ibp_status check_boxes_host(const ibp_case *c, int n_box, const double *l
     return IBP_OK;
 }
 
-extern "C" ibp_status ibp_bound(ibp_case *c, int32_t n_box, const double *box_lo,
-                                const double *box_hi, double *obj_lo, double *obj_hi,
-                                double *obj_err, float *flow_lo, float *flow_hi, int32_t ptr_mode,
-                                void *cuda_stream) {
+static ibp_status bound_entry(ibp_case *c, int32_t n_box, const double *box_lo,
+                              const double *box_hi, double *obj_lo, double *obj_hi, double *obj_err,
+                              float *flow_lo, float *flow_hi, int32_t ptr_mode, void *cuda_stream,
+                              bool paper) {
     if (!c) return fail(IBP_EINVAL, "case is NULL");
     if (n_box < 0) return fail(IBP_EINVAL, "n_box must be >= 0");
     if (ptr_mode != 0 && ptr_mode != 1) return fail(IBP_EINVAL, "ptr_mode must be 0 or 1");
@@ -986,7 +998,8 @@ extern "C" ibp_status ibp_bound(ibp_case *c, int32_t n_box, const double *box_lo
     if (!guard.ok) return fail(IBP_ECUDA, "cannot select device %d", c->device);
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     if (ptr_mode == 1)
-        return enqueue_bound(c, n_box, box_lo, box_hi, obj_lo, obj_hi, obj_err, flow_lo, flow_hi, s);
+        return enqueue_bound(c, n_box, box_lo, box_hi, obj_lo, obj_hi, obj_err, flow_lo, flow_hi, s,
+                             false, paper);
 
     ibp_status st = ensure_workspace(c, n_box);
     if (st != IBP_OK) return st;
@@ -1002,7 +1015,7 @@ extern "C" ibp_status ibp_bound(ibp_case *c, int32_t n_box, const double *box_lo
     }
     double *dobj = c->obj.p;
     st = enqueue_bound(c, n_box, c->box_lo.p, c->box_hi.p, dobj, dobj + n_box, dobj + 2 * n_box,
-                       dflo, dfhi, s);
+                       dflo, dfhi, s, false, paper);
     if (st != IBP_OK) return st;
     CUDA_TRY(cudaMemcpyAsync(obj_lo, dobj, n_box * sizeof(double), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaMemcpyAsync(obj_hi, dobj + n_box, n_box * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -1015,6 +1028,21 @@ extern "C" ibp_status ibp_bound(ibp_case *c, int32_t n_box, const double *box_lo
     st = read_err_word(c);
     if (st != IBP_OK) return st;
     return ok();
+}
+
+extern "C" ibp_status ibp_bound(ibp_case *c, int32_t n_box, const double *box_lo,
+                                const double *box_hi, double *obj_lo, double *obj_hi,
+                                double *obj_err, float *flow_lo, float *flow_hi, int32_t ptr_mode,
+                                void *cuda_stream) {
+    return bound_entry(c, n_box, box_lo, box_hi, obj_lo, obj_hi, obj_err, flow_lo, flow_hi, ptr_mode,
+                       cuda_stream, false);
+}
+
+extern "C" ibp_status ibp_bound_paper(ibp_case *c, int32_t n_box, const double *box_lo,
+                                      const double *box_hi, double *obj_lo, double *obj_hi,
+                                      double *obj_err, int32_t ptr_mode, void *cuda_stream) {
+    return bound_entry(c, n_box, box_lo, box_hi, obj_lo, obj_hi, obj_err, nullptr, nullptr, ptr_mode,
+                       cuda_stream, true);
 }
 
 static ibp_status ensure_bwd_workspace(ibp_case *c, int n_box) {

@@ -121,6 +121,21 @@ struct ScreenArgs {
     int n_w;                 // row width (a multiple of 32)
 };
 
+// Paper-mode objective: every contingency flow takes the two-part interval
+// c_kl +- (R_l + |L[l,k]| R_k) (eq. (ctg flow matrix form) propagated as the
+// paper does), and the violation sums of eq. (slack-Sc) go to partial rows
+// [gridDim.x * gridDim.y][n_box][kPartVals].
+struct PaperArgs {
+    int n_l, n_c, n_box;
+    const float *lodf;       // [n_c][n_l]
+    const int *ctg_line;     // [n_c]
+    const float *line_c, *line_e, *line_R;  // [n_box][n_l]
+    const float *box_consts;                // [n_box][4]
+    const float *rate_up, *rate_dn;         // contingency ratings
+    float gamma_base;        // relative excess of the base radius sums R~
+    double *partials;
+};
+
 // Radius of each bus class (the active buses whose PTDF columns coincide on
 // every non-bridge line): rcls[j] = RU(sum of rbus over the class members).
 struct ClsArgs {
@@ -205,6 +220,8 @@ void multi_tile_shape(int *BL, int *BK, int *CH);
 cudaError_t launch_assemble(const AsmArgs &a, cudaStream_t s);
 cudaError_t launch_screen(const ScreenArgs &a, int num_sms, cudaStream_t s);
 cudaError_t launch_class_radius(const ClsArgs &a, cudaStream_t s);
+int paper_partials_count(int n_l, int n_c);
+cudaError_t launch_paper(const PaperArgs &a, cudaStream_t s);
 cudaError_t launch_backward(const BwdArgs &a, cudaStream_t s);
 cudaError_t launch_wait_selftest(int *flag, unsigned long long limit_ns, cudaStream_t s);
 cudaError_t launch_or_err(int *dst, const int *src, cudaStream_t s);

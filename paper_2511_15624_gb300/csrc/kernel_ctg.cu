@@ -295,7 +295,7 @@ __global__ void __launch_bounds__(WL * WK * 32, MINB)
                     pair_epilogue(a, 0, l, k, Lr[i][j], __fadd_ru(a3, acc2[i][j]), slo, shi, whi, wlo);
                 }
             }
-        write_warp_partials(a, tile, warp, 0, slo, shi, whi, wlo);
+        write_warp_partials(a, tile, warp, 0, slo, shi, whi, wlo, ML * MK);
     }
     // Every warp gets here (all waits are bounded).  After an abort, copies
     // may still be in flight: wait (bounded) for the last one of each stage.
@@ -606,7 +606,7 @@ __device__ __forceinline__ void multi_body(const Plan &P, unsigned long long wai
             }
             // partial rows per item: kWarpsHalf (the warp's place in its
             // half; each box belongs to exactly one half)
-            write_warp_partials(a, tlk, wq, box, slo, shi, whi, wlo);
+            write_warp_partials(a, tlk, wq, box, slo, shi, whi, wlo, ML);
         }
     }
     __syncthreads();

@@ -156,6 +156,102 @@ cudaError_t launch_class_radius(const ClsArgs &a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// Paper-mode objective terms.  Per pair, the certified enclosure of the
+// two-part interval is [c~ - rho, c~ + rho] with rho = RU(e_c + rp) and
+// rp = RU((1 + 4u) m + 2 eta_r (1 + |L~|)), m = RU(R~_l + |L~| R~_k), as in the
+// screen above.  Each violation is within
+//   w = (gamma_base + 10u) m + 2 e_c + u rating + 4 eta_r (1 + |L~|)
+// of its exact paper-mode value (R~ exceeds the exact radius sum by at most
+// (gamma_base + 2.01u) of it plus eta, L~ is within u of L).  One thread per
+// line and block of kScreenK contingencies; FP32 directed per thread, FP64
+// directed per block.
+int paper_partials_count(int n_l, int n_c) {
+    return ((n_l + kScreenThreads - 1) / kScreenThreads) * ((n_c + kScreenK - 1) / kScreenK);
+}
+
+__global__ void __launch_bounds__(kScreenThreads) k_paper(const PaperArgs a) {
+    const int l = blockIdx.x * kScreenThreads + threadIdx.x;
+    const int j = blockIdx.z;
+    const int k0 = blockIdx.y * kScreenK, k1 = min(k0 + kScreenK, a.n_c);
+    float slo = 0.0f, shi = 0.0f, whi = 0.0f, wlo = 0.0f;
+    if (l < a.n_l) {
+        const size_t ob = (size_t)j * a.n_l;
+        const float cl = __ldg(&a.line_c[ob + l]), el = __ldg(&a.line_e[ob + l]);
+        const float Rl = __ldg(&a.line_R[ob + l]);
+        const float eta_r = __ldg(&a.box_consts[(size_t)j * 4]);
+        const float eta_c = __ldg(&a.box_consts[(size_t)j * 4 + 1]);
+        const float rup = __ldg(&a.rate_up[l]), rdn = __ldg(&a.rate_dn[l]);
+        for (int k = k0; k < k1; ++k) {
+            const int kl = __ldg(&a.ctg_line[k]);
+            if (kl == l) continue;  // the outaged line carries exactly nothing
+            const float Lt = __ldg(&a.lodf[(size_t)k * a.n_l + l]);
+            const float ck = __ldg(&a.line_c[ob + kl]), ek = __ldg(&a.line_e[ob + kl]);
+            const float Rk = __ldg(&a.line_R[ob + kl]);
+            const float aL = fabsf(Lt);
+            const float one_l = __fadd_ru(1.0f, aL);
+            const float eta = __fmul_ru(eta_r, one_l);
+            float c, ec;
+            pair_centre(Lt, cl, ck, el, ek, eta_c, one_l, c, ec);
+            const float m = __fmaf_ru(aL, Rk, Rl);
+            float rp = __fmaf_ru(4.0f * kU, m, m);
+            rp = __fmaf_ru(2.0f, eta, rp);
+            const float rho = __fadd_ru(rp, ec);
+            float alo, ahi;
+            abs_interval(__fsub_rd(c, rho), __fadd_ru(c, rho), alo, ahi);
+            const float vlo = fmax0(__fsub_rd(alo, rup));
+            const float vhi = fmax0(__fsub_ru(ahi, rdn));
+            slo = __fadd_rd(slo, vlo);
+            shi = __fadd_ru(shi, vhi);
+            if (vhi > 0.0f) {
+                float w = __fmaf_ru(a.gamma_base + 10.0f * kU, m, __fmul_ru(2.0f, ec));
+                w = __fmaf_ru(kU, rup, w);
+                w = __fmaf_ru(4.0f, eta, w);
+                wlo = __fadd_ru(wlo, w);
+                if (__fadd_ru(__fsub_ru(alo, rdn), w) > 0.0f) whi = __fadd_ru(whi, w);
+            }
+        }
+    }
+    // the FP32 directed sums of up to kScreenK terms are within 2u kScreenK
+    // of the exact sums
+    const float g = 2.02f * kU * (float)kScreenK;
+    whi = __fmaf_ru(g, slo, whi);
+    wlo = __fmaf_ru(g, shi, wlo);
+    double d0 = warp_sum_rd((double)slo), d1 = warp_sum_ru((double)shi);
+    double d2 = warp_sum_ru((double)whi), d3 = warp_sum_ru((double)wlo);
+    __shared__ double sh[kScreenThreads / 32][4];
+    const int w = threadIdx.x >> 5;
+    if ((threadIdx.x & 31) == 0) {
+        sh[w][0] = d0;
+        sh[w][1] = d1;
+        sh[w][2] = d2;
+        sh[w][3] = d3;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double r0 = 0.0, r1 = 0.0, r2 = 0.0, r3 = 0.0;
+        for (int i = 0; i < kScreenThreads / 32; ++i) {
+            r0 = __dadd_rd(r0, sh[i][0]);
+            r1 = __dadd_ru(r1, sh[i][1]);
+            r2 = __dadd_ru(r2, sh[i][2]);
+            r3 = __dadd_ru(r3, sh[i][3]);
+        }
+        const size_t row = (size_t)blockIdx.y * gridDim.x + blockIdx.x;
+        double *p = a.partials + (row * a.n_box + j) * kPartVals;
+        p[0] = r0;
+        p[1] = r1;
+        p[2] = r2;
+        p[3] = r3;
+    }
+}
+
+cudaError_t launch_paper(const PaperArgs &a, cudaStream_t s) {
+    if (a.n_l <= 0 || a.n_c <= 0 || a.n_box <= 0) return cudaSuccess;
+    const dim3 g((a.n_l + kScreenThreads - 1) / kScreenThreads, (a.n_c + kScreenK - 1) / kScreenK,
+                 a.n_box);
+    k_paper<<<g, kScreenThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_screen(const ScreenArgs &a, int num_sms, cudaStream_t s) {
     cudaError_t e = cudaMemsetAsync(a.live_flag, 0, (size_t)a.n_l * sizeof(int), s);
     if (e != cudaSuccess) return e;

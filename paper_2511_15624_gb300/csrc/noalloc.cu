@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(256, 1)
                 if (l < a.n_l && k < a.n_c)
                     pair_epilogue(a, 0, l, k, Lr[i][j], __fadd_ru(acc3[i][j], acc2[i][j]), slo, shi, whi, wlo);
             }
-        write_warp_partials(a, tile, warp, 0, slo, shi, whi, wlo);
+        write_warp_partials(a, tile, warp, 0, slo, shi, whi, wlo, ML * MK);
     }
 }
 

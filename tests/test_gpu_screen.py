@@ -227,3 +227,32 @@ def test_reduction_multi_box_and_adjoint(P):
     tol = 1e-6 * (1 + np.abs(o_lo).max() + np.abs(o_hi).max())
     np.testing.assert_allclose(a_lo, o_lo, rtol=0, atol=tol)
     np.testing.assert_allclose(a_hi, o_hi, rtol=0, atol=tol)
+
+
+@pytest.mark.parametrize("which", ["cfg1", "cfg2", "multi", "point"])
+def test_paper_mode_bound(P, which):
+    """ibp_bound_paper against the oracle's paper-mode bound (the paper's own
+    two-part contingency intervals): sound, within 1e-5 and its own error
+    bound; it encloses the tight bound of ibp_bound, and equals it at a point
+    box, where both radii vanish."""
+    if which == "multi":
+        case = time_index_boxes(make_config(1), 20, seed=9)
+        sens = _sens(1, make_config(1))
+        lo, hi = case.box_lo, case.box_hi
+    else:
+        cfg = 2 if which == "cfg2" else 1
+        case = make_config(cfg)
+        sens = _sens(cfg, case)
+        lo, hi = case.box_lo, case.box_hi
+        if which == "point":
+            lo = hi = 0.5 * (case.box_lo + case.box_hi)
+    gpu = P.Case(case, device=0)
+    plo, phi, perr = gpu.bound_paper(lo, hi)
+    ref = O.bound(case, sens, lo=lo, hi=hi, mode="paper")
+    check_objective(plo, phi, perr, ref)
+    tlo, thi, terr = gpu.bound(lo, hi)
+    assert np.all(phi >= thi - terr[:, 0]) and np.all(plo <= tlo + terr[:, 1])
+    if which == "point":
+        assert np.all(np.abs(phi - thi) <= perr[:, 0] + terr[:, 0])
+    else:
+        assert np.all(phi > thi)

@@ -316,6 +316,27 @@ def test_screen_keeps_every_violating_line(cases):
     assert 0 < want.sum() < c.n_line
 
 
+def test_paper_mode_bound_encloses_tight_and_meets_it_at_points(cases):
+    """The paper-mode objective interval contains the tight one (its flow
+    radii are larger), and at a point box both radii vanish so the two bounds
+    coincide."""
+    for cfg in (0, 1):
+        c = cases(cfg)
+        s = O.sensitivities(c)
+        tight = O.bound(c, s)
+        paper = O.bound(c, s, mode="paper")
+        scale = np.abs(tight.terms["costs"]).sum() + 1e3 * tight.terms["fc"][1].sum()
+        assert np.all(paper.hi >= tight.hi - 1e-9 * scale)
+        assert np.all(paper.lo <= tight.lo + 1e-9 * scale)
+        mid = 0.5 * (c.box_lo + c.box_hi)
+        tp = O.bound(c, s, lo=mid, hi=mid)
+        pp = O.bound(c, s, lo=mid, hi=mid, mode="paper")
+        np.testing.assert_allclose(pp.hi, tp.hi, rtol=1e-9)
+        np.testing.assert_allclose(pp.lo, tp.lo, rtol=1e-9)
+    # the root box of the 118-bus case: paper mode is strictly looser
+    assert paper.hi[0] > tight.hi[0]
+
+
 def test_inclusion_monotone(cases):
     c = cases(1)
     s = O.sensitivities(c)
