@@ -1,6 +1,6 @@
 """GPU vs oracle parity of the certified bound (calls go through the C ABI).
 
-Tolerances (written here, derived in the design doc):
+Tolerances (derived from the outward-rounding error analysis of the kernels):
 * soundness: the GPU interval must contain the oracle's, up to the FP64
   difference between the two independent sensitivity builds, 1e-9 of the
   operand scale;
