@@ -287,6 +287,12 @@ ibp_status ibp_case_reduction(const ibp_case *c, int32_t *class_of_active, int32
 ibp_status ibp_case_set_timing(ibp_case *c, int32_t enable);
 ibp_status ibp_case_last_timing(ibp_case *c, float *ms, int32_t n);
 
+/* Allocation-failure hook for tests: from this call on, every device buffer
+ * the library allocates that is larger than `bytes` fails as if the device
+ * were out of memory (the call returns IBP_ENOMEM and leaves the case as it
+ * was); 0 removes the limit.  Process-wide.  No counterpart in the paper. */
+ibp_status ibp_set_alloc_limit(int64_t bytes);
+
 /* Bounded-wait self test: launches one kernel that waits on an mbarrier that
  * no thread arrives at, with a limit of limit_us microseconds; returns
  * IBP_ETIMEOUT when the wait ran out and the kernel returned (expected), or

@@ -25,7 +25,7 @@ EXPORTED = (
     "ibp_case_sync", "ibp_case_info", "ibp_case_set_variant", "ibp_kernel_variants",
     "ibp_case_set_timing", "ibp_case_last_timing", "ibp_selftest_wait_timeout", "ibp_last_error",
     "ibp_status_string", "ibp_bound_noalloc", "ibp_case_set_screen", "ibp_case_last_live",
-    "ibp_case_set_reduction", "ibp_case_reduction", "ibp_bound_paper",
+    "ibp_case_set_reduction", "ibp_case_reduction", "ibp_bound_paper", "ibp_set_alloc_limit",
 )
 
 
@@ -64,6 +64,8 @@ def lib():
         L.ibp_case_destroy.restype = None
         L.ibp_bound.argtypes = [P, I32, P, P, P, P, P, P, P, I32, P]
         L.ibp_bound.restype = ctypes.c_int
+        L.ibp_set_alloc_limit.argtypes = [ctypes.c_int64]
+        L.ibp_set_alloc_limit.restype = ctypes.c_int
         L.ibp_bound_paper.argtypes = [P, I32, P, P, P, P, P, I32, P]
         L.ibp_bound_paper.restype = ctypes.c_int
         L.ibp_bound_backward.argtypes = [P, I32, P, P, P, P, P, P, I32, P]
@@ -166,6 +168,10 @@ def ibp_bound(handle, n_box, box_lo, box_hi, obj_lo, obj_hi, obj_err, flow_lo=No
                          _ptr(obj_lo), _ptr(obj_hi), _ptr(obj_err), _ptr(flow_lo), _ptr(flow_hi),
                          int(ptr_mode), stream)
     _check(st)
+
+
+def ibp_set_alloc_limit(nbytes: int):
+    _check(lib().ibp_set_alloc_limit(int(nbytes)))
 
 
 def ibp_bound_paper(handle, n_box, box_lo, box_hi, obj_lo, obj_hi, obj_err, ptr_mode=0, stream=None):

@@ -6,6 +6,7 @@
 #include <cusolverDn.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -58,6 +59,10 @@ struct DeviceGuard {
     }
 };
 
+// Test hook: device allocations larger than this many bytes fail as if the
+// device were out of memory (0: no limit).  See ibp_set_alloc_limit.
+static std::atomic<long long> g_alloc_limit{0};
+
 template <class T>
 struct DevBuf {
     T *p = nullptr;
@@ -65,6 +70,8 @@ struct DevBuf {
     cudaError_t alloc(size_t count) {
         free();
         if (count == 0) count = 1;
+        const long long lim = g_alloc_limit.load();
+        if (lim > 0 && (long long)(count * sizeof(T)) > lim) return cudaErrorMemoryAllocation;
         cudaError_t e = cudaMalloc(&p, count * sizeof(T));
         if (e == cudaSuccess) n = count;
         else p = nullptr;
@@ -748,6 +755,10 @@ static ibp_status ensure_workspace(ibp_case *c, int n_box) {
     if (n_box <= c->cap_box) return IBP_OK;
     const int cap = std::max(n_box, 1);
     const size_t na = c->n_a_pad;
+    // buffers move from here on: a failure part-way leaves cap_box = 0, so the
+    // next call allocates every buffer again
+    c->cap_box = 0;
+    ++c->ws_gen;
     CUDA_TRY(c->box_lo.alloc((size_t)cap * c->n_dev));
     CUDA_TRY(c->box_hi.alloc((size_t)cap * c->n_dev));
     CUDA_TRY(c->obj.alloc((size_t)cap * 4));
@@ -764,7 +775,7 @@ static ibp_status ensure_workspace(ibp_case *c, int n_box) {
     CUDA_TRY(c->part_stage.alloc((size_t)kPartStages * cap * kPartVals));
     const int cap_pad = (cap + kBoxTile - 1) / kBoxTile * kBoxTile;
     CUDA_TRY(c->rbus_t.alloc(na * cap_pad));
-    if (!c->live.p) {
+    if (!c->live.p || !c->live_flag.p || !c->n_live.p) {
         CUDA_TRY(c->live_flag.alloc(std::max(c->n_line, 1)));
         CUDA_TRY(c->live.alloc(std::max(c->n_line, 1)));
         CUDA_TRY(c->n_live.alloc(1));
@@ -776,8 +787,9 @@ static ibp_status ensure_workspace(ibp_case *c, int n_box) {
 
 // class radii of the reduction, sized like the other per-box buffers
 static ibp_status ensure_class_ws(ibp_case *c) {
-    if (c->rcls.n >= (size_t)c->cap_box * c->n_r_pad) return IBP_OK;
     const size_t cap_pad = (size_t)(c->cap_box + kBoxTile - 1) / kBoxTile * kBoxTile;
+    if (c->rcls.n >= (size_t)c->cap_box * c->n_r_pad && c->rcls_t.n >= cap_pad * c->n_r_pad)
+        return IBP_OK;
     CUDA_TRY(c->rcls.alloc((size_t)c->cap_box * c->n_r_pad));
     CUDA_TRY(c->rcls_t.alloc(cap_pad * c->n_r_pad));
     ++c->ws_gen;
@@ -1048,6 +1060,7 @@ extern "C" ibp_status ibp_bound_paper(ibp_case *c, int32_t n_box, const double *
 static ibp_status ensure_bwd_workspace(ibp_case *c, int n_box) {
     if (n_box <= c->bwd_cap_box) return IBP_OK;
     const int cap = std::max(n_box, 1);
+    c->bwd_cap_box = 0;  // a failure part-way makes the next call start over
     // active-pair list: about 16M entries (256 MB) shared by the boxes
     const long long pairs = (long long)c->n_ctg * c->n_line + c->n_line;
     c->act_cap = (int)std::max<long long>(4096, std::min<long long>(pairs, (16ll << 20) / cap));
@@ -1443,6 +1456,12 @@ extern "C" ibp_status ibp_case_set_variant(ibp_case *c, int32_t variant) {
     if (!c) return fail(IBP_EINVAL, "case is NULL");
     if (variant != 0 && !ctg_variant_by_id(variant)) return fail(IBP_EINVAL, "unknown variant %d", variant);
     c->variant = variant;
+    return ok();
+}
+
+extern "C" ibp_status ibp_set_alloc_limit(int64_t bytes) {
+    if (bytes < 0) return fail(IBP_EINVAL, "bytes must be >= 0");
+    g_alloc_limit.store(bytes);
     return ok();
 }
 
