@@ -15,7 +15,9 @@ from typing import Optional
 import numpy as np
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "_lib", "libibp_gb300.so")
+# IBP_LIB=check loads the checked build (index guards; see build.py)
+LIB_PATH = os.path.join(_PKG, "_lib", "libibp_gb300_check.so" if os.environ.get("IBP_LIB") == "check"
+                        else "libibp_gb300.so")
 
 IBP_OK, IBP_EINVAL, IBP_EISLAND, IBP_ESINGULAR, IBP_ENOMEM, IBP_ECUDA, IBP_ETIMEOUT, \
     IBP_EUNSOUND, IBP_ENOTSUP = range(9)

@@ -10,6 +10,19 @@
 
 namespace ibp {
 
+// Index guards.  In a checked build (-DIBP_CHECK) a failed guard records
+// kErrBounds in the call's error word and the caller skips the access; other
+// builds compile the guards to `true`.
+__device__ __forceinline__ bool idx_ok(bool cond, int *err) {
+    if (!cond) atomicOr(err, kErrBounds);
+    return cond;
+}
+#ifdef IBP_CHECK
+#define IBP_IDX_OK(cond, err) ::ibp::idx_ok((cond), (err))
+#else
+#define IBP_IDX_OK(cond, err) true
+#endif
+
 // unit roundoff of FP32 round-to-nearest, 2^-24
 constexpr float kU = 5.9604644775390625e-08f;
 

@@ -27,6 +27,7 @@ __device__ __forceinline__ void pair_epilogue(const CtgArgs &a, int box, int l, 
                                               float A, float &slo_acc, float &shi_acc,
                                               float &whi_acc, float &wlo_acc) {
     const int kl = __ldg(&a.ctg_line[k]);
+    if (!IBP_IDX_OK(kl >= 0 && kl < a.n_l && l >= 0 && l < a.n_l && box < a.n_box, a.err)) return;
     const size_t ob = (size_t)box * a.n_l;
     const float cl = __ldg(&a.line_c[ob + l]), ck = __ldg(&a.line_c[ob + kl]);
     const float el = __ldg(&a.line_e[ob + l]), ek = __ldg(&a.line_e[ob + kl]);
@@ -107,7 +108,8 @@ __device__ __forceinline__ void write_warp_partials(const CtgArgs &a, int tile, 
     const double dhi = warp_sum_ru((double)shi);
     const double dwh = warp_sum_ru((double)whi);
     const double dwl = warp_sum_ru((double)wlo);
-    if (lane == 0) {
+    if (lane == 0 &&
+        IBP_IDX_OK(a.part_rows_cap <= 0 || tile * a.warps_per_tile + warp < a.part_rows_cap, a.err)) {
         double *p = a.partials + (((size_t)tile * a.warps_per_tile + warp) * a.n_box + box) * kPartVals;
         p[0] = dlo;
         p[1] = dhi;

@@ -880,6 +880,7 @@ static ibp_status enqueue_bound(ibp_case *c, int n_box, const double *lo, const 
         sa.rows = c->hat_l.p;
         sa.hat_k = multi ? nullptr : c->hat_k.p;
         sa.n_w = n_w;
+        sa.err = c->err.p;
         CUDA_TRY(launch_screen(sa, c->num_sms, s));
     }
     if (c->timing) CUDA_TRY(cudaEventRecord(c->ev[3], s));
@@ -908,6 +909,7 @@ static ibp_status enqueue_bound(ibp_case *c, int n_box, const double *lo, const 
     ca.flow_lo = flo; ca.flow_hi = fhi; ca.partials = c->part_ctg.p; ca.err = c->err.p;
     ca.wait_ns = 2000000000ull;
     ca.warps_per_tile = ctg_warps(*v);
+    ca.part_rows_cap = (int)max_part_rows(c);
     if (record) {
         ca.act_count = c->act_count.p;
         ca.act_list = c->act_list.p;
@@ -923,7 +925,7 @@ static ibp_status enqueue_bound(ibp_case *c, int n_box, const double *lo, const 
         pa.lodf = c->lodf.p; pa.ctg_line = c->ctg_line.p;
         pa.line_c = c->line_c.p; pa.line_e = c->line_e.p; pa.line_R = c->line_R.p;
         pa.box_consts = c->box_consts.p; pa.rate_up = c->rate_c_up.p; pa.rate_dn = c->rate_c_dn.p;
-        pa.gamma_base = bb.gamma_base; pa.partials = c->part_ctg.p;
+        pa.gamma_base = bb.gamma_base; pa.partials = c->part_ctg.p; pa.err = c->err.p;
         CUDA_TRY(launch_paper(pa, s));
     } else if (ca.n_tiles > 0) {
         CUtensorMap mL, mK, mR;
@@ -974,6 +976,7 @@ static ibp_status read_err_word(ibp_case *c) {
     if (e & kErrBadBox) return fail(IBP_EINVAL, "a box has lo > hi or a non-finite entry");
     if (e & kErrOverflow)
         return fail(IBP_ENOMEM, "too many active pairs for the adjoint's list; call with fewer boxes");
+    if (e & kErrBounds) return fail(IBP_EUNSOUND, "an index guard of the checked build failed");
     return IBP_OK;
 }
 
@@ -1194,6 +1197,7 @@ static CtgArgs multi_args(const ibp_case *c, int n_box, int BL, int BK, int CH, 
     ca.flow_lo = nullptr; ca.flow_hi = nullptr; ca.partials = c->part_ctg.p; ca.err = c->err.p;
     ca.wait_ns = 2000000000ull;
     ca.warps_per_tile = 8;
+    ca.part_rows_cap = (int)max_part_rows(c);
     if (reduced) {
         ca.live = c->nb_list.p;
         ca.n_live = c->nb_count.p;

@@ -16,6 +16,7 @@ namespace ibp {
 constexpr int kErrTimeout = 1;
 constexpr int kErrBadBox = 2;
 constexpr int kErrOverflow = 4;  // active-pair list of the adjoint ran out of room
+constexpr int kErrBounds = 8;    // an index guard of a checked build (-DIBP_CHECK) failed
 // values per partial-sum row: sum s_lo, sum s_hi, error of obj_hi, error of obj_lo
 constexpr int kPartVals = 4;
 
@@ -89,6 +90,7 @@ struct CtgArgs {
     int *act_count;
     int4 *act_list;
     int act_cap;
+    int part_rows_cap;       // rows the partials buffer holds (index guard of checked builds)
     // line screen (null: all n_l lines): line tile rows index the compacted
     // list live[0 .. *n_live) of lines that can carry a violation
     const int *live;
@@ -119,6 +121,7 @@ struct ScreenArgs {
     float *rows;             // [n_l][n_w]
     float *hat_k;            // [n_c][n_w] or null
     int n_w;                 // row width (a multiple of 32)
+    int *err;
 };
 
 // Paper-mode objective: every contingency flow takes the two-part interval
@@ -134,6 +137,7 @@ struct PaperArgs {
     const float *rate_up, *rate_dn;         // contingency ratings
     float gamma_base;        // relative excess of the base radius sums R~
     double *partials;
+    int *err;
 };
 
 // Radius of each bus class (the active buses whose PTDF columns coincide on

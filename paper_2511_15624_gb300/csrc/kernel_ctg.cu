@@ -156,7 +156,8 @@ __global__ void __launch_bounds__(WL * WK * 32, MINB)
 #pragma unroll
         for (int i = 0; i < ML; ++i) {
             const int lq = l0 + tl + TL * i;
-            const int l = lq < n_ll ? (a.live ? __ldg(&a.live[lq]) : lq) : -1;
+            int l = lq < n_ll ? (a.live ? __ldg(&a.live[lq]) : lq) : -1;
+            if (l >= 0 && !IBP_IDX_OK(l < a.n_l, a.err)) l = -1;
 #pragma unroll
             for (int j = 0; j < MK; ++j) {
                 const int k = k0 + tk + TK * j;
@@ -481,7 +482,8 @@ __device__ __forceinline__ void multi_body(const Plan &P, unsigned long long wai
 #pragma unroll
         for (int i = 0; i < ML; ++i) {
             const int lq = l0 + tl + TL * i;
-            const int l = lq < n_ll ? (a.live ? __ldg(&a.live[lq]) : lq) : -1;
+            int l = lq < n_ll ? (a.live ? __ldg(&a.live[lq]) : lq) : -1;
+            if (l >= 0 && !IBP_IDX_OK(l < n_l, a.err)) l = -1;
             Lr[i] = (l >= 0 && k < n_c) ? __ldg(&a.lodf[(size_t)k * n_l + l]) : 0.0f;
         }
         float acc1[ML][kMBT], acc2[ML][kMBT];

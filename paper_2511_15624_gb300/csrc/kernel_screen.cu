@@ -53,6 +53,7 @@ __global__ void __launch_bounds__(kScreenThreads) k_screen(const ScreenArgs a) {
         for (int k = k0; k < k1; ++k) {
             const int kl = __ldg(&a.ctg_line[k]);
             if (kl == l) continue;  // the outaged line carries exactly nothing
+            if (!IBP_IDX_OK(kl >= 0 && kl < a.n_l, a.err)) continue;
             const float Lt = __ldg(&a.lodf[(size_t)k * a.n_l + l]);
             const float ck = __ldg(&a.line_c[ob + kl]), ek = __ldg(&a.line_e[ob + kl]);
             const float Rk = __ldg(&a.line_R[ob + kl]);
@@ -118,6 +119,7 @@ __global__ void __launch_bounds__(256) k_gather_live_rows(const ScreenArgs a) {
     const float4 *rr = reinterpret_cast<const float4 *>(a.radius);
     for (int i = gw; i < n_rows; i += nw) {
         const int row = i < n ? a.live[i] : a.ctg_line[i - n];
+        if (!IBP_IDX_OK(row >= 0 && row < a.n_l, a.err)) continue;
         const float4 *src = reinterpret_cast<const float4 *>(a.src + (size_t)row * a.n_w);
         float *d = i < n ? a.rows + (size_t)i * a.n_w : a.hat_k + (size_t)(i - n) * a.n_w;
         float4 *dst = reinterpret_cast<float4 *>(d);
@@ -184,6 +186,7 @@ __global__ void __launch_bounds__(kScreenThreads) k_paper(const PaperArgs a) {
         for (int k = k0; k < k1; ++k) {
             const int kl = __ldg(&a.ctg_line[k]);
             if (kl == l) continue;  // the outaged line carries exactly nothing
+            if (!IBP_IDX_OK(kl >= 0 && kl < a.n_l, a.err)) continue;
             const float Lt = __ldg(&a.lodf[(size_t)k * a.n_l + l]);
             const float ck = __ldg(&a.line_c[ob + kl]), ek = __ldg(&a.line_e[ob + kl]);
             const float Rk = __ldg(&a.line_R[ob + kl]);
