@@ -899,10 +899,10 @@ static ibp_status enqueue_bound(ibp_case *c, int n_box, const double *lo, const 
     // round-up adds per radius sum: level 1 within a chunk (one per bus, or a
     // depth-2 tree per 4 buses plus one add), level 2 over 256/CH chunks, level 3
     {
-        const bool tree = !multi && v->id >= 6;
-        // packed two-lane sums (12, 13): one more add to join the lanes
-        const bool packed = !multi && (v->id == 12 || v->id == 13 || v->id == 15 || v->id == 16);
-        const long n1 = tree ? v->CH / 4 + 2 + (packed ? 1 : 0) : v->CH;
+        const bool tree = !multi && v->body >= 1;
+        // two level-1 sums per pair (packed body): one more add to join them
+        const bool two_sums = !multi && v->body >= 2;
+        const long n1 = tree ? v->CH / 4 + 2 + (two_sums ? 1 : 0) : v->CH;
         const long n2 = 256 / v->CH;
         ca.gamma = rup_gamma(n1, n2, (n_chunks + n2 - 1) / n2);
     }

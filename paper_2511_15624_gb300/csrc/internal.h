@@ -196,6 +196,9 @@ struct CtgVariant {
     int batched;     // 0: one-box scaled kernel, 1: multi-box kernel
     int BL, BK, CH, ST;
     int boxes_per_thread;
+    // one-box inner sum: 0 one round-up add per bus, 1 a 4-bus add tree,
+    // 2 packed two-lane sums (-1: multi-box)
+    int body;
     const char *name;
 };
 

@@ -718,29 +718,29 @@ void multi_tile_shape(int *BL, int *BK, int *CH) {
 // ---------------------------------------------------------------------------
 // Variant table and launcher
 // ---------------------------------------------------------------------------
-// {id, batched, BL, BK, CH, ST, boxes per thread, name}; warps and the loop
+// {id, batched, BL, BK, CH, ST, boxes per thread, body, name}; warps and the loop
 // body are fixed per id in launch_ctg / ctg_warps.
 static const CtgVariant kVariants[] = {
-    {1, 0, 128, 64, 32, 4, 1, "8 warps, 8x4/thread, 32-bus chunks, 4 stages, 1 add per bus"},
-    {3, 0, 128, 64, 32, 4, 1, "16 warps, 4x4/thread, 32-bus chunks, 4 stages, 1 add per bus"},
-    {6, 0, 128, 64, 32, 4, 1, "8 warps, 8x4/thread, 32-bus chunks, 4 stages, 4-bus add tree"},
-    {7, 0, 128, 64, 64, 3, 1, "8 warps, 8x4/thread, 64-bus chunks, 3 stages, 4-bus add tree"},
-    {8, 0, 128, 64, 32, 4, 1, "16 warps, 4x4/thread, 32-bus chunks, 4 stages, 4-bus add tree"},
-    {9, 0, 128, 64, 64, 3, 1, "16 warps, 4x4/thread, 64-bus chunks, 3 stages, 4-bus add tree"},
-    {10, 0, 64, 64, 32, 4, 1, "2 CTAs/SM x 8 warps, 4x4/thread, 32-bus chunks, 4 stages, tree"},
-    {11, 0, 64, 64, 64, 2, 1, "2 CTAs/SM x 8 warps, 4x4/thread, 64-bus chunks, 2 stages, tree"},
-    {12, 0, 128, 64, 64, 3, 1, "16 warps, 4x4/thread, 64-bus chunks, 3 stages, packed two-lane sums"},
-    {13, 0, 128, 64, 32, 4, 1, "16 warps, 4x4/thread, 32-bus chunks, 4 stages, packed two-lane sums"},
-    {15, 0, 64, 64, 32, 4, 1, "2 CTAs/SM x 8 warps, 4x4/thread, 32-bus chunks, 4 stages, packed"},
-    {16, 0, 64, 64, 64, 2, 1, "2 CTAs/SM x 8 warps, 4x4/thread, 64-bus chunks, 2 stages, packed"},
-    {20, 1, 64, 16, 32, 4, 16, "multi-box 64x16x16, 8 warps, 4 lines x 16 boxes/thread, 4 stages"},
-    {21, 1, 64, 16, 32, 6, 16, "multi-box 64x16x16, 8 warps, 4 lines x 16 boxes/thread, 6 stages"},
-    {22, 1, 64, 16, 32, 4, 8, "multi-box 64x16x16, 16 warps, 4 lines x 8 boxes/thread, 4 stages"},
-    {23, 1, 64, 16, 32, 6, 8, "multi-box 64x16x16, 16 warps, 4 lines x 8 boxes/thread, 6 stages"},
-    {24, 1, 64, 16, 32, 4, 16, "multi-box 64x16x16, 16 warps, 2 lines x 16 boxes/thread, 4 stages"},
-    {25, 1, 64, 16, 32, 6, 16, "multi-box 64x16x16, 16 warps, 2 lines x 16 boxes/thread, 6 stages"},
-    {26, 1, 64, 16, 32, 4, 16, "multi-box 64x16x16, 8 warps, 4 lines x 16 boxes/thread, packed FMA"},
-    {27, 1, 64, 16, 32, 4, 8, "multi-box 64x16x16, 16 warps, 4 lines x 8 boxes/thread, packed FMA"},
+    {1, 0, 128, 64, 32, 4, 1, 0, "8 warps, 8x4/thread, 32-bus chunks, 4 stages, 1 add per bus"},
+    {3, 0, 128, 64, 32, 4, 1, 0, "16 warps, 4x4/thread, 32-bus chunks, 4 stages, 1 add per bus"},
+    {6, 0, 128, 64, 32, 4, 1, 1, "8 warps, 8x4/thread, 32-bus chunks, 4 stages, 4-bus add tree"},
+    {7, 0, 128, 64, 64, 3, 1, 1, "8 warps, 8x4/thread, 64-bus chunks, 3 stages, 4-bus add tree"},
+    {8, 0, 128, 64, 32, 4, 1, 1, "16 warps, 4x4/thread, 32-bus chunks, 4 stages, 4-bus add tree"},
+    {9, 0, 128, 64, 64, 3, 1, 1, "16 warps, 4x4/thread, 64-bus chunks, 3 stages, 4-bus add tree"},
+    {10, 0, 64, 64, 32, 4, 1, 1, "2 CTAs/SM x 8 warps, 4x4/thread, 32-bus chunks, 4 stages, tree"},
+    {11, 0, 64, 64, 64, 2, 1, 1, "2 CTAs/SM x 8 warps, 4x4/thread, 64-bus chunks, 2 stages, tree"},
+    {12, 0, 128, 64, 64, 3, 1, 2, "16 warps, 4x4/thread, 64-bus chunks, 3 stages, packed two-lane sums"},
+    {13, 0, 128, 64, 32, 4, 1, 2, "16 warps, 4x4/thread, 32-bus chunks, 4 stages, packed two-lane sums"},
+    {15, 0, 64, 64, 32, 4, 1, 2, "2 CTAs/SM x 8 warps, 4x4/thread, 32-bus chunks, 4 stages, packed"},
+    {16, 0, 64, 64, 64, 2, 1, 2, "2 CTAs/SM x 8 warps, 4x4/thread, 64-bus chunks, 2 stages, packed"},
+    {20, 1, 64, 16, 32, 4, 16, -1, "multi-box 64x16x16, 8 warps, 4 lines x 16 boxes/thread, 4 stages"},
+    {21, 1, 64, 16, 32, 6, 16, -1, "multi-box 64x16x16, 8 warps, 4 lines x 16 boxes/thread, 6 stages"},
+    {22, 1, 64, 16, 32, 4, 8, -1, "multi-box 64x16x16, 16 warps, 4 lines x 8 boxes/thread, 4 stages"},
+    {23, 1, 64, 16, 32, 6, 8, -1, "multi-box 64x16x16, 16 warps, 4 lines x 8 boxes/thread, 6 stages"},
+    {24, 1, 64, 16, 32, 4, 16, -1, "multi-box 64x16x16, 16 warps, 2 lines x 16 boxes/thread, 4 stages"},
+    {25, 1, 64, 16, 32, 6, 16, -1, "multi-box 64x16x16, 16 warps, 2 lines x 16 boxes/thread, 6 stages"},
+    {26, 1, 64, 16, 32, 4, 16, -1, "multi-box 64x16x16, 8 warps, 4 lines x 16 boxes/thread, packed FMA"},
+    {27, 1, 64, 16, 32, 4, 8, -1, "multi-box 64x16x16, 16 warps, 4 lines x 8 boxes/thread, packed FMA"},
 };
 
 const CtgVariant *ctg_variants(int *count) {
