@@ -725,7 +725,7 @@ ibp_status set_error(ibp_status s, const char *msg) {
 // pairs per thread, 64-bus chunks in 2 stages, packed two-lane sums; many
 // boxes, 8 warps, 4 lines x 16 boxes per thread, packed FMA
 constexpr int kDefaultOneBoxVariant = 16;
-constexpr int kDefaultMultiBoxVariant = 26;
+constexpr int kDefaultMultiBoxVariant = 29;
 
 static const CtgVariant *pick_variant(const ibp_case *c, int n_box) {
     if (c->variant > 0) {
@@ -1156,6 +1156,7 @@ struct MultiPlan {
     std::vector<const ibp_case *> cases;
     std::vector<int> n_box, gens, reduced;
     int device = -1, grid = 0;
+    int variant = 0, rows_per_item = 0;  // kernel body (the first case's variant) and its partial rows
     DevBuf<MultiItem> items;
     DevBuf<int> cta_start, err;
     DevBuf<uint32_t> prefix;
@@ -1181,7 +1182,8 @@ static void drop_plans_of(const ibp_case *c) {
                   g_plans.end());
 }
 
-static CtgArgs multi_args(const ibp_case *c, int n_box, int BL, int BK, int CH, bool reduced) {
+static CtgArgs multi_args(const ibp_case *c, int n_box, int BL, int BK, int CH, bool reduced,
+                          int rows_per_item) {
     const int n_box_pad = (n_box + kBoxTile - 1) / kBoxTile * kBoxTile;
     const int n_rows = reduced ? c->n_nb : c->n_line;
     const int tiles_l = (n_rows + BL - 1) / BL, tiles_k = (c->n_ctg + BK - 1) / BK;
@@ -1196,7 +1198,7 @@ static CtgArgs multi_args(const ibp_case *c, int n_box, int BL, int BK, int CH, 
     ca.gamma = rup_gamma(CH, 256 / CH, (n_chunks + 256 / CH - 1) / (256 / CH));
     ca.flow_lo = nullptr; ca.flow_hi = nullptr; ca.partials = c->part_ctg.p; ca.err = c->err.p;
     ca.wait_ns = 2000000000ull;
-    ca.warps_per_tile = 8;
+    ca.warps_per_tile = rows_per_item;
     ca.part_rows_cap = (int)max_part_rows(c);
     if (reduced) {
         ca.live = c->nb_list.p;
@@ -1234,6 +1236,8 @@ static ibp_status build_plan(ibp_case *const *cases, const int32_t *n_box, int n
     multi_tile_shape(&BL, &BK, &CH);
     std::unique_ptr<MultiPlan> P(new MultiPlan());
     P->device = cases[0]->device;
+    P->variant = cases[0]->variant;
+    P->rows_per_item = cases_rows_per_item(P->variant);
     std::vector<CtgArgs> args(n_case);
     std::vector<CUtensorMap> maps(3 * (size_t)n_case);
     struct Item { MultiItem m; long long cost; int order; };
@@ -1245,7 +1249,7 @@ static ibp_status build_plan(ibp_case *const *cases, const int32_t *n_box, int n
         P->gens.push_back(c->ws_gen);
         const bool red = multi_reduced(c);
         P->reduced.push_back(red ? 1 : 0);
-        args[i] = multi_args(c, n_box[i], BL, BK, CH, red);
+        args[i] = multi_args(c, n_box[i], BL, BK, CH, red, P->rows_per_item);
         const int n_box_pad = args[i].n_box_pad;
         const int w = red ? c->n_r_pad : c->n_a_pad;
         const float *rows = red ? c->phi_nb.p : c->phi_a.p;
@@ -1308,7 +1312,7 @@ static ibp_status build_plan(ibp_case *const *cases, const int32_t *n_box, int n
 
 static MultiPlan *find_plan(ibp_case *const *cases, const int32_t *n_box, int n_case) {
     for (auto &p : g_plans) {
-        if ((int)p->cases.size() != n_case) continue;
+        if ((int)p->cases.size() != n_case || p->variant != cases[0]->variant) continue;
         bool same = true;
         for (int i = 0; i < n_case && same; ++i)
             same = p->cases[i] == cases[i] && p->n_box[i] == n_box[i] && p->gens[i] == cases[i]->ws_gen &&
@@ -1396,7 +1400,7 @@ extern "C" ibp_status ibp_bound_multi(int32_t n_case, ibp_case *const *cases, co
         CUDA_TRY(launch_base(bb, c->n_part_base, s));
     }
     // one persistent launch over the contingency tiles of every case
-    CUDA_TRY(launch_ctg_cases(cases[0]->variant, P->items.p, P->cta_start.p, P->prefix.p, P->args.p,
+    CUDA_TRY(launch_ctg_cases(P->variant, P->items.p, P->cta_start.p, P->prefix.p, P->args.p,
                               P->maps.p, P->grid, 2000000000ull, P->err.p, s));
     int BL, BK, CH;
     multi_tile_shape(&BL, &BK, &CH);
@@ -1406,7 +1410,7 @@ extern "C" ibp_status ibp_bound_multi(int32_t n_case, ibp_case *const *cases, co
         AsmArgs aa{};
         aa.n_box = n_box[i]; aa.n_dev = c->n_dev; aa.n_gen = c->n_gen;
         const int rows = P->reduced[i] ? c->n_nb : c->n_line;
-        aa.n_part_ctg = ((rows + BL - 1) / BL) * ((c->n_ctg + BK - 1) / BK) * 8;
+        aa.n_part_ctg = ((rows + BL - 1) / BL) * ((c->n_ctg + BK - 1) / BK) * P->rows_per_item;
         aa.part_stage = c->part_stage.p; aa.n_stage = kPartStages;
         aa.n_part_base = c->n_part_base;
         aa.part_ctg = c->part_ctg.p; aa.part_base = c->part_base.p; aa.box_lo = box_lo[i]; aa.box_hi = box_hi[i];

@@ -224,6 +224,8 @@ cudaError_t launch_ctg_cases(int variant, const MultiItem *items, const int *cta
                              const uint32_t *prefix, const CtgArgs *args, const CUtensorMap *maps,
                              int grid, unsigned long long wait_ns, int *err, cudaStream_t s);
 void multi_tile_shape(int *BL, int *BK, int *CH);
+// partial rows per work item of the body launch_ctg_cases runs for `variant`
+int cases_rows_per_item(int variant);
 cudaError_t launch_assemble(const AsmArgs &a, cudaStream_t s);
 cudaError_t launch_screen(const ScreenArgs &a, int num_sms, cudaStream_t s);
 cudaError_t launch_class_radius(const ClsArgs &a, cudaStream_t s);

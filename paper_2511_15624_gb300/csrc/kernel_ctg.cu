@@ -311,32 +311,37 @@ __global__ void __launch_bounds__(WL * WK * 32, MINB)
 
 // ---------------------------------------------------------------------------
 // Multi-box kernel.  Work item = (line tile of 64, contingency tile of 16,
-// box tile of 16).  8 warps = 4 line groups x 2 contingency groups; a warp is 4
-// line-lanes x 8 contingency-lanes; thread (tl, tk) owns lines tl + 16 i
-// (i < 4), contingency tk and all 16 boxes of the box tile.  Per (pair, bus):
-//   h = RN(L~ Phi~[k,b] + Phi~[l,b]),  acc_j <- RU(|h| r_jb + acc_j)  (j < 16)
-// i.e. 18 instructions for 17 counted FMAs.  Stage = unscaled PTDF rows of the
-// line and contingency tiles (SWIZZLE_128B) and the radius tile [32 buses][16
-// boxes] (bus-major, broadcast reads).  Level-3 radius sums live in shared
-// memory.
+// box tile of 16).  A warp is 4 line-lanes x 8 contingency-lanes.  With one
+// contingency per thread (MK = 1), 8 warps = 4 line groups x 2 contingency
+// groups and thread (tl, tk) owns lines tl + 16 i (i < 4), contingency tk and
+// all 16 boxes (BH = 1); per (pair, bus)
+//   h = RN(L~ Phi~[k,b] + Phi~[l,b]),  acc_j <- RU(|h| r_jb + acc_j)  (j < 16).
+// The default (MK = 2, BH = 2) gives a thread contingencies tk and tk + 8 and
+// one half of the boxes, so each radius it loads serves 8 pairs instead of 4;
+// both halves form h.  Stage = unscaled PTDF rows of the line and contingency
+// tiles (SWIZZLE_128B) and the radius tile [32 buses][16 boxes] (bus-major,
+// broadcast reads).  Level-3 radius sums live in shared memory.
 // ---------------------------------------------------------------------------
 constexpr int kMB = 16;  // boxes per work item
 
 // BH = box halves: 1 -> each thread 16 boxes; 2 -> the second set of warps
 // takes boxes 8..15 of the item (h is formed by both halves).  ML = lines per
 // thread: 4 -> 8 warps per half, 2 -> 16 warps per half (64 lines per item).
-template <int ST, int BH = 1, int ML_ = 4>
+// MK = contingencies per thread: 2 halves the warps per half, and each radius
+// a thread loads serves twice the pairs.
+template <int ST, int BH = 1, int ML_ = 4, int MK_ = 1>
 struct MultiShape {
-    static constexpr int ML = ML_;
-    static constexpr int TL = 64 / ML, TK = 16;
-    static constexpr int kWarpsHalf = TL / 4 * 2;  // warps of one box half
+    static constexpr int ML = ML_, MK = MK_;
+    static constexpr int TL = 64 / ML, TK = 16 / MK;  // line / contingency lanes
+    static_assert(TK % 8 == 0, "a warp spans 8 contingency lanes");
+    static constexpr int kWarpsHalf = TL / 4 * (TK / 8);  // warps of one box half
     static constexpr int kWarps = kWarpsHalf * BH, kThreads = 32 * kWarps;
     static constexpr int kMBT = kMB / BH;  // boxes per thread
-    static constexpr int BL = TL * ML, BK = TK;
+    static constexpr int BL = TL * ML, BK = TK * MK;
     static constexpr int CH = 32;
     static constexpr int kStageFloats = (BL + BK) * CH + CH * kMB;
     static constexpr size_t kRing = (size_t)ST * kStageFloats * sizeof(float);
-    static constexpr size_t kAcc3 = (size_t)ML * kMBT * kThreads * sizeof(float);
+    static constexpr size_t kAcc3 = (size_t)ML * MK * kMBT * kThreads * sizeof(float);
     static constexpr size_t kCtl = ST * sizeof(uint64_t) + 2 * ST * sizeof(int) + 16;
     // per-warp copy of the current item's kernel arguments
     static constexpr size_t kArgs = (size_t)kWarps * ((sizeof(CtgArgs) + 15) / 16 * 16);
@@ -394,10 +399,10 @@ struct CasesPlan {
     }
 };
 
-template <int ST, int BH, int ML, class Plan>
+template <int ST, int BH, int ML, int MK, class Plan>
 __device__ __forceinline__ void issue_multi(const Plan &P, float *ring, uint64_t *full,
                                             int *last_issued, uint32_t c, int i, int ch) {
-    using S = MultiShape<ST, BH, ML>;
+    using S = MultiShape<ST, BH, ML, MK>;
     constexpr uint32_t kBytes = (uint32_t)S::kStageFloats * sizeof(float);
     const int s = (int)(c % ST);
     const MultiItemView v = P.item(i);
@@ -412,15 +417,16 @@ __device__ __forceinline__ void issue_multi(const Plan &P, float *ring, uint64_t
 }
 
 // PK: accumulate box pairs with the packed two-lane FMA (same rounding per lane)
-template <int ST, int BH, int ML_, class Plan, bool PK = false>
+template <int ST, int BH, int ML_, class Plan, bool PK = false, int MK_ = 1>
 __device__ __forceinline__ void multi_body(const Plan &P, unsigned long long wait_ns, int *err) {
-    using S = MultiShape<ST, BH, ML_>;
-    constexpr int CH = S::CH, ML = S::ML, TL = S::TL, BL = S::BL, kMBT = S::kMBT;
+    using S = MultiShape<ST, BH, ML_, MK_>;
+    constexpr int CH = S::CH, ML = S::ML, MK = S::MK, TL = S::TL, TK = S::TK, BL = S::BL,
+                  kMBT = S::kMBT;
     extern __shared__ unsigned char smem_raw[];
     float *ring = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                             ~uintptr_t(1023));
     float *acc3 = reinterpret_cast<float *>(reinterpret_cast<unsigned char *>(ring) + S::kRing) +
-                  threadIdx.x;  // slot (i, j) at acc3[(i * kMBT + j) * kThreads]
+                  threadIdx.x;  // slot (i, c, j) at acc3[((i * MK + c) * kMBT + j) * kThreads]
     constexpr size_t kArgSlot = (sizeof(CtgArgs) + 15) / 16 * 16;
     unsigned char *arg_base = reinterpret_cast<unsigned char *>(ring) + S::kRing + S::kAcc3;
     uint64_t *full = reinterpret_cast<uint64_t *>(arg_base + S::kArgs);
@@ -451,16 +457,17 @@ __device__ __forceinline__ void multi_body(const Plan &P, unsigned long long wai
                 ch -= P.item(i).n_chunks;
                 ++i;
             }
-            issue_multi<ST, BH, ML_>(P, ring, full, last_issued, c, i, ch);
+            issue_multi<ST, BH, ML_, MK_>(P, ring, full, last_issued, c, i, ch);
             ++ch;
         }
     }
 
     // box half of this warp (BH = 2) and its position inside the half
     const int half = warp / S::kWarpsHalf, wq = warp % S::kWarpsHalf;
-    const int tl = (wq >> 1) * 4 + (lane >> 3);
-    const int tk = (wq & 1) * 8 + (lane & 7);
-    const int xl = tl & 7, xk = tk & 7;
+    constexpr int kGK = TK / 8;  // contingency lane groups (warps) per line group
+    const int tl = (wq / kGK) * 4 + (lane >> 3);
+    const int tk = (wq % kGK) * 8 + (lane & 7);
+    const int xl = tl & 7, xk = tk & 7;  // rows tk + TK c share the swizzle phase of tk
     uint32_t it = 0;
     bool stop = false;
     for (int ii = 0; ii < my_items && !stop; ++ii) {
@@ -474,26 +481,31 @@ __device__ __forceinline__ void multi_body(const Plan &P, unsigned long long wai
         }
         const CtgArgs &a = *my_args;
         const int l0 = v.l0, b0 = v.b0, tlk = v.tlk;
-        const int k = v.k0 + tk;
         const int n_l = a.n_l, n_c = a.n_c, n_box = a.n_box;
         // screened calls walk the compacted line list live[0 .. n_ll)
         const int n_ll = a.n_live ? *a.n_live : n_l;
-        float Lr[ML];
+        float Lr[ML][MK];
 #pragma unroll
         for (int i = 0; i < ML; ++i) {
             const int lq = l0 + tl + TL * i;
             int l = lq < n_ll ? (a.live ? __ldg(&a.live[lq]) : lq) : -1;
             if (l >= 0 && !IBP_IDX_OK(l < n_l, a.err)) l = -1;
-            Lr[i] = (l >= 0 && k < n_c) ? __ldg(&a.lodf[(size_t)k * n_l + l]) : 0.0f;
+#pragma unroll
+            for (int c = 0; c < MK; ++c) {
+                const int k = v.k0 + tk + TK * c;
+                Lr[i][c] = (l >= 0 && k < n_c) ? __ldg(&a.lodf[(size_t)k * n_l + l]) : 0.0f;
+            }
         }
-        float acc1[ML][kMBT], acc2[ML][kMBT];
+        float acc1[ML][MK][kMBT], acc2[ML][MK][kMBT];
 #pragma unroll
         for (int i = 0; i < ML; ++i)
 #pragma unroll
-            for (int j = 0; j < kMBT; ++j) {
-                acc1[i][j] = acc2[i][j] = 0.0f;
-                acc3[(i * kMBT + j) * S::kThreads] = 0.0f;
-            }
+            for (int c = 0; c < MK; ++c)
+#pragma unroll
+                for (int j = 0; j < kMBT; ++j) {
+                    acc1[i][c][j] = acc2[i][c][j] = 0.0f;
+                    acc3[((i * MK + c) * kMBT + j) * S::kThreads] = 0.0f;
+                }
         for (int ch = 0; ch < v.n_chunks; ++ch, ++it) {
             const int s = (int)(it % ST);
             const uint32_t par = (it / ST) & 1u;
@@ -512,7 +524,10 @@ __device__ __forceinline__ void multi_body(const Plan &P, unsigned long long wai
             const float *sR = sK + S::BK * CH;
 #pragma unroll 2
             for (int q = 0; q < CH / 4; ++q) {
-                const float4 fk = *reinterpret_cast<const float4 *>(sK + tk * CH + ((q ^ xk) << 2));
+                float4 fk[MK];
+#pragma unroll
+                for (int c = 0; c < MK; ++c)
+                    fk[c] = *reinterpret_cast<const float4 *>(sK + (tk + TK * c) * CH + ((q ^ xk) << 2));
                 float4 fl[ML];
 #pragma unroll
                 for (int i = 0; i < ML; ++i)
@@ -529,23 +544,27 @@ __device__ __forceinline__ void multi_body(const Plan &P, unsigned long long wai
                         r[4 * u + 2] = r4.z;
                         r[4 * u + 3] = r4.w;
                     }
-                    const float fkt = t == 0 ? fk.x : t == 1 ? fk.y : t == 2 ? fk.z : fk.w;
 #pragma unroll
                     for (int i = 0; i < ML; ++i) {
                         const float flt = t == 0 ? fl[i].x : t == 1 ? fl[i].y : t == 2 ? fl[i].z : fl[i].w;
-                        const float ah = fabsf(__fmaf_rn(Lr[i], fkt, flt));
-                        if constexpr (PK) {
-                            const float2 ah2 = make_float2(ah, ah);
 #pragma unroll
-                            for (int j = 0; j < kMBT; j += 2) {
-                                const float2 v = __ffma2_ru(ah2, make_float2(r[j], r[j + 1]),
-                                                            make_float2(acc1[i][j], acc1[i][j + 1]));
-                                acc1[i][j] = v.x;
-                                acc1[i][j + 1] = v.y;
+                        for (int c = 0; c < MK; ++c) {
+                            const float fkt = t == 0 ? fk[c].x : t == 1 ? fk[c].y : t == 2 ? fk[c].z : fk[c].w;
+                            const float ah = fabsf(__fmaf_rn(Lr[i][c], fkt, flt));
+                            float *ac = acc1[i][c];
+                            if constexpr (PK) {
+                                const float2 ah2 = make_float2(ah, ah);
+#pragma unroll
+                                for (int j = 0; j < kMBT; j += 2) {
+                                    const float2 v = __ffma2_ru(ah2, make_float2(r[j], r[j + 1]),
+                                                                make_float2(ac[j], ac[j + 1]));
+                                    ac[j] = v.x;
+                                    ac[j + 1] = v.y;
+                                }
+                            } else {
+#pragma unroll
+                                for (int j = 0; j < kMBT; ++j) ac[j] = __fmaf_ru(ah, r[j], ac[j]);
                             }
-                        } else {
-#pragma unroll
-                            for (int j = 0; j < kMBT; ++j) acc1[i][j] = __fmaf_ru(ah, r[j], acc1[i][j]);
                         }
                     }
                 }
@@ -564,26 +583,30 @@ __device__ __forceinline__ void multi_body(const Plan &P, unsigned long long wai
                             ++i2;
                         }
                         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                        issue_multi<ST, BH, ML_>(P, ring, full, last_issued, nxt, i2, ch2);
+                        issue_multi<ST, BH, ML_, MK_>(P, ring, full, last_issued, nxt, i2, ch2);
                     }
                 }
             }
 #pragma unroll
             for (int i = 0; i < ML; ++i)
 #pragma unroll
-                for (int j = 0; j < kMBT; ++j) {
-                    acc2[i][j] = __fadd_ru(acc2[i][j], acc1[i][j]);
-                    acc1[i][j] = 0.0f;
-                }
+                for (int c = 0; c < MK; ++c)
+#pragma unroll
+                    for (int j = 0; j < kMBT; ++j) {
+                        acc2[i][c][j] = __fadd_ru(acc2[i][c][j], acc1[i][c][j]);
+                        acc1[i][c][j] = 0.0f;
+                    }
             if ((ch & (kFold3 - 1)) == kFold3 - 1) {
 #pragma unroll
                 for (int i = 0; i < ML; ++i)
 #pragma unroll
-                    for (int j = 0; j < kMBT; ++j) {
-                        float &a3 = acc3[(i * kMBT + j) * S::kThreads];
-                        a3 = __fadd_ru(a3, acc2[i][j]);
-                        acc2[i][j] = 0.0f;
-                    }
+                    for (int c = 0; c < MK; ++c)
+#pragma unroll
+                        for (int j = 0; j < kMBT; ++j) {
+                            float &a3 = acc3[((i * MK + c) * kMBT + j) * S::kThreads];
+                            a3 = __fadd_ru(a3, acc2[i][c][j]);
+                            acc2[i][c][j] = 0.0f;
+                        }
             }
         }
         if (stop) break;
@@ -595,20 +618,24 @@ __device__ __forceinline__ void multi_body(const Plan &P, unsigned long long wai
 #pragma unroll
             for (int i = 0; i < ML; ++i) {
                 const int lq = l0 + tl + TL * i;
-                if (lq < n_ll && k < n_c) {
-                    const int l = a.live ? __ldg(&a.live[lq]) : lq;
-                    float a2 = 0.0f;
-                    // registers cannot be indexed by the runtime j: select it
 #pragma unroll
-                    for (int jj = 0; jj < kMBT; ++jj)
-                        if (jj == j) a2 = acc2[i][jj];
-                    const float A = __fadd_ru(acc3[(i * kMBT + j) * S::kThreads], a2);
-                    pair_epilogue(a, box, l, k, Lr[i], A, slo, shi, whi, wlo);
+                for (int c = 0; c < MK; ++c) {
+                    const int k = v.k0 + tk + TK * c;
+                    if (lq < n_ll && k < n_c) {
+                        const int l = a.live ? __ldg(&a.live[lq]) : lq;
+                        float a2 = 0.0f;
+                        // registers cannot be indexed by the runtime j: select it
+#pragma unroll
+                        for (int jj = 0; jj < kMBT; ++jj)
+                            if (jj == j) a2 = acc2[i][c][jj];
+                        const float A = __fadd_ru(acc3[((i * MK + c) * kMBT + j) * S::kThreads], a2);
+                        pair_epilogue(a, box, l, k, Lr[i][c], A, slo, shi, whi, wlo);
+                    }
                 }
             }
             // partial rows per item: kWarpsHalf (the warp's place in its
             // half; each box belongs to exactly one half)
-            write_warp_partials(a, tlk, wq, box, slo, shi, whi, wlo, ML);
+            write_warp_partials(a, tlk, wq, box, slo, shi, whi, wlo, ML * MK);
         }
     }
     __syncthreads();
@@ -620,11 +647,11 @@ __device__ __forceinline__ void multi_body(const Plan &P, unsigned long long wai
     }
 }
 
-template <int ST, int BH, int ML, bool PK>
-__global__ void __launch_bounds__(MultiShape<ST, BH, ML>::kThreads, 1)
+template <int ST, int BH, int ML, bool PK, int MK>
+__global__ void __launch_bounds__(MultiShape<ST, BH, ML, MK>::kThreads, 1)
     k_ctg_multi(const __grid_constant__ CUtensorMap mL, const __grid_constant__ CUtensorMap mK,
                 const __grid_constant__ CUtensorMap mR, const CtgArgs a) {
-    using S = MultiShape<ST, BH, ML>;
+    using S = MultiShape<ST, BH, ML, MK>;
     if (threadIdx.x == 0) {
         prefetch_tensormap(&mL);
         prefetch_tensormap(&mK);
@@ -635,27 +662,27 @@ __global__ void __launch_bounds__(MultiShape<ST, BH, ML>::kThreads, 1)
     const int tiles_l = a.n_live ? (n_ll + S::BL - 1) / S::BL : a.tiles_l;
     const int n_tiles = a.n_live ? tiles_l * tiles_k * box_tiles : a.n_tiles;
     const SinglePlan P{&a, &mL, &mK, &mR, tiles_l, tiles_k, box_tiles, S::BL, S::BK, n_tiles};
-    multi_body<ST, BH, ML, SinglePlan, PK>(P, a.wait_ns, a.err);
+    multi_body<ST, BH, ML, SinglePlan, PK, MK>(P, a.wait_ns, a.err);
 }
 
 // Many cases in one persistent launch: CTA b walks items [start[b], start[b+1])
 // of the host-built table (longest items first, dealt round-robin).
-template <int ST, int BH, bool PK>
-__global__ void __launch_bounds__(MultiShape<ST, BH>::kThreads, 1)
+template <int ST, int BH, bool PK, int MK>
+__global__ void __launch_bounds__(MultiShape<ST, BH, 4, MK>::kThreads, 1)
     k_ctg_cases(const MultiItem *__restrict__ items, const int *__restrict__ cta_start,
                 const uint32_t *__restrict__ prefix, const CtgArgs *__restrict__ args,
                 const CUtensorMap *__restrict__ maps, unsigned long long wait_ns, int *err) {
     const int s0 = cta_start[blockIdx.x], s1 = cta_start[blockIdx.x + 1];
     const CasesPlan P{items + s0, prefix + s0 + blockIdx.x, s1 - s0, args, maps};
-    multi_body<ST, BH, 4, CasesPlan, PK>(P, wait_ns, err);
+    multi_body<ST, BH, 4, CasesPlan, PK, MK>(P, wait_ns, err);
 }
 
-template <int ST, int BH, int ML = 4, bool PK = false>
+template <int ST, int BH, int ML = 4, bool PK = false, int MK = 1>
 static cudaError_t launch_multi(const CUtensorMap &mL, const CUtensorMap &mK,
                                 const CUtensorMap &mR, const CtgArgs &a, int grid,
                                 cudaStream_t s) {
-    using S = MultiShape<ST, BH, ML>;
-    auto kern = k_ctg_multi<ST, BH, ML, PK>;
+    using S = MultiShape<ST, BH, ML, MK>;
+    auto kern = k_ctg_multi<ST, BH, ML, PK, MK>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)S::kBytes);
     if (e != cudaSuccess) return e;
@@ -676,16 +703,18 @@ cudaError_t launch_ctg_multi(const CtgVariant &v, const CUtensorMap &mL, const C
     case 25: return launch_multi<6, 1, 2>(mL, mK, mR, a, grid, s);
     case 26: return launch_multi<4, 1, 4, true>(mL, mK, mR, a, grid, s);
     case 27: return launch_multi<4, 2, 4, true>(mL, mK, mR, a, grid, s);
+    case 28: return launch_multi<4, 2, 4, true, 2>(mL, mK, mR, a, grid, s);
+    case 29: return launch_multi<6, 2, 4, true, 2>(mL, mK, mR, a, grid, s);
     default: return cudaErrorInvalidValue;
     }
 }
 
-template <int BH, bool PK>
+template <int ST, int BH, bool PK, int MK>
 static cudaError_t launch_cases(const MultiItem *items, const int *cta_start, const uint32_t *prefix,
                                 const CtgArgs *args, const CUtensorMap *maps, int grid,
                                 unsigned long long wait_ns, int *err, cudaStream_t s) {
-    using S = MultiShape<4, BH>;
-    auto kern = k_ctg_cases<4, BH, PK>;
+    using S = MultiShape<ST, BH, 4, MK>;
+    auto kern = k_ctg_cases<ST, BH, PK, MK>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)S::kBytes);
     if (e != cudaSuccess) return e;
@@ -693,19 +722,30 @@ static cudaError_t launch_cases(const MultiItem *items, const int *cta_start, co
     return cudaGetLastError();
 }
 
-// The many-case launch runs the 4-stage body of multi-box variant `variant`
-// (20/21: 8 warps, 22/23: box halves, 27: box halves and packed FMA; 26 and
-// any other value: the default, 8 warps with packed FMA).  All write 8
-// partial rows per work item.
+// The many-case launch runs the body of multi-box variant `variant`: 20/21
+// (8 warps), 22/23 (box halves), 26 (8 warps, packed FMA), 27 (box halves,
+// packed FMA), each with 4 stages, and 28 (4 lines x 2 contingencies x 8 boxes
+// per thread); 29 and any other value run the default, 28's body with 6
+// stages.  cases_rows_per_item gives the partial rows each body writes per
+// work item; the two switches must agree.
 cudaError_t launch_ctg_cases(int variant, const MultiItem *items, const int *cta_start,
                              const uint32_t *prefix, const CtgArgs *args, const CUtensorMap *maps,
                              int grid, unsigned long long wait_ns, int *err, cudaStream_t s) {
     if (grid <= 0) return cudaSuccess;
     switch (variant) {
-    case 20: case 21: return launch_cases<1, false>(items, cta_start, prefix, args, maps, grid, wait_ns, err, s);
-    case 22: case 23: return launch_cases<2, false>(items, cta_start, prefix, args, maps, grid, wait_ns, err, s);
-    case 27: return launch_cases<2, true>(items, cta_start, prefix, args, maps, grid, wait_ns, err, s);
-    default: return launch_cases<1, true>(items, cta_start, prefix, args, maps, grid, wait_ns, err, s);
+    case 20: case 21: return launch_cases<4, 1, false, 1>(items, cta_start, prefix, args, maps, grid, wait_ns, err, s);
+    case 22: case 23: return launch_cases<4, 2, false, 1>(items, cta_start, prefix, args, maps, grid, wait_ns, err, s);
+    case 26: return launch_cases<4, 1, true, 1>(items, cta_start, prefix, args, maps, grid, wait_ns, err, s);
+    case 27: return launch_cases<4, 2, true, 1>(items, cta_start, prefix, args, maps, grid, wait_ns, err, s);
+    case 28: return launch_cases<4, 2, true, 2>(items, cta_start, prefix, args, maps, grid, wait_ns, err, s);
+    default: return launch_cases<6, 2, true, 2>(items, cta_start, prefix, args, maps, grid, wait_ns, err, s);
+    }
+}
+
+int cases_rows_per_item(int variant) {
+    switch (variant) {
+    case 20: case 21: case 22: case 23: case 26: case 27: return MultiShape<4, 1, 4, 1>::kWarpsHalf;
+    default: return MultiShape<6, 2, 4, 2>::kWarpsHalf;
     }
 }
 
@@ -741,6 +781,8 @@ static const CtgVariant kVariants[] = {
     {25, 1, 64, 16, 32, 6, 16, -1, "multi-box 64x16x16, 16 warps, 2 lines x 16 boxes/thread, 6 stages"},
     {26, 1, 64, 16, 32, 4, 16, -1, "multi-box 64x16x16, 8 warps, 4 lines x 16 boxes/thread, packed FMA"},
     {27, 1, 64, 16, 32, 4, 8, -1, "multi-box 64x16x16, 16 warps, 4 lines x 8 boxes/thread, packed FMA"},
+    {28, 1, 64, 16, 32, 4, 8, -1, "multi-box 64x16x16, 8 warps, 4 lines x 2 ctgs x 8 boxes/thread, packed FMA"},
+    {29, 1, 64, 16, 32, 6, 8, -1, "multi-box 64x16x16, 8 warps, 4 lines x 2 ctgs x 8 boxes/thread, packed FMA, 6 stages"},
 };
 
 const CtgVariant *ctg_variants(int *count) {
@@ -786,6 +828,7 @@ static cudaError_t launch_one(const CUtensorMap &mL, const CUtensorMap &mK, cons
 int ctg_warps(const CtgVariant &v) {
     switch (v.id) {
     case 3: case 8: case 9: case 12: case 13: case 24: case 25: return 16;
+    case 28: case 29: return MultiShape<6, 2, 4, 2>::kWarpsHalf;
     default: return 8;
     }
 }
