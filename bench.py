@@ -419,8 +419,11 @@ def run_bisection_study(args):
     out = {"study": "bisection", "workload": workload(case, 2, 1) + " (root box)",
            "rounds": args.rounds, "max_leaves": 256}
     for batched in (True, False):
+        # warm-up rounds, not reported: they reach several leaves, so the first
+        # multi-box calls and the framework's first sorts and gathers over more
+        # than one leaf happen here
         b = Bisection(gpu, case.box_lo, case.box_hi, max_leaves=256, batched=batched)
-        b.step()  # warm-up round, not reported
+        b.run(3)
         b = Bisection(gpu, case.box_lo, case.box_hi, max_leaves=256, batched=batched)
         hist = b.run(args.rounds)
         out["batched" if batched else "single"] = [
