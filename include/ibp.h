@@ -210,7 +210,10 @@ ibp_status ibp_case_info(const ibp_case *c, ibp_case_info_t *out);
  * Kernel-shape selection for the contingency kernel (used by the autotuner).
  * variant: 0 = library default for the box count; other values select one of
  * the compiled tile shapes listed by ibp_kernel_variants().  Returns
- * IBP_EINVAL for an unknown variant.
+ * IBP_EINVAL for an unknown variant.  A one-box variant applies to calls with
+ * one box and a multi-box variant to calls with more (the other calls keep
+ * the default).  ibp_bound_multi runs the multi-box body of the first case's
+ * variant, or the default body for 0 or an id without a many-case form.
  */
 ibp_status ibp_case_set_variant(ibp_case *c, int32_t variant);
 int32_t ibp_kernel_variants(int32_t *ids, int32_t cap, int32_t batched);

@@ -49,6 +49,28 @@ def test_multi_matches_per_case_and_oracle(env):
             assert np.all(np.abs(hi - ref.hi) <= 1e-5 * np.abs(ref.hi) + 1e-9 * scale)
 
 
+@pytest.mark.parametrize("variant", [26, 28])
+def test_multi_other_bodies(env, variant):
+    """The many-case launch runs the body of the first case's variant: 26
+    writes 8 partial rows per work item, 28 and the default 4.  Every body
+    gives the default's bound up to the FP64 summation order, inside the
+    reported error."""
+    P, torch, nets, cases, los, his = env
+    ref = [tuple(t.cpu().numpy() for t in o) for o in P.bound_multi(cases, los, his)]
+    cases[0].set_variant(variant)
+    try:
+        outs = P.bound_multi(cases, los, his)
+        torch.cuda.synchronize()
+        for (lo0, hi0, e0), o in zip(ref, outs):
+            lo, hi, err = (t.cpu().numpy() for t in o)
+            assert np.all(np.abs(hi - hi0) <= e0[:, 0] + err[:, 0])
+            assert np.all(np.abs(lo - lo0) <= e0[:, 1] + err[:, 1])
+    finally:
+        cases[0].set_variant(0)
+    for c in cases:
+        c.sync()
+
+
 def test_multi_without_reduction(env):
     """With the reduction off, the many-case launch streams every line and
     active bus; it agrees with the per-case plain call the same way."""
