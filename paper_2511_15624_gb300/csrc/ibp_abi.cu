@@ -772,7 +772,7 @@ static ibp_status ensure_workspace(ibp_case *c, int n_box) {
     CUDA_TRY(c->line_R.alloc((size_t)cap * c->n_line));
     CUDA_TRY(c->part_base.alloc((size_t)c->n_part_base * cap * kPartVals));
     CUDA_TRY(c->part_ctg.alloc(max_part_rows(c) * cap * kPartVals));
-    CUDA_TRY(c->part_stage.alloc((size_t)kPartStages * cap * kPartVals));
+    CUDA_TRY(c->part_stage.alloc((size_t)kPartStages * cap * kAsmVals));
     const int cap_pad = (cap + kBoxTile - 1) / kBoxTile * kBoxTile;
     CUDA_TRY(c->rbus_t.alloc(na * cap_pad));
     if (!c->live.p || !c->live_flag.p || !c->n_live.p) {

@@ -19,6 +19,8 @@ constexpr int kErrOverflow = 4;  // active-pair list of the adjoint ran out of r
 constexpr int kErrBounds = 8;    // an index guard of a checked build (-DIBP_CHECK) failed
 // values per partial-sum row: sum s_lo, sum s_hi, error of obj_hi, error of obj_lo
 constexpr int kPartVals = 4;
+// sums of the objective assembly per (box, stage-1 block)
+constexpr int kAsmVals = 18;
 
 // ---------------------------------------------------------------- kernel args
 struct BusArgs {
@@ -176,8 +178,8 @@ struct AsmArgs {
     // tiles x tiles_k x rows_per_tile rows (n_part_ctg is ignored)
     const int *n_live;
     int live_BL, live_tiles_k, live_rows_per_tile;
-    // two-stage reduction of the contingency partials (null: one block per
-    // box reads them all): stage 1 writes [n_box][n_stage][kPartVals]
+    // two-stage assembly (null: one block per box reads every row and device):
+    // stage 1 writes [n_box][n_stage][kAsmVals]
     double *part_stage;
     int n_stage;
     const double *part_ctg;   // [n_part_ctg][n_box][kPartVals]

@@ -216,15 +216,18 @@ __device__ __forceinline__ void ff_add_prod(FF &acc, float p, float2 c) {
     acc.e = __fmaf_rn(p, c.y, __fadd_rn(acc.e, __fadd_rn(err, me)));
 }
 
-// Box-grouped base flows: a warp takes one line and up to kBaseGroup boxes,
-// reads the PTDF row once and keeps the sums of every box of the group.
+// Box-grouped base flows: a warp takes one line and up to G boxes, reads the
+// PTDF row once and keeps the sums of every box of the group.  One-box calls
+// use G = 1, whose few registers leave room to unroll the row loop (more
+// loads in flight per warp).
 constexpr int kBaseGroup = 8;
 
+template <int G>
 __global__ void __launch_bounds__(kBaseWarps * 32) k_base_ff(BaseArgs a) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int gw = blockIdx.x * kBaseWarps + warp;
     const int nw = gridDim.x * kBaseWarps;
-    const int n_groups = (a.n_box + kBaseGroup - 1) / kBaseGroup;
+    const int n_groups = (a.n_box + G - 1) / G;
     const int n_items = a.n_l * n_groups + (a.hat_k ? a.n_c : 0);
     const int nv = a.n_a_pad >> 2;  // float4 per row
     double *part = a.partials + (size_t)gw * a.n_box * kPartVals;
@@ -245,24 +248,24 @@ __global__ void __launch_bounds__(kBaseWarps * 32) k_base_ff(BaseArgs a) {
             }
             continue;
         }
-        const int l = item / n_groups, j0 = (item % n_groups) * kBaseGroup;
-        const int bg = min(kBaseGroup, a.n_box - j0);
+        const int l = item / n_groups, j0 = (item % n_groups) * G;
+        const int bg = min(G, a.n_box - j0);
         const float4 *prow = reinterpret_cast<const float4 *>(a.phi + (size_t)l * a.n_a_pad);
         float4 *hl = a.hat_l ? reinterpret_cast<float4 *>(a.hat_l + (size_t)l * a.n_a_pad) : nullptr;
         // C and R keep one round-up sum per bus of the float4 (the same
         // summation tree as the FP64 kernel, so gamma_base holds for both)
-        FF cs[kBaseGroup];
-        float4 C[kBaseGroup], R[kBaseGroup];
+        FF cs[G];
+        float4 C[G], R[G];
 #pragma unroll
-        for (int jj = 0; jj < kBaseGroup; ++jj) {
+        for (int jj = 0; jj < G; ++jj) {
             cs[jj] = FF{0.0f, 0.0f};
             C[jj] = R[jj] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         }
-        for (int v = lane; v < nv; v += 32) {
-            const float4 p = prow[v];
+        // one float4 of the row (4 buses) into the sums of the group's boxes
+        auto step = [&](const float4 p, int v) {
             const float4 ap = make_float4(fabsf(p.x), fabsf(p.y), fabsf(p.z), fabsf(p.w));
 #pragma unroll
-            for (int jj = 0; jj < kBaseGroup; ++jj) {
+            for (int jj = 0; jj < G; ++jj) {
                 if (jj >= bg) break;
                 const size_t o = (size_t)(j0 + jj) * a.n_a_pad;
                 const float4 *c2 = reinterpret_cast<const float4 *>(a.cbus2 + o) + 2 * v;
@@ -285,9 +288,34 @@ __global__ void __launch_bounds__(kBaseWarps * 32) k_base_ff(BaseArgs a) {
                     hl[v] = make_float4(__fmul_rn(p.x, r.x), __fmul_rn(p.y, r.y), __fmul_rn(p.z, r.z),
                                         __fmul_rn(p.w, r.w));
             }
+        };
+        if constexpr (G == 1) {
+            // the lane's row entries v = lane + 32 i in ascending i, as below;
+            // the next kPf row loads are in flight while the current ones are used
+            constexpr int kPf = 8;
+            float4 nxt[kPf];
+#pragma unroll
+            for (int u = 0; u < kPf; ++u) {
+                const int v = lane + 32 * u;
+                nxt[u] = v < nv ? prow[v] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            }
+            for (int v0 = lane; v0 < nv; v0 += 32 * kPf) {
+                float4 cur[kPf];
+#pragma unroll
+                for (int u = 0; u < kPf; ++u) {
+                    cur[u] = nxt[u];
+                    const int v = v0 + 32 * (kPf + u);
+                    nxt[u] = v < nv ? prow[v] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                }
+#pragma unroll
+                for (int u = 0; u < kPf; ++u)
+                    if (v0 + 32 * u < nv) step(cur[u], v0 + 32 * u);
+            }
+        } else {
+            for (int v = lane; v < nv; v += 32) step(prow[v], v);
         }
 #pragma unroll
-        for (int jj = 0; jj < kBaseGroup; ++jj) {
+        for (int jj = 0; jj < G; ++jj) {
             if (jj >= bg) break;
             // lanes' compensated sums are exact in FP64; the 5-level FP64 tree
             // adds about 5 * 2^-53 relative
@@ -371,7 +399,8 @@ __global__ void __launch_bounds__(kBaseWarps * 32) k_base(BaseArgs a) {
 
 cudaError_t launch_base(const BaseArgs &a, int n_part, cudaStream_t s) {
     const int grid = n_part / kBaseWarps;
-    if (a.cbus2) k_base_ff<<<grid, kBaseWarps * 32, 0, s>>>(a);
+    if (a.cbus2 && a.n_box == 1) k_base_ff<1><<<grid, kBaseWarps * 32, 0, s>>>(a);
+    else if (a.cbus2) k_base_ff<kBaseGroup><<<grid, kBaseWarps * 32, 0, s>>>(a);
     else k_base<<<grid, kBaseWarps * 32, 0, s>>>(a);
     return cudaGetLastError();
 }
@@ -434,112 +463,103 @@ __device__ __forceinline__ int ctg_partial_rows(const AsmArgs &a) {
     return a.n_part_ctg;
 }
 
-// Stage 1 of the contingency partial sums: block (g, box) sums the rows
-// g*128 + t + k*(n_stage*128) of its box (directed FP64), then reduces its
-// 128 threads in a fixed tree; the result does not depend on timing.
+// The sums of the objective assembly (directed FP64; kAsmUp: rounded up):
+//   0 Sfc_lo(rd) 1 Sfc_hi(ru) 2 Wfc_hi(ru) 3 Wfc_lo(ru)   contingency partial rows
+//   4 Sfb_lo 5 Sfb_hi 6 Wfb_hi 7 Wfb_lo                   base partial rows
+//   8 Clo_dn 9 Chi_up 10 Glo_dn 11 Ghi_up 12 cost_err_hi(ru) 13 cost_err_lo(ru)
+//   14 Plo_dn 15 Plo_up 16 Phi_dn 17 Phi_up               devices
+__device__ __forceinline__ bool asm_up(int i) {
+    return !(i == 0 || i == 4 || i == 8 || i == 10 || i == 14 || i == 16);
+}
+
+__device__ __forceinline__ void add_rows(double *v, const double *q) {
+    const double4 r = *reinterpret_cast<const double4 *>(q);
+    v[0] = __dadd_rd(v[0], r.x);
+    v[1] = __dadd_ru(v[1], r.y);
+    v[2] = __dadd_ru(v[2], r.z);
+    v[3] = __dadd_ru(v[3], r.w);
+}
+
+// cost, value and injection terms of device d of box j (eq. (penalized-objective))
+__device__ __forceinline__ void add_device(const AsmArgs &a, int j, int d, double *v) {
+    const double x = a.box_lo[(size_t)j * a.n_dev + d], y = a.box_hi[(size_t)j * a.n_dev + d];
+    const int s0 = a.seg_ptr[d], ns = a.seg_ptr[d + 1] - s0;
+    const double *sl = a.slope + s0, *bk = a.bkpt + s0;
+    const double vlo_dn = pwl_eval(sl, bk, ns, x, false);
+    const double vlo_up = pwl_eval(sl, bk, ns, x, true);
+    const double vhi_dn = pwl_eval(sl, bk, ns, y, false);
+    const double vhi_up = pwl_eval(sl, bk, ns, y, true);
+    if (d >= a.n_gen) {  // load value c_j: C(hi) enters obj_hi, C(lo) enters obj_lo
+        v[8] = __dadd_rd(v[8], vlo_dn);
+        v[9] = __dadd_ru(v[9], vhi_up);
+        v[12] = __dadd_ru(v[12], __dsub_ru(vhi_up, vhi_dn));
+        v[13] = __dadd_ru(v[13], __dsub_ru(vlo_up, vlo_dn));
+        v[14] = __dadd_rd(v[14], -y);
+        v[15] = __dadd_ru(v[15], -y);
+        v[16] = __dadd_rd(v[16], -x);
+        v[17] = __dadd_ru(v[17], -x);
+    } else {  // generator cost g_i: G(lo) enters obj_hi, G(hi) enters obj_lo
+        v[10] = __dadd_rd(v[10], vlo_dn);
+        v[11] = __dadd_ru(v[11], vhi_up);
+        v[12] = __dadd_ru(v[12], __dsub_ru(vlo_up, vlo_dn));
+        v[13] = __dadd_ru(v[13], __dsub_ru(vhi_up, vhi_dn));
+        v[14] = __dadd_rd(v[14], x);
+        v[15] = __dadd_ru(v[15], x);
+        v[16] = __dadd_rd(v[16], y);
+        v[17] = __dadd_ru(v[17], y);
+    }
+}
+
+// Stage 1 of the assembly: block (g, box) sums its slice -- items g*128 + t +
+// k*(n_stage*128) -- of the contingency partial rows, the base partial rows and
+// the devices (directed FP64), then reduces its 128 threads in a fixed tree
+// and writes the kAsmVals sums; the result does not depend on timing.
 __global__ void __launch_bounds__(128) k_partials(AsmArgs a) {
     const int g = blockIdx.x, j = blockIdx.y;
-    const int n = ctg_partial_rows(a);
-    double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
-    for (int p = g * 128 + threadIdx.x; p < n; p += a.n_stage * 128) {
-        const double4 q = *reinterpret_cast<const double4 *>(a.part_ctg + ((size_t)p * a.n_box + j) * kPartVals);
-        v0 = __dadd_rd(v0, q.x);
-        v1 = __dadd_ru(v1, q.y);
-        v2 = __dadd_ru(v2, q.z);
-        v3 = __dadd_ru(v3, q.w);
+    const int n = ctg_partial_rows(a), first = g * 128 + (int)threadIdx.x, stride = a.n_stage * 128;
+    double v[kAsmVals];
+    bool up[kAsmVals];
+#pragma unroll
+    for (int i = 0; i < kAsmVals; ++i) {
+        v[i] = 0.0;
+        up[i] = asm_up(i);
     }
-    v0 = warp_sum_rd(v0);
-    v1 = warp_sum_ru(v1);
-    v2 = warp_sum_ru(v2);
-    v3 = warp_sum_ru(v3);
-    __shared__ double sh[4][4];
-    const int w = threadIdx.x >> 5;
-    if ((threadIdx.x & 31) == 0) {
-        sh[w][0] = v0;
-        sh[w][1] = v1;
-        sh[w][2] = v2;
-        sh[w][3] = v3;
-    }
-    __syncthreads();
+    for (int p = first; p < n; p += stride)
+        add_rows(v, a.part_ctg + ((size_t)p * a.n_box + j) * kPartVals);
+    for (int p = first; p < a.n_part_base; p += stride)
+        add_rows(v + 4, a.part_base + ((size_t)p * a.n_box + j) * kPartVals);
+    for (int d = first; d < a.n_dev; d += stride) add_device(a, j, d, v);
+    __shared__ double sh[4 * kAsmVals];
+    block_sum(v, kAsmVals, up, sh);
     if (threadIdx.x == 0) {
-        double r0 = 0.0, r1 = 0.0, r2 = 0.0, r3 = 0.0;
-        for (int i = 0; i < 4; ++i) {
-            r0 = __dadd_rd(r0, sh[i][0]);
-            r1 = __dadd_ru(r1, sh[i][1]);
-            r2 = __dadd_ru(r2, sh[i][2]);
-            r3 = __dadd_ru(r3, sh[i][3]);
-        }
-        double *o = a.part_stage + ((size_t)j * a.n_stage + g) * kPartVals;
-        o[0] = r0;
-        o[1] = r1;
-        o[2] = r2;
-        o[3] = r3;
+        double *o = a.part_stage + ((size_t)j * a.n_stage + g) * kAsmVals;
+#pragma unroll
+        for (int i = 0; i < kAsmVals; ++i) o[i] = v[i];
     }
 }
 
 __global__ void __launch_bounds__(256) k_assemble(AsmArgs a) {
     const int j = blockIdx.x;
-    // 0 Sfc_lo(rd) 1 Sfc_hi(ru) 2 Wfc_hi(ru) 3 Wfc_lo(ru) 4 Sfb_lo 5 Sfb_hi 6 Wfb_hi 7 Wfb_lo
-    // 8 Clo_dn 9 Chi_up 10 Glo_dn 11 Ghi_up 12 cost_err_hi(ru) 13 cost_err_lo(ru)
-    // 14 Plo_dn 15 Plo_up 16 Phi_dn 17 Phi_up
-    constexpr int N = 18;
+    constexpr int N = kAsmVals;
     double v[N];
-    bool up[N] = {false, true, true, true, false, true, true, true, false, true, false, true,
-                  true, true, false, true, false, true};
-    for (int i = 0; i < N; ++i) v[i] = 0.0;
+    bool up[N];
+    for (int i = 0; i < N; ++i) {
+        v[i] = 0.0;
+        up[i] = asm_up(i);
+    }
     if (a.part_stage) {
+        // stage 1 (k_partials) summed the rows and devices: combine its blocks
         for (int p = threadIdx.x; p < a.n_stage; p += blockDim.x) {
-            const double *q = a.part_stage + ((size_t)j * a.n_stage + p) * kPartVals;
-            v[0] = __dadd_rd(v[0], q[0]);
-            v[1] = __dadd_ru(v[1], q[1]);
-            v[2] = __dadd_ru(v[2], q[2]);
-            v[3] = __dadd_ru(v[3], q[3]);
+            const double *q = a.part_stage + ((size_t)j * a.n_stage + p) * N;
+            for (int i = 0; i < N; ++i) v[i] = up[i] ? __dadd_ru(v[i], q[i]) : __dadd_rd(v[i], q[i]);
         }
     } else {
         const int n_part_ctg = ctg_partial_rows(a);
-        for (int p = threadIdx.x; p < n_part_ctg; p += blockDim.x) {
-            const double *q = a.part_ctg + ((size_t)p * a.n_box + j) * kPartVals;
-            v[0] = __dadd_rd(v[0], q[0]);
-            v[1] = __dadd_ru(v[1], q[1]);
-            v[2] = __dadd_ru(v[2], q[2]);
-            v[3] = __dadd_ru(v[3], q[3]);
-        }
-    }
-    for (int p = threadIdx.x; p < a.n_part_base; p += blockDim.x) {
-        const double *q = a.part_base + ((size_t)p * a.n_box + j) * kPartVals;
-        v[4] = __dadd_rd(v[4], q[0]);
-        v[5] = __dadd_ru(v[5], q[1]);
-        v[6] = __dadd_ru(v[6], q[2]);
-        v[7] = __dadd_ru(v[7], q[3]);
-    }
-    const double *lo = a.box_lo + (size_t)j * a.n_dev;
-    const double *hi = a.box_hi + (size_t)j * a.n_dev;
-    for (int d = threadIdx.x; d < a.n_dev; d += blockDim.x) {
-        const int s0 = a.seg_ptr[d], ns = a.seg_ptr[d + 1] - s0;
-        const double *sl = a.slope + s0, *bk = a.bkpt + s0;
-        const double vlo_dn = pwl_eval(sl, bk, ns, lo[d], false);
-        const double vlo_up = pwl_eval(sl, bk, ns, lo[d], true);
-        const double vhi_dn = pwl_eval(sl, bk, ns, hi[d], false);
-        const double vhi_up = pwl_eval(sl, bk, ns, hi[d], true);
-        if (d >= a.n_gen) {  // load value c_j: C(hi) enters obj_hi, C(lo) enters obj_lo
-            v[8] = __dadd_rd(v[8], vlo_dn);
-            v[9] = __dadd_ru(v[9], vhi_up);
-            v[12] = __dadd_ru(v[12], __dsub_ru(vhi_up, vhi_dn));
-            v[13] = __dadd_ru(v[13], __dsub_ru(vlo_up, vlo_dn));
-            v[14] = __dadd_rd(v[14], -hi[d]);
-            v[15] = __dadd_ru(v[15], -hi[d]);
-            v[16] = __dadd_rd(v[16], -lo[d]);
-            v[17] = __dadd_ru(v[17], -lo[d]);
-        } else {  // generator cost g_i: G(lo) enters obj_hi, G(hi) enters obj_lo
-            v[10] = __dadd_rd(v[10], vlo_dn);
-            v[11] = __dadd_ru(v[11], vhi_up);
-            v[12] = __dadd_ru(v[12], __dsub_ru(vlo_up, vlo_dn));
-            v[13] = __dadd_ru(v[13], __dsub_ru(vhi_up, vhi_dn));
-            v[14] = __dadd_rd(v[14], lo[d]);
-            v[15] = __dadd_ru(v[15], lo[d]);
-            v[16] = __dadd_rd(v[16], hi[d]);
-            v[17] = __dadd_ru(v[17], hi[d]);
-        }
+        for (int p = threadIdx.x; p < n_part_ctg; p += blockDim.x)
+            add_rows(v, a.part_ctg + ((size_t)p * a.n_box + j) * kPartVals);
+        for (int p = threadIdx.x; p < a.n_part_base; p += blockDim.x)
+            add_rows(v + 4, a.part_base + ((size_t)p * a.n_box + j) * kPartVals);
+        for (int d = threadIdx.x; d < a.n_dev; d += blockDim.x) add_device(a, j, d, v);
     }
     __shared__ double sh[8 * N];
     block_sum(v, N, up, sh);
