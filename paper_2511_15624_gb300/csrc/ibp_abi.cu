@@ -124,7 +124,7 @@ struct ibp_case {
     DevBuf<double> box_lo, box_hi, obj;
     DevBuf<double> cbus;
     DevBuf<float2> cbus2;
-    DevBuf<float> rbus, cabs, box_consts, line_c, line_e, line_R, rbus_t;
+    DevBuf<float> rbus, cabs, box_consts, line_c, line_e, line_R, rbus_t, bus_part;
     DevBuf<double> part_base, part_ctg, part_stage;
     DevBuf<float> flows;
     DevBuf<int> err;
@@ -151,7 +151,7 @@ struct ibp_case {
             rate_c_dn.free(); ctg_line.free(); act_ptr.free(); act_dev.free(); seg_ptr.free();
             slope.free(); bkpt.free(); hat_l.free(); hat_k.free(); phi_k.free(); rbus_t.free();
             box_lo.free(); box_hi.free();
-            obj.free(); cbus.free(); cbus2.free(); rbus.free(); cabs.free(); box_consts.free(); line_c.free();
+            obj.free(); cbus.free(); cbus2.free(); rbus.free(); cabs.free(); box_consts.free(); bus_part.free(); line_c.free();
             line_e.free(); line_R.free(); part_base.free(); part_ctg.free(); part_stage.free(); flows.free(); err.free();
             live_flag.free(); live.free(); n_live.free(); is_bridge.free(); cls_ptr.free();
             cls_col.free(); phi_r.free(); phi_kr.free(); rcls.free(); rcls_t.free(); nb_list.free();
@@ -767,6 +767,7 @@ static ibp_status ensure_workspace(ibp_case *c, int n_box) {
     CUDA_TRY(c->rbus.alloc(cap * na));
     CUDA_TRY(c->cabs.alloc(cap * na));
     CUDA_TRY(c->box_consts.alloc((size_t)cap * 4));
+    CUDA_TRY(c->bus_part.alloc((size_t)cap * bus_blocks(c->n_a_pad) * 4));
     CUDA_TRY(c->line_c.alloc((size_t)cap * c->n_line));
     CUDA_TRY(c->line_e.alloc((size_t)cap * c->n_line));
     CUDA_TRY(c->line_R.alloc((size_t)cap * c->n_line));
@@ -832,6 +833,7 @@ static ibp_status enqueue_bound(ibp_case *c, int n_box, const double *lo, const 
     ba.cbus = c->cbus.p; ba.cbus2 = c->cbus2.p; ba.rbus = c->rbus.p; ba.rbus_t = multi ? c->rbus_t.p : nullptr;
     ba.n_box_pad = n_box_pad;
     ba.cabs = c->cabs.p; ba.box_consts = c->box_consts.p; ba.err = c->err.p;
+    ba.bus_part = c->bus_part.p;
     CUDA_TRY(launch_bus(ba, s));
     if (reduced) {
         ClsArgs ra{};
@@ -1376,6 +1378,7 @@ extern "C" ibp_status ibp_bound_multi(int32_t n_case, ibp_case *const *cases, co
         ba.cbus = c->cbus.p; ba.cbus2 = c->cbus2.p; ba.rbus = c->rbus.p; ba.rbus_t = c->rbus_t.p;
         ba.n_box_pad = n_box_pad;
         ba.cabs = c->cabs.p; ba.box_consts = c->box_consts.p; ba.err = c->err.p;
+        ba.bus_part = c->bus_part.p;
         CUDA_TRY(launch_bus(ba, s));
         if (red) {
             ClsArgs ra{};

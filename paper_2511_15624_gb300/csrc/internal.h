@@ -37,7 +37,13 @@ struct BusArgs {
     float *cabs;            // [n_box][n_a_pad] |centre| rounded up
     float *box_consts;      // [n_box][4] eta_r, eta_c, sum r, sum |c|
     int *err;
+    // [n_box][bus_blocks(n_a_pad)][4] per-block sums (sum r, sum |c|, bad box);
+    // null: one block per box writes box_consts itself
+    float *bus_part;
 };
+
+// column blocks per box of the box -> bus kernel when it has bus_part
+inline int bus_blocks(int n_a_pad) { return (n_a_pad + 255) / 256; }
 
 struct BaseArgs {
     int n_l, n_c, n_a, n_a_pad, n_box;

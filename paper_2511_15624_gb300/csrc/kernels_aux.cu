@@ -16,19 +16,39 @@ namespace ibp {
 //   P_lo = sum_{g@b} lo_g - sum_{d@b} hi_d,  P_hi = sum_{g@b} hi_g - sum_{d@b} lo_d
 // (rounded down / up).  The centre c = (P_lo + P_hi)/2 may round; the radius
 // r = max(P_hi - c, c - P_lo) is rounded up, so [c - r, c + r] contains the
-// interval whatever c is.  One block per box.
+// interval whatever c is.  Block (b, j) takes the columns b*256 + t +
+// k*(gridDim.x*256) of box j; the per-box sums of r and |c| are round-up sums
+// in a fixed order (blocks, then k_bus_consts over the blocks when there are
+// several).
 // ---------------------------------------------------------------------------
+// round-up sums of r and |c| and the bad-box flag -> the box constants
+__device__ __forceinline__ void write_box_consts(const BusArgs &a, int j, float R, float C, int B) {
+    // Absolute error allowances for FP32 underflow (entries of Phi and L
+    // below 2^-120 are stored as 0; products may be subnormal):
+    //   eta_r covers sum_b |dPhi| r_b and per-term subnormal rounding,
+    //   eta_c covers sum_b |dPhi| |c_b|.
+    const float t120 = 7.52316384526264e-37f;   // 2^-120
+    const float t99 = 1.5777218104420236e-30f;  // 2^-99
+    float *bc = a.box_consts + (size_t)j * 4;
+    bc[0] = __fadd_ru(__fmul_ru(t99, R), __fmul_ru(t120, (float)a.n_a));
+    bc[1] = __fmul_ru(t99, C);
+    bc[2] = R;
+    bc[3] = C;
+    if (B) atomicOr(a.err, kErrBadBox);
+}
+
 __global__ void __launch_bounds__(256) k_bus(BusArgs a) {
-    const int j = blockIdx.x;
+    const int j = blockIdx.y;
+    const int first = blockIdx.x * blockDim.x + threadIdx.x, stride = gridDim.x * blockDim.x;
     const double *lo = a.box_lo + (size_t)j * a.n_dev;
     const double *hi = a.box_hi + (size_t)j * a.n_dev;
     float rsum = 0.0f, csum = 0.0f;
     int bad = 0;
-    for (int d = threadIdx.x; d < a.n_dev; d += blockDim.x) {
+    for (int d = first; d < a.n_dev; d += stride) {
         const double x = lo[d], y = hi[d];
         if (!(x <= y) || !isfinite(x) || !isfinite(y)) bad = 1;
     }
-    for (int col = threadIdx.x; col < a.n_a_pad; col += blockDim.x) {
+    for (int col = first; col < a.n_a_pad; col += stride) {
         double c = 0.0;
         float r32 = 0.0f, ca = 0.0f;
         if (col < a.n_a) {
@@ -79,23 +99,38 @@ __global__ void __launch_bounds__(256) k_bus(BusArgs a) {
             C = __fadd_ru(C, sc[i]);
             B |= sbad[i];
         }
-        // Absolute error allowances for FP32 underflow (entries of Phi and L
-        // below 2^-120 are stored as 0; products may be subnormal):
-        //   eta_r covers sum_b |dPhi| r_b and per-term subnormal rounding,
-        //   eta_c covers sum_b |dPhi| |c_b|.
-        const float t120 = 7.52316384526264e-37f;   // 2^-120
-        const float t99 = 1.5777218104420236e-30f;  // 2^-99
-        float *bc = a.box_consts + (size_t)j * 4;
-        bc[0] = __fadd_ru(__fmul_ru(t99, R), __fmul_ru(t120, (float)a.n_a));
-        bc[1] = __fmul_ru(t99, C);
-        bc[2] = R;
-        bc[3] = C;
-        if (B) atomicOr(a.err, kErrBadBox);
+        if (gridDim.x == 1) {
+            write_box_consts(a, j, R, C, B);
+        } else {
+            float *q = a.bus_part + ((size_t)j * gridDim.x + blockIdx.x) * 4;
+            q[0] = R;
+            q[1] = C;
+            q[2] = B ? 1.0f : 0.0f;
+        }
     }
 }
 
+// the blocks' sums of box j, in block order
+__global__ void k_bus_consts(BusArgs a, int n_blocks) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= a.n_box) return;
+    float R = 0.0f, C = 0.0f;
+    int B = 0;
+    for (int b = 0; b < n_blocks; ++b) {
+        const float *q = a.bus_part + ((size_t)j * n_blocks + b) * 4;
+        R = __fadd_ru(R, q[0]);
+        C = __fadd_ru(C, q[1]);
+        B |= q[2] != 0.0f;
+    }
+    write_box_consts(a, j, R, C, B);
+}
+
 cudaError_t launch_bus(const BusArgs &a, cudaStream_t s) {
-    k_bus<<<a.n_box, 256, 0, s>>>(a);
+    const int nb = a.bus_part ? bus_blocks(a.n_a_pad) : 1;
+    k_bus<<<dim3(nb, a.n_box), 256, 0, s>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || nb == 1) return e;
+    k_bus_consts<<<(a.n_box + 127) / 128, 128, 0, s>>>(a, nb);
     return cudaGetLastError();
 }
 
