@@ -388,9 +388,12 @@ def run_gb300(args):
         "e2e": {"value": e2e_ms / bounds, "unit": "ms",
                 "h2d_bytes_per_step": int(2 * case.box_lo.nbytes),
                 "d2h_bytes_per_step": int(3 * 8 * nb)},
-        # per step: box->bus, base flows, contingency, partial sums, assembly;
-        # screen, compaction and row gather; class radii under the reduction
-        "gpu_launches": (5 + (3 if n_live_screened else 0) + (1 if reduced else 0)) * args.steps,
+        # per step: box->bus and its per-box totals (one launch when the
+        # active columns fit one block), base flows, contingency, partial
+        # sums, assembly; screen, compaction and row gather; class radii under
+        # the reduction
+        "gpu_launches": (5 + (1 if info.n_active_pad > 256 else 0) + (3 if n_live_screened else 0)
+                         + (1 if reduced else 0)) * args.steps,
         "batched": None if batched is None else {
             **batched, "frac": batched["achieved_tflops"] / fp32_peak,
             "interval_flows_per_s": case.n_ctg * case.n_line * batched["boxes"] / (batched["ms_per_call"] * 1e-3)},
