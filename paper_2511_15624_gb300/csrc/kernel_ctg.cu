@@ -726,27 +726,42 @@ static cudaError_t launch_cases(const MultiItem *items, const int *cta_start, co
 // (8 warps), 22/23 (box halves), 26 (8 warps, packed FMA), 27 (box halves,
 // packed FMA), each with 4 stages, and 28 (4 lines x 2 contingencies x 8 boxes
 // per thread); 29 and any other value run the default, 28's body with 6
-// stages.  cases_rows_per_item gives the partial rows each body writes per
-// work item; the two switches must agree.
+// stages.  The launch and the partial-row count both dispatch through
+// with_cases_body, so they agree.
+template <int ST_, int BH_, bool PK_, int MK_>
+struct CasesBody {
+    static constexpr int ST = ST_, BH = BH_, MK = MK_;
+    static constexpr bool PK = PK_;
+};
+
+template <class F>
+static auto with_cases_body(int variant, F f) {
+    switch (variant) {
+    case 20: case 21: return f(CasesBody<4, 1, false, 1>{});
+    case 22: case 23: return f(CasesBody<4, 2, false, 1>{});
+    case 26: return f(CasesBody<4, 1, true, 1>{});
+    case 27: return f(CasesBody<4, 2, true, 1>{});
+    case 28: return f(CasesBody<4, 2, true, 2>{});
+    default: return f(CasesBody<6, 2, true, 2>{});
+    }
+}
+
 cudaError_t launch_ctg_cases(int variant, const MultiItem *items, const int *cta_start,
                              const uint32_t *prefix, const CtgArgs *args, const CUtensorMap *maps,
                              int grid, unsigned long long wait_ns, int *err, cudaStream_t s) {
     if (grid <= 0) return cudaSuccess;
-    switch (variant) {
-    case 20: case 21: return launch_cases<4, 1, false, 1>(items, cta_start, prefix, args, maps, grid, wait_ns, err, s);
-    case 22: case 23: return launch_cases<4, 2, false, 1>(items, cta_start, prefix, args, maps, grid, wait_ns, err, s);
-    case 26: return launch_cases<4, 1, true, 1>(items, cta_start, prefix, args, maps, grid, wait_ns, err, s);
-    case 27: return launch_cases<4, 2, true, 1>(items, cta_start, prefix, args, maps, grid, wait_ns, err, s);
-    case 28: return launch_cases<4, 2, true, 2>(items, cta_start, prefix, args, maps, grid, wait_ns, err, s);
-    default: return launch_cases<6, 2, true, 2>(items, cta_start, prefix, args, maps, grid, wait_ns, err, s);
-    }
+    return with_cases_body(variant, [&](auto body) {
+        using B = decltype(body);
+        return launch_cases<B::ST, B::BH, B::PK, B::MK>(items, cta_start, prefix, args, maps, grid,
+                                                        wait_ns, err, s);
+    });
 }
 
 int cases_rows_per_item(int variant) {
-    switch (variant) {
-    case 20: case 21: case 22: case 23: case 26: case 27: return MultiShape<4, 1, 4, 1>::kWarpsHalf;
-    default: return MultiShape<6, 2, 4, 2>::kWarpsHalf;
-    }
+    return with_cases_body(variant, [](auto body) {
+        using B = decltype(body);
+        return MultiShape<B::ST, B::BH, 4, B::MK>::kWarpsHalf;
+    });
 }
 
 void multi_tile_shape(int *BL, int *BK, int *CH) {
