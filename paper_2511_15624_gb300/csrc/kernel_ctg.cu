@@ -6,9 +6,10 @@
 //
 // |H_k| is never stored: each CTA owns a tile of BL lines x BK contingencies
 // and streams bus chunks of the two PTDF row blocks through shared memory with
-// TMA (SWIZZLE_128B, a ring of ST stages guarded by mbarriers), while 8 warps
-// hold the tile's LODF entries and radius accumulators in registers.  Persistent launch: one CTA per SM walks the tile
-// list with a static stride (deterministic output).
+// TMA (SWIZZLE_128B, a ring of ST stages guarded by mbarriers), while its warps
+// hold the tile's LODF entries and radius accumulators in registers.
+// Persistent launch: as many CTAs as fit on the SMs walk the tile list with a
+// static stride (deterministic output).
 //
 // One-box variant: the rows are pre-scaled by the bus radius,
 //   hat[x,b] = RN(Phi~[x,b] r_b),   h' = RN(hat[l,b] + L~ hat[k,b]),
@@ -20,10 +21,11 @@
 // so  r_kl <= (1 + u) sum|h'| + 4u (R~_l + |L~| R~_k)  (+ eta for underflow),
 // and sum|h'| <= A (the round-up sum), giving the certified radius
 //   rbar = RU((1 + u) A + 4u (R~_l + |L~| R~_k) + eta).
-// The round-up sum is hierarchical (32 buses per chunk, 8 chunks per level-2
-// sum, the rest in level 3) to keep its excess
-// small; gamma bounds it.  Eight warps (two per SM sub-partition) leave room
-// for 255 registers per thread, so all three levels stay in registers.
+// The round-up sum is hierarchical (one chunk of CH buses, 256 / CH chunks per
+// level-2 sum, the rest in level 3, which S3 keeps in shared memory) to keep
+// its excess small; gamma bounds it.  The default one-box shape runs two CTAs
+// of 8 warps per SM at 128 registers per thread; a thread owns 4 x 4 pairs and
+// sums each pair in two packed lanes (BODY 2).
 //
 // Multi-box variant: h = RN(Phi~[l,b] + L~ Phi~[k,b]) once per (pair, bus),
 // then acc_j <- RU(acc_j + |h| r_jb) for the thread's boxes; the same bound
