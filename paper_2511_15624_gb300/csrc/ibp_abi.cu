@@ -723,7 +723,8 @@ ibp_status set_error(ibp_status s, const char *msg) {
 // ----------------------------------------------------------------- workspace
 // fastest shapes measured on GB300: one box, 2 CTAs per SM of 8 warps, 4x4
 // pairs per thread, 64-bus chunks in 2 stages, packed two-lane sums; many
-// boxes, 8 warps, 4 lines x 16 boxes per thread, packed FMA
+// boxes, 8 warps in two box halves, 4 lines x 2 contingencies x 8 boxes per
+// thread, packed FMA, 6 stages
 constexpr int kDefaultOneBoxVariant = 16;
 constexpr int kDefaultMultiBoxVariant = 29;
 

@@ -441,7 +441,9 @@ cudaError_t launch_base(const BaseArgs &a, int n_part, cudaStream_t s) {
 }
 
 // ---------------------------------------------------------------------------
-// Objective assembly, one block per box (eq. (penalized-objective), appendix
+// Objective assembly, in two stages: k_partials (64 blocks per box) sums
+// slices of the rows and devices, k_assemble (one block per box) adds them and
+// forms the objective (eq. (penalized-objective), appendix
 // eq. (ibp_f) under eq. (IBP)):
 //   hi = C(pd_hi) - G(pg_lo) - z_inj s_inj,lo - z_f (S_fb,lo + S_fc,lo)
 //   lo = C(pd_lo) - G(pg_hi) - z_inj s_inj,hi - z_f (S_fb,hi + S_fc,hi)
