@@ -28,6 +28,10 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "ms per certified N-1 objective bound, 8316-bus"
+# FP32 FMA throughput a register-only loop reaches on a GB300 (8 independent
+# FFMA chains per thread, 8 CTAs of 256 threads per SM, CUDA events): 37.2e12
+# lane-FMAs/s, reported beside the nominal peak as a second reference
+FMA_LOOP_TFLOPS = 74.4
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
 # contingency kernel, from a one-pass ncu capture of this same kernel build on
@@ -383,7 +387,10 @@ def run_gb300(args):
                      "frac": achieved / fp32_peak,
                      "traffic": MEASURED_TRAFFIC.get((args.config, args.variant, not args.no_screen,
                                                       reduced)),
-                     "peak_source": f"{sm_count} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz"},
+                     "peak_source": f"{sm_count} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz",
+                     "fma_loop_peak": {"value": FMA_LOOP_TFLOPS, "unit": "TFLOP/s",
+                                       "frac": achieved / FMA_LOOP_TFLOPS,
+                                       "source": "register-only FFMA loop on GB300 (measured)"}},
         "clocks": clocks,
         "e2e": {"value": e2e_ms / bounds, "unit": "ms",
                 "h2d_bytes_per_step": int(2 * case.box_lo.nbytes),
