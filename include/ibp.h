@@ -123,7 +123,10 @@ void ibp_case_destroy(ibp_case *c);
  *     obj_hi < 0 certifies that the box is welfare-negative, eq. (inf-or-wn).
  *   flow_lo, flow_hi [n_box][n_ctg][n_line] (FP32) or NULL: outward-rounded
  *     post-contingency flow intervals (the outaged line is exactly [0, 0]).
- * n_box >= 1 (n_box == 0 is a no-op returning IBP_OK).
+ * 1 <= n_box <= 65535 (n_box == 0 is a no-op returning IBP_OK; more than
+ * 65535 boxes return IBP_EINVAL: split them over several calls).  The same
+ * limit holds for ibp_bound_paper, ibp_bound_backward and each case of
+ * ibp_bound_multi.
  */
 ibp_status ibp_bound(ibp_case *c, int32_t n_box, const double *box_lo,
                      const double *box_hi, double *obj_lo, double *obj_hi,

@@ -995,12 +995,16 @@ static ibp_status check_boxes_host(const ibp_case *c, int n_box, const double *l
     return IBP_OK;
 }
 
+// boxes per call: several kernels put the box index on a grid's y dimension
+constexpr int32_t kMaxBoxesPerCall = 65535;
+
 static ibp_status bound_entry(ibp_case *c, int32_t n_box, const double *box_lo,
                               const double *box_hi, double *obj_lo, double *obj_hi, double *obj_err,
                               float *flow_lo, float *flow_hi, int32_t ptr_mode, void *cuda_stream,
                               bool paper) {
     if (!c) return fail(IBP_EINVAL, "case is NULL");
     if (n_box < 0) return fail(IBP_EINVAL, "n_box must be >= 0");
+    if (n_box > kMaxBoxesPerCall) return fail(IBP_EINVAL, "n_box must be <= %d", kMaxBoxesPerCall);
     if (ptr_mode != 0 && ptr_mode != 1) return fail(IBP_EINVAL, "ptr_mode must be 0 or 1");
     if (n_box == 0) return ok();
     if (!box_lo || !box_hi || !obj_lo || !obj_hi || !obj_err)
@@ -1113,6 +1117,7 @@ extern "C" ibp_status ibp_bound_backward(ibp_case *c, int32_t n_box, const doubl
                                          int32_t ptr_mode, void *cuda_stream) {
     if (!c) return fail(IBP_EINVAL, "case is NULL");
     if (n_box < 0) return fail(IBP_EINVAL, "n_box must be >= 0");
+    if (n_box > kMaxBoxesPerCall) return fail(IBP_EINVAL, "n_box must be <= %d", kMaxBoxesPerCall);
     if (ptr_mode != 0 && ptr_mode != 1) return fail(IBP_EINVAL, "ptr_mode must be 0 or 1");
     if (n_box == 0) return ok();
     if (!box_lo || !box_hi || !grad_obj_hi || !grad_lo || !grad_hi)
@@ -1337,7 +1342,8 @@ extern "C" ibp_status ibp_bound_multi(int32_t n_case, ibp_case *const *cases, co
         if (!cases[i]) return fail(IBP_EINVAL, "case %d is NULL", i);
         if (cases[i]->device < 0) return fail(IBP_ENOTSUP, "case %d was created without a device", i);
         if (cases[i]->device != cases[0]->device) return fail(IBP_EINVAL, "cases live on different devices");
-        if (n_box[i] < 1) return fail(IBP_EINVAL, "n_box[%d] must be >= 1", i);
+        if (n_box[i] < 1 || n_box[i] > kMaxBoxesPerCall)
+            return fail(IBP_EINVAL, "n_box[%d] must be in [1, %d]", i, kMaxBoxesPerCall);
         if (!box_lo[i] || !box_hi[i] || !obj_lo[i] || !obj_hi[i] || !obj_err[i])
             return fail(IBP_EINVAL, "pointers of case %d must not be NULL", i);
         for (int j = 0; j < i; ++j)

@@ -96,6 +96,11 @@ def test_box_validation_before_device(pkg):
     _expect(P, P._abi.IBP_ENOTSUP, lambda: d.bound(c.box_lo, c.box_hi))
     with pytest.raises(ValueError):
         d.bound(c.box_lo[:, :3], c.box_hi[:, :3])
+    # at most 65535 boxes per call (the box index is a grid's y dimension)
+    many_lo = np.repeat(c.box_lo, 65536, axis=0)
+    many_hi = np.repeat(c.box_hi, 65536, axis=0)
+    _expect(P, P._abi.IBP_EINVAL, lambda: d.bound(many_lo, many_hi))
+    _expect(P, P._abi.IBP_EINVAL, lambda: d.backward(many_lo, many_hi, np.ones(65536)))
 
 
 def test_no_cpu_fallback_without_device(pkg):
