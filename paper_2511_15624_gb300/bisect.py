@@ -71,6 +71,10 @@ class Bisection:
         self._t0 = None
         self._elapsed = 0.0
 
+    def _sync(self):
+        if self.device.type == "cuda":
+            torch.cuda.synchronize(self.device)
+
     # -------------------------------------------------------------- bounds
     def _bound(self, lo, hi):
         if self.batched:
@@ -96,7 +100,7 @@ class Bisection:
 
     # -------------------------------------------------------------- rounds
     def step(self) -> RoundRecord:
-        torch.cuda.synchronize(self.device)
+        self._sync()
         t0 = time.perf_counter()
         n = self.lo.shape[0]
         both_lo = torch.cat([self.lo, self.y])
@@ -155,7 +159,7 @@ class Bisection:
             self.s = torch.cat([sv[rest], ss, ss])
         else:
             self.lo, self.hi, self.x, self.fx, self.y, self.s = lo, hi, x, fx, y, sv
-        torch.cuda.synchronize(self.device)
+        self._sync()
         self._elapsed += time.perf_counter() - t0
         self.round += 1
         gap = (self.ub - self.lb) / max(abs(self.lb), 1e-300)
