@@ -4,6 +4,8 @@ the leaves stay inside the root box and do not overlap, the upper bound never
 rises and stays above f at every sampled point of the root box, the lower
 bound never falls and never passes the upper bound, and a saved frontier
 reloads to the same next round."""
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -14,7 +16,10 @@ from paper_2511_15624_gb300.bisect import Bisection
 
 
 class OracleCase:
-    """bound() and backward() of the case API, computed by the oracle."""
+    """bound() and backward() of the case API, computed by the oracle on one
+    thread (its threaded sums add in scheduling order, so two calls on the same
+    boxes could differ in the last bit, and the checkpoint test compares
+    exactly)."""
 
     def __init__(self, case):
         self.case = case
@@ -22,11 +27,11 @@ class OracleCase:
         self.device = 0
 
     def bound(self, lo, hi):
-        r = O.bound(self.case, self.sens, lo.numpy(), hi.numpy())
+        r = O.bound(self.case, self.sens, lo.numpy(), hi.numpy(), nthreads=1)
         return torch.tensor(r.lo), torch.tensor(r.hi), None
 
     def backward(self, lo, hi, g):
-        gl, gh, _ = O.grad_hi(self.case, self.sens, lo.numpy(), hi.numpy())
+        gl, gh, _ = O.grad_hi(self.case, self.sens, lo.numpy(), hi.numpy(), nthreads=1)
         w = g.numpy()[:, None]
         return torch.tensor(gl * w), torch.tensor(gh * w)
 
@@ -34,7 +39,10 @@ class OracleCase:
 @pytest.fixture(scope="module")
 def ring():
     case = make_config(0)
-    return case, OracleCase(case)
+    oc = OracleCase(case)
+    yield case, oc
+    # the oracle's thread count is process-wide: give the later tests all cores again
+    O.bound(case, oc.sens, nthreads=len(os.sched_getaffinity(0)))
 
 
 def _run(ring, batched, rounds):
