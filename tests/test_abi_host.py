@@ -159,3 +159,15 @@ def test_network_reduction_partition(pkg, which):
         assert np.abs(s.lodf[br.astype(bool)]).max() <= 1e-9
     if which in ("sparse", "two-core"):
         assert info.n_bus_classes < info.n_active
+
+
+def test_kernel_variant_lists(pkg):
+    """The compiled kernel shapes (no GPU needed): one-box and multi-box ids are
+    disjoint and unique, and each list holds the library's default for its box
+    count (16 for one box, 29 for several)."""
+    P = pkg
+    one = P._abi.ibp_kernel_variants(False)
+    many = P._abi.ibp_kernel_variants(True)
+    assert len(set(one)) == len(one) and len(set(many)) == len(many)
+    assert not set(one) & set(many)
+    assert 16 in one and 29 in many
