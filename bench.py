@@ -372,6 +372,7 @@ def run_gb300(args):
     fp32_peak = sm_count * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s, FMA lanes x 2 x max clock
     flop = P.algorithmic_flop(case.n_ctg, n_live, n_cols, nb)
     achieved = flop / (ctg_ms * 1e-3) / 1e12
+    traffic = MEASURED_TRAFFIC.get((args.config, args.variant, not args.no_screen, reduced))
     line = {
         "metric": METRIC, "value": value, "unit": "ms", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": False,
@@ -385,8 +386,10 @@ def run_gb300(args):
                    "kernel_ms": tot_k},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                      "frac": achieved / fp32_peak,
-                     "traffic": MEASURED_TRAFFIC.get((args.config, args.variant, not args.no_screen,
-                                                      reduced)),
+                     "traffic": traffic,
+                     # DRAM rate of the contingency kernel: measured bytes per launch over
+                     # its live duration
+                     "traffic_gbs": None if traffic is None else traffic / (ctg_ms * 1e-3) / 1e9,
                      "peak_source": f"{sm_count} SMs x 128 FP32 lanes x 2 flop x {sm_max:.0f} MHz",
                      "fma_loop_peak": {"value": FMA_LOOP_TFLOPS, "unit": "TFLOP/s",
                                        "frac": achieved / FMA_LOOP_TFLOPS,
