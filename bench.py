@@ -34,17 +34,49 @@ METRIC = "ms per certified N-1 objective bound, 8316-bus"
 FMA_LOOP_TFLOPS = 74.4
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the
-# contingency kernel, from a one-pass ncu capture of this same kernel build on
-# the same workload; keyed by (config, tile-shape variant, screen on,
-# network reduction on).  Other workloads, tile shapes or kernel builds
-# report null.
-MEASURED_TRAFFIC = {(3, 0, True, True): 0.9031e9}
+# contingency kernel, from a one-pass ncu capture on the same workload; keyed
+# by (config, tile-shape variant, screen on, network reduction on) and stored
+# with the SHA-256 prefix of the kernel sources it was taken on
+# (KERNEL_SOURCES).  Other workloads or tile shapes report null; a kernel
+# build whose sources no longer match reports null with a note.
+MEASURED_TRAFFIC = {(3, 0, True, True): (0.9031e9, "")}
+KERNEL_SOURCES = ("kernel_ctg.cu", "ctg_epilogue.cuh", "common.cuh", "internal.h")
+
+
+def kernel_sources_sha():
+    """SHA-256 prefix (16 hex digits) of the contingency kernel's sources."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2511_15624_gb300", "csrc", name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(key):
+    """(bytes per launch or None, note)."""
+    hit = MEASURED_TRAFFIC.get(key)
+    if hit is None:
+        return None, "no ncu capture of this workload and tile shape"
+    value, sha = hit
+    now = kernel_sources_sha()
+    if sha != now:
+        return None, (f"stale: the stored capture was taken on kernel sources {sha or 'unrecorded'}, "
+                      f"this build is {now}")
+    return value, f"ncu capture of kernel sources {sha}"
 
 
 def workload(case, cfg, nb):
     return (f"{case.name}: {case.n_bus} buses, {case.n_line} lines, {case.n_ctg} N-1 "
             f"contingencies, {case.n_gen} gens, {case.n_load} flexible loads, seed {1000 + cfg}, "
             f"{nb} box per bound")
+
+
+def bench_config(case, cfg, nb):
+    """The config object both arms print (the same keys and values)."""
+    return {"workload": workload(case, cfg, nb), "boxes": nb,
+            "l2": "no flush: the inputs exceed the cache (the streamed FP32 PTDF rows, 345 MB, "
+                  "exceed the 129 MB L2 of the GPU arm)"}
 
 
 def _args():
@@ -61,6 +93,8 @@ def _args():
                    help="run every line through the contingency kernel (no paper-mode line screen)")
     p.add_argument("--no-reduction", action="store_true",
                    help="stream every active bus and line (no exact network reduction)")
+    p.add_argument("--no-refine", action="store_true",
+                   help="FP32 bounds only (no FP64 refinement of the terms that can reach obj_hi)")
     p.add_argument("--boxes", type=int, default=32,
                    help="box count of the batched measurement on the same network (0 = skip)")
     p.add_argument("--study", default="", choices=["", "bisection", "ragged"],
@@ -212,7 +246,7 @@ def run_reference(args):
             "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": workload(case, args.config, 1), "boxes": 1, "l2": "n/a (CPU)"},
+            "config": bench_config(case, args.config, 1),
             "cpu_baseline": {"value": v, "unit": "ms", "cores": threads, "kind": "oracle",
                              "sample": desc},
             "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -241,6 +275,8 @@ def run_gb300(args):
         gpu.set_screen(False)
     if args.no_reduction:
         gpu.set_reduction(False)
+    if args.no_refine:
+        gpu.set_refine(False)
     info = gpu.info()
     # columns the contingency kernel streams: bus classes under the reduction
     reduced = (not args.no_reduction) and (info.n_bridges > 0 or info.n_bus_classes < info.n_active)
@@ -372,21 +408,20 @@ def run_gb300(args):
     fp32_peak = sm_count * 128 * 2 * sm_max * 1e6 / 1e12  # TFLOP/s, FMA lanes x 2 x max clock
     flop = P.algorithmic_flop(case.n_ctg, n_live, n_cols, nb)
     achieved = flop / (ctg_ms * 1e-3) / 1e12
-    traffic = MEASURED_TRAFFIC.get((args.config, args.variant, not args.no_screen, reduced))
+    traffic, traffic_note = measured_traffic((args.config, args.variant, not args.no_screen, reduced))
     line = {
         "metric": METRIC, "value": value, "unit": "ms", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": dev_ms / args.steps, "higher_is_better": False,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": workload(case, args.config, nb), "boxes": nb,
-                   "n_active_buses": info.n_active, "lines_kept_by_screen": n_live,
+        "config": bench_config(case, args.config, nb),
+        "detail": {"n_active_buses": info.n_active, "lines_kept_by_screen": n_live,
                    "network_reduction": {"on": reduced, "bus_classes": info.n_bus_classes,
                                          "bridges": info.n_bridges},
                    "interval_flows_per_s": case.n_ctg * case.n_line * nb / (value * 1e-3),
-                   "l2": "no flush: the streamed PTDF rows (345 MB) exceed the 129 MB L2",
                    "kernel_ms": tot_k},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                      "frac": achieved / fp32_peak,
-                     "traffic": traffic,
+                     "traffic": traffic, "traffic_source": traffic_note,
                      # DRAM rate of the contingency kernel: measured bytes per launch over
                      # its live duration
                      "traffic_gbs": None if traffic is None else traffic / (ctg_ms * 1e-3) / 1e9,

@@ -137,8 +137,13 @@ ibp_status ibp_bound(ibp_case *c, int32_t n_box, const double *box_lo,
  * Adjoint of obj_hi (not certified; FP32 kernels with FP64 accumulation).
  * Given grad_obj_hi [n_box] (d loss / d obj_hi), writes
  *   grad_lo, grad_hi [n_box][n_gen + n_load]: d loss / d box_lo, d box_hi
- *   grad_rating [n_box][n_line] or NULL: d loss / d rating_ctg (contingency
- *     ratings; base ratings add their own term)
+ *   grad_rating [n_box][n_line] or NULL: d loss / d rating[l] when the base
+ *     rating and the contingency rating of line l move together (the shared
+ *     rating of a case created with rating_ctg = NULL):
+ *     zeta_f * grad_obj_hi * (the line's active base flow, 0 or 1, plus its
+ *     active contingency pairs), eqs. (slack-sfb), (slack-Sc).  With separate
+ *     contingency ratings, the base part alone is the derivative in rating
+ *     and the pair count alone the one in rating_ctg.
  * The derivative is taken with the active set of the forward pass (pairs whose
  * certified lower violation bound is > 0); it is valid away from kinks.
  */
@@ -173,14 +178,20 @@ ibp_status ibp_bound_multi(int32_t n_case, ibp_case *const *cases,
  *   box_lo, box_hi [n_gen + n_load], obj_lo, obj_hi [1], obj_err [2]: DEVICE
  *     pointers; the work is only enqueued on cuda_stream (NULL = legacy
  *     default stream).  Same results as ibp_bound up to FP32 rounding order
- *     (same certified arithmetic, unscaled PTDF rows); flows are not written.
+ *     (same certified arithmetic, unscaled PTDF rows, the same FP64
+ *     refinement of the obj_hi terms, queued per warp in shared memory);
+ *     flows are not written.
  * Limits and behaviour:
  *   - returns IBP_EINVAL, touching nothing, when the case needs more scratch
- *     than the array holds (about 1.5 MiB for 8316 buses, 10500 lines and
- *     5000 contingencies);
- *   - the first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress), so make that first call before any stream
- *     capture;
+ *     than the array holds.  The scratch is 24 bytes per active bus, 12 per
+ *     line, 256 per tile of 128 lines x 64 contingencies and 512 per SM, each
+ *     part rounded up to 256 bytes: 2,015,744 bytes (1.9 MiB) for 8316 buses
+ *     (5474 with a device), 10500 lines and 5000 contingencies on a 152-SM GPU;
+ *   - the first call on a device (in a CUDA context) looks up the array's
+ *     device address (cudaGetSymbolAddress), so make that first call before
+ *     any stream capture; after the context is created again (e.g. after
+ *     cudaDeviceReset) the next call looks the address up again, and must
+ *     likewise come before any capture;
  *   - every call, on every case, shares the one array (it keeps the last
  *     call's contents; the error word is cleared at the start of each call):
  *     calls whose work overlaps on the GPU race and must be serialised by the
@@ -280,15 +291,34 @@ ibp_status ibp_case_last_live(ibp_case *c, int32_t *n_live, int32_t *lines);
  * Works on dry-run cases.  No counterpart in the paper.
  */
 ibp_status ibp_case_set_reduction(ibp_case *c, int32_t enable);
+
+/*
+ * FP64 refinement of the terms that can reach obj_hi (enabled by default;
+ * enable = 0 disables).  obj_hi takes -zeta_f s_lo for every base line and
+ * contingency pair, s_lo = max(|c| - r - rating, 0) (eqs. (slack-sfb),
+ * (slack-Sc) under eq. (IBP)), and only the few terms whose lower violation
+ * bound can be positive contribute.  With the refinement on, the FP32 kernels
+ * leave those terms to one warp each, which recomputes the flow interval from
+ * the FP64 PTDF (kept on the device as the FP32 copy plus its FP32 remainder,
+ * about 4 bytes per line and active bus more) and the FP64 bus intervals with
+ * FP64 sums and an explicit error bound.  The term keeps its certification
+ * (a lower bound of the exact s_lo), and its share of obj_err falls from tens
+ * of FP32 units of the flow's magnitude to FP64 rounding.  All bound entry
+ * points (ibp_bound, ibp_bound_paper, ibp_bound_backward, ibp_bound_multi and
+ * ibp_bound_noalloc) use it.  obj_lo is unaffected.  No counterpart in the
+ * paper.
+ */
+ibp_status ibp_case_set_refine(ibp_case *c, int32_t enable);
 ibp_status ibp_case_reduction(const ibp_case *c, int32_t *class_of_active, int32_t *is_bridge);
 
 /*
  * Optional per-kernel timing of the last ibp_bound call, recorded with CUDA
  * events on the call's stream when enabled (0 disables).  ms[0..n) receives
- * {box_to_bus, base_flow, screen, contingency, assemble} durations in
+ * {box_to_bus, base_flow, screen, contingency, refine, assemble} durations in
  * milliseconds (screen is the paper-mode line screen and the gather of the
- * kept rows, about 0 when the call does not screen); the call synchronises
- * the stream.
+ * kept rows, about 0 when the call does not screen; refine is the FP64
+ * refinement of the queued pairs, see ibp_case_set_refine); the call
+ * synchronises the stream.
  */
 ibp_status ibp_case_set_timing(ibp_case *c, int32_t enable);
 ibp_status ibp_case_last_timing(ibp_case *c, float *ms, int32_t n);

@@ -20,6 +20,7 @@ Every function names the passage of the paper it follows:
 * ``ctg_terms``           eqs. (slack-Sc), (slack-sagg)
 * ``bound``               eq. (penalized-objective) / appendix eq. (ibp_f) under eq. (IBP)
 * ``grad_hi``             hand-derived adjoint of the upper bound (the paper has none)
+* ``grad_hi_ratings``     its rating part, split into base and contingency ratings
 * ``paper_mode_flows``    IBP applied literally to eq. (ctg flow matrix form)
 * ``screen_lines``        lines whose paper-mode contingency interval can exceed the rating
 * ``paper_ctg_terms``     eq. (slack-Sc) sums over the paper-mode intervals (``bound(mode="paper")``)
@@ -409,7 +410,7 @@ def bound(case, sens: Optional[Sensitivities] = None, lo=None, hi=None, nthreads
         out_lo[j] = C_lo - G_hi - case.zeta_inj * inj_hi[j] - case.zeta_f * (fb_hi[j] + fc_hi[j])
     return Bound(lo=out_lo, hi=out_hi,
                  terms=dict(costs=np.array(costs), inj=(inj_lo, inj_hi), fb=(fb_lo, fb_hi),
-                            fc=(fc_lo, fc_hi)))
+                            fc=(fc_lo, fc_hi), zeta=(case.zeta_inj, case.zeta_f)))
 
 
 # ----------------------------------------------------------------------------
@@ -478,13 +479,11 @@ def grad_hi(case, sens: Sensitivities, lo=None, hi=None, nthreads=None):
     # d hi / d c, d hi / d r
     dc = -case.zeta_f * (gc_c + gc_b) - case.zeta_inj * gc_i
     dr = -case.zeta_f * (gr_c + gr_b) - case.zeta_inj * gr_i
-    # rating gradient: -z_f * d(sum s_lo)/d rating = +z_f * #active
-    rating_c = case.rating if case.rating_ctg is None else case.rating_ctg
-    cent, rad = all_ctg_flows(case, sens, c, r, nthreads) if case.n_ctg * case.n_line <= 4_000_000 else (None, None)
+    # rating gradient for base and contingency ratings moving together
     g_rating = None
-    if cent is not None:
-        act_c = (np.abs(cent) - rad - rating_c[None, None, :]) > 0
-        g_rating = case.zeta_f * (act_c.sum(axis=1) + act_b)
+    if case.n_ctg * case.n_line <= 4_000_000:
+        g_base, g_ctg = grad_hi_ratings(case, sens, lo, hi, nthreads)
+        g_rating = g_base + g_ctg
     # chain to device endpoints
     ng = case.n_gen
     bus = np.concatenate([case.gen_bus, case.load_bus])
@@ -497,6 +496,30 @@ def grad_hi(case, sens: Sensitivities, lo=None, hi=None, nthreads=None):
         for d, (a, b) in enumerate(_segments(case.load_nseg, case.load_slope, case.load_bkpt)):
             g_hi[j, ng + d] += _pwl_slope(a, b, hi[j, ng + d])
     return g_lo, g_hi, g_rating
+
+
+def grad_hi_ratings(case, sens: Sensitivities, lo=None, hi=None, nthreads=None):
+    """d hi / d rating (base ratings, eq. (slack-sfb)) and d hi / d rating_ctg
+    (contingency ratings, eq. (slack-Sc)), per box and line.
+
+    hi takes -z_f s_lo with s_lo = max(|c| - r - rating, 0) for every base line
+    and every (k, l) pair, so each pair whose lower violation bound is positive
+    adds +z_f to the derivative in its own rating: the base part counts the
+    active base lines, the contingency part the active pairs of each line.
+    When the case has no separate contingency ratings both parts belong to the
+    one rating vector, whose derivative is their sum.  Every contingency flow
+    is formed, so this is for small cases.
+    """
+    lo = case.box_lo if lo is None else np.atleast_2d(lo)
+    hi = case.box_hi if hi is None else np.atleast_2d(hi)
+    c, r = bus_box(case, lo, hi)
+    fc = c @ sens.phi.T
+    fr = r @ np.abs(sens.phi).T
+    act_b = (np.abs(fc) - fr - case.rating[None, :]) > 0
+    rating_c = case.rating if case.rating_ctg is None else case.rating_ctg
+    cent, rad = all_ctg_flows(case, sens, c, r, nthreads)
+    act_c = (np.abs(cent) - rad - rating_c[None, None, :]) > 0
+    return case.zeta_f * act_b.astype(float), case.zeta_f * act_c.sum(axis=1).astype(float)
 
 
 def paper_mode_flows(case, sens: Sensitivities, c, r):

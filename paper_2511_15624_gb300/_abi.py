@@ -27,7 +27,7 @@ EXPORTED = (
     "ibp_case_sync", "ibp_case_info", "ibp_case_set_variant", "ibp_kernel_variants",
     "ibp_case_set_timing", "ibp_case_last_timing", "ibp_selftest_wait_timeout", "ibp_last_error",
     "ibp_status_string", "ibp_bound_noalloc", "ibp_case_set_screen", "ibp_case_last_live",
-    "ibp_case_set_reduction", "ibp_case_reduction", "ibp_bound_paper", "ibp_set_alloc_limit",
+    "ibp_case_set_reduction", "ibp_case_set_refine", "ibp_case_reduction", "ibp_bound_paper", "ibp_set_alloc_limit",
 )
 
 
@@ -93,6 +93,8 @@ def lib():
         L.ibp_case_last_live.argtypes = [P, P, P]
         L.ibp_case_set_reduction.argtypes = [P, I32]
         L.ibp_case_set_reduction.restype = ctypes.c_int
+        L.ibp_case_set_refine.argtypes = [P, I32]
+        L.ibp_case_set_refine.restype = ctypes.c_int
         L.ibp_case_reduction.argtypes = [P, P, P]
         L.ibp_case_reduction.restype = ctypes.c_int
         L.ibp_case_last_live.restype = ctypes.c_int
@@ -235,10 +237,10 @@ def ibp_case_set_timing(handle, enable: bool):
 
 
 def ibp_case_last_timing(handle):
-    ms = (ctypes.c_float * 5)()
-    _check(lib().ibp_case_last_timing(ctypes.c_void_p(handle), ms, 5))
+    ms = (ctypes.c_float * 6)()
+    _check(lib().ibp_case_last_timing(ctypes.c_void_p(handle), ms, 6))
     return {"box_to_bus": ms[0], "base_flow": ms[1], "screen": ms[2], "contingency": ms[3],
-            "assemble": ms[4]}
+            "refine": ms[4], "assemble": ms[5]}
 
 
 def ibp_case_set_screen(handle, enable: bool):
@@ -247,6 +249,10 @@ def ibp_case_set_screen(handle, enable: bool):
 
 def ibp_case_set_reduction(handle, enable: bool):
     _check(lib().ibp_case_set_reduction(ctypes.c_void_p(handle), int(bool(enable))))
+
+
+def ibp_case_set_refine(handle, enable: bool):
+    _check(lib().ibp_case_set_refine(ctypes.c_void_p(handle), int(bool(enable))))
 
 
 def ibp_case_reduction(handle, n_active: int, n_line: int):

@@ -157,6 +157,10 @@ class Case:
         """Exact network reduction of the contingency pass (default on)."""
         _abi.ibp_case_set_reduction(self._h, enable)
 
+    def set_refine(self, enable: bool):
+        """FP64 refinement of the terms that can reach obj_hi (default on)."""
+        _abi.ibp_case_set_refine(self._h, enable)
+
     def reduction(self):
         """(class of each active bus column or -1 for the slack's class,
         bridge flag of each line)."""

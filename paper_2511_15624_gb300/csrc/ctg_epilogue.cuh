@@ -5,6 +5,7 @@
 
 #include "common.cuh"
 #include "internal.h"
+#include "refine.cuh"
 
 namespace ibp {
 
@@ -23,11 +24,17 @@ __device__ __forceinline__ void pair_centre(float Lt, float cl, float ck, float 
 }
 
 // Epilogue for one (k, l) pair: flow interval, violation interval, error term.
-__device__ __forceinline__ void pair_epilogue(const CtgArgs &a, int box, int l, int k, float Lt,
+// Returns true when the pair's lower violation bound can be positive and the
+// FP64 refinement is on (a.ref.phi64): its obj_hi terms (s_lo and the
+// allowance) then go to cslo_acc / cwhi_acc, which the caller adds only when
+// the pair is not queued for the refinement; its obj_lo terms are added here.
+__device__ __forceinline__ bool pair_epilogue(const CtgArgs &a, int box, int l, int k, float Lt,
                                               float A, float &slo_acc, float &shi_acc,
-                                              float &whi_acc, float &wlo_acc) {
+                                              float &whi_acc, float &wlo_acc, float &cslo_acc,
+                                              float &cwhi_acc) {
     const int kl = __ldg(&a.ctg_line[k]);
-    if (!IBP_IDX_OK(kl >= 0 && kl < a.n_l && l >= 0 && l < a.n_l && box < a.n_box, a.err)) return;
+    if (!IBP_IDX_OK(kl >= 0 && kl < a.n_l && l >= 0 && l < a.n_l && box < a.n_box, a.err)) return false;
+    bool refine = false;
     const size_t ob = (size_t)box * a.n_l;
     const float cl = __ldg(&a.line_c[ob + l]), ck = __ldg(&a.line_c[ob + kl]);
     const float el = __ldg(&a.line_e[ob + l]), ek = __ldg(&a.line_e[ob + kl]);
@@ -66,7 +73,10 @@ __device__ __forceinline__ void pair_epilogue(const CtgArgs &a, int box, int l, 
             w = __fmaf_ru(kU, rup, w);
             w = __fmaf_ru(2.0f, eta, w);
             wlo = w;
-            if (__fadd_ru(__fsub_ru(alo, rdn), w) > 0.0f) whi = w;
+            if (__fadd_ru(__fsub_ru(alo, rdn), w) > 0.0f) {
+                whi = w;
+                refine = a.ref.phi64 != nullptr;
+            }
         }
         if (a.act_list && slo > 0.0f) {
             // certified active: record for the adjoint
@@ -83,10 +93,16 @@ __device__ __forceinline__ void pair_epilogue(const CtgArgs &a, int box, int l, 
         a.flow_lo[o] = flo;
         a.flow_hi[o] = fhi;
     }
-    slo_acc = __fadd_rd(slo_acc, slo);
+    if (refine) {
+        cslo_acc = __fadd_rd(cslo_acc, slo);
+        cwhi_acc = __fadd_ru(cwhi_acc, whi);
+    } else {
+        slo_acc = __fadd_rd(slo_acc, slo);
+        whi_acc = __fadd_ru(whi_acc, whi);
+    }
     shi_acc = __fadd_ru(shi_acc, shi);
-    whi_acc = __fadd_ru(whi_acc, whi);
     wlo_acc = __fadd_ru(wlo_acc, wlo);
+    return refine;
 }
 
 // Per-warp FP64 partial sums (deterministic tree, directed rounding):

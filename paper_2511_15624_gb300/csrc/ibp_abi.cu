@@ -96,6 +96,7 @@ struct ibp_case {
     int variant = 0;
     bool screen = true;      // paper-mode line screen ahead of the contingency kernel
     bool reduce = true;      // exact network reduction (bridges, bus classes)
+    bool refine = true;      // FP64 refinement of the terms that can reach obj_hi
     bool has_reduction = false;
     int n_r = 0, n_r_pad = 0, n_bridges = 0;  // bus classes, bridge lines
     std::vector<int> cls_ptr_h, cls_col_h, is_bridge_h;
@@ -104,6 +105,9 @@ struct ibp_case {
 
     // persistent device data
     DevBuf<float> phi_a, lodf, rate_up, rate_dn, rate_c_up, rate_c_dn;
+    DevBuf<double> phi64;             // the FP64 PTDF of the active columns
+    DevBuf<float> lodf_lo;             // RN32(L - L~) of the contingency list
+    DevBuf<double> rate64, rate_c64;   // ratings as given (FP64)
     DevBuf<int> ctg_line, act_ptr, act_dev, seg_ptr, dev_col;
     DevBuf<double> slope, bkpt;
     DevBuf<float> hat_l, hat_k;  // one-box scaled rows (lazily allocated)
@@ -125,6 +129,13 @@ struct ibp_case {
     DevBuf<double> cbus;
     DevBuf<float2> cbus2;
     DevBuf<float> rbus, cabs, box_consts, line_c, line_e, line_R, rbus_t, bus_part;
+    DevBuf<double> rbus64;
+    DevBuf<double> lc64, lR64;  // paper-mode refinement: per-line FP64 centre and radius
+    DevBuf<float> lX;
+    // refinement queues of the contingency launch (regions per CTA and warp)
+    DevBuf<int4> refq;
+    DevBuf<int> refq_cnt;
+    DevBuf<double2> refq_res;
     DevBuf<double> part_base, part_ctg, part_stage;
     DevBuf<float> flows;
     DevBuf<int> err;
@@ -139,15 +150,27 @@ struct ibp_case {
 
     // timing
     bool timing = false;
-    static constexpr int kEvents = 6;
-    cudaEvent_t ev[kEvents] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    static constexpr int kEvents = 7;
+    cudaEvent_t ev[kEvents] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    // completion of the case's last enqueued call (recorded on that call's
+    // stream), and a private non-blocking stream for reading the error word:
+    // ibp_case_sync waits for this case's work only, not the whole device.
+    // A call enqueued while its stream was being captured cannot be waited
+    // for through the event; the next sync then waits for the device.
+    cudaEvent_t done = nullptr;
+    cudaStream_t side = nullptr;
+    bool captured = false;
 
     ~ibp_case() {
         if (device >= 0) {
             DeviceGuard g(device);
             for (auto &e : ev)
                 if (e) cudaEventDestroy(e);
+            if (done) cudaEventDestroy(done);
+            if (side) cudaStreamDestroy(side);
             phi_a.free(); lodf.free(); rate_up.free(); rate_dn.free(); rate_c_up.free();
+            phi64.free(); lodf_lo.free(); rate64.free(); rate_c64.free(); rbus64.free();
+            lc64.free(); lR64.free(); lX.free(); refq.free(); refq_cnt.free(); refq_res.free();
             rate_c_dn.free(); ctg_line.free(); act_ptr.free(); act_dev.free(); seg_ptr.free();
             slope.free(); bkpt.free(); hat_l.free(); hat_k.free(); phi_k.free(); rbus_t.free();
             box_lo.free(); box_hi.free();
@@ -452,7 +475,8 @@ static ibp_status build_sensitivities(ibp_case *c, const std::vector<int> &from,
     if (!act_red.empty())
         CUDA_TRY(cudaMemcpy(dact.p, act_red.data(), act_red.size() * sizeof(int), cudaMemcpyHostToDevice));
     CUDA_TRY(c->phi_a.alloc((size_t)n_l * c->n_a_pad));
-    CUDA_TRY(launch_extract_phi(dZ.p, nb_r, n_l, dact.p, c->n_a, c->n_a_pad, c->phi_a.p, s));
+    CUDA_TRY(c->phi64.alloc((size_t)n_l * c->n_a_pad));
+    CUDA_TRY(launch_extract_phi(dZ.p, nb_r, n_l, dact.p, c->n_a, c->n_a_pad, c->phi_a.p, c->phi64.p, s));
     CUDA_TRY(c->phi_k.alloc((size_t)std::max(n_c, 1) * c->n_a_pad));
     CUDA_TRY(launch_gather_rows(c->phi_a.p, c->n_a_pad, c->ctg_line.p, n_c, c->phi_k.p, s));
 
@@ -474,8 +498,9 @@ static ibp_status build_sensitivities(ibp_case *c, const std::vector<int> &from,
         CUDA_TRY(cudaMemcpy(dcf.p, cf.data(), n_c * sizeof(int), cudaMemcpyHostToDevice));
         CUDA_TRY(cudaMemcpy(dct.p, ct.data(), n_c * sizeof(int), cudaMemcpyHostToDevice));
         CUDA_TRY(cudaMemset(dmax.p, 0, sizeof(float)));
-        CUDA_TRY(launch_lodf(dZ.p, nb_r, n_l, n_c, dcf.p, dct.p, c->ctg_line.p, c->lodf.p, dden.p,
-                             dmax.p, s));
+        CUDA_TRY(c->lodf_lo.alloc((size_t)n_c * n_l));
+        CUDA_TRY(launch_lodf(dZ.p, nb_r, n_l, n_c, dcf.p, dct.p, c->ctg_line.p, c->lodf.p, c->lodf_lo.p,
+                             dden.p, dmax.p, s));
         std::vector<double> den(n_c);
         float mx = 0;
         CUDA_TRY(cudaMemcpy(den.data(), dden.p, n_c * sizeof(double), cudaMemcpyDeviceToHost));
@@ -618,6 +643,14 @@ extern "C" ibp_status ibp_case_create(int32_t n_bus, int32_t slack_bus, int32_t 
         rcu[l] = up32(rc);
         rcd[l] = dn32(rc);
     }
+    {
+        std::vector<double> r64(rating, rating + n_line), rc64(n_line);
+        for (int l = 0; l < n_line; ++l) rc64[l] = rating_ctg ? rating_ctg[l] : rating[l];
+        CUDA_TRY(c->rate64.alloc(n_line));
+        CUDA_TRY(c->rate_c64.alloc(n_line));
+        CUDA_TRY(cudaMemcpy(c->rate64.p, r64.data(), n_line * sizeof(double), cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(c->rate_c64.p, rc64.data(), n_line * sizeof(double), cudaMemcpyHostToDevice));
+    }
     CUDA_TRY(c->rate_up.alloc(n_line));
     CUDA_TRY(c->rate_dn.alloc(n_line));
     CUDA_TRY(c->rate_c_up.alloc(n_line));
@@ -689,6 +722,8 @@ extern "C" ibp_status ibp_case_create(int32_t n_bus, int32_t slack_bus, int32_t 
     c->build_seconds =
         std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     for (auto &e : c->ev) CUDA_TRY(cudaEventCreate(&e));
+    CUDA_TRY(cudaEventCreateWithFlags(&c->done, cudaEventDisableTiming));
+    CUDA_TRY(cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking));
     c->n_part_base = base_partials_count(c->num_sms);
     *out = c.release();
     return ok();
@@ -711,6 +746,9 @@ bool case_view(const ibp_case *c, CaseView *v) {
     v->rate_c_up = c->rate_c_up.p; v->rate_c_dn = c->rate_c_dn.p; v->ctg_line = c->ctg_line.p;
     v->act_ptr = c->act_ptr.p; v->act_dev = c->act_dev.p; v->seg_ptr = c->seg_ptr.p;
     v->slope = c->slope.p; v->bkpt = c->bkpt.p; v->n_part_base = c->n_part_base;
+    v->phi64 = c->refine ? c->phi64.p : nullptr;
+    v->lodf_lo = c->lodf_lo.p;
+    v->rate64 = c->rate64.p; v->rate_c64 = c->rate_c64.p;
     return true;
 }
 
@@ -766,6 +804,7 @@ static ibp_status ensure_workspace(ibp_case *c, int n_box) {
     CUDA_TRY(c->cbus.alloc(cap * na));
     CUDA_TRY(c->cbus2.alloc(cap * na));
     CUDA_TRY(c->rbus.alloc(cap * na));
+    CUDA_TRY(c->rbus64.alloc(cap * na));
     CUDA_TRY(c->cabs.alloc(cap * na));
     CUDA_TRY(c->box_consts.alloc((size_t)cap * 4));
     CUDA_TRY(c->bus_part.alloc((size_t)cap * bus_blocks(c->n_a_pad) * 4));
@@ -795,6 +834,56 @@ static ibp_status ensure_class_ws(ibp_case *c) {
     CUDA_TRY(c->rcls.alloc((size_t)c->cap_box * c->n_r_pad));
     CUDA_TRY(c->rcls_t.alloc(cap_pad * c->n_r_pad));
     ++c->ws_gen;
+    return IBP_OK;
+}
+
+// Arguments of the FP64 refinement of the terms that can reach obj_hi (all
+// null when the case does not refine).
+static RefArgs ref_args(const ibp_case *c) {
+    RefArgs r{};
+    if (!c->refine || !c->phi64.p) return r;
+    r.phi_hi = c->phi_a.p; r.phi64 = c->phi64.p; r.cbus = c->cbus.p; r.rbus64 = c->rbus64.p;
+    r.rbus = c->rbus.p; r.cabs = c->cabs.p; r.box_consts = c->box_consts.p;
+    r.rate64 = c->rate64.p; r.rate_c64 = c->rate_c64.p; r.n_a_pad = c->n_a_pad;
+    r.lodf = c->lodf.p; r.lodf_lo = c->lodf_lo.p; r.n_l = c->n_line;
+    return r;
+}
+
+// The global refinement queues of a contingency launch: kRefQCap entries per
+// (CTA, warp) region, for up to kRefRegionsPerSm regions per SM.
+static int ref_regions(int num_sms) { return num_sms * kRefRegionsPerSm; }
+
+template <class Q>
+static ibp_status ensure_ref_queue(Q *q, int num_sms) {
+    const size_t n = (size_t)ref_regions(num_sms);
+    if (q->refq.n >= n * kRefQCap && q->refq_cnt.n >= n && q->refq_res.n >= n * kRefQCap) return IBP_OK;
+    CUDA_TRY(q->refq.alloc(n * kRefQCap));
+    CUDA_TRY(q->refq_cnt.alloc(n));
+    CUDA_TRY(q->refq_res.alloc(n * kRefQCap));
+    return IBP_OK;
+}
+
+// Record the completion of the work just enqueued on s for ibp_case_sync.
+static ibp_status mark_done(ibp_case *c, cudaStream_t s) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CUDA_TRY(cudaStreamIsCapturing(s, &cs));
+    if (cs != cudaStreamCaptureStatusNone) {
+        c->captured = true;
+        return IBP_OK;
+    }
+    CUDA_TRY(cudaEventRecord(c->done, s));
+    return IBP_OK;
+}
+
+// Wait for the case's last call: its completion event, or the device when a
+// call was captured into a graph since the last wait.
+static ibp_status wait_case(ibp_case *c) {
+    if (c->captured) {
+        CUDA_TRY(cudaDeviceSynchronize());
+        c->captured = false;
+    } else {
+        CUDA_TRY(cudaEventSynchronize(c->done));
+    }
     return IBP_OK;
 }
 
@@ -832,6 +921,7 @@ static ibp_status enqueue_bound(ibp_case *c, int n_box, const double *lo, const 
     ba.n_a = c->n_a; ba.n_a_pad = c->n_a_pad; ba.n_dev = c->n_dev; ba.n_gen = c->n_gen; ba.n_box = n_box;
     ba.act_ptr = c->act_ptr.p; ba.act_dev = c->act_dev.p; ba.box_lo = lo; ba.box_hi = hi;
     ba.cbus = c->cbus.p; ba.cbus2 = c->cbus2.p; ba.rbus = c->rbus.p; ba.rbus_t = multi ? c->rbus_t.p : nullptr;
+    ba.rbus64 = c->rbus64.p;
     ba.n_box_pad = n_box_pad;
     ba.cabs = c->cabs.p; ba.box_consts = c->box_consts.p; ba.err = c->err.p;
     ba.bus_part = c->bus_part.p;
@@ -866,6 +956,7 @@ static ibp_status enqueue_bound(ibp_case *c, int n_box, const double *lo, const 
         bb.act_list = c->act_list.p;
         bb.act_cap = c->act_cap;
     }
+    bb.ref = ref_args(c);
     CUDA_TRY(launch_base(bb, c->n_part_base, s));
     if (c->timing) CUDA_TRY(cudaEventRecord(c->ev[2], s));
 
@@ -912,6 +1003,13 @@ static ibp_status enqueue_bound(ibp_case *c, int n_box, const double *lo, const 
     ca.flow_lo = flo; ca.flow_hi = fhi; ca.partials = c->part_ctg.p; ca.err = c->err.p;
     ca.wait_ns = 2000000000ull;
     ca.warps_per_tile = ctg_warps(*v);
+    ca.ref = ref_args(c);
+    const bool queue = !paper && ca.ref.phi64 && ca.n_tiles > 0;
+    if (queue) {
+        if ((st = ensure_ref_queue(c, c->num_sms)) != IBP_OK) return st;
+        ca.refq = c->refq.p; ca.refq_cnt = c->refq_cnt.p; ca.refq_cap = kRefQCap;
+        CUDA_TRY(cudaMemsetAsync(c->refq_cnt.p, 0, (size_t)ref_regions(c->num_sms) * sizeof(int), s));
+    }
     ca.part_rows_cap = (int)max_part_rows(c);
     if (record) {
         ca.act_count = c->act_count.p;
@@ -929,6 +1027,21 @@ static ibp_status enqueue_bound(ibp_case *c, int n_box, const double *lo, const 
         pa.line_c = c->line_c.p; pa.line_e = c->line_e.p; pa.line_R = c->line_R.p;
         pa.box_consts = c->box_consts.p; pa.rate_up = c->rate_c_up.p; pa.rate_dn = c->rate_c_dn.p;
         pa.gamma_base = bb.gamma_base; pa.partials = c->part_ctg.p; pa.err = c->err.p;
+        pa.ref = ref_args(c);
+        if (pa.ref.phi64) {
+            // FP64 base-flow values of every line for the refinement
+            const size_t nl = (size_t)c->cap_box * c->n_line;
+            if (c->lc64.n < nl || c->lR64.n < nl || c->lX.n < nl) {
+                CUDA_TRY(c->lc64.alloc(nl));
+                CUDA_TRY(c->lR64.alloc(nl));
+                CUDA_TRY(c->lX.alloc(nl));
+            }
+            LineExactArgs la{};
+            la.ref = pa.ref; la.n_l = c->n_line; la.n_box = n_box;
+            la.c64 = c->lc64.p; la.R64 = c->lR64.p; la.X = c->lX.p;
+            CUDA_TRY(launch_line_exact(la, c->num_sms, s));
+            pa.lc64 = c->lc64.p; pa.lR64 = c->lR64.p; pa.lX = c->lX.p;
+        }
         CUDA_TRY(launch_paper(pa, s));
     } else if (ca.n_tiles > 0) {
         CUtensorMap mL, mK, mR;
@@ -949,8 +1062,17 @@ static ibp_status enqueue_bound(ibp_case *c, int n_box, const double *lo, const 
                 return fail(IBP_ECUDA, "%s", err.c_str());
             CUDA_TRY(launch_ctg(*v, mL, mK, ca, c->num_sms, s));
         }
+        if (c->timing) CUDA_TRY(cudaEventRecord(c->ev[4], s));
+        if (queue) {
+            RefQueueArgs qa{};
+            qa.args = nullptr; qa.one = ca; qa.n_regions = ref_regions(c->num_sms); qa.cap = kRefQCap;
+            qa.e = c->refq.p; qa.cnt = c->refq_cnt.p; qa.res = c->refq_res.p;
+            CUDA_TRY(launch_refine_queue(qa, c->num_sms, s));
+        }
+    } else if (c->timing) {
+        CUDA_TRY(cudaEventRecord(c->ev[4], s));
     }
-    if (c->timing) CUDA_TRY(cudaEventRecord(c->ev[4], s));
+    if (c->timing) CUDA_TRY(cudaEventRecord(c->ev[5], s));
 
     AsmArgs aa{};
     aa.n_box = n_box; aa.n_dev = c->n_dev; aa.n_gen = c->n_gen;
@@ -968,13 +1090,16 @@ static ibp_status enqueue_bound(ibp_case *c, int n_box, const double *lo, const 
         aa.live_rows_per_tile = ca.warps_per_tile;
     }
     CUDA_TRY(launch_assemble(aa, s));
-    if (c->timing) CUDA_TRY(cudaEventRecord(c->ev[5], s));
-    return IBP_OK;
+    if (c->timing) CUDA_TRY(cudaEventRecord(c->ev[6], s));
+    return mark_done(c, s);
 }
 
+// Reads the error word through the case's private stream (no wait on other
+// streams); the caller has waited for the work that writes it.
 static ibp_status read_err_word(ibp_case *c) {
     int e = 0;
-    CUDA_TRY(cudaMemcpy(&e, c->err.p, sizeof(int), cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemcpyAsync(&e, c->err.p, sizeof(int), cudaMemcpyDeviceToHost, c->side));
+    CUDA_TRY(cudaStreamSynchronize(c->side));
     if (e & kErrTimeout) return fail(IBP_ETIMEOUT, "a bounded device wait ran out");
     if (e & kErrBadBox) return fail(IBP_EINVAL, "a box has lo > hi or a non-finite entry");
     if (e & kErrOverflow)
@@ -1108,7 +1233,7 @@ static ibp_status enqueue_backward(ibp_case *c, int n_box, const double *lo, con
     b.slope = c->slope.p; b.bkpt = c->bkpt.p; b.zeta_inj = c->zeta_inj; b.zeta_f = c->zeta_f;
     b.grad_obj_hi = gobj; b.grad_lo = glo; b.grad_hi = ghi; b.grad_rating = grat;
     CUDA_TRY(launch_backward(b, s));
-    return IBP_OK;
+    return mark_done(c, s);
 }
 
 extern "C" ibp_status ibp_bound_backward(ibp_case *c, int32_t n_box, const double *box_lo,
@@ -1170,10 +1295,16 @@ struct MultiPlan {
     DevBuf<uint32_t> prefix;
     DevBuf<CtgArgs> args;
     DevBuf<CUtensorMap> maps;
+    // refinement queues of the launch (shared by the cases), when a case refines
+    bool refine = false;
+    DevBuf<int4> refq;
+    DevBuf<int> refq_cnt;
+    DevBuf<double2> refq_res;
     ~MultiPlan() {
         if (device >= 0) {
             DeviceGuard g(device);
             items.free(); cta_start.free(); err.free(); prefix.free(); args.free(); maps.free();
+            refq.free(); refq_cnt.free(); refq_res.free();
         }
     }
 };
@@ -1208,6 +1339,7 @@ static CtgArgs multi_args(const ibp_case *c, int n_box, int BL, int BK, int CH, 
     ca.wait_ns = 2000000000ull;
     ca.warps_per_tile = rows_per_item;
     ca.part_rows_cap = (int)max_part_rows(c);
+    ca.ref = ref_args(c);
     if (reduced) {
         ca.live = c->nb_list.p;
         ca.n_live = c->nb_count.p;
@@ -1302,6 +1434,15 @@ static ibp_status build_plan(ibp_case *const *cases, const int32_t *n_box, int n
     }
     start[G] = (int)items.size();
     P->grid = all.empty() ? 0 : G;
+    // one set of refinement queues for the launch, when any case refines
+    for (int i = 0; i < n_case; ++i) P->refine = P->refine || args[i].ref.phi64 != nullptr;
+    if (P->refine) {
+        ibp_status st = ensure_ref_queue(P.get(), num_sms);
+        if (st != IBP_OK) return st;
+        for (int i = 0; i < n_case; ++i) {
+            args[i].refq = P->refq.p; args[i].refq_cnt = P->refq_cnt.p; args[i].refq_cap = kRefQCap;
+        }
+    }
     CUDA_TRY(P->items.alloc(std::max<size_t>(items.size(), 1)));
     CUDA_TRY(P->cta_start.alloc(start.size()));
     CUDA_TRY(P->prefix.alloc(prefix.size() + 1));
@@ -1383,6 +1524,7 @@ extern "C" ibp_status ibp_bound_multi(int32_t n_case, ibp_case *const *cases, co
         ba.n_a = c->n_a; ba.n_a_pad = c->n_a_pad; ba.n_dev = c->n_dev; ba.n_gen = c->n_gen; ba.n_box = nb;
         ba.act_ptr = c->act_ptr.p; ba.act_dev = c->act_dev.p; ba.box_lo = box_lo[i]; ba.box_hi = box_hi[i];
         ba.cbus = c->cbus.p; ba.cbus2 = c->cbus2.p; ba.rbus = c->rbus.p; ba.rbus_t = c->rbus_t.p;
+        ba.rbus64 = c->rbus64.p;
         ba.n_box_pad = n_box_pad;
         ba.cabs = c->cabs.p; ba.box_consts = c->box_consts.p; ba.err = c->err.p;
         ba.bus_part = c->bus_part.p;
@@ -1407,11 +1549,21 @@ extern "C" ibp_status ibp_bound_multi(int32_t n_case, ibp_case *const *cases, co
             bb.rate_c_up = c->rate_c_up.p;
             bb.rate_c_dn = c->rate_c_dn.p;
         }
+        bb.ref = ref_args(c);
         CUDA_TRY(launch_base(bb, c->n_part_base, s));
     }
     // one persistent launch over the contingency tiles of every case
+    const int num_sms = cases[0]->num_sms;
+    if (P->refine)
+        CUDA_TRY(cudaMemsetAsync(P->refq_cnt.p, 0, (size_t)ref_regions(num_sms) * sizeof(int), s));
     CUDA_TRY(launch_ctg_cases(P->variant, P->items.p, P->cta_start.p, P->prefix.p, P->args.p,
                               P->maps.p, P->grid, 2000000000ull, P->err.p, s));
+    if (P->refine) {
+        RefQueueArgs qa{};
+        qa.args = P->args.p; qa.n_regions = ref_regions(num_sms); qa.cap = kRefQCap;
+        qa.e = P->refq.p; qa.cnt = P->refq_cnt.p; qa.res = P->refq_res.p;
+        CUDA_TRY(launch_refine_queue(qa, num_sms, s));
+    }
     int BL, BK, CH;
     multi_tile_shape(&BL, &BK, &CH);
     for (int i = 0; i < n_case; ++i) {
@@ -1428,6 +1580,7 @@ extern "C" ibp_status ibp_bound_multi(int32_t n_case, ibp_case *const *cases, co
         aa.zeta_inj = c->zeta_inj; aa.zeta_f = c->zeta_f;
         aa.obj_lo = obj_lo[i]; aa.obj_hi = obj_hi[i]; aa.obj_err = obj_err[i]; aa.err = c->err.p;
         CUDA_TRY(launch_assemble(aa, s));
+        if ((st = mark_done(c, s)) != IBP_OK) return st;
     }
     return ok();
 }
@@ -1436,8 +1589,9 @@ extern "C" ibp_status ibp_case_sync(ibp_case *c) {
     if (!c) return fail(IBP_EINVAL, "case is NULL");
     if (c->device < 0) return fail(IBP_ENOTSUP, "case was created without a device (dry run)");
     DeviceGuard guard(c->device);
-    CUDA_TRY(cudaDeviceSynchronize());
-    ibp_status st = read_err_word(c);
+    ibp_status st = wait_case(c);
+    if (st != IBP_OK) return st;
+    st = read_err_word(c);
     if (st != IBP_OK) return st;
     return ok();
 }
@@ -1448,6 +1602,7 @@ extern "C" ibp_status ibp_case_info(const ibp_case *c, ibp_case_info_t *o) {
     o->n_load = c->n_load; o->n_active = c->n_a; o->n_active_pad = c->n_a_pad; o->device = c->device;
     int64_t bytes = 0;
     bytes += (int64_t)c->phi_a.n * 4 + (int64_t)c->lodf.n * 4 + (int64_t)c->hat_l.n * 4 + (int64_t)c->hat_k.n * 4;
+    bytes += (int64_t)c->phi64.n * 8 + (int64_t)c->lodf_lo.n * 4;
     bytes += (int64_t)(c->cbus.n + c->part_base.n + c->part_ctg.n + c->box_lo.n + c->box_hi.n) * 8;
     bytes += (int64_t)(c->rbus.n + c->cabs.n + c->line_c.n + c->line_e.n + c->line_R.n + c->flows.n) * 4;
     o->device_bytes = bytes;
@@ -1489,6 +1644,13 @@ extern "C" ibp_status ibp_case_set_screen(ibp_case *c, int32_t enable) {
     return ok();
 }
 
+extern "C" ibp_status ibp_case_set_refine(ibp_case *c, int32_t enable) {
+    if (!c) return fail(IBP_EINVAL, "case is NULL");
+    c->refine = enable != 0;
+    ++c->ws_gen;  // cached many-case plans carry the refinement arguments
+    return ok();
+}
+
 extern "C" ibp_status ibp_case_set_reduction(ibp_case *c, int32_t enable) {
     if (!c) return fail(IBP_EINVAL, "case is NULL");
     c->reduce = enable != 0;
@@ -1503,11 +1665,16 @@ extern "C" ibp_status ibp_case_last_live(ibp_case *c, int32_t *n_live, int32_t *
         return ok();
     }
     DeviceGuard guard(c->device);
-    CUDA_TRY(cudaDeviceSynchronize());
-    CUDA_TRY(cudaMemcpy(n_live, c->n_live.p, sizeof(int32_t), cudaMemcpyDeviceToHost));
+    ibp_status st = wait_case(c);
+    if (st != IBP_OK) return st;
+    CUDA_TRY(cudaMemcpyAsync(n_live, c->n_live.p, sizeof(int32_t), cudaMemcpyDeviceToHost, c->side));
+    CUDA_TRY(cudaStreamSynchronize(c->side));
     if (*n_live < 0 || *n_live > c->n_line) return fail(IBP_ECUDA, "corrupt live-line count");
-    if (lines && *n_live > 0)
-        CUDA_TRY(cudaMemcpy(lines, c->live.p, (size_t)*n_live * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    if (lines && *n_live > 0) {
+        CUDA_TRY(cudaMemcpyAsync(lines, c->live.p, (size_t)*n_live * sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                 c->side));
+        CUDA_TRY(cudaStreamSynchronize(c->side));
+    }
     return ok();
 }
 

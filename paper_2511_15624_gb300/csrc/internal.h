@@ -23,6 +23,22 @@ constexpr int kPartVals = 4;
 constexpr int kAsmVals = 18;
 
 // ---------------------------------------------------------------- kernel args
+// FP64 refinement of the pairs that can reach obj_hi (null phi64: off).
+struct RefArgs {
+    const float *phi_hi;     // [n_l][n_a_pad] Phi~ = RN32(Phi) (the FP32 PTDF)
+    const double *phi64;     // [n_l][n_a_pad] Phi, the FP64 PTDF of the active columns, or null
+    const double *cbus;      // [n_box][n_a_pad] bus centres (FP64)
+    const double *rbus64;    // [n_box][n_a_pad] bus radii (FP64, rounded up)
+    const float *rbus;       // [n_box][n_a_pad] bus radii (FP32, rounded up)
+    const float *cabs;       // [n_box][n_a_pad] |centre| (FP32, rounded up)
+    const float *box_consts; // [n_box][4]: ..., sum r, sum |c|
+    const double *rate64;    // [n_l] base ratings (FP64, as given)
+    const double *rate_c64;  // [n_l] contingency ratings (FP64, as given)
+    const float *lodf;       // [n_c][n_l] L~ = RN32(L)
+    const float *lodf_lo;    // [n_c][n_l] RN32(L - L~)
+    int n_a_pad, n_l;
+};
+
 struct BusArgs {
     int n_a, n_a_pad, n_dev, n_gen, n_box;
     const int *act_ptr;     // [n_a + 1] CSR over active bus columns
@@ -32,6 +48,7 @@ struct BusArgs {
     double *cbus;           // [n_box][n_a_pad] bus injection centre (FP64)
     float2 *cbus2;          // [n_box][n_a_pad] the same as hi + lo FP32 pair, or null
     float *rbus;            // [n_box][n_a_pad] radius, rounded up
+    double *rbus64;         // [n_box][n_a_pad] the FP64 radius, rounded up (or null)
     float *rbus_t;          // [n_a_pad][n_box_pad] transposed radius (or null)
     int n_box_pad;
     float *cabs;            // [n_box][n_a_pad] |centre| rounded up
@@ -75,6 +92,7 @@ struct BaseArgs {
     // interval, judged against the contingency ratings
     const int *is_bridge;    // [n_l]
     const float *rate_c_up, *rate_c_dn;
+    RefArgs ref;             // FP64 refinement of base lines and bridges that can reach obj_hi
 };
 
 struct CtgArgs {
@@ -103,7 +121,30 @@ struct CtgArgs {
     // list live[0 .. *n_live) of lines that can carry a violation
     const int *live;
     const int *n_live;
+    RefArgs ref;             // FP64 refinement of the pairs that can reach obj_hi
+    // global queues of the refinement, one region of refq_cap entries per
+    // (CTA, warp) of the launch; null: queue in shared memory and refine in
+    // the kernel
+    int4 *refq;
+    int *refq_cnt;
+    int refq_cap;
 };
+
+// The refinement of the queued pairs, after a contingency launch: every queue
+// entry (l, k, case << 16 | box, row) is refined by one warp anywhere on the
+// GPU (k_refine_queue), then each region's results are added to their
+// partial-sum rows in queue order (k_refine_apply).
+struct RefQueueArgs {
+    const CtgArgs *args;     // per case (device array), or null: `one`
+    CtgArgs one;
+    int n_regions, cap;
+    const int4 *e;           // [n_regions][cap]
+    const int *cnt;          // [n_regions]
+    double2 *res;            // [n_regions][cap]: refined s_lo, allowance
+};
+cudaError_t launch_refine_queue(const RefQueueArgs &a, int num_sms, cudaStream_t s);
+constexpr int kRefRegionsPerSm = 32;  // queue regions the workspace holds per SM
+constexpr int kRefQCap = 128;         // entries per region
 
 // Paper-mode line screen (Sec. II-C, the interval of eq. (ctg flow matrix
 // form) propagated in two parts): line l needs the tight radius only if, for
@@ -146,7 +187,24 @@ struct PaperArgs {
     float gamma_base;        // relative excess of the base radius sums R~
     double *partials;
     int *err;
+    // FP64 refinement of the pairs that can reach obj_hi (ref.phi64 null:
+    // off), from the per-line FP64 values of k_line_exact: centre c64, radius
+    // R64 and X = sum_b |Phi~_l,b| (r_b + |c_b|), each [n_box][n_l]
+    RefArgs ref;
+    const double *lc64, *lR64;
+    const float *lX;
 };
+
+// Per (box, line) FP64 values of the base flow from the FP64 PTDF (the paper
+// mode's refinement): c64 = sum_b Phi_l,b c_b, R64 = sum_b |Phi_l,b| r_b
+// (round-up), X = sum_b |Phi~_l,b| (r_b + |c_b|) (FP32 round-up).
+struct LineExactArgs {
+    RefArgs ref;
+    int n_l, n_box;
+    double *c64, *R64;       // [n_box][n_l]
+    float *X;                // [n_box][n_l]
+};
+cudaError_t launch_line_exact(const LineExactArgs &a, int num_sms, cudaStream_t s);
 
 // Radius of each bus class (the active buses whose PTDF columns coincide on
 // every non-bridge line): rcls[j] = RU(sum of rbus over the class members).
@@ -247,9 +305,9 @@ cudaError_t launch_or_err(int *dst, const int *src, cudaStream_t s);
 cudaError_t launch_scatter_dense(double *dst, int64_t ld, const int *rows, const int *cols,
                                  const double *vals, int nnz, cudaStream_t s);
 cudaError_t launch_extract_phi(const double *Z, int nb_r, int n_l, const int *act_red, int n_a,
-                               int n_a_pad, float *phi_a, cudaStream_t s);
+                               int n_a_pad, float *phi_a, double *phi64, cudaStream_t s);
 cudaError_t launch_lodf(const double *Z, int nb_r, int n_l, int n_c, const int *ctg_from_red,
-                        const int *ctg_to_red, const int *ctg_line, float *lodf,
+                        const int *ctg_to_red, const int *ctg_line, float *lodf, float *lodf_lo,
                         double *den_out, float *maxabs_out, cudaStream_t s);
 cudaError_t launch_gather_rows(const float *src, int ld, const int *rows, int n_rows,
                                float *dst, cudaStream_t s);
@@ -265,6 +323,9 @@ struct CaseView {
     const int *ctg_line, *act_ptr, *act_dev, *seg_ptr;
     const double *slope, *bkpt;
     int n_part_base;
+    const double *phi64;                // null when the case does not refine
+    const float *lodf_lo;
+    const double *rate64, *rate_c64;
 };
 bool case_view(const ibp_case *c, CaseView *v);
 ibp_status set_error(ibp_status s, const char *msg);

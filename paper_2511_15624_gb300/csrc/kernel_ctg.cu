@@ -67,7 +67,9 @@ struct Shape {
     static constexpr size_t kAcc3 = S3 ? (size_t)ML * MK * kThreads * sizeof(float) : 0;
     // full[ST] mbarriers, arrival counters[ST], last issued chunk[ST], abort flag
     static constexpr size_t kCtl = ST * sizeof(uint64_t) + 2 * ST * sizeof(int) + 16;
-    static constexpr size_t kBytes = kRing + kAcc3 + kCtl + 1024;
+    // per-warp queues of the pairs for the FP64 refinement (16-byte aligned)
+    static constexpr size_t kQueueOff = kRing + kAcc3 + (kCtl + 15) / 16 * 16;
+    static constexpr size_t kBytes = kQueueOff + ref_queue_bytes(kWarps) + 1024;
     static_assert(TL % 8 == 0 && TK % 8 == 0, "swizzle phase must be per-thread constant");
     static_assert(CH == 32 || CH == 64, "chunk of one or two 128-byte rows");
     static_assert(BL <= 256 && BK <= 256, "TMA box rows");
@@ -121,6 +123,13 @@ __global__ void __launch_bounds__(WL * WK * 32, MINB)
     volatile int *abort_flag = last_issued + ST;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // the warp's refinement queue (rebuilt where used: nothing of it stays live
+    // through the tile loop)
+    auto rq_of = [&]() {
+        return ref_queue_of(reinterpret_cast<unsigned char *>(ring) + S::kQueueOff, warp, a.refq,
+                            a.refq_cap, S::kWarps);
+    };
+    ref_queue_init(rq_of());
     // level-2 sums are folded into level 3 every kFold3 chunks (256 buses)
     constexpr int kFold3 = 256 / CH;
     const int tiles_k = (a.n_c + S::BK - 1) / S::BK;
@@ -284,7 +293,8 @@ __global__ void __launch_bounds__(WL * WK * 32, MINB)
             }
         }
         if (stop) break;
-        float slo = 0.0f, shi = 0.0f, whi = 0.0f, wlo = 0.0f;
+        float slo = 0.0f, shi = 0.0f, whi = 0.0f, wlo = 0.0f, cslo = 0.0f, cwhi = 0.0f;
+        uint64_t rmask = 0;
 #pragma unroll
         for (int i = 0; i < ML; ++i)
 #pragma unroll
@@ -295,11 +305,30 @@ __global__ void __launch_bounds__(WL * WK * 32, MINB)
                     float a3;
                     if constexpr (S3) a3 = acc3s[(i * MK + j) * S::kThreads];
                     else a3 = acc3[i][j];
-                    pair_epilogue(a, 0, l, k, Lr[i][j], __fadd_ru(a3, acc2[i][j]), slo, shi, whi, wlo);
+                    if (pair_epilogue(a, 0, l, k, Lr[i][j], __fadd_ru(a3, acc2[i][j]), slo, shi, whi, wlo,
+                                      cslo, cwhi))
+                        rmask |= 1ull << (i * MK + j);
                 }
             }
-        write_warp_partials(a, tile, warp, 0, slo, shi, whi, wlo, ML * MK);
+        // candidates of the FP64 refinement: queued, or (queue full) the FP32 terms
+        const bool queued =
+            a.ref.phi64 &&
+            ref_enqueue<ML * MK>(
+                rq_of(), rmask,
+                [&](int q, int &l, int &k) {
+                    const int lq = l0 + tl + TL * (q / MK);
+                    l = a.live ? __ldg(&a.live[lq]) : lq;
+                    k = k0 + tk + TK * (q % MK);
+                },
+                0, tile * a.warps_per_tile + warp);
+        if (!queued) {
+            slo = __fadd_rd(slo, cslo);
+            whi = __fadd_ru(whi, cwhi);
+        }
+        write_warp_partials(a, tile, warp, 0, slo, shi, whi, wlo, ML * MK + 1);
     }
+    // the queued refinements: published for k_refine_queue, or refined here
+    if (a.ref.phi64) ref_finish(rq_of(), a.refq_cnt, S::kWarps, [&](int) -> const CtgArgs & { return a; });
     // Every warp gets here (all waits are bounded).  After an abort, copies
     // may still be in flight: wait (bounded) for the last one of each stage.
     __syncthreads();
@@ -347,7 +376,9 @@ struct MultiShape {
     static constexpr size_t kCtl = ST * sizeof(uint64_t) + 2 * ST * sizeof(int) + 16;
     // per-warp copy of the current item's kernel arguments
     static constexpr size_t kArgs = (size_t)kWarps * ((sizeof(CtgArgs) + 15) / 16 * 16);
-    static constexpr size_t kBytes = kRing + kAcc3 + kArgs + kCtl + 1024;
+    // per-warp queues of the pairs for the FP64 refinement (16-byte aligned)
+    static constexpr size_t kQueueOff = kRing + kAcc3 + kArgs + (kCtl + 15) / 16 * 16;
+    static constexpr size_t kBytes = kQueueOff + ref_queue_bytes(kWarps) + 1024;
     static_assert((BL + BK) * CH * sizeof(float) % 1024 == 0, "radius tile alignment");
     static_assert(kStageFloats * sizeof(float) % 1024 == 0, "stage alignment");
 };
@@ -366,7 +397,7 @@ __device__ __forceinline__ void multi_origin(int item, int tiles_l, int tiles_k,
 struct MultiItemView {
     const CtgArgs *a;
     const CUtensorMap *mL, *mK, *mR;
-    int l0, k0, b0, tlk, n_chunks;
+    int l0, k0, b0, tlk, n_chunks, cid;  // cid: the case's index in the plan
 };
 
 // Work plan of one case: item i of this CTA is blockIdx.x + i * gridDim.x.
@@ -378,11 +409,12 @@ struct SinglePlan {
         return max(0, (n_tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x);
     }
     __device__ MultiItemView item(int i) const {
-        MultiItemView v{a, mL, mK, mR, 0, 0, 0, 0, a->n_chunks};
+        MultiItemView v{a, mL, mK, mR, 0, 0, 0, 0, a->n_chunks, 0};
         multi_origin((int)blockIdx.x + i * (int)gridDim.x, tiles_l, tiles_k, box_tiles, BL, BK,
                      v.l0, v.k0, v.b0, v.tlk);
         return v;
     }
+    __device__ const CtgArgs &case_args(int) const { return *a; }
 };
 
 // Work plan of many cases: a host-built table, sliced per CTA.
@@ -396,9 +428,10 @@ struct CasesPlan {
     __device__ MultiItemView item(int i) const {
         const MultiItem m = items[i];
         MultiItemView v{args + m.case_id, maps + 3 * m.case_id, maps + 3 * m.case_id + 1,
-                        maps + 3 * m.case_id + 2, m.l0, m.k0, m.b0, m.tile_lk, m.n_chunks};
+                        maps + 3 * m.case_id + 2, m.l0, m.k0, m.b0, m.tile_lk, m.n_chunks, m.case_id};
         return v;
     }
+    __device__ const CtgArgs &case_args(int cid) const { return args[cid]; }
 };
 
 template <int ST, int BH, int ML, int MK, class Plan>
@@ -438,6 +471,10 @@ __device__ __forceinline__ void multi_body(const Plan &P, unsigned long long wai
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     CtgArgs *my_args = reinterpret_cast<CtgArgs *>(arg_base + warp * kArgSlot);
+    const CtgArgs &a0 = P.case_args(0);
+    const RefQueue rq = ref_queue_of(reinterpret_cast<unsigned char *>(ring) + S::kQueueOff, warp,
+                                     a0.refq, a0.refq_cap, S::kWarps);
+    ref_queue_init(rq);
     constexpr int kFold3 = 8;
     const int my_items = P.n_items();
     uint32_t total = 0;
@@ -616,7 +653,8 @@ __device__ __forceinline__ void multi_body(const Plan &P, unsigned long long wai
         for (int j = 0; j < kMBT; ++j) {
             const int box = b0 + half * kMBT + j;
             if (box >= n_box) break;
-            float slo = 0.0f, shi = 0.0f, whi = 0.0f, wlo = 0.0f;
+            float slo = 0.0f, shi = 0.0f, whi = 0.0f, wlo = 0.0f, cslo = 0.0f, cwhi = 0.0f;
+            uint64_t rmask = 0;
 #pragma unroll
             for (int i = 0; i < ML; ++i) {
                 const int lq = l0 + tl + TL * i;
@@ -631,15 +669,33 @@ __device__ __forceinline__ void multi_body(const Plan &P, unsigned long long wai
                         for (int jj = 0; jj < kMBT; ++jj)
                             if (jj == j) a2 = acc2[i][c][jj];
                         const float A = __fadd_ru(acc3[((i * MK + c) * kMBT + j) * S::kThreads], a2);
-                        pair_epilogue(a, box, l, k, Lr[i][c], A, slo, shi, whi, wlo);
+                        if (pair_epilogue(a, box, l, k, Lr[i][c], A, slo, shi, whi, wlo, cslo, cwhi))
+                            rmask |= 1ull << (i * MK + c);
                     }
                 }
             }
+            // candidates of the FP64 refinement: queued, or (queue full) the FP32 terms
+            const bool queued =
+                a.ref.phi64 &&
+                ref_enqueue<ML * MK>(
+                    rq, rmask,
+                    [&](int q, int &l, int &k) {
+                        const int lq = l0 + tl + TL * (q / MK);
+                        l = a.live ? __ldg(&a.live[lq]) : lq;
+                        k = v.k0 + tk + TK * (q % MK);
+                    },
+                    (v.cid << 16) | box, tlk * a.warps_per_tile + wq);
+            if (!queued) {
+                slo = __fadd_rd(slo, cslo);
+                whi = __fadd_ru(whi, cwhi);
+            }
             // partial rows per item: kWarpsHalf (the warp's place in its
             // half; each box belongs to exactly one half)
-            write_warp_partials(a, tlk, wq, box, slo, shi, whi, wlo, ML * MK);
+            write_warp_partials(a, tlk, wq, box, slo, shi, whi, wlo, ML * MK + 1);
         }
     }
+    // the queued refinements: published for k_refine_queue, or refined here
+    ref_finish(rq, a0.refq_cnt, S::kWarps, [&](int cid) -> const CtgArgs & { return P.case_args(cid); });
     __syncthreads();
     if (threadIdx.x == 0 && *abort_flag) {
         for (int s = 0; s < ST; ++s) {
@@ -872,4 +928,81 @@ cudaError_t launch_ctg(const CtgVariant &v, const CUtensorMap &mL, const CUtenso
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// The refinement of the queued pairs (see refine.cuh): k_refine_queue refines
+// every entry of every region with one warp, k_refine_apply adds each region's
+// results to their partial-sum rows in queue order (regions of different warps
+// never share a row, so the sums do not depend on timing).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_refine_queue(const RefQueueArgs a) {
+    extern __shared__ int soff[];  // [n_regions + 1] exclusive prefix of the counts
+    __shared__ int part[256];
+    const int n = a.n_regions, t = threadIdx.x;
+    const int per = (n + 255) / 256;
+    int sum = 0;
+    for (int i = t * per; i < min(n, (t + 1) * per); ++i) sum += min(a.cnt[i], a.cap);
+    part[t] = sum;
+    __syncthreads();
+    if (t == 0) {
+        int run = 0;
+        for (int i = 0; i < 256; ++i) {
+            const int v = part[i];
+            part[i] = run;
+            run += v;
+        }
+        soff[n] = run;
+    }
+    __syncthreads();
+    int run = part[t];
+    for (int i = t * per; i < min(n, (t + 1) * per); ++i) {
+        soff[i] = run;
+        run += min(a.cnt[i], a.cap);
+    }
+    __syncthreads();
+    const int total = soff[n];
+    const int lane = t & 31;
+    const int gw = (int)((blockIdx.x * blockDim.x + t) >> 5), nw = (int)((gridDim.x * blockDim.x) >> 5);
+    for (int e = gw; e < total; e += nw) {
+        int lo = 0, hi = n;  // the region g with soff[g] <= e < soff[g + 1]
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (soff[mid] <= e) lo = mid;
+            else hi = mid;
+        }
+        const size_t slot = (size_t)lo * a.cap + (e - soff[lo]);
+        const int4 q = a.e[slot];
+        const CtgArgs &c = a.args ? a.args[q.z >> 16] : a.one;
+        const int box = q.z & 0xffff;
+        const int kl = __ldg(&c.ctg_line[q.y]);
+        const float Lt = __ldg(&c.lodf[(size_t)q.y * c.n_l + q.x]);
+        const RefOut o = refine_term(c.ref, box, q.x, kl, q.y, Lt, __ldg(&c.ref.rate_c64[q.x]), kRefPair);
+        if (lane == 0) a.res[slot] = make_double2(o.s_lo, o.w);
+    }
+}
+
+__global__ void k_refine_apply(const RefQueueArgs a) {
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= a.n_regions) return;
+    const int n = min(a.cnt[g], a.cap);
+    for (int i = 0; i < n; ++i) {
+        const size_t slot = (size_t)g * a.cap + i;
+        const int4 q = a.e[slot];
+        const CtgArgs &c = a.args ? a.args[q.z >> 16] : a.one;
+        const double2 r = a.res[slot];
+        double *p = c.partials + ((size_t)q.w * c.n_box + (q.z & 0xffff)) * kPartVals;
+        p[0] = __dadd_rd(p[0], r.x);
+        p[2] = __dadd_ru(p[2], r.y);
+    }
+}
+
+cudaError_t launch_refine_queue(const RefQueueArgs &a, int num_sms, cudaStream_t s) {
+    if (a.n_regions <= 0) return cudaSuccess;
+    const size_t smem = (size_t)(a.n_regions + 1) * sizeof(int);
+    k_refine_queue<<<num_sms * 4, 256, smem, s>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_refine_apply<<<(a.n_regions + 127) / 128, 128, 0, s>>>(a);
+    return cudaGetLastError();
+}
 }  // namespace ibp

@@ -167,6 +167,94 @@ cudaError_t launch_class_radius(const ClsArgs &a, cudaStream_t s) {
 // (gamma_base + 2.01u) of it plus eta, L~ is within u of L).  One thread per
 // line and block of kScreenK contingencies; FP32 directed per thread, FP64
 // directed per block.
+// FP64 paper-mode interval of pair (k, l): centre c_l + L c_k, radius
+// R_l + |L| R_k from the per-line FP64 values, with the bound
+//   E = (n + 2) u64 X + e_L (|c_k| + R_k + n u64 X_k) + u64 (|c| + rad)
+//       + 2^-118 (1 + |L|)(1 + e_L) (sum r + sum |c|)
+// on its distance from the exact paper-mode interval (X, X_k, e_L as in the
+// tight pairs' refinement); s_lo and w as there.
+struct PaperRef {
+    double s_lo, w;
+};
+__device__ __forceinline__ PaperRef paper_refine(const PaperArgs &a, int j, int l, int kl, int k, float Lt) {
+    double eL;
+    const double L = ref_lodf(a.ref, k, l, Lt, eL), aL = fabs(L);
+    const size_t ob = (size_t)j * a.n_l;
+    const double cl = a.lc64[ob + l], ck = a.lc64[ob + kl];
+    const double Rl = a.lR64[ob + l], Rk = a.lR64[ob + kl];
+    const double Xl = (double)a.lX[ob + l], Xk = (double)a.lX[ob + kl];
+    const double c = fma(L, ck, cl);
+    const double rad = __fma_ru(aL, Rk, Rl);
+    const float *bc = a.ref.box_consts + (size_t)j * 4;
+    const double tot = __dadd_ru((double)bc[2], (double)bc[3]);
+    const double nu = ref_nu(a.ref.n_a_pad);
+    double E = __dmul_ru(__dadd_ru(nu, 2.0 * kU64), __dmul_ru(k2m20p, __fma_ru(aL, Xk, Xl)));
+    E = __fma_ru(eL, __fma_ru(nu, Xk, __dadd_ru(fabs(ck), Rk)), E);
+    E = __fma_ru(kU64, __dadd_ru(fabs(c), rad), E);
+    E = __fma_ru(__dmul_ru(2.0 * k2m119, __dmul_ru(__dadd_ru(1.0, aL), __dadd_ru(1.0, eL))), tot, E);
+    const double rho = __dadd_ru(rad, E);
+    const double lo = __dsub_rd(c, rho), hi = __dadd_ru(c, rho);
+    const double alo = lo >= 0.0 ? lo : (hi <= 0.0 ? -hi : 0.0);
+    const double rating = a.ref.rate_c64[l];
+    PaperRef o;
+    o.s_lo = fmax(__dsub_rd(alo, rating), 0.0);
+    o.w = __fma_ru(4.0 * kU64, __dadd_ru(__dadd_ru(rad, fabs(c)), rating), __dmul_ru(2.0, E));
+    return o;
+}
+
+// One warp per (line, box): the FP64 base-flow values of the paper mode's
+// refinement (LineExactArgs).
+__global__ void __launch_bounds__(256) k_line_exact(const LineExactArgs a) {
+    const int lane = threadIdx.x & 31;
+    const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+    const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+    const int nv = a.ref.n_a_pad >> 2;
+    for (int item = gw; item < a.n_l * a.n_box; item += nw) {
+        const int l = item % a.n_l, j = item / a.n_l;
+        const size_t ob = (size_t)j * a.ref.n_a_pad;
+        const float4 *ph = reinterpret_cast<const float4 *>(a.ref.phi_hi + (size_t)l * a.ref.n_a_pad);
+        const double2 *pl = reinterpret_cast<const double2 *>(a.ref.phi64 + (size_t)l * a.ref.n_a_pad);
+        const double2 *cb = reinterpret_cast<const double2 *>(a.ref.cbus + ob);
+        const double2 *rb = reinterpret_cast<const double2 *>(a.ref.rbus64 + ob);
+        const float4 *r32 = reinterpret_cast<const float4 *>(a.ref.rbus + ob);
+        const float4 *c32 = reinterpret_cast<const float4 *>(a.ref.cabs + ob);
+        double S = 0.0, C = 0.0;
+        float X = 0.0f;
+        auto col = [&](float h, double p, double c, double r, float rc) {
+            S = __fma_ru(fabs(p), r, S);
+            C = fma(p, c, C);
+            X = __fmaf_ru(fabsf(h), rc, X);
+        };
+        for (int v = lane; v < nv; v += 32) {
+            const float4 h = __ldg(&ph[v]);
+            const double2 p01 = __ldg(&pl[2 * v]), p23 = __ldg(&pl[2 * v + 1]);
+            const double2 c01 = __ldg(&cb[2 * v]), c23 = __ldg(&cb[2 * v + 1]);
+            const double2 r01 = __ldg(&rb[2 * v]), r23 = __ldg(&rb[2 * v + 1]);
+            const float4 q = __ldg(&r32[v]), ca = __ldg(&c32[v]);
+            col(h.x, p01.x, c01.x, r01.x, __fadd_ru(q.x, ca.x));
+            col(h.y, p01.y, c01.y, r01.y, __fadd_ru(q.y, ca.y));
+            col(h.z, p23.x, c23.x, r23.x, __fadd_ru(q.z, ca.z));
+            col(h.w, p23.y, c23.y, r23.y, __fadd_ru(q.w, ca.w));
+        }
+        S = warp_sum_ru(S);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) C += __shfl_xor_sync(0xffffffffu, C, o);
+        X = warp_sum_ru_f(X);
+        if (lane == 0) {
+            const size_t o = (size_t)j * a.n_l + l;
+            a.c64[o] = C;
+            a.R64[o] = S;
+            a.X[o] = X;
+        }
+    }
+}
+
+cudaError_t launch_line_exact(const LineExactArgs &a, int num_sms, cudaStream_t s) {
+    if (a.n_l <= 0 || a.n_box <= 0) return cudaSuccess;
+    k_line_exact<<<num_sms * 8, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
 int paper_partials_count(int n_l, int n_c) {
     return ((n_l + kScreenThreads - 1) / kScreenThreads) * ((n_c + kScreenK - 1) / kScreenK);
 }
@@ -176,6 +264,7 @@ __global__ void __launch_bounds__(kScreenThreads) k_paper(const PaperArgs a) {
     const int j = blockIdx.z;
     const int k0 = blockIdx.y * kScreenK, k1 = min(k0 + kScreenK, a.n_c);
     float slo = 0.0f, shi = 0.0f, whi = 0.0f, wlo = 0.0f;
+    double rs = 0.0, rw = 0.0;  // refined obj_hi terms of this thread (FP64)
     if (l < a.n_l) {
         const size_t ob = (size_t)j * a.n_l;
         const float cl = __ldg(&a.line_c[ob + l]), el = __ldg(&a.line_e[ob + l]);
@@ -201,17 +290,27 @@ __global__ void __launch_bounds__(kScreenThreads) k_paper(const PaperArgs a) {
             const float rho = __fadd_ru(rp, ec);
             float alo, ahi;
             abs_interval(__fsub_rd(c, rho), __fadd_ru(c, rho), alo, ahi);
-            const float vlo = fmax0(__fsub_rd(alo, rup));
+            float vlo = fmax0(__fsub_rd(alo, rup));
             const float vhi = fmax0(__fsub_ru(ahi, rdn));
-            slo = __fadd_rd(slo, vlo);
             shi = __fadd_ru(shi, vhi);
             if (vhi > 0.0f) {
                 float w = __fmaf_ru(a.gamma_base + 10.0f * kU, m, __fmul_ru(2.0f, ec));
                 w = __fmaf_ru(kU, rup, w);
                 w = __fmaf_ru(4.0f, eta, w);
                 wlo = __fadd_ru(wlo, w);
-                if (__fadd_ru(__fsub_ru(alo, rdn), w) > 0.0f) whi = __fadd_ru(whi, w);
+                if (__fadd_ru(__fsub_ru(alo, rdn), w) > 0.0f) {
+                    if (a.ref.phi64) {
+                        // the FP64 paper-mode interval from the per-line FP64 values
+                        const PaperRef pr = paper_refine(a, j, l, kl, k, Lt);
+                        rs = __dadd_rd(rs, pr.s_lo);
+                        rw = __dadd_ru(rw, pr.w);
+                        vlo = 0.0f;
+                    } else {
+                        whi = __fadd_ru(whi, w);
+                    }
+                }
             }
+            slo = __fadd_rd(slo, vlo);
         }
     }
     // the FP32 directed sums of up to kScreenK terms are within 2u kScreenK
@@ -219,8 +318,8 @@ __global__ void __launch_bounds__(kScreenThreads) k_paper(const PaperArgs a) {
     const float g = 2.02f * kU * (float)kScreenK;
     whi = __fmaf_ru(g, slo, whi);
     wlo = __fmaf_ru(g, shi, wlo);
-    double d0 = warp_sum_rd((double)slo), d1 = warp_sum_ru((double)shi);
-    double d2 = warp_sum_ru((double)whi), d3 = warp_sum_ru((double)wlo);
+    double d0 = warp_sum_rd(__dadd_rd((double)slo, rs)), d1 = warp_sum_ru((double)shi);
+    double d2 = warp_sum_ru(__dadd_ru((double)whi, rw)), d3 = warp_sum_ru((double)wlo);
     __shared__ double sh[kScreenThreads / 32][4];
     const int w = threadIdx.x >> 5;
     if ((threadIdx.x & 31) == 0) {

@@ -5,6 +5,7 @@
 // or carries an explicit error term; see the comment of each kernel.
 #include "common.cuh"
 #include "internal.h"
+#include "refine.cuh"
 
 #include <cfloat>
 
@@ -49,7 +50,7 @@ __global__ void __launch_bounds__(256) k_bus(BusArgs a) {
         if (!(x <= y) || !isfinite(x) || !isfinite(y)) bad = 1;
     }
     for (int col = first; col < a.n_a_pad; col += stride) {
-        double c = 0.0;
+        double c = 0.0, rd64 = 0.0;
         float r32 = 0.0f, ca = 0.0f;
         if (col < a.n_a) {
             double plo = 0.0, phi = 0.0;
@@ -65,7 +66,8 @@ __global__ void __launch_bounds__(256) k_bus(BusArgs a) {
             }
             c = 0.5 * (plo + phi);
             const double r = fmax(__dadd_ru(phi, -c), __dadd_ru(c, -plo));
-            r32 = __double2float_ru(fmax(r, 0.0));
+            rd64 = fmax(r, 0.0);
+            r32 = __double2float_ru(rd64);
             ca = __double2float_ru(fabs(c));
         }
         a.cbus[(size_t)j * a.n_a_pad + col] = c;
@@ -74,6 +76,7 @@ __global__ void __launch_bounds__(256) k_bus(BusArgs a) {
             a.cbus2[(size_t)j * a.n_a_pad + col] = make_float2(ch, __double2float_rn(c - (double)ch));
         }
         a.rbus[(size_t)j * a.n_a_pad + col] = r32;
+        if (a.rbus64) a.rbus64[(size_t)j * a.n_a_pad + col] = rd64;
         a.cabs[(size_t)j * a.n_a_pad + col] = ca;
         if (a.rbus_t) a.rbus_t[(size_t)col * a.n_box_pad + j] = r32;
         rsum = __fadd_ru(rsum, r32);
@@ -161,9 +164,15 @@ int base_partials_count(int num_sms) { return num_sms * 2 * kBaseWarps; }
 // Per (line, box) epilogue of the base flows: certified interval, violation
 // interval of eq. (slack-sfb), error allowance, active-set recording and, for
 // bridge lines, their n_c contingency pairs in closed form.  c = FP32 centre,
-// C, R = round-up sums of |Phi~||c_b| and |Phi~| r_b.
-__device__ __forceinline__ void base_epilogue(const BaseArgs &a, int l, int j, float c, float C,
-                                              float R, double *part) {
+// C, R = round-up sums of |Phi~||c_b| and |Phi~| r_b.  Every lane of the warp
+// calls it with the same values; `writer` (one lane) stores the results.  With
+// the FP64 refinement on (a.ref.phi64), a base term whose lower violation
+// bound can be positive is left out of the partial sums and bit 0 of the
+// result is set; bit 1 likewise for the bridge's contingency pairs.
+__device__ __forceinline__ int base_epilogue(const BaseArgs &a, int l, int j, float c, float C,
+                                             float R, double *part, bool writer) {
+    const bool refine = a.ref.phi64 != nullptr;
+    int flags = 0;
     const float *bc = a.box_consts + (size_t)j * 4;
     const float eta_r = bc[0], eta_c = bc[1];
     const float e = __fadd_ru(__fmul_ru(2.1f * kU, C), eta_c);
@@ -172,7 +181,8 @@ __device__ __forceinline__ void base_epilogue(const BaseArgs &a, int l, int j, f
     const float flo = __fsub_rd(c, rho), fhi = __fadd_ru(c, rho);
     float alo, ahi;
     abs_interval(flo, fhi, alo, ahi);
-    const float slo = fmax0(__fsub_rd(alo, a.rate_up[l]));
+    const float slo_f = fmax0(__fsub_rd(alo, a.rate_up[l]));
+    float slo = slo_f;
     const float shi = fmax0(__fsub_ru(ahi, a.rate_dn[l]));
     float whi = 0.0f, wlo = 0.0f;
     if (shi > 0.0f) {
@@ -181,12 +191,21 @@ __device__ __forceinline__ void base_epilogue(const BaseArgs &a, int l, int j, f
         const float w = __fmaf_ru(a.gamma_base + 3.0f * kU, R,
                                   __fmaf_ru(2.0f, e, __fmaf_ru(kU, a.rate_up[l], 2.0f * eta_r)));
         wlo = w;
-        if (__fadd_ru(__fsub_ru(alo, a.rate_dn[l]), w) > 0.0f) whi = w;
+        if (__fadd_ru(__fsub_ru(alo, a.rate_dn[l]), w) > 0.0f) {
+            whi = w;
+            if (refine) {
+                flags |= 1;
+                slo = whi = 0.0f;  // base_refine adds the FP64 term
+            }
+        }
     }
-    a.line_c[(size_t)j * a.n_l + l] = c;
-    a.line_e[(size_t)j * a.n_l + l] = e;
-    a.line_R[(size_t)j * a.n_l + l] = R;
-    if (a.act_list && slo > 0.0f) {
+    if (writer) {
+        a.line_c[(size_t)j * a.n_l + l] = c;
+        a.line_e[(size_t)j * a.n_l + l] = e;
+        a.line_R[(size_t)j * a.n_l + l] = R;
+    }
+    // the adjoint's active set: certified by the FP32 bound
+    if (writer && a.act_list && slo_f > 0.0f) {
         const int idx = atomicAdd(&a.act_count[j], 1);
         if (idx < a.act_cap)
             a.act_list[(size_t)j * a.act_cap + idx] =
@@ -195,10 +214,12 @@ __device__ __forceinline__ void base_epilogue(const BaseArgs &a, int l, int j, f
             atomicOr(a.err, kErrOverflow);
     }
     double *q = part + j * kPartVals;
-    q[0] = __dadd_rd(q[0], (double)slo);
-    q[1] = __dadd_ru(q[1], (double)shi);
-    q[2] = __dadd_ru(q[2], (double)whi);
-    q[3] = __dadd_ru(q[3], (double)wlo);
+    if (writer) {
+        q[0] = __dadd_rd(q[0], (double)slo);
+        q[1] = __dadd_ru(q[1], (double)shi);
+        q[2] = __dadd_ru(q[2], (double)whi);
+        q[3] = __dadd_ru(q[3], (double)wlo);
+    }
     if (a.is_bridge && a.is_bridge[l] && a.n_c > 0) {
         // A bridge carries the net injection of the side away from
         // the slack; no non-islanding outage changes that, so
@@ -206,21 +227,30 @@ __device__ __forceinline__ void base_epilogue(const BaseArgs &a, int l, int j, f
         // base interval [c - rho, c + rho] (eq. (slack-Sc) with the
         // contingency rating), n_c times.
         const float rcu = a.rate_c_up[l], rcd = a.rate_c_dn[l];
-        const float clo = fmax0(__fsub_rd(alo, rcu));
+        const float clo_f = fmax0(__fsub_rd(alo, rcu));
+        float clo = clo_f;
         const float chi = fmax0(__fsub_ru(ahi, rcd));
         float cwh = 0.0f, cwl = 0.0f;
         if (chi > 0.0f) {
             const float w = __fmaf_ru(a.gamma_base + 3.0f * kU, R,
                                       __fmaf_ru(2.0f, e, __fmaf_ru(kU, rcu, 2.0f * eta_r)));
             cwl = w;
-            if (__fadd_ru(__fsub_ru(alo, rcd), w) > 0.0f) cwh = w;
+            if (__fadd_ru(__fsub_ru(alo, rcd), w) > 0.0f) {
+                cwh = w;
+                if (refine) {
+                    flags |= 2;
+                    clo = cwh = 0.0f;
+                }
+            }
         }
         const double nc = (double)a.n_c;
-        q[0] = __dadd_rd(q[0], __dmul_rd(nc, (double)clo));
-        q[1] = __dadd_ru(q[1], __dmul_ru(nc, (double)chi));
-        q[2] = __dadd_ru(q[2], __dmul_ru(nc, (double)cwh));
-        q[3] = __dadd_ru(q[3], __dmul_ru(nc, (double)cwl));
-        if (a.act_list && clo > 0.0f) {
+        if (writer) {
+            q[0] = __dadd_rd(q[0], __dmul_rd(nc, (double)clo));
+            q[1] = __dadd_ru(q[1], __dmul_ru(nc, (double)chi));
+            q[2] = __dadd_ru(q[2], __dmul_ru(nc, (double)cwh));
+            q[3] = __dadd_ru(q[3], __dmul_ru(nc, (double)cwl));
+        }
+        if (writer && a.act_list && clo_f > 0.0f) {
             const int idx = atomicAdd(&a.act_count[j], 1);
             if (idx < a.act_cap)
                 a.act_list[(size_t)j * a.act_cap + idx] =
@@ -230,11 +260,33 @@ __device__ __forceinline__ void base_epilogue(const BaseArgs &a, int l, int j, f
                 atomicOr(a.err, kErrOverflow);
         }
     }
+    return flags;
+}
+
+// The FP64 refinement of the terms base_epilogue left out (flags): the base
+// violation of line l (base rating) and, for a bridge, its n_c contingency
+// pairs (contingency rating).  Warp-cooperative; lane 0 writes.
+static __device__ __noinline__ void base_refine(const BaseArgs &a, int l, int j, int flags, double *part) {
+    const int lane = threadIdx.x & 31;
+    double *q = part + j * kPartVals;
+    for (int t = 0; t < 2; ++t) {
+        if (!((flags >> t) & 1)) continue;
+        const double rating = t == 0 ? a.ref.rate64[l] : a.ref.rate_c64[l];
+        const RefOut o = refine_term(a.ref, j, l, l, -1, 0.0f, rating, kRefLine);
+        const double m = t == 0 ? 1.0 : (double)a.n_c;
+        if (lane == 0) {
+            q[0] = __dadd_rd(q[0], __dmul_rd(m, o.s_lo));
+            q[2] = __dadd_ru(q[2], __dmul_ru(m, o.w));
+        }
+    }
 }
 
 // Compensated FP32 accumulation of sum_b Phi~[l,b] c_b with c_b = hi + lo:
 // each product Phi~ hi is split exactly (FMA remainder), the running sum uses
-// TwoSum, and Phi~ lo goes to the compensation term.  The error is below
+// TwoSum (Knuth, The Art of Computer Programming vol. 2, Sec. 4.2.2; the
+// summation is the compensated dot product of Ogita, Rump and Oishi,
+// "Accurate sum and dot product", SIAM J. Sci. Comput. 26(6), 2005), and
+// Phi~ lo goes to the compensation term.  The error is below
 // n u^2 sum_b |Phi~[l,b] c_b| plus the representation of c_b (u^2 |c_b|), far
 // inside the 0.1 u C_l left in e_l = 2.1 u C_l for the summation.
 struct FF {
@@ -361,7 +413,8 @@ __global__ void __launch_bounds__(kBaseWarps * 32) k_base_ff(BaseArgs a) {
                 __fadd_ru(__fadd_ru(C[jj].x, C[jj].y), __fadd_ru(C[jj].z, C[jj].w)));
             const float Rs = warp_sum_ru_f(
                 __fadd_ru(__fadd_ru(R[jj].x, R[jj].y), __fadd_ru(R[jj].z, R[jj].w)));
-            if (lane == 0) base_epilogue(a, l, j0 + jj, __double2float_rn(d), Cs, Rs, part);
+            const int f = base_epilogue(a, l, j0 + jj, __double2float_rn(d), Cs, Rs, part, lane == 0);
+            if (f) base_refine(a, l, j0 + jj, f, part);
         }
     }
 }
@@ -426,7 +479,8 @@ __global__ void __launch_bounds__(kBaseWarps * 32) k_base(BaseArgs a) {
             for (int o = 16; o > 0; o >>= 1) cs += __shfl_xor_sync(0xffffffffu, cs, o);
             C = warp_sum_ru_f(C);
             R = warp_sum_ru_f(R);
-            if (lane == 0) base_epilogue(a, l, j, __double2float_rn(cs), C, R, part);
+            const int f = base_epilogue(a, l, j, __double2float_rn(cs), C, R, part, lane == 0);
+            if (f) base_refine(a, l, j, f, part);
             hl = nullptr;
         }
     }
@@ -702,22 +756,25 @@ __device__ __forceinline__ float to_f32_flushed(double x) {
 }
 
 // Z is column-major (nb_r x n_l): column l holds Phi_r[l, :] (reduced buses).
+// phi_a = the FP32 PTDF of the active columns; phi64 (optional) = the same
+// columns in FP64, as built.
 __global__ void k_extract_phi(const double *Z, int nb_r, int n_l, const int *act_red, int n_a,
-                              int n_a_pad, float *phi_a) {
+                              int n_a_pad, float *phi_a, double *phi64) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t tot = (int64_t)n_l * n_a_pad;
     if (i >= tot) return;
     const int l = (int)(i / n_a_pad), a = (int)(i % n_a_pad);
-    float v = 0.0f;
-    if (a < n_a) v = to_f32_flushed(Z[(int64_t)l * nb_r + act_red[a]]);
-    phi_a[i] = v;
+    double x = 0.0;
+    if (a < n_a) x = Z[(int64_t)l * nb_r + act_red[a]];
+    phi_a[i] = a < n_a ? to_f32_flushed(x) : 0.0f;
+    if (phi64) phi64[i] = x;
 }
 
 cudaError_t launch_extract_phi(const double *Z, int nb_r, int n_l, const int *act_red, int n_a,
-                               int n_a_pad, float *phi_a, cudaStream_t s) {
+                               int n_a_pad, float *phi_a, double *phi64, cudaStream_t s) {
     const int64_t tot = (int64_t)n_l * n_a_pad;
     k_extract_phi<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(Z, nb_r, n_l, act_red, n_a, n_a_pad,
-                                                                phi_a);
+                                                                phi_a, phi64);
     return cudaGetLastError();
 }
 
@@ -725,7 +782,8 @@ cudaError_t launch_extract_phi(const double *Z, int nb_r, int n_l, const int *ac
 // PTDF_line[l,k] = Phi[l, from_k] - Phi[l, to_k] (slack entries are 0).
 // One block per contingency.
 __global__ void k_lodf(const double *Z, int nb_r, int n_l, int n_c, const int *fr, const int *to,
-                       const int *ctg_line, float *lodf, double *den_out, float *maxabs) {
+                       const int *ctg_line, float *lodf, float *lodf_lo, double *den_out,
+                       float *maxabs) {
     const int k = blockIdx.x;
     const int f = fr[k], t = to[k], kl = ctg_line[k];
     auto ptl = [&](int l) -> double {
@@ -738,13 +796,16 @@ __global__ void k_lodf(const double *Z, int nb_r, int n_l, int n_c, const int *f
     if (threadIdx.x == 0) den_out[k] = den;
     float mx = 0.0f;
     for (int l = threadIdx.x; l < n_l; l += blockDim.x) {
-        float v;
+        float v, w = 0.0f;
         if (l == kl) {
             v = -1.0f;
         } else {
-            v = to_f32_flushed(ptl(l) / den);
+            const double x = ptl(l) / den;
+            v = to_f32_flushed(x);
+            w = __double2float_rn(x - (double)v);  // the FP64 remainder (optional copy)
         }
         lodf[(int64_t)k * n_l + l] = v;
+        if (lodf_lo) lodf_lo[(int64_t)k * n_l + l] = w;
         mx = fmaxf(mx, fabsf(v));
     }
     mx = warp_max_f(mx);
@@ -752,11 +813,11 @@ __global__ void k_lodf(const double *Z, int nb_r, int n_l, int n_c, const int *f
 }
 
 cudaError_t launch_lodf(const double *Z, int nb_r, int n_l, int n_c, const int *ctg_from_red,
-                        const int *ctg_to_red, const int *ctg_line, float *lodf, double *den_out,
-                        float *maxabs_out, cudaStream_t s) {
+                        const int *ctg_to_red, const int *ctg_line, float *lodf, float *lodf_lo,
+                        double *den_out, float *maxabs_out, cudaStream_t s) {
     if (n_c <= 0) return cudaSuccess;
-    k_lodf<<<n_c, 256, 0, s>>>(Z, nb_r, n_l, n_c, ctg_from_red, ctg_to_red, ctg_line, lodf, den_out,
-                               maxabs_out);
+    k_lodf<<<n_c, 256, 0, s>>>(Z, nb_r, n_l, n_c, ctg_from_red, ctg_to_red, ctg_line, lodf, lodf_lo,
+                               den_out, maxabs_out);
     return cudaGetLastError();
 }
 

@@ -28,10 +28,31 @@ constexpr size_t kNoAllocBytes = size_t(8) << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
 // Host-side device addresses of g_noalloc_scratch, one per device ordinal,
-// filled on the first call on that device.
+// filled on the first call on that device, together with the CUDA context
+// they belong to: after the context is destroyed and created again (e.g. by
+// cudaDeviceReset) the module is loaded anew, and the next call looks the
+// address up again instead of using the stale one.
 constexpr int kMaxDevices = 64;
 static std::mutex g_noalloc_mu;
 static unsigned char *g_noalloc_base[kMaxDevices] = {};
+static void *g_noalloc_ctx[kMaxDevices] = {};
+
+// The current driver context (CUcontext) of the calling thread, through the
+// runtime's driver entry point (the library does not link libcuda directly).
+static bool current_context(void **ctx) {
+    typedef int (*GetCtx)(void **);
+    static GetCtx fn = nullptr;
+    if (!fn) {
+        cudaDriverEntryPointQueryResult q;
+        void *p = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess || !p)
+            return false;
+        fn = reinterpret_cast<GetCtx>(p);
+    }
+    return fn(ctx) == 0 && *ctx != nullptr;
+}
 
 constexpr int kPlainBL = 128, kPlainBK = 64, kPlainCH = 32;
 
@@ -46,7 +67,10 @@ __global__ void __launch_bounds__(256, 1)
     __shared__ __align__(16) float sL[BL * PAD];
     __shared__ __align__(16) float sK[BK * PAD];
     __shared__ __align__(16) float sR[CH];
+    __shared__ __align__(16) unsigned char squeue[ref_queue_bytes(8)];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const RefQueue rq = ref_queue_of(squeue, warp);
+    ref_queue_init(rq);
     const int tl = (warp >> 1) * 4 + (lane >> 3);
     const int tk = (warp & 1) * 8 + (lane & 7);
     for (int tile = blockIdx.x; tile < a.n_tiles; tile += gridDim.x) {
@@ -121,17 +145,36 @@ __global__ void __launch_bounds__(256, 1)
                     }
             }
         }
-        float slo = 0.0f, shi = 0.0f, whi = 0.0f, wlo = 0.0f;
+        float slo = 0.0f, shi = 0.0f, whi = 0.0f, wlo = 0.0f, cslo = 0.0f, cwhi = 0.0f;
+        uint64_t rmask = 0;
 #pragma unroll
         for (int i = 0; i < ML; ++i)
 #pragma unroll
             for (int j = 0; j < MK; ++j) {
                 const int l = l0 + tl + 16 * i, k = k0 + tk + 16 * j;
-                if (l < a.n_l && k < a.n_c)
-                    pair_epilogue(a, 0, l, k, Lr[i][j], __fadd_ru(acc3[i][j], acc2[i][j]), slo, shi, whi, wlo);
+                if (l < a.n_l && k < a.n_c &&
+                    pair_epilogue(a, 0, l, k, Lr[i][j], __fadd_ru(acc3[i][j], acc2[i][j]), slo, shi, whi,
+                                  wlo, cslo, cwhi))
+                    rmask |= 1ull << (i * MK + j);
             }
-        write_warp_partials(a, tile, warp, 0, slo, shi, whi, wlo, ML * MK);
+        // candidates of the FP64 refinement: queued, or (queue full) the FP32 terms
+        const bool queued =
+            a.ref.phi64 &&
+            ref_enqueue<ML * MK>(
+                rq, rmask,
+                [&](int q, int &l, int &k) {
+                    l = l0 + tl + 16 * (q / MK);
+                    k = k0 + tk + 16 * (q % MK);
+                },
+                0, tile * a.warps_per_tile + warp);
+        if (!queued) {
+            slo = __fadd_rd(slo, cslo);
+            whi = __fadd_ru(whi, cwhi);
+        }
+        write_warp_partials(a, tile, warp, 0, slo, shi, whi, wlo, ML * MK + 1);
     }
+    // the queued refinements, after the last tile
+    if (a.ref.phi64) ref_finish(rq, nullptr, 8, [&](int) -> const CtgArgs & { return a; });
 }
 
 static float noalloc_gamma(long n1, long n2, long n3) {
@@ -140,7 +183,7 @@ static float noalloc_gamma(long n1, long n2, long n3) {
 }
 
 struct NoAllocLayout {
-    size_t err, consts, cbus, rbus, cabs, line_c, line_e, line_R, part_base, part_ctg, total;
+    size_t err, consts, cbus, rbus, rbus64, cabs, line_c, line_e, line_R, part_base, part_ctg, total;
 };
 
 static NoAllocLayout noalloc_layout(const CaseView &v, int n_tiles) {
@@ -155,6 +198,7 @@ static NoAllocLayout noalloc_layout(const CaseView &v, int n_tiles) {
     L.consts = take(4 * sizeof(float));
     L.cbus = take((size_t)v.n_a_pad * sizeof(double));
     L.rbus = take((size_t)v.n_a_pad * sizeof(float));
+    L.rbus64 = take((size_t)v.n_a_pad * sizeof(double));
     L.cabs = take((size_t)v.n_a_pad * sizeof(float));
     L.line_c = take((size_t)v.n_line * sizeof(float));
     L.line_e = take((size_t)v.n_line * sizeof(float));
@@ -200,6 +244,12 @@ extern "C" ibp_status ibp_bound_noalloc(ibp_case *c, const double *box_lo, const
     unsigned char *base = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        void *ctx = nullptr;
+        if (!current_context(&ctx)) return set_error(IBP_ECUDA, "no current CUDA context on the case's device");
+        if (g_noalloc_ctx[v.device] != ctx) {
+            g_noalloc_base[v.device] = nullptr;
+            g_noalloc_ctx[v.device] = ctx;
+        }
         if (!g_noalloc_base[v.device]) {
             void *p = nullptr;
             const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
@@ -218,6 +268,7 @@ extern "C" ibp_status ibp_bound_noalloc(ibp_case *c, const double *box_lo, const
     float *consts = reinterpret_cast<float *>(base + lay.consts);
     double *cbus = reinterpret_cast<double *>(base + lay.cbus);
     float *rbus = reinterpret_cast<float *>(base + lay.rbus);
+    double *rbus64 = reinterpret_cast<double *>(base + lay.rbus64);
     float *cabs = reinterpret_cast<float *>(base + lay.cabs);
     float *line_c = reinterpret_cast<float *>(base + lay.line_c);
     float *line_e = reinterpret_cast<float *>(base + lay.line_e);
@@ -231,7 +282,7 @@ extern "C" ibp_status ibp_bound_noalloc(ibp_case *c, const double *box_lo, const
     BusArgs ba{};
     ba.n_a = v.n_a; ba.n_a_pad = v.n_a_pad; ba.n_dev = v.n_dev; ba.n_gen = v.n_gen; ba.n_box = 1;
     ba.act_ptr = v.act_ptr; ba.act_dev = v.act_dev; ba.box_lo = box_lo; ba.box_hi = box_hi;
-    ba.cbus = cbus; ba.rbus = rbus; ba.rbus_t = nullptr; ba.n_box_pad = 0; ba.cabs = cabs;
+    ba.cbus = cbus; ba.rbus = rbus; ba.rbus64 = rbus64; ba.rbus_t = nullptr; ba.n_box_pad = 0; ba.cabs = cabs;
     ba.box_consts = consts; ba.err = err;
     if (e == cudaSuccess) e = launch_bus(ba, s);
 
@@ -242,6 +293,15 @@ extern "C" ibp_status ibp_bound_noalloc(ibp_case *c, const double *box_lo, const
     bb.gamma_base = noalloc_gamma((v.n_a_pad / 4 + 31) / 32, 2, 5);
     bb.line_c = line_c; bb.line_e = line_e; bb.line_R = line_R;
     bb.hat_l = nullptr; bb.hat_k = nullptr; bb.partials = part_base; bb.err = err;
+    // FP64 refinement of the terms that can reach obj_hi (as in ibp_bound)
+    RefArgs ref{};
+    if (v.phi64) {
+        ref.phi_hi = v.phi_a; ref.phi64 = v.phi64; ref.cbus = cbus; ref.rbus64 = rbus64;
+        ref.rbus = rbus; ref.cabs = cabs; ref.box_consts = consts;
+        ref.rate64 = v.rate64; ref.rate_c64 = v.rate_c64; ref.n_a_pad = v.n_a_pad;
+        ref.lodf = v.lodf; ref.lodf_lo = v.lodf_lo; ref.n_l = v.n_line;
+    }
+    bb.ref = ref;
     if (e == cudaSuccess) e = launch_base(bb, v.n_part_base, s);
 
     const int n_chunks = (v.n_a + kPlainCH - 1) / kPlainCH;
@@ -254,6 +314,7 @@ extern "C" ibp_status ibp_bound_noalloc(ibp_case *c, const double *box_lo, const
     ca.flow_lo = nullptr; ca.flow_hi = nullptr; ca.partials = part_ctg; ca.err = err;
     ca.wait_ns = 0;
     ca.warps_per_tile = kConsumerWarps;
+    ca.ref = ref;
     if (e == cudaSuccess && n_tiles > 0) {
         const int grid = std::min(v.num_sms, n_tiles);
         k_ctg_plain<kPlainBL, kPlainBK><<<grid, 256, 0, s>>>(ca, v.phi_a, v.n_a_pad, rbus);

@@ -32,6 +32,11 @@ def test_reference_line():
     assert d["steps"] == 2 and d["warmup"] == 1 and d["n_gpus"] == 1
     assert d["value"] > 0 and d["ms_per_step"] == d["value"]
     assert d["config"]["workload"].startswith("mesh118: 118 buses")
+    # the same config object as the GPU arm prints for this workload
+    sys.path.insert(0, ROOT)
+    import bench
+    from gen import make_config
+    assert d["config"] == bench.bench_config(make_config(1), 1, 1)
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1
     assert "contingencies" in cb["sample"]
@@ -43,3 +48,24 @@ def test_reference_other_ranks_print_nothing():
     r = _run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
     assert r.returncode == 0, r.stderr[-2000:]
     assert r.stdout.strip() == ""
+
+
+def test_stored_traffic_is_tied_to_the_kernel_sources():
+    """A stored DRAM-traffic figure is reported only for the kernel sources it
+    was measured on; after any change to them the bench reports null."""
+    sys.path.insert(0, ROOT)
+    import bench
+    sha = bench.kernel_sources_sha()
+    assert len(sha) == 16
+    key = (3, 0, True, True)
+    saved = dict(bench.MEASURED_TRAFFIC)
+    try:
+        bench.MEASURED_TRAFFIC[key] = (1.0e9, sha)
+        assert bench.measured_traffic(key) == (1.0e9, f"ncu capture of kernel sources {sha}")
+        bench.MEASURED_TRAFFIC[key] = (1.0e9, "0" * 16)
+        value, note = bench.measured_traffic(key)
+        assert value is None and note.startswith("stale")
+        assert bench.measured_traffic((9, 9, False, False))[0] is None
+    finally:
+        bench.MEASURED_TRAFFIC.clear()
+        bench.MEASURED_TRAFFIC.update(saved)

@@ -1,18 +1,26 @@
 """GPU vs oracle parity of the certified bound (calls go through the C ABI).
 
 Tolerances (derived from the outward-rounding error analysis of the kernels):
-* soundness: the GPU interval must contain the oracle's, up to the FP64
-  difference between the two independent sensitivity builds, 1e-9 of the
-  operand scale;
+* FP64 allowance: the library builds its own FP64 sensitivities (Cholesky on
+  the GPU), the oracle its own (LU on the host).  Two independent FP64 builds
+  moved obj_hi by at most 1.8e-13 of its hi-side terms and obj_lo by 1.3e-14
+  of its lo-side terms on the 2000-bus workload (LU against Cholesky, both on
+  the host; ``tests/test_oracle_fp64_builds.py`` keeps that measurement).  The
+  tests allow F64 = 1e-10 of each side's own terms: for obj_hi the terms obj_hi
+  is made of (|C_hi| + |G_lo| + z_inj s_inj,lo + z_f (s_fb,lo + s_fc,lo)), for
+  obj_lo those of obj_lo;
+* soundness: the GPU interval must contain the oracle's up to that allowance;
 * objective: |gpu - oracle| <= 1e-5 |oracle| at both ends, and <= obj_err
-  (the GPU's own error bound) plus the same FP64 allowance;
-* flows: |gpu - oracle| <= 1e-5 s_kl at both ends, where
+  (the GPU's own error bound), each plus the same FP64 allowance;
+* flows: each checked pair's interval [lo, hi] is compared at both ends with
+  1e-5 of its magnitude max(|lo|, |hi|) where the FP32 operands do not cancel
+  (s_kl <= 8 max(|lo|, |hi|)), else with 1e-5 s_kl, where
   s_kl = S_l + |L_lk| S_k with S_x = sum_b |Phi[x,b]| (|c_b| + r_b) is the
   magnitude of the FP32 operands combined for the pair (a centre or a
   post-outage flow that cancels to ~0 keeps an FP32-sized error relative to
-  these operands), plus an absolute
-  floor of 1e-12 max s_kl for lines whose exact flow is identically zero
-  (both FP64 builds leave noise of that size there).
+  these operands), plus an absolute floor of 1e-12 max s_kl for lines whose
+  exact flow is identically zero (both FP64 builds leave noise of that size
+  there).
 """
 import numpy as np
 import pytest
@@ -42,26 +50,53 @@ def _sens(key, case):
     return _SENS[key]
 
 
-def _obj_scale(ref):
-    C = ref.terms["costs"]
-    z = np.abs(C).sum(axis=1)
-    return z + 1e4 * (ref.terms["inj"][1]) + 1e3 * (ref.terms["fb"][1] + ref.terms["fc"][1])
+F64 = 1e-10   # FP64 build allowance, relative to each side's own terms
+
+
+def side_scales(ref):
+    """The terms each end of the objective is made of, in absolute value:
+    obj_hi = C_hi - G_lo - z_inj s_inj,lo - z_f (s_fb,lo + s_fc,lo) and
+    obj_lo = C_lo - G_hi - z_inj s_inj,hi - z_f (s_fb,hi + s_fc,hi)."""
+    C = np.atleast_2d(ref.terms["costs"])
+    zi, zf = ref.terms["zeta"]
+    hi_s = (np.abs(C[:, 1]) + np.abs(C[:, 2]) + zi * ref.terms["inj"][0]
+            + zf * (ref.terms["fb"][0] + ref.terms["fc"][0]))
+    lo_s = (np.abs(C[:, 0]) + np.abs(C[:, 3]) + zi * ref.terms["inj"][1]
+            + zf * (ref.terms["fb"][1] + ref.terms["fc"][1]))
+    return hi_s, lo_s
 
 
 def check_objective(lo, hi, err, ref, rel=1e-5, rel_scale=None):
-    """rel_scale (default |oracle value|) is what the 1e-5 relative bar is
-    taken of; small networks whose objective cancels far below its cost terms
-    pass the cost scale instead."""
-    scale = _obj_scale(ref)
-    d = 1e-9 * scale
+    """Soundness, 1e-5 agreement and error-bound coverage of both ends.
+
+    rel_scale (default |oracle value|) is what the 1e-5 relative bar is taken
+    of; the small synthetic networks whose objective cancels to about a tenth
+    of its cost terms pass the cost scale instead.  Returns the measured
+    relative deviations ((hi - ref.hi) / |ref.hi|, (lo - ref.lo) / |ref.lo|)."""
+    hi_s, lo_s = side_scales(ref)
+    d_hi, d_lo = F64 * hi_s, F64 * lo_s
     rs_hi = np.abs(ref.hi) if rel_scale is None else rel_scale
     rs_lo = np.abs(ref.lo) if rel_scale is None else np.maximum(rel_scale, np.abs(ref.lo))
-    assert np.all(hi >= ref.hi - d), (hi, ref.hi)
-    assert np.all(lo <= ref.lo + d), (lo, ref.lo)
-    assert np.all(np.abs(hi - ref.hi) <= rel * rs_hi + d), (hi, ref.hi)
-    assert np.all(np.abs(lo - ref.lo) <= rel * rs_lo + d), (lo, ref.lo)
-    assert np.all(np.abs(hi - ref.hi) <= err[:, 0] + d), (hi - ref.hi, err[:, 0])
-    assert np.all(np.abs(lo - ref.lo) <= err[:, 1] + d), (lo - ref.lo, err[:, 1])
+    assert np.all(hi >= ref.hi - d_hi), ("unsound hi", hi, ref.hi, d_hi)
+    assert np.all(lo <= ref.lo + d_lo), ("unsound lo", lo, ref.lo, d_lo)
+    assert np.all(np.abs(hi - ref.hi) <= rel * rs_hi + d_hi), (hi, ref.hi)
+    assert np.all(np.abs(lo - ref.lo) <= rel * rs_lo + d_lo), (lo, ref.lo)
+    assert np.all(np.abs(hi - ref.hi) <= err[:, 0] + d_hi), (hi - ref.hi, err[:, 0])
+    assert np.all(np.abs(lo - ref.lo) <= err[:, 1] + d_lo), (lo - ref.lo, err[:, 1])
+    return (hi - ref.hi) / np.abs(ref.hi), (lo - ref.lo) / np.abs(ref.lo)
+
+
+def bound_rows(ref, j):
+    """Box j of an oracle Bound, as a one-box Bound."""
+    terms = {}
+    for k, v in ref.terms.items():
+        if k == "zeta":
+            terms[k] = v
+        elif isinstance(v, tuple):
+            terms[k] = tuple(t[j:j + 1] for t in v)
+        else:
+            terms[k] = v[j:j + 1]
+    return O.Bound(lo=ref.lo[j:j + 1], hi=ref.hi[j:j + 1], terms=terms)
 
 
 def flow_scale(case, sens, cb, rb, pk, pl):
@@ -79,7 +114,13 @@ def _worst(excess, pk, pl):
     return f"worst excess {excess[i]:.3e} at box {i[0]} k={pk[i[1]]} l={pl[i[1]]}"
 
 
+Q_CANCEL = 8.0  # s_kl / max(|lo|, |hi|) above which a pair counts as cancelling
+
+
 def check_flows(case, sens, lo_box, hi_box, flo, fhi, pk, pl, rel=1e-5):
+    """Flow intervals of the sampled pairs against the oracle (bars in the
+    module docstring).  Returns (worst s_kl / max(|lo|, |hi|), share of pairs
+    checked against the operand scale)."""
     cb, rb = O.bus_box(case, lo_box, hi_box)
     cent, rad = O.ctg_flows(case, sens, cb, rb, pk, pl)
     s = flow_scale(case, sens, cb, rb, pk, pl)
@@ -88,16 +129,26 @@ def check_flows(case, sens, lo_box, hi_box, flo, fhi, pk, pl, rel=1e-5):
     floor = 1e-12 * s.max()
     g_lo = flo[:, pk, pl]
     g_hi = fhi[:, pk, pl]
+    mag = np.abs(cent) + rad
+    ratio = s / np.maximum(mag, 1e-300)
+    cancel = ratio > Q_CANCEL
+    scale = np.where(cancel, s, mag)
     d = 1e-9 * s + floor
     assert np.all(g_lo <= cent - rad + d), _worst(g_lo - (cent - rad) - d, pk, pl)
     assert np.all(g_hi >= cent + rad - d), _worst((cent + rad) - g_hi - d, pk, pl)
-    assert np.all(np.abs(g_lo - (cent - rad)) <= rel * s + floor), \
-        _worst(np.abs(g_lo - (cent - rad)) - rel * s - floor, pk, pl)
-    assert np.all(np.abs(g_hi - (cent + rad)) <= rel * s + floor), \
-        _worst(np.abs(g_hi - (cent + rad)) - rel * s - floor, pk, pl)
+    assert np.all(np.abs(g_lo - (cent - rad)) <= rel * scale + floor), \
+        _worst(np.abs(g_lo - (cent - rad)) - rel * scale - floor, pk, pl)
+    assert np.all(np.abs(g_hi - (cent + rad)) <= rel * scale + floor), \
+        _worst(np.abs(g_hi - (cent + rad)) - rel * scale - floor, pk, pl)
     # the outaged line is exactly [0, 0]
     out = pl == case.ctg_line[pk]
     assert np.all(g_lo[:, out] == 0) and np.all(g_hi[:, out] == 0)
+    live = ~np.broadcast_to(out, ratio.shape) & (mag > floor)
+    worst = float(ratio[live].max()) if live.any() else 0.0
+    share = float(cancel[live].mean()) if live.any() else 0.0
+    print(f"flows: {pk.size} pairs x {ratio.shape[0]} boxes, worst s/max(|lo|,|hi|) = {worst:.3g}, "
+          f"{100 * share:.2f}% checked against the operand scale")
+    return worst, share
 
 
 @pytest.mark.parametrize("cfg", [0, 1, 2])
@@ -157,10 +208,7 @@ def test_point_box_and_sub_boxes(P):
     ref = O.bound(case, sens, lo=slo, hi=shi)
     for j in range(slo.shape[0]):
         lo, hi, err = gpu.bound(slo[j:j + 1], shi[j:j + 1])
-        sub = O.Bound(lo=ref.lo[j:j + 1], hi=ref.hi[j:j + 1],
-                      terms={k: (v[j:j + 1] if not isinstance(v, tuple) else tuple(t[j:j + 1] for t in v))
-                             for k, v in ref.terms.items()})
-        check_objective(lo, hi, err, sub)
+        check_objective(lo, hi, err, bound_rows(ref, j))
 
 
 def test_edge_cases(P):

@@ -390,3 +390,58 @@ def test_hand_adjoint_matches_finite_differences(cases, cfg):
             fd = (fp - fm) / (2 * h)
             scale = max(abs(fd), abs(g[0, d]), 1e-3 * np.abs(g).max())
             assert abs(fd - g[0, d]) <= 1e-4 * scale, (which, d, fd, g[0, d])
+
+
+def _rating_fd(c, s, lo, hi, field, l, h):
+    """Central difference of the oracle's hi in one line's rating.  field is
+    "rating" (base ratings; contingency ratings follow when the case has none
+    of its own) or "rating_ctg"."""
+    import dataclasses
+    vals = []
+    for sgn in (1.0, -1.0):
+        v = getattr(c, field).copy()
+        v[l] += sgn * h
+        cc = dataclasses.replace(c, **{field: v})
+        vals.append(O.bound(cc, s, lo=lo[None], hi=hi[None]).hi[0])
+    return (vals[0] - vals[1]) / (2 * h)
+
+
+@pytest.mark.parametrize("cfg", [0, 1])
+def test_rating_gradient_matches_finite_differences(cases, cfg):
+    """The rating part of the hand adjoint against central differences of the
+    oracle's own upper bound, in the shared rating vector, in the base ratings
+    alone and in separate contingency ratings.  Each checked line sits at
+    least 50 steps from every kink of its violation terms, so the difference
+    is exact up to rounding; lines with active pairs are among those checked."""
+    import dataclasses
+    c = cases(cfg)
+    s = O.sensitivities(c)
+    rng = np.random.default_rng(31 + cfg)
+    lo0, hi0 = c.box_lo[0], c.box_hi[0]
+    a = lo0 + 0.4 * rng.random(c.n_dev) * (hi0 - lo0)
+    b = hi0 - 0.4 * rng.random(c.n_dev) * (hi0 - lo0)
+    cb, rb = O.bus_box(c, a[None], b[None])
+    cent, rad = O.all_ctg_flows(c, s, cb, rb)
+    fb, fr = (cb @ s.phi.T)[0], (rb @ np.abs(s.phi).T)[0]
+    # the distance of each line's decisions from their kinks
+    kc = np.abs(np.abs(cent[0]) - rad[0] - c.rating[None, :]).min(axis=0)
+    kb = np.abs(np.abs(fb) - fr - c.rating)
+    dist = np.minimum(kc, kb)
+    g_base, g_ctg = O.grad_hi_ratings(c, s, a[None], b[None])
+    _, _, g_shared = O.grad_hi(c, s, lo=a[None], hi=b[None])
+    np.testing.assert_array_equal(g_shared, g_base + g_ctg)
+    active = np.flatnonzero((g_base[0] + g_ctg[0]) > 0)
+    assert active.size > 0, "the sub-box has no active pair"
+    h = 1e-3
+    ok = np.flatnonzero(dist > 50 * h)
+    lines = np.union1d(np.intersect1d(active, ok)[:6], ok[:3])
+    assert np.intersect1d(lines, active).size > 0
+    sep = dataclasses.replace(c, rating_ctg=c.rating.copy())
+    for l in lines:
+        fd = _rating_fd(c, s, a, b, "rating", l, h)
+        assert abs(fd - g_shared[0, l]) <= 1e-6 * max(1.0, abs(fd)), (l, fd, g_shared[0, l])
+        # with separate contingency ratings, each vector has its own part
+        fd_b = _rating_fd(sep, s, a, b, "rating", l, h)
+        fd_c = _rating_fd(sep, s, a, b, "rating_ctg", l, h)
+        assert abs(fd_b - g_base[0, l]) <= 1e-6 * max(1.0, abs(fd_b)), (l, fd_b, g_base[0, l])
+        assert abs(fd_c - g_ctg[0, l]) <= 1e-6 * max(1.0, abs(fd_c)), (l, fd_c, g_ctg[0, l])
