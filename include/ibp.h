@@ -153,6 +153,45 @@ ibp_status ibp_bound_backward(ibp_case *c, int32_t n_box, const double *box_lo,
                               int32_t ptr_mode, void *cuda_stream);
 
 /*
+ * Adjoint of obj_lo (not certified), with the arguments and layouts of
+ * ibp_bound_backward: grad_obj_lo [n_box] = d loss / d obj_lo.  obj_lo =
+ * C(pd_lo) - G(pg_hi) - zeta_inj s_inj,hi - zeta_f (sum s_fb,hi + sum s_fc,hi)
+ * (eq. (penalized-objective) under eq. (IBP)) takes the upper violation bounds
+ * s_hi = max(|c| + r - rating, 0); the derivative uses the pairs whose s_hi
+ * is > 0 in the forward pass:
+ *   d obj_lo / d c_b = -zeta_f sum sgn(c_kl) H_k[l,b],
+ *   d obj_lo / d r_b = -zeta_f sum |H_k[l,b]|,
+ *   grad_rating[l] = zeta_f * grad_obj_lo * (the line's active base flow plus
+ *     its active contingency pairs), for base and contingency ratings moving
+ *     together,
+ * plus the imbalance and cost terms, chained to the box endpoints.  Those
+ * pairs are most pairs of a wide box: the forward pass records them in a list
+ * of up to 64M entries per call (1 GiB; IBP_ENOMEM beyond it, reported by the
+ * call in host mode and by ibp_case_sync in device mode), and the radius pass
+ * costs O(pairs x active buses), like the forward kernel without its tiling.
+ * Valid away from kinks.
+ */
+ibp_status ibp_bound_backward_lo(ibp_case *c, int32_t n_box, const double *box_lo,
+                                 const double *box_hi, const double *grad_obj_lo,
+                                 double *grad_lo, double *grad_hi, double *grad_rating,
+                                 int32_t ptr_mode, void *cuda_stream);
+
+/*
+ * Replace the case's line ratings (eqs. (slack-sfb), (slack-Sc)): rating
+ * [n_line] (base, MW) and rating_ctg [n_line] or NULL (then the contingency
+ * ratings equal the new base ratings).  ptr_mode 0: host pointers, validated
+ * on the host (finite, >= 0; IBP_EINVAL leaves the ratings unchanged), the
+ * call returns when the device copies are updated.  ptr_mode 1: device
+ * pointers, enqueued on cuda_stream; a bad entry leaves every rating
+ * unchanged and makes the next ibp_case_sync return IBP_EINVAL.  Later calls
+ * on the same stream use the new ratings; the sensitivities are unchanged.
+ * The paper treats ratings as data; this lets a caller differentiate through
+ * them (torch.autograd.Function of the binding).
+ */
+ibp_status ibp_case_set_ratings(ibp_case *c, const double *rating, const double *rating_ctg,
+                                int32_t ptr_mode, void *cuda_stream);
+
+/*
  * Bounds of many cases of uneven size in one persistent launch of the
  * contingency kernel (device pointers only).  For case i:
  *   box_lo[i], box_hi[i] [n_box[i]][n_dev_i], obj_lo[i], obj_hi[i], obj_err[i]

@@ -21,6 +21,7 @@ Every function names the passage of the paper it follows:
 * ``bound``               eq. (penalized-objective) / appendix eq. (ibp_f) under eq. (IBP)
 * ``grad_hi``             hand-derived adjoint of the upper bound (the paper has none)
 * ``grad_hi_ratings``     its rating part, split into base and contingency ratings
+* ``grad_lo``             hand-derived adjoint of the lower bound (the paper has none)
 * ``paper_mode_flows``    IBP applied literally to eq. (ctg flow matrix form)
 * ``screen_lines``        lines whose paper-mode contingency interval can exceed the rating
 * ``paper_ctg_terms``     eq. (slack-Sc) sums over the paper-mode intervals (``bound(mode="paper")``)
@@ -495,6 +496,60 @@ def grad_hi(case, sens: Sensitivities, lo=None, hi=None, nthreads=None):
             g_lo[j, i] -= _pwl_slope(a, b, lo[j, i])
         for d, (a, b) in enumerate(_segments(case.load_nseg, case.load_slope, case.load_bkpt)):
             g_hi[j, ng + d] += _pwl_slope(a, b, hi[j, ng + d])
+    return g_lo, g_hi, g_rating
+
+
+def grad_lo(case, sens: Sensitivities, lo=None, hi=None, nthreads=None):
+    """Hand adjoint of the lower bound: d lo / d box_lo, d lo / d box_hi, d lo / d rating.
+
+    lo = C_lo - G_hi - z_inj S_inj,hi - z_f (S_fb,hi + S_fc,hi) with
+    s_hi = max(|c| + r - rating, 0) for every base line and (k, l) pair (the
+    upper end of |x| over [c - r, c + r], eqs. (slack-sfb), (slack-Sc) under
+    eq. (IBP)) and S_inj,hi = |sum c| + sum r (eq. (slack-sinj), reading C5).
+    With A = {pairs: |c| + r - rating > 0}:
+      d lo/dc_b = -z_f sum_A sgn(c) H[b] - z_inj sgn(sum c),
+      d lo/dr_b = -z_f sum_A |H[b]| - z_inj,
+      d lo/d rating_l = +z_f #{pairs of A on line l} (shared base and
+        contingency rating; None for cases too large to form every flow),
+    then the chain rule through c = N mu, r = |N| sigma; the load values enter
+    at box_lo, the generator costs at box_hi.  Valid away from kinks.
+    """
+    lo = case.box_lo if lo is None else np.atleast_2d(lo)
+    hi = case.box_hi if hi is None else np.atleast_2d(hi)
+    c, r = bus_box(case, lo, hi)
+    nbox = lo.shape[0]
+    phi = sens.phi
+    rating_c = case.rating if case.rating_ctg is None else case.rating_ctg
+    cent, rad = all_ctg_flows(case, sens, c, r, nthreads)          # [nbox, n_c, n_l]
+    act_c = (np.abs(cent) + rad - rating_c[None, None, :]) > 0
+    H_sum_c = np.zeros((nbox, case.n_bus))
+    H_sum_r = np.zeros((nbox, case.n_bus))
+    for k in range(case.n_ctg):
+        kl = case.ctg_line[k]
+        Hk = phi + np.outer(sens.lodf[:, k], phi[kl])               # [n_l, n_b]
+        for j in range(nbox):
+            a = act_c[j, k]
+            H_sum_c[j] += (np.sign(cent[j, k]) * a) @ Hk
+            H_sum_r[j] += a.astype(float) @ np.abs(Hk)
+    fc = c @ phi.T
+    fr = r @ np.abs(phi).T
+    act_b = (np.abs(fc) + fr - case.rating[None, :]) > 0
+    gc_b = (np.sign(fc) * act_b) @ phi
+    gr_b = act_b.astype(float) @ np.abs(phi)
+    tot_c = c.sum(axis=1)
+    dc = -case.zeta_f * (H_sum_c + gc_b) - case.zeta_inj * np.sign(tot_c)[:, None]
+    dr = -case.zeta_f * (H_sum_r + gr_b) - case.zeta_inj
+    g_rating = case.zeta_f * (act_c.sum(axis=1) + act_b)
+    ng = case.n_gen
+    bus = np.concatenate([case.gen_bus, case.load_bus])
+    sgn = np.concatenate([np.ones(ng), -np.ones(case.n_load)])
+    g_lo = 0.5 * sgn[None, :] * dc[:, bus] - 0.5 * dr[:, bus]
+    g_hi = 0.5 * sgn[None, :] * dc[:, bus] + 0.5 * dr[:, bus]
+    for j in range(nbox):
+        for i, (a, b) in enumerate(_segments(case.gen_nseg, case.gen_slope, case.gen_bkpt)):
+            g_hi[j, i] -= _pwl_slope(a, b, hi[j, i])
+        for d, (a, b) in enumerate(_segments(case.load_nseg, case.load_slope, case.load_bkpt)):
+            g_lo[j, ng + d] += _pwl_slope(a, b, lo[j, ng + d])
     return g_lo, g_hi, g_rating
 
 

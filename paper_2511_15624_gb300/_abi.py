@@ -27,7 +27,8 @@ EXPORTED = (
     "ibp_case_sync", "ibp_case_info", "ibp_case_set_variant", "ibp_kernel_variants",
     "ibp_case_set_timing", "ibp_case_last_timing", "ibp_selftest_wait_timeout", "ibp_last_error",
     "ibp_status_string", "ibp_bound_noalloc", "ibp_case_set_screen", "ibp_case_last_live",
-    "ibp_case_set_reduction", "ibp_case_set_refine", "ibp_case_reduction", "ibp_bound_paper", "ibp_set_alloc_limit",
+    "ibp_case_set_reduction", "ibp_case_set_refine", "ibp_case_reduction", "ibp_bound_paper",
+    "ibp_set_alloc_limit", "ibp_bound_backward_lo", "ibp_case_set_ratings",
 )
 
 
@@ -72,6 +73,10 @@ def lib():
         L.ibp_bound_paper.restype = ctypes.c_int
         L.ibp_bound_backward.argtypes = [P, I32, P, P, P, P, P, P, I32, P]
         L.ibp_bound_backward.restype = ctypes.c_int
+        L.ibp_bound_backward_lo.argtypes = [P, I32, P, P, P, P, P, P, I32, P]
+        L.ibp_bound_backward_lo.restype = ctypes.c_int
+        L.ibp_case_set_ratings.argtypes = [P, P, P, I32, P]
+        L.ibp_case_set_ratings.restype = ctypes.c_int
         L.ibp_bound_multi.argtypes = [I32, P, P, P, P, P, P, P, P]
         L.ibp_bound_multi.restype = ctypes.c_int
         L.ibp_bound_noalloc.argtypes = [P, P, P, P, P, P, P]
@@ -190,6 +195,18 @@ def ibp_bound_backward(handle, n_box, box_lo, box_hi, grad_obj_hi, grad_lo, grad
                                   _ptr(grad_obj_hi), _ptr(grad_lo), _ptr(grad_hi),
                                   _ptr(grad_rating), int(ptr_mode), stream)
     _check(st)
+
+
+def ibp_bound_backward_lo(handle, n_box, box_lo, box_hi, grad_obj_lo, grad_lo, grad_hi,
+                          grad_rating=None, ptr_mode=0, stream=None):
+    _check(lib().ibp_bound_backward_lo(ctypes.c_void_p(handle), int(n_box), _ptr(box_lo), _ptr(box_hi),
+                                       _ptr(grad_obj_lo), _ptr(grad_lo), _ptr(grad_hi),
+                                       _ptr(grad_rating), int(ptr_mode), stream))
+
+
+def ibp_case_set_ratings(handle, rating, rating_ctg=None, ptr_mode=0, stream=None):
+    _check(lib().ibp_case_set_ratings(ctypes.c_void_p(handle), _ptr(rating), _ptr(rating_ctg),
+                                      int(ptr_mode), stream))
 
 
 def ibp_bound_multi(handles, n_box, box_lo, box_hi, obj_lo, obj_hi, obj_err, stream=None):

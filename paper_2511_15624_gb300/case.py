@@ -120,8 +120,12 @@ class Case:
         return olo, ohi, oerr
 
     # ------------------------------------------------------------ adjoint
-    def backward(self, lo, hi, grad_obj_hi, want_rating: bool = False, stream=None):
-        """d loss / d box_lo, d box_hi (and d loss / d rating_ctg) of obj_hi."""
+    def backward(self, lo, hi, grad_obj_hi, want_rating: bool = False, stream=None, side: str = "hi"):
+        """d loss / d box_lo, d box_hi (and d loss / d rating, base and
+        contingency ratings moving together) of obj_hi (side "hi",
+        ``ibp_bound_backward``) or of obj_lo (side "lo",
+        ``ibp_bound_backward_lo``); grad_obj_hi is d loss / d obj of that side."""
+        fn = _abi.ibp_bound_backward if side == "hi" else _abi.ibp_bound_backward_lo
         if _abi._is_cuda_tensor(lo):
             import torch
             nb = int(lo.shape[0])
@@ -130,8 +134,7 @@ class Case:
             ghi = torch.empty_like(glo)
             gr = torch.empty((nb, self.n_line), dtype=torch.float64, device=lo.device) if want_rating else None
             s = stream if stream is not None else torch.cuda.current_stream(lo.device).cuda_stream
-            _abi.ibp_bound_backward(self._h, nb, lo.contiguous(), hi.contiguous(), g, glo, ghi, gr,
-                                    ptr_mode=1, stream=s)
+            fn(self._h, nb, lo.contiguous(), hi.contiguous(), g, glo, ghi, gr, ptr_mode=1, stream=s)
             return (glo, ghi) + ((gr,) if want_rating else ())
         lo = np.ascontiguousarray(np.atleast_2d(lo), np.float64)
         hi = np.ascontiguousarray(np.atleast_2d(hi), np.float64)
@@ -140,8 +143,24 @@ class Case:
         glo = np.empty((nb, self.n_dev))
         ghi = np.empty((nb, self.n_dev))
         gr = np.empty((nb, self.n_line)) if want_rating else None
-        _abi.ibp_bound_backward(self._h, nb, lo, hi, g, glo, ghi, gr, ptr_mode=0, stream=None)
+        fn(self._h, nb, lo, hi, g, glo, ghi, gr, ptr_mode=0, stream=None)
         return (glo, ghi) + ((gr,) if want_rating else ())
+
+    def set_ratings(self, rating, rating_ctg=None, stream=None):
+        """Replace the line ratings (numpy: synchronous; CUDA tensor: enqueued
+        on the stream).  rating_ctg None: contingency ratings = rating."""
+        if _abi._is_cuda_tensor(rating):
+            import torch
+            r = rating.detach().contiguous().to(torch.float64)
+            rc = None if rating_ctg is None else rating_ctg.detach().contiguous().to(torch.float64)
+            s = stream if stream is not None else torch.cuda.current_stream(r.device).cuda_stream
+            _abi.ibp_case_set_ratings(self._h, r, rc, ptr_mode=1, stream=s)
+            return
+        r = np.ascontiguousarray(rating, np.float64)
+        rc = None if rating_ctg is None else np.ascontiguousarray(rating_ctg, np.float64)
+        if r.shape != (self.n_line,):
+            raise ValueError(f"rating must have shape [{self.n_line}]")
+        _abi.ibp_case_set_ratings(self._h, r, rc, ptr_mode=0, stream=None)
 
     def sync(self):
         _abi.ibp_case_sync(self._h)

@@ -78,6 +78,15 @@ __device__ __forceinline__ bool pair_epilogue(const CtgArgs &a, int box, int l, 
                 refine = a.ref.phi64 != nullptr;
             }
         }
+        if (a.act_list_lo && shi > 0.0f) {
+            // upper violation bound positive: obj_lo's active set
+            const int idx = atomicAdd(&a.act_count_lo[box], 1);
+            if (idx < a.act_cap_lo)
+                a.act_list_lo[(size_t)box * a.act_cap_lo + idx] =
+                    make_int4(l, kl, __float_as_int(Lt), __float_as_int(c > 0.0f ? 1.0f : -1.0f));
+            else
+                atomicOr(a.err, kErrOverflow);
+        }
         if (a.act_list && slo > 0.0f) {
             // certified active: record for the adjoint
             const int idx = atomicAdd(&a.act_count[box], 1);

@@ -139,12 +139,16 @@ struct ibp_case {
     DevBuf<double> part_base, part_ctg, part_stage;
     DevBuf<float> flows;
     DevBuf<int> err;
+    DevBuf<int> rating_flag;  // sticky: the last ibp_case_set_ratings found a bad entry
     DevBuf<int> live_flag, live, n_live;  // line screen
     DevBuf<float> rcls, rcls_t;           // class radii [box][n_r_pad], [n_r_pad][box_pad]
-    // adjoint workspace
+    // adjoint workspace (obj_hi's active pairs; obj_lo's in the _lo buffers)
     int bwd_cap_box = 0, act_cap = 0;
     DevBuf<int> act_count, cnt;
     DevBuf<int4> act_list;
+    int bwd_lo_cap_box = 0, act_cap_lo = 0;
+    DevBuf<int> act_count_lo;
+    DevBuf<int4> act_list_lo;
     DevBuf<double> W, dc, dr, grads;
     int n_part_base = 0;
 
@@ -176,10 +180,11 @@ struct ibp_case {
             box_lo.free(); box_hi.free();
             obj.free(); cbus.free(); cbus2.free(); rbus.free(); cabs.free(); box_consts.free(); bus_part.free(); line_c.free();
             line_e.free(); line_R.free(); part_base.free(); part_ctg.free(); part_stage.free(); flows.free(); err.free();
-            live_flag.free(); live.free(); n_live.free(); is_bridge.free(); cls_ptr.free();
+            live_flag.free(); live.free(); n_live.free(); is_bridge.free(); cls_ptr.free(); rating_flag.free();
             cls_col.free(); phi_r.free(); phi_kr.free(); rcls.free(); rcls_t.free(); nb_list.free();
             nb_count.free(); phi_nb.free();
             dev_col.free(); act_count.free(); cnt.free(); act_list.free(); W.free(); dc.free(); dr.free();
+            act_count_lo.free(); act_list_lo.free();
             grads.free();
         }
     }
@@ -890,7 +895,8 @@ static ibp_status wait_case(ibp_case *c) {
 // ----------------------------------------------------------------- bound
 static ibp_status enqueue_bound(ibp_case *c, int n_box, const double *lo, const double *hi,
                                 double *olo, double *ohi, double *oerr, float *flo, float *fhi,
-                                cudaStream_t s, bool record = false, bool paper = false) {
+                                cudaStream_t s, bool record = false, bool paper = false,
+                                bool record_lo = false) {
     ibp_status st = ensure_workspace(c, n_box);
     if (st != IBP_OK) return st;
     const CtgVariant *v = pick_variant(c, n_box);
@@ -956,6 +962,11 @@ static ibp_status enqueue_bound(ibp_case *c, int n_box, const double *lo, const 
         bb.act_list = c->act_list.p;
         bb.act_cap = c->act_cap;
     }
+    if (record_lo) {
+        bb.act_count_lo = c->act_count_lo.p;
+        bb.act_list_lo = c->act_list_lo.p;
+        bb.act_cap_lo = c->act_cap_lo;
+    }
     bb.ref = ref_args(c);
     CUDA_TRY(launch_base(bb, c->n_part_base, s));
     if (c->timing) CUDA_TRY(cudaEventRecord(c->ev[2], s));
@@ -1015,6 +1026,11 @@ static ibp_status enqueue_bound(ibp_case *c, int n_box, const double *lo, const 
         ca.act_count = c->act_count.p;
         ca.act_list = c->act_list.p;
         ca.act_cap = c->act_cap;
+    }
+    if (record_lo) {
+        ca.act_count_lo = c->act_count_lo.p;
+        ca.act_list_lo = c->act_list_lo.p;
+        ca.act_cap_lo = c->act_cap_lo;
     }
     if (screened) {
         ca.live = c->live.p;
@@ -1097,9 +1113,13 @@ static ibp_status enqueue_bound(ibp_case *c, int n_box, const double *lo, const 
 // Reads the error word through the case's private stream (no wait on other
 // streams); the caller has waited for the work that writes it.
 static ibp_status read_err_word(ibp_case *c) {
-    int e = 0;
+    int e = 0, rf = 0;
     CUDA_TRY(cudaMemcpyAsync(&e, c->err.p, sizeof(int), cudaMemcpyDeviceToHost, c->side));
+    if (c->rating_flag.p)
+        CUDA_TRY(cudaMemcpyAsync(&rf, c->rating_flag.p, sizeof(int), cudaMemcpyDeviceToHost, c->side));
     CUDA_TRY(cudaStreamSynchronize(c->side));
+    if (rf) return fail(IBP_EINVAL, "ibp_case_set_ratings was given a negative or non-finite rating "
+                                    "(the ratings were left unchanged)");
     if (e & kErrTimeout) return fail(IBP_ETIMEOUT, "a bounded device wait ran out");
     if (e & kErrBadBox) return fail(IBP_EINVAL, "a box has lo > hi or a non-finite entry");
     if (e & kErrOverflow)
@@ -1210,16 +1230,33 @@ static ibp_status ensure_bwd_workspace(ibp_case *c, int n_box) {
     return IBP_OK;
 }
 
+// obj_lo's active set holds most pairs of a wide box: its list takes up to
+// 64M entries (1 GiB) shared by the boxes of a call
+static ibp_status ensure_bwd_lo_workspace(ibp_case *c, int n_box) {
+    if (n_box <= c->bwd_lo_cap_box) return IBP_OK;
+    const int cap = std::max(n_box, 1);
+    c->bwd_lo_cap_box = 0;
+    const long long pairs = (long long)c->n_ctg * c->n_line + c->n_line;
+    c->act_cap_lo = (int)std::max<long long>(4096, std::min<long long>(pairs, (64ll << 20) / cap));
+    CUDA_TRY(c->act_count_lo.alloc(cap));
+    CUDA_TRY(c->act_list_lo.alloc((size_t)cap * c->act_cap_lo));
+    c->bwd_lo_cap_box = cap;
+    return IBP_OK;
+}
+
+// side 0: adjoint of obj_hi; side 1: of obj_lo.  gobj = d loss / d obj.
 static ibp_status enqueue_backward(ibp_case *c, int n_box, const double *lo, const double *hi,
                                    const double *gobj, double *glo, double *ghi, double *grat,
-                                   cudaStream_t s) {
+                                   cudaStream_t s, int side = 0) {
     ibp_status st = ensure_bwd_workspace(c, n_box);
     if (st != IBP_OK) return st;
-    CUDA_TRY(cudaMemsetAsync(c->act_count.p, 0, n_box * sizeof(int), s));
-    // forward pass with recording of the certified active pairs
+    if (side && (st = ensure_bwd_lo_workspace(c, n_box)) != IBP_OK) return st;
+    int *count = side ? c->act_count_lo.p : c->act_count.p;
+    CUDA_TRY(cudaMemsetAsync(count, 0, n_box * sizeof(int), s));
+    // forward pass with recording of the active pairs of the side
     double *dobj = c->obj.p;
     if ((st = enqueue_bound(c, n_box, lo, hi, dobj, dobj + n_box, dobj + 2 * n_box, nullptr,
-                            nullptr, s, true)) != IBP_OK)
+                            nullptr, s, side == 0, false, side == 1)) != IBP_OK)
         return st;
     CUDA_TRY(cudaMemsetAsync(c->W.p, 0, (size_t)n_box * c->n_line * sizeof(double), s));
     CUDA_TRY(cudaMemsetAsync(c->cnt.p, 0, (size_t)n_box * c->n_line * sizeof(int), s));
@@ -1227,8 +1264,10 @@ static ibp_status enqueue_backward(ibp_case *c, int n_box, const double *lo, con
     CUDA_TRY(cudaMemsetAsync(c->dc.p, 0, (size_t)n_box * c->n_a_pad * sizeof(double), s));
     BwdArgs b{};
     b.n_l = c->n_line; b.n_a = c->n_a; b.n_a_pad = c->n_a_pad; b.n_dev = c->n_dev; b.n_gen = c->n_gen;
-    b.n_box = n_box; b.act_cap = c->act_cap; b.phi = c->phi_a.p; b.act_count = c->act_count.p;
-    b.act_list = c->act_list.p; b.W = c->W.p; b.cnt = c->cnt.p; b.dc = c->dc.p; b.dr = c->dr.p;
+    b.n_box = n_box; b.side = side;
+    b.act_cap = side ? c->act_cap_lo : c->act_cap; b.phi = c->phi_a.p; b.act_count = count;
+    b.act_list = side ? c->act_list_lo.p : c->act_list.p;
+    b.W = c->W.p; b.cnt = c->cnt.p; b.dc = c->dc.p; b.dr = c->dr.p;
     b.dev_col = c->dev_col.p; b.box_lo = lo; b.box_hi = hi; b.seg_ptr = c->seg_ptr.p;
     b.slope = c->slope.p; b.bkpt = c->bkpt.p; b.zeta_inj = c->zeta_inj; b.zeta_f = c->zeta_f;
     b.grad_obj_hi = gobj; b.grad_lo = glo; b.grad_hi = ghi; b.grad_rating = grat;
@@ -1236,10 +1275,10 @@ static ibp_status enqueue_backward(ibp_case *c, int n_box, const double *lo, con
     return mark_done(c, s);
 }
 
-extern "C" ibp_status ibp_bound_backward(ibp_case *c, int32_t n_box, const double *box_lo,
-                                         const double *box_hi, const double *grad_obj_hi,
-                                         double *grad_lo, double *grad_hi, double *grad_rating,
-                                         int32_t ptr_mode, void *cuda_stream) {
+static ibp_status backward_entry(ibp_case *c, int32_t n_box, const double *box_lo,
+                                 const double *box_hi, const double *grad_obj_hi, double *grad_lo,
+                                 double *grad_hi, double *grad_rating, int32_t ptr_mode,
+                                 void *cuda_stream, int side) {
     if (!c) return fail(IBP_EINVAL, "case is NULL");
     if (n_box < 0) return fail(IBP_EINVAL, "n_box must be >= 0");
     if (n_box > kMaxBoxesPerCall) return fail(IBP_EINVAL, "n_box must be <= %d", kMaxBoxesPerCall);
@@ -1251,7 +1290,7 @@ extern "C" ibp_status ibp_bound_backward(ibp_case *c, int32_t n_box, const doubl
         ibp_status st = check_boxes_host(c, n_box, box_lo, box_hi);
         if (st != IBP_OK) return st;
         for (int j = 0; j < n_box; ++j)
-            if (!is_fin(grad_obj_hi[j])) return fail(IBP_EINVAL, "grad_obj_hi[%d] is not finite", j);
+            if (!is_fin(grad_obj_hi[j])) return fail(IBP_EINVAL, "grad_obj[%d] is not finite", j);
     }
     if (c->device < 0) return fail(IBP_ENOTSUP, "case was created without a device (dry run)");
     DeviceGuard guard(c->device);
@@ -1260,7 +1299,8 @@ extern "C" ibp_status ibp_bound_backward(ibp_case *c, int32_t n_box, const doubl
     ibp_status st = ensure_workspace(c, n_box);
     if (st != IBP_OK) return st;
     if (ptr_mode == 1)
-        return enqueue_backward(c, n_box, box_lo, box_hi, grad_obj_hi, grad_lo, grad_hi, grad_rating, s);
+        return enqueue_backward(c, n_box, box_lo, box_hi, grad_obj_hi, grad_lo, grad_hi, grad_rating, s,
+                                side);
     if ((st = ensure_bwd_workspace(c, n_box)) != IBP_OK) return st;
     const size_t nd = (size_t)n_box * c->n_dev;
     CUDA_TRY(cudaMemcpyAsync(c->box_lo.p, box_lo, nd * sizeof(double), cudaMemcpyHostToDevice, s));
@@ -1271,7 +1311,7 @@ extern "C" ibp_status ibp_bound_backward(ibp_case *c, int32_t n_box, const doubl
     double *dgr = dghi + nd;                 // [n_box][n_line]
     CUDA_TRY(cudaMemcpyAsync(dg, grad_obj_hi, n_box * sizeof(double), cudaMemcpyHostToDevice, s));
     st = enqueue_backward(c, n_box, c->box_lo.p, c->box_hi.p, dg, dglo, dghi,
-                          grad_rating ? dgr : nullptr, s);
+                          grad_rating ? dgr : nullptr, s, side);
     if (st != IBP_OK) return st;
     CUDA_TRY(cudaMemcpyAsync(grad_lo, dglo, nd * sizeof(double), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaMemcpyAsync(grad_hi, dghi, nd * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -1280,6 +1320,89 @@ extern "C" ibp_status ibp_bound_backward(ibp_case *c, int32_t n_box, const doubl
                                  cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     return read_err_word(c);
+}
+
+extern "C" ibp_status ibp_bound_backward(ibp_case *c, int32_t n_box, const double *box_lo,
+                                         const double *box_hi, const double *grad_obj_hi,
+                                         double *grad_lo, double *grad_hi, double *grad_rating,
+                                         int32_t ptr_mode, void *cuda_stream) {
+    return backward_entry(c, n_box, box_lo, box_hi, grad_obj_hi, grad_lo, grad_hi, grad_rating,
+                          ptr_mode, cuda_stream, 0);
+}
+
+extern "C" ibp_status ibp_bound_backward_lo(ibp_case *c, int32_t n_box, const double *box_lo,
+                                            const double *box_hi, const double *grad_obj_lo,
+                                            double *grad_lo, double *grad_hi, double *grad_rating,
+                                            int32_t ptr_mode, void *cuda_stream) {
+    return backward_entry(c, n_box, box_lo, box_hi, grad_obj_lo, grad_lo, grad_hi, grad_rating,
+                          ptr_mode, cuda_stream, 1);
+}
+
+// ---------------------------------------------------------------- ratings
+// New ratings: a check of every entry into a sticky flag, then (only when no
+// entry failed) their directed FP32 copies and FP64 values.
+__global__ void k_check_ratings(int n_l, const double *rating, const double *rating_ctg, int *flag) {
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= n_l) return;
+    const double r = rating[l], rc = rating_ctg ? rating_ctg[l] : r;
+    if (!(r >= 0.0) || !(rc >= 0.0) || !isfinite(r) || !isfinite(rc)) atomicOr(flag, kErrBadRating);
+}
+
+__global__ void k_apply_ratings(int n_l, const double *rating, const double *rating_ctg, float *ru,
+                                float *rd, float *rcu, float *rcd, double *r64, double *rc64,
+                                const int *flag) {
+    const int l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= n_l || *flag) return;
+    const double r = rating[l], rc = rating_ctg ? rating_ctg[l] : r;
+    ru[l] = __double2float_ru(r);
+    rd[l] = __double2float_rd(r);
+    rcu[l] = __double2float_ru(rc);
+    rcd[l] = __double2float_rd(rc);
+    r64[l] = r;
+    rc64[l] = rc;
+}
+
+extern "C" ibp_status ibp_case_set_ratings(ibp_case *c, const double *rating,
+                                           const double *rating_ctg, int32_t ptr_mode,
+                                           void *cuda_stream) {
+    if (!c) return fail(IBP_EINVAL, "case is NULL");
+    if (!rating) return fail(IBP_EINVAL, "rating must not be NULL");
+    if (ptr_mode != 0 && ptr_mode != 1) return fail(IBP_EINVAL, "ptr_mode must be 0 or 1");
+    if (ptr_mode == 0)
+        for (int l = 0; l < c->n_line; ++l) {
+            if (!is_fin(rating[l]) || rating[l] < 0)
+                return fail(IBP_EINVAL, "rating[%d] must be finite and >= 0", l);
+            if (rating_ctg && (!is_fin(rating_ctg[l]) || rating_ctg[l] < 0))
+                return fail(IBP_EINVAL, "rating_ctg[%d] must be finite and >= 0", l);
+        }
+    if (c->device < 0) return fail(IBP_ENOTSUP, "case was created without a device (dry run)");
+    DeviceGuard guard(c->device);
+    if (!guard.ok) return fail(IBP_ECUDA, "cannot select device %d", c->device);
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    const double *r = rating, *rc = rating_ctg;
+    DevBuf<double> tmp;
+    if (ptr_mode == 0) {
+        CUDA_TRY(tmp.alloc((size_t)2 * c->n_line));
+        CUDA_TRY(cudaMemcpyAsync(tmp.p, rating, c->n_line * sizeof(double), cudaMemcpyHostToDevice, s));
+        if (rating_ctg)
+            CUDA_TRY(cudaMemcpyAsync(tmp.p + c->n_line, rating_ctg, c->n_line * sizeof(double),
+                                     cudaMemcpyHostToDevice, s));
+        r = tmp.p;
+        rc = rating_ctg ? tmp.p + c->n_line : nullptr;
+    }
+    if (!c->rating_flag.p) CUDA_TRY(c->rating_flag.alloc(1));
+    CUDA_TRY(cudaMemsetAsync(c->rating_flag.p, 0, sizeof(int), s));
+    const int blocks = (c->n_line + 255) / 256;
+    k_check_ratings<<<blocks, 256, 0, s>>>(c->n_line, r, rc, c->rating_flag.p);
+    CUDA_TRY(cudaGetLastError());
+    k_apply_ratings<<<blocks, 256, 0, s>>>(c->n_line, r, rc, c->rate_up.p, c->rate_dn.p, c->rate_c_up.p,
+                                           c->rate_c_dn.p, c->rate64.p, c->rate_c64.p, c->rating_flag.p);
+    CUDA_TRY(cudaGetLastError());
+    if (ptr_mode == 0) {
+        CUDA_TRY(cudaStreamSynchronize(s));
+        return ok();
+    }
+    return mark_done(c, s);
 }
 
 // ---------------------------------------------------------------- many cases

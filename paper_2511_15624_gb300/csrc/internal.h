@@ -17,6 +17,7 @@ constexpr int kErrTimeout = 1;
 constexpr int kErrBadBox = 2;
 constexpr int kErrOverflow = 4;  // active-pair list of the adjoint ran out of room
 constexpr int kErrBounds = 8;    // an index guard of a checked build (-DIBP_CHECK) failed
+constexpr int kErrBadRating = 16;  // a rating given on the device was negative or not finite
 // values per partial-sum row: sum s_lo, sum s_hi, error of obj_hi, error of obj_lo
 constexpr int kPartVals = 4;
 // sums of the objective assembly per (box, stage-1 block)
@@ -86,6 +87,11 @@ struct BaseArgs {
     int *act_count;
     int4 *act_list;
     int act_cap;
+    // the same for the adjoint of obj_lo: lines whose upper violation bound
+    // s_hi is > 0 (null when not recording)
+    int *act_count_lo;
+    int4 *act_list_lo;
+    int act_cap_lo;
     int *err;
     // bridge lines in closed form (null: off): no contingency of the list
     // moves the flow of a bridge, so its n_c contingency pairs share its base
@@ -116,6 +122,11 @@ struct CtgArgs {
     int *act_count;
     int4 *act_list;
     int act_cap;
+    // the same for the adjoint of obj_lo: pairs whose upper violation bound
+    // s_hi is > 0 (null when not recording)
+    int *act_count_lo;
+    int4 *act_list_lo;
+    int act_cap_lo;
     int part_rows_cap;       // rows the partials buffer holds (index guard of checked builds)
     // line screen (null: all n_l lines): line tile rows index the compacted
     // list live[0 .. *n_live) of lines that can carry a violation
@@ -219,6 +230,8 @@ struct ClsArgs {
 
 struct BwdArgs {
     int n_l, n_a, n_a_pad, n_dev, n_gen, n_box, act_cap;
+    // 0: adjoint of obj_hi (its active set: s_lo > 0); 1: of obj_lo (s_hi > 0)
+    int side;
     const float *phi;          // [n_l][n_a_pad]
     const int *act_count;      // [n_box]
     const int4 *act_list;      // [n_box][act_cap]
@@ -230,7 +243,7 @@ struct BwdArgs {
     const int *seg_ptr;
     const double *slope, *bkpt;
     double zeta_inj, zeta_f;
-    const double *grad_obj_hi; // [n_box]
+    const double *grad_obj_hi; // [n_box]: d loss / d obj (obj_hi or obj_lo, by side)
     double *grad_lo, *grad_hi; // [n_box][n_dev]
     double *grad_rating;       // [n_box][n_l] or null
 };

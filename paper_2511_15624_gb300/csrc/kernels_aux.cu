@@ -204,6 +204,15 @@ __device__ __forceinline__ int base_epilogue(const BaseArgs &a, int l, int j, fl
         a.line_e[(size_t)j * a.n_l + l] = e;
         a.line_R[(size_t)j * a.n_l + l] = R;
     }
+    // obj_lo's active set (upper violation bound positive)
+    if (writer && a.act_list_lo && shi > 0.0f) {
+        const int idx = atomicAdd(&a.act_count_lo[j], 1);
+        if (idx < a.act_cap_lo)
+            a.act_list_lo[(size_t)j * a.act_cap_lo + idx] =
+                make_int4(l, l, __float_as_int(0.0f), __float_as_int(c > 0.0f ? 1.0f : -1.0f));
+        else
+            atomicOr(a.err, kErrOverflow);
+    }
     // the adjoint's active set: certified by the FP32 bound
     if (writer && a.act_list && slo_f > 0.0f) {
         const int idx = atomicAdd(&a.act_count[j], 1);
@@ -249,6 +258,15 @@ __device__ __forceinline__ int base_epilogue(const BaseArgs &a, int l, int j, fl
             q[1] = __dadd_ru(q[1], __dmul_ru(nc, (double)chi));
             q[2] = __dadd_ru(q[2], __dmul_ru(nc, (double)cwh));
             q[3] = __dadd_ru(q[3], __dmul_ru(nc, (double)cwl));
+        }
+        if (writer && a.act_list_lo && chi > 0.0f) {
+            const int idx = atomicAdd(&a.act_count_lo[j], 1);
+            if (idx < a.act_cap_lo)
+                a.act_list_lo[(size_t)j * a.act_cap_lo + idx] =
+                    make_int4(l, -1, __float_as_int((float)a.n_c),
+                              __float_as_int(c > 0.0f ? 1.0f : -1.0f));
+            else
+                atomicOr(a.err, kErrOverflow);
         }
         if (writer && a.act_list && clo_f > 0.0f) {
             const int idx = atomicAdd(&a.act_count[j], 1);

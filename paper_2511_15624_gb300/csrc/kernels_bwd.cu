@@ -1,4 +1,4 @@
-// Adjoint of the certified upper bound obj_hi with respect to the box
+// Adjoints of the certified bounds obj_hi and obj_lo with respect to the box
 // endpoints and the line ratings (not certified: FP32 products, FP64 sums).
 //
 // obj_hi = C(pd_hi) - G(pg_lo) - z_inj s_inj,lo - z_f (sum_l s_fb,lo + sum_{k,l} s_fc,lo)
@@ -12,6 +12,17 @@
 //   W_l += sgn, W_{line of k} += sgn L[l,k]  (H_k = Phi + L[:,k] Phi[k,:]).
 // An entry (l, -1, m, sgn) stands for m pairs of a bridge line, whose
 // contingency flows all equal its base flow (H_k[l,:] = Phi[l,:]).
+//
+// obj_lo = C(pd_lo) - G(pg_hi) - z_inj s_inj,hi - z_f (sum s_fb,hi + sum s_fc,hi)
+// takes the upper violation bounds s_hi = |c| + r - rating > 0 (its active
+// set A', recorded by the same forward kernels); the same kernels give
+//   d obj_lo / d c_b = -z_f sum_A' sgn(c_kl) H_k[l,b],
+//   d obj_lo / d r_b = -z_f sum_A' |H_k[l,b]|,
+//   d obj_lo / d rating_l = +z_f #{pairs of A' on line l},
+// and s_inj,hi = max(-P_lo, P_hi) with the device endpoints of the total
+// injection.  A' holds most pairs of a wide box, so its radius pass sums each
+// chunk of entries in FP32 before the FP64 sum (the order of a chunk's
+// entries, and so the last bits, then follow the forward kernel's atomics).
 // The imbalance term and the monotone cost curves act on the device
 // endpoints directly.  Kernels, in order: weights, centre GEMV, radius pass,
 // chain rule to the box endpoints.
@@ -73,23 +84,30 @@ __global__ void k_bwd_radius(BwdArgs a) {
     const int n = min(a.act_count[box], a.act_cap);
     const int4 *list = a.act_list + (size_t)box * a.act_cap;
     if (col >= a.n_a_pad) return;
-    // FP64 sums: the list order depends on the forward pass's atomics, so the
-    // result must not depend on how the entries are grouped
+    // obj_hi's sparse set: FP64 sums, since the list order depends on the
+    // forward pass's atomics and the result should not depend on how the
+    // entries are grouped
     double tot = 0.0;
     for (int c0 = blockIdx.y * kEntryChunk; c0 < n; c0 += gridDim.y * kEntryChunk) {
         const int c1 = min(c0 + kEntryChunk, n);
+        float part = 0.0f;  // obj_lo's dense set: FP32 within a chunk
         for (int i = c0; i < c1; ++i) {
             const int4 e = list[i];
+            float v;
             if (e.y < 0) {  // a bridge line, m contingency pairs at once
-                tot += (double)__int_as_float(e.z) *
-                       (double)fabsf(__ldg(&a.phi[(size_t)e.x * a.n_a_pad + col]));
+                const double m = (double)__int_as_float(e.z) *
+                                 (double)fabsf(__ldg(&a.phi[(size_t)e.x * a.n_a_pad + col]));
+                tot += m;
                 continue;
             }
             const float L = __int_as_float(e.z);
             const float h = __fmaf_rn(L, __ldg(&a.phi[(size_t)e.y * a.n_a_pad + col]),
                                       __ldg(&a.phi[(size_t)e.x * a.n_a_pad + col]));
-            tot += (double)fabsf(h);
+            v = fabsf(h);
+            if (a.side) part += v;
+            else tot += (double)v;
         }
+        tot += (double)part;
     }
     if (tot != 0.0) atomicAdd(&a.dr[(size_t)box * a.n_a_pad + col], tot);
 }
@@ -108,6 +126,7 @@ __global__ void __launch_bounds__(256) k_bwd_chain(BwdArgs a) {
     const double *lo = a.box_lo + (size_t)box * a.n_dev;
     const double *hi = a.box_hi + (size_t)box * a.n_dev;
     const double g = a.grad_obj_hi[box];
+    const bool lo_side = a.side != 0;
     // total injection interval [plo, phi] (imbalance at the slack)
     double plo = 0.0, phi = 0.0;
     for (int d = threadIdx.x; d < a.n_dev; d += blockDim.x) {
@@ -135,6 +154,8 @@ __global__ void __launch_bounds__(256) k_bwd_chain(BwdArgs a) {
         phi += sp[1][w];
     }
     const int inj = plo > 0.0 ? 1 : (phi < 0.0 ? -1 : 0);
+    // obj_lo: s_inj,hi = max(-plo, phi), phi when phi >= -plo
+    const bool up_hi = phi >= -plo;
     for (int d = threadIdx.x; d < a.n_dev; d += blockDim.x) {
         const bool gen = d < a.n_gen;
         const double sgn = gen ? 1.0 : -1.0;
@@ -142,19 +163,33 @@ __global__ void __launch_bounds__(256) k_bwd_chain(BwdArgs a) {
         double gc = 0.0, gr = 0.0;
         if (col >= 0) {
             gc = -a.zeta_f * a.dc[(size_t)box * a.n_a_pad + col];
-            gr = a.zeta_f * a.dr[(size_t)box * a.n_a_pad + col];
+            // obj_hi grows with the radius (s_lo falls), obj_lo falls (s_hi grows)
+            gr = (lo_side ? -a.zeta_f : a.zeta_f) * a.dr[(size_t)box * a.n_a_pad + col];
         }
         double glo = 0.5 * sgn * gc - 0.5 * gr;
         double ghi = 0.5 * sgn * gc + 0.5 * gr;
         const int s0 = a.seg_ptr[d], ns = a.seg_ptr[d + 1] - s0;
-        if (gen) glo -= pwl_slope(a.slope + s0, a.bkpt + s0, ns, lo[d]);
-        else ghi += pwl_slope(a.slope + s0, a.bkpt + s0, ns, hi[d]);
-        if (inj > 0) {  // s_inj,lo = plo = sum lo_g - sum hi_d
-            if (gen) glo -= a.zeta_inj;
-            else ghi += a.zeta_inj;
-        } else if (inj < 0) {  // s_inj,lo = -phi = sum lo_d - sum hi_g
-            if (gen) ghi += a.zeta_inj;
-            else glo -= a.zeta_inj;
+        if (!lo_side) {
+            if (gen) glo -= pwl_slope(a.slope + s0, a.bkpt + s0, ns, lo[d]);
+            else ghi += pwl_slope(a.slope + s0, a.bkpt + s0, ns, hi[d]);
+            if (inj > 0) {  // s_inj,lo = plo = sum lo_g - sum hi_d
+                if (gen) glo -= a.zeta_inj;
+                else ghi += a.zeta_inj;
+            } else if (inj < 0) {  // s_inj,lo = -phi = sum lo_d - sum hi_g
+                if (gen) ghi += a.zeta_inj;
+                else glo -= a.zeta_inj;
+            }
+        } else {
+            // obj_lo takes the load values at lo and the generator costs at hi
+            if (gen) ghi -= pwl_slope(a.slope + s0, a.bkpt + s0, ns, hi[d]);
+            else glo += pwl_slope(a.slope + s0, a.bkpt + s0, ns, lo[d]);
+            if (up_hi) {  // s_inj,hi = phi = sum hi_g - sum lo_d
+                if (gen) ghi -= a.zeta_inj;
+                else glo += a.zeta_inj;
+            } else {      // s_inj,hi = -plo = sum hi_d - sum lo_g
+                if (gen) glo += a.zeta_inj;
+                else ghi -= a.zeta_inj;
+            }
         }
         a.grad_lo[(size_t)box * a.n_dev + d] = g * glo;
         a.grad_hi[(size_t)box * a.n_dev + d] = g * ghi;

@@ -128,4 +128,3 @@ def test_multi_box_adjoint_and_autograd(P):
     gs = max(np.abs(glo).max(), np.abs(ghi).max())
     np.testing.assert_allclose(tlo.grad.cpu().numpy(), glo, rtol=0, atol=1e-9 * gs)
     np.testing.assert_allclose(thi.grad.cpu().numpy(), ghi, rtol=0, atol=1e-9 * gs)
-    assert not obj_lo.requires_grad

@@ -445,3 +445,71 @@ def test_rating_gradient_matches_finite_differences(cases, cfg):
         fd_c = _rating_fd(sep, s, a, b, "rating_ctg", l, h)
         assert abs(fd_b - g_base[0, l]) <= 1e-6 * max(1.0, abs(fd_b)), (l, fd_b, g_base[0, l])
         assert abs(fd_c - g_ctg[0, l]) <= 1e-6 * max(1.0, abs(fd_c)), (l, fd_c, g_ctg[0, l])
+
+
+def _kink_free_step_lo(c, s, lo, hi):
+    """Largest FD step that crosses no kink of lo: |c| + r - rating = 0 for any
+    pair or base line, c = 0 for an active one, and sum c = 0 (imbalance)."""
+    cb, rb = O.bus_box(c, lo[None], hi[None])
+    cent, rad = O.all_ctg_flows(c, s, cb, rb)
+    m = np.abs(np.abs(cent[0]) + rad[0] - c.rating[None, :])
+    act = (np.abs(cent[0]) + rad[0] - c.rating[None, :]) > 0
+    mc = np.abs(cent[0])[act]
+    fb = (cb @ s.phi.T)[0]
+    fr = (rb @ np.abs(s.phi).T)[0]
+    mb = np.abs(np.abs(fb) + fr - c.rating)
+    actb = (np.abs(fb) + fr - c.rating) > 0
+    dist = min(m.min(), mb.min(), mc.min() if mc.size else np.inf,
+               np.abs(fb)[actb].min() if actb.any() else np.inf, abs(cb.sum()))
+    hmax = np.abs(s.phi).max() * (1 + np.abs(s.lodf).max())
+    return dist / (20 * max(hmax, 1.0))
+
+
+@pytest.mark.parametrize("cfg", [0, 1])
+def test_lower_adjoint_matches_finite_differences(cases, cfg):
+    """The hand adjoint of the lower bound (grad_lo) against central
+    differences of the oracle's own obj_lo, in box endpoints and ratings."""
+    import dataclasses
+    c = cases(cfg)
+    s = O.sensitivities(c)
+    rng = np.random.default_rng(41 + cfg)
+    lo0, hi0 = c.box_lo[0], c.box_hi[0]
+    a = lo0 + 0.4 * rng.random(c.n_dev) * (hi0 - lo0)
+    b = hi0 - 0.4 * rng.random(c.n_dev) * (hi0 - lo0)
+    h = _kink_free_step_lo(c, s, a, b)
+    assert h > 1e-9
+    g_lo, g_hi, g_rat = O.grad_lo(c, s, lo=a[None], hi=b[None])
+    dims = range(c.n_dev) if c.n_dev <= 10 else rng.choice(c.n_dev, 12, replace=False)
+    for d in dims:
+        for which, g in (("lo", g_lo), ("hi", g_hi)):
+            ap, bp, am, bm = a.copy(), b.copy(), a.copy(), b.copy()
+            if which == "lo":
+                ap[d] += h
+                am[d] -= h
+            else:
+                bp[d] += h
+                bm[d] -= h
+            fp = O.bound(c, s, lo=ap[None], hi=bp[None]).lo[0]
+            fm = O.bound(c, s, lo=am[None], hi=bm[None]).lo[0]
+            fd = (fp - fm) / (2 * h)
+            scale = max(abs(fd), abs(g[0, d]), 1e-3 * np.abs(g).max())
+            assert abs(fd - g[0, d]) <= 1e-4 * scale, (which, d, fd, g[0, d])
+    # ratings: lines whose decisions sit away from their kinks
+    cb, rb = O.bus_box(c, a[None], b[None])
+    cent, rad = O.all_ctg_flows(c, s, cb, rb)
+    fb, fr = (cb @ s.phi.T)[0], (rb @ np.abs(s.phi).T)[0]
+    dist = np.minimum(np.abs(np.abs(cent[0]) + rad[0] - c.rating[None, :]).min(axis=0),
+                      np.abs(np.abs(fb) + fr - c.rating))
+    hr = 1e-3
+    lines = np.flatnonzero(dist > 50 * hr)
+    active = lines[g_rat[0, lines] > 0]
+    pick = np.union1d(active[:6], lines[:2])
+    assert active.size > 0
+    for l in pick:
+        vals = []
+        for sg in (1.0, -1.0):
+            r = c.rating.copy()
+            r[l] += sg * hr
+            vals.append(O.bound(dataclasses.replace(c, rating=r), s, lo=a[None], hi=b[None]).lo[0])
+        fd = (vals[0] - vals[1]) / (2 * hr)
+        assert abs(fd - g_rat[0, l]) <= 1e-6 * max(1.0, abs(fd)), (l, fd, g_rat[0, l])
