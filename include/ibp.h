@@ -177,6 +177,42 @@ ibp_status ibp_bound_backward_lo(ibp_case *c, int32_t n_box, const double *box_l
                                  int32_t ptr_mode, void *cuda_stream);
 
 /*
+ * Linear (CROWN-style) relaxation bound of max f over each box, the dual of
+ * the LP whose optimum is max f (the paper bounds f by IBP and names linear
+ * relaxations of the CROWN family as related work, Sec. I).  Every penalty
+ * term is bounded below by a line with slope a in [-1, 1] --
+ * max(|y| - R, 0) >= a y - |a| R for the base and contingency flows of
+ * eqs. (slack-sfb), (slack-Sc), |y| >= a y for the total injection of
+ * eq. (slack-sinj) -- so f <= l_a on the box for every choice of slopes, and
+ * max over the box of l_a, which is separable per device, is exact.  The
+ * slopes are optimised by n_iter primal-dual hybrid gradient iterations
+ * (restarts to the averages every 1000 iterations, primal weight starting at
+ * primal_weight, 1.0 by default, and adapted at each restart); any slopes
+ * give a certified bound, and the iteration approaches the LP optimum.
+ *   box_lo, box_hi [n_box][n_gen + n_load]; obj_hi [n_box]: the smallest
+ *     certified value of the dual function met at a restart (computed from
+ *     the FP64 sensitivities with outward rounding: obj_hi >= max f);
+ *   obj_err [n_box]: a bound on its rounding error;
+ *   x_point [n_box][n_gen + n_load] or NULL: the averaged primal point, a
+ *     candidate maximiser (f there, e.g. from ibp_bound on the zero-width box
+ *     at it, is a certified lower bound of max f).
+ * The first call on a case measures the operator norm (a power iteration;
+ * the call synchronises its stream once).  Memory: 12 bytes per (box,
+ * contingency, line).  ptr_mode and stream as in ibp_bound.
+ */
+ibp_status ibp_bound_linear(ibp_case *c, int32_t n_box, const double *box_lo,
+                            const double *box_hi, int32_t n_iter, double primal_weight,
+                            double *obj_hi, double *obj_err, double *x_point, int32_t ptr_mode,
+                            void *cuda_stream);
+
+/* The slopes of the last ibp_bound_linear call of the case (host arrays):
+ * a_ctg [n_box][n_ctg][n_line], a_base [n_box][n_line], a_inj [n_box].  For an
+ * independent evaluation of the certified value.  Synchronises the case's
+ * last call.  No counterpart in the paper. */
+ibp_status ibp_case_linear_slopes(ibp_case *c, int32_t n_box, float *a_ctg, float *a_base,
+                                  double *a_inj);
+
+/*
  * Replace the case's line ratings (eqs. (slack-sfb), (slack-Sc)): rating
  * [n_line] (base, MW) and rating_ctg [n_line] or NULL (then the contingency
  * ratings equal the new base ratings).  ptr_mode 0: host pointers, validated

@@ -22,6 +22,7 @@ Every function names the passage of the paper it follows:
 * ``grad_hi``             hand-derived adjoint of the upper bound (the paper has none)
 * ``grad_hi_ratings``     its rating part, split into base and contingency ratings
 * ``grad_lo``             hand-derived adjoint of the lower bound (the paper has none)
+* ``linear_bound``        the linear (CROWN-style) relaxation bound at given slopes (the paper has none)
 * ``paper_mode_flows``    IBP applied literally to eq. (ctg flow matrix form)
 * ``screen_lines``        lines whose paper-mode contingency interval can exceed the rating
 * ``paper_ctg_terms``     eq. (slack-Sc) sums over the paper-mode intervals (``bound(mode="paper")``)
@@ -551,6 +552,59 @@ def grad_lo(case, sens: Sensitivities, lo=None, hi=None, nthreads=None):
         for d, (a, b) in enumerate(_segments(case.load_nseg, case.load_slope, case.load_bkpt)):
             g_lo[j, ng + d] += _pwl_slope(a, b, lo[j, ng + d])
     return g_lo, g_hi, g_rating
+
+
+def linear_bound(case, sens: Sensitivities, lo, hi, a_base, a_ctg, a_inj, factored: bool = False):
+    """The linear relaxation bound U(a) = max over the box of l_a (the dual
+    function of the LP whose optimum is max f).
+
+    For slopes a in [-1, 1] every penalty term has a linear lower bound,
+    max(|y| - R, 0) >= a y - |a| R (base flows y = f_l with the base rating,
+    contingency flows y = f_kl with the contingency rating, eqs. (slack-sfb),
+    (slack-Sc)) and |1^T p| >= a_inj 1^T p (eq. (slack-sinj), reading C5), so
+      f(x) <= l_a(x) = C(p_d) - G(p_g) - z_inj a_inj 1^T p
+                       - z_f (sum_t a_t y_t(x) - |a_t| R_t)
+    on the box (appendix eq. (ibp_f)).  l_a is a sum of one-device functions,
+    so its maximum is taken device by device over the endpoints and the
+    breakpoints of the device's PWL curve inside its interval.
+    a_base [n_line], a_ctg [n_ctg, n_line], a_inj a scalar; lo, hi one box.
+    The slope of x_i in sum_t a_t y_t is s_i sum_t a_t H_t[b(i)] with H_t the
+    flow's row (Phi_l, or Phi_l + L[l,k] Phi_k); factored=False forms every
+    H_k, factored=True uses sum_t a_t H_t = Phi^T w with w_l = a_l + sum_k a_kl,
+    w_{line of k} += sum_l a_kl L[l,k] (the same sum regrouped).
+    """
+    lo = np.asarray(lo, np.float64).ravel()
+    hi = np.asarray(hi, np.float64).ravel()
+    a_base = np.asarray(a_base, np.float64)
+    a_ctg = np.asarray(a_ctg, np.float64).reshape(case.n_ctg, case.n_line)
+    phi, L = sens.phi, sens.lodf
+    rating_c = case.rating if case.rating_ctg is None else case.rating_ctg
+    if factored:
+        w = a_base + a_ctg.sum(axis=0)
+        np.add.at(w, case.ctg_line, (a_ctg * L.T).sum(axis=1))
+        row = w @ phi
+    else:
+        row = a_base @ phi
+        for k in range(case.n_ctg):
+            Hk = phi + np.outer(L[:, k], phi[case.ctg_line[k]])
+            row = row + a_ctg[k] @ Hk
+    const = case.zeta_f * (np.abs(a_base) @ case.rating + (np.abs(a_ctg) * rating_c[None, :]).sum())
+    ng = case.n_gen
+    bus = np.concatenate([case.gen_bus, case.load_bus])
+    sgn = np.concatenate([np.ones(ng), -np.ones(case.n_load)])
+    coef = -sgn * (case.zeta_f * row[bus] + case.zeta_inj * float(a_inj))
+    total = const
+    segs = _segments(case.gen_nseg, case.gen_slope, case.gen_bkpt) + \
+        _segments(case.load_nseg, case.load_slope, case.load_bkpt)
+    for i in range(case.n_dev):
+        a, b = segs[i]
+        pts = [lo[i], hi[i]] + [v for v in b if lo[i] < v < hi[i]]
+        vals = []
+        for xv in pts:
+            v = pwl_value(a, b, xv)
+            vals.append((-v if i < ng else v) + coef[i] * xv)
+        total += max(vals)
+    return total
 
 
 def grad_hi_ratings(case, sens: Sensitivities, lo=None, hi=None, nthreads=None):

@@ -28,7 +28,8 @@ EXPORTED = (
     "ibp_case_set_timing", "ibp_case_last_timing", "ibp_selftest_wait_timeout", "ibp_last_error",
     "ibp_status_string", "ibp_bound_noalloc", "ibp_case_set_screen", "ibp_case_last_live",
     "ibp_case_set_reduction", "ibp_case_set_refine", "ibp_case_reduction", "ibp_bound_paper",
-    "ibp_set_alloc_limit", "ibp_bound_backward_lo", "ibp_case_set_ratings",
+    "ibp_set_alloc_limit", "ibp_bound_backward_lo", "ibp_case_set_ratings", "ibp_bound_linear",
+    "ibp_case_linear_slopes",
 )
 
 
@@ -77,6 +78,10 @@ def lib():
         L.ibp_bound_backward_lo.restype = ctypes.c_int
         L.ibp_case_set_ratings.argtypes = [P, P, P, I32, P]
         L.ibp_case_set_ratings.restype = ctypes.c_int
+        L.ibp_bound_linear.argtypes = [P, I32, P, P, I32, D, P, P, P, I32, P]
+        L.ibp_bound_linear.restype = ctypes.c_int
+        L.ibp_case_linear_slopes.argtypes = [P, I32, P, P, P]
+        L.ibp_case_linear_slopes.restype = ctypes.c_int
         L.ibp_bound_multi.argtypes = [I32, P, P, P, P, P, P, P, P]
         L.ibp_bound_multi.restype = ctypes.c_int
         L.ibp_bound_noalloc.argtypes = [P, P, P, P, P, P, P]
@@ -295,3 +300,18 @@ def ibp_case_last_live(handle, n_line: int):
 def ibp_selftest_wait_timeout(device: int, limit_us: int) -> int:
     """Returns the status code (IBP_ETIMEOUT is the expected outcome)."""
     return int(lib().ibp_selftest_wait_timeout(int(device), int(limit_us)))
+
+
+def ibp_bound_linear(handle, n_box, box_lo, box_hi, n_iter, primal_weight, obj_hi, obj_err,
+                     x_point=None, ptr_mode=0, stream=None):
+    _check(lib().ibp_bound_linear(ctypes.c_void_p(handle), int(n_box), _ptr(box_lo), _ptr(box_hi),
+                                  int(n_iter), float(primal_weight), _ptr(obj_hi), _ptr(obj_err),
+                                  _ptr(x_point), int(ptr_mode), stream))
+
+
+def ibp_case_linear_slopes(handle, n_box, n_ctg, n_line):
+    a_c = np.empty((n_box, n_ctg, n_line), np.float32)
+    a_b = np.empty((n_box, n_line), np.float32)
+    a0 = np.empty(n_box)
+    _check(lib().ibp_case_linear_slopes(ctypes.c_void_p(handle), int(n_box), _ptr(a_c), _ptr(a_b), _ptr(a0)))
+    return a_c, a_b, a0

@@ -146,6 +146,35 @@ class Case:
         fn(self._h, nb, lo, hi, g, glo, ghi, gr, ptr_mode=0, stream=None)
         return (glo, ghi) + ((gr,) if want_rating else ())
 
+    def bound_linear(self, lo, hi, n_iter: int = 20000, primal_weight: float = 1.0, stream=None):
+        """Linear (CROWN-style) relaxation bound with optimised slopes
+        (``ibp_bound_linear``): returns (obj_hi, obj_err, x_point) -- the
+        certified upper bound of max f, its rounding bound and the averaged
+        primal point -- as numpy arrays for numpy boxes, CUDA tensors for CUDA
+        boxes (enqueued on the stream)."""
+        if _abi._is_cuda_tensor(lo):
+            import torch
+            lo = lo.contiguous().to(torch.float64)
+            hi = hi.contiguous().to(torch.float64)
+            nb = int(lo.shape[0])
+            ub = torch.empty(nb, dtype=torch.float64, device=lo.device)
+            err = torch.empty_like(ub)
+            xp = torch.empty_like(lo)
+            s = stream if stream is not None else torch.cuda.current_stream(lo.device).cuda_stream
+            _abi.ibp_bound_linear(self._h, nb, lo, hi, n_iter, primal_weight, ub, err, xp, ptr_mode=1,
+                                  stream=s)
+            return ub, err, xp
+        lo = np.ascontiguousarray(np.atleast_2d(lo), np.float64)
+        hi = np.ascontiguousarray(np.atleast_2d(hi), np.float64)
+        nb = lo.shape[0]
+        ub, err, xp = np.empty(nb), np.empty(nb), np.empty_like(lo)
+        _abi.ibp_bound_linear(self._h, nb, lo, hi, n_iter, primal_weight, ub, err, xp, ptr_mode=0)
+        return ub, err, xp
+
+    def linear_slopes(self, n_box: int = 1):
+        """(a_ctg, a_base, a_inj) of the last ``bound_linear`` call."""
+        return _abi.ibp_case_linear_slopes(self._h, n_box, self.n_ctg, self.n_line)
+
     def set_ratings(self, rating, rating_ctg=None, stream=None):
         """Replace the line ratings (numpy: synchronous; CUDA tensor: enqueued
         on the stream).  rating_ctg None: contingency ratings = rating."""

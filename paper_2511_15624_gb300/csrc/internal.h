@@ -217,6 +217,54 @@ struct LineExactArgs {
 };
 cudaError_t launch_line_exact(const LineExactArgs &a, int num_sms, cudaStream_t s);
 
+// Linear (CROWN-style) relaxation of the penalty terms and its optimised
+// slopes (ibp_bound_linear).  Every penalty term t -- a base line, a
+// contingency pair, the imbalance -- is bounded below by a line with slope
+// a_t in [-1, 1]: max(|y| - R, 0) >= a y - |a| R and |y| >= a y, so for every
+// choice of slopes f(x) <= l_a(x) on the box and max f <= max_x l_a(x), whose
+// maximum over the box is exact because l_a is separable per device.  The
+// slopes are optimised by a primal-dual hybrid gradient iteration on
+// max_x min_a l_a(x); any slopes give a certified bound.
+struct LinArgs {
+    int n_l, n_c, n_a, n_a_pad, n_dev, n_gen, n_box;
+    const float *phi;          // [n_l][n_a_pad] FP32 PTDF (iterations)
+    const double *phi64;       // [n_l][n_a_pad] FP64 PTDF (certified value)
+    const float *lodf, *lodf_lo;  // [n_c][n_l]
+    const int *ctg_line;       // [n_c]
+    const int *cl_ptr, *cl_ctg;   // CSR: contingencies whose outaged line is l
+    const int *act_ptr, *act_dev, *dev_col;
+    const double *rate64, *rate_c64;
+    const double *box_lo, *box_hi;  // [n_box][n_dev]
+    const int *seg_ptr;
+    const double *slope, *bkpt;
+    double zeta_inj, zeta_f;
+    double step;               // 0.9 / ||D K|| (D: zeta scaling of the terms)
+    int power;                 // 1: power iteration for ||D K|| (no state update)
+    // iteration state
+    double *w;                 // [n_box] primal weight
+    double *x, *sx, *xb, *x_last;          // [n_box][n_dev]
+    float *a_c, *s_c, *c_last;             // [n_box][n_c][n_l]
+    float *a_b, *s_b, *b_last;             // [n_box][n_l]
+    double *a0, *s0, *a0_last;             // [n_box]
+    float *p;                  // [n_box][n_a_pad] bus injections of xb
+    double *stot;              // [n_box] total injection of xb
+    float *f;                  // [n_box][n_l] base flows of xb
+    float *colsum;             // [n_box][n_l]
+    float *rowdot;             // [n_box][n_c]
+    float *g;                  // [n_box][n_a_pad] zeta_f (Phi^T W)_b
+    double *red;               // [n_box][4] restart reductions
+    int n_avg;                 // iterations in the running sums
+    // certified value of the dual function at the slopes (a_c, a_b, a0)
+    double *W64, *Wabs, *constl;           // [n_box][n_l]
+    double *rd64, *rda;                    // [n_box][n_c]
+    double *g64, *G64;                     // [n_box][n_a_pad]
+    double *ub, *ub_err;                   // [n_box]
+};
+cudaError_t lin_iteration(const LinArgs &a, int num_sms, cudaStream_t s);
+cudaError_t lin_restart(const LinArgs &a, int num_sms, cudaStream_t s);
+cudaError_t lin_certify(const LinArgs &a, int num_sms, cudaStream_t s);
+cudaError_t lin_power_norm(const LinArgs &a, int num_sms, cudaStream_t s);
+
 // Radius of each bus class (the active buses whose PTDF columns coincide on
 // every non-bridge line): rcls[j] = RU(sum of rbus over the class members).
 struct ClsArgs {

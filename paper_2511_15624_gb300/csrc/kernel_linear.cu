@@ -1,0 +1,499 @@
+// Linear (CROWN-style) relaxation bound of the objective and the
+// primal-dual iteration that optimises its slopes (ibp_bound_linear).
+//
+// f(x) = C(p_d) - G(p_g) - z_inj |sum_b p_b| - z_f (sum_l s_l + sum_{k,l} s_kl),
+// s = max(|y| - R, 0) for the base flows y = f_l and the post-contingency
+// flows y = f_kl = f_l + L[l,k] f_k (eq. (penalized-objective), eqs.
+// (slack-sinj), (slack-sfb), (slack-Sc)).  For slopes a in [-1, 1],
+//   max(|y| - R, 0) >= a y - |a| R,   |y| >= a0 y,
+// so f(x) <= l_a(x) = C - G - z_inj a0 sum p - z_f sum_t (a_t y_t - |a_t| R_t)
+// on the whole box, and max f <= U(a) = max_x l_a(x).  l_a is affine in the bus
+// injections, sum_t a_t y_t = sum_b (Phi^T W)_b p_b with line weights
+// W_l = a_l + sum_k a_kl and W_{line of k} += sum_l a_kl L[l,k], so
+//   U(a) = z_f sum_t |a_t| R_t + sum_i max_{x_i in [lo_i, hi_i]} [phi_i(x_i) + c_i x_i],
+//   c_i = -s_i (z_f (Phi^T W)_b(i) + z_inj a0)   (s_i = +1 generator, -1 load),
+// exact per device (phi_i: the load's value or minus the generator's cost).
+// U is the Lagrangian dual function of the LP whose optimum is max f; any
+// slopes give a certified bound, and minimising U over them reaches that LP
+// optimum.  The slopes are driven by a primal-dual hybrid gradient iteration
+// (Chambolle and Pock, J. Math. Imaging Vision 40, 2011) on max_x min_a l_a(x)
+// with the operator D K (K: x -> the flows and the total injection, D: their
+// z_f / z_inj weights), step 0.9 / ||D K|| split by a primal weight, restarts
+// to the running averages with the primal weight adapted to the ratio of the
+// dual and primal moves (as in PDLP, Applegate et al., NeurIPS 2021).
+// The iterations run in FP32/FP64 without rounding control; the certified
+// value U(a) at the final slopes is computed in FP64 with an explicit error
+// bound (lin_certify).
+#include <algorithm>
+
+#include "common.cuh"
+#include "internal.h"
+
+namespace ibp {
+
+constexpr double kU64Lin = 1.1102230246251565e-16;  // 2^-53
+
+// slope of a device's PWL curve at x (right segment at a breakpoint)
+__device__ __forceinline__ double lin_pwl_slope(const double *s, const double *b, int n, double x) {
+    if (x < b[0]) return 0.0;
+    int i = 0;
+    while (i + 1 < n && b[i + 1] <= x) ++i;
+    return s[i];
+}
+
+// value of the ReLU chain of eqs. (single ReLU), (combined ReLUs) at x,
+// rounded up (up) or down
+__device__ __forceinline__ double lin_pwl_value(const double *a, const double *b, int n, double x, bool up) {
+    double F = 0.0, U = 0.0;
+    for (int m = 0; m < n; ++m) {
+        if (up) F = __dadd_ru(F, __dmul_ru(a[m], fmax(__dsub_ru(x, b[m]), 0.0)));
+        else F = __dadd_rd(F, __dmul_rd(a[m], fmax(__dsub_rd(x, b[m]), 0.0)));
+        if (m + 1 < n) {
+            U = up ? __dadd_ru(U, __dmul_ru(a[m], __dsub_ru(b[m + 1], b[m])))
+                   : __dadd_rd(U, __dmul_rd(a[m], __dsub_rd(b[m + 1], b[m])));
+            F = fmin(F, U);
+        }
+    }
+    return F;
+}
+
+template <bool UP>
+__device__ __forceinline__ double block_sum_d(double v, double *sh) {
+    v = UP ? warp_sum_ru(v) : warp_sum_rd(v);
+    const int w = threadIdx.x >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t = UP ? __dadd_ru(t, sh[i]) : __dadd_rd(t, sh[i]);
+    return t;  // in thread 0
+}
+
+// ------------------------------------------------------------------ x step
+// One block per box: projected gradient ascent on x, the extrapolated point
+// xb = 2 x_new - x, its bus injections and total injection.  In power mode x
+// holds the power iteration's vector and only its injections are formed.
+__global__ void __launch_bounds__(256) k_lin_x(const LinArgs a) {
+    const int j = blockIdx.x;
+    const size_t od = (size_t)j * a.n_dev;
+    const double *lo = a.box_lo + od, *hi = a.box_hi + od;
+    double *x = a.x + od, *xb = a.xb + od, *sx = a.sx + od;
+    const float *g = a.g + (size_t)j * a.n_a_pad;
+    const double tx = a.step / a.w[j];
+    const double a0 = a.a0[j];
+    double part = 0.0;
+    for (int d = threadIdx.x; d < a.n_dev; d += blockDim.x) {
+        const bool gen = d < a.n_gen;
+        const double sg = gen ? 1.0 : -1.0;
+        if (a.power) {
+            xb[d] = x[d];
+        } else {
+            const int col = a.dev_col[d];
+            const double gb = col >= 0 ? (double)g[col] : 0.0;
+            const int s0 = a.seg_ptr[d], ns = a.seg_ptr[d + 1] - s0;
+            const double sl = lin_pwl_slope(a.slope + s0, a.bkpt + s0, ns, x[d]);
+            const double grad = (gen ? -sl : sl) - sg * (gb + a.zeta_inj * a0);
+            const double xn = fmin(fmax(x[d] + tx * grad, lo[d]), hi[d]);
+            xb[d] = 2.0 * xn - x[d];
+            x[d] = xn;
+            sx[d] += xn;
+        }
+        part += sg * xb[d];
+    }
+    __shared__ double sh[8];
+    // a plain (round-to-nearest) block sum
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = part;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += sh[i];
+        a.stot[j] = t;
+    }
+    for (int col = threadIdx.x; col < a.n_a_pad; col += blockDim.x) {
+        double v = 0.0;
+        if (col < a.n_a)
+            for (int q = a.act_ptr[col]; q < a.act_ptr[col + 1]; ++q) {
+                const int d = a.act_dev[q];
+                v += (d < a.n_gen ? 1.0 : -1.0) * xb[d];
+            }
+        a.p[(size_t)j * a.n_a_pad + col] = (float)v;
+    }
+}
+
+// base flows f = Phi p of xb: one warp per (line, box)
+__global__ void __launch_bounds__(256) k_lin_flows(const LinArgs a) {
+    const int j = blockIdx.y;
+    const int l = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (l >= a.n_l) return;
+    const float4 *row = reinterpret_cast<const float4 *>(a.phi + (size_t)l * a.n_a_pad);
+    const float4 *p = reinterpret_cast<const float4 *>(a.p + (size_t)j * a.n_a_pad);
+    float s = 0.0f;
+    for (int v = lane; v < (a.n_a_pad >> 2); v += 32) {
+        const float4 r = __ldg(&row[v]), q = p[v];
+        s = fmaf(r.x, q.x, fmaf(r.y, q.y, fmaf(r.z, q.z, fmaf(r.w, q.w, s))));
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) a.f[(size_t)j * a.n_l + l] = s;
+}
+
+__device__ __forceinline__ float lin_prox(float v, float thr) {
+    // soft threshold by thr (the prox of thr |.|), then the projection on [-1, 1]
+    const float t = fminf(fmaxf(fabsf(v) - thr, 0.0f), 1.0f);
+    return copysignf(t, v);
+}
+
+// Dual step on the slopes: block (x: 256 lines, y: 32 contingencies, z: box);
+// blocks with y == 0 also take the base flows, block (0, 0) the imbalance.
+// Accumulates the line weights' column sums and the rows' dot products with L.
+__global__ void __launch_bounds__(256) k_lin_pairs(const LinArgs a) {
+    const int j = blockIdx.z;
+    const int l = blockIdx.x * 256 + threadIdx.x;
+    const int k0 = blockIdx.y * 32;
+    const double sa = a.step * a.w[j];
+    const float gain = (float)(sa * a.zeta_f);
+    const float *f = a.f + (size_t)j * a.n_l;
+    const bool lv = l < a.n_l;
+    const float fl = lv ? f[l] : 0.0f;
+    const float thr = lv ? gain * (float)a.rate_c64[l] : 0.0f;
+    float col = 0.0f;
+    float rowv[32];
+#pragma unroll
+    for (int kk = 0; kk < 32; ++kk) {
+        const int k = k0 + kk;
+        float v = 0.0f;
+        if (lv && k < a.n_c) {
+            const float Lt = __ldg(&a.lodf[(size_t)k * a.n_l + l]);
+            const float fc = fmaf(Lt, f[__ldg(&a.ctg_line[k])], fl);
+            const size_t o = ((size_t)j * a.n_c + k) * a.n_l + l;
+            float an;
+            if (a.power) {
+                an = (float)a.zeta_f * fc;
+            } else {
+                an = lin_prox(fmaf(gain, fc, a.a_c[o]), thr);
+                a.a_c[o] = an;
+                a.s_c[o] += an;
+            }
+            col += an;
+            v = an * Lt;
+        }
+        rowv[kk] = v;
+    }
+    __shared__ float sh[8][33];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+    for (int kk = 0; kk < 32; ++kk) {
+        float v = rowv[kk];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) sh[w][kk] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 32 && k0 + threadIdx.x < a.n_c) {
+        float t = 0.0f;
+        for (int i = 0; i < 8; ++i) t += sh[i][threadIdx.x];
+        atomicAdd(&a.rowdot[(size_t)j * a.n_c + k0 + threadIdx.x], t);
+    }
+    if (blockIdx.y == 0 && lv) {
+        float an;
+        if (a.power) {
+            an = (float)a.zeta_f * fl;
+        } else {
+            const size_t o = (size_t)j * a.n_l + l;
+            an = lin_prox(fmaf(gain, fl, a.a_b[o]), gain * (float)a.rate64[l]);
+            a.a_b[o] = an;
+            a.s_b[o] += an;
+        }
+        col += an;
+    }
+    if (lv) atomicAdd(&a.colsum[(size_t)j * a.n_l + l], col);
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
+        if (a.power) {
+            a.a0[j] = a.zeta_inj * a.stot[j];
+        } else {
+            a.a0[j] = fmin(fmax(a.a0[j] + sa * a.zeta_inj * a.stot[j], -1.0), 1.0);
+            a.s0[j] += a.a0[j];
+        }
+    }
+}
+
+// line weights W_l = colsum_l + sum over the contingencies of line l of their row dots
+__global__ void k_lin_W(const LinArgs a) {
+    const int j = blockIdx.y, l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= a.n_l) return;
+    float t = a.colsum[(size_t)j * a.n_l + l];
+    for (int q = a.cl_ptr[l]; q < a.cl_ptr[l + 1]; ++q) t += a.rowdot[(size_t)j * a.n_c + a.cl_ctg[q]];
+    a.colsum[(size_t)j * a.n_l + l] = t;
+}
+
+// g_b = z_f sum_l W_l Phi[l][b]: column blocks x 32 line splits, atomics into g
+constexpr int kLinSplit = 32;
+__global__ void k_lin_g(const LinArgs a) {
+    const int j = blockIdx.z, col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= a.n_a_pad) return;
+    const int l0 = (int)((long long)blockIdx.y * a.n_l / kLinSplit);
+    const int l1 = (int)((long long)(blockIdx.y + 1) * a.n_l / kLinSplit);
+    const float *W = a.colsum + (size_t)j * a.n_l;
+    float acc = 0.0f;
+    for (int l = l0; l < l1; ++l) {
+        const float w = W[l];
+        if (w != 0.0f) acc = fmaf(w, __ldg(&a.phi[(size_t)l * a.n_a_pad + col]), acc);
+    }
+    if (acc != 0.0f) atomicAdd(&a.g[(size_t)j * a.n_a_pad + col], (float)a.zeta_f * acc);
+}
+
+// power mode: v <- K^T D^2 K v (from g and a0), then its norm; box 0 only
+__global__ void __launch_bounds__(256) k_lin_power(const LinArgs a) {
+    double part = 0.0;
+    for (int d = threadIdx.x; d < a.n_dev; d += blockDim.x) {
+        const int col = a.dev_col[d];
+        const double v = (d < a.n_gen ? 1.0 : -1.0) * ((col >= 0 ? (double)a.g[col] : 0.0) + a.zeta_inj * a.a0[0]);
+        a.xb[d] = v;
+        part += v * v;
+    }
+    __shared__ double sh[8];
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = part;
+    __syncthreads();
+    __shared__ double nrm;
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += sh[i];
+        nrm = sqrt(t);
+        a.red[0] = nrm;  // ||K^T D^2 K v|| for the unit vector v
+    }
+    __syncthreads();
+    for (int d = threadIdx.x; d < a.n_dev; d += blockDim.x) a.x[d] = nrm > 0.0 ? a.xb[d] / nrm : 0.0;
+}
+
+cudaError_t lin_iteration(const LinArgs &a, int num_sms, cudaStream_t s) {
+    cudaError_t e;
+    if ((e = cudaMemsetAsync(a.colsum, 0, (size_t)a.n_box * a.n_l * sizeof(float), s)) != cudaSuccess) return e;
+    if (a.n_c > 0 &&
+        (e = cudaMemsetAsync(a.rowdot, 0, (size_t)a.n_box * a.n_c * sizeof(float), s)) != cudaSuccess)
+        return e;
+    k_lin_x<<<a.n_box, 256, 0, s>>>(a);
+    k_lin_flows<<<dim3((a.n_l + 7) / 8, a.n_box), 256, 0, s>>>(a);
+    k_lin_pairs<<<dim3((a.n_l + 255) / 256, std::max((a.n_c + 31) / 32, 1), a.n_box), 256, 0, s>>>(a);
+    k_lin_W<<<dim3((a.n_l + 255) / 256, a.n_box), 256, 0, s>>>(a);
+    if ((e = cudaMemsetAsync(a.g, 0, (size_t)a.n_box * a.n_a_pad * sizeof(float), s)) != cudaSuccess) return e;
+    k_lin_g<<<dim3((a.n_a_pad + 127) / 128, kLinSplit, a.n_box), 128, 0, s>>>(a);
+    if (a.power) k_lin_power<<<1, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ restarts
+// State <- running averages; accumulate |Delta x|^2 and |Delta a|^2 since the
+// last restart (red[j][0], red[j][1]); running sums restart at 0.
+__global__ void k_lin_avg(const LinArgs a) {
+    const int j = blockIdx.y;
+    const double inv = 1.0 / (double)a.n_avg;
+    const size_t npair = (size_t)a.n_c * a.n_l;
+    const size_t tot = (size_t)a.n_dev + a.n_l + npair + 1;
+    double dx = 0.0, da = 0.0;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += (size_t)gridDim.x * blockDim.x) {
+        if (i < (size_t)a.n_dev) {
+            const size_t o = (size_t)j * a.n_dev + i;
+            const double v = a.sx[o] * inv;
+            dx += (v - a.x_last[o]) * (v - a.x_last[o]);
+            a.x[o] = v;
+            a.x_last[o] = v;
+            a.sx[o] = 0.0;
+        } else if (i < (size_t)a.n_dev + a.n_l) {
+            const size_t o = (size_t)j * a.n_l + (i - a.n_dev);
+            const float v = (float)(a.s_b[o] * inv);
+            da += (double)(v - a.b_last[o]) * (double)(v - a.b_last[o]);
+            a.a_b[o] = v;
+            a.b_last[o] = v;
+            a.s_b[o] = 0.0f;
+        } else if (i < (size_t)a.n_dev + a.n_l + npair) {
+            const size_t o = (size_t)j * npair + (i - a.n_dev - a.n_l);
+            const float v = (float)(a.s_c[o] * inv);
+            da += (double)(v - a.c_last[o]) * (double)(v - a.c_last[o]);
+            a.a_c[o] = v;
+            a.c_last[o] = v;
+            a.s_c[o] = 0.0f;
+        } else {
+            const double v = a.s0[j] * inv;
+            da += (v - a.a0_last[j]) * (v - a.a0_last[j]);
+            a.a0[j] = v;
+            a.a0_last[j] = v;
+            a.s0[j] = 0.0;
+        }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        dx += __shfl_xor_sync(0xffffffffu, dx, o);
+        da += __shfl_xor_sync(0xffffffffu, da, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&a.red[(size_t)j * 4], dx);
+        atomicAdd(&a.red[(size_t)j * 4 + 1], da);
+    }
+}
+
+// primal weight <- exp(0.5 log(|Delta a| / |Delta x|) + 0.5 log w)
+__global__ void k_lin_weight(const LinArgs a) {
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= a.n_box) return;
+    const double dx = sqrt(a.red[(size_t)j * 4]), da = sqrt(a.red[(size_t)j * 4 + 1]);
+    if (dx > 1e-12 && da > 1e-12) a.w[j] = exp(0.5 * log(da / dx) + 0.5 * log(a.w[j]));
+    a.red[(size_t)j * 4] = 0.0;
+    a.red[(size_t)j * 4 + 1] = 0.0;
+}
+
+cudaError_t lin_restart(const LinArgs &a, int num_sms, cudaStream_t s) {
+    if (a.n_avg <= 0) return cudaSuccess;
+    k_lin_avg<<<dim3(num_sms * 4, a.n_box), 256, 0, s>>>(a);
+    k_lin_weight<<<(a.n_box + 127) / 128, 128, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ certified value
+// Column pass (thread per line): W_l = a_l + sum_k a_kl (round to nearest),
+// Wabs_l = |a_l| + sum_k |a_kl| (round up), constl_l = |a_l| R_l + Rc_l sum_k |a_kl|
+// (round up).
+__global__ void k_cert_col(const LinArgs a) {
+    const int j = blockIdx.y, l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= a.n_l) return;
+    double cs = 0.0, ca = 0.0;
+    for (int k = 0; k < a.n_c; ++k) {
+        const double v = (double)a.a_c[((size_t)j * a.n_c + k) * a.n_l + l];
+        cs += v;
+        ca = __dadd_ru(ca, fabs(v));
+    }
+    const double ab = (double)a.a_b[(size_t)j * a.n_l + l];
+    const size_t o = (size_t)j * a.n_l + l;
+    a.W64[o] = ab + cs;
+    a.Wabs[o] = __dadd_ru(fabs(ab), ca);
+    a.constl[o] = __dadd_ru(__dmul_ru(fabs(ab), a.rate64[l]), __dmul_ru(ca, a.rate_c64[l]));
+}
+
+// Row pass (block per contingency): rd_k = sum_l a_kl L[l,k], rda_k = sum_l |a_kl| |L[l,k]|
+// with the FP64 LODF L~ + L_lo
+__global__ void __launch_bounds__(256) k_cert_row(const LinArgs a) {
+    const int j = blockIdx.y, k = blockIdx.x;
+    double rd = 0.0, rda = 0.0;
+    for (int l = threadIdx.x; l < a.n_l; l += blockDim.x) {
+        const size_t q = (size_t)k * a.n_l + l;
+        const double L = (double)a.lodf[q] + (a.lodf_lo ? (double)a.lodf_lo[q] : 0.0);
+        const double v = (double)a.a_c[((size_t)j * a.n_c + k) * a.n_l + l];
+        rd = fma(v, L, rd);
+        rda = __fma_ru(fabs(v), fabs(L), rda);
+    }
+    __shared__ double sh[8];
+    double t = rd;
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += sh[i];
+        a.rd64[(size_t)j * a.n_c + k] = s;
+    }
+    const double ra = block_sum_d<true>(rda, sh);
+    if (threadIdx.x == 0) a.rda[(size_t)j * a.n_c + k] = ra;
+}
+
+__global__ void k_cert_W(const LinArgs a) {
+    const int j = blockIdx.y, l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= a.n_l) return;
+    const size_t o = (size_t)j * a.n_l + l;
+    double w = a.W64[o], wa = a.Wabs[o];
+    for (int q = a.cl_ptr[l]; q < a.cl_ptr[l + 1]; ++q) {
+        const int k = a.cl_ctg[q];
+        w += a.rd64[(size_t)j * a.n_c + k];
+        wa = __dadd_ru(wa, a.rda[(size_t)j * a.n_c + k]);
+    }
+    a.W64[o] = w;
+    a.Wabs[o] = wa;
+}
+
+// column b: g64_b = sum_l W_l Phi[l][b] (FP64 PTDF), G64_b = sum_l Wabs_l |Phi[l][b]| (round up)
+__global__ void k_cert_g(const LinArgs a) {
+    const int j = blockIdx.y, col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= a.n_a_pad) return;
+    double g = 0.0, G = 0.0;
+    for (int l = 0; l < a.n_l; ++l) {
+        const double ph = a.phi64[(size_t)l * a.n_a_pad + col];
+        g = fma(a.W64[(size_t)j * a.n_l + l], ph, g);
+        G = __fma_ru(a.Wabs[(size_t)j * a.n_l + l], fabs(ph), G);
+    }
+    a.g64[(size_t)j * a.n_a_pad + col] = g;
+    a.G64[(size_t)j * a.n_a_pad + col] = G;
+}
+
+// one block per box: U(a) = z_f sum |a| R + sum_i max_x [phi_i(x) + c_i x], with the
+// error of c_i (from W and g64) taken at |x|, all rounded up
+__global__ void __launch_bounds__(256) k_cert_ub(const LinArgs a) {
+    const int j = blockIdx.x;
+    __shared__ double sh[8];
+    // relative error of g64 against the exact Phi^T W: the column sums (n_c terms),
+    // the row dots (n_l terms), the GEMV (n_l terms), the FP64 LODF (2^-47)
+    const double gam = __fma_ru((double)(2 * a.n_l + a.n_c + 64), 1.01 * kU64Lin, 2.842170943040401e-14);
+    double cst = 0.0;
+    for (int l = threadIdx.x; l < a.n_l; l += blockDim.x) cst = __dadd_ru(cst, a.constl[(size_t)j * a.n_l + l]);
+    cst = block_sum_d<true>(cst, sh);
+    __shared__ double cst_s;
+    if (threadIdx.x == 0) cst_s = __dmul_ru(a.zeta_f, cst);
+    __syncthreads();
+    const double a0 = a.a0[j];
+    double sum = 0.0, err = 0.0, mag = 0.0;
+    for (int d = threadIdx.x; d < a.n_dev; d += blockDim.x) {
+        const bool gen = d < a.n_gen;
+        const int col = a.dev_col[d];
+        const double g = col >= 0 ? a.g64[(size_t)j * a.n_a_pad + col] : 0.0;
+        const double G = col >= 0 ? a.G64[(size_t)j * a.n_a_pad + col] : 0.0;
+        // c_i = -s_i (z_f g + z_inj a0), and a bound on its error
+        const double lin = (gen ? -1.0 : 1.0) * fma(a.zeta_f, g, a.zeta_inj * a0);
+        const double e = __fma_ru(__dmul_ru(a.zeta_f, gam), G,
+                                  __dmul_ru(4.0 * kU64Lin, __dadd_ru(fabs(a.zeta_f * g), fabs(a.zeta_inj * a0))));
+        const double lo = a.box_lo[(size_t)j * a.n_dev + d], hi = a.box_hi[(size_t)j * a.n_dev + d];
+        const int s0 = a.seg_ptr[d], ns = a.seg_ptr[d + 1] - s0;
+        const double *sl = a.slope + s0, *bk = a.bkpt + s0;
+        // candidates: the endpoints and the breakpoints inside the interval
+        double best = -INFINITY;
+        for (int c = -2; c < ns; ++c) {
+            const double xv = c == -2 ? lo : (c == -1 ? hi : bk[c]);
+            if (xv < lo || xv > hi) continue;
+            // phi_i rounded up: the load value up, minus the generator cost rounded down
+            const double ph = gen ? -lin_pwl_value(sl, bk, ns, xv, false) : lin_pwl_value(sl, bk, ns, xv, true);
+            const double v = __dadd_ru(__dadd_ru(ph, __dmul_ru(lin, xv)), __dmul_ru(e, fabs(xv)));
+            best = fmax(best, v);
+        }
+        sum = __dadd_ru(sum, best);
+        err = __dadd_ru(err, __dmul_ru(e, fmax(fabs(lo), fabs(hi))));
+        mag = __dadd_ru(mag, fabs(best));
+    }
+    sum = block_sum_d<true>(sum, sh);
+    const double es = block_sum_d<true>(err, sh);
+    const double ms = block_sum_d<true>(mag, sh);
+    if (threadIdx.x == 0) {
+        const double u = __dadd_ru(cst_s, sum);
+        a.ub[j] = u;
+        a.ub_err[j] = __fma_ru(1e-12, __dadd_ru(fabs(cst_s), ms), __dmul_ru(2.0, es));
+    }
+}
+
+cudaError_t lin_certify(const LinArgs &a, int num_sms, cudaStream_t s) {
+    k_cert_col<<<dim3((a.n_l + 255) / 256, a.n_box), 256, 0, s>>>(a);
+    if (a.n_c > 0) k_cert_row<<<dim3(a.n_c, a.n_box), 256, 0, s>>>(a);
+    k_cert_W<<<dim3((a.n_l + 255) / 256, a.n_box), 256, 0, s>>>(a);
+    k_cert_g<<<dim3((a.n_a_pad + 127) / 128, a.n_box), 128, 0, s>>>(a);
+    k_cert_ub<<<a.n_box, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+// ||D K|| by power iteration on K^T D^2 K (box 0 of the workspace; x holds the
+// vector, red[0] the last norm)
+cudaError_t lin_power_norm(const LinArgs &a0, int num_sms, cudaStream_t s) {
+    LinArgs a = a0;
+    a.power = 1;
+    a.n_box = 1;
+    for (int it = 0; it < 40; ++it) {
+        cudaError_t e = lin_iteration(a, num_sms, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace ibp

@@ -129,8 +129,10 @@ def test_point_box_is_point_evaluation(cases, cfg):
         assert abs(b.lo[0] - ref) <= 1e-9 * abs(ref)
 
 
-def _lp_optimum(c, s):
-    """max f over the box as an LP (Problem 1 with slacks), scipy HiGHS."""
+def _lp_optimum(c, s, duals: bool = False):
+    """max f over the box as an LP (Problem 1 with slacks), scipy HiGHS.
+    With duals=True also returns the multipliers of the penalty rows mapped to
+    the slopes of oracle.linear_bound: (a_base, a_ctg, a_inj)."""
     sp = pytest.importorskip("scipy.optimize")
     scsp = pytest.importorskip("scipy.sparse")
     ng, nd, nl, nc, nb = c.n_gen, c.n_load, c.n_line, c.n_ctg, c.n_bus
@@ -206,7 +208,23 @@ def _lp_optimum(c, s):
         + [(0, None)] * (nb + nl + nc * nl)
     res = sp.linprog(cost, A_ub=A, b_ub=np.array(rhs), bounds=bounds, method="highs")
     assert res.status == 0, res.message
-    return -res.fun, res.x[:nx]
+    if not duals:
+        return -res.fun, res.x[:nx]
+    # rows: 2 per bus (imbalance), 2 per line (base), 2 per pair (contingency),
+    # each pair (+y, -y); the multipliers lam = -marginal >= 0 of y - s <= R
+    # and -y - s <= R give the slope a = (lam+ - lam-) / zeta
+    lam = -res.ineqlin.marginals
+    r = 0
+    ib = lam[:2 * nb].reshape(nb, 2)
+    r += 2 * nb
+    # the imbalance row at the slack is -(1^T p): its slope is minus its multiplier difference
+    a_inj = -(ib[c.slack, 0] - ib[c.slack, 1]) / c.zeta_inj
+    bb = lam[r:r + 2 * nl].reshape(nl, 2)
+    r += 2 * nl
+    a_base = (bb[:, 0] - bb[:, 1]) / c.zeta_f
+    cc = lam[r:r + 2 * nc * nl].reshape(nc, nl, 2)
+    a_ctg = (cc[..., 0] - cc[..., 1]) / c.zeta_f
+    return -res.fun, res.x[:nx], (a_base, a_ctg, a_inj)
 
 
 @pytest.mark.parametrize("cfg,nseg", [(0, 1), (0, 3), (1, 1)])
