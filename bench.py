@@ -454,8 +454,22 @@ def run_gb300(args):
     print(json.dumps(line), flush=True)
 
 
+def _at_time(hist, t):
+    """The gap a run had reached by wall time t (inf before its first round)."""
+    g = float("inf")
+    for r in hist:
+        if r["s"] <= t:
+            g = r["gap"]
+    return g
+
+
 def run_bisection_study(args):
-    """Gap (UB - LB)/|LB| against wall seconds, batched vs one box per call."""
+    """Gap (UB - LB)/|LB| against wall seconds on the 2000-bus case, for the
+    batched driver (one call per round for all leaves) and the per-box driver
+    (one call per leaf), with IBP leaves (256-leaf frontier) and with
+    linear-relaxation leaves (16-leaf frontier, 1000 iterations per round,
+    children continuing their parent's slopes).  A third linear curve keeps
+    the root box alone and continues its iteration by 1000 per round."""
     import torch
 
     import paper_2511_15624_gb300 as P
@@ -464,19 +478,58 @@ def run_bisection_study(args):
 
     case = make_config(2)
     gpu = P.Case(case, device=0)
+    lin_kw = dict(bound="linear", max_leaves=16, linear_iters=1000, linear_root_iters=10000)
+    modes = {"ibp_batched": dict(max_leaves=256, batched=True),
+             "ibp_single": dict(max_leaves=256, batched=False),
+             "linear_batched": dict(lin_kw, batched=True),
+             "linear_single": dict(lin_kw, batched=False)}
     out = {"study": "bisection", "workload": workload(case, 2, 1) + " (root box)",
-           "rounds": args.rounds, "max_leaves": 256}
-    for batched in (True, False):
-        # warm-up rounds, not reported: they reach several leaves, so the first
-        # multi-box calls and the framework's first sorts and gathers over more
-        # than one leaf happen here
-        b = Bisection(gpu, case.box_lo, case.box_hi, max_leaves=256, batched=batched)
-        b.run(3)
-        b = Bisection(gpu, case.box_lo, case.box_hi, max_leaves=256, batched=batched)
-        hist = b.run(args.rounds)
-        out["batched" if batched else "single"] = [
-            {"round": r.round, "s": round(r.seconds, 4), "ub": r.ub, "lb": r.lb, "gap": r.gap,
-             "leaves": r.n_leaves} for r in hist]
+           "rounds": args.rounds, "modes": {k: {kk: vv for kk, vv in v.items()} for k, v in modes.items()},
+           "ibp_root": {}}
+    lo0, hi0, err0 = gpu.bound(case.box_lo, case.box_hi)
+    out["ibp_root"] = {"ub": float(hi0[0]), "err": float(err0[0, 0])}
+    limit = 120.0  # seconds per curve
+    for name, kw in modes.items():
+        # warm-up rounds, not reported: the first multi-box calls and the
+        # framework's first sorts and gathers over several leaves happen here
+        Bisection(gpu, case.box_lo, case.box_hi, **kw).run(2)
+        b = Bisection(gpu, case.box_lo, case.box_hi, **kw)
+        hist = []
+        for _ in range(args.rounds):
+            r = b.step()
+            hist.append({"round": r.round, "s": round(r.seconds, 4), "ub": r.ub, "lb": r.lb, "gap": r.gap,
+                         "leaves": r.n_leaves, "bound_s": round(r.bound_seconds, 4),
+                         "driver_s": round(r.round_seconds - r.bound_seconds, 4)})
+            if r.seconds > limit:
+                break
+        out[name] = hist
+    # the root box alone, its linear bound continued round by round
+    lo = torch.tensor(case.box_lo, device="cuda")
+    hi = torch.tensor(case.box_hi, device="cuda")
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hist, lb = [], -float("inf")
+    for rnd in range(args.rounds + 1):
+        ub, _, xp = gpu.bound_linear(lo, hi, 10000 if rnd == 0 else 1000, warm=rnd > 0)
+        _, ph, pe = gpu.bound(xp, xp)
+        lb = max(lb, float(ph[0] - pe[0, 0]))
+        u = float(ub[0]) if rnd == 0 else min(hist[-1]["ub"], float(ub[0]))
+        torch.cuda.synchronize()
+        hist.append({"round": rnd + 1, "s": round(time.perf_counter() - t0, 4), "ub": u, "lb": lb,
+                     "gap": (u - lb) / abs(lb), "leaves": 1})
+    out["linear_root_only"] = hist
+    # batched against per-box at equal wall time: at every round end of the
+    # per-box run, the gap the batched run had reached by then
+    cmp = {}
+    for kind in ("ibp", "linear"):
+        bh, sh = out[kind + "_batched"], out[kind + "_single"]
+        pts = [(r["s"], _at_time(bh, r["s"]), r["gap"]) for r in sh]
+        cmp[kind] = {"points": len(pts), "batched_at_or_below": sum(1 for _, gb, gs in pts if gb <= gs),
+                     "ub_fall": (bh[0]["ub"] - bh[-1]["ub"]) / abs(bh[0]["ub"]),
+                     "ub_fall_from_ibp_root": (out["ibp_root"]["ub"] - bh[-1]["ub"]) / abs(bh[-1]["ub"]),
+                     "final": {"batched": {k: bh[-1][k] for k in ("s", "ub", "lb", "gap", "leaves")},
+                               "single": {k: sh[-1][k] for k in ("s", "ub", "lb", "gap", "leaves")}}}
+    out["equal_time"] = cmp
     torch.cuda.synchronize()
     print(json.dumps(out), flush=True)
 

@@ -189,21 +189,43 @@ ibp_status ibp_bound_backward_lo(ibp_case *c, int32_t n_box, const double *box_l
  * (restarts to the averages every 1000 iterations, primal weight starting at
  * primal_weight, 1.0 by default, and adapted at each restart); any slopes
  * give a certified bound, and the iteration approaches the LP optimum.
+ * A call restarts at its end too, so a sequence of warm calls follows one
+ * long call only when each runs a multiple of 1000 iterations (calls of 500
+ * restart twice as often, which was measured to make the restart values
+ * oscillate).
  *   box_lo, box_hi [n_box][n_gen + n_load]; obj_hi [n_box]: the smallest
- *     certified value of the dual function met at a restart (computed from
+ *     certified value of the dual function met at a restart (or, warm, at
+ *     the start of the call; computed from
  *     the FP64 sensitivities with outward rounding: obj_hi >= max f);
  *   obj_err [n_box]: a bound on its rounding error;
  *   x_point [n_box][n_gen + n_load] or NULL: the averaged primal point, a
  *     candidate maximiser (f there, e.g. from ibp_bound on the zero-width box
- *     at it, is a certified lower bound of max f).
+ *     at it, is a certified lower bound of max f);
+ *   warm: 0 starts from zero slopes and the box midpoints (the case then
+ *     holds state for these n_box boxes); warm = 1 + f (f >= 0) continues
+ *     the iteration from the state the case holds for its boxes
+ *     [f, f + n_box) (see ibp_case_linear_inherit), the points moved into the
+ *     boxes, keeping the state of the other held boxes (IBP_EINVAL when those
+ *     boxes are not held); obj_hi is then also at most the certified value at
+ *     the held slopes, so a sub-box continued from its parent never gets a
+ *     larger bound than the parent's last one.
  * The first call on a case measures the operator norm (a power iteration;
  * the call synchronises its stream once).  Memory: 12 bytes per (box,
  * contingency, line).  ptr_mode and stream as in ibp_bound.
  */
 ibp_status ibp_bound_linear(ibp_case *c, int32_t n_box, const double *box_lo,
                             const double *box_hi, int32_t n_iter, double primal_weight,
-                            double *obj_hi, double *obj_err, double *x_point, int32_t ptr_mode,
-                            void *cuda_stream);
+                            int32_t warm, double *obj_hi, double *obj_err, double *x_point,
+                            int32_t ptr_mode, void *cuda_stream);
+
+/* Keep optimising from the state a case holds (warm != 0 in ibp_bound_linear,
+ * primal_weight then ignored): box j of the next call continues from the
+ * slopes, running sums, point and primal weight of box parent[j] of the last
+ * call or inheritance (host array [n_new]).  A sub-box can start from its
+ * parent's slopes: any slopes give a certified bound, and the parent's bound
+ * already holds for the sub-box.  Synchronises the device.  No counterpart in
+ * the paper. */
+ibp_status ibp_case_linear_inherit(ibp_case *c, int32_t n_new, const int32_t *parent);
 
 /* The slopes of the last ibp_bound_linear call of the case (host arrays):
  * a_ctg [n_box][n_ctg][n_line], a_base [n_box][n_line], a_inj [n_box].  For an
@@ -238,6 +260,29 @@ ibp_status ibp_bound_multi(int32_t n_case, ibp_case *const *cases,
                            const double *const *box_hi, double *const *obj_lo,
                            double *const *obj_hi, double *const *obj_err,
                            void *cuda_stream);
+
+/*
+ * Adjoint of many cases' bounds (ibp_bound_backward for side 0: obj_hi;
+ * ibp_bound_backward_lo for side 1: obj_lo), device pointers only.  The
+ * forward pass runs as in ibp_bound_multi, one persistent launch over every
+ * case's contingency tiles, recording the side's active pairs; the weights,
+ * centre and radius passes then run once each over all (case, box) items,
+ * and the chain rule to the box endpoints once per case.  For case i:
+ *   box_lo[i], box_hi[i] [n_box[i]][n_dev_i]; grad_obj[i] [n_box[i]]:
+ *   d loss / d obj; grad_lo[i], grad_hi[i] [n_box[i]][n_dev_i] (written);
+ *   grad_rating NULL, or grad_rating[i] NULL or [n_box[i]][n_line_i]
+ *   (written, as in ibp_bound_backward).
+ * At most 65535 boxes over all cases (IBP_EINVAL).  The work plan is cached
+ * per set of cases and box counts (separately from ibp_bound_multi's), so
+ * later calls only enqueue kernels and can be captured in a CUDA graph.  The
+ * paper differentiates nothing; this is the batched form of the adjoint.
+ */
+ibp_status ibp_bound_multi_backward(int32_t n_case, ibp_case *const *cases,
+                                    const int32_t *n_box, const double *const *box_lo,
+                                    const double *const *box_hi,
+                                    const double *const *grad_obj, double *const *grad_lo,
+                                    double *const *grad_hi, double *const *grad_rating,
+                                    int32_t side, void *cuda_stream);
 
 /*
  * One-box bound that allocates no device memory (the paper has no counterpart:

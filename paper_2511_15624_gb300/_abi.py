@@ -29,7 +29,7 @@ EXPORTED = (
     "ibp_status_string", "ibp_bound_noalloc", "ibp_case_set_screen", "ibp_case_last_live",
     "ibp_case_set_reduction", "ibp_case_set_refine", "ibp_case_reduction", "ibp_bound_paper",
     "ibp_set_alloc_limit", "ibp_bound_backward_lo", "ibp_case_set_ratings", "ibp_bound_linear",
-    "ibp_case_linear_slopes",
+    "ibp_case_linear_slopes", "ibp_case_linear_inherit", "ibp_bound_multi_backward",
 )
 
 
@@ -78,12 +78,16 @@ def lib():
         L.ibp_bound_backward_lo.restype = ctypes.c_int
         L.ibp_case_set_ratings.argtypes = [P, P, P, I32, P]
         L.ibp_case_set_ratings.restype = ctypes.c_int
-        L.ibp_bound_linear.argtypes = [P, I32, P, P, I32, D, P, P, P, I32, P]
+        L.ibp_bound_linear.argtypes = [P, I32, P, P, I32, D, I32, P, P, P, I32, P]
+        L.ibp_case_linear_inherit.argtypes = [P, I32, P]
+        L.ibp_case_linear_inherit.restype = ctypes.c_int
         L.ibp_bound_linear.restype = ctypes.c_int
         L.ibp_case_linear_slopes.argtypes = [P, I32, P, P, P]
         L.ibp_case_linear_slopes.restype = ctypes.c_int
         L.ibp_bound_multi.argtypes = [I32, P, P, P, P, P, P, P, P]
         L.ibp_bound_multi.restype = ctypes.c_int
+        L.ibp_bound_multi_backward.argtypes = [I32, P, P, P, P, P, P, P, P, I32, P]
+        L.ibp_bound_multi_backward.restype = ctypes.c_int
         L.ibp_bound_noalloc.argtypes = [P, P, P, P, P, P, P]
         L.ibp_bound_noalloc.restype = ctypes.c_int
         L.ibp_case_sync.argtypes = [P]
@@ -226,6 +230,20 @@ def ibp_bound_multi(handles, n_box, box_lo, box_hi, obj_lo, obj_hi, obj_err, str
     _check(st)
 
 
+def ibp_bound_multi_backward(handles, n_box, box_lo, box_hi, grad_obj, grad_lo, grad_hi,
+                             grad_rating=None, side=0, stream=None):
+    n = len(handles)
+    H = (ctypes.c_void_p * n)(*[ctypes.c_void_p(h) for h in handles])
+    NB = (ctypes.c_int32 * n)(*[int(b) for b in n_box])
+
+    def arr(xs):
+        return (ctypes.c_void_p * n)(*[ctypes.c_void_p(_ptr(x)) for x in xs])
+    GR = None if grad_rating is None else arr(grad_rating)
+    st = lib().ibp_bound_multi_backward(n, H, NB, arr(box_lo), arr(box_hi), arr(grad_obj), arr(grad_lo),
+                                        arr(grad_hi), GR, int(side), stream)
+    _check(st)
+
+
 def ibp_bound_noalloc(handle, box_lo, box_hi, obj_lo, obj_hi, obj_err, stream=None):
     """One-box bound with no device allocation; all pointers are device pointers."""
     st = lib().ibp_bound_noalloc(ctypes.c_void_p(handle), _ptr(box_lo), _ptr(box_hi), _ptr(obj_lo),
@@ -303,10 +321,16 @@ def ibp_selftest_wait_timeout(device: int, limit_us: int) -> int:
 
 
 def ibp_bound_linear(handle, n_box, box_lo, box_hi, n_iter, primal_weight, obj_hi, obj_err,
-                     x_point=None, ptr_mode=0, stream=None):
+                     x_point=None, ptr_mode=0, stream=None, warm=0):
+    """warm: 0 cold, 1 + f to continue the held boxes [f, f + n_box)."""
     _check(lib().ibp_bound_linear(ctypes.c_void_p(handle), int(n_box), _ptr(box_lo), _ptr(box_hi),
-                                  int(n_iter), float(primal_weight), _ptr(obj_hi), _ptr(obj_err),
-                                  _ptr(x_point), int(ptr_mode), stream))
+                                  int(n_iter), float(primal_weight), int(warm), _ptr(obj_hi),
+                                  _ptr(obj_err), _ptr(x_point), int(ptr_mode), stream))
+
+
+def ibp_case_linear_inherit(handle, parent):
+    par = np.ascontiguousarray(parent, np.int32)
+    _check(lib().ibp_case_linear_inherit(ctypes.c_void_p(handle), par.size, _ptr(par)))
 
 
 def ibp_case_linear_slopes(handle, n_box, n_ctg, n_line):

@@ -54,6 +54,49 @@ class IBPBoundFunction(torch.autograd.Function):
         return glo, ghi, (grat.sum(dim=0) if want_r else None), None
 
 
+class IBPBoundMultiFunction(torch.autograd.Function):
+    """Many cases of uneven size: forward in one persistent launch
+    (``ibp_bound_multi``), backward through ``ibp_bound_multi_backward``
+    (one launch per backward pass over all cases).  Inputs after ``cases``:
+    box_lo_0, box_hi_0, box_lo_1, box_hi_1, ...; outputs: obj_lo_0,
+    obj_hi_0, obj_lo_1, obj_hi_1, ..."""
+
+    @staticmethod
+    def forward(ctx, cases, *boxes):
+        from .case import bound_multi
+        los = [b.detach().contiguous().to(torch.float64) for b in boxes[0::2]]
+        his = [b.detach().contiguous().to(torch.float64) for b in boxes[1::2]]
+        outs = bound_multi(list(cases), los, his)
+        ctx.cases = list(cases)
+        ctx.save_for_backward(*[t for pair in zip(los, his) for t in pair])
+        return tuple(t for o in outs for t in (o[0], o[1]))
+
+    @staticmethod
+    def backward(ctx, *grads):
+        from .case import bound_multi_backward
+        saved = ctx.saved_tensors
+        los, his = list(saved[0::2]), list(saved[1::2])
+        g_lo = [torch.zeros_like(lo) for lo in los]
+        g_hi = [torch.zeros_like(hi) for hi in his]
+        for side, gs in (("hi", grads[1::2]), ("lo", grads[0::2])):
+            if all(g is None for g in gs):
+                continue
+            gobj = [torch.zeros(lo.shape[0], dtype=torch.float64, device=lo.device) if g is None
+                    else g.detach().to(torch.float64) for g, lo in zip(gs, los)]
+            for i, (a, b, _) in enumerate(bound_multi_backward(ctx.cases, los, his, gobj, side=side)):
+                g_lo[i] += a
+                g_hi[i] += b
+        return (None,) + tuple(t for pair in zip(g_lo, g_hi) for t in pair)
+
+
+def ibp_bound_multi(cases, box_lo, box_hi):
+    """Differentiable [(obj_lo, obj_hi)] of many cases, one persistent launch
+    forward and one batched adjoint backward."""
+    flat = [t for pair in zip(box_lo, box_hi) for t in pair]
+    out = IBPBoundMultiFunction.apply(tuple(cases), *flat)
+    return [(out[2 * i], out[2 * i + 1]) for i in range(len(cases))]
+
+
 def ibp_bound(case: Case, box_lo: torch.Tensor, box_hi: torch.Tensor,
               rating: Optional[torch.Tensor] = None):
     """Differentiable (obj_lo, obj_hi) of every box; gradients flow to the box
@@ -61,4 +104,4 @@ def ibp_bound(case: Case, box_lo: torch.Tensor, box_hi: torch.Tensor,
     return IBPBoundFunction.apply(box_lo, box_hi, rating, case)
 
 
-__all__ = ["IBPBoundFunction", "ibp_bound"]
+__all__ = ["IBPBoundFunction", "IBPBoundMultiFunction", "ibp_bound", "ibp_bound_multi"]

@@ -146,12 +146,15 @@ class Case:
         fn(self._h, nb, lo, hi, g, glo, ghi, gr, ptr_mode=0, stream=None)
         return (glo, ghi) + ((gr,) if want_rating else ())
 
-    def bound_linear(self, lo, hi, n_iter: int = 20000, primal_weight: float = 1.0, stream=None):
+    def bound_linear(self, lo, hi, n_iter: int = 20000, primal_weight: float = 1.0, stream=None,
+                     warm: bool = False, first: int = 0):
         """Linear (CROWN-style) relaxation bound with optimised slopes
         (``ibp_bound_linear``): returns (obj_hi, obj_err, x_point) -- the
         certified upper bound of max f, its rounding bound and the averaged
         primal point -- as numpy arrays for numpy boxes, CUDA tensors for CUDA
-        boxes (enqueued on the stream)."""
+        boxes (enqueued on the stream).  warm=True continues the held state of
+        boxes [first, first + n_box)."""
+        warm = (1 + int(first)) if warm else 0
         if _abi._is_cuda_tensor(lo):
             import torch
             lo = lo.contiguous().to(torch.float64)
@@ -162,14 +165,19 @@ class Case:
             xp = torch.empty_like(lo)
             s = stream if stream is not None else torch.cuda.current_stream(lo.device).cuda_stream
             _abi.ibp_bound_linear(self._h, nb, lo, hi, n_iter, primal_weight, ub, err, xp, ptr_mode=1,
-                                  stream=s)
+                                  stream=s, warm=warm)
             return ub, err, xp
         lo = np.ascontiguousarray(np.atleast_2d(lo), np.float64)
         hi = np.ascontiguousarray(np.atleast_2d(hi), np.float64)
         nb = lo.shape[0]
         ub, err, xp = np.empty(nb), np.empty(nb), np.empty_like(lo)
-        _abi.ibp_bound_linear(self._h, nb, lo, hi, n_iter, primal_weight, ub, err, xp, ptr_mode=0)
+        _abi.ibp_bound_linear(self._h, nb, lo, hi, n_iter, primal_weight, ub, err, xp, ptr_mode=0,
+                              warm=warm)
         return ub, err, xp
+
+    def linear_inherit(self, parent):
+        """Box j of the next warm ``bound_linear`` continues from box parent[j]."""
+        _abi.ibp_case_linear_inherit(self._h, parent)
 
     def linear_slopes(self, n_box: int = 1):
         """(a_ctg, a_base, a_inj) of the last ``bound_linear`` call."""
@@ -266,3 +274,27 @@ def bound_multi(cases, box_lo, box_hi, stream=None):
     _abi.ibp_bound_multi([c.handle for c in cases], [int(x.shape[0]) for x in los], los, his,
                          [o[0] for o in outs], [o[1] for o in outs], [o[2] for o in outs], stream=s)
     return outs
+
+
+def bound_multi_backward(cases, box_lo, box_hi, grad_obj, side: str = "hi", want_rating: bool = False,
+                         stream=None):
+    """Adjoint of many cases' bounds (``ibp_bound_multi_backward``): the
+    forward pass in one persistent launch over all cases, then one launch per
+    backward pass over every (case, box).  ``grad_obj[i]`` [n_box_i] is
+    d loss / d obj_hi (side "hi") or d loss / d obj_lo (side "lo").  Returns a
+    list of (grad_lo, grad_hi, grad_rating or None) per case, CUDA tensors
+    enqueued on ``stream``."""
+    import torch
+    if side not in ("hi", "lo"):
+        raise ValueError("side must be 'hi' or 'lo'")
+    los = [lo.contiguous().to(torch.float64) for lo in box_lo]
+    his = [hi.contiguous().to(torch.float64) for hi in box_hi]
+    gs = [g.contiguous().to(torch.float64) for g in grad_obj]
+    glo = [torch.empty_like(lo) for lo in los]
+    ghi = [torch.empty_like(hi) for hi in his]
+    grat = [torch.empty(lo.shape[0], c.n_line, dtype=torch.float64, device=lo.device)
+            for c, lo in zip(cases, los)] if want_rating else None
+    s = stream if stream is not None else torch.cuda.current_stream(los[0].device).cuda_stream
+    _abi.ibp_bound_multi_backward([c.handle for c in cases], [int(x.shape[0]) for x in los], los, his, gs,
+                                  glo, ghi, grat, side=0 if side == "hi" else 1, stream=s)
+    return [(glo[i], ghi[i], None if grat is None else grat[i]) for i in range(len(cases))]

@@ -133,7 +133,7 @@ struct ibp_case {
     DevBuf<double> lc64, lR64;  // paper-mode refinement: per-line FP64 centre and radius
     DevBuf<float> lX;
     // linear (CROWN-style) relaxation bound: iteration state and certified value
-    int lin_cap_box = 0;
+    int lin_cap_box = 0, lin_state_box = 0;  // boxes the workspace holds / the state describes
     double lin_step = 0.0;                 // 0.9 / ||D K||, measured once per case
     DevBuf<int> cl_ptr, cl_ctg;            // contingencies per outaged line
     DevBuf<double> lw, lx, lsx, lxb, lx_last, la0, ls0, la0_last, lstot, lred, lub, lub_err, lbest;
@@ -1236,6 +1236,7 @@ static ibp_status ensure_bwd_workspace(ibp_case *c, int n_box) {
     CUDA_TRY(c->dr.alloc((size_t)cap * c->n_a_pad));
     CUDA_TRY(c->grads.alloc((size_t)cap * (2 * c->n_dev + c->n_line + 1)));
     c->bwd_cap_box = cap;
+    ++c->ws_gen;  // cached many-case plans hold these pointers
     return IBP_OK;
 }
 
@@ -1250,6 +1251,7 @@ static ibp_status ensure_bwd_lo_workspace(ibp_case *c, int n_box) {
     CUDA_TRY(c->act_count_lo.alloc(cap));
     CUDA_TRY(c->act_list_lo.alloc((size_t)cap * c->act_cap_lo));
     c->bwd_lo_cap_box = cap;
+    ++c->ws_gen;
     return IBP_OK;
 }
 
@@ -1383,7 +1385,9 @@ static ibp_status ensure_lin_workspace(ibp_case *c, int n_box) {
     return IBP_OK;
 }
 
-static LinArgs lin_args(const ibp_case *c, int n_box, const double *lo, const double *hi) {
+// first: the held box whose state the call's box 0 uses (the iteration state
+// is box-major; the scratch buffers always start at box 0)
+static LinArgs lin_args(const ibp_case *c, int n_box, const double *lo, const double *hi, int first = 0) {
     LinArgs a{};
     a.n_l = c->n_line; a.n_c = c->n_ctg; a.n_a = c->n_a; a.n_a_pad = c->n_a_pad; a.n_dev = c->n_dev;
     a.n_gen = c->n_gen; a.n_box = n_box;
@@ -1401,6 +1405,14 @@ static LinArgs lin_args(const ibp_case *c, int n_box, const double *lo, const do
     a.g = c->lg.p; a.red = c->lred.p;
     a.W64 = c->lW64.p; a.Wabs = c->lWabs.p; a.constl = c->lconst.p; a.rd64 = c->lrd64.p;
     a.rda = c->lrda.p; a.g64 = c->lg64.p; a.G64 = c->lG64.p; a.ub = c->lub.p; a.ub_err = c->lub_err.p;
+    if (first > 0) {
+        const size_t f = (size_t)first, fd = f * c->n_dev, fl = f * c->n_line;
+        const size_t fc = f * std::max(c->n_ctg, 1) * c->n_line;
+        a.w += f; a.x += fd; a.sx += fd; a.x_last += fd;
+        a.a_c += fc; a.s_c += fc; a.c_last += fc;
+        a.a_b += fl; a.s_b += fl; a.b_last += fl;
+        a.a0 += f; a.s0 += f; a.a0_last += f;
+    }
     return a;
 }
 
@@ -1420,6 +1432,21 @@ __global__ void k_lin_init(int n, const double *lo, const double *hi, double *x,
 }
 
 // keep the smaller certified bound of each box (and its error bound)
+// warm start: points clipped into their boxes, running sums of the points at 0,
+// best bound +inf (the slopes, sums and primal weight stay)
+__global__ void k_lin_warm(int n, const double *lo, const double *hi, double *x, double *x_last,
+                           int n_box, double *best) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        x[i] = fmin(fmax(x[i], lo[i]), hi[i]);
+        x_last[i] = x[i];
+    }
+    if (i < n_box) {
+        best[2 * i] = INFINITY;
+        best[2 * i + 1] = 0.0;
+    }
+}
+
 __global__ void k_lin_best(int n_box, const double *ub, const double *err, double *best) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j < n_box && ub[j] < best[2 * j]) {
@@ -1440,7 +1467,11 @@ constexpr int kLinRestart = 1000;   // iterations between restarts (and certifie
 constexpr int kLinChunk = 50;       // iterations per CUDA graph launch
 
 static ibp_status lin_run(ibp_case *c, int n_box, const double *lo, const double *hi, int n_iter,
-                          double w0, double *obj_hi, double *obj_err, double *x_point, cudaStream_t s) {
+                          double w0, double *obj_hi, double *obj_err, double *x_point, cudaStream_t s,
+                          bool warm = false, int first = 0) {
+    if (warm && (first < 0 || n_box > c->lin_state_box - first))
+        return fail(IBP_EINVAL, "no linear state for boxes [%d, %d) to continue from (%d held)", first,
+                    first + n_box, c->lin_state_box);
     ibp_status st = ensure_lin_workspace(c, n_box);
     if (st != IBP_OK) return st;
     const size_t nd = (size_t)n_box * c->n_dev, np = (size_t)n_box * std::max(c->n_ctg, 1) * c->n_line;
@@ -1460,6 +1491,14 @@ static ibp_status lin_run(ibp_case *c, int n_box, const double *lo, const double
         if (!(lam > 0.0) || !std::isfinite(lam)) return fail(IBP_ECUDA, "power iteration gave no norm");
         c->lin_step = 0.9 / std::sqrt(lam);
     }
+    if (warm) {
+        // continue from the state held for these boxes: the points are moved
+        // into their (possibly smaller) boxes; the best bound restarts
+        const size_t fd = (size_t)first * c->n_dev;
+        k_lin_warm<<<(unsigned)((std::max(nd, (size_t)n_box) + 255) / 256), 256, 0, s>>>(
+            (int)nd, lo, hi, c->lx.p + fd, c->lx_last.p + fd, n_box, c->lbest.p);
+        CUDA_TRY(cudaGetLastError());
+    } else {
     k_lin_init<<<(unsigned)((std::max(nd, (size_t)n_box) + 255) / 256), 256, 0, s>>>(
         (int)nd, lo, hi, c->lx.p, c->lx_last.p, n_box, c->lw.p, w0, c->lbest.p);
     CUDA_TRY(cudaGetLastError());
@@ -1472,7 +1511,20 @@ static ibp_status lin_run(ibp_case *c, int n_box, const double *lo, const double
     CUDA_TRY(zero(c->la0_last.p, n_box * sizeof(double)));
     CUDA_TRY(zero(c->lred.p, (size_t)n_box * 4 * sizeof(double)));
     CUDA_TRY(zero(c->lg.p, (size_t)n_box * c->n_a_pad * sizeof(float)));
-    LinArgs a = lin_args(c, n_box, lo, hi);
+    }
+    // the state is box-major: a warm call on held boxes [first, first + n_box)
+    // leaves the rest of the held state as it was
+    if (!warm) c->lin_state_box = n_box;
+    LinArgs a = lin_args(c, n_box, lo, hi, warm ? first : 0);
+    if (warm) {
+        // the dual gradient g of the inherited slopes (the iteration's first x
+        // step uses it), and the certified value at those slopes: on a sub-box
+        // it is at most the parent's, so a continued bound never rises
+        CUDA_TRY(lin_gradient(a, c->num_sms, s));
+        CUDA_TRY(lin_certify(a, c->num_sms, s));
+        k_lin_best<<<(n_box + 127) / 128, 128, 0, s>>>(n_box, c->lub.p, c->lub_err.p, c->lbest.p);
+        CUDA_TRY(cudaGetLastError());
+    }
     // a chunk of iterations as one CUDA graph, captured on a private stream
     // (the arguments hold this call's box pointers, so each call captures anew)
     const int chunk = std::min(kLinChunk, kLinRestart);
@@ -1512,23 +1564,24 @@ static ibp_status lin_run(ibp_case *c, int n_box, const double *lo, const double
             CUDA_TRY(cudaGetLastError());
         }
     }
-    if (n_iter == 0) {
+    if (n_iter == 0 && !warm) {
         CUDA_TRY(lin_certify(a, c->num_sms, s));
         k_lin_best<<<(n_box + 127) / 128, 128, 0, s>>>(n_box, c->lub.p, c->lub_err.p, c->lbest.p);
     }
     k_lin_out<<<(n_box + 127) / 128, 128, 0, s>>>(n_box, c->lbest.p, obj_hi, obj_err);
     CUDA_TRY(cudaGetLastError());
-    if (x_point) CUDA_TRY(cudaMemcpyAsync(x_point, c->lx.p, nd * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (x_point) CUDA_TRY(cudaMemcpyAsync(x_point, a.x, nd * sizeof(double), cudaMemcpyDeviceToDevice, s));
     return mark_done(c, s);
 }
 
 extern "C" ibp_status ibp_bound_linear(ibp_case *c, int32_t n_box, const double *box_lo,
                                        const double *box_hi, int32_t n_iter, double primal_weight,
-                                       double *obj_hi, double *obj_err, double *x_point,
-                                       int32_t ptr_mode, void *cuda_stream) {
+                                       int32_t warm, double *obj_hi, double *obj_err,
+                                       double *x_point, int32_t ptr_mode, void *cuda_stream) {
     if (!c) return fail(IBP_EINVAL, "case is NULL");
     if (n_box < 0 || n_box > kMaxBoxesPerCall) return fail(IBP_EINVAL, "n_box must be in [0, %d]", kMaxBoxesPerCall);
     if (n_iter < 0) return fail(IBP_EINVAL, "n_iter must be >= 0");
+    if (warm < 0) return fail(IBP_EINVAL, "warm must be >= 0");
     if (!(primal_weight > 0.0) || !std::isfinite(primal_weight))
         return fail(IBP_EINVAL, "primal_weight must be finite and > 0");
     if (ptr_mode != 0 && ptr_mode != 1) return fail(IBP_EINVAL, "ptr_mode must be 0 or 1");
@@ -1545,7 +1598,9 @@ extern "C" ibp_status ibp_bound_linear(ibp_case *c, int32_t n_box, const double 
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     ibp_status st = ensure_workspace(c, n_box);
     if (st != IBP_OK) return st;
-    if (ptr_mode == 1) return lin_run(c, n_box, box_lo, box_hi, n_iter, primal_weight, obj_hi, obj_err, x_point, s);
+    if (ptr_mode == 1)
+        return lin_run(c, n_box, box_lo, box_hi, n_iter, primal_weight, obj_hi, obj_err, x_point, s, warm != 0,
+                       warm - 1);
     const size_t nd = (size_t)n_box * c->n_dev;
     CUDA_TRY(cudaMemcpyAsync(c->box_lo.p, box_lo, nd * sizeof(double), cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaMemcpyAsync(c->box_hi.p, box_hi, nd * sizeof(double), cudaMemcpyHostToDevice, s));
@@ -1553,12 +1608,90 @@ extern "C" ibp_status ibp_bound_linear(ibp_case *c, int32_t n_box, const double 
     DevBuf<double> dx;
     if (x_point) CUDA_TRY(dx.alloc(nd));
     st = lin_run(c, n_box, c->box_lo.p, c->box_hi.p, n_iter, primal_weight, dobj, dobj + n_box,
-                 x_point ? dx.p : nullptr, s);
+                 x_point ? dx.p : nullptr, s, warm != 0, warm - 1);
     if (st != IBP_OK) return st;
     CUDA_TRY(cudaMemcpyAsync(obj_hi, dobj, n_box * sizeof(double), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaMemcpyAsync(obj_err, dobj + n_box, n_box * sizeof(double), cudaMemcpyDeviceToHost, s));
     if (x_point) CUDA_TRY(cudaMemcpyAsync(x_point, dx.p, nd * sizeof(double), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
+    return ok();
+}
+
+// Rearranges the linear state for a new list of boxes: box j takes the state
+// (slopes, running sums, point, primal weight) of box parent[j] (host array).
+__global__ void k_lin_gather_f(const float *src, float *dst, const int *parent, int n_new, size_t per) {
+    const size_t tot = (size_t)n_new * per;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = src[(size_t)parent[i / per] * per + i % per];
+}
+__global__ void k_lin_gather_d(const double *src, double *dst, const int *parent, int n_new, size_t per) {
+    const size_t tot = (size_t)n_new * per;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = src[(size_t)parent[i / per] * per + i % per];
+}
+
+extern "C" ibp_status ibp_case_linear_inherit(ibp_case *c, int32_t n_new, const int32_t *parent) {
+    if (!c || !parent) return fail(IBP_EINVAL, "NULL argument");
+    if (c->device < 0) return fail(IBP_ENOTSUP, "dry-run case");
+    if (n_new < 1 || n_new > kMaxBoxesPerCall) return fail(IBP_EINVAL, "n_new must be in [1, %d]", kMaxBoxesPerCall);
+    for (int j = 0; j < n_new; ++j)
+        if (parent[j] < 0 || parent[j] >= c->lin_state_box)
+            return fail(IBP_EINVAL, "parent[%d] = %d is not a box of the linear state (%d boxes)", j, parent[j],
+                        c->lin_state_box);
+    DeviceGuard guard(c->device);
+    if (!guard.ok) return fail(IBP_ECUDA, "cannot select device %d", c->device);
+    ibp_status st = wait_case(c);
+    if (st != IBP_OK) return st;
+    const int old_cap = c->lin_cap_box;
+    DevBuf<int> dpar;
+    CUDA_TRY(dpar.alloc(n_new));
+    CUDA_TRY(cudaMemcpy(dpar.p, parent, n_new * sizeof(int), cudaMemcpyHostToDevice));
+    const size_t pc = (size_t)std::max(c->n_ctg, 1) * c->n_line;
+    // gather into fresh buffers, then replace the old ones
+    auto gf = [&](DevBuf<float> &b, size_t per) -> ibp_status {
+        DevBuf<float> t;
+        CUDA_TRY(t.alloc((size_t)std::max(n_new, old_cap) * per));
+        k_lin_gather_f<<<c->num_sms * 8, 256>>>(b.p, t.p, dpar.p, n_new, per);
+        CUDA_TRY(cudaGetLastError());
+        CUDA_TRY(cudaDeviceSynchronize());
+        std::swap(b.p, t.p);
+        std::swap(b.n, t.n);
+        return IBP_OK;
+    };
+    auto gd = [&](DevBuf<double> &b, size_t per) -> ibp_status {
+        DevBuf<double> t;
+        CUDA_TRY(t.alloc((size_t)std::max(n_new, old_cap) * per));
+        k_lin_gather_d<<<c->num_sms * 8, 256>>>(b.p, t.p, dpar.p, n_new, per);
+        CUDA_TRY(cudaGetLastError());
+        CUDA_TRY(cudaDeviceSynchronize());
+        std::swap(b.p, t.p);
+        std::swap(b.n, t.n);
+        return IBP_OK;
+    };
+    if ((st = gf(c->lac, pc)) || (st = gf(c->lsc, pc)) || (st = gf(c->lc_last, pc)) ||
+        (st = gf(c->lab, c->n_line)) || (st = gf(c->lsb, c->n_line)) || (st = gf(c->lb_last, c->n_line)) ||
+        (st = gd(c->la0, 1)) || (st = gd(c->ls0, 1)) || (st = gd(c->la0_last, 1)) || (st = gd(c->lw, 1)) ||
+        (st = gd(c->lx, c->n_dev)) || (st = gd(c->lsx, c->n_dev)))
+        return st;
+    CUDA_TRY(cudaDeviceSynchronize());
+    // the other per-box buffers only need the room
+    if (n_new > old_cap) {
+        c->lin_cap_box = old_cap;  // ensure_lin_workspace grows the rest (its state buffers are resized above)
+        const size_t nd = (size_t)n_new * c->n_dev, nl = (size_t)n_new * c->n_line;
+        const size_t na = (size_t)n_new * c->n_a_pad, nc = (size_t)n_new * std::max(c->n_ctg, 1);
+        CUDA_TRY(c->lx_last.alloc(nd)); CUDA_TRY(c->lxb.alloc(nd));
+        CUDA_TRY(c->lstot.alloc(n_new)); CUDA_TRY(c->lred.alloc((size_t)n_new * 4));
+        CUDA_TRY(c->lub.alloc(n_new)); CUDA_TRY(c->lub_err.alloc(n_new)); CUDA_TRY(c->lbest.alloc((size_t)n_new * 2));
+        CUDA_TRY(c->lp.alloc(na)); CUDA_TRY(c->lf.alloc(nl)); CUDA_TRY(c->lcol.alloc(nl));
+        CUDA_TRY(c->lrow.alloc(nc)); CUDA_TRY(c->lg.alloc(na));
+        CUDA_TRY(c->lW64.alloc(nl)); CUDA_TRY(c->lWabs.alloc(nl)); CUDA_TRY(c->lconst.alloc(nl));
+        CUDA_TRY(c->lrd64.alloc(nc)); CUDA_TRY(c->lrda.alloc(nc)); CUDA_TRY(c->lg64.alloc(na));
+        CUDA_TRY(c->lG64.alloc(na));
+        c->lin_cap_box = n_new;
+        ++c->ws_gen;
+    }
+    CUDA_TRY(cudaMemset(c->lred.p, 0, (size_t)c->lin_cap_box * 4 * sizeof(double)));
+    c->lin_state_box = n_new;
     return ok();
 }
 
@@ -1665,11 +1798,17 @@ struct MultiPlan {
     DevBuf<int4> refq;
     DevBuf<int> refq_cnt;
     DevBuf<double2> refq_res;
+    // 0: plain bound; 1 + side: the forward pass of a backward, recording the
+    // side's active pairs, with the backward's (case, box) items and arguments
+    int record = 0;
+    int n_items = 0, max_n_a_pad = 0;
+    DevBuf<BwdArgs> bargs;
+    DevBuf<int2> bitems;
     ~MultiPlan() {
         if (device >= 0) {
             DeviceGuard g(device);
             items.free(); cta_start.free(); err.free(); prefix.free(); args.free(); maps.free();
-            refq.free(); refq_cnt.free(); refq_res.free();
+            refq.free(); refq_cnt.free(); refq_res.free(); bargs.free(); bitems.free();
         }
     }
 };
@@ -1687,7 +1826,7 @@ static void drop_plans_of(const ibp_case *c) {
 }
 
 static CtgArgs multi_args(const ibp_case *c, int n_box, int BL, int BK, int CH, bool reduced,
-                          int rows_per_item) {
+                          int rows_per_item, int record) {
     const int n_box_pad = (n_box + kBoxTile - 1) / kBoxTile * kBoxTile;
     const int n_rows = reduced ? c->n_nb : c->n_line;
     const int tiles_l = (n_rows + BL - 1) / BL, tiles_k = (c->n_ctg + BK - 1) / BK;
@@ -1709,7 +1848,30 @@ static CtgArgs multi_args(const ibp_case *c, int n_box, int BL, int BK, int CH, 
         ca.live = c->nb_list.p;
         ca.n_live = c->nb_count.p;
     }
+    if (record == 1) {
+        ca.act_count = c->act_count.p;
+        ca.act_list = c->act_list.p;
+        ca.act_cap = c->act_cap;
+    } else if (record == 2) {
+        ca.act_count_lo = c->act_count_lo.p;
+        ca.act_list_lo = c->act_list_lo.p;
+        ca.act_cap_lo = c->act_cap_lo;
+    }
     return ca;
+}
+
+// the backward's arguments of one case without the per-call pointers
+static BwdArgs bwd_args(const ibp_case *c, int n_box, int side) {
+    BwdArgs b{};
+    b.n_l = c->n_line; b.n_a = c->n_a; b.n_a_pad = c->n_a_pad; b.n_dev = c->n_dev; b.n_gen = c->n_gen;
+    b.n_box = n_box; b.side = side;
+    b.act_cap = side ? c->act_cap_lo : c->act_cap; b.phi = c->phi_a.p;
+    b.act_count = side ? c->act_count_lo.p : c->act_count.p;
+    b.act_list = side ? c->act_list_lo.p : c->act_list.p;
+    b.W = c->W.p; b.cnt = c->cnt.p; b.dc = c->dc.p; b.dr = c->dr.p;
+    b.dev_col = c->dev_col.p; b.seg_ptr = c->seg_ptr.p;
+    b.slope = c->slope.p; b.bkpt = c->bkpt.p; b.zeta_inj = c->zeta_inj; b.zeta_f = c->zeta_f;
+    return b;
 }
 
 // the many-case launch uses the static part of the network reduction: every
@@ -1736,7 +1898,7 @@ static ibp_status ensure_nonbridge_rows(ibp_case *c) {
 }
 
 static ibp_status build_plan(ibp_case *const *cases, const int32_t *n_box, int n_case, int num_sms,
-                             MultiPlan **out) {
+                             int record, MultiPlan **out) {
     int BL, BK, CH;
     multi_tile_shape(&BL, &BK, &CH);
     std::unique_ptr<MultiPlan> P(new MultiPlan());
@@ -1754,7 +1916,7 @@ static ibp_status build_plan(ibp_case *const *cases, const int32_t *n_box, int n
         P->gens.push_back(c->ws_gen);
         const bool red = multi_reduced(c);
         P->reduced.push_back(red ? 1 : 0);
-        args[i] = multi_args(c, n_box[i], BL, BK, CH, red, P->rows_per_item);
+        args[i] = multi_args(c, n_box[i], BL, BK, CH, red, P->rows_per_item, record);
         const int n_box_pad = args[i].n_box_pad;
         const int w = red ? c->n_r_pad : c->n_a_pad;
         const float *rows = red ? c->phi_nb.p : c->phi_a.p;
@@ -1820,13 +1982,28 @@ static ibp_status build_plan(ibp_case *const *cases, const int32_t *n_box, int n
     CUDA_TRY(cudaMemcpy(P->prefix.p, prefix.data(), prefix.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(P->args.p, args.data(), args.size() * sizeof(CtgArgs), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(P->maps.p, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice));
+    P->record = record;
+    if (record) {
+        std::vector<BwdArgs> bargs(n_case);
+        std::vector<int2> bitems;
+        for (int i = 0; i < n_case; ++i) {
+            bargs[i] = bwd_args(cases[i], n_box[i], record - 1);
+            P->max_n_a_pad = std::max(P->max_n_a_pad, cases[i]->n_a_pad);
+            for (int j = 0; j < n_box[i]; ++j) bitems.push_back(make_int2(i, j));
+        }
+        P->n_items = (int)bitems.size();
+        CUDA_TRY(P->bargs.alloc(bargs.size()));
+        CUDA_TRY(P->bitems.alloc(bitems.size()));
+        CUDA_TRY(cudaMemcpy(P->bargs.p, bargs.data(), bargs.size() * sizeof(BwdArgs), cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(P->bitems.p, bitems.data(), bitems.size() * sizeof(int2), cudaMemcpyHostToDevice));
+    }
     *out = P.release();
     return IBP_OK;
 }
 
-static MultiPlan *find_plan(ibp_case *const *cases, const int32_t *n_box, int n_case) {
+static MultiPlan *find_plan(ibp_case *const *cases, const int32_t *n_box, int n_case, int record) {
     for (auto &p : g_plans) {
-        if ((int)p->cases.size() != n_case || p->variant != cases[0]->variant) continue;
+        if ((int)p->cases.size() != n_case || p->variant != cases[0]->variant || p->record != record) continue;
         bool same = true;
         for (int i = 0; i < n_case && same; ++i)
             same = p->cases[i] == cases[i] && p->n_box[i] == n_box[i] && p->gens[i] == cases[i]->ws_gen &&
@@ -1836,44 +2013,50 @@ static MultiPlan *find_plan(ibp_case *const *cases, const int32_t *n_box, int n_
     return nullptr;
 }
 
-extern "C" ibp_status ibp_bound_multi(int32_t n_case, ibp_case *const *cases, const int32_t *n_box,
-                                      const double *const *box_lo, const double *const *box_hi,
-                                      double *const *obj_lo, double *const *obj_hi,
-                                      double *const *obj_err, void *cuda_stream) {
+static ibp_status check_multi_args(int32_t n_case, ibp_case *const *cases, const int32_t *n_box,
+                                   const double *const *box_lo, const double *const *box_hi) {
     if (n_case < 0) return fail(IBP_EINVAL, "n_case must be >= 0");
-    if (n_case == 0) return ok();
-    if (!cases || !n_box || !box_lo || !box_hi || !obj_lo || !obj_hi || !obj_err)
-        return fail(IBP_EINVAL, "array arguments must not be NULL");
+    if (n_case == 0) return IBP_OK;
+    if (!cases || !n_box || !box_lo || !box_hi) return fail(IBP_EINVAL, "array arguments must not be NULL");
     for (int i = 0; i < n_case; ++i) {
         if (!cases[i]) return fail(IBP_EINVAL, "case %d is NULL", i);
         if (cases[i]->device < 0) return fail(IBP_ENOTSUP, "case %d was created without a device", i);
         if (cases[i]->device != cases[0]->device) return fail(IBP_EINVAL, "cases live on different devices");
         if (n_box[i] < 1 || n_box[i] > kMaxBoxesPerCall)
             return fail(IBP_EINVAL, "n_box[%d] must be in [1, %d]", i, kMaxBoxesPerCall);
-        if (!box_lo[i] || !box_hi[i] || !obj_lo[i] || !obj_hi[i] || !obj_err[i])
-            return fail(IBP_EINVAL, "pointers of case %d must not be NULL", i);
+        if (!box_lo[i] || !box_hi[i]) return fail(IBP_EINVAL, "box pointers of case %d must not be NULL", i);
         for (int j = 0; j < i; ++j)
             if (cases[j] == cases[i]) return fail(IBP_EINVAL, "case %d appears twice", i);
     }
-    DeviceGuard guard(cases[0]->device);
-    if (!guard.ok) return fail(IBP_ECUDA, "cannot select device %d", cases[0]->device);
-    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    return IBP_OK;
+}
+
+// the many-case forward pass (record: 0 plain, 1 + side: record the side's
+// active pairs for a backward); returns the plan it ran
+static ibp_status enqueue_multi(int32_t n_case, ibp_case *const *cases, const int32_t *n_box,
+                                const double *const *box_lo, const double *const *box_hi,
+                                double *const *obj_lo, double *const *obj_hi, double *const *obj_err,
+                                cudaStream_t s, int record, MultiPlan **plan_out) {
     ibp_status st;
     for (int i = 0; i < n_case; ++i) {
         if ((st = ensure_workspace(cases[i], n_box[i])) != IBP_OK) return st;
         if (multi_reduced(cases[i]) &&
             ((st = ensure_class_ws(cases[i])) != IBP_OK || (st = ensure_nonbridge_rows(cases[i])) != IBP_OK))
             return st;
+        if (record && (st = ensure_bwd_workspace(cases[i], n_box[i])) != IBP_OK) return st;
+        if (record == 2 && (st = ensure_bwd_lo_workspace(cases[i], n_box[i])) != IBP_OK) return st;
     }
     MultiPlan *P = nullptr;
     {
         std::lock_guard<std::mutex> lk(g_plan_mu);
-        P = find_plan(cases, n_box, n_case);
+        P = find_plan(cases, n_box, n_case, record);
         if (!P) {
-            if ((st = build_plan(cases, n_box, n_case, cases[0]->num_sms, &P)) != IBP_OK) return st;
+            if ((st = build_plan(cases, n_box, n_case, cases[0]->num_sms, record, &P)) != IBP_OK) return st;
             g_plans.emplace_back(P);
         }
     }
+    if (plan_out) *plan_out = P;
+    if (record) CUDA_TRY(launch_bwd_zero_cases(P->bargs.p, P->bitems.p, P->n_items, true, s));
     CUDA_TRY(cudaMemsetAsync(P->err.p, 0, sizeof(int), s));
     // per-case box intervals and base flows
     for (int i = 0; i < n_case; ++i) {
@@ -1915,6 +2098,15 @@ extern "C" ibp_status ibp_bound_multi(int32_t n_case, ibp_case *const *cases, co
             bb.rate_c_dn = c->rate_c_dn.p;
         }
         bb.ref = ref_args(c);
+        if (record == 1) {
+            bb.act_count = c->act_count.p;
+            bb.act_list = c->act_list.p;
+            bb.act_cap = c->act_cap;
+        } else if (record == 2) {
+            bb.act_count_lo = c->act_count_lo.p;
+            bb.act_list_lo = c->act_list_lo.p;
+            bb.act_cap_lo = c->act_cap_lo;
+        }
         CUDA_TRY(launch_base(bb, c->n_part_base, s));
     }
     // one persistent launch over the contingency tiles of every case
@@ -1945,6 +2137,73 @@ extern "C" ibp_status ibp_bound_multi(int32_t n_case, ibp_case *const *cases, co
         aa.zeta_inj = c->zeta_inj; aa.zeta_f = c->zeta_f;
         aa.obj_lo = obj_lo[i]; aa.obj_hi = obj_hi[i]; aa.obj_err = obj_err[i]; aa.err = c->err.p;
         CUDA_TRY(launch_assemble(aa, s));
+        if ((st = mark_done(c, s)) != IBP_OK) return st;
+    }
+    return IBP_OK;
+}
+
+extern "C" ibp_status ibp_bound_multi(int32_t n_case, ibp_case *const *cases, const int32_t *n_box,
+                                      const double *const *box_lo, const double *const *box_hi,
+                                      double *const *obj_lo, double *const *obj_hi,
+                                      double *const *obj_err, void *cuda_stream) {
+    ibp_status st = check_multi_args(n_case, cases, n_box, box_lo, box_hi);
+    if (st != IBP_OK) return st;
+    if (n_case == 0) return ok();
+    if (!obj_lo || !obj_hi || !obj_err) return fail(IBP_EINVAL, "array arguments must not be NULL");
+    for (int i = 0; i < n_case; ++i)
+        if (!obj_lo[i] || !obj_hi[i] || !obj_err[i])
+            return fail(IBP_EINVAL, "pointers of case %d must not be NULL", i);
+    DeviceGuard guard(cases[0]->device);
+    if (!guard.ok) return fail(IBP_ECUDA, "cannot select device %d", cases[0]->device);
+    st = enqueue_multi(n_case, cases, n_box, box_lo, box_hi, obj_lo, obj_hi, obj_err,
+                       static_cast<cudaStream_t>(cuda_stream), 0, nullptr);
+    if (st != IBP_OK) return st;
+    return ok();
+}
+
+extern "C" ibp_status ibp_bound_multi_backward(int32_t n_case, ibp_case *const *cases, const int32_t *n_box,
+                                               const double *const *box_lo, const double *const *box_hi,
+                                               const double *const *grad_obj, double *const *grad_lo,
+                                               double *const *grad_hi, double *const *grad_rating,
+                                               int32_t side, void *cuda_stream) {
+    ibp_status st = check_multi_args(n_case, cases, n_box, box_lo, box_hi);
+    if (st != IBP_OK) return st;
+    if (side != 0 && side != 1) return fail(IBP_EINVAL, "side must be 0 (obj_hi) or 1 (obj_lo)");
+    if (n_case == 0) return ok();
+    if (!grad_obj || !grad_lo || !grad_hi) return fail(IBP_EINVAL, "array arguments must not be NULL");
+    long long n_items = 0;
+    for (int i = 0; i < n_case; ++i) {
+        if (!grad_obj[i] || !grad_lo[i] || !grad_hi[i])
+            return fail(IBP_EINVAL, "gradient pointers of case %d must not be NULL", i);
+        n_items += n_box[i];
+    }
+    if (n_items > 65535) return fail(IBP_EINVAL, "at most 65535 boxes over all cases (%lld given)", n_items);
+    DeviceGuard guard(cases[0]->device);
+    if (!guard.ok) return fail(IBP_ECUDA, "cannot select device %d", cases[0]->device);
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    // the forward pass, recording the side's active pairs; its objective goes
+    // to each case's scratch
+    std::vector<double *> olo(n_case), ohi(n_case), oerr(n_case);
+    for (int i = 0; i < n_case; ++i) {
+        if ((st = ensure_workspace(cases[i], n_box[i])) != IBP_OK) return st;
+        double *d = cases[i]->obj.p;
+        olo[i] = d;
+        ohi[i] = d + n_box[i];
+        oerr[i] = d + 2 * n_box[i];
+    }
+    MultiPlan *P = nullptr;
+    st = enqueue_multi(n_case, cases, n_box, box_lo, box_hi, olo.data(), ohi.data(), oerr.data(), s, 1 + side, &P);
+    if (st != IBP_OK) return st;
+    // weights, centre and radius passes of every (case, box) in one launch each
+    CUDA_TRY(launch_backward_cases(P->bargs.p, P->bitems.p, P->n_items, P->max_n_a_pad, s));
+    // the chain rule to each case's box endpoints
+    for (int i = 0; i < n_case; ++i) {
+        ibp_case *c = cases[i];
+        BwdArgs b = bwd_args(c, n_box[i], side);
+        b.box_lo = box_lo[i]; b.box_hi = box_hi[i];
+        b.grad_obj_hi = grad_obj[i]; b.grad_lo = grad_lo[i]; b.grad_hi = grad_hi[i];
+        b.grad_rating = grad_rating ? grad_rating[i] : nullptr;
+        CUDA_TRY(launch_bwd_chain(b, s));
         if ((st = mark_done(c, s)) != IBP_OK) return st;
     }
     return ok();

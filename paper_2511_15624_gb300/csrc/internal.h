@@ -264,6 +264,7 @@ cudaError_t lin_iteration(const LinArgs &a, int num_sms, cudaStream_t s);
 cudaError_t lin_restart(const LinArgs &a, int num_sms, cudaStream_t s);
 cudaError_t lin_certify(const LinArgs &a, int num_sms, cudaStream_t s);
 cudaError_t lin_power_norm(const LinArgs &a, int num_sms, cudaStream_t s);
+cudaError_t lin_gradient(const LinArgs &a, int num_sms, cudaStream_t s);
 
 // Radius of each bus class (the active buses whose PTDF columns coincide on
 // every non-bridge line): rcls[j] = RU(sum of rbus over the class members).
@@ -359,6 +360,13 @@ cudaError_t launch_class_radius(const ClsArgs &a, cudaStream_t s);
 int paper_partials_count(int n_l, int n_c);
 cudaError_t launch_paper(const PaperArgs &a, cudaStream_t s);
 cudaError_t launch_backward(const BwdArgs &a, cudaStream_t s);
+// many cases: items = (case, box) pairs, args = the cases' BwdArgs in device
+// memory (per-call pointers unused); the chain rule runs per case
+cudaError_t launch_bwd_zero_cases(const BwdArgs *args, const int2 *items, int n_items, bool counts,
+                                  cudaStream_t s);
+cudaError_t launch_backward_cases(const BwdArgs *args, const int2 *items, int n_items, int max_n_a_pad,
+                                  cudaStream_t s);
+cudaError_t launch_bwd_chain(const BwdArgs &a, cudaStream_t s);
 cudaError_t launch_wait_selftest(int *flag, unsigned long long limit_ns, cudaStream_t s);
 cudaError_t launch_or_err(int *dst, const int *src, cudaStream_t s);
 

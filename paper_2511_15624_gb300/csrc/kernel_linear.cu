@@ -282,6 +282,40 @@ cudaError_t lin_iteration(const LinArgs &a, int num_sms, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// the dual gradient g = z_f Phi^T W of the current slopes (no step)
+__global__ void k_lin_colsum_state(const LinArgs a) {
+    const int j = blockIdx.y, l = blockIdx.x * blockDim.x + threadIdx.x;
+    if (l >= a.n_l) return;
+    float t = a.a_b[(size_t)j * a.n_l + l];
+    for (int k = 0; k < a.n_c; ++k) t += a.a_c[((size_t)j * a.n_c + k) * a.n_l + l];
+    a.colsum[(size_t)j * a.n_l + l] = t;
+}
+__global__ void __launch_bounds__(256) k_lin_rowdot_state(const LinArgs a) {
+    const int j = blockIdx.y, k = blockIdx.x;
+    float t = 0.0f;
+    for (int l = threadIdx.x; l < a.n_l; l += blockDim.x)
+        t = fmaf(a.a_c[((size_t)j * a.n_c + k) * a.n_l + l], __ldg(&a.lodf[(size_t)k * a.n_l + l]), t);
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    __shared__ float sh[8];
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float s = 0.0f;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += sh[i];
+        a.rowdot[(size_t)j * a.n_c + k] = s;
+    }
+}
+
+cudaError_t lin_gradient(const LinArgs &a, int num_sms, cudaStream_t s) {
+    k_lin_colsum_state<<<dim3((a.n_l + 255) / 256, a.n_box), 256, 0, s>>>(a);
+    if (a.n_c > 0) k_lin_rowdot_state<<<dim3(a.n_c, a.n_box), 256, 0, s>>>(a);
+    k_lin_W<<<dim3((a.n_l + 255) / 256, a.n_box), 256, 0, s>>>(a);
+    cudaError_t e = cudaMemsetAsync(a.g, 0, (size_t)a.n_box * a.n_a_pad * sizeof(float), s);
+    if (e != cudaSuccess) return e;
+    k_lin_g<<<dim3((a.n_a_pad + 127) / 128, kLinSplit, a.n_box), 128, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------------------ restarts
 // State <- running averages; accumulate |Delta x|^2 and |Delta a|^2 since the
 // last restart (red[j][0], red[j][1]); running sums restart at 0.

@@ -34,13 +34,15 @@ namespace ibp {
 constexpr int kEntryChunk = 128;
 constexpr int kEntryBlocks = 64;
 
-__global__ void k_bwd_weights(BwdArgs a) {
-    const int box = blockIdx.y;
+// Each pass is a body over (box, block coordinates), run by a one-case kernel
+// (the box from the grid) and by a many-case kernel whose grid rows walk a
+// table of (case, box) items with the cases' arguments in device memory.
+__device__ __forceinline__ void bwd_weights_body(const BwdArgs &a, int box, int bx, int nbx) {
     const int n = min(a.act_count[box], a.act_cap);
     const int4 *list = a.act_list + (size_t)box * a.act_cap;
     double *W = a.W + (size_t)box * a.n_l;
     int *cnt = a.cnt + (size_t)box * a.n_l;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    for (int i = bx * blockDim.x + threadIdx.x; i < n; i += nbx * blockDim.x) {
         const int4 e = list[i];
         const float sg = __int_as_float(e.w);
         if (e.y < 0) {  // a bridge line, m contingency pairs at once
@@ -56,17 +58,23 @@ __global__ void k_bwd_weights(BwdArgs a) {
     }
 }
 
+__global__ void k_bwd_weights(BwdArgs a) { bwd_weights_body(a, blockIdx.y, blockIdx.x, gridDim.x); }
+
+__global__ void k_bwd_weights_cases(const BwdArgs *__restrict__ args, const int2 *__restrict__ items) {
+    const int2 it = items[blockIdx.y];
+    bwd_weights_body(args[it.x], it.y, blockIdx.x, gridDim.x);
+}
+
 // dc[box][col] = sum_l W[box][l] Phi[l][col]  (lines with W = 0 are skipped);
 // block row y takes lines [y n_l / kCenterSplit, (y + 1) n_l / kCenterSplit)
 // and adds its sum into dc (zeroed by the caller)
 constexpr int kCenterSplit = 32;
 
-__global__ void k_bwd_center(BwdArgs a) {
-    const int box = blockIdx.z;
-    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void bwd_center_body(const BwdArgs &a, int box, int bx, int by) {
+    const int col = bx * blockDim.x + threadIdx.x;
     const double *W = a.W + (size_t)box * a.n_l;
-    const int l0 = (int)((long long)blockIdx.y * a.n_l / kCenterSplit);
-    const int l1 = (int)((long long)(blockIdx.y + 1) * a.n_l / kCenterSplit);
+    const int l0 = (int)((long long)by * a.n_l / kCenterSplit);
+    const int l1 = (int)((long long)(by + 1) * a.n_l / kCenterSplit);
     double acc = 0.0;
     if (col < a.n_a_pad) {
         for (int l = l0; l < l1; ++l) {
@@ -77,10 +85,18 @@ __global__ void k_bwd_center(BwdArgs a) {
     }
 }
 
+__global__ void k_bwd_center(BwdArgs a) { bwd_center_body(a, blockIdx.z, blockIdx.x, blockIdx.y); }
+
+__global__ void k_bwd_center_cases(const BwdArgs *__restrict__ args, const int2 *__restrict__ items) {
+    const int2 it = items[blockIdx.z];
+    const BwdArgs &a = args[it.x];
+    if ((int)(blockIdx.x * blockDim.x) >= a.n_a_pad) return;  // columns of a wider case
+    bwd_center_body(a, it.y, blockIdx.x, blockIdx.y);
+}
+
 // dr[box][col] += sum over a chunk of entries of |Phi[l][col] + L Phi[kline][col]|
-__global__ void k_bwd_radius(BwdArgs a) {
-    const int box = blockIdx.z;
-    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void bwd_radius_body(const BwdArgs &a, int box, int bx, int by, int nby) {
+    const int col = bx * blockDim.x + threadIdx.x;
     const int n = min(a.act_count[box], a.act_cap);
     const int4 *list = a.act_list + (size_t)box * a.act_cap;
     if (col >= a.n_a_pad) return;
@@ -88,7 +104,7 @@ __global__ void k_bwd_radius(BwdArgs a) {
     // forward pass's atomics and the result should not depend on how the
     // entries are grouped
     double tot = 0.0;
-    for (int c0 = blockIdx.y * kEntryChunk; c0 < n; c0 += gridDim.y * kEntryChunk) {
+    for (int c0 = by * kEntryChunk; c0 < n; c0 += nby * kEntryChunk) {
         const int c1 = min(c0 + kEntryChunk, n);
         float part = 0.0f;  // obj_lo's dense set: FP32 within a chunk
         for (int i = c0; i < c1; ++i) {
@@ -110,6 +126,34 @@ __global__ void k_bwd_radius(BwdArgs a) {
         tot += (double)part;
     }
     if (tot != 0.0) atomicAdd(&a.dr[(size_t)box * a.n_a_pad + col], tot);
+}
+
+__global__ void k_bwd_radius(BwdArgs a) { bwd_radius_body(a, blockIdx.z, blockIdx.x, blockIdx.y, gridDim.y); }
+
+__global__ void k_bwd_radius_cases(const BwdArgs *__restrict__ args, const int2 *__restrict__ items) {
+    const int2 it = items[blockIdx.z];
+    const BwdArgs &a = args[it.x];
+    if ((int)(blockIdx.x * blockDim.x) >= a.n_a_pad) return;
+    bwd_radius_body(a, it.y, blockIdx.x, blockIdx.y, gridDim.y);
+}
+
+// zero the per-box accumulators of every item (and, before the forward
+// pass, the active-pair counts of its side)
+__global__ void k_bwd_zero_cases(const BwdArgs *__restrict__ args, const int2 *__restrict__ items,
+                                 int counts) {
+    const int2 it = items[blockIdx.y];
+    const BwdArgs &a = args[it.x];
+    const int t = blockIdx.x * blockDim.x + threadIdx.x, nt = gridDim.x * blockDim.x;
+    const size_t ol = (size_t)it.y * a.n_l, oa = (size_t)it.y * a.n_a_pad;
+    for (int i = t; i < a.n_l; i += nt) {
+        a.W[ol + i] = 0.0;
+        a.cnt[ol + i] = 0;
+    }
+    for (int i = t; i < a.n_a_pad; i += nt) {
+        a.dc[oa + i] = 0.0;
+        a.dr[oa + i] = 0.0;
+    }
+    if (counts && t == 0) const_cast<int *>(a.act_count)[it.y] = 0;
 }
 
 __device__ __forceinline__ double pwl_slope(const double *s, const double *b, int n, double x) {
@@ -210,6 +254,31 @@ cudaError_t launch_backward(const BwdArgs &a, cudaStream_t s) {
     const dim3 gr((a.n_a_pad + 127) / 128, kEntryBlocks / 4, a.n_box);
     k_bwd_radius<<<gr, 128, 0, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_bwd_chain<<<a.n_box, 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bwd_zero_cases(const BwdArgs *args, const int2 *items, int n_items, bool counts,
+                                  cudaStream_t s) {
+    if (n_items <= 0) return cudaSuccess;
+    k_bwd_zero_cases<<<dim3(8, n_items), 256, 0, s>>>(args, items, counts ? 1 : 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_backward_cases(const BwdArgs *args, const int2 *items, int n_items, int max_n_a_pad,
+                                  cudaStream_t s) {
+    if (n_items <= 0) return cudaSuccess;
+    k_bwd_weights_cases<<<dim3(kEntryBlocks, n_items), 256, 0, s>>>(args, items);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    const int cb = (max_n_a_pad + 127) / 128;
+    k_bwd_center_cases<<<dim3(cb, kCenterSplit, n_items), 128, 0, s>>>(args, items);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_bwd_radius_cases<<<dim3(cb, kEntryBlocks / 4, n_items), 128, 0, s>>>(args, items);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bwd_chain(const BwdArgs &a, cudaStream_t s) {
     k_bwd_chain<<<a.n_box, 256, 0, s>>>(a);
     return cudaGetLastError();
 }

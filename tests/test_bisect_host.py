@@ -28,7 +28,8 @@ class OracleCase:
 
     def bound(self, lo, hi):
         r = O.bound(self.case, self.sens, lo.numpy(), hi.numpy(), nthreads=1)
-        return torch.tensor(r.lo), torch.tensor(r.hi), None
+        # the oracle's FP64 bound: no separate rounding allowance
+        return torch.tensor(r.lo), torch.tensor(r.hi), torch.zeros(lo.shape[0], 2, dtype=torch.float64)
 
     def backward(self, lo, hi, g):
         gl, gh, _ = O.grad_hi(self.case, self.sens, lo.numpy(), hi.numpy(), nthreads=1)

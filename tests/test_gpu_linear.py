@@ -78,3 +78,54 @@ def test_linear_bound_closes_the_gap(P):
     assert opt - lb <= 0.02 * abs(opt)
     assert lb_gpu <= lb + 1e-9 * abs(lb) and lb - lb_gpu <= 1e-6 * abs(lb)
     gpu.close()
+
+
+def test_warm_start_and_inheritance(P):
+    """ibp_case_linear_inherit moves state exactly, a warm call of fewer boxes
+    keeps the rest of the held state, and sub-boxes continued from their
+    parent's slopes get certified bounds no worse than the parent's."""
+    case = make_config(1)
+    sens = O.sensitivities(case)
+    gpu = P.Case(case, device=0)
+    lo, hi = case.box_lo[0], case.box_hi[0]
+    ub0, err0, _ = gpu.bound_linear(lo, hi, n_iter=2000)
+    # split the widest coordinate; both halves continue from the root's state
+    d = int(np.argmax(hi - lo))
+    m = 0.5 * (lo[d] + hi[d])
+    clo, chi = np.stack([lo, lo]), np.stack([hi, hi])
+    chi[0, d] = m
+    clo[1, d] = m
+    gpu.linear_inherit(np.array([0, 0], np.int32))
+    ubc, errc, xc = gpu.bound_linear(clo, chi, n_iter=1000, warm=True)
+    a_c, a_b, a0 = gpu.linear_slopes(2)
+    dd = F64 * _scale(case, lo, hi)
+    for j in range(2):
+        ref = O.linear_bound(case, sens, clo[j], chi[j], a_b[j], a_c[j], a0[j])
+        assert ubc[j] >= ref - dd and ubc[j] - ref <= errc[j] + dd, (j, ubc[j], ref)
+        assert np.all(xc[j] >= clo[j] - 1e-9) and np.all(xc[j] <= chi[j] + 1e-9)
+    # each half's bound holds over a part of the root box: no looser than the root's
+    assert ubc.max() <= ub0[0] + err0[0] + dd, (ubc, ub0)
+    # a permutation moves the slopes exactly (no iterations: the certified
+    # value at the held slopes)
+    gpu.linear_inherit(np.array([1, 0], np.int32))
+    ubp, _, _ = gpu.bound_linear(clo[::-1].copy(), chi[::-1].copy(), n_iter=0, warm=True)
+    p_c, p_b, p0 = gpu.linear_slopes(2)
+    assert np.array_equal(p_c, a_c[::-1]) and np.array_equal(p_b, a_b[::-1])
+    assert np.array_equal(p0, a0[::-1])
+    # held box 1 on its own (first=1): the same certified value as in the two-box call
+    u1, e1, _ = gpu.bound_linear(clo[0:1], chi[0:1], n_iter=0, warm=True, first=1)
+    assert abs(u1[0] - ubp[1]) <= e1[0] + dd, (u1, ubp)
+    # a warm call on the first box alone keeps the second box's state
+    gpu.bound_linear(clo[1:2], chi[1:2], n_iter=0, warm=True)
+    gpu.linear_inherit(np.array([1], np.int32))
+    gpu.bound_linear(clo[0:1], chi[0:1], n_iter=0, warm=True)
+    q_c, q_b, q0 = gpu.linear_slopes(1)
+    assert np.array_equal(q_c[0], a_c[0]) and np.array_equal(q_b[0], a_b[0]) and q0[0] == a0[0]
+    # more boxes than the case holds state for is refused
+    with pytest.raises(P.IBPError):
+        gpu.bound_linear(clo, chi, n_iter=0, warm=True)
+    with pytest.raises(P.IBPError):
+        gpu.bound_linear(clo[0:1], chi[0:1], n_iter=0, warm=True, first=1)
+    with pytest.raises(P.IBPError):
+        gpu.linear_inherit(np.array([0, 1], np.int32))
+    gpu.close()
