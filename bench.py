@@ -39,8 +39,8 @@ FMA_LOOP_TFLOPS = 74.4
 # with the SHA-256 prefix of the kernel sources it was taken on
 # (KERNEL_SOURCES).  Other workloads or tile shapes report null; a kernel
 # build whose sources no longer match reports null with a note.
-MEASURED_TRAFFIC = {(3, 0, True, True): (0.9031e9, "")}
-KERNEL_SOURCES = ("kernel_ctg.cu", "ctg_epilogue.cuh", "common.cuh", "internal.h")
+MEASURED_TRAFFIC = {(3, 0, True, True): (0.93466e9, "f1318fd5a8f6e4fa")}
+KERNEL_SOURCES = ("kernel_ctg.cu", "ctg_epilogue.cuh", "refine.cuh", "common.cuh", "internal.h")
 
 
 def kernel_sources_sha():
@@ -97,9 +97,11 @@ def _args():
                    help="FP32 bounds only (no FP64 refinement of the terms that can reach obj_hi)")
     p.add_argument("--boxes", type=int, default=32,
                    help="box count of the batched measurement on the same network (0 = skip)")
-    p.add_argument("--study", default="", choices=["", "bisection", "ragged"],
+    p.add_argument("--study", default="", choices=["", "bisection", "ragged", "linear"],
                    help="bisection: batched vs per-box gradient-guided bisection on mesh2000; "
-                        "ragged: 64 uneven networks x 16 sub-boxes in one persistent launch")
+                        "ragged: 64 uneven networks x 16 sub-boxes in one persistent launch; "
+                        "linear: the linear relaxation bound on mesh2000 (time per iteration, "
+                        "certified bound against iterations)")
     p.add_argument("--rounds", type=int, default=20)
     p.add_argument("--adjoint", action="store_true",
                    help="also time the adjoint of the upper bound (1 box and the batch)")
@@ -534,6 +536,54 @@ def run_bisection_study(args):
     print(json.dumps(out), flush=True)
 
 
+def run_linear_study(args):
+    """The linear relaxation bound on the 2000-bus case: device time per
+    iteration for 1, 4 and 16 boxes, then the certified bound of the root box
+    after 10000 iterations and after each further ``--rounds`` chunk of 1000
+    (warm calls), with the certified value f at the averaged primal point (the
+    lower end of the gap) through the paper-mode bound."""
+    import torch
+
+    import paper_2511_15624_gb300 as P
+    from gen import make_config
+
+    case = make_config(2)
+    gpu = P.Case(case, device=0)
+    lo = torch.tensor(case.box_lo, device="cuda")
+    hi = torch.tensor(case.box_hi, device="cuda")
+    gpu.bound_linear(lo, hi, n_iter=100)  # the operator norm, first graph capture
+    torch.cuda.synchronize()
+    per_iter = {}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for nb in (1, 4, 16):
+        L, H = lo.repeat(nb, 1), hi.repeat(nb, 1)
+        gpu.bound_linear(L, H, n_iter=100)
+        torch.cuda.synchronize()
+        e0.record()
+        gpu.bound_linear(L, H, n_iter=500)
+        e1.record()
+        torch.cuda.synchronize()
+        per_iter[nb] = e0.elapsed_time(e1) / 500
+    traj = []
+    t0 = time.perf_counter()
+    it, best, lb = 0, float("inf"), -float("inf")
+    for rnd in range(args.rounds + 1):
+        n = 10000 if rnd == 0 else 1000
+        ub, err, xp = gpu.bound_linear(lo, hi, n_iter=n, warm=rnd > 0)
+        it += n
+        _, ph, pe = gpu.bound_paper(xp, xp)
+        best = min(best, float(ub[0]))
+        fx = float(ph[0] - pe[0, 0])
+        lb = max(lb, fx)
+        torch.cuda.synchronize()
+        traj.append({"iterations": it, "s": round(time.perf_counter() - t0, 4), "ub": best,
+                     "ub_err": float(err[0]), "f_at_point": fx, "lb": lb, "gap": (best - lb) / abs(lb)})
+    _, ihi, _ = gpu.bound(lo, hi)
+    out = {"study": "linear", "workload": workload(case, 2, 1), "ms_per_iteration": per_iter,
+           "ibp_ub": float(ihi[0]), "trajectory": traj}
+    print(json.dumps(out), flush=True)
+
+
 def run_ragged_study(args):
     """64 networks of uneven size, 16 sub-boxes each: one persistent launch of
     the contingency kernel replayed from a CUDA graph, against one call per case."""
@@ -610,6 +660,9 @@ def main():
         return
     if args.study == "bisection":
         run_bisection_study(args)
+        return
+    if args.study == "linear":
+        run_linear_study(args)
         return
     if args.impl == "reference":
         run_reference(args)

@@ -13,7 +13,9 @@ may still hold the maximiser:
 * LB = max over evaluated points y of a certified lower bound of f(y): at a
   zero-width box the IBP bound is f(y) itself, so obj_hi(y) - err_hi(y) <=
   f(y) (obj_err bounds the distance of obj_hi from the exact IBP value, which
-  the FP64 refinement makes FP64-small).  Each leaf carries an accepted point
+  the FP64 refinement makes FP64-small); with every radius 0 the paper's
+  two-part contingency interval is exact, so points go through
+  ibp_bound_paper.  Each leaf carries an accepted point
   x (its centre at first), the certified value at x and a step s in (0, 1].
   Every round evaluates the proposal y made in the round before; y replaces x
   when its value is higher (s grows by 1.5, else s halves).  The next
@@ -112,16 +114,26 @@ class Bisection:
 
     # -------------------------------------------------------------- bounds
     def _bound(self, lo, hi):
-        """(certified point values: obj_hi - err_hi, obj_hi) of every box."""
+        """obj_hi of every leaf box."""
         if self.batched:
-            obj_lo, obj_hi, err = self._timed(self.case.bound, lo, hi)
-            return obj_hi - err[:, 0], obj_hi
-        outs_lo, outs_hi = [], []
-        for j in range(lo.shape[0]):
-            a, b, e = self._timed(self.case.bound, lo[j:j + 1], hi[j:j + 1])
-            outs_lo.append(b - e[:, 0])
-            outs_hi.append(b)
-        return torch.cat(outs_lo), torch.cat(outs_hi)
+            return self._timed(self.case.bound, lo, hi)[1]
+        return torch.cat([self._timed(self.case.bound, lo[j:j + 1], hi[j:j + 1])[1]
+                          for j in range(lo.shape[0])])
+
+    def _points(self, y):
+        """Certified lower bounds obj_hi - err_hi of f at the points y.  At a
+        zero-width box every radius is 0, so the paper's two-part contingency
+        interval (ibp_bound_paper, O(n_ctg n_line)) is exact there and the
+        contingency kernel is not needed."""
+        fn = getattr(self.case, "bound_paper", None) or self.case.bound
+        if self.batched:
+            _, hi, err = self._timed(fn, y, y)
+            return hi - err[:, 0]
+        out = []
+        for j in range(y.shape[0]):
+            _, hi, err = self._timed(fn, y[j:j + 1], y[j:j + 1])
+            out.append(hi - err[:, 0])
+        return torch.cat(out)
 
     def _grad(self, lo, hi):
         ones = torch.ones(lo.shape[0], dtype=torch.float64, device=self.device)
@@ -166,27 +178,22 @@ class Bisection:
         t0 = time.perf_counter()
         self._tb = 0.0
         n = self.lo.shape[0]
-        cand = [self.lo, self.y]
-        cand_hi = [self.hi, self.y]
-        leaf_ub = None
+        pts = [self.y]
+        leaf_hi = self._bound(self.lo, self.hi)
         if self.bound_kind == "linear":
             lub, xp = self._linear(self.lo, self.hi)
-            leaf_ub = lub
+            leaf_hi = torch.minimum(leaf_hi, lub)
             self._xlin = xp
-            cand.append(xp)
-            cand_hi.append(xp)
-        both_lo = torch.cat(cand)
-        both_hi = torch.cat(cand_hi)
-        pv, obj_hi = self._bound(both_lo, both_hi)
-        leaf_hi = obj_hi[:n] if leaf_ub is None else torch.minimum(obj_hi[:n], leaf_ub)
-        fy = pv[n:2 * n]
-        self.lb = max(self.lb, float(pv[n:].max()))
+            pts.append(xp)
+        pv = self._points(torch.cat(pts))
+        fy = pv[:n]
+        self.lb = max(self.lb, float(pv.max()))
         # accept the proposals that improved their leaf's point
         better = fy > self.fx
         self.x = torch.where(better[:, None], self.y, self.x)
         self.fx = torch.where(better, fy, self.fx)
         if self.bound_kind == "linear":
-            fl = pv[2 * n:]
+            fl = pv[n:]
             bl = fl > self.fx
             self.x = torch.where(bl[:, None], self._xlin, self.x)
             self.fx = torch.where(bl, fl, self.fx)

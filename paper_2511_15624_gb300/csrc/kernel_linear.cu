@@ -71,47 +71,37 @@ __device__ __forceinline__ double block_sum_d(double v, double *sh) {
 }
 
 // ------------------------------------------------------------------ x step
-// One block per box: projected gradient ascent on x, the extrapolated point
-// xb = 2 x_new - x, its bus injections and total injection.  In power mode x
-// holds the power iteration's vector and only its injections are formed.
-__global__ void __launch_bounds__(256) k_lin_x(const LinArgs a) {
-    const int j = blockIdx.x;
-    const size_t od = (size_t)j * a.n_dev;
-    const double *lo = a.box_lo + od, *hi = a.box_hi + od;
-    double *x = a.x + od, *xb = a.xb + od, *sx = a.sx + od;
-    const float *g = a.g + (size_t)j * a.n_a_pad;
-    const double tx = a.step / a.w[j];
-    const double a0 = a.a0[j];
-    double part = 0.0;
-    for (int d = threadIdx.x; d < a.n_dev; d += blockDim.x) {
-        const bool gen = d < a.n_gen;
-        const double sg = gen ? 1.0 : -1.0;
-        if (a.power) {
-            xb[d] = x[d];
-        } else {
-            const int col = a.dev_col[d];
-            const double gb = col >= 0 ? (double)g[col] : 0.0;
-            const int s0 = a.seg_ptr[d], ns = a.seg_ptr[d + 1] - s0;
-            const double sl = lin_pwl_slope(a.slope + s0, a.bkpt + s0, ns, x[d]);
-            const double grad = (gen ? -sl : sl) - sg * (gb + a.zeta_inj * a0);
-            const double xn = fmin(fmax(x[d] + tx * grad, lo[d]), hi[d]);
-            xb[d] = 2.0 * xn - x[d];
-            x[d] = xn;
-            sx[d] += xn;
-        }
-        part += sg * xb[d];
+// Thread per (device, box): projected gradient ascent on x and the
+// extrapolated point xb = 2 x_new - x.  In power mode x holds the power
+// iteration's vector and xb = x.
+__global__ void __launch_bounds__(128) k_lin_x(const LinArgs a) {
+    const int j = blockIdx.y, d = blockIdx.x * blockDim.x + threadIdx.x;
+    if (d >= a.n_dev) return;
+    const size_t o = (size_t)j * a.n_dev + d;
+    if (a.power) {
+        a.xb[o] = a.x[o];
+        return;
     }
-    __shared__ double sh[8];
-    // a plain (round-to-nearest) block sum
-    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = part;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += sh[i];
-        a.stot[j] = t;
-    }
-    for (int col = threadIdx.x; col < a.n_a_pad; col += blockDim.x) {
+    const bool gen = d < a.n_gen;
+    const double sg = gen ? 1.0 : -1.0;
+    const double xo = a.x[o];
+    const int col = a.dev_col[d];
+    const double gb = col >= 0 ? (double)a.g[(size_t)j * a.n_a_pad + col] : 0.0;
+    const int s0 = a.seg_ptr[d], ns = a.seg_ptr[d + 1] - s0;
+    const double sl = lin_pwl_slope(a.slope + s0, a.bkpt + s0, ns, xo);
+    const double grad = (gen ? -sl : sl) - sg * (gb + a.zeta_inj * a.a0[j]);
+    const double xn = fmin(fmax(xo + (a.step / a.w[j]) * grad, a.box_lo[o]), a.box_hi[o]);
+    a.xb[o] = 2.0 * xn - xo;
+    a.x[o] = xn;
+    a.sx[o] += xn;
+}
+
+// Thread per (active column, box): the bus injection of xb; block 0 of each
+// box also forms the total injection (a fixed-order block sum)
+__global__ void __launch_bounds__(128) k_lin_p(const LinArgs a) {
+    const int j = blockIdx.y, col = blockIdx.x * blockDim.x + threadIdx.x;
+    const double *xb = a.xb + (size_t)j * a.n_dev;
+    if (col < a.n_a_pad) {
         double v = 0.0;
         if (col < a.n_a)
             for (int q = a.act_ptr[col]; q < a.act_ptr[col + 1]; ++q) {
@@ -120,6 +110,14 @@ __global__ void __launch_bounds__(256) k_lin_x(const LinArgs a) {
             }
         a.p[(size_t)j * a.n_a_pad + col] = (float)v;
     }
+    if (blockIdx.x != 0) return;
+    double part = 0.0;
+    for (int d = threadIdx.x; d < a.n_dev; d += blockDim.x) part += (d < a.n_gen ? 1.0 : -1.0) * xb[d];
+    __shared__ double sh[4];
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = part;
+    __syncthreads();
+    if (threadIdx.x == 0) a.stot[j] = sh[0] + sh[1] + sh[2] + sh[3];
 }
 
 // base flows f = Phi p of xb: one warp per (line, box)
@@ -147,6 +145,8 @@ __device__ __forceinline__ float lin_prox(float v, float thr) {
 // Dual step on the slopes: block (x: 256 lines, y: 32 contingencies, z: box);
 // blocks with y == 0 also take the base flows, block (0, 0) the imbalance.
 // Accumulates the line weights' column sums and the rows' dot products with L.
+// The block's 32 outaged-line flows are staged in shared memory, and each
+// group of 8 contingencies loads its L, slopes and sums before any store.
 __global__ void __launch_bounds__(256) k_lin_pairs(const LinArgs a) {
     const int j = blockIdx.z;
     const int l = blockIdx.x * 256 + threadIdx.x;
@@ -154,31 +154,52 @@ __global__ void __launch_bounds__(256) k_lin_pairs(const LinArgs a) {
     const double sa = a.step * a.w[j];
     const float gain = (float)(sa * a.zeta_f);
     const float *f = a.f + (size_t)j * a.n_l;
+    __shared__ float fk_s[32];
+    if (threadIdx.x < 32) {
+        const int k = k0 + threadIdx.x;
+        fk_s[threadIdx.x] = k < a.n_c ? f[__ldg(&a.ctg_line[k])] : 0.0f;
+    }
+    __syncthreads();
     const bool lv = l < a.n_l;
     const float fl = lv ? f[l] : 0.0f;
     const float thr = lv ? gain * (float)a.rate_c64[l] : 0.0f;
+    const float *__restrict__ lodf = a.lodf;
+    float *__restrict__ ac = a.a_c;
+    float *__restrict__ sc = a.s_c;
     float col = 0.0f;
     float rowv[32];
 #pragma unroll
-    for (int kk = 0; kk < 32; ++kk) {
-        const int k = k0 + kk;
-        float v = 0.0f;
-        if (lv && k < a.n_c) {
-            const float Lt = __ldg(&a.lodf[(size_t)k * a.n_l + l]);
-            const float fc = fmaf(Lt, f[__ldg(&a.ctg_line[k])], fl);
+    for (int g8 = 0; g8 < 4; ++g8) {
+        float Lt[8], av[8], sv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int k = k0 + g8 * 8 + u;
+            const bool ok = lv && k < a.n_c;
             const size_t o = ((size_t)j * a.n_c + k) * a.n_l + l;
-            float an;
-            if (a.power) {
-                an = (float)a.zeta_f * fc;
-            } else {
-                an = lin_prox(fmaf(gain, fc, a.a_c[o]), thr);
-                a.a_c[o] = an;
-                a.s_c[o] += an;
-            }
-            col += an;
-            v = an * Lt;
+            Lt[u] = ok ? __ldg(&lodf[(size_t)k * a.n_l + l]) : 0.0f;
+            av[u] = ok && !a.power ? ac[o] : 0.0f;
+            sv[u] = ok && !a.power ? sc[o] : 0.0f;
         }
-        rowv[kk] = v;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int kk = g8 * 8 + u, k = k0 + kk;
+            float v = 0.0f;
+            if (lv && k < a.n_c) {
+                const float fc = fmaf(Lt[u], fk_s[kk], fl);
+                float an;
+                if (a.power) {
+                    an = (float)a.zeta_f * fc;
+                } else {
+                    const size_t o = ((size_t)j * a.n_c + k) * a.n_l + l;
+                    an = lin_prox(fmaf(gain, fc, av[u]), thr);
+                    ac[o] = an;
+                    sc[o] = sv[u] + an;
+                }
+                col += an;
+                v = an * Lt[u];
+            }
+            rowv[kk] = v;
+        }
     }
     __shared__ float sh[8][33];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -226,20 +247,30 @@ __global__ void k_lin_W(const LinArgs a) {
     a.colsum[(size_t)j * a.n_l + l] = t;
 }
 
-// g_b = z_f sum_l W_l Phi[l][b]: column blocks x 32 line splits, atomics into g
-constexpr int kLinSplit = 32;
-__global__ void k_lin_g(const LinArgs a) {
-    const int j = blockIdx.z, col = blockIdx.x * blockDim.x + threadIdx.x;
-    if (col >= a.n_a_pad) return;
-    const int l0 = (int)((long long)blockIdx.y * a.n_l / kLinSplit);
-    const int l1 = (int)((long long)(blockIdx.y + 1) * a.n_l / kLinSplit);
+// g_b = z_f sum_l W_l Phi[l][b]: a thread takes 4 adjacent columns (one
+// 16-byte load per line) and a block row 32 lines; atomics into g
+constexpr int kLinGLines = 32;
+__global__ void __launch_bounds__(128) k_lin_g(const LinArgs a) {
+    const int j = blockIdx.z, c4 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (4 * c4 >= a.n_a_pad) return;
+    const int l0 = blockIdx.y * kLinGLines, l1 = min(l0 + kLinGLines, a.n_l);
     const float *W = a.colsum + (size_t)j * a.n_l;
-    float acc = 0.0f;
+    float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll 8
     for (int l = l0; l < l1; ++l) {
         const float w = W[l];
-        if (w != 0.0f) acc = fmaf(w, __ldg(&a.phi[(size_t)l * a.n_a_pad + col]), acc);
+        const float4 ph = __ldg(reinterpret_cast<const float4 *>(a.phi + (size_t)l * a.n_a_pad) + c4);
+        acc.x = fmaf(w, ph.x, acc.x);
+        acc.y = fmaf(w, ph.y, acc.y);
+        acc.z = fmaf(w, ph.z, acc.z);
+        acc.w = fmaf(w, ph.w, acc.w);
     }
-    if (acc != 0.0f) atomicAdd(&a.g[(size_t)j * a.n_a_pad + col], (float)a.zeta_f * acc);
+    float *g = a.g + (size_t)j * a.n_a_pad + 4 * c4;
+    const float zf = (float)a.zeta_f;
+    if (acc.x != 0.0f) atomicAdd(g, zf * acc.x);
+    if (acc.y != 0.0f) atomicAdd(g + 1, zf * acc.y);
+    if (acc.z != 0.0f) atomicAdd(g + 2, zf * acc.z);
+    if (acc.w != 0.0f) atomicAdd(g + 3, zf * acc.w);
 }
 
 // power mode: v <- K^T D^2 K v (from g and a0), then its norm; box 0 only
@@ -272,12 +303,13 @@ cudaError_t lin_iteration(const LinArgs &a, int num_sms, cudaStream_t s) {
     if (a.n_c > 0 &&
         (e = cudaMemsetAsync(a.rowdot, 0, (size_t)a.n_box * a.n_c * sizeof(float), s)) != cudaSuccess)
         return e;
-    k_lin_x<<<a.n_box, 256, 0, s>>>(a);
+    k_lin_x<<<dim3((a.n_dev + 127) / 128, a.n_box), 128, 0, s>>>(a);
+    k_lin_p<<<dim3((a.n_a_pad + 127) / 128, a.n_box), 128, 0, s>>>(a);
     k_lin_flows<<<dim3((a.n_l + 7) / 8, a.n_box), 256, 0, s>>>(a);
     k_lin_pairs<<<dim3((a.n_l + 255) / 256, std::max((a.n_c + 31) / 32, 1), a.n_box), 256, 0, s>>>(a);
     k_lin_W<<<dim3((a.n_l + 255) / 256, a.n_box), 256, 0, s>>>(a);
     if ((e = cudaMemsetAsync(a.g, 0, (size_t)a.n_box * a.n_a_pad * sizeof(float), s)) != cudaSuccess) return e;
-    k_lin_g<<<dim3((a.n_a_pad + 127) / 128, kLinSplit, a.n_box), 128, 0, s>>>(a);
+    k_lin_g<<<dim3((a.n_a_pad / 4 + 127) / 128, (a.n_l + kLinGLines - 1) / kLinGLines, a.n_box), 128, 0, s>>>(a);
     if (a.power) k_lin_power<<<1, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
@@ -312,7 +344,7 @@ cudaError_t lin_gradient(const LinArgs &a, int num_sms, cudaStream_t s) {
     k_lin_W<<<dim3((a.n_l + 255) / 256, a.n_box), 256, 0, s>>>(a);
     cudaError_t e = cudaMemsetAsync(a.g, 0, (size_t)a.n_box * a.n_a_pad * sizeof(float), s);
     if (e != cudaSuccess) return e;
-    k_lin_g<<<dim3((a.n_a_pad + 127) / 128, kLinSplit, a.n_box), 128, 0, s>>>(a);
+    k_lin_g<<<dim3((a.n_a_pad / 4 + 127) / 128, (a.n_l + kLinGLines - 1) / kLinGLines, a.n_box), 128, 0, s>>>(a);
     return cudaGetLastError();
 }
 
