@@ -186,8 +186,11 @@ ibp_status ibp_bound_backward_lo(ibp_case *c, int32_t n_box, const double *box_l
  * eq. (slack-sinj) -- so f <= l_a on the box for every choice of slopes, and
  * max over the box of l_a, which is separable per device, is exact.  The
  * slopes are optimised by n_iter primal-dual hybrid gradient iterations
- * (restarts to the averages every 1000 iterations, primal weight starting at
- * primal_weight, 1.0 by default, and adapted at each restart); any slopes
+ * with diagonal step sizes (the inverse row and column sums of the operator,
+ * bounded by the triangle inequality), restarts to the averages every 1000
+ * iterations, and a primal weight starting at primal_weight and adapted at
+ * each restart (a scale of the dual steps against the primal ones; the
+ * binding starts at 0.01); any slopes
  * give a certified bound, and the iteration approaches the LP optimum.
  * A call restarts at its end too, so a sequence of warm calls follows one
  * long call only when each runs a multiple of 1000 iterations (calls of 500
@@ -209,8 +212,9 @@ ibp_status ibp_bound_backward_lo(ibp_case *c, int32_t n_box, const double *box_l
  *     boxes are not held); obj_hi is then also at most the certified value at
  *     the held slopes, so a sub-box continued from its parent never gets a
  *     larger bound than the parent's last one.
- * The first call on a case measures the operator norm (a power iteration;
- * the call synchronises its stream once).  Memory: 12 bytes per (box,
+ * The first call on a case computes the diagonal step sizes of the
+ * iteration (row and column sums of the operator, O(n_line n_active +
+ * n_ctg n_active), no synchronisation).  Memory: 12 bytes per (box,
  * contingency, line).  ptr_mode and stream as in ibp_bound.
  */
 ibp_status ibp_bound_linear(ibp_case *c, int32_t n_box, const double *box_lo,

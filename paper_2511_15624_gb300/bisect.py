@@ -72,7 +72,8 @@ class Bisection:
     def __init__(self, case: Case, root_lo, root_hi, max_leaves: int = 256,
                  batched: bool = True, device: Optional[torch.device] = None,
                  split_per_round: Optional[int] = None, bound: str = "ibp",
-                 linear_iters: int = 1000, linear_root_iters: Optional[int] = None):
+                 linear_iters: int = 1000, linear_root_iters: Optional[int] = None,
+                 primal_weight: float = 0.01):
         self.case = case
         self.device = device or torch.device("cuda", case.device)
         lo = torch.as_tensor(np.atleast_2d(root_lo), dtype=torch.float64, device=self.device)
@@ -86,6 +87,7 @@ class Bisection:
         self.bound_kind = bound
         self.linear_iters = int(linear_iters)
         self.linear_root_iters = int(linear_root_iters or 10 * linear_iters)
+        self.primal_weight = float(primal_weight)
         n = self.lo.shape[0]
         self.x = 0.5 * (self.lo + self.hi)  # accepted point per leaf
         self.fx = torch.full((n,), -float("inf"), dtype=torch.float64, device=self.device)
@@ -153,19 +155,20 @@ class Bisection:
         iters = self.linear_iters if warm else self.linear_root_iters
         if not warm and not self.batched and lo.shape[0] > 1:
             # a reloaded frontier: hold zero slopes for every leaf, then continue each
-            self._timed(self.case.bound_linear, lo, hi, 0)
+            self._timed(self.case.bound_linear, lo, hi, 0, self.primal_weight)
             warm = True
         if self.batched or lo.shape[0] == 1:
-            ub, _, xp = self._timed(self.case.bound_linear, lo, hi, iters, 1.0, None, warm)
+            ub, _, xp = self._timed(self.case.bound_linear, lo, hi, iters, self.primal_weight, None, warm)
         else:
             # one box per call, each continuing its own held state
             ubs, xps = [], []
             for j in range(lo.shape[0]):
                 if warm:
-                    u, _, x = self._timed(self.case.bound_linear, lo[j:j + 1], hi[j:j + 1], iters, 1.0,
-                                          None, True, j)
+                    u, _, x = self._timed(self.case.bound_linear, lo[j:j + 1], hi[j:j + 1], iters,
+                                          self.primal_weight, None, True, j)
                 else:  # a fresh root: one box
-                    u, _, x = self._timed(self.case.bound_linear, lo[j:j + 1], hi[j:j + 1], iters)
+                    u, _, x = self._timed(self.case.bound_linear, lo[j:j + 1], hi[j:j + 1], iters,
+                                          self.primal_weight)
                 ubs.append(u)
                 xps.append(x)
             ub, xp = torch.cat(ubs), torch.cat(xps)

@@ -146,14 +146,16 @@ class Case:
         fn(self._h, nb, lo, hi, g, glo, ghi, gr, ptr_mode=0, stream=None)
         return (glo, ghi) + ((gr,) if want_rating else ())
 
-    def bound_linear(self, lo, hi, n_iter: int = 20000, primal_weight: float = 1.0, stream=None,
+    def bound_linear(self, lo, hi, n_iter: int = 20000, primal_weight: float = 0.01, stream=None,
                      warm: bool = False, first: int = 0):
         """Linear (CROWN-style) relaxation bound with optimised slopes
         (``ibp_bound_linear``): returns (obj_hi, obj_err, x_point) -- the
         certified upper bound of max f, its rounding bound and the averaged
         primal point -- as numpy arrays for numpy boxes, CUDA tensors for CUDA
         boxes (enqueued on the stream).  warm=True continues the held state of
-        boxes [first, first + n_box)."""
+        boxes [first, first + n_box).  The start weight 0.01 balances the
+        preconditioned primal and dual steps on the synthetic networks (the
+        restarts adapt it)."""
         warm = (1 + int(first)) if warm else 0
         if _abi._is_cuda_tensor(lo):
             import torch

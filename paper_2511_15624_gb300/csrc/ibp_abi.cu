@@ -134,7 +134,9 @@ struct ibp_case {
     DevBuf<float> lX;
     // linear (CROWN-style) relaxation bound: iteration state and certified value
     int lin_cap_box = 0, lin_state_box = 0;  // boxes the workspace holds / the state describes
-    double lin_step = 0.0;                 // 0.9 / ||D K||, measured once per case
+    bool lin_pc_ready = false;             // the diagonal step sizes are computed (once per case)
+    DevBuf<float> lpcS;                    // [n_line] row sums S_l of the step sizes
+    DevBuf<double> lpctau, lpcA, lpcB, lpcL;  // [n_dev] primal steps; scratch of their build
     DevBuf<int> cl_ptr, cl_ctg;            // contingencies per outaged line
     DevBuf<double> lw, lx, lsx, lxb, lx_last, la0, ls0, la0_last, lstot, lred, lub, lub_err, lbest;
     DevBuf<float> lac, lsc, lc_last, lab, lsb, lb_last, lp, lf, lcol, lrow, lg;
@@ -1396,7 +1398,8 @@ static LinArgs lin_args(const ibp_case *c, int n_box, const double *lo, const do
     a.act_ptr = c->act_ptr.p; a.act_dev = c->act_dev.p; a.dev_col = c->dev_col.p;
     a.rate64 = c->rate64.p; a.rate_c64 = c->rate_c64.p; a.box_lo = lo; a.box_hi = hi;
     a.seg_ptr = c->seg_ptr.p; a.slope = c->slope.p; a.bkpt = c->bkpt.p;
-    a.zeta_inj = c->zeta_inj; a.zeta_f = c->zeta_f; a.step = c->lin_step;
+    a.zeta_inj = c->zeta_inj; a.zeta_f = c->zeta_f;
+    a.pc_S = c->lpcS.p; a.pc_tau = c->lpctau.p;
     a.w = c->lw.p; a.x = c->lx.p; a.sx = c->lsx.p; a.xb = c->lxb.p; a.x_last = c->lx_last.p;
     a.a_c = c->lac.p; a.s_c = c->lsc.p; a.c_last = c->lc_last.p;
     a.a_b = c->lab.p; a.s_b = c->lsb.p; a.b_last = c->lb_last.p;
@@ -1477,19 +1480,16 @@ static ibp_status lin_run(ibp_case *c, int n_box, const double *lo, const double
     const size_t nd = (size_t)n_box * c->n_dev, np = (size_t)n_box * std::max(c->n_ctg, 1) * c->n_line;
     const size_t nl = (size_t)n_box * c->n_line;
     auto zero = [&](void *p, size_t bytes) { return cudaMemsetAsync(p, 0, bytes, s); };
-    if (c->lin_step <= 0.0) {
-        // ||D K|| once per case (power iteration from the first box's midpoint)
+    if (!c->lin_pc_ready) {
+        // the diagonal step sizes, once per case (they depend on the network only)
+        if (!c->lpcS.p) {
+            CUDA_TRY(c->lpcS.alloc(c->n_line)); CUDA_TRY(c->lpctau.alloc(c->n_dev));
+            CUDA_TRY(c->lpcA.alloc(c->n_a_pad)); CUDA_TRY(c->lpcB.alloc(c->n_a_pad));
+            CUDA_TRY(c->lpcL.alloc(std::max(c->n_ctg, 1)));
+        }
         LinArgs a = lin_args(c, 1, lo, hi);
-        k_lin_init<<<(c->n_dev + 255) / 256, 256, 0, s>>>(c->n_dev, lo, hi, c->lx.p, c->lx_last.p, 1,
-                                                         c->lw.p, 1.0, c->lbest.p);
-        CUDA_TRY(cudaGetLastError());
-        a.step = 1.0;
-        CUDA_TRY(lin_power_norm(a, c->num_sms, s));
-        double lam = 0.0;
-        CUDA_TRY(cudaMemcpyAsync(&lam, c->lred.p, sizeof(double), cudaMemcpyDeviceToHost, s));
-        CUDA_TRY(cudaStreamSynchronize(s));
-        if (!(lam > 0.0) || !std::isfinite(lam)) return fail(IBP_ECUDA, "power iteration gave no norm");
-        c->lin_step = 0.9 / std::sqrt(lam);
+        CUDA_TRY(lin_precondition(a, c->lpcS.p, c->lpctau.p, c->lpcA.p, c->lpcB.p, c->lpcL.p, s));
+        c->lin_pc_ready = true;
     }
     if (warm) {
         // continue from the state held for these boxes: the points are moved

@@ -238,8 +238,12 @@ struct LinArgs {
     const int *seg_ptr;
     const double *slope, *bkpt;
     double zeta_inj, zeta_f;
-    double step;               // 0.9 / ||D K|| (D: zeta scaling of the terms)
-    int power;                 // 1: power iteration for ||D K|| (no state update)
+    // diagonal step sizes (Pock-Chambolle, alpha = 1, with row and column sums
+    // of |D K| bounded by the triangle inequality): a pair's dual step is
+    // 1 / (z_f (S_l + |L_lk| S_k)), a base line's 1 / (z_f S_l), the
+    // imbalance's 1 / (z_inj n_dev); a device's primal step is tau[d]
+    const float *pc_S;         // [n_l] S_l = sum_b |Phi[l,b]| (devices at b)
+    const double *pc_tau;      // [n_dev]
     // iteration state
     double *w;                 // [n_box] primal weight
     double *x, *sx, *xb, *x_last;          // [n_box][n_dev]
@@ -263,7 +267,9 @@ struct LinArgs {
 cudaError_t lin_iteration(const LinArgs &a, int num_sms, cudaStream_t s);
 cudaError_t lin_restart(const LinArgs &a, int num_sms, cudaStream_t s);
 cudaError_t lin_certify(const LinArgs &a, int num_sms, cudaStream_t s);
-cudaError_t lin_power_norm(const LinArgs &a, int num_sms, cudaStream_t s);
+// the preconditioner of a case (once): S, tau; A, B [n_a_pad] and Lsum [n_c] scratch
+cudaError_t lin_precondition(const LinArgs &a, float *S, double *tau, double *A, double *B, double *Lsum,
+                             cudaStream_t s);
 cudaError_t lin_gradient(const LinArgs &a, int num_sms, cudaStream_t s);
 
 // Radius of each bus class (the active buses whose PTDF columns coincide on

@@ -18,9 +18,12 @@
 // optimum.  The slopes are driven by a primal-dual hybrid gradient iteration
 // (Chambolle and Pock, J. Math. Imaging Vision 40, 2011) on max_x min_a l_a(x)
 // with the operator D K (K: x -> the flows and the total injection, D: their
-// z_f / z_inj weights), step 0.9 / ||D K|| split by a primal weight, restarts
+// z_f / z_inj weights) and diagonal step sizes (Pock and Chambolle, ICCV
+// 2011, alpha = 1: the inverse row and column sums of |D K|, here bounded
+// from above by the triangle inequality) split by a primal weight, restarts
 // to the running averages with the primal weight adapted to the ratio of the
-// dual and primal moves (as in PDLP, Applegate et al., NeurIPS 2021).
+// dual and primal moves in the step-weighted norms (as in PDLP, Applegate et
+// al., NeurIPS 2021).
 // The iterations run in FP32/FP64 without rounding control; the certified
 // value U(a) at the final slopes is computed in FP64 with an explicit error
 // bound (lin_certify).
@@ -72,16 +75,11 @@ __device__ __forceinline__ double block_sum_d(double v, double *sh) {
 
 // ------------------------------------------------------------------ x step
 // Thread per (device, box): projected gradient ascent on x and the
-// extrapolated point xb = 2 x_new - x.  In power mode x holds the power
-// iteration's vector and xb = x.
+// extrapolated point xb = 2 x_new - x.
 __global__ void __launch_bounds__(128) k_lin_x(const LinArgs a) {
     const int j = blockIdx.y, d = blockIdx.x * blockDim.x + threadIdx.x;
     if (d >= a.n_dev) return;
     const size_t o = (size_t)j * a.n_dev + d;
-    if (a.power) {
-        a.xb[o] = a.x[o];
-        return;
-    }
     const bool gen = d < a.n_gen;
     const double sg = gen ? 1.0 : -1.0;
     const double xo = a.x[o];
@@ -90,7 +88,7 @@ __global__ void __launch_bounds__(128) k_lin_x(const LinArgs a) {
     const int s0 = a.seg_ptr[d], ns = a.seg_ptr[d + 1] - s0;
     const double sl = lin_pwl_slope(a.slope + s0, a.bkpt + s0, ns, xo);
     const double grad = (gen ? -sl : sl) - sg * (gb + a.zeta_inj * a.a0[j]);
-    const double xn = fmin(fmax(xo + (a.step / a.w[j]) * grad, a.box_lo[o]), a.box_hi[o]);
+    const double xn = fmin(fmax(xo + (a.pc_tau[d] / a.w[j]) * grad, a.box_lo[o]), a.box_hi[o]);
     a.xb[o] = 2.0 * xn - xo;
     a.x[o] = xn;
     a.sx[o] += xn;
@@ -145,40 +143,45 @@ __device__ __forceinline__ float lin_prox(float v, float thr) {
 // Dual step on the slopes: block (x: 256 lines, y: 32 contingencies, z: box);
 // blocks with y == 0 also take the base flows, block (0, 0) the imbalance.
 // Accumulates the line weights' column sums and the rows' dot products with L.
-// The block's 32 outaged-line flows are staged in shared memory, and each
-// group of 8 contingencies loads its L, slopes and sums before any store.
-__global__ void __launch_bounds__(256) k_lin_pairs(const LinArgs a) {
+// The block's 32 outaged-line flows and S values are staged in shared memory,
+// and each group of 8 contingencies loads its L, slopes and sums before any
+// store.  A pair's step (z_f times its dual step size times the primal
+// weight) is w / (S_l + |L_lk| S_k).
+__global__ void __launch_bounds__(256, 3) k_lin_pairs(const LinArgs a) {
     const int j = blockIdx.z;
     const int l = blockIdx.x * 256 + threadIdx.x;
     const int k0 = blockIdx.y * 32;
-    const double sa = a.step * a.w[j];
-    const float gain = (float)(sa * a.zeta_f);
+    const float w = (float)a.w[j];
     const float *f = a.f + (size_t)j * a.n_l;
-    __shared__ float fk_s[32];
+    __shared__ float fk_s[32], sk_s[32];
     if (threadIdx.x < 32) {
         const int k = k0 + threadIdx.x;
-        fk_s[threadIdx.x] = k < a.n_c ? f[__ldg(&a.ctg_line[k])] : 0.0f;
+        const int kl = k < a.n_c ? __ldg(&a.ctg_line[k]) : 0;
+        fk_s[threadIdx.x] = k < a.n_c ? f[kl] : 0.0f;
+        sk_s[threadIdx.x] = k < a.n_c ? a.pc_S[kl] : 0.0f;
     }
     __syncthreads();
     const bool lv = l < a.n_l;
     const float fl = lv ? f[l] : 0.0f;
-    const float thr = lv ? gain * (float)a.rate_c64[l] : 0.0f;
+    const float Sl = lv ? a.pc_S[l] : 1.0f;
+    const float Rc = lv ? (float)a.rate_c64[l] : 0.0f;
     const float *__restrict__ lodf = a.lodf;
     float *__restrict__ ac = a.a_c;
     float *__restrict__ sc = a.s_c;
     float col = 0.0f;
-    float rowv[32];
+    __shared__ float sh[8][33];
+    const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
     for (int g8 = 0; g8 < 4; ++g8) {
-        float Lt[8], av[8], sv[8];
+        float Lt[8], av[8], sv[8], rowv[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             const int k = k0 + g8 * 8 + u;
             const bool ok = lv && k < a.n_c;
             const size_t o = ((size_t)j * a.n_c + k) * a.n_l + l;
             Lt[u] = ok ? __ldg(&lodf[(size_t)k * a.n_l + l]) : 0.0f;
-            av[u] = ok && !a.power ? ac[o] : 0.0f;
-            sv[u] = ok && !a.power ? sc[o] : 0.0f;
+            av[u] = ok ? ac[o] : 0.0f;
+            sv[u] = ok ? sc[o] : 0.0f;
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
@@ -186,28 +189,23 @@ __global__ void __launch_bounds__(256) k_lin_pairs(const LinArgs a) {
             float v = 0.0f;
             if (lv && k < a.n_c) {
                 const float fc = fmaf(Lt[u], fk_s[kk], fl);
-                float an;
-                if (a.power) {
-                    an = (float)a.zeta_f * fc;
-                } else {
-                    const size_t o = ((size_t)j * a.n_c + k) * a.n_l + l;
-                    an = lin_prox(fmaf(gain, fc, av[u]), thr);
-                    ac[o] = an;
-                    sc[o] = sv[u] + an;
-                }
+                const float gain = __fdividef(w, fmaf(fabsf(Lt[u]), sk_s[kk], Sl));
+                const size_t o = ((size_t)j * a.n_c + k) * a.n_l + l;
+                const float an = lin_prox(fmaf(gain, fc, av[u]), gain * Rc);
+                ac[o] = an;
+                sc[o] = sv[u] + an;
                 col += an;
                 v = an * Lt[u];
             }
-            rowv[kk] = v;
+            rowv[u] = v;
         }
-    }
-    __shared__ float sh[8][33];
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        // the warp's share of the 8 rows' dot products with L
 #pragma unroll
-    for (int kk = 0; kk < 32; ++kk) {
-        float v = rowv[kk];
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) sh[w][kk] = v;
+        for (int u = 0; u < 8; ++u) {
+            float v = rowv[u];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+            if (lane == 0) sh[wp][g8 * 8 + u] = v;
+        }
     }
     __syncthreads();
     if (threadIdx.x < 32 && k0 + threadIdx.x < a.n_c) {
@@ -216,25 +214,18 @@ __global__ void __launch_bounds__(256) k_lin_pairs(const LinArgs a) {
         atomicAdd(&a.rowdot[(size_t)j * a.n_c + k0 + threadIdx.x], t);
     }
     if (blockIdx.y == 0 && lv) {
-        float an;
-        if (a.power) {
-            an = (float)a.zeta_f * fl;
-        } else {
-            const size_t o = (size_t)j * a.n_l + l;
-            an = lin_prox(fmaf(gain, fl, a.a_b[o]), gain * (float)a.rate64[l]);
-            a.a_b[o] = an;
-            a.s_b[o] += an;
-        }
+        const size_t o = (size_t)j * a.n_l + l;
+        const float gain = __fdividef(w, Sl);
+        const float an = lin_prox(fmaf(gain, fl, a.a_b[o]), gain * (float)a.rate64[l]);
+        a.a_b[o] = an;
+        a.s_b[o] += an;
         col += an;
     }
     if (lv) atomicAdd(&a.colsum[(size_t)j * a.n_l + l], col);
     if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
-        if (a.power) {
-            a.a0[j] = a.zeta_inj * a.stot[j];
-        } else {
-            a.a0[j] = fmin(fmax(a.a0[j] + sa * a.zeta_inj * a.stot[j], -1.0), 1.0);
-            a.s0[j] += a.a0[j];
-        }
+        // z_inj times the imbalance's step 1 / (z_inj n_dev) times w
+        a.a0[j] = fmin(fmax(a.a0[j] + a.w[j] * a.stot[j] / (double)a.n_dev, -1.0), 1.0);
+        a.s0[j] += a.a0[j];
     }
 }
 
@@ -273,30 +264,6 @@ __global__ void __launch_bounds__(128) k_lin_g(const LinArgs a) {
     if (acc.w != 0.0f) atomicAdd(g + 3, zf * acc.w);
 }
 
-// power mode: v <- K^T D^2 K v (from g and a0), then its norm; box 0 only
-__global__ void __launch_bounds__(256) k_lin_power(const LinArgs a) {
-    double part = 0.0;
-    for (int d = threadIdx.x; d < a.n_dev; d += blockDim.x) {
-        const int col = a.dev_col[d];
-        const double v = (d < a.n_gen ? 1.0 : -1.0) * ((col >= 0 ? (double)a.g[col] : 0.0) + a.zeta_inj * a.a0[0]);
-        a.xb[d] = v;
-        part += v * v;
-    }
-    __shared__ double sh[8];
-    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = part;
-    __syncthreads();
-    __shared__ double nrm;
-    if (threadIdx.x == 0) {
-        double t = 0.0;
-        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += sh[i];
-        nrm = sqrt(t);
-        a.red[0] = nrm;  // ||K^T D^2 K v|| for the unit vector v
-    }
-    __syncthreads();
-    for (int d = threadIdx.x; d < a.n_dev; d += blockDim.x) a.x[d] = nrm > 0.0 ? a.xb[d] / nrm : 0.0;
-}
-
 cudaError_t lin_iteration(const LinArgs &a, int num_sms, cudaStream_t s) {
     cudaError_t e;
     if ((e = cudaMemsetAsync(a.colsum, 0, (size_t)a.n_box * a.n_l * sizeof(float), s)) != cudaSuccess) return e;
@@ -310,7 +277,6 @@ cudaError_t lin_iteration(const LinArgs &a, int num_sms, cudaStream_t s) {
     k_lin_W<<<dim3((a.n_l + 255) / 256, a.n_box), 256, 0, s>>>(a);
     if ((e = cudaMemsetAsync(a.g, 0, (size_t)a.n_box * a.n_a_pad * sizeof(float), s)) != cudaSuccess) return e;
     k_lin_g<<<dim3((a.n_a_pad / 4 + 127) / 128, (a.n_l + kLinGLines - 1) / kLinGLines, a.n_box), 128, 0, s>>>(a);
-    if (a.power) k_lin_power<<<1, 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -361,27 +327,32 @@ __global__ void k_lin_avg(const LinArgs a) {
         if (i < (size_t)a.n_dev) {
             const size_t o = (size_t)j * a.n_dev + i;
             const double v = a.sx[o] * inv;
-            dx += (v - a.x_last[o]) * (v - a.x_last[o]);
+            dx += (v - a.x_last[o]) * (v - a.x_last[o]) / a.pc_tau[i];
             a.x[o] = v;
             a.x_last[o] = v;
             a.sx[o] = 0.0;
         } else if (i < (size_t)a.n_dev + a.n_l) {
-            const size_t o = (size_t)j * a.n_l + (i - a.n_dev);
+            const int l = (int)(i - a.n_dev);
+            const size_t o = (size_t)j * a.n_l + l;
             const float v = (float)(a.s_b[o] * inv);
-            da += (double)(v - a.b_last[o]) * (double)(v - a.b_last[o]);
+            da += (double)(v - a.b_last[o]) * (double)(v - a.b_last[o]) * a.zeta_f * (double)a.pc_S[l];
             a.a_b[o] = v;
             a.b_last[o] = v;
             a.s_b[o] = 0.0f;
         } else if (i < (size_t)a.n_dev + a.n_l + npair) {
-            const size_t o = (size_t)j * npair + (i - a.n_dev - a.n_l);
+            const size_t q = i - a.n_dev - a.n_l;
+            const size_t o = (size_t)j * npair + q;
+            const int k = (int)(q / a.n_l), l = (int)(q % a.n_l);
+            const double wgt = a.zeta_f * ((double)a.pc_S[l] +
+                                           fabs((double)a.lodf[q]) * (double)a.pc_S[a.ctg_line[k]]);
             const float v = (float)(a.s_c[o] * inv);
-            da += (double)(v - a.c_last[o]) * (double)(v - a.c_last[o]);
+            da += (double)(v - a.c_last[o]) * (double)(v - a.c_last[o]) * wgt;
             a.a_c[o] = v;
             a.c_last[o] = v;
             a.s_c[o] = 0.0f;
         } else {
             const double v = a.s0[j] * inv;
-            da += (v - a.a0_last[j]) * (v - a.a0_last[j]);
+            da += (v - a.a0_last[j]) * (v - a.a0_last[j]) * a.zeta_inj * (double)a.n_dev;
             a.a0[j] = v;
             a.a0_last[j] = v;
             a.s0[j] = 0.0;
@@ -549,17 +520,56 @@ cudaError_t lin_certify(const LinArgs &a, int num_sms, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-// ||D K|| by power iteration on K^T D^2 K (box 0 of the workspace; x holds the
-// vector, red[0] the last norm)
-cudaError_t lin_power_norm(const LinArgs &a0, int num_sms, cudaStream_t s) {
-    LinArgs a = a0;
-    a.power = 1;
-    a.n_box = 1;
-    for (int it = 0; it < 40; ++it) {
-        cudaError_t e = lin_iteration(a, num_sms, s);
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
+// ------------------------------------------------------------------ preconditioner
+// S_l = sum over active columns of |Phi[l,col]| times the column's device
+// count (one warp per line); a row no active bus reaches keeps S = 1
+__global__ void k_pc_rows(const LinArgs a, float *S) {
+    const int l = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (l >= a.n_l) return;
+    double t = 0.0;
+    for (int col = lane; col < a.n_a; col += 32)
+        t += fabs((double)a.phi[(size_t)l * a.n_a_pad + col]) * (double)(a.act_ptr[col + 1] - a.act_ptr[col]);
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) S[l] = t > 0.0 ? (float)t : 1.0f;
+}
+// Lsum_k = sum_l |L[l,k]| (one warp per contingency)
+__global__ void k_pc_lsum(const LinArgs a, double *Lsum) {
+    const int k = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (k >= a.n_c) return;
+    double t = 0.0;
+    for (int l = lane; l < a.n_l; l += 32) t += fabs((double)a.lodf[(size_t)k * a.n_l + l]);
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+    if (lane == 0) Lsum[k] = t;
+}
+// column col: A = sum_l |Phi[l,col]|, B = sum_k |Phi[line of k, col]| Lsum_k
+__global__ void k_pc_cols(const LinArgs a, const double *Lsum, double *A, double *B) {
+    const int col = blockIdx.x * blockDim.x + threadIdx.x;
+    if (col >= a.n_a_pad) return;
+    double sa = 0.0, sb = 0.0;
+    for (int l = 0; l < a.n_l; ++l) sa += fabs((double)a.phi[(size_t)l * a.n_a_pad + col]);
+    for (int k = 0; k < a.n_c; ++k)
+        sb += fabs((double)a.phi[(size_t)a.ctg_line[k] * a.n_a_pad + col]) * Lsum[k];
+    A[col] = sa;
+    B[col] = sb;
+}
+// tau[d] = 1 / (z_f (A (1 + n_c) + B) + z_inj): the inverse of the bound on
+// the column sum of |D K| (the sum over pairs of |H_k[l,b]| is at most
+// n_c A + B)
+__global__ void k_pc_tau(const LinArgs a, const double *A, const double *B, double *tau) {
+    const int d = blockIdx.x * blockDim.x + threadIdx.x;
+    if (d >= a.n_dev) return;
+    const int col = a.dev_col[d];
+    const double cs = col >= 0 ? a.zeta_f * (A[col] * (1.0 + a.n_c) + B[col]) : 0.0;
+    tau[d] = 1.0 / (cs + a.zeta_inj);
+}
+
+cudaError_t lin_precondition(const LinArgs &a, float *S, double *tau, double *A, double *B, double *Lsum,
+                             cudaStream_t s) {
+    k_pc_rows<<<(a.n_l + 7) / 8, 256, 0, s>>>(a, S);
+    if (a.n_c > 0) k_pc_lsum<<<(a.n_c + 7) / 8, 256, 0, s>>>(a, Lsum);
+    k_pc_cols<<<(a.n_a_pad + 127) / 128, 128, 0, s>>>(a, Lsum, A, B);
+    k_pc_tau<<<(a.n_dev + 127) / 128, 128, 0, s>>>(a, A, B, tau);
+    return cudaGetLastError();
 }
 
 }  // namespace ibp
