@@ -103,6 +103,8 @@ def _args():
                         "linear: the linear relaxation bound on mesh2000 (time per iteration, "
                         "certified bound against iterations)")
     p.add_argument("--rounds", type=int, default=20)
+    p.add_argument("--linear-config", type=int, default=2,
+                   help="workload of --study linear (default: the 2000-bus case)")
     p.add_argument("--adjoint", action="store_true",
                    help="also time the adjoint of the upper bound (1 box and the batch)")
     p.add_argument("--cpu-seconds", type=float, default=20.0,
@@ -537,21 +539,23 @@ def run_bisection_study(args):
 
 
 def run_linear_study(args):
-    """The linear relaxation bound on the 2000-bus case: device time per
-    iteration for 1, 4 and 16 boxes, then the certified bound of the root box
-    after 10000 iterations and after each further ``--rounds`` chunk of 1000
-    (warm calls), with the certified value f at the averaged primal point (the
-    lower end of the gap) through the paper-mode bound."""
+    """The linear relaxation bound (default: the 2000-bus case; see
+    ``--linear-config``): device time per iteration for 1, 4 and 16 boxes,
+    then the certified bound of the root box after 10000 iterations and after
+    each further ``--rounds`` chunk of 1000 (warm calls), with the certified
+    value f at the averaged primal point (the lower end of the gap) through
+    the paper-mode bound."""
     import torch
 
     import paper_2511_15624_gb300 as P
     from gen import make_config
 
-    case = make_config(2)
+    cfg = args.linear_config
+    case = make_config(cfg)
     gpu = P.Case(case, device=0)
     lo = torch.tensor(case.box_lo, device="cuda")
     hi = torch.tensor(case.box_hi, device="cuda")
-    gpu.bound_linear(lo, hi, n_iter=100)  # the operator norm, first graph capture
+    gpu.bound_linear(lo, hi, n_iter=100)  # the step sizes, first graph capture
     torch.cuda.synchronize()
     per_iter = {}
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -579,7 +583,7 @@ def run_linear_study(args):
         traj.append({"iterations": it, "s": round(time.perf_counter() - t0, 4), "ub": best,
                      "ub_err": float(err[0]), "f_at_point": fx, "lb": lb, "gap": (best - lb) / abs(lb)})
     _, ihi, _ = gpu.bound(lo, hi)
-    out = {"study": "linear", "workload": workload(case, 2, 1), "ms_per_iteration": per_iter,
+    out = {"study": "linear", "workload": workload(case, cfg, 1), "ms_per_iteration": per_iter,
            "ibp_ub": float(ihi[0]), "trajectory": traj}
     print(json.dumps(out), flush=True)
 
