@@ -187,23 +187,22 @@ ibp_status ibp_bound_backward_lo(ibp_case *c, int32_t n_box, const double *box_l
  * max over the box of l_a, which is separable per device, is exact.  The
  * slopes are optimised by n_iter primal-dual hybrid gradient iterations
  * with diagonal step sizes (the inverse row and column sums of the operator,
- * bounded by the triangle inequality), restarts to the averages every 1000
- * iterations, and a primal weight starting at primal_weight and adapted at
- * each restart (a scale of the dual steps against the primal ones; the
- * binding starts at 0.01); any slopes
- * give a certified bound, and the iteration approaches the LP optimum.
- * A call restarts at its end too, so a sequence of warm calls follows one
- * long call only when each runs a multiple of 1000 iterations (calls of 500
- * restart twice as often, which was measured to make the restart values
- * oscillate).
+ * bounded by the triangle inequality) and a primal weight starting at
+ * primal_weight (a scale of the dual steps against the primal ones; the
+ * binding starts at 0.01), adapted every 1000 iterations and at the end of a
+ * call, when the dual function is also certified at the current slopes; any
+ * slopes give a certified bound, and the iteration approaches the LP
+ * optimum.  Warm calls of any length follow one long call closely (calls of
+ * 500 iterations were measured to end within 1e-5 of it).
  *   box_lo, box_hi [n_box][n_gen + n_load]; obj_hi [n_box]: the smallest
- *     certified value of the dual function met at a restart (or, warm, at
- *     the start of the call; computed from
- *     the FP64 sensitivities with outward rounding: obj_hi >= max f);
+ *     certified value of the dual function met at an adaptation (or, warm,
+ *     at the start of the call), computed from the FP64 sensitivities with
+ *     outward rounding: obj_hi >= max f;
  *   obj_err [n_box]: a bound on its rounding error;
- *   x_point [n_box][n_gen + n_load] or NULL: the averaged primal point, a
- *     candidate maximiser (f there, e.g. from ibp_bound on the zero-width box
- *     at it, is a certified lower bound of max f);
+ *   x_point [n_box][n_gen + n_load] or NULL: the primal point averaged over
+ *     the last adaptation window, a candidate maximiser (f there, e.g. from
+ *     ibp_bound on the zero-width box at it, is a certified lower bound of
+ *     max f);
  *   warm: 0 starts from zero slopes and the box midpoints (the case then
  *     holds state for these n_box boxes); warm = 1 + f (f >= 0) continues
  *     the iteration from the state the case holds for its boxes
@@ -214,7 +213,7 @@ ibp_status ibp_bound_backward_lo(ibp_case *c, int32_t n_box, const double *box_l
  *     larger bound than the parent's last one.
  * The first call on a case computes the diagonal step sizes of the
  * iteration (row and column sums of the operator, O(n_line n_active +
- * n_ctg n_active), no synchronisation).  Memory: 12 bytes per (box,
+ * n_ctg n_active), no synchronisation).  Memory: 8 bytes per (box,
  * contingency, line).  ptr_mode and stream as in ibp_bound.
  */
 ibp_status ibp_bound_linear(ibp_case *c, int32_t n_box, const double *box_lo,

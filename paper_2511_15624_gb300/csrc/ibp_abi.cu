@@ -138,8 +138,8 @@ struct ibp_case {
     DevBuf<float> lpcS;                    // [n_line] row sums S_l of the step sizes
     DevBuf<double> lpctau, lpcA, lpcB, lpcL;  // [n_dev] primal steps; scratch of their build
     DevBuf<int> cl_ptr, cl_ctg;            // contingencies per outaged line
-    DevBuf<double> lw, lx, lsx, lxb, lx_last, la0, ls0, la0_last, lstot, lred, lub, lub_err, lbest;
-    DevBuf<float> lac, lsc, lc_last, lab, lsb, lb_last, lp, lf, lcol, lrow, lg;
+    DevBuf<double> lw, lx, lsx, lxb, lx_last, lxavg, la0, la0_last, lstot, lred, lub, lub_err, lbest;
+    DevBuf<float> lac, lc_last, lab, lb_last, lp, lf, lcol, lrow, lg;
     DevBuf<double> lW64, lWabs, lconst, lrd64, lrda, lg64, lG64;
     cudaGraphExec_t lin_graph = nullptr;   // a chunk of iterations
     // refinement queues of the contingency launch (regions per CTA and warp)
@@ -1359,12 +1359,12 @@ static ibp_status ensure_lin_workspace(ibp_case *c, int n_box) {
     const size_t nd = (size_t)cap * c->n_dev, nl = (size_t)cap * c->n_line;
     const size_t np = (size_t)cap * std::max(c->n_ctg, 1) * c->n_line, na = (size_t)cap * c->n_a_pad;
     const size_t nc = (size_t)cap * std::max(c->n_ctg, 1);
-    CUDA_TRY(c->lw.alloc(cap)); CUDA_TRY(c->la0.alloc(cap)); CUDA_TRY(c->ls0.alloc(cap));
+    CUDA_TRY(c->lw.alloc(cap)); CUDA_TRY(c->la0.alloc(cap));
     CUDA_TRY(c->la0_last.alloc(cap)); CUDA_TRY(c->lstot.alloc(cap)); CUDA_TRY(c->lred.alloc((size_t)cap * 4));
     CUDA_TRY(c->lub.alloc(cap)); CUDA_TRY(c->lub_err.alloc(cap)); CUDA_TRY(c->lbest.alloc((size_t)cap * 2));
     CUDA_TRY(c->lx.alloc(nd)); CUDA_TRY(c->lsx.alloc(nd)); CUDA_TRY(c->lxb.alloc(nd)); CUDA_TRY(c->lx_last.alloc(nd));
-    CUDA_TRY(c->lac.alloc(np)); CUDA_TRY(c->lsc.alloc(np)); CUDA_TRY(c->lc_last.alloc(np));
-    CUDA_TRY(c->lab.alloc(nl)); CUDA_TRY(c->lsb.alloc(nl)); CUDA_TRY(c->lb_last.alloc(nl));
+    CUDA_TRY(c->lac.alloc(np)); CUDA_TRY(c->lc_last.alloc(np)); CUDA_TRY(c->lxavg.alloc(nd));
+    CUDA_TRY(c->lab.alloc(nl)); CUDA_TRY(c->lb_last.alloc(nl));
     CUDA_TRY(c->lp.alloc(na)); CUDA_TRY(c->lf.alloc(nl)); CUDA_TRY(c->lcol.alloc(nl));
     CUDA_TRY(c->lrow.alloc(nc)); CUDA_TRY(c->lg.alloc(na));
     CUDA_TRY(c->lW64.alloc(nl)); CUDA_TRY(c->lWabs.alloc(nl)); CUDA_TRY(c->lconst.alloc(nl));
@@ -1401,9 +1401,10 @@ static LinArgs lin_args(const ibp_case *c, int n_box, const double *lo, const do
     a.zeta_inj = c->zeta_inj; a.zeta_f = c->zeta_f;
     a.pc_S = c->lpcS.p; a.pc_tau = c->lpctau.p;
     a.w = c->lw.p; a.x = c->lx.p; a.sx = c->lsx.p; a.xb = c->lxb.p; a.x_last = c->lx_last.p;
-    a.a_c = c->lac.p; a.s_c = c->lsc.p; a.c_last = c->lc_last.p;
-    a.a_b = c->lab.p; a.s_b = c->lsb.p; a.b_last = c->lb_last.p;
-    a.a0 = c->la0.p; a.s0 = c->ls0.p; a.a0_last = c->la0_last.p;
+    a.a_c = c->lac.p; a.c_last = c->lc_last.p;
+    a.a_b = c->lab.p; a.b_last = c->lb_last.p;
+    a.a0 = c->la0.p; a.a0_last = c->la0_last.p;
+    a.x_avg = c->lxavg.p;
     a.p = c->lp.p; a.stot = c->lstot.p; a.f = c->lf.p; a.colsum = c->lcol.p; a.rowdot = c->lrow.p;
     a.g = c->lg.p; a.red = c->lred.p;
     a.W64 = c->lW64.p; a.Wabs = c->lWabs.p; a.constl = c->lconst.p; a.rd64 = c->lrd64.p;
@@ -1411,10 +1412,10 @@ static LinArgs lin_args(const ibp_case *c, int n_box, const double *lo, const do
     if (first > 0) {
         const size_t f = (size_t)first, fd = f * c->n_dev, fl = f * c->n_line;
         const size_t fc = f * std::max(c->n_ctg, 1) * c->n_line;
-        a.w += f; a.x += fd; a.sx += fd; a.x_last += fd;
-        a.a_c += fc; a.s_c += fc; a.c_last += fc;
-        a.a_b += fl; a.s_b += fl; a.b_last += fl;
-        a.a0 += f; a.s0 += f; a.a0_last += f;
+        a.w += f; a.x += fd; a.sx += fd; a.x_last += fd; a.x_avg += fd;
+        a.a_c += fc; a.c_last += fc;
+        a.a_b += fl; a.b_last += fl;
+        a.a0 += f; a.a0_last += f;
     }
     return a;
 }
@@ -1434,9 +1435,10 @@ __global__ void k_lin_init(int n, const double *lo, const double *hi, double *x,
     }
 }
 
-// keep the smaller certified bound of each box (and its error bound)
-// warm start: points clipped into their boxes, running sums of the points at 0,
-// best bound +inf (the slopes, sums and primal weight stay)
+// warm start: points clipped into their boxes and taken as the reference of
+// the next adaptation; best bound +inf (the slopes, the slope references and
+// the primal weight stay; the running sum of the points is 0 after the
+// previous call's last adaptation)
 __global__ void k_lin_warm(int n, const double *lo, const double *hi, double *x, double *x_last,
                            int n_box, double *best) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1450,6 +1452,7 @@ __global__ void k_lin_warm(int n, const double *lo, const double *hi, double *x,
     }
 }
 
+// keep the smaller certified bound of each box (and its error bound)
 __global__ void k_lin_best(int n_box, const double *ub, const double *err, double *best) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j < n_box && ub[j] < best[2 * j]) {
@@ -1466,7 +1469,7 @@ __global__ void k_lin_out(int n_box, const double *best, double *obj_hi, double 
     }
 }
 
-constexpr int kLinRestart = 1000;   // iterations between restarts (and certified values)
+constexpr int kLinRestart = 1000;   // iterations between adaptations of the primal weight (and certified values)
 constexpr int kLinChunk = 50;       // iterations per CUDA graph launch
 
 static ibp_status lin_run(ibp_case *c, int n_box, const double *lo, const double *hi, int n_iter,
@@ -1503,11 +1506,11 @@ static ibp_status lin_run(ibp_case *c, int n_box, const double *lo, const double
         (int)nd, lo, hi, c->lx.p, c->lx_last.p, n_box, c->lw.p, w0, c->lbest.p);
     CUDA_TRY(cudaGetLastError());
     CUDA_TRY(zero(c->lsx.p, nd * sizeof(double)));
-    CUDA_TRY(zero(c->lac.p, np * sizeof(float))); CUDA_TRY(zero(c->lsc.p, np * sizeof(float)));
+    CUDA_TRY(zero(c->lac.p, np * sizeof(float)));
     CUDA_TRY(zero(c->lc_last.p, np * sizeof(float)));
-    CUDA_TRY(zero(c->lab.p, nl * sizeof(float))); CUDA_TRY(zero(c->lsb.p, nl * sizeof(float)));
+    CUDA_TRY(zero(c->lab.p, nl * sizeof(float)));
     CUDA_TRY(zero(c->lb_last.p, nl * sizeof(float)));
-    CUDA_TRY(zero(c->la0.p, n_box * sizeof(double))); CUDA_TRY(zero(c->ls0.p, n_box * sizeof(double)));
+    CUDA_TRY(zero(c->la0.p, n_box * sizeof(double)));
     CUDA_TRY(zero(c->la0_last.p, n_box * sizeof(double)));
     CUDA_TRY(zero(c->lred.p, (size_t)n_box * 4 * sizeof(double)));
     CUDA_TRY(zero(c->lg.p, (size_t)n_box * c->n_a_pad * sizeof(float)));
@@ -1570,7 +1573,7 @@ static ibp_status lin_run(ibp_case *c, int n_box, const double *lo, const double
     }
     k_lin_out<<<(n_box + 127) / 128, 128, 0, s>>>(n_box, c->lbest.p, obj_hi, obj_err);
     CUDA_TRY(cudaGetLastError());
-    if (x_point) CUDA_TRY(cudaMemcpyAsync(x_point, a.x, nd * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    if (x_point) CUDA_TRY(cudaMemcpyAsync(x_point, a.x_avg, nd * sizeof(double), cudaMemcpyDeviceToDevice, s));
     return mark_done(c, s);
 }
 
@@ -1668,10 +1671,10 @@ extern "C" ibp_status ibp_case_linear_inherit(ibp_case *c, int32_t n_new, const 
         std::swap(b.n, t.n);
         return IBP_OK;
     };
-    if ((st = gf(c->lac, pc)) || (st = gf(c->lsc, pc)) || (st = gf(c->lc_last, pc)) ||
-        (st = gf(c->lab, c->n_line)) || (st = gf(c->lsb, c->n_line)) || (st = gf(c->lb_last, c->n_line)) ||
-        (st = gd(c->la0, 1)) || (st = gd(c->ls0, 1)) || (st = gd(c->la0_last, 1)) || (st = gd(c->lw, 1)) ||
-        (st = gd(c->lx, c->n_dev)) || (st = gd(c->lsx, c->n_dev)))
+    if ((st = gf(c->lac, pc)) || (st = gf(c->lc_last, pc)) ||
+        (st = gf(c->lab, c->n_line)) || (st = gf(c->lb_last, c->n_line)) ||
+        (st = gd(c->la0, 1)) || (st = gd(c->la0_last, 1)) || (st = gd(c->lw, 1)) ||
+        (st = gd(c->lx, c->n_dev)) || (st = gd(c->lsx, c->n_dev)) || (st = gd(c->lxavg, c->n_dev)))
         return st;
     CUDA_TRY(cudaDeviceSynchronize());
     // the other per-box buffers only need the room

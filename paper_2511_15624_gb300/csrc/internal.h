@@ -246,10 +246,10 @@ struct LinArgs {
     const double *pc_tau;      // [n_dev]
     // iteration state
     double *w;                 // [n_box] primal weight
-    double *x, *sx, *xb, *x_last;          // [n_box][n_dev]
-    float *a_c, *s_c, *c_last;             // [n_box][n_c][n_l]
-    float *a_b, *s_b, *b_last;             // [n_box][n_l]
-    double *a0, *s0, *a0_last;             // [n_box]
+    double *x, *sx, *xb, *x_last, *x_avg;  // [n_box][n_dev]
+    float *a_c, *c_last;                   // [n_box][n_c][n_l]
+    float *a_b, *b_last;                   // [n_box][n_l]
+    double *a0, *a0_last;                  // [n_box]
     float *p;                  // [n_box][n_a_pad] bus injections of xb
     double *stot;              // [n_box] total injection of xb
     float *f;                  // [n_box][n_l] base flows of xb
@@ -257,7 +257,7 @@ struct LinArgs {
     float *rowdot;             // [n_box][n_c]
     float *g;                  // [n_box][n_a_pad] zeta_f (Phi^T W)_b
     double *red;               // [n_box][4] restart reductions
-    int n_avg;                 // iterations in the running sums
+    int n_avg;                 // iterations in the running sum of x
     // certified value of the dual function at the slopes (a_c, a_b, a0)
     double *W64, *Wabs, *constl;           // [n_box][n_l]
     double *rd64, *rda;                    // [n_box][n_c]

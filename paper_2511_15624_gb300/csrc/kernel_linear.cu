@@ -23,7 +23,9 @@
 // from above by the triangle inequality) split by a primal weight, restarts
 // to the running averages with the primal weight adapted to the ratio of the
 // dual and primal moves in the step-weighted norms (as in PDLP, Applegate et
-// al., NeurIPS 2021).
+// al., NeurIPS 2021).  A restart keeps the current iterate (no averaging of
+// the slopes, so the slope step moves 12 bytes per pair, not 20); the
+// averaged primal point of each restart window is the candidate maximiser.
 // The iterations run in FP32/FP64 without rounding control; the certified
 // value U(a) at the final slopes is computed in FP64 with an explicit error
 // bound (lin_certify).
@@ -167,13 +169,12 @@ __global__ void __launch_bounds__(256, 3) k_lin_pairs(const LinArgs a) {
     const float Rc = lv ? (float)a.rate_c64[l] : 0.0f;
     const float *__restrict__ lodf = a.lodf;
     float *__restrict__ ac = a.a_c;
-    float *__restrict__ sc = a.s_c;
     float col = 0.0f;
     __shared__ float sh[8][33];
     const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
     for (int g8 = 0; g8 < 4; ++g8) {
-        float Lt[8], av[8], sv[8], rowv[8];
+        float Lt[8], av[8], rowv[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             const int k = k0 + g8 * 8 + u;
@@ -181,7 +182,6 @@ __global__ void __launch_bounds__(256, 3) k_lin_pairs(const LinArgs a) {
             const size_t o = ((size_t)j * a.n_c + k) * a.n_l + l;
             Lt[u] = ok ? __ldg(&lodf[(size_t)k * a.n_l + l]) : 0.0f;
             av[u] = ok ? ac[o] : 0.0f;
-            sv[u] = ok ? sc[o] : 0.0f;
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
@@ -193,7 +193,6 @@ __global__ void __launch_bounds__(256, 3) k_lin_pairs(const LinArgs a) {
                 const size_t o = ((size_t)j * a.n_c + k) * a.n_l + l;
                 const float an = lin_prox(fmaf(gain, fc, av[u]), gain * Rc);
                 ac[o] = an;
-                sc[o] = sv[u] + an;
                 col += an;
                 v = an * Lt[u];
             }
@@ -218,14 +217,12 @@ __global__ void __launch_bounds__(256, 3) k_lin_pairs(const LinArgs a) {
         const float gain = __fdividef(w, Sl);
         const float an = lin_prox(fmaf(gain, fl, a.a_b[o]), gain * (float)a.rate64[l]);
         a.a_b[o] = an;
-        a.s_b[o] += an;
         col += an;
     }
     if (lv) atomicAdd(&a.colsum[(size_t)j * a.n_l + l], col);
     if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
         // z_inj times the imbalance's step 1 / (z_inj n_dev) times w
         a.a0[j] = fmin(fmax(a.a0[j] + a.w[j] * a.stot[j] / (double)a.n_dev, -1.0), 1.0);
-        a.s0[j] += a.a0[j];
     }
 }
 
@@ -315,8 +312,9 @@ cudaError_t lin_gradient(const LinArgs &a, int num_sms, cudaStream_t s) {
 }
 
 // ------------------------------------------------------------------ restarts
-// State <- running averages; accumulate |Delta x|^2 and |Delta a|^2 since the
-// last restart (red[j][0], red[j][1]); running sums restart at 0.
+// The averaged point of the window (x_avg), and the step-weighted squared
+// moves of x and of the slopes since the last restart (red[j][0], red[j][1]);
+// the references move to the current iterate and the running sum restarts.
 __global__ void k_lin_avg(const LinArgs a) {
     const int j = blockIdx.y;
     const double inv = 1.0 / (double)a.n_avg;
@@ -326,36 +324,30 @@ __global__ void k_lin_avg(const LinArgs a) {
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += (size_t)gridDim.x * blockDim.x) {
         if (i < (size_t)a.n_dev) {
             const size_t o = (size_t)j * a.n_dev + i;
-            const double v = a.sx[o] * inv;
+            const double v = a.x[o];
             dx += (v - a.x_last[o]) * (v - a.x_last[o]) / a.pc_tau[i];
-            a.x[o] = v;
             a.x_last[o] = v;
+            a.x_avg[o] = a.sx[o] * inv;
             a.sx[o] = 0.0;
         } else if (i < (size_t)a.n_dev + a.n_l) {
             const int l = (int)(i - a.n_dev);
             const size_t o = (size_t)j * a.n_l + l;
-            const float v = (float)(a.s_b[o] * inv);
+            const float v = a.a_b[o];
             da += (double)(v - a.b_last[o]) * (double)(v - a.b_last[o]) * a.zeta_f * (double)a.pc_S[l];
-            a.a_b[o] = v;
             a.b_last[o] = v;
-            a.s_b[o] = 0.0f;
         } else if (i < (size_t)a.n_dev + a.n_l + npair) {
             const size_t q = i - a.n_dev - a.n_l;
             const size_t o = (size_t)j * npair + q;
             const int k = (int)(q / a.n_l), l = (int)(q % a.n_l);
             const double wgt = a.zeta_f * ((double)a.pc_S[l] +
                                            fabs((double)a.lodf[q]) * (double)a.pc_S[a.ctg_line[k]]);
-            const float v = (float)(a.s_c[o] * inv);
+            const float v = a.a_c[o];
             da += (double)(v - a.c_last[o]) * (double)(v - a.c_last[o]) * wgt;
-            a.a_c[o] = v;
             a.c_last[o] = v;
-            a.s_c[o] = 0.0f;
         } else {
-            const double v = a.s0[j] * inv;
+            const double v = a.a0[j];
             da += (v - a.a0_last[j]) * (v - a.a0_last[j]) * a.zeta_inj * (double)a.n_dev;
-            a.a0[j] = v;
             a.a0_last[j] = v;
-            a.s0[j] = 0.0;
         }
     }
     for (int o = 16; o > 0; o >>= 1) {

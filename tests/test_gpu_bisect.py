@@ -83,7 +83,7 @@ def test_linear_bisection_closes_the_sandwich(P, batched):
     """Linear-relaxation leaves (children continue their parent's slopes):
     after 4 rounds of up to 8 leaves, opt - 0.25% <= LB <= opt <= UB <=
     opt + 0.25%, i.e. at least 99.7% of the IBP root bound's excess over opt
-    removed (measured: UB 0.03% above opt, LB 0.03% below)."""
+    removed (measured: UB 0.04% above opt, LB 0.01% below)."""
     from paper_2511_15624_gb300.bisect import Bisection
     from tests.test_oracle_ibp import _lp_optimum
     case = make_config(1)

@@ -8,7 +8,7 @@ optimised on the GPU.
   it is also above the LP optimum (weak duality);
 * it closes the gap: on the 118-bus box, 20000 iterations bring the bound
   within 0.25% of the LP optimum (IBP: 102% above it), and f at the averaged
-  primal point within 0.25% below it (measured: 0.05% on either side)."""
+  primal point within 0.25% below it (measured: +0.05% and -0.03%)."""
 import numpy as np
 import pytest
 
