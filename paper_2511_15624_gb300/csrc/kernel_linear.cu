@@ -142,84 +142,134 @@ __device__ __forceinline__ float lin_prox(float v, float thr) {
     return copysignf(t, v);
 }
 
-// Dual step on the slopes: block (x: 256 lines, y: 32 contingencies, z: box);
-// blocks with y == 0 also take the base flows, block (0, 0) the imbalance.
-// Accumulates the line weights' column sums and the rows' dot products with L.
-// The block's 32 outaged-line flows and S values are staged in shared memory,
-// and each group of 8 contingencies loads its L, slopes and sums before any
-// store.  A pair's step (z_f times its dual step size times the primal
-// weight) is w / (S_l + |L_lk| S_k).
+// V consecutive floats (V = 1, 2, 4): one aligned vector load or store
+template <int V>
+struct VecF {
+    float v[V];
+    __device__ __forceinline__ void load(const float *p) {
+        if constexpr (V == 4) {
+            const float4 t = *reinterpret_cast<const float4 *>(p);
+            v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+        } else if constexpr (V == 2) {
+            const float2 t = *reinterpret_cast<const float2 *>(p);
+            v[0] = t.x; v[1] = t.y;
+        } else {
+            v[0] = *p;
+        }
+    }
+    __device__ __forceinline__ void load_ro(const float *p) {
+        if constexpr (V == 4) {
+            const float4 t = __ldg(reinterpret_cast<const float4 *>(p));
+            v[0] = t.x; v[1] = t.y; v[2] = t.z; v[3] = t.w;
+        } else if constexpr (V == 2) {
+            const float2 t = __ldg(reinterpret_cast<const float2 *>(p));
+            v[0] = t.x; v[1] = t.y;
+        } else {
+            v[0] = __ldg(p);
+        }
+    }
+    __device__ __forceinline__ void store(float *p) const {
+        if constexpr (V == 4) *reinterpret_cast<float4 *>(p) = make_float4(v[0], v[1], v[2], v[3]);
+        else if constexpr (V == 2) *reinterpret_cast<float2 *>(p) = make_float2(v[0], v[1]);
+        else *p = v[0];
+    }
+};
+
+// Dual step on the slopes: block (x: 256 threads of V adjacent lines each,
+// y: 32 / V contingencies, z: box), so a thread takes 32 pairs whatever V;
+// n_l is a multiple of V, so every row of L and of the slopes starts
+// V-aligned.  Blocks with y == 0 also take the base
+// flows, block (0, 0) the imbalance.  Accumulates the line weights' column
+// sums and the rows' dot products with L.  The block's 32 outaged-line flows
+// and S values are staged in shared memory, and each group of G contingencies
+// loads its L and slopes before storing any.  A pair's step (z_f times its
+// dual step size times the primal weight) is w / (S_l + |L_lk| S_k).
+template <int V>
 __global__ void __launch_bounds__(256, 3) k_lin_pairs(const LinArgs a) {
+    constexpr int KB = 32 / V;  // contingencies per block
+    constexpr int G = 8 / V;    // contingencies per load group (8 / V vectors of V lines)
     const int j = blockIdx.z;
-    const int l = blockIdx.x * 256 + threadIdx.x;
-    const int k0 = blockIdx.y * 32;
+    const int l0 = (blockIdx.x * 256 + threadIdx.x) * V;
+    const int k0 = blockIdx.y * KB;
     const float w = (float)a.w[j];
     const float *f = a.f + (size_t)j * a.n_l;
-    __shared__ float fk_s[32], sk_s[32];
-    if (threadIdx.x < 32) {
+    __shared__ float fk_s[KB], sk_s[KB];
+    if (threadIdx.x < KB) {
         const int k = k0 + threadIdx.x;
         const int kl = k < a.n_c ? __ldg(&a.ctg_line[k]) : 0;
         fk_s[threadIdx.x] = k < a.n_c ? f[kl] : 0.0f;
         sk_s[threadIdx.x] = k < a.n_c ? a.pc_S[kl] : 0.0f;
     }
     __syncthreads();
-    const bool lv = l < a.n_l;
-    const float fl = lv ? f[l] : 0.0f;
-    const float Sl = lv ? a.pc_S[l] : 1.0f;
-    const float Rc = lv ? (float)a.rate_c64[l] : 0.0f;
-    const float *__restrict__ lodf = a.lodf;
-    float *__restrict__ ac = a.a_c;
-    float col = 0.0f;
+    const bool lv = l0 < a.n_l;
+    float fl[V], Sl[V], Rc[V], col[V];
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        fl[v] = lv ? f[l0 + v] : 0.0f;
+        Sl[v] = lv ? a.pc_S[l0 + v] : 1.0f;
+        Rc[v] = lv ? (float)a.rate_c64[l0 + v] : 0.0f;
+        col[v] = 0.0f;
+    }
     __shared__ float sh[8][33];
     const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #pragma unroll
-    for (int g8 = 0; g8 < 4; ++g8) {
-        float Lt[8], av[8], rowv[8];
+    for (int g = 0; g < KB / G; ++g) {
+        VecF<V> Lt[G], av[G];
+        float rowv[G];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int k = k0 + g8 * 8 + u;
-            const bool ok = lv && k < a.n_c;
-            const size_t o = ((size_t)j * a.n_c + k) * a.n_l + l;
-            Lt[u] = ok ? __ldg(&lodf[(size_t)k * a.n_l + l]) : 0.0f;
-            av[u] = ok ? ac[o] : 0.0f;
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int kk = g8 * 8 + u, k = k0 + kk;
-            float v = 0.0f;
+        for (int u = 0; u < G; ++u) {
+            const int k = k0 + g * G + u;
             if (lv && k < a.n_c) {
-                const float fc = fmaf(Lt[u], fk_s[kk], fl);
-                const float gain = __fdividef(w, fmaf(fabsf(Lt[u]), sk_s[kk], Sl));
-                const size_t o = ((size_t)j * a.n_c + k) * a.n_l + l;
-                const float an = lin_prox(fmaf(gain, fc, av[u]), gain * Rc);
-                ac[o] = an;
-                col += an;
-                v = an * Lt[u];
+                Lt[u].load_ro(a.lodf + (size_t)k * a.n_l + l0);
+                av[u].load(a.a_c + ((size_t)j * a.n_c + k) * a.n_l + l0);
             }
-            rowv[u] = v;
         }
-        // the warp's share of the 8 rows' dot products with L
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            float v = rowv[u];
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) sh[wp][g8 * 8 + u] = v;
+        for (int u = 0; u < G; ++u) {
+            const int kk = g * G + u, k = k0 + kk;
+            float r = 0.0f;
+            if (lv && k < a.n_c) {
+                VecF<V> an;
+#pragma unroll
+                for (int v = 0; v < V; ++v) {
+                    const float L = Lt[u].v[v];
+                    const float fc = fmaf(L, fk_s[kk], fl[v]);
+                    const float gain = __fdividef(w, fmaf(fabsf(L), sk_s[kk], Sl[v]));
+                    an.v[v] = lin_prox(fmaf(gain, fc, av[u].v[v]), gain * Rc[v]);
+                    col[v] += an.v[v];
+                    r = fmaf(an.v[v], L, r);
+                }
+                an.store(a.a_c + ((size_t)j * a.n_c + k) * a.n_l + l0);
+            }
+            rowv[u] = r;
+        }
+        // the warp's share of the G rows' dot products with L
+#pragma unroll
+        for (int u = 0; u < G; ++u) {
+            float r = rowv[u];
+            for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+            if (lane == 0) sh[wp][g * G + u] = r;
         }
     }
     __syncthreads();
-    if (threadIdx.x < 32 && k0 + threadIdx.x < a.n_c) {
+    if (threadIdx.x < KB && k0 + threadIdx.x < a.n_c) {
         float t = 0.0f;
         for (int i = 0; i < 8; ++i) t += sh[i][threadIdx.x];
         atomicAdd(&a.rowdot[(size_t)j * a.n_c + k0 + threadIdx.x], t);
     }
-    if (blockIdx.y == 0 && lv) {
-        const size_t o = (size_t)j * a.n_l + l;
-        const float gain = __fdividef(w, Sl);
-        const float an = lin_prox(fmaf(gain, fl, a.a_b[o]), gain * (float)a.rate64[l]);
-        a.a_b[o] = an;
-        col += an;
+    if (!lv) return;
+#pragma unroll
+    for (int v = 0; v < V; ++v) {
+        const int l = l0 + v;
+        if (blockIdx.y == 0) {
+            const size_t o = (size_t)j * a.n_l + l;
+            const float gain = __fdividef(w, Sl[v]);
+            const float an = lin_prox(fmaf(gain, fl[v], a.a_b[o]), gain * (float)a.rate64[l]);
+            a.a_b[o] = an;
+            col[v] += an;
+        }
+        atomicAdd(&a.colsum[(size_t)j * a.n_l + l], col[v]);
     }
-    if (lv) atomicAdd(&a.colsum[(size_t)j * a.n_l + l], col);
     if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0) {
         // z_inj times the imbalance's step 1 / (z_inj n_dev) times w
         a.a0[j] = fmin(fmax(a.a0[j] + a.w[j] * a.stot[j] / (double)a.n_dev, -1.0), 1.0);
@@ -270,7 +320,12 @@ cudaError_t lin_iteration(const LinArgs &a, int num_sms, cudaStream_t s) {
     k_lin_x<<<dim3((a.n_dev + 127) / 128, a.n_box), 128, 0, s>>>(a);
     k_lin_p<<<dim3((a.n_a_pad + 127) / 128, a.n_box), 128, 0, s>>>(a);
     k_lin_flows<<<dim3((a.n_l + 7) / 8, a.n_box), 256, 0, s>>>(a);
-    k_lin_pairs<<<dim3((a.n_l + 255) / 256, std::max((a.n_c + 31) / 32, 1), a.n_box), 256, 0, s>>>(a);
+    const dim3 gp4((a.n_l / 4 + 255) / 256, std::max((a.n_c + 7) / 8, 1), a.n_box);
+    const dim3 gp2((a.n_l / 2 + 255) / 256, std::max((a.n_c + 15) / 16, 1), a.n_box);
+    const dim3 gp1((a.n_l + 255) / 256, std::max((a.n_c + 31) / 32, 1), a.n_box);
+    if (a.n_l % 4 == 0) k_lin_pairs<4><<<gp4, 256, 0, s>>>(a);
+    else if (a.n_l % 2 == 0) k_lin_pairs<2><<<gp2, 256, 0, s>>>(a);
+    else k_lin_pairs<1><<<gp1, 256, 0, s>>>(a);
     k_lin_W<<<dim3((a.n_l + 255) / 256, a.n_box), 256, 0, s>>>(a);
     if ((e = cudaMemsetAsync(a.g, 0, (size_t)a.n_box * a.n_a_pad * sizeof(float), s)) != cudaSuccess) return e;
     k_lin_g<<<dim3((a.n_a_pad / 4 + 127) / 128, (a.n_l + kLinGLines - 1) / kLinGLines, a.n_box), 128, 0, s>>>(a);

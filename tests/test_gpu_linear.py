@@ -13,7 +13,7 @@ import numpy as np
 import pytest
 
 import oracle as O
-from gen import make_config
+from gen import make_config, make_network_case
 from tests.test_gpu_parity import F64
 from tests.test_oracle_ibp import _lp_optimum
 
@@ -37,9 +37,12 @@ def _scale(case, lo, hi):
                  + case.zeta_f * (ref.terms["fb"][1][0] + ref.terms["fc"][1][0]))
 
 
-@pytest.mark.parametrize("cfg,n_iter", [(0, 3000), (1, 3000), (2, 1000)])
+@pytest.mark.parametrize("cfg,n_iter", [(0, 3000), (1, 3000), (2, 1000), ("odd", 3000)])
 def test_linear_bound_is_certified(P, cfg, n_iter):
-    case = make_config(cfg)
+    """Configs 0 and 1 have an even line count (the slope step reads two lines
+    per load), config 2 a multiple of 4 (four lines), the 37-bus network 61
+    lines (one line per load)."""
+    case = make_network_case("odd", 37, 61, 9, 20, seed=77) if cfg == "odd" else make_config(cfg)
     sens = O.sensitivities(case)
     gpu = P.Case(case, device=0)
     ub, err, xp = gpu.bound_linear(case.box_lo, case.box_hi, n_iter=n_iter)
@@ -51,7 +54,7 @@ def test_linear_bound_is_certified(P, cfg, n_iter):
     print(f"cfg {cfg}: GPU linear bound {ub[0]:.9g} (err {err[0]:.3g}), oracle at its slopes {ref:.9g}")
     assert ub[0] >= ref - d, (ub[0], ref, d)
     assert ub[0] - ref <= err[0] + d, (ub[0] - ref, err[0], d)
-    if cfg < 2:
+    if cfg in (0, 1, "odd"):
         opt, _ = _lp_optimum(case, sens)
         assert ub[0] >= opt - d
     # the primal point lies in the box
