@@ -305,8 +305,8 @@ __global__ void __launch_bounds__(WL * WK * 32, MINB)
                     float a3;
                     if constexpr (S3) a3 = acc3s[(i * MK + j) * S::kThreads];
                     else a3 = acc3[i][j];
-                    if (pair_epilogue(a, 0, l, k, Lr[i][j], __fadd_ru(a3, acc2[i][j]), slo, shi, whi, wlo,
-                                      cslo, cwhi))
+                    if (pair_epilogue_call(a, 0, l, k, Lr[i][j], __fadd_ru(a3, acc2[i][j]), slo, shi, whi, wlo,
+                                           cslo, cwhi))
                         rmask |= 1ull << (i * MK + j);
                 }
             }
