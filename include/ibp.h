@@ -277,8 +277,11 @@ ibp_status ibp_bound_multi(int32_t n_case, ibp_case *const *cases,
  *   (written, as in ibp_bound_backward).
  * At most 65535 boxes over all cases (IBP_EINVAL).  The work plan is cached
  * per set of cases and box counts (separately from ibp_bound_multi's), so
- * later calls only enqueue kernels and can be captured in a CUDA graph.  The
- * paper differentiates nothing; this is the batched form of the adjoint.
+ * later calls only enqueue kernels and can be captured in a CUDA graph.
+ * Device-side errors (a box with lo > hi, an active-pair list that
+ * overflows) are reported by ibp_case_sync of the case concerned, as for
+ * the other device-pointer calls.  The paper differentiates nothing; this is
+ * the batched form of the adjoint.
  */
 ibp_status ibp_bound_multi_backward(int32_t n_case, ibp_case *const *cases,
                                     const int32_t *n_box, const double *const *box_lo,

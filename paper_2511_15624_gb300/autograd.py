@@ -59,7 +59,8 @@ class IBPBoundMultiFunction(torch.autograd.Function):
     (``ibp_bound_multi``), backward through ``ibp_bound_multi_backward``
     (one launch per backward pass over all cases).  Inputs after ``cases``:
     box_lo_0, box_hi_0, box_lo_1, box_hi_1, ...; outputs: obj_lo_0,
-    obj_hi_0, obj_lo_1, obj_hi_1, ..."""
+    obj_hi_0, obj_lo_1, obj_hi_1, ...  Like every call on device tensors,
+    device-side errors surface at ``Case.sync()`` of the case concerned."""
 
     @staticmethod
     def forward(ctx, cases, *boxes):

@@ -208,6 +208,10 @@ class Bisection:
         v = torch.where(g > 0, self.hi, torch.where(g < 0, self.lo, self.x))
         self.y = self.x + self.s[:, None] * (v - self.x)
         keep = leaf_hi >= self.lb
+        if not bool(keep.any()):
+            # cannot happen in exact arithmetic (the leaf holding the best point
+            # bounds it from above); keep the top leaf rather than an empty frontier
+            keep = leaf_hi == leaf_hi.max()
         kidx = torch.nonzero(keep).flatten()
         lo, hi, leaf_hi = self.lo[keep], self.hi[keep], leaf_hi[keep]
         x, fx, y, sv = self.x[keep], self.fx[keep], self.y[keep], self.s[keep]
