@@ -138,7 +138,7 @@ struct ibp_case {
     DevBuf<float> lpcS;                    // [n_line] row sums S_l of the step sizes
     DevBuf<double> lpctau, lpcA, lpcB, lpcL;  // [n_dev] primal steps; scratch of their build
     DevBuf<int> cl_ptr, cl_ctg;            // contingencies per outaged line
-    DevBuf<double> lw, lx, lsx, lxb, lx_last, lxavg, la0, la0_last, lstot, lred, lub, lub_err, lbest;
+    DevBuf<double> lw, lx, lsx, lxb, lx_last, lxavg, la0, la0_last, lstot, lstotp, lred, lub, lub_err, lbest;
     DevBuf<float> lac, lc_last, lab, lb_last, lp, lf, lcol, lrow, lg;
     DevBuf<double> lW64, lWabs, lconst, lrd64, lrda, lg64, lG64;
     cudaGraphExec_t lin_graph = nullptr;   // a chunk of iterations
@@ -1361,6 +1361,7 @@ static ibp_status ensure_lin_workspace(ibp_case *c, int n_box) {
     const size_t nc = (size_t)cap * std::max(c->n_ctg, 1);
     CUDA_TRY(c->lw.alloc(cap)); CUDA_TRY(c->la0.alloc(cap));
     CUDA_TRY(c->la0_last.alloc(cap)); CUDA_TRY(c->lstot.alloc(cap)); CUDA_TRY(c->lred.alloc((size_t)cap * 4));
+    CUDA_TRY(c->lstotp.alloc((size_t)cap * ((c->n_dev + 127) / 128)));
     CUDA_TRY(c->lub.alloc(cap)); CUDA_TRY(c->lub_err.alloc(cap)); CUDA_TRY(c->lbest.alloc((size_t)cap * 2));
     CUDA_TRY(c->lx.alloc(nd)); CUDA_TRY(c->lsx.alloc(nd)); CUDA_TRY(c->lxb.alloc(nd)); CUDA_TRY(c->lx_last.alloc(nd));
     CUDA_TRY(c->lac.alloc(np)); CUDA_TRY(c->lc_last.alloc(np)); CUDA_TRY(c->lxavg.alloc(nd));
@@ -1405,7 +1406,7 @@ static LinArgs lin_args(const ibp_case *c, int n_box, const double *lo, const do
     a.a_b = c->lab.p; a.b_last = c->lb_last.p;
     a.a0 = c->la0.p; a.a0_last = c->la0_last.p;
     a.x_avg = c->lxavg.p;
-    a.p = c->lp.p; a.stot = c->lstot.p; a.f = c->lf.p; a.colsum = c->lcol.p; a.rowdot = c->lrow.p;
+    a.p = c->lp.p; a.stot = c->lstot.p; a.stot_part = c->lstotp.p; a.f = c->lf.p; a.colsum = c->lcol.p; a.rowdot = c->lrow.p;
     a.g = c->lg.p; a.red = c->lred.p;
     a.W64 = c->lW64.p; a.Wabs = c->lWabs.p; a.constl = c->lconst.p; a.rd64 = c->lrd64.p;
     a.rda = c->lrda.p; a.g64 = c->lg64.p; a.G64 = c->lG64.p; a.ub = c->lub.p; a.ub_err = c->lub_err.p;
@@ -1684,6 +1685,7 @@ extern "C" ibp_status ibp_case_linear_inherit(ibp_case *c, int32_t n_new, const 
         const size_t na = (size_t)n_new * c->n_a_pad, nc = (size_t)n_new * std::max(c->n_ctg, 1);
         CUDA_TRY(c->lx_last.alloc(nd)); CUDA_TRY(c->lxb.alloc(nd));
         CUDA_TRY(c->lstot.alloc(n_new)); CUDA_TRY(c->lred.alloc((size_t)n_new * 4));
+        CUDA_TRY(c->lstotp.alloc((size_t)n_new * ((c->n_dev + 127) / 128)));
         CUDA_TRY(c->lub.alloc(n_new)); CUDA_TRY(c->lub_err.alloc(n_new)); CUDA_TRY(c->lbest.alloc((size_t)n_new * 2));
         CUDA_TRY(c->lp.alloc(na)); CUDA_TRY(c->lf.alloc(nl)); CUDA_TRY(c->lcol.alloc(nl));
         CUDA_TRY(c->lrow.alloc(nc)); CUDA_TRY(c->lg.alloc(na));

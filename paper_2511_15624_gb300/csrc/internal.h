@@ -252,6 +252,7 @@ struct LinArgs {
     double *a0, *a0_last;                  // [n_box]
     float *p;                  // [n_box][n_a_pad] bus injections of xb
     double *stot;              // [n_box] total injection of xb
+    double *stot_part;         // [n_box][ceil(n_dev / 128)] per-block partial sums of it
     float *f;                  // [n_box][n_l] base flows of xb
     float *colsum;             // [n_box][n_l]
     float *rowdot;             // [n_box][n_c]

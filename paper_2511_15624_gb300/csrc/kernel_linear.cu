@@ -80,24 +80,35 @@ __device__ __forceinline__ double block_sum_d(double v, double *sh) {
 // extrapolated point xb = 2 x_new - x.
 __global__ void __launch_bounds__(128) k_lin_x(const LinArgs a) {
     const int j = blockIdx.y, d = blockIdx.x * blockDim.x + threadIdx.x;
-    if (d >= a.n_dev) return;
-    const size_t o = (size_t)j * a.n_dev + d;
-    const bool gen = d < a.n_gen;
-    const double sg = gen ? 1.0 : -1.0;
-    const double xo = a.x[o];
-    const int col = a.dev_col[d];
-    const double gb = col >= 0 ? (double)a.g[(size_t)j * a.n_a_pad + col] : 0.0;
-    const int s0 = a.seg_ptr[d], ns = a.seg_ptr[d + 1] - s0;
-    const double sl = lin_pwl_slope(a.slope + s0, a.bkpt + s0, ns, xo);
-    const double grad = (gen ? -sl : sl) - sg * (gb + a.zeta_inj * a.a0[j]);
-    const double xn = fmin(fmax(xo + (a.pc_tau[d] / a.w[j]) * grad, a.box_lo[o]), a.box_hi[o]);
-    a.xb[o] = 2.0 * xn - xo;
-    a.x[o] = xn;
-    a.sx[o] += xn;
+    double part = 0.0;  // this block's share of the total injection of xb
+    if (d < a.n_dev) {
+        const size_t o = (size_t)j * a.n_dev + d;
+        const bool gen = d < a.n_gen;
+        const double sg = gen ? 1.0 : -1.0;
+        const double xo = a.x[o];
+        const int col = a.dev_col[d];
+        const double gb = col >= 0 ? (double)a.g[(size_t)j * a.n_a_pad + col] : 0.0;
+        const int s0 = a.seg_ptr[d], ns = a.seg_ptr[d + 1] - s0;
+        const double sl = lin_pwl_slope(a.slope + s0, a.bkpt + s0, ns, xo);
+        const double grad = (gen ? -sl : sl) - sg * (gb + a.zeta_inj * a.a0[j]);
+        const double xn = fmin(fmax(xo + (a.pc_tau[d] / a.w[j]) * grad, a.box_lo[o]), a.box_hi[o]);
+        const double xbn = 2.0 * xn - xo;
+        a.xb[o] = xbn;
+        a.x[o] = xn;
+        a.sx[o] += xn;
+        part = sg * xbn;
+    }
+    __shared__ double sh[4];
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = part;
+    __syncthreads();
+    if (threadIdx.x == 0)
+        a.stot_part[(size_t)j * gridDim.x + blockIdx.x] = sh[0] + sh[1] + sh[2] + sh[3];
 }
 
 // Thread per (active column, box): the bus injection of xb; block 0 of each
-// box also forms the total injection (a fixed-order block sum)
+// box also adds k_lin_x's per-block partials of the total injection, in
+// block order
 __global__ void __launch_bounds__(128) k_lin_p(const LinArgs a) {
     const int j = blockIdx.y, col = blockIdx.x * blockDim.x + threadIdx.x;
     const double *xb = a.xb + (size_t)j * a.n_dev;
@@ -110,14 +121,11 @@ __global__ void __launch_bounds__(128) k_lin_p(const LinArgs a) {
             }
         a.p[(size_t)j * a.n_a_pad + col] = (float)v;
     }
-    if (blockIdx.x != 0) return;
-    double part = 0.0;
-    for (int d = threadIdx.x; d < a.n_dev; d += blockDim.x) part += (d < a.n_gen ? 1.0 : -1.0) * xb[d];
-    __shared__ double sh[4];
-    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = part;
-    __syncthreads();
-    if (threadIdx.x == 0) a.stot[j] = sh[0] + sh[1] + sh[2] + sh[3];
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    const int nb = (a.n_dev + 127) / 128;
+    double t = 0.0;
+    for (int b = 0; b < nb; ++b) t += a.stot_part[(size_t)j * nb + b];
+    a.stot[j] = t;
 }
 
 // base flows f = Phi p of xb: one warp per (line, box)
@@ -276,27 +284,30 @@ __global__ void __launch_bounds__(256, 3) k_lin_pairs(const LinArgs a) {
     }
 }
 
-// line weights W_l = colsum_l + sum over the contingencies of line l of their row dots
-__global__ void k_lin_W(const LinArgs a) {
-    const int j = blockIdx.y, l = blockIdx.x * blockDim.x + threadIdx.x;
-    if (l >= a.n_l) return;
-    float t = a.colsum[(size_t)j * a.n_l + l];
-    for (int q = a.cl_ptr[l]; q < a.cl_ptr[l + 1]; ++q) t += a.rowdot[(size_t)j * a.n_c + a.cl_ctg[q]];
-    a.colsum[(size_t)j * a.n_l + l] = t;
-}
-
 // g_b = z_f sum_l W_l Phi[l][b]: a thread takes 4 adjacent columns (one
-// 16-byte load per line) and a block row 32 lines; atomics into g
+// 16-byte load per line) and a block row 32 lines, whose weights W_l =
+// colsum_l + the row dots of the contingencies of line l it forms first in
+// shared memory; atomics into g
 constexpr int kLinGLines = 32;
 __global__ void __launch_bounds__(128) k_lin_g(const LinArgs a) {
     const int j = blockIdx.z, c4 = blockIdx.x * blockDim.x + threadIdx.x;
-    if (4 * c4 >= a.n_a_pad) return;
     const int l0 = blockIdx.y * kLinGLines, l1 = min(l0 + kLinGLines, a.n_l);
-    const float *W = a.colsum + (size_t)j * a.n_l;
+    __shared__ float W[kLinGLines];
+    if (threadIdx.x < kLinGLines) {
+        const int l = l0 + threadIdx.x;
+        float t = 0.0f;
+        if (l < a.n_l) {
+            t = a.colsum[(size_t)j * a.n_l + l];
+            for (int q = a.cl_ptr[l]; q < a.cl_ptr[l + 1]; ++q) t += a.rowdot[(size_t)j * a.n_c + a.cl_ctg[q]];
+        }
+        W[threadIdx.x] = t;
+    }
+    __syncthreads();
+    if (4 * c4 >= a.n_a_pad) return;
     float4 acc = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
 #pragma unroll 8
     for (int l = l0; l < l1; ++l) {
-        const float w = W[l];
+        const float w = W[l - l0];
         const float4 ph = __ldg(reinterpret_cast<const float4 *>(a.phi + (size_t)l * a.n_a_pad) + c4);
         acc.x = fmaf(w, ph.x, acc.x);
         acc.y = fmaf(w, ph.y, acc.y);
@@ -326,7 +337,6 @@ cudaError_t lin_iteration(const LinArgs &a, int num_sms, cudaStream_t s) {
     if (a.n_l % 4 == 0) k_lin_pairs<4><<<gp4, 256, 0, s>>>(a);
     else if (a.n_l % 2 == 0) k_lin_pairs<2><<<gp2, 256, 0, s>>>(a);
     else k_lin_pairs<1><<<gp1, 256, 0, s>>>(a);
-    k_lin_W<<<dim3((a.n_l + 255) / 256, a.n_box), 256, 0, s>>>(a);
     if ((e = cudaMemsetAsync(a.g, 0, (size_t)a.n_box * a.n_a_pad * sizeof(float), s)) != cudaSuccess) return e;
     k_lin_g<<<dim3((a.n_a_pad / 4 + 127) / 128, (a.n_l + kLinGLines - 1) / kLinGLines, a.n_box), 128, 0, s>>>(a);
     return cudaGetLastError();
@@ -359,7 +369,6 @@ __global__ void __launch_bounds__(256) k_lin_rowdot_state(const LinArgs a) {
 cudaError_t lin_gradient(const LinArgs &a, int num_sms, cudaStream_t s) {
     k_lin_colsum_state<<<dim3((a.n_l + 255) / 256, a.n_box), 256, 0, s>>>(a);
     if (a.n_c > 0) k_lin_rowdot_state<<<dim3(a.n_c, a.n_box), 256, 0, s>>>(a);
-    k_lin_W<<<dim3((a.n_l + 255) / 256, a.n_box), 256, 0, s>>>(a);
     cudaError_t e = cudaMemsetAsync(a.g, 0, (size_t)a.n_box * a.n_a_pad * sizeof(float), s);
     if (e != cudaSuccess) return e;
     k_lin_g<<<dim3((a.n_a_pad / 4 + 127) / 128, (a.n_l + kLinGLines - 1) / kLinGLines, a.n_box), 128, 0, s>>>(a);
