@@ -213,8 +213,10 @@ ibp_status ibp_bound_backward_lo(ibp_case *c, int32_t n_box, const double *box_l
  *     larger bound than the parent's last one.
  * The first call on a case computes the diagonal step sizes of the
  * iteration (row and column sums of the operator, O(n_line n_active +
- * n_ctg n_active), no synchronisation).  Memory: 8 bytes per (box,
- * contingency, line).  ptr_mode and stream as in ibp_bound.
+ * n_ctg n_active), no synchronisation).  Each call captures its chunk of 50
+ * iterations into a CUDA graph on a private stream, so the call itself must
+ * not be made while the caller's stream is being captured.  Memory: 8 bytes
+ * per (box, contingency, line).  ptr_mode and stream as in ibp_bound.
  */
 ibp_status ibp_bound_linear(ibp_case *c, int32_t n_box, const double *box_lo,
                             const double *box_hi, int32_t n_iter, double primal_weight,
