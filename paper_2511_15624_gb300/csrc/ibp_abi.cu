@@ -2171,9 +2171,9 @@ extern "C" ibp_status ibp_bound_multi_backward(int32_t n_case, ibp_case *const *
                                                const double *const *grad_obj, double *const *grad_lo,
                                                double *const *grad_hi, double *const *grad_rating,
                                                int32_t side, void *cuda_stream) {
+    if (side != 0 && side != 1) return fail(IBP_EINVAL, "side must be 0 (obj_hi) or 1 (obj_lo)");
     ibp_status st = check_multi_args(n_case, cases, n_box, box_lo, box_hi);
     if (st != IBP_OK) return st;
-    if (side != 0 && side != 1) return fail(IBP_EINVAL, "side must be 0 (obj_hi) or 1 (obj_lo)");
     if (n_case == 0) return ok();
     if (!grad_obj || !grad_lo || !grad_hi) return fail(IBP_EINVAL, "array arguments must not be NULL");
     long long n_items = 0;

@@ -171,3 +171,30 @@ def test_kernel_variant_lists(pkg):
     assert len(set(one)) == len(one) and len(set(many)) == len(many)
     assert not set(one) & set(many)
     assert 16 in one and 29 in many
+
+
+def test_linear_and_batched_adjoint_validation(pkg):
+    """The linear-relaxation and batched-adjoint entry points check their
+    arguments on the host, before any device work: boxes, iteration count,
+    primal weight, warm-start index, adjoint side."""
+    P = pkg
+    c = make_config(0)
+    d = P.dry_run_case(c)
+    lo, hi = c.box_lo.copy(), c.box_hi.copy()
+    bad = lo.copy()
+    bad[0, 1] = hi[0, 1] + 1.0
+    _expect(P, P._abi.IBP_EINVAL, lambda: d.bound_linear(bad, hi, n_iter=10))
+    _expect(P, P._abi.IBP_EINVAL, lambda: d.bound_linear(lo, hi, n_iter=-1))
+    _expect(P, P._abi.IBP_EINVAL, lambda: d.bound_linear(lo, hi, n_iter=10, primal_weight=0.0))
+    _expect(P, P._abi.IBP_EINVAL, lambda: d.bound_linear(lo, hi, n_iter=10, primal_weight=float("nan")))
+    ub, err, xp = np.empty(1), np.empty(1), np.empty_like(lo)
+    _expect(P, P._abi.IBP_EINVAL, lambda: P._abi.ibp_bound_linear(d.handle, 1, lo, hi, 10, 0.01, ub, err, xp,
+                                                                   ptr_mode=0, warm=-1))
+    _expect(P, P._abi.IBP_ENOTSUP, lambda: d.bound_linear(lo, hi, n_iter=10))
+    _expect(P, P._abi.IBP_ENOTSUP, lambda: d.linear_inherit(np.zeros(1, np.int32)))
+    g = [np.ones(1)]
+    out = [np.empty_like(lo)]
+    _expect(P, P._abi.IBP_EINVAL, lambda: P._abi.ibp_bound_multi_backward(
+        [d.handle], [1], [lo], [hi], g, out, out, side=2))
+    _expect(P, P._abi.IBP_ENOTSUP, lambda: P._abi.ibp_bound_multi_backward(
+        [d.handle], [1], [lo], [hi], g, out, out, side=0))
