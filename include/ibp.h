@@ -225,7 +225,8 @@ ibp_status ibp_bound_linear(ibp_case *c, int32_t n_box, const double *box_lo,
 
 /* Keep optimising from the state a case holds (warm != 0 in ibp_bound_linear,
  * primal_weight then ignored): box j of the next call continues from the
- * slopes, running sums, point and primal weight of box parent[j] of the last
+ * slopes, their last adaptation's reference, the point, its running sum and
+ * the primal weight of box parent[j] of the last
  * call or inheritance (host array [n_new]).  A sub-box can start from its
  * parent's slopes: any slopes give a certified bound, and the parent's bound
  * already holds for the sub-box.  Synchronises the device.  No counterpart in
