@@ -175,3 +175,50 @@ def test_ragged_autograd_fd_on_8_networks_of_all_sizes(env):
                     (net.name, which, d, fd, g[d], allow[d])
         print(f"{net.name}: FD checked on {min(4, len(ok_dims))} devices ({n_near} decisions near a kink, "
               f"{len(ok_dims)} of {net.n_dev} devices eligible)")
+
+
+def test_batched_backward_in_cuda_graph():
+    """The batched adjoint's plan is built outside capture; captured in a CUDA
+    graph, a replay gives the direct call's gradients (up to the order of the
+    FP64 atomic sums, 1e-9) and picks up new boxes written into the same input
+    tensors."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2511_15624_gb300 as P
+    nets = make_ragged_batch(n_net=6, n_sub=4, seed=77, sizes=(73, 300, 500))
+    cases = [P.Case(n, device=0) for n in nets]
+    los = [torch.tensor(n.box_lo, device="cuda") for n in nets]
+    his = [torch.tensor(n.box_hi, device="cuda") for n in nets]
+    gobj = [torch.ones(n.n_box, dtype=torch.float64, device="cuda") for n in nets]
+    ref = P.bound_multi_backward(cases, los, his, gobj)  # plan and workspaces, outside capture
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        P.bound_multi_backward(cases, los, his, gobj, stream=s.cuda_stream)
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        outs = P.bound_multi_backward(cases, los, his, gobj, stream=s.cuda_stream)
+    g.replay()
+    torch.cuda.synchronize()
+    def close(x, y):
+        x, y = x.cpu().numpy(), y.cpu().numpy()
+        np.testing.assert_allclose(x, y, rtol=1e-9, atol=1e-12 * max(np.abs(y).max(), 1.0))
+
+    for (a, b, _), (c, d, _) in zip(outs, ref):
+        close(a, c)
+        close(b, d)
+    # new boxes in the same tensors: the replay follows them
+    his[0].copy_(his[0] - 0.1 * (his[0] - los[0]))
+    g.replay()
+    torch.cuda.synchronize()
+    direct = P.bound_multi_backward(cases[:1], los[:1], his[:1], gobj[:1])
+    torch.cuda.synchronize()
+    close(outs[0][0], direct[0][0])
+    close(outs[0][1], direct[0][1])
+    for c in cases:
+        c.sync()
+        c.close()
