@@ -119,3 +119,90 @@ def test_multi_in_cuda_graph(env):
     lo1, hi1, _ = cases[0].bound(nets[0].box_lo, his[0].cpu().numpy())
     cases[0].set_screen(True)
     np.testing.assert_allclose(outs[0][1].cpu().numpy(), hi1, rtol=1e-12)
+
+
+def test_multi_edge_cases():
+    """The many-case launch and its batched adjoint with the cases a batch can
+    hold at its edges: a network without contingencies, duplicated
+    contingencies, separate contingency ratings, an odd line count, one box,
+    and 17 boxes (a second, nearly empty box tile).  Forward against the
+    oracle at the objective bar; adjoint against the per-case adjoint."""
+    import dataclasses
+
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2511_15624_gb300 as P
+    from gen import make_config, make_network_case, split_boxes
+    from tests.test_gpu_parity import check_objective
+
+    base = make_config(1)
+    rng = np.random.default_rng(11)
+    nets = [
+        dataclasses.replace(base, ctg_line=np.zeros(0, np.int32)),               # no contingencies
+        dataclasses.replace(make_config(0), ctg_line=np.concatenate(
+            [make_config(0).ctg_line, make_config(0).ctg_line[:2]]).astype(np.int32)),  # duplicates
+        dataclasses.replace(base, rating_ctg=base.rating * 1.3),                 # separate ratings
+        make_network_case("odd", 37, 61, 9, 20, seed=77),                       # odd line count
+    ]
+    # box counts 1, 17, 4, 17
+    counts = [1, 17, 4, 17]
+    boxed = []
+    for n, nb in zip(nets, counts):
+        if nb == 1:
+            boxed.append(n)
+            continue
+        levels = int(np.ceil(np.log2(nb)))
+        lo, hi = split_boxes(n.box_lo[0], n.box_hi[0], levels, rng)
+        boxed.append(n.with_boxes(lo[:nb], hi[:nb]))
+    cases = [P.Case(n, device=0) for n in boxed]
+    los = [torch.tensor(n.box_lo, device="cuda") for n in boxed]
+    his = [torch.tensor(n.box_hi, device="cuda") for n in boxed]
+    outs = P.bound_multi(cases, los, his)
+    torch.cuda.synchronize()
+    for n, c, o in zip(boxed, cases, outs):
+        c.sync()
+        lo, hi, err = (t.cpu().numpy() for t in o)
+        ref = O.bound(n, O.sensitivities(n))
+        check_objective(lo, hi, err, ref, rel_scale=np.abs(ref.terms["costs"]).sum(axis=1))
+    gobj = [torch.ones(n.n_box, dtype=torch.float64, device="cuda") for n in boxed]
+    grads = P.bound_multi_backward(cases, los, his, gobj)
+    torch.cuda.synchronize()
+    for n, c, (glo, ghi, _) in zip(boxed, cases, grads):
+        c.sync()
+        c.set_screen(False)
+        rlo, rhi = c.backward(n.box_lo, n.box_hi, np.ones(n.n_box))
+        c.set_screen(True)
+        scale = max(np.abs(rlo).max(), np.abs(rhi).max(), 1e-300)
+        assert np.abs(glo.cpu().numpy() - rlo).max() <= 1e-9 * scale, n.name
+        assert np.abs(ghi.cpu().numpy() - rhi).max() <= 1e-9 * scale, n.name
+    for c in cases:
+        c.close()
+
+
+def test_linear_bound_without_contingencies():
+    """The linear relaxation on a network without contingencies (only base
+    lines and the imbalance carry slopes): certified against the oracle's
+    evaluation at the GPU's slopes and above the LP optimum."""
+    import dataclasses
+
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    import paper_2511_15624_gb300 as P
+    from gen import make_config
+    from tests.test_gpu_parity import F64, side_scales
+    from tests.test_oracle_ibp import _lp_optimum
+
+    case = dataclasses.replace(make_config(1), ctg_line=np.zeros(0, np.int32))
+    sens = O.sensitivities(case)
+    gpu = P.Case(case, device=0)
+    ub, err, xp = gpu.bound_linear(case.box_lo, case.box_hi, n_iter=5000)
+    a_c, a_b, a0 = gpu.linear_slopes(1)
+    ref = O.linear_bound(case, sens, case.box_lo[0], case.box_hi[0], a_b[0], a_c[0], a0[0])
+    d = F64 * float(side_scales(O.bound(case, sens))[0][0])
+    assert ub[0] >= ref - d and ub[0] - ref <= err[0] + d, (ub[0], ref)
+    opt, _ = _lp_optimum(case, sens)
+    assert ub[0] >= opt - d
+    print(f"no contingencies: linear {ub[0]:.7g}, LP optimum {opt:.7g}")
+    gpu.close()
