@@ -20,12 +20,13 @@
 // with the operator D K (K: x -> the flows and the total injection, D: their
 // z_f / z_inj weights) and diagonal step sizes (Pock and Chambolle, ICCV
 // 2011, alpha = 1: the inverse row and column sums of |D K|, here bounded
-// from above by the triangle inequality) split by a primal weight, restarts
-// to the running averages with the primal weight adapted to the ratio of the
-// dual and primal moves in the step-weighted norms (as in PDLP, Applegate et
-// al., NeurIPS 2021).  A restart keeps the current iterate (no averaging of
-// the slopes, so the slope step moves 12 bytes per pair, not 20); the
-// averaged primal point of each restart window is the candidate maximiser.
+// from above by the triangle inequality) split by a primal weight, which
+// every 1000 iterations moves halfway (in log) to the ratio of the dual and
+// primal moves in the step-weighted norms (PDLP's primal weight update,
+// Applegate et al., NeurIPS 2021).  The iterate is kept at these adaptations
+// (no restart to averages of the slopes, so the slope step moves 12 bytes per
+// pair, not 20); the primal point averaged over each window is the candidate
+// maximiser.
 // The iterations run in FP32/FP64 without rounding control; the certified
 // value U(a) at the final slopes is computed in FP64 with an explicit error
 // bound (lin_certify).
@@ -186,10 +187,10 @@ struct VecF {
 // Dual step on the slopes: block (x: 256 threads of V adjacent lines each,
 // y: 32 / V contingencies, z: box), so a thread takes 32 pairs whatever V;
 // n_l is a multiple of V, so every row of L and of the slopes starts
-// V-aligned.  Blocks with y == 0 also take the base
-// flows, block (0, 0) the imbalance.  Accumulates the line weights' column
-// sums and the rows' dot products with L.  The block's 32 outaged-line flows
-// and S values are staged in shared memory, and each group of G contingencies
+// V-aligned.  Blocks with y == 0 also take the base flows, block (0, 0) the
+// imbalance.  Accumulates the line weights' column sums and the rows' dot
+// products with L.  The block's outaged-line flows and S values are staged in
+// shared memory, and each group of G contingencies
 // loads its L and slopes before storing any.  A pair's step (z_f times its
 // dual step size times the primal weight) is w / (S_l + |L_lk| S_k).
 template <int V>
