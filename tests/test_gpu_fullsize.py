@@ -42,6 +42,16 @@ def _report(olo, ohi, err, ref, what):
     assert dev_lo[0] <= F64 * lo_s[0] / abs(ref.lo[0]) and dev_lo[0] >= -1e-5
 
 
+_ROOT = {}
+
+
+def _root_bound(case, sens):
+    """The oracle's complete bound of the root box (computed once per module)."""
+    if "ref" not in _ROOT:
+        _ROOT["ref"] = O.bound(case, sens)
+    return _ROOT["ref"]
+
+
 def test_fullsize_one_box_default_launch(env):
     P, torch, case, sens, gpu = env
     lo = torch.tensor(case.box_lo, device="cuda")
@@ -49,7 +59,7 @@ def test_fullsize_one_box_default_launch(env):
     olo, ohi, err = (t.cpu().numpy() for t in gpu.bound(lo, hi))
     n, _ = gpu.last_live()
     assert 0 < n < case.n_line  # the screen and the reduction were in the path
-    ref = O.bound(case, sens)
+    ref = _root_bound(case, sens)
     _report(olo, ohi, err, ref, "one box")
 
 
@@ -72,3 +82,24 @@ def test_fullsize_sampled_flows(env):
     pl = rng.integers(0, case.n_line, 20000)
     pl[:200] = case.ctg_line[pk[:200]]  # include outaged lines
     check_flows(case, sens, case.box_lo, case.box_hi, flo, fhi, pk, pl)
+
+
+def test_fullsize_linear_bound_is_certified(env):
+    """The linear relaxation at 8316 buses: at the slopes the GPU ends with,
+    the oracle's own evaluation of the dual function (factored form, pinned
+    against the explicit one on small cases) lies at or below the GPU's
+    certified value and within its error bound plus the FP64 build allowance
+    (1e-10 of the objective's terms); the bound is far below IBP's."""
+    P, torch, case, sens, gpu = env
+    ub, err, xp = gpu.bound_linear(case.box_lo, case.box_hi, n_iter=2000)
+    a_c, a_b, a0 = gpu.linear_slopes(1)
+    val = O.linear_bound(case, sens, case.box_lo[0], case.box_hi[0], a_b[0], a_c[0], a0[0], factored=True)
+    ref = _root_bound(case, sens)
+    scale = float(np.abs(ref.terms["costs"]).sum() + case.zeta_inj * ref.terms["inj"][1][0]
+                  + case.zeta_f * (ref.terms["fb"][1][0] + ref.terms["fc"][1][0]))
+    d = F64 * scale
+    print(f"mesh8316 linear: GPU {ub[0]:.10g} (err {err[0]:.3g}), oracle at its slopes {val:.10g}, "
+          f"difference {ub[0] - val:.3g}, allowance {d:.3g}; IBP hi {ref.hi[0]:.6g}")
+    assert ub[0] >= val - d, (ub[0], val, d)
+    assert ub[0] - val <= err[0] + d, (ub[0] - val, err[0], d)
+    assert ub[0] < ref.hi[0]
