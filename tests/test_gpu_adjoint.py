@@ -128,3 +128,31 @@ def test_multi_box_adjoint_and_autograd(P):
     gs = max(np.abs(glo).max(), np.abs(ghi).max())
     np.testing.assert_allclose(tlo.grad.cpu().numpy(), glo, rtol=0, atol=1e-9 * gs)
     np.testing.assert_allclose(thi.grad.cpu().numpy(), ghi, rtol=0, atol=1e-9 * gs)
+
+
+def test_adjoint_on_the_2000_bus_case(P):
+    """The adjoint of obj_hi at the 2000-bus root box against the oracle's hand
+    gradient, device by device: within 1e-6 of the gradient's scale plus, per
+    device, the contribution of the few active-set decisions that sit within
+    1e-5 of the flow scale of their kink (each may be taken either way by the
+    GPU's rounding; see the 64-network test's allowance); both the box
+    endpoints and the rating gradient."""
+    from tests.test_gpu_ragged import _fd_setup
+    case = make_config(2)
+    sens = O.sensitivities(case)
+    gpu = P.Case(case, device=0)
+    g_lo, g_hi, g_r = gpu.backward(case.box_lo, case.box_hi, np.ones(1), want_rating=True)
+    o_lo, o_hi, o_r = O.grad_hi(case, sens)
+    setup = _fd_setup(case, sens, case.box_lo[0], case.box_hi[0])
+    assert setup is not None
+    _, allow, n_near = setup
+    gscale = max(np.abs(o_lo).max(), np.abs(o_hi).max())
+    dev = max(np.max(np.abs(g_lo[0] - o_lo[0]) - allow), np.max(np.abs(g_hi[0] - o_hi[0]) - allow))
+    print(f"2000 buses: adjoint excess over the near-kink allowance {dev / gscale:.2e} of the scale "
+          f"({n_near} decisions near a kink)")
+    assert dev <= 1e-6 * gscale
+    # rating gradient: z_f times the active counts; a near-kink decision moves one count
+    rb, rc = O.grad_hi_ratings(case, sens, case.box_lo, case.box_hi)
+    o_r = (rb + rc)[0]
+    assert np.all(np.abs(g_r[0] - o_r) <= case.zeta_f * n_near + 1e-9 * case.zeta_f)
+    gpu.close()
