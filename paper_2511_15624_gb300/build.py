@@ -19,8 +19,8 @@ CSRC = os.path.join(PKG, "csrc")
 OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "libibp_gb300.so")
 LIB_CHECK = os.path.join(OUT_DIR, "libibp_gb300_check.so")
-SOURCES = ["ibp_abi.cu", "kernels_aux.cu", "kernel_ctg.cu", "kernel_screen.cu", "kernels_bwd.cu",
-           "noalloc.cu", "kernel_linear.cu"]
+SOURCES = ["ibp_abi.cu", "abi_linear.cu", "abi_multi.cu", "kernels_aux.cu", "kernel_ctg.cu",
+           "kernel_screen.cu", "kernels_bwd.cu", "noalloc.cu", "kernel_linear.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -1,30 +1,13 @@
 // C ABI of the library: argument validation, host-side graph checks, the FP64
-// sensitivity build, per-call workspace and the launch sequence of a bound.
-#include "internal.h"
-
-#include <cudaTypedefs.h>
-#include <cusolverDn.h>
-
-#include <algorithm>
-#include <atomic>
-#include <chrono>
-#include <cmath>
-#include <cstdarg>
-#include <cstdio>
-#include <cstring>
-#include <map>
-#include <mutex>
-#include <memory>
-#include <numeric>
-#include <string>
-#include <vector>
-
-using namespace ibp;
+// sensitivity build, per-call workspace, the launch sequence of a bound and of
+// its adjoints, and the case settings.  The linear relaxation bound is in
+// abi_linear.cu, many cases in one launch in abi_multi.cu.
+#include "abi_case.h"
 
 // ----------------------------------------------------------------- errors
 static thread_local std::string g_last_error;
 
-static ibp_status fail(ibp_status s, const char *fmt, ...) {
+ibp_status fail(ibp_status s, const char *fmt, ...) {
     char buf[512];
     va_list ap;
     va_start(ap, fmt);
@@ -34,175 +17,17 @@ static ibp_status fail(ibp_status s, const char *fmt, ...) {
     return s;
 }
 
-static ibp_status ok() {
+ibp_status ok() {
     g_last_error.clear();
     return IBP_OK;
 }
 
-#define CUDA_TRY(expr)                                                                      \
-    do {                                                                                    \
-        cudaError_t _e = (expr);                                                            \
-        if (_e != cudaSuccess)                                                              \
-            return fail(_e == cudaErrorMemoryAllocation ? IBP_ENOMEM : IBP_ECUDA,           \
-                        "%s failed: %s", #expr, cudaGetErrorString(_e));                    \
-    } while (0)
-
-// Restores the caller's current device on scope exit.
-struct DeviceGuard {
-    int prev = -1;
-    bool ok = false;
-    explicit DeviceGuard(int dev) {
-        if (cudaGetDevice(&prev) == cudaSuccess && cudaSetDevice(dev) == cudaSuccess) ok = true;
-    }
-    ~DeviceGuard() {
-        if (prev >= 0) cudaSetDevice(prev);
-    }
-};
-
 // Test hook: device allocations larger than this many bytes fail as if the
 // device were out of memory (0: no limit).  See ibp_set_alloc_limit.
-static std::atomic<long long> g_alloc_limit{0};
-
-template <class T>
-struct DevBuf {
-    T *p = nullptr;
-    size_t n = 0;
-    cudaError_t alloc(size_t count) {
-        free();
-        if (count == 0) count = 1;
-        const long long lim = g_alloc_limit.load();
-        if (lim > 0 && (long long)(count * sizeof(T)) > lim) return cudaErrorMemoryAllocation;
-        cudaError_t e = cudaMalloc(&p, count * sizeof(T));
-        if (e == cudaSuccess) n = count;
-        else p = nullptr;
-        return e;
-    }
-    void free() {
-        if (p) cudaFree(p);
-        p = nullptr;
-        n = 0;
-    }
-    ~DevBuf() { free(); }
-};
-
-// ----------------------------------------------------------------- the case
-struct ibp_case {
-    int device = -1;
-    int n_bus = 0, slack = 0, n_line = 0, n_gen = 0, n_load = 0, n_dev = 0, n_ctg = 0;
-    int n_a = 0, n_a_pad = 0;
-    double zeta_inj = 0, zeta_f = 0;
-    double build_seconds = 0, max_abs_lodf = 0;
-    int num_sms = 0;
-    int variant = 0;
-    bool screen = true;      // paper-mode line screen ahead of the contingency kernel
-    bool reduce = true;      // exact network reduction (bridges, bus classes)
-    bool refine = true;      // FP64 refinement of the terms that can reach obj_hi
-    bool has_reduction = false;
-    int n_r = 0, n_r_pad = 0, n_bridges = 0;  // bus classes, bridge lines
-    std::vector<int> cls_ptr_h, cls_col_h, is_bridge_h;
-    int last_screened = 0;   // whether the last bound call ran the screen
-    std::vector<int> ctg_line_h;
-
-    // persistent device data
-    DevBuf<float> phi_a, lodf, rate_up, rate_dn, rate_c_up, rate_c_dn;
-    DevBuf<double> phi64;             // the FP64 PTDF of the active columns
-    DevBuf<float> lodf_lo;             // RN32(L - L~) of the contingency list
-    DevBuf<double> rate64, rate_c64;   // ratings as given (FP64)
-    DevBuf<int> ctg_line, act_ptr, act_dev, seg_ptr, dev_col;
-    DevBuf<double> slope, bkpt;
-    DevBuf<float> hat_l, hat_k;  // one-box scaled rows (lazily allocated)
-    DevBuf<float> phi_k;         // unscaled PTDF rows of the contingency lines
-    // network reduction: bridge flags, bus classes (CSR over active columns)
-    // and the PTDF columns of one member per class, [n_l][n_r_pad] and the
-    // contingency rows [n_c][n_r_pad]
-    DevBuf<int> is_bridge, cls_ptr, cls_col;
-    DevBuf<float> phi_r, phi_kr;
-    // many-case launch: the non-bridge lines (list, count on the device) and
-    // their reduced rows [n_nb][n_r_pad], built on first use
-    int n_nb = -1;
-    DevBuf<int> nb_list, nb_count;
-    DevBuf<float> phi_nb;
-
-    // per-call workspace (ws_gen changes whenever its buffers move)
-    int cap_box = 0, ws_gen = 0;
-    DevBuf<double> box_lo, box_hi, obj;
-    DevBuf<double> cbus;
-    DevBuf<float2> cbus2;
-    DevBuf<float> rbus, cabs, box_consts, line_c, line_e, line_R, rbus_t, bus_part;
-    DevBuf<double> rbus64;
-    DevBuf<double> lc64, lR64;  // paper-mode refinement: per-line FP64 centre and radius
-    DevBuf<float> lX;
-    // linear (CROWN-style) relaxation bound: iteration state and certified value
-    int lin_cap_box = 0, lin_state_box = 0;  // boxes the workspace holds / the state describes
-    bool lin_pc_ready = false;             // the diagonal step sizes are computed (once per case)
-    DevBuf<float> lpcS;                    // [n_line] row sums S_l of the step sizes
-    DevBuf<double> lpctau, lpcA, lpcB, lpcL;  // [n_dev] primal steps; scratch of their build
-    DevBuf<int> cl_ptr, cl_ctg;            // contingencies per outaged line
-    DevBuf<double> lw, lx, lsx, lxb, lx_last, lxavg, la0, la0_last, lstot, lstotp, lred, lub, lub_err, lbest;
-    DevBuf<float> lac, lc_last, lab, lb_last, lp, lf, lcol, lrow, lg;
-    DevBuf<double> lW64, lWabs, lconst, lrd64, lrda, lg64, lG64;
-    cudaGraphExec_t lin_graph = nullptr;   // a chunk of iterations
-    // refinement queues of the contingency launch (regions per CTA and warp)
-    DevBuf<int4> refq;
-    DevBuf<int> refq_cnt;
-    DevBuf<double2> refq_res;
-    DevBuf<double> part_base, part_ctg, part_stage;
-    DevBuf<float> flows;
-    DevBuf<int> err;
-    DevBuf<int> rating_flag;  // sticky: the last ibp_case_set_ratings found a bad entry
-    DevBuf<int> live_flag, live, n_live;  // line screen
-    DevBuf<float> rcls, rcls_t;           // class radii [box][n_r_pad], [n_r_pad][box_pad]
-    // adjoint workspace (obj_hi's active pairs; obj_lo's in the _lo buffers)
-    int bwd_cap_box = 0, act_cap = 0;
-    DevBuf<int> act_count, cnt;
-    DevBuf<int4> act_list;
-    int bwd_lo_cap_box = 0, act_cap_lo = 0;
-    DevBuf<int> act_count_lo;
-    DevBuf<int4> act_list_lo;
-    DevBuf<double> W, dc, dr, grads;
-    int n_part_base = 0;
-
-    // timing
-    bool timing = false;
-    static constexpr int kEvents = 7;
-    cudaEvent_t ev[kEvents] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-    // completion of the case's last enqueued call (recorded on that call's
-    // stream), and a private non-blocking stream for reading the error word:
-    // ibp_case_sync waits for this case's work only, not the whole device.
-    // A call enqueued while its stream was being captured cannot be waited
-    // for through the event; the next sync then waits for the device.
-    cudaEvent_t done = nullptr;
-    cudaStream_t side = nullptr;
-    bool captured = false;
-
-    ~ibp_case() {
-        if (device >= 0) {
-            DeviceGuard g(device);
-            for (auto &e : ev)
-                if (e) cudaEventDestroy(e);
-            if (done) cudaEventDestroy(done);
-            if (lin_graph) cudaGraphExecDestroy(lin_graph);
-            if (side) cudaStreamDestroy(side);
-            phi_a.free(); lodf.free(); rate_up.free(); rate_dn.free(); rate_c_up.free();
-            phi64.free(); lodf_lo.free(); rate64.free(); rate_c64.free(); rbus64.free();
-            lc64.free(); lR64.free(); lX.free(); refq.free(); refq_cnt.free(); refq_res.free();
-            rate_c_dn.free(); ctg_line.free(); act_ptr.free(); act_dev.free(); seg_ptr.free();
-            slope.free(); bkpt.free(); hat_l.free(); hat_k.free(); phi_k.free(); rbus_t.free();
-            box_lo.free(); box_hi.free();
-            obj.free(); cbus.free(); cbus2.free(); rbus.free(); cabs.free(); box_consts.free(); bus_part.free(); line_c.free();
-            line_e.free(); line_R.free(); part_base.free(); part_ctg.free(); part_stage.free(); flows.free(); err.free();
-            live_flag.free(); live.free(); n_live.free(); is_bridge.free(); cls_ptr.free(); rating_flag.free();
-            cls_col.free(); phi_r.free(); phi_kr.free(); rcls.free(); rcls_t.free(); nb_list.free();
-            nb_count.free(); phi_nb.free();
-            dev_col.free(); act_count.free(); cnt.free(); act_list.free(); W.free(); dc.free(); dr.free();
-            act_count_lo.free(); act_list_lo.free();
-            grads.free();
-        }
-    }
-};
+std::atomic<long long> g_alloc_limit{0};
 
 // ----------------------------------------------------------------- helpers
-static bool is_fin(double x) { return std::isfinite(x); }
+bool is_fin(double x) { return std::isfinite(x); }
 
 static ibp_status check_pwl(const char *what, int n, const int32_t *nseg, const double *slope,
                             const double *bkpt, std::vector<int> &ptr) {
@@ -358,7 +183,7 @@ static void bus_classes(int n, const std::vector<std::vector<std::pair<int, int>
 
 // worst-case relative excess of a round-up sum accumulated in levels of
 // n1, n2, n3 terms: (1 + 2u)^(n1 + n2 + n3) - 1, with slack
-static float rup_gamma(long n1, long n2, long n3) {
+float rup_gamma(long n1, long n2, long n3) {
     const double u = std::ldexp(1.0, -24);
     const double n = (double)(n1 + n2 + n3 + 2);
     return (float)(std::expm1(n * std::log1p(2 * u)) * 1.01);
@@ -745,7 +570,6 @@ extern "C" ibp_status ibp_case_create(int32_t n_bus, int32_t slack_bus, int32_t 
     return ok();
 }
 
-static void drop_plans_of(const ibp_case *c);
 extern "C" void ibp_case_destroy(ibp_case *c) {
     if (!c) return;
     drop_plans_of(c);
@@ -791,7 +615,7 @@ static const CtgVariant *pick_variant(const ibp_case *c, int n_box) {
 }
 
 // partial-sum rows of the contingency kernels: (line, contingency) tiles x warps
-static size_t max_part_rows(const ibp_case *c) {
+size_t max_part_rows(const ibp_case *c) {
     int n;
     size_t best = 1;
     const CtgVariant *v = ctg_variants(&n);
@@ -804,9 +628,8 @@ static size_t max_part_rows(const ibp_case *c) {
 }
 
 // blocks per box of the first stage of the contingency partial sums
-constexpr int kPartStages = 64;
 
-static ibp_status ensure_workspace(ibp_case *c, int n_box) {
+ibp_status ensure_workspace(ibp_case *c, int n_box) {
     if (n_box <= c->cap_box) return IBP_OK;
     const int cap = std::max(n_box, 1);
     const size_t na = c->n_a_pad;
@@ -843,7 +666,7 @@ static ibp_status ensure_workspace(ibp_case *c, int n_box) {
 }
 
 // class radii of the reduction, sized like the other per-box buffers
-static ibp_status ensure_class_ws(ibp_case *c) {
+ibp_status ensure_class_ws(ibp_case *c) {
     const size_t cap_pad = (size_t)(c->cap_box + kBoxTile - 1) / kBoxTile * kBoxTile;
     if (c->rcls.n >= (size_t)c->cap_box * c->n_r_pad && c->rcls_t.n >= cap_pad * c->n_r_pad)
         return IBP_OK;
@@ -855,7 +678,7 @@ static ibp_status ensure_class_ws(ibp_case *c) {
 
 // Arguments of the FP64 refinement of the terms that can reach obj_hi (all
 // null when the case does not refine).
-static RefArgs ref_args(const ibp_case *c) {
+RefArgs ref_args(const ibp_case *c) {
     RefArgs r{};
     if (!c->refine || !c->phi64.p) return r;
     r.phi_hi = c->phi_a.p; r.phi64 = c->phi64.p; r.cbus = c->cbus.p; r.rbus64 = c->rbus64.p;
@@ -867,20 +690,11 @@ static RefArgs ref_args(const ibp_case *c) {
 
 // The global refinement queues of a contingency launch: kRefQCap entries per
 // (CTA, warp) region, for up to kRefRegionsPerSm regions per SM.
-static int ref_regions(int num_sms) { return num_sms * kRefRegionsPerSm; }
+int ref_regions(int num_sms) { return num_sms * kRefRegionsPerSm; }
 
-template <class Q>
-static ibp_status ensure_ref_queue(Q *q, int num_sms) {
-    const size_t n = (size_t)ref_regions(num_sms);
-    if (q->refq.n >= n * kRefQCap && q->refq_cnt.n >= n && q->refq_res.n >= n * kRefQCap) return IBP_OK;
-    CUDA_TRY(q->refq.alloc(n * kRefQCap));
-    CUDA_TRY(q->refq_cnt.alloc(n));
-    CUDA_TRY(q->refq_res.alloc(n * kRefQCap));
-    return IBP_OK;
-}
 
 // Record the completion of the work just enqueued on s for ibp_case_sync.
-static ibp_status mark_done(ibp_case *c, cudaStream_t s) {
+ibp_status mark_done(ibp_case *c, cudaStream_t s) {
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     CUDA_TRY(cudaStreamIsCapturing(s, &cs));
     if (cs != cudaStreamCaptureStatusNone) {
@@ -893,7 +707,7 @@ static ibp_status mark_done(ibp_case *c, cudaStream_t s) {
 
 // Wait for the case's last call: its completion event, or the device when a
 // call was captured into a graph since the last wait.
-static ibp_status wait_case(ibp_case *c) {
+ibp_status wait_case(ibp_case *c) {
     if (c->captured) {
         CUDA_TRY(cudaDeviceSynchronize());
         c->captured = false;
@@ -1123,7 +937,7 @@ static ibp_status enqueue_bound(ibp_case *c, int n_box, const double *lo, const 
 
 // Reads the error word through the case's private stream (no wait on other
 // streams); the caller has waited for the work that writes it.
-static ibp_status read_err_word(ibp_case *c) {
+ibp_status read_err_word(ibp_case *c) {
     int e = 0, rf = 0;
     CUDA_TRY(cudaMemcpyAsync(&e, c->err.p, sizeof(int), cudaMemcpyDeviceToHost, c->side));
     if (c->rating_flag.p)
@@ -1139,7 +953,7 @@ static ibp_status read_err_word(ibp_case *c) {
     return IBP_OK;
 }
 
-static ibp_status check_boxes_host(const ibp_case *c, int n_box, const double *lo, const double *hi) {
+ibp_status check_boxes_host(const ibp_case *c, int n_box, const double *lo, const double *hi) {
     const size_t n = (size_t)n_box * c->n_dev;
     for (size_t i = 0; i < n; ++i) {
         if (!is_fin(lo[i]) || !is_fin(hi[i]))
@@ -1152,7 +966,6 @@ static ibp_status check_boxes_host(const ibp_case *c, int n_box, const double *l
 }
 
 // boxes per call: several kernels put the box index on a grid's y dimension
-constexpr int32_t kMaxBoxesPerCall = 65535;
 
 static ibp_status bound_entry(ibp_case *c, int32_t n_box, const double *box_lo,
                               const double *box_hi, double *obj_lo, double *obj_hi, double *obj_err,
@@ -1223,7 +1036,7 @@ extern "C" ibp_status ibp_bound_paper(ibp_case *c, int32_t n_box, const double *
                        cuda_stream, true);
 }
 
-static ibp_status ensure_bwd_workspace(ibp_case *c, int n_box) {
+ibp_status ensure_bwd_workspace(ibp_case *c, int n_box) {
     if (n_box <= c->bwd_cap_box) return IBP_OK;
     const int cap = std::max(n_box, 1);
     c->bwd_cap_box = 0;  // a failure part-way makes the next call start over
@@ -1244,7 +1057,7 @@ static ibp_status ensure_bwd_workspace(ibp_case *c, int n_box) {
 
 // obj_lo's active set holds most pairs of a wide box: its list takes up to
 // 64M entries (1 GiB) shared by the boxes of a call
-static ibp_status ensure_bwd_lo_workspace(ibp_case *c, int n_box) {
+ibp_status ensure_bwd_lo_workspace(ibp_case *c, int n_box) {
     if (n_box <= c->bwd_lo_cap_box) return IBP_OK;
     const int cap = std::max(n_box, 1);
     c->bwd_lo_cap_box = 0;
@@ -1351,373 +1164,6 @@ extern "C" ibp_status ibp_bound_backward_lo(ibp_case *c, int32_t n_box, const do
                           ptr_mode, cuda_stream, 1);
 }
 
-// ---------------------------------------------------------------- linear bound
-static ibp_status ensure_lin_workspace(ibp_case *c, int n_box) {
-    if (n_box <= c->lin_cap_box) return IBP_OK;
-    const int cap = std::max(n_box, 1);
-    c->lin_cap_box = 0;
-    const size_t nd = (size_t)cap * c->n_dev, nl = (size_t)cap * c->n_line;
-    const size_t np = (size_t)cap * std::max(c->n_ctg, 1) * c->n_line, na = (size_t)cap * c->n_a_pad;
-    const size_t nc = (size_t)cap * std::max(c->n_ctg, 1);
-    CUDA_TRY(c->lw.alloc(cap)); CUDA_TRY(c->la0.alloc(cap));
-    CUDA_TRY(c->la0_last.alloc(cap)); CUDA_TRY(c->lstot.alloc(cap)); CUDA_TRY(c->lred.alloc((size_t)cap * 4));
-    CUDA_TRY(c->lstotp.alloc((size_t)cap * ((c->n_dev + 127) / 128)));
-    CUDA_TRY(c->lub.alloc(cap)); CUDA_TRY(c->lub_err.alloc(cap)); CUDA_TRY(c->lbest.alloc((size_t)cap * 2));
-    CUDA_TRY(c->lx.alloc(nd)); CUDA_TRY(c->lsx.alloc(nd)); CUDA_TRY(c->lxb.alloc(nd)); CUDA_TRY(c->lx_last.alloc(nd));
-    CUDA_TRY(c->lac.alloc(np)); CUDA_TRY(c->lc_last.alloc(np)); CUDA_TRY(c->lxavg.alloc(nd));
-    CUDA_TRY(c->lab.alloc(nl)); CUDA_TRY(c->lb_last.alloc(nl));
-    CUDA_TRY(c->lp.alloc(na)); CUDA_TRY(c->lf.alloc(nl)); CUDA_TRY(c->lcol.alloc(nl));
-    CUDA_TRY(c->lrow.alloc(nc)); CUDA_TRY(c->lg.alloc(na));
-    CUDA_TRY(c->lW64.alloc(nl)); CUDA_TRY(c->lWabs.alloc(nl)); CUDA_TRY(c->lconst.alloc(nl));
-    CUDA_TRY(c->lrd64.alloc(nc)); CUDA_TRY(c->lrda.alloc(nc)); CUDA_TRY(c->lg64.alloc(na));
-    CUDA_TRY(c->lG64.alloc(na));
-    if (!c->cl_ptr.p) {
-        std::vector<int> ptr(c->n_line + 1, 0), ctg;
-        for (int k = 0; k < c->n_ctg; ++k) ++ptr[c->ctg_line_h[k] + 1];
-        for (int l = 0; l < c->n_line; ++l) ptr[l + 1] += ptr[l];
-        ctg.resize(std::max(c->n_ctg, 1));
-        std::vector<int> fill(ptr.begin(), ptr.end() - 1);
-        for (int k = 0; k < c->n_ctg; ++k) ctg[fill[c->ctg_line_h[k]]++] = k;
-        CUDA_TRY(c->cl_ptr.alloc(ptr.size()));
-        CUDA_TRY(c->cl_ctg.alloc(ctg.size()));
-        CUDA_TRY(cudaMemcpy(c->cl_ptr.p, ptr.data(), ptr.size() * sizeof(int), cudaMemcpyHostToDevice));
-        CUDA_TRY(cudaMemcpy(c->cl_ctg.p, ctg.data(), ctg.size() * sizeof(int), cudaMemcpyHostToDevice));
-    }
-    c->lin_cap_box = cap;
-    ++c->ws_gen;
-    return IBP_OK;
-}
-
-// first: the held box whose state the call's box 0 uses (the iteration state
-// is box-major; the scratch buffers always start at box 0)
-static LinArgs lin_args(const ibp_case *c, int n_box, const double *lo, const double *hi, int first = 0) {
-    LinArgs a{};
-    a.n_l = c->n_line; a.n_c = c->n_ctg; a.n_a = c->n_a; a.n_a_pad = c->n_a_pad; a.n_dev = c->n_dev;
-    a.n_gen = c->n_gen; a.n_box = n_box;
-    a.phi = c->phi_a.p; a.phi64 = c->phi64.p; a.lodf = c->lodf.p; a.lodf_lo = c->lodf_lo.p;
-    a.ctg_line = c->ctg_line.p; a.cl_ptr = c->cl_ptr.p; a.cl_ctg = c->cl_ctg.p;
-    a.act_ptr = c->act_ptr.p; a.act_dev = c->act_dev.p; a.dev_col = c->dev_col.p;
-    a.rate64 = c->rate64.p; a.rate_c64 = c->rate_c64.p; a.box_lo = lo; a.box_hi = hi;
-    a.seg_ptr = c->seg_ptr.p; a.slope = c->slope.p; a.bkpt = c->bkpt.p;
-    a.zeta_inj = c->zeta_inj; a.zeta_f = c->zeta_f;
-    a.pc_S = c->lpcS.p; a.pc_tau = c->lpctau.p;
-    a.w = c->lw.p; a.x = c->lx.p; a.sx = c->lsx.p; a.xb = c->lxb.p; a.x_last = c->lx_last.p;
-    a.a_c = c->lac.p; a.c_last = c->lc_last.p;
-    a.a_b = c->lab.p; a.b_last = c->lb_last.p;
-    a.a0 = c->la0.p; a.a0_last = c->la0_last.p;
-    a.x_avg = c->lxavg.p;
-    a.p = c->lp.p; a.stot = c->lstot.p; a.stot_part = c->lstotp.p; a.f = c->lf.p; a.colsum = c->lcol.p; a.rowdot = c->lrow.p;
-    a.g = c->lg.p; a.red = c->lred.p;
-    a.W64 = c->lW64.p; a.Wabs = c->lWabs.p; a.constl = c->lconst.p; a.rd64 = c->lrd64.p;
-    a.rda = c->lrda.p; a.g64 = c->lg64.p; a.G64 = c->lG64.p; a.ub = c->lub.p; a.ub_err = c->lub_err.p;
-    if (first > 0) {
-        const size_t f = (size_t)first, fd = f * c->n_dev, fl = f * c->n_line;
-        const size_t fc = f * std::max(c->n_ctg, 1) * c->n_line;
-        a.w += f; a.x += fd; a.sx += fd; a.x_last += fd; a.x_avg += fd;
-        a.a_c += fc; a.c_last += fc;
-        a.a_b += fl; a.b_last += fl;
-        a.a0 += f; a.a0_last += f;
-    }
-    return a;
-}
-
-// x <- the box midpoints (and x_last); primal weight w0; best bound +inf
-__global__ void k_lin_init(int n, const double *lo, const double *hi, double *x, double *x_last,
-                           int n_box, double *w, double w0, double *best) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) {
-        x[i] = 0.5 * (lo[i] + hi[i]);
-        x_last[i] = x[i];
-    }
-    if (i < n_box) {
-        w[i] = w0;
-        best[2 * i] = INFINITY;
-        best[2 * i + 1] = 0.0;
-    }
-}
-
-// warm start: points clipped into their boxes and taken as the reference of
-// the next adaptation; best bound +inf (the slopes, the slope references and
-// the primal weight stay; the running sum of the points is 0 after the
-// previous call's last adaptation)
-__global__ void k_lin_warm(int n, const double *lo, const double *hi, double *x, double *x_last,
-                           int n_box, double *best) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) {
-        x[i] = fmin(fmax(x[i], lo[i]), hi[i]);
-        x_last[i] = x[i];
-    }
-    if (i < n_box) {
-        best[2 * i] = INFINITY;
-        best[2 * i + 1] = 0.0;
-    }
-}
-
-// keep the smaller certified bound of each box (and its error bound)
-__global__ void k_lin_best(int n_box, const double *ub, const double *err, double *best) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < n_box && ub[j] < best[2 * j]) {
-        best[2 * j] = ub[j];
-        best[2 * j + 1] = err[j];
-    }
-}
-
-__global__ void k_lin_out(int n_box, const double *best, double *obj_hi, double *obj_err) {
-    const int j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (j < n_box) {
-        obj_hi[j] = best[2 * j];
-        obj_err[j] = best[2 * j + 1];
-    }
-}
-
-constexpr int kLinRestart = 1000;   // iterations between adaptations of the primal weight (and certified values)
-constexpr int kLinChunk = 50;       // iterations per CUDA graph launch
-
-static ibp_status lin_run(ibp_case *c, int n_box, const double *lo, const double *hi, int n_iter,
-                          double w0, double *obj_hi, double *obj_err, double *x_point, cudaStream_t s,
-                          bool warm = false, int first = 0) {
-    if (warm && (first < 0 || n_box > c->lin_state_box - first))
-        return fail(IBP_EINVAL, "no linear state for boxes [%d, %d) to continue from (%d held)", first,
-                    first + n_box, c->lin_state_box);
-    ibp_status st = ensure_lin_workspace(c, n_box);
-    if (st != IBP_OK) return st;
-    const size_t nd = (size_t)n_box * c->n_dev, np = (size_t)n_box * std::max(c->n_ctg, 1) * c->n_line;
-    const size_t nl = (size_t)n_box * c->n_line;
-    auto zero = [&](void *p, size_t bytes) { return cudaMemsetAsync(p, 0, bytes, s); };
-    if (!c->lin_pc_ready) {
-        // the diagonal step sizes, once per case (they depend on the network only)
-        if (!c->lpcS.p) {
-            CUDA_TRY(c->lpcS.alloc(c->n_line)); CUDA_TRY(c->lpctau.alloc(c->n_dev));
-            CUDA_TRY(c->lpcA.alloc(c->n_a_pad)); CUDA_TRY(c->lpcB.alloc(c->n_a_pad));
-            CUDA_TRY(c->lpcL.alloc(std::max(c->n_ctg, 1)));
-        }
-        LinArgs a = lin_args(c, 1, lo, hi);
-        CUDA_TRY(lin_precondition(a, c->lpcS.p, c->lpctau.p, c->lpcA.p, c->lpcB.p, c->lpcL.p, s));
-        c->lin_pc_ready = true;
-    }
-    if (warm) {
-        // continue from the state held for these boxes: the points are moved
-        // into their (possibly smaller) boxes; the best bound restarts
-        const size_t fd = (size_t)first * c->n_dev;
-        k_lin_warm<<<(unsigned)((std::max(nd, (size_t)n_box) + 255) / 256), 256, 0, s>>>(
-            (int)nd, lo, hi, c->lx.p + fd, c->lx_last.p + fd, n_box, c->lbest.p);
-        CUDA_TRY(cudaGetLastError());
-    } else {
-    k_lin_init<<<(unsigned)((std::max(nd, (size_t)n_box) + 255) / 256), 256, 0, s>>>(
-        (int)nd, lo, hi, c->lx.p, c->lx_last.p, n_box, c->lw.p, w0, c->lbest.p);
-    CUDA_TRY(cudaGetLastError());
-    CUDA_TRY(zero(c->lsx.p, nd * sizeof(double)));
-    CUDA_TRY(zero(c->lac.p, np * sizeof(float)));
-    CUDA_TRY(zero(c->lc_last.p, np * sizeof(float)));
-    CUDA_TRY(zero(c->lab.p, nl * sizeof(float)));
-    CUDA_TRY(zero(c->lb_last.p, nl * sizeof(float)));
-    CUDA_TRY(zero(c->la0.p, n_box * sizeof(double)));
-    CUDA_TRY(zero(c->la0_last.p, n_box * sizeof(double)));
-    CUDA_TRY(zero(c->lred.p, (size_t)n_box * 4 * sizeof(double)));
-    CUDA_TRY(zero(c->lg.p, (size_t)n_box * c->n_a_pad * sizeof(float)));
-    }
-    // the state is box-major: a warm call on held boxes [first, first + n_box)
-    // leaves the rest of the held state as it was
-    if (!warm) c->lin_state_box = n_box;
-    LinArgs a = lin_args(c, n_box, lo, hi, warm ? first : 0);
-    if (warm) {
-        // the dual gradient g of the inherited slopes (the iteration's first x
-        // step uses it), and the certified value at those slopes: on a sub-box
-        // it is at most the parent's, so a continued bound never rises
-        CUDA_TRY(lin_gradient(a, c->num_sms, s));
-        CUDA_TRY(lin_certify(a, c->num_sms, s));
-        k_lin_best<<<(n_box + 127) / 128, 128, 0, s>>>(n_box, c->lub.p, c->lub_err.p, c->lbest.p);
-        CUDA_TRY(cudaGetLastError());
-    }
-    // a chunk of iterations as one CUDA graph, captured on a private stream
-    // (the arguments hold this call's box pointers, so each call captures anew)
-    const int chunk = std::min(kLinChunk, kLinRestart);
-    {
-        if (c->lin_graph) {
-            cudaGraphExecDestroy(c->lin_graph);
-            c->lin_graph = nullptr;
-        }
-        cudaStream_t cs = nullptr;
-        CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-        cudaGraph_t graph = nullptr;
-        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-        for (int i = 0; e == cudaSuccess && i < chunk; ++i) e = lin_iteration(a, c->num_sms, cs);
-        cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
-        if (e == cudaSuccess) e = e2;
-        if (e == cudaSuccess) e = cudaGraphInstantiate(&c->lin_graph, graph, 0);
-        if (graph) cudaGraphDestroy(graph);
-        cudaStreamDestroy(cs);
-        CUDA_TRY(e);
-    }
-    int done = 0, since = 0;
-    while (done < n_iter) {
-        const int m = std::min(chunk, n_iter - done);
-        if (m == chunk) {
-            CUDA_TRY(cudaGraphLaunch(c->lin_graph, s));
-        } else {
-            for (int i = 0; i < m; ++i) CUDA_TRY(lin_iteration(a, c->num_sms, s));
-        }
-        done += m;
-        since += m;
-        if (since >= kLinRestart || done == n_iter) {
-            a.n_avg = since;
-            CUDA_TRY(lin_restart(a, c->num_sms, s));
-            since = 0;
-            CUDA_TRY(lin_certify(a, c->num_sms, s));
-            k_lin_best<<<(n_box + 127) / 128, 128, 0, s>>>(n_box, c->lub.p, c->lub_err.p, c->lbest.p);
-            CUDA_TRY(cudaGetLastError());
-        }
-    }
-    if (n_iter == 0 && !warm) {
-        CUDA_TRY(lin_certify(a, c->num_sms, s));
-        k_lin_best<<<(n_box + 127) / 128, 128, 0, s>>>(n_box, c->lub.p, c->lub_err.p, c->lbest.p);
-    }
-    k_lin_out<<<(n_box + 127) / 128, 128, 0, s>>>(n_box, c->lbest.p, obj_hi, obj_err);
-    CUDA_TRY(cudaGetLastError());
-    if (x_point) CUDA_TRY(cudaMemcpyAsync(x_point, a.x_avg, nd * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    return mark_done(c, s);
-}
-
-extern "C" ibp_status ibp_bound_linear(ibp_case *c, int32_t n_box, const double *box_lo,
-                                       const double *box_hi, int32_t n_iter, double primal_weight,
-                                       int32_t warm, double *obj_hi, double *obj_err,
-                                       double *x_point, int32_t ptr_mode, void *cuda_stream) {
-    if (!c) return fail(IBP_EINVAL, "case is NULL");
-    if (n_box < 0 || n_box > kMaxBoxesPerCall) return fail(IBP_EINVAL, "n_box must be in [0, %d]", kMaxBoxesPerCall);
-    if (n_iter < 0) return fail(IBP_EINVAL, "n_iter must be >= 0");
-    if (warm < 0) return fail(IBP_EINVAL, "warm must be >= 0");
-    if (!(primal_weight > 0.0) || !std::isfinite(primal_weight))
-        return fail(IBP_EINVAL, "primal_weight must be finite and > 0");
-    if (ptr_mode != 0 && ptr_mode != 1) return fail(IBP_EINVAL, "ptr_mode must be 0 or 1");
-    if (n_box == 0) return ok();
-    if (!box_lo || !box_hi || !obj_hi || !obj_err) return fail(IBP_EINVAL, "box and output pointers must not be NULL");
-    if (ptr_mode == 0) {
-        ibp_status st = check_boxes_host(c, n_box, box_lo, box_hi);
-        if (st != IBP_OK) return st;
-    }
-    if (c->device < 0) return fail(IBP_ENOTSUP, "case was created without a device (dry run)");
-    if (!c->phi64.p) return fail(IBP_ENOTSUP, "the case holds no FP64 PTDF");
-    DeviceGuard guard(c->device);
-    if (!guard.ok) return fail(IBP_ECUDA, "cannot select device %d", c->device);
-    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-    ibp_status st = ensure_workspace(c, n_box);
-    if (st != IBP_OK) return st;
-    if (ptr_mode == 1)
-        return lin_run(c, n_box, box_lo, box_hi, n_iter, primal_weight, obj_hi, obj_err, x_point, s, warm != 0,
-                       warm - 1);
-    const size_t nd = (size_t)n_box * c->n_dev;
-    CUDA_TRY(cudaMemcpyAsync(c->box_lo.p, box_lo, nd * sizeof(double), cudaMemcpyHostToDevice, s));
-    CUDA_TRY(cudaMemcpyAsync(c->box_hi.p, box_hi, nd * sizeof(double), cudaMemcpyHostToDevice, s));
-    double *dobj = c->obj.p;  // [n_box] bound, [n_box] error
-    DevBuf<double> dx;
-    if (x_point) CUDA_TRY(dx.alloc(nd));
-    st = lin_run(c, n_box, c->box_lo.p, c->box_hi.p, n_iter, primal_weight, dobj, dobj + n_box,
-                 x_point ? dx.p : nullptr, s, warm != 0, warm - 1);
-    if (st != IBP_OK) return st;
-    CUDA_TRY(cudaMemcpyAsync(obj_hi, dobj, n_box * sizeof(double), cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(cudaMemcpyAsync(obj_err, dobj + n_box, n_box * sizeof(double), cudaMemcpyDeviceToHost, s));
-    if (x_point) CUDA_TRY(cudaMemcpyAsync(x_point, dx.p, nd * sizeof(double), cudaMemcpyDeviceToHost, s));
-    CUDA_TRY(cudaStreamSynchronize(s));
-    return ok();
-}
-
-// Rearranges the linear state for a new list of boxes: box j takes the state
-// (slopes, running sums, point, primal weight) of box parent[j] (host array).
-__global__ void k_lin_gather_f(const float *src, float *dst, const int *parent, int n_new, size_t per) {
-    const size_t tot = (size_t)n_new * per;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += (size_t)gridDim.x * blockDim.x)
-        dst[i] = src[(size_t)parent[i / per] * per + i % per];
-}
-__global__ void k_lin_gather_d(const double *src, double *dst, const int *parent, int n_new, size_t per) {
-    const size_t tot = (size_t)n_new * per;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += (size_t)gridDim.x * blockDim.x)
-        dst[i] = src[(size_t)parent[i / per] * per + i % per];
-}
-
-extern "C" ibp_status ibp_case_linear_inherit(ibp_case *c, int32_t n_new, const int32_t *parent) {
-    if (!c || !parent) return fail(IBP_EINVAL, "NULL argument");
-    if (c->device < 0) return fail(IBP_ENOTSUP, "dry-run case");
-    if (n_new < 1 || n_new > kMaxBoxesPerCall) return fail(IBP_EINVAL, "n_new must be in [1, %d]", kMaxBoxesPerCall);
-    for (int j = 0; j < n_new; ++j)
-        if (parent[j] < 0 || parent[j] >= c->lin_state_box)
-            return fail(IBP_EINVAL, "parent[%d] = %d is not a box of the linear state (%d boxes)", j, parent[j],
-                        c->lin_state_box);
-    DeviceGuard guard(c->device);
-    if (!guard.ok) return fail(IBP_ECUDA, "cannot select device %d", c->device);
-    ibp_status st = wait_case(c);
-    if (st != IBP_OK) return st;
-    const int old_cap = c->lin_cap_box;
-    DevBuf<int> dpar;
-    CUDA_TRY(dpar.alloc(n_new));
-    CUDA_TRY(cudaMemcpy(dpar.p, parent, n_new * sizeof(int), cudaMemcpyHostToDevice));
-    const size_t pc = (size_t)std::max(c->n_ctg, 1) * c->n_line;
-    // gather into fresh buffers, then replace the old ones
-    auto gf = [&](DevBuf<float> &b, size_t per) -> ibp_status {
-        DevBuf<float> t;
-        CUDA_TRY(t.alloc((size_t)std::max(n_new, old_cap) * per));
-        k_lin_gather_f<<<c->num_sms * 8, 256>>>(b.p, t.p, dpar.p, n_new, per);
-        CUDA_TRY(cudaGetLastError());
-        CUDA_TRY(cudaDeviceSynchronize());
-        std::swap(b.p, t.p);
-        std::swap(b.n, t.n);
-        return IBP_OK;
-    };
-    auto gd = [&](DevBuf<double> &b, size_t per) -> ibp_status {
-        DevBuf<double> t;
-        CUDA_TRY(t.alloc((size_t)std::max(n_new, old_cap) * per));
-        k_lin_gather_d<<<c->num_sms * 8, 256>>>(b.p, t.p, dpar.p, n_new, per);
-        CUDA_TRY(cudaGetLastError());
-        CUDA_TRY(cudaDeviceSynchronize());
-        std::swap(b.p, t.p);
-        std::swap(b.n, t.n);
-        return IBP_OK;
-    };
-    if ((st = gf(c->lac, pc)) || (st = gf(c->lc_last, pc)) ||
-        (st = gf(c->lab, c->n_line)) || (st = gf(c->lb_last, c->n_line)) ||
-        (st = gd(c->la0, 1)) || (st = gd(c->la0_last, 1)) || (st = gd(c->lw, 1)) ||
-        (st = gd(c->lx, c->n_dev)) || (st = gd(c->lsx, c->n_dev)) || (st = gd(c->lxavg, c->n_dev)))
-        return st;
-    CUDA_TRY(cudaDeviceSynchronize());
-    // the other per-box buffers only need the room
-    if (n_new > old_cap) {
-        c->lin_cap_box = old_cap;  // ensure_lin_workspace grows the rest (its state buffers are resized above)
-        const size_t nd = (size_t)n_new * c->n_dev, nl = (size_t)n_new * c->n_line;
-        const size_t na = (size_t)n_new * c->n_a_pad, nc = (size_t)n_new * std::max(c->n_ctg, 1);
-        CUDA_TRY(c->lx_last.alloc(nd)); CUDA_TRY(c->lxb.alloc(nd));
-        CUDA_TRY(c->lstot.alloc(n_new)); CUDA_TRY(c->lred.alloc((size_t)n_new * 4));
-        CUDA_TRY(c->lstotp.alloc((size_t)n_new * ((c->n_dev + 127) / 128)));
-        CUDA_TRY(c->lub.alloc(n_new)); CUDA_TRY(c->lub_err.alloc(n_new)); CUDA_TRY(c->lbest.alloc((size_t)n_new * 2));
-        CUDA_TRY(c->lp.alloc(na)); CUDA_TRY(c->lf.alloc(nl)); CUDA_TRY(c->lcol.alloc(nl));
-        CUDA_TRY(c->lrow.alloc(nc)); CUDA_TRY(c->lg.alloc(na));
-        CUDA_TRY(c->lW64.alloc(nl)); CUDA_TRY(c->lWabs.alloc(nl)); CUDA_TRY(c->lconst.alloc(nl));
-        CUDA_TRY(c->lrd64.alloc(nc)); CUDA_TRY(c->lrda.alloc(nc)); CUDA_TRY(c->lg64.alloc(na));
-        CUDA_TRY(c->lG64.alloc(na));
-        c->lin_cap_box = n_new;
-        ++c->ws_gen;
-    }
-    CUDA_TRY(cudaMemset(c->lred.p, 0, (size_t)c->lin_cap_box * 4 * sizeof(double)));
-    c->lin_state_box = n_new;
-    return ok();
-}
-
-// The slopes of the last ibp_bound_linear call (host copies, for checking the
-// certified value against an independent evaluation): a_ctg [n_box][n_ctg][n_line],
-// a_base [n_box][n_line], a_inj [n_box].
-extern "C" ibp_status ibp_case_linear_slopes(ibp_case *c, int32_t n_box, float *a_ctg, float *a_base,
-                                             double *a_inj) {
-    if (!c || !a_ctg || !a_base || !a_inj) return fail(IBP_EINVAL, "NULL argument");
-    if (c->device < 0) return fail(IBP_ENOTSUP, "dry-run case");
-    if (n_box < 1 || n_box > c->lin_cap_box) return fail(IBP_EINVAL, "no linear bound of that many boxes");
-    DeviceGuard guard(c->device);
-    ibp_status st = wait_case(c);
-    if (st != IBP_OK) return st;
-    const size_t np = (size_t)n_box * c->n_ctg * c->n_line;
-    if (np) CUDA_TRY(cudaMemcpy(a_ctg, c->lac.p, np * sizeof(float), cudaMemcpyDeviceToHost));
-    CUDA_TRY(cudaMemcpy(a_base, c->lab.p, (size_t)n_box * c->n_line * sizeof(float), cudaMemcpyDeviceToHost));
-    CUDA_TRY(cudaMemcpy(a_inj, c->la0.p, n_box * sizeof(double), cudaMemcpyDeviceToHost));
-    return ok();
-}
-
 // ---------------------------------------------------------------- ratings
 // New ratings: a check of every entry into a sticky flag, then (only when no
 // entry failed) their directed FP32 copies and FP64 values.
@@ -1783,435 +1229,6 @@ extern "C" ibp_status ibp_case_set_ratings(ibp_case *c, const double *rating,
         return ok();
     }
     return mark_done(c, s);
-}
-
-// ---------------------------------------------------------------- many cases
-// Work plan of one ibp_bound_multi configuration (cases, box counts and their
-// workspace generations), built and uploaded once, then reused.
-struct MultiPlan {
-    std::vector<const ibp_case *> cases;
-    std::vector<int> n_box, gens, reduced;
-    int device = -1, grid = 0;
-    int variant = 0, rows_per_item = 0;  // kernel body (the first case's variant) and its partial rows
-    DevBuf<MultiItem> items;
-    DevBuf<int> cta_start, err;
-    DevBuf<uint32_t> prefix;
-    DevBuf<CtgArgs> args;
-    DevBuf<CUtensorMap> maps;
-    // refinement queues of the launch (shared by the cases), when a case refines
-    bool refine = false;
-    DevBuf<int4> refq;
-    DevBuf<int> refq_cnt;
-    DevBuf<double2> refq_res;
-    // 0: plain bound; 1 + side: the forward pass of a backward, recording the
-    // side's active pairs, with the backward's (case, box) items and arguments
-    int record = 0;
-    int n_items = 0, max_n_a_pad = 0;
-    DevBuf<BwdArgs> bargs;
-    DevBuf<int2> bitems;
-    ~MultiPlan() {
-        if (device >= 0) {
-            DeviceGuard g(device);
-            items.free(); cta_start.free(); err.free(); prefix.free(); args.free(); maps.free();
-            refq.free(); refq_cnt.free(); refq_res.free(); bargs.free(); bitems.free();
-        }
-    }
-};
-static std::mutex g_plan_mu;
-static std::vector<std::unique_ptr<MultiPlan>> g_plans;
-
-static void drop_plans_of(const ibp_case *c) {
-    std::lock_guard<std::mutex> lk(g_plan_mu);
-    g_plans.erase(std::remove_if(g_plans.begin(), g_plans.end(),
-                                 [c](const std::unique_ptr<MultiPlan> &p) {
-                                     return std::find(p->cases.begin(), p->cases.end(), c) !=
-                                            p->cases.end();
-                                 }),
-                  g_plans.end());
-}
-
-static CtgArgs multi_args(const ibp_case *c, int n_box, int BL, int BK, int CH, bool reduced,
-                          int rows_per_item, int record) {
-    const int n_box_pad = (n_box + kBoxTile - 1) / kBoxTile * kBoxTile;
-    const int n_rows = reduced ? c->n_nb : c->n_line;
-    const int tiles_l = (n_rows + BL - 1) / BL, tiles_k = (c->n_ctg + BK - 1) / BK;
-    const int n_chunks = ((reduced ? c->n_r_pad : c->n_a_pad) + CH - 1) / CH;
-    CtgArgs ca{};
-    ca.n_l = c->n_line; ca.n_c = c->n_ctg; ca.n_a = c->n_a; ca.n_chunks = n_chunks; ca.n_box = n_box;
-    ca.tiles_l = tiles_l; ca.n_tiles = tiles_l * tiles_k * (n_box_pad / kBoxTile);
-    ca.lodf = c->lodf.p; ca.ctg_line = c->ctg_line.p;
-    ca.line_c = c->line_c.p; ca.line_e = c->line_e.p; ca.line_R = c->line_R.p;
-    ca.rate_up = c->rate_c_up.p; ca.rate_dn = c->rate_c_dn.p; ca.box_consts = c->box_consts.p;
-    ca.rbus_t = reduced ? c->rcls_t.p : c->rbus_t.p; ca.n_box_pad = n_box_pad;
-    ca.gamma = rup_gamma(CH, 256 / CH, (n_chunks + 256 / CH - 1) / (256 / CH));
-    ca.flow_lo = nullptr; ca.flow_hi = nullptr; ca.partials = c->part_ctg.p; ca.err = c->err.p;
-    ca.wait_ns = 2000000000ull;
-    ca.warps_per_tile = rows_per_item;
-    ca.part_rows_cap = (int)max_part_rows(c);
-    ca.ref = ref_args(c);
-    if (reduced) {
-        ca.live = c->nb_list.p;
-        ca.n_live = c->nb_count.p;
-    }
-    if (record == 1) {
-        ca.act_count = c->act_count.p;
-        ca.act_list = c->act_list.p;
-        ca.act_cap = c->act_cap;
-    } else if (record == 2) {
-        ca.act_count_lo = c->act_count_lo.p;
-        ca.act_list_lo = c->act_list_lo.p;
-        ca.act_cap_lo = c->act_cap_lo;
-    }
-    return ca;
-}
-
-// the backward's arguments of one case without the per-call pointers
-static BwdArgs bwd_args(const ibp_case *c, int n_box, int side) {
-    BwdArgs b{};
-    b.n_l = c->n_line; b.n_a = c->n_a; b.n_a_pad = c->n_a_pad; b.n_dev = c->n_dev; b.n_gen = c->n_gen;
-    b.n_box = n_box; b.side = side;
-    b.act_cap = side ? c->act_cap_lo : c->act_cap; b.phi = c->phi_a.p;
-    b.act_count = side ? c->act_count_lo.p : c->act_count.p;
-    b.act_list = side ? c->act_list_lo.p : c->act_list.p;
-    b.W = c->W.p; b.cnt = c->cnt.p; b.dc = c->dc.p; b.dr = c->dr.p;
-    b.dev_col = c->dev_col.p; b.seg_ptr = c->seg_ptr.p;
-    b.slope = c->slope.p; b.bkpt = c->bkpt.p; b.zeta_inj = c->zeta_inj; b.zeta_f = c->zeta_f;
-    return b;
-}
-
-// the many-case launch uses the static part of the network reduction: every
-// non-bridge line, with its reduced row
-static bool multi_reduced(const ibp_case *c) { return c->reduce && c->has_reduction && c->n_ctg > 0; }
-
-static ibp_status ensure_nonbridge_rows(ibp_case *c) {
-    if (c->n_nb >= 0) return IBP_OK;
-    std::vector<int> nb;
-    for (int l = 0; l < c->n_line; ++l)
-        if (!c->is_bridge_h[l]) nb.push_back(l);
-    const int n = (int)nb.size();
-    CUDA_TRY(c->nb_list.alloc(std::max(n, 1)));
-    CUDA_TRY(c->nb_count.alloc(1));
-    CUDA_TRY(c->phi_nb.alloc((size_t)std::max(n, 1) * c->n_r_pad));
-    if (n > 0) {
-        CUDA_TRY(cudaMemcpy(c->nb_list.p, nb.data(), n * sizeof(int), cudaMemcpyHostToDevice));
-        CUDA_TRY(launch_gather_rows(c->phi_r.p, c->n_r_pad, c->nb_list.p, n, c->phi_nb.p, nullptr));
-    }
-    CUDA_TRY(cudaMemcpy(c->nb_count.p, &n, sizeof(int), cudaMemcpyHostToDevice));
-    CUDA_TRY(cudaDeviceSynchronize());
-    c->n_nb = n;
-    return IBP_OK;
-}
-
-static ibp_status build_plan(ibp_case *const *cases, const int32_t *n_box, int n_case, int num_sms,
-                             int record, MultiPlan **out) {
-    int BL, BK, CH;
-    multi_tile_shape(&BL, &BK, &CH);
-    std::unique_ptr<MultiPlan> P(new MultiPlan());
-    P->device = cases[0]->device;
-    P->variant = cases[0]->variant;
-    P->rows_per_item = cases_rows_per_item(P->variant);
-    std::vector<CtgArgs> args(n_case);
-    std::vector<CUtensorMap> maps(3 * (size_t)n_case);
-    struct Item { MultiItem m; long long cost; int order; };
-    std::vector<Item> all;
-    for (int i = 0; i < n_case; ++i) {
-        const ibp_case *c = cases[i];
-        P->cases.push_back(c);
-        P->n_box.push_back(n_box[i]);
-        P->gens.push_back(c->ws_gen);
-        const bool red = multi_reduced(c);
-        P->reduced.push_back(red ? 1 : 0);
-        args[i] = multi_args(c, n_box[i], BL, BK, CH, red, P->rows_per_item, record);
-        const int n_box_pad = args[i].n_box_pad;
-        const int w = red ? c->n_r_pad : c->n_a_pad;
-        const float *rows = red ? c->phi_nb.p : c->phi_a.p;
-        const int n_rows = std::max(red ? c->n_nb : c->n_line, 1);
-        std::string err;
-        if (!encode_map_2d(&maps[3 * i], rows, w, n_rows, w, 32, BL, &err) ||
-            !encode_map_2d(&maps[3 * i + 1], red ? c->phi_kr.p : c->phi_k.p, w, std::max(c->n_ctg, 1), w,
-                           32, BK, &err) ||
-            !encode_map_2d(&maps[3 * i + 2], red ? c->rcls_t.p : c->rbus_t.p, n_box_pad, w, n_box_pad,
-                           kBoxTile, 32, &err, false))
-            return fail(IBP_ECUDA, "%s", err.c_str());
-        if (c->n_ctg == 0) continue;
-        const int tiles_l = args[i].tiles_l, tiles_k = (c->n_ctg + BK - 1) / BK;
-        const long long cost = (long long)args[i].n_chunks * BL * BK * kBoxTile;
-        for (int tl = 0; tl < tiles_l; ++tl)
-            for (int tk = 0; tk < tiles_k; ++tk)
-                for (int bt = 0; bt < n_box_pad / kBoxTile; ++bt) {
-                    Item it;
-                    it.m = MultiItem{i, tl * BL, tk * BK, bt * kBoxTile, tl * tiles_k + tk, args[i].n_chunks};
-                    it.cost = cost;
-                    it.order = (int)all.size();
-                    all.push_back(it);
-                }
-    }
-    // longest items first, dealt round-robin to the persistent CTAs
-    std::stable_sort(all.begin(), all.end(), [](const Item &a, const Item &b) { return a.cost > b.cost; });
-    const int G = std::max(1, std::min<int>(num_sms, (int)all.size()));
-    std::vector<std::vector<MultiItem>> per(G);
-    for (size_t k = 0; k < all.size(); ++k) per[k % G].push_back(all[k].m);
-    std::vector<MultiItem> items;
-    std::vector<int> start(G + 1, 0);
-    std::vector<uint32_t> prefix;
-    for (int b = 0; b < G; ++b) {
-        start[b] = (int)items.size();
-        uint32_t acc = 0;
-        for (const MultiItem &m : per[b]) {
-            items.push_back(m);
-            prefix.push_back(acc);
-            acc += (uint32_t)m.n_chunks;
-        }
-        prefix.push_back(acc);
-    }
-    start[G] = (int)items.size();
-    P->grid = all.empty() ? 0 : G;
-    // one set of refinement queues for the launch, when any case refines
-    for (int i = 0; i < n_case; ++i) P->refine = P->refine || args[i].ref.phi64 != nullptr;
-    if (P->refine) {
-        ibp_status st = ensure_ref_queue(P.get(), num_sms);
-        if (st != IBP_OK) return st;
-        for (int i = 0; i < n_case; ++i) {
-            args[i].refq = P->refq.p; args[i].refq_cnt = P->refq_cnt.p; args[i].refq_cap = kRefQCap;
-        }
-    }
-    CUDA_TRY(P->items.alloc(std::max<size_t>(items.size(), 1)));
-    CUDA_TRY(P->cta_start.alloc(start.size()));
-    CUDA_TRY(P->prefix.alloc(prefix.size() + 1));
-    CUDA_TRY(P->args.alloc(args.size()));
-    CUDA_TRY(P->maps.alloc(maps.size()));
-    CUDA_TRY(P->err.alloc(1));
-    if (!items.empty())
-        CUDA_TRY(cudaMemcpy(P->items.p, items.data(), items.size() * sizeof(MultiItem), cudaMemcpyHostToDevice));
-    CUDA_TRY(cudaMemcpy(P->cta_start.p, start.data(), start.size() * sizeof(int), cudaMemcpyHostToDevice));
-    CUDA_TRY(cudaMemcpy(P->prefix.p, prefix.data(), prefix.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
-    CUDA_TRY(cudaMemcpy(P->args.p, args.data(), args.size() * sizeof(CtgArgs), cudaMemcpyHostToDevice));
-    CUDA_TRY(cudaMemcpy(P->maps.p, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice));
-    P->record = record;
-    if (record) {
-        std::vector<BwdArgs> bargs(n_case);
-        std::vector<int2> bitems;
-        for (int i = 0; i < n_case; ++i) {
-            bargs[i] = bwd_args(cases[i], n_box[i], record - 1);
-            P->max_n_a_pad = std::max(P->max_n_a_pad, cases[i]->n_a_pad);
-            for (int j = 0; j < n_box[i]; ++j) bitems.push_back(make_int2(i, j));
-        }
-        P->n_items = (int)bitems.size();
-        CUDA_TRY(P->bargs.alloc(bargs.size()));
-        CUDA_TRY(P->bitems.alloc(bitems.size()));
-        CUDA_TRY(cudaMemcpy(P->bargs.p, bargs.data(), bargs.size() * sizeof(BwdArgs), cudaMemcpyHostToDevice));
-        CUDA_TRY(cudaMemcpy(P->bitems.p, bitems.data(), bitems.size() * sizeof(int2), cudaMemcpyHostToDevice));
-    }
-    *out = P.release();
-    return IBP_OK;
-}
-
-static MultiPlan *find_plan(ibp_case *const *cases, const int32_t *n_box, int n_case, int record) {
-    for (auto &p : g_plans) {
-        if ((int)p->cases.size() != n_case || p->variant != cases[0]->variant || p->record != record) continue;
-        bool same = true;
-        for (int i = 0; i < n_case && same; ++i)
-            same = p->cases[i] == cases[i] && p->n_box[i] == n_box[i] && p->gens[i] == cases[i]->ws_gen &&
-                   p->reduced[i] == (int)multi_reduced(cases[i]);
-        if (same) return p.get();
-    }
-    return nullptr;
-}
-
-static ibp_status check_multi_args(int32_t n_case, ibp_case *const *cases, const int32_t *n_box,
-                                   const double *const *box_lo, const double *const *box_hi) {
-    if (n_case < 0) return fail(IBP_EINVAL, "n_case must be >= 0");
-    if (n_case == 0) return IBP_OK;
-    if (!cases || !n_box || !box_lo || !box_hi) return fail(IBP_EINVAL, "array arguments must not be NULL");
-    for (int i = 0; i < n_case; ++i) {
-        if (!cases[i]) return fail(IBP_EINVAL, "case %d is NULL", i);
-        if (cases[i]->device < 0) return fail(IBP_ENOTSUP, "case %d was created without a device", i);
-        if (cases[i]->device != cases[0]->device) return fail(IBP_EINVAL, "cases live on different devices");
-        if (n_box[i] < 1 || n_box[i] > kMaxBoxesPerCall)
-            return fail(IBP_EINVAL, "n_box[%d] must be in [1, %d]", i, kMaxBoxesPerCall);
-        if (!box_lo[i] || !box_hi[i]) return fail(IBP_EINVAL, "box pointers of case %d must not be NULL", i);
-        for (int j = 0; j < i; ++j)
-            if (cases[j] == cases[i]) return fail(IBP_EINVAL, "case %d appears twice", i);
-    }
-    return IBP_OK;
-}
-
-// the many-case forward pass (record: 0 plain, 1 + side: record the side's
-// active pairs for a backward); returns the plan it ran
-static ibp_status enqueue_multi(int32_t n_case, ibp_case *const *cases, const int32_t *n_box,
-                                const double *const *box_lo, const double *const *box_hi,
-                                double *const *obj_lo, double *const *obj_hi, double *const *obj_err,
-                                cudaStream_t s, int record, MultiPlan **plan_out) {
-    ibp_status st;
-    for (int i = 0; i < n_case; ++i) {
-        if ((st = ensure_workspace(cases[i], n_box[i])) != IBP_OK) return st;
-        if (multi_reduced(cases[i]) &&
-            ((st = ensure_class_ws(cases[i])) != IBP_OK || (st = ensure_nonbridge_rows(cases[i])) != IBP_OK))
-            return st;
-        if (record && (st = ensure_bwd_workspace(cases[i], n_box[i])) != IBP_OK) return st;
-        if (record == 2 && (st = ensure_bwd_lo_workspace(cases[i], n_box[i])) != IBP_OK) return st;
-    }
-    MultiPlan *P = nullptr;
-    {
-        std::lock_guard<std::mutex> lk(g_plan_mu);
-        P = find_plan(cases, n_box, n_case, record);
-        if (!P) {
-            if ((st = build_plan(cases, n_box, n_case, cases[0]->num_sms, record, &P)) != IBP_OK) return st;
-            g_plans.emplace_back(P);
-        }
-    }
-    if (plan_out) *plan_out = P;
-    if (record) CUDA_TRY(launch_bwd_zero_cases(P->bargs.p, P->bitems.p, P->n_items, true, s));
-    CUDA_TRY(cudaMemsetAsync(P->err.p, 0, sizeof(int), s));
-    // per-case box intervals and base flows
-    for (int i = 0; i < n_case; ++i) {
-        ibp_case *c = cases[i];
-        const int nb = n_box[i];
-        const int n_box_pad = (nb + kBoxTile - 1) / kBoxTile * kBoxTile;
-        CUDA_TRY(cudaMemsetAsync(c->err.p, 0, sizeof(int), s));
-        CUDA_TRY(cudaMemsetAsync(c->rbus_t.p, 0, (size_t)c->n_a_pad * n_box_pad * sizeof(float), s));
-        const bool red = P->reduced[i] != 0;
-        if (red)
-            CUDA_TRY(cudaMemsetAsync(c->rcls_t.p, 0, (size_t)c->n_r_pad * n_box_pad * sizeof(float), s));
-        BusArgs ba{};
-        ba.n_a = c->n_a; ba.n_a_pad = c->n_a_pad; ba.n_dev = c->n_dev; ba.n_gen = c->n_gen; ba.n_box = nb;
-        ba.act_ptr = c->act_ptr.p; ba.act_dev = c->act_dev.p; ba.box_lo = box_lo[i]; ba.box_hi = box_hi[i];
-        ba.cbus = c->cbus.p; ba.cbus2 = c->cbus2.p; ba.rbus = c->rbus.p; ba.rbus_t = c->rbus_t.p;
-        ba.rbus64 = c->rbus64.p;
-        ba.n_box_pad = n_box_pad;
-        ba.cabs = c->cabs.p; ba.box_consts = c->box_consts.p; ba.err = c->err.p;
-        ba.bus_part = c->bus_part.p;
-        CUDA_TRY(launch_bus(ba, s));
-        if (red) {
-            ClsArgs ra{};
-            ra.n_box = nb; ra.n_r = c->n_r; ra.n_r_pad = c->n_r_pad; ra.n_a_pad = c->n_a_pad;
-            ra.n_box_pad = n_box_pad; ra.cls_ptr = c->cls_ptr.p; ra.cls_col = c->cls_col.p;
-            ra.rbus = c->rbus.p; ra.rcls = c->rcls.p; ra.rcls_t = c->rcls_t.p;
-            CUDA_TRY(launch_class_radius(ra, s));
-        }
-        BaseArgs bb{};
-        bb.n_l = c->n_line; bb.n_c = c->n_ctg; bb.n_a = c->n_a; bb.n_a_pad = c->n_a_pad; bb.n_box = nb;
-        bb.phi = c->phi_a.p; bb.ctg_line = c->ctg_line.p; bb.cbus = c->cbus.p; bb.cbus2 = c->cbus2.p; bb.rbus = c->rbus.p;
-        bb.cabs = c->cabs.p; bb.rate_up = c->rate_up.p; bb.rate_dn = c->rate_dn.p;
-        bb.box_consts = c->box_consts.p;
-        bb.gamma_base = rup_gamma((c->n_a_pad / 4 + 31) / 32, 2, 5);
-        bb.line_c = c->line_c.p; bb.line_e = c->line_e.p; bb.line_R = c->line_R.p;
-        bb.partials = c->part_base.p; bb.err = c->err.p;
-        if (red) {
-            bb.is_bridge = c->is_bridge.p;
-            bb.rate_c_up = c->rate_c_up.p;
-            bb.rate_c_dn = c->rate_c_dn.p;
-        }
-        bb.ref = ref_args(c);
-        if (record == 1) {
-            bb.act_count = c->act_count.p;
-            bb.act_list = c->act_list.p;
-            bb.act_cap = c->act_cap;
-        } else if (record == 2) {
-            bb.act_count_lo = c->act_count_lo.p;
-            bb.act_list_lo = c->act_list_lo.p;
-            bb.act_cap_lo = c->act_cap_lo;
-        }
-        CUDA_TRY(launch_base(bb, c->n_part_base, s));
-    }
-    // one persistent launch over the contingency tiles of every case
-    const int num_sms = cases[0]->num_sms;
-    if (P->refine)
-        CUDA_TRY(cudaMemsetAsync(P->refq_cnt.p, 0, (size_t)ref_regions(num_sms) * sizeof(int), s));
-    CUDA_TRY(launch_ctg_cases(P->variant, P->items.p, P->cta_start.p, P->prefix.p, P->args.p,
-                              P->maps.p, P->grid, 2000000000ull, P->err.p, s));
-    if (P->refine) {
-        RefQueueArgs qa{};
-        qa.args = P->args.p; qa.n_regions = ref_regions(num_sms); qa.cap = kRefQCap;
-        qa.e = P->refq.p; qa.cnt = P->refq_cnt.p; qa.res = P->refq_res.p;
-        CUDA_TRY(launch_refine_queue(qa, num_sms, s));
-    }
-    int BL, BK, CH;
-    multi_tile_shape(&BL, &BK, &CH);
-    for (int i = 0; i < n_case; ++i) {
-        ibp_case *c = cases[i];
-        CUDA_TRY(launch_or_err(c->err.p, P->err.p, s));
-        AsmArgs aa{};
-        aa.n_box = n_box[i]; aa.n_dev = c->n_dev; aa.n_gen = c->n_gen;
-        const int rows = P->reduced[i] ? c->n_nb : c->n_line;
-        aa.n_part_ctg = ((rows + BL - 1) / BL) * ((c->n_ctg + BK - 1) / BK) * P->rows_per_item;
-        aa.part_stage = c->part_stage.p; aa.n_stage = kPartStages;
-        aa.n_part_base = c->n_part_base;
-        aa.part_ctg = c->part_ctg.p; aa.part_base = c->part_base.p; aa.box_lo = box_lo[i]; aa.box_hi = box_hi[i];
-        aa.seg_ptr = c->seg_ptr.p; aa.slope = c->slope.p; aa.bkpt = c->bkpt.p;
-        aa.zeta_inj = c->zeta_inj; aa.zeta_f = c->zeta_f;
-        aa.obj_lo = obj_lo[i]; aa.obj_hi = obj_hi[i]; aa.obj_err = obj_err[i]; aa.err = c->err.p;
-        CUDA_TRY(launch_assemble(aa, s));
-        if ((st = mark_done(c, s)) != IBP_OK) return st;
-    }
-    return IBP_OK;
-}
-
-extern "C" ibp_status ibp_bound_multi(int32_t n_case, ibp_case *const *cases, const int32_t *n_box,
-                                      const double *const *box_lo, const double *const *box_hi,
-                                      double *const *obj_lo, double *const *obj_hi,
-                                      double *const *obj_err, void *cuda_stream) {
-    ibp_status st = check_multi_args(n_case, cases, n_box, box_lo, box_hi);
-    if (st != IBP_OK) return st;
-    if (n_case == 0) return ok();
-    if (!obj_lo || !obj_hi || !obj_err) return fail(IBP_EINVAL, "array arguments must not be NULL");
-    for (int i = 0; i < n_case; ++i)
-        if (!obj_lo[i] || !obj_hi[i] || !obj_err[i])
-            return fail(IBP_EINVAL, "pointers of case %d must not be NULL", i);
-    DeviceGuard guard(cases[0]->device);
-    if (!guard.ok) return fail(IBP_ECUDA, "cannot select device %d", cases[0]->device);
-    st = enqueue_multi(n_case, cases, n_box, box_lo, box_hi, obj_lo, obj_hi, obj_err,
-                       static_cast<cudaStream_t>(cuda_stream), 0, nullptr);
-    if (st != IBP_OK) return st;
-    return ok();
-}
-
-extern "C" ibp_status ibp_bound_multi_backward(int32_t n_case, ibp_case *const *cases, const int32_t *n_box,
-                                               const double *const *box_lo, const double *const *box_hi,
-                                               const double *const *grad_obj, double *const *grad_lo,
-                                               double *const *grad_hi, double *const *grad_rating,
-                                               int32_t side, void *cuda_stream) {
-    if (side != 0 && side != 1) return fail(IBP_EINVAL, "side must be 0 (obj_hi) or 1 (obj_lo)");
-    ibp_status st = check_multi_args(n_case, cases, n_box, box_lo, box_hi);
-    if (st != IBP_OK) return st;
-    if (n_case == 0) return ok();
-    if (!grad_obj || !grad_lo || !grad_hi) return fail(IBP_EINVAL, "array arguments must not be NULL");
-    long long n_items = 0;
-    for (int i = 0; i < n_case; ++i) {
-        if (!grad_obj[i] || !grad_lo[i] || !grad_hi[i])
-            return fail(IBP_EINVAL, "gradient pointers of case %d must not be NULL", i);
-        n_items += n_box[i];
-    }
-    if (n_items > 65535) return fail(IBP_EINVAL, "at most 65535 boxes over all cases (%lld given)", n_items);
-    DeviceGuard guard(cases[0]->device);
-    if (!guard.ok) return fail(IBP_ECUDA, "cannot select device %d", cases[0]->device);
-    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
-    // the forward pass, recording the side's active pairs; its objective goes
-    // to each case's scratch
-    std::vector<double *> olo(n_case), ohi(n_case), oerr(n_case);
-    for (int i = 0; i < n_case; ++i) {
-        if ((st = ensure_workspace(cases[i], n_box[i])) != IBP_OK) return st;
-        double *d = cases[i]->obj.p;
-        olo[i] = d;
-        ohi[i] = d + n_box[i];
-        oerr[i] = d + 2 * n_box[i];
-    }
-    MultiPlan *P = nullptr;
-    st = enqueue_multi(n_case, cases, n_box, box_lo, box_hi, olo.data(), ohi.data(), oerr.data(), s, 1 + side, &P);
-    if (st != IBP_OK) return st;
-    // weights, centre and radius passes of every (case, box) in one launch each
-    CUDA_TRY(launch_backward_cases(P->bargs.p, P->bitems.p, P->n_items, P->max_n_a_pad, s));
-    // the chain rule to each case's box endpoints
-    for (int i = 0; i < n_case; ++i) {
-        ibp_case *c = cases[i];
-        BwdArgs b = bwd_args(c, n_box[i], side);
-        b.box_lo = box_lo[i]; b.box_hi = box_hi[i];
-        b.grad_obj_hi = grad_obj[i]; b.grad_lo = grad_lo[i]; b.grad_hi = grad_hi[i];
-        b.grad_rating = grad_rating ? grad_rating[i] : nullptr;
-        CUDA_TRY(launch_bwd_chain(b, s));
-        if ((st = mark_done(c, s)) != IBP_OK) return st;
-    }
-    return ok();
 }
 
 extern "C" ibp_status ibp_case_sync(ibp_case *c) {
