@@ -440,9 +440,10 @@ def run_gb300(args):
         # per step: box->bus and its per-box totals (one launch when the
         # active columns fit one block), base flows, contingency, partial
         # sums, assembly; screen, compaction and row gather; class radii under
-        # the reduction
+        # the reduction; the FP64 refinement of the queued pairs and its
+        # application
         "gpu_launches": (5 + (1 if info.n_active_pad > 256 else 0) + (3 if n_live_screened else 0)
-                         + (1 if reduced else 0)) * args.steps,
+                         + (1 if reduced else 0) + (0 if args.no_refine else 2)) * args.steps,
         "batched": None if batched is None else {
             **batched, "frac": batched["achieved_tflops"] / fp32_peak,
             "interval_flows_per_s": case.n_ctg * case.n_line * batched["boxes"] / (batched["ms_per_call"] * 1e-3)},
