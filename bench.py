@@ -436,7 +436,7 @@ def run_gb300(args):
         "clocks": clocks,
         "e2e": {"value": e2e_ms / bounds, "unit": "ms",
                 "h2d_bytes_per_step": int(2 * case.box_lo.nbytes),
-                "d2h_bytes_per_step": int(3 * 8 * nb)},
+                "d2h_bytes_per_step": int(4 * 8 * nb)},  # obj_lo, obj_hi, obj_err[2]
         # per step: box->bus and its per-box totals (one launch when the
         # active columns fit one block), base flows, contingency, partial
         # sums, assembly; screen, compaction and row gather; class radii under
