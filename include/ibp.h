@@ -145,7 +145,10 @@ ibp_status ibp_bound(ibp_case *c, int32_t n_box, const double *box_lo,
  *     contingency ratings, the base part alone is the derivative in rating
  *     and the pair count alone the one in rating_ctg.
  * The derivative is taken with the active set of the forward pass (pairs whose
- * certified lower violation bound is > 0); it is valid away from kinks.
+ * certified lower violation bound is > 0); it is valid away from kinks.  The
+ * forward pass records that set in a list of up to 16M entries per call,
+ * shared by the boxes (IBP_ENOMEM beyond it, as for any device-side error, and
+ * the gradients of a box whose share overflowed are NaN).
  */
 ibp_status ibp_bound_backward(ibp_case *c, int32_t n_box, const double *box_lo,
                               const double *box_hi, const double *grad_obj_hi,
@@ -166,9 +169,11 @@ ibp_status ibp_bound_backward(ibp_case *c, int32_t n_box, const double *box_lo,
  *     together,
  * plus the imbalance and cost terms, chained to the box endpoints.  Those
  * pairs are most pairs of a wide box: the forward pass records them in a list
- * of up to 64M entries per call (1 GiB; IBP_ENOMEM beyond it, reported by the
- * call in host mode and by ibp_case_sync in device mode), and the radius pass
- * costs O(pairs x active buses), like the forward kernel without its tiling.
+ * of up to 64M entries per call, shared by the boxes (1 GiB; IBP_ENOMEM beyond
+ * it, reported by the call in host mode and by ibp_case_sync in device mode,
+ * and the gradients of a box whose share overflowed are NaN), and the radius
+ * pass costs O(pairs x active buses), like the forward kernel without its
+ * tiling.
  * Valid away from kinks.
  */
 ibp_status ibp_bound_backward_lo(ibp_case *c, int32_t n_box, const double *box_lo,

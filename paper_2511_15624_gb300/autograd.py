@@ -26,6 +26,8 @@ class IBPBoundFunction(torch.autograd.Function):
         if rating is not None:
             case.set_ratings(rating.detach().contiguous().to(torch.float64))
         obj_lo, obj_hi, _ = case.bound(lo, hi)
+        # an end the loss does not use gets no gradient (None): its adjoint pass is skipped
+        ctx.set_materialize_grads(False)
         ctx.case = case
         ctx.has_rating = rating is not None
         ctx.save_for_backward(lo, hi, None if rating is None else rating.detach())
@@ -68,6 +70,7 @@ class IBPBoundMultiFunction(torch.autograd.Function):
         los = [b.detach().contiguous().to(torch.float64) for b in boxes[0::2]]
         his = [b.detach().contiguous().to(torch.float64) for b in boxes[1::2]]
         outs = bound_multi(list(cases), los, his)
+        ctx.set_materialize_grads(False)
         ctx.cases = list(cases)
         ctx.save_for_backward(*[t for pair in zip(los, his) for t in pair])
         return tuple(t for o in outs for t in (o[0], o[1]))

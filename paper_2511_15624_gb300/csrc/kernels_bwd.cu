@@ -169,7 +169,12 @@ __global__ void __launch_bounds__(256) k_bwd_chain(BwdArgs a) {
     const int box = blockIdx.x;
     const double *lo = a.box_lo + (size_t)box * a.n_dev;
     const double *hi = a.box_hi + (size_t)box * a.n_dev;
-    const double g = a.grad_obj_hi[box];
+    // an active-pair list that overflowed its capacity holds only part of the
+    // pairs: the box's gradients are then NaN unless its incoming gradient is
+    // 0 (the error word says IBP_ENOMEM either way)
+    const double g0 = a.grad_obj_hi[box];
+    const double g = (a.act_count[box] > a.act_cap && g0 != 0.0) ? __longlong_as_double(0x7ff8000000000000ll)
+                                                                  : g0;
     const bool lo_side = a.side != 0;
     // total injection interval [plo, phi] (imbalance at the slack)
     double plo = 0.0, phi = 0.0;

@@ -222,3 +222,25 @@ def test_batched_backward_in_cuda_graph():
     for c in cases:
         c.sync()
         c.close()
+
+
+def test_lo_list_overflow_poisons_the_gradients(env):
+    """obj_lo's active set holds most pairs of a wide box; 16 boxes of a
+    2000-bus network need more entries than the case's list holds.  The batched
+    adjoint then writes NaN into the overflowed boxes' gradients (no partial
+    gradient is returned silently), and the case's sync reports IBP_ENOMEM."""
+    P, torch, nets, cases, los, his = env
+    i = next(i for i, n in enumerate(nets) if n.n_bus == 2000)
+    gobj = [torch.ones(nets[i].n_box, dtype=torch.float64, device="cuda")]
+    (glo, ghi, _), = P.bound_multi_backward([cases[i]], [los[i]], [his[i]], gobj, side="lo")
+    torch.cuda.synchronize()
+    glo, ghi = glo.cpu().numpy(), ghi.cpu().numpy()
+    bad = np.isnan(glo).all(axis=1) & np.isnan(ghi).all(axis=1)
+    print(f"{nets[i].name}: {int(bad.sum())} of {nets[i].n_box} boxes overflowed obj_lo's list")
+    assert bad.any()
+    assert np.all(np.isfinite(glo[~bad])) and np.all(np.isfinite(ghi[~bad]))
+    with pytest.raises(P.IBPError) as ei:
+        cases[i].sync()
+    assert ei.value.status == P._abi.IBP_ENOMEM
+    # the next call on the case starts clean
+    cases[i].bound(nets[i].box_lo[:1], nets[i].box_hi[:1])
