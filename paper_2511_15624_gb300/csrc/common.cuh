@@ -111,6 +111,25 @@ __device__ __forceinline__ double warp_sum_ru(double v) {
     for (int o = 16; o > 0; o >>= 1) v = __dadd_ru(v, __shfl_xor_sync(0xffffffffu, v, o));
     return v;
 }
+// Four FP64 sums over the warp, each rounded up, by recursive halving: the
+// lanes split the four values between them (xor 16, then xor 8) before the
+// butterfly over the low three lane bits, so a lane does 6 adds instead of 20.
+// Lane L returns the total of value (L >> 3) & 3.  The order is fixed, so the
+// result does not depend on timing.
+__device__ __forceinline__ double warp_sum4_ru(double v0, double v1, double v2, double v3) {
+    const int lane = threadIdx.x & 31;
+    const bool b16 = (lane & 16) != 0, b8 = (lane & 8) != 0;
+    double k0 = b16 ? v2 : v0, k1 = b16 ? v3 : v1;
+    const double s0 = b16 ? v0 : v2, s1 = b16 ? v1 : v3;
+    k0 = __dadd_ru(k0, __shfl_xor_sync(0xffffffffu, s0, 16));
+    k1 = __dadd_ru(k1, __shfl_xor_sync(0xffffffffu, s1, 16));
+    double k = b8 ? k1 : k0;
+    k = __dadd_ru(k, __shfl_xor_sync(0xffffffffu, b8 ? k0 : k1, 8));
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) k = __dadd_ru(k, __shfl_xor_sync(0xffffffffu, k, o));
+    return k;
+}
+
 __device__ __forceinline__ float warp_sum_ru_f(float v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = __fadd_ru(v, __shfl_xor_sync(0xffffffffu, v, o));

@@ -23,24 +23,44 @@ __device__ __forceinline__ void pair_centre(float Lt, float cl, float ck, float 
     ec = __fmaf_ru(eta_c, one_l, ec);
 }
 
-// Epilogue for one (k, l) pair: flow interval, violation interval, error term.
-// Returns true when the pair's lower violation bound can be positive and the
-// FP64 refinement is on (a.ref.phi64): its obj_hi terms (s_lo and the
-// allowance) then go to cslo_acc / cwhi_acc, which the caller adds only when
-// the pair is not queued for the refinement; its obj_lo terms are added here.
-__device__ __forceinline__ bool pair_epilogue(const CtgArgs &a, int box, int l, int k, float Lt,
-                                              float A, float &slo_acc, float &shi_acc,
-                                              float &whi_acc, float &wlo_acc, float &cslo_acc,
-                                              float &cwhi_acc) {
+// The per-line inputs of a pair's epilogue (line l, box): base centre, its
+// error bound, base radius sum, contingency ratings rounded up and down.
+struct LineIn {
+    float c, e, R, rup, rdn;
+};
+// ... and of its contingency k: the outaged line kl and its c, e, R.
+struct CtgIn {
+    int kl;
+    float c, e, R;
+};
+
+__device__ __forceinline__ LineIn load_line_in(const CtgArgs &a, int box, int l) {
+    const size_t o = (size_t)box * a.n_l + l;
+    return LineIn{__ldg(&a.line_c[o]), __ldg(&a.line_e[o]), __ldg(&a.line_R[o]), __ldg(&a.rate_up[l]),
+                  __ldg(&a.rate_dn[l])};
+}
+__device__ __forceinline__ CtgIn load_ctg_in(const CtgArgs &a, int box, int k) {
     const int kl = __ldg(&a.ctg_line[k]);
+    if (!IBP_IDX_OK(kl >= 0 && kl < a.n_l && box < a.n_box, a.err)) return CtgIn{-1, 0.0f, 0.0f, 0.0f};
+    const size_t o = (size_t)box * a.n_l + kl;
+    return CtgIn{kl, __ldg(&a.line_c[o]), __ldg(&a.line_e[o]), __ldg(&a.line_R[o])};
+}
+
+// Epilogue for one (k, l) pair from its loaded inputs: flow interval,
+// violation interval, error term.  Returns true when the pair's lower
+// violation bound can be positive and the FP64 refinement is on
+// (a.ref.phi64): its obj_hi terms (s_lo and the allowance) then go to
+// cslo_acc / cwhi_acc, which the caller adds only when the pair is not queued
+// for the refinement; its obj_lo terms are added here.
+__device__ __forceinline__ bool pair_epilogue_in(const CtgArgs &a, int box, int l, int k, float Lt,
+                                                 float A, const LineIn &li, const CtgIn &ci,
+                                                 float eta_r, float eta_c, float &slo_acc,
+                                                 float &shi_acc, float &whi_acc, float &wlo_acc,
+                                                 float &cslo_acc, float &cwhi_acc) {
+    const int kl = ci.kl;
     if (!IBP_IDX_OK(kl >= 0 && kl < a.n_l && l >= 0 && l < a.n_l && box < a.n_box, a.err)) return false;
     bool refine = false;
-    const size_t ob = (size_t)box * a.n_l;
-    const float cl = __ldg(&a.line_c[ob + l]), ck = __ldg(&a.line_c[ob + kl]);
-    const float el = __ldg(&a.line_e[ob + l]), ek = __ldg(&a.line_e[ob + kl]);
-    const float Rl = __ldg(&a.line_R[ob + l]), Rk = __ldg(&a.line_R[ob + kl]);
-    const float *bc = a.box_consts + (size_t)box * 4;
-    const float eta_r = __ldg(&bc[0]), eta_c = __ldg(&bc[1]);
+    const float cl = li.c, ck = ci.c, el = li.e, ek = ci.e, Rl = li.R, Rk = ci.R;
     const float aL = fabsf(Lt);
     float flo, fhi, slo, shi, whi, wlo;
     if (l == kl) {
@@ -61,7 +81,7 @@ __device__ __forceinline__ bool pair_epilogue(const CtgArgs &a, int box, int l, 
         fhi = __fadd_ru(c, rho);
         float alo, ahi;
         abs_interval(flo, fhi, alo, ahi);
-        const float rup = __ldg(&a.rate_up[l]), rdn = __ldg(&a.rate_dn[l]);
+        const float rup = li.rup, rdn = li.rdn;
         slo = fmax0(__fsub_rd(alo, rup));
         shi = fmax0(__fsub_ru(ahi, rdn));
         whi = wlo = 0.0f;
@@ -114,18 +134,34 @@ __device__ __forceinline__ bool pair_epilogue(const CtgArgs &a, int box, int l, 
     return refine;
 }
 
+// The same with its inputs loaded here.
+__device__ __forceinline__ bool pair_epilogue(const CtgArgs &a, int box, int l, int k, float Lt,
+                                              float A, float &slo_acc, float &shi_acc,
+                                              float &whi_acc, float &wlo_acc, float &cslo_acc,
+                                              float &cwhi_acc) {
+    const float *bc = a.box_consts + (size_t)box * 4;
+    const CtgIn ci = load_ctg_in(a, box, k);
+    if (ci.kl < 0 || !IBP_IDX_OK(l >= 0 && l < a.n_l, a.err)) return false;
+    return pair_epilogue_in(a, box, l, k, Lt, A, load_line_in(a, box, l), ci, __ldg(&bc[0]), __ldg(&bc[1]),
+                            slo_acc, shi_acc, whi_acc, wlo_acc, cslo_acc, cwhi_acc);
+}
+
 // The one-box kernel calls the epilogue out of line: its 16 pairs per thread
 // inlined raise the kernel's register pressure in the main loop (measured: the
 // contingency kernel takes 0.9% less time this way on mesh8316, while the
-// many-box kernel, at 255 registers, is 3.4% slower with the call).
+// many-box kernel, at 255 registers, is 3.4% slower with the call).  The
+// caller loads every pair's inputs first (one round of independent loads per
+// tile instead of dependent loads in each call).
 static __device__ __noinline__ bool pair_epilogue_call(const CtgArgs &a, int box, int l, int k, float Lt,
-                                                       float A, float &slo_acc, float &shi_acc,
-                                                       float &whi_acc, float &wlo_acc, float &cslo_acc,
-                                                       float &cwhi_acc) {
-    return pair_epilogue(a, box, l, k, Lt, A, slo_acc, shi_acc, whi_acc, wlo_acc, cslo_acc, cwhi_acc);
+                                                       float A, LineIn li, CtgIn ci,
+                                                       float eta_r, float eta_c, float &slo_acc,
+                                                       float &shi_acc, float &whi_acc, float &wlo_acc,
+                                                       float &cslo_acc, float &cwhi_acc) {
+    return pair_epilogue_in(a, box, l, k, Lt, A, li, ci, eta_r, eta_c, slo_acc, shi_acc, whi_acc, wlo_acc,
+                            cslo_acc, cwhi_acc);
 }
 
-// Per-warp FP64 partial sums (deterministic tree, directed rounding):
+// Per-warp FP64 partial sums (deterministic order, directed rounding):
 // {sum s_lo (down), sum s_hi (up), error allowance of obj_hi, of obj_lo}.
 // partial-sum rows per tile: at most the largest warp count of any kernel
 constexpr int kPartRowsPerTile = 16;
@@ -140,17 +176,13 @@ __device__ __forceinline__ void write_warp_partials(const CtgArgs &a, int tile, 
     const float g = 2.02f * kU * (float)n_terms;
     whi = __fmaf_ru(g, slo, whi);  // obj_hi takes sum s_lo
     wlo = __fmaf_ru(g, shi, wlo);  // obj_lo takes sum s_hi
-    const double dlo = warp_sum_rd((double)slo);
-    const double dhi = warp_sum_ru((double)shi);
-    const double dwh = warp_sum_ru((double)whi);
-    const double dwl = warp_sum_ru((double)wlo);
-    if (lane == 0 &&
+    // sum s_lo rounded down as minus the round-up sum of -s_lo
+    const double d = warp_sum4_ru(-(double)slo, (double)shi, (double)whi, (double)wlo);
+    const int q = (lane >> 3) & 3;  // the value this lane holds the total of
+    if ((lane & 7) == 0 &&
         IBP_IDX_OK(a.part_rows_cap <= 0 || tile * a.warps_per_tile + warp < a.part_rows_cap, a.err)) {
         double *p = a.partials + (((size_t)tile * a.warps_per_tile + warp) * a.n_box + box) * kPartVals;
-        p[0] = dlo;
-        p[1] = dhi;
-        p[2] = dwh;
-        p[3] = dwl;
+        p[q] = q == 0 ? -d : d;
     }
 }
 

@@ -295,18 +295,36 @@ __global__ void __launch_bounds__(WL * WK * 32, MINB)
         if (stop) break;
         float slo = 0.0f, shi = 0.0f, whi = 0.0f, wlo = 0.0f, cslo = 0.0f, cwhi = 0.0f;
         uint64_t rmask = 0;
+        // the inputs of the thread's pairs, loaded together (two rounds of
+        // independent loads per tile rather than dependent loads per pair)
+        int ls[ML];
+        LineIn lin[ML];
+        CtgIn cin[MK];
+#pragma unroll
+        for (int i = 0; i < ML; ++i) {
+            const int lq = l0 + tl + TL * i;
+            ls[i] = lq < n_ll ? (a.live ? __ldg(&a.live[lq]) : lq) : -1;
+            if (ls[i] >= 0 && !IBP_IDX_OK(ls[i] < a.n_l, a.err)) ls[i] = -1;
+        }
+#pragma unroll
+        for (int j = 0; j < MK; ++j) {
+            const int k = k0 + tk + TK * j;
+            cin[j] = k < a.n_c ? load_ctg_in(a, 0, k) : CtgIn{-1, 0.0f, 0.0f, 0.0f};
+        }
+#pragma unroll
+        for (int i = 0; i < ML; ++i)
+            lin[i] = ls[i] >= 0 ? load_line_in(a, 0, ls[i]) : LineIn{0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+        const float eta_r = __ldg(&a.box_consts[0]), eta_c = __ldg(&a.box_consts[1]);
 #pragma unroll
         for (int i = 0; i < ML; ++i)
 #pragma unroll
             for (int j = 0; j < MK; ++j) {
-                const int lq = l0 + tl + TL * i, k = k0 + tk + TK * j;
-                if (lq < n_ll && k < a.n_c) {
-                    const int l = a.live ? __ldg(&a.live[lq]) : lq;
+                if (ls[i] >= 0 && cin[j].kl >= 0) {
                     float a3;
                     if constexpr (S3) a3 = acc3s[(i * MK + j) * S::kThreads];
                     else a3 = acc3[i][j];
-                    if (pair_epilogue_call(a, 0, l, k, Lr[i][j], __fadd_ru(a3, acc2[i][j]), slo, shi, whi, wlo,
-                                           cslo, cwhi))
+                    if (pair_epilogue_call(a, 0, ls[i], k0 + tk + TK * j, Lr[i][j], __fadd_ru(a3, acc2[i][j]),
+                                           lin[i], cin[j], eta_r, eta_c, slo, shi, whi, wlo, cslo, cwhi))
                         rmask |= 1ull << (i * MK + j);
                 }
             }
@@ -649,27 +667,59 @@ __device__ __forceinline__ void multi_body(const Plan &P, unsigned long long wai
             }
         }
         if (stop) break;
+        // the box-independent inputs of the thread's pairs: lines, outaged
+        // lines and ratings, loaded once per item
+        int ls[ML], kls[MK];
+        float rup[ML], rdn[ML];
+#pragma unroll
+        for (int i = 0; i < ML; ++i) {
+            const int lq = l0 + tl + TL * i;
+            ls[i] = lq < n_ll ? (a.live ? __ldg(&a.live[lq]) : lq) : -1;
+            if (ls[i] >= 0 && !IBP_IDX_OK(ls[i] < a.n_l, a.err)) ls[i] = -1;
+            rup[i] = ls[i] >= 0 ? __ldg(&a.rate_up[ls[i]]) : 0.0f;
+            rdn[i] = ls[i] >= 0 ? __ldg(&a.rate_dn[ls[i]]) : 0.0f;
+        }
+#pragma unroll
+        for (int c = 0; c < MK; ++c) {
+            const int k = v.k0 + tk + TK * c;
+            kls[c] = k < n_c ? __ldg(&a.ctg_line[k]) : -1;
+            if (kls[c] >= 0 && !IBP_IDX_OK(kls[c] < a.n_l, a.err)) kls[c] = -1;
+        }
 #pragma unroll 1
         for (int j = 0; j < kMBT; ++j) {
             const int box = b0 + half * kMBT + j;
             if (box >= n_box) break;
             float slo = 0.0f, shi = 0.0f, whi = 0.0f, wlo = 0.0f, cslo = 0.0f, cwhi = 0.0f;
             uint64_t rmask = 0;
+            // this box's inputs, loaded together
+            const size_t ob = (size_t)box * a.n_l;
+            LineIn lin[ML];
+            CtgIn cin[MK];
+#pragma unroll
+            for (int i = 0; i < ML; ++i)
+                lin[i] = ls[i] >= 0 ? LineIn{__ldg(&a.line_c[ob + ls[i]]), __ldg(&a.line_e[ob + ls[i]]),
+                                             __ldg(&a.line_R[ob + ls[i]]), rup[i], rdn[i]}
+                                    : LineIn{0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+            for (int c = 0; c < MK; ++c)
+                cin[c] = kls[c] >= 0 ? CtgIn{kls[c], __ldg(&a.line_c[ob + kls[c]]), __ldg(&a.line_e[ob + kls[c]]),
+                                             __ldg(&a.line_R[ob + kls[c]])}
+                                     : CtgIn{-1, 0.0f, 0.0f, 0.0f};
+            const float eta_r = __ldg(&a.box_consts[(size_t)box * 4]);
+            const float eta_c = __ldg(&a.box_consts[(size_t)box * 4 + 1]);
 #pragma unroll
             for (int i = 0; i < ML; ++i) {
-                const int lq = l0 + tl + TL * i;
 #pragma unroll
                 for (int c = 0; c < MK; ++c) {
-                    const int k = v.k0 + tk + TK * c;
-                    if (lq < n_ll && k < n_c) {
-                        const int l = a.live ? __ldg(&a.live[lq]) : lq;
+                    if (ls[i] >= 0 && kls[c] >= 0) {
                         float a2 = 0.0f;
                         // registers cannot be indexed by the runtime j: select it
 #pragma unroll
                         for (int jj = 0; jj < kMBT; ++jj)
                             if (jj == j) a2 = acc2[i][c][jj];
                         const float A = __fadd_ru(acc3[((i * MK + c) * kMBT + j) * S::kThreads], a2);
-                        if (pair_epilogue(a, box, l, k, Lr[i][c], A, slo, shi, whi, wlo, cslo, cwhi))
+                        if (pair_epilogue_in(a, box, ls[i], v.k0 + tk + TK * c, Lr[i][c], A, lin[i], cin[c],
+                                             eta_r, eta_c, slo, shi, whi, wlo, cslo, cwhi))
                             rmask |= 1ull << (i * MK + c);
                     }
                 }
@@ -680,8 +730,7 @@ __device__ __forceinline__ void multi_body(const Plan &P, unsigned long long wai
                 ref_enqueue<ML * MK>(
                     rq, rmask,
                     [&](int q, int &l, int &k) {
-                        const int lq = l0 + tl + TL * (q / MK);
-                        l = a.live ? __ldg(&a.live[lq]) : lq;
+                        l = ls[q / MK];
                         k = v.k0 + tk + TK * (q % MK);
                     },
                     (v.cid << 16) | box, tlk * a.warps_per_tile + wq);
