@@ -75,17 +75,14 @@ struct Shape {
     static_assert(BL <= 256 && BK <= 256, "TMA box rows");
 };
 
-// Issue the TMA copies of chunk c (global index within this CTA's tile list).
+// Issue the TMA copies of chunk c (global index within this CTA's tile list),
+// chunk ch of the tile at (l0, k0).
 template <class S, int ST>
-__device__ __forceinline__ void issue_chunk(const CUtensorMap *mL, const CUtensorMap *mK,
-                                            const CtgArgs &a, float *ring, uint64_t *full,
-                                            int *last_issued, uint32_t c, int tiles_l, int tiles_k) {
+__device__ __forceinline__ void issue_chunk_at(const CUtensorMap *mL, const CUtensorMap *mK, float *ring,
+                                               uint64_t *full, int *last_issued, uint32_t c, int l0, int k0,
+                                               int ch) {
     constexpr uint32_t kBytes = (uint32_t)S::kStageFloats * sizeof(float);
     const int s = (int)(c % ST);
-    const int ti = (int)(c / (uint32_t)a.n_chunks), ch = (int)(c % (uint32_t)a.n_chunks);
-    const int tile = blockIdx.x + ti * gridDim.x;
-    int l0, k0;
-    tile_origin(tile, tiles_l, tiles_k, S::BL, S::BK, l0, k0);
     // stage layout: [sub][BL rows][32] line block, then [sub][BK rows][32]
     float *sL = ring + (size_t)s * S::kStageFloats;
     float *sK = sL + S::BL * S::CH;
@@ -96,6 +93,19 @@ __device__ __forceinline__ void issue_chunk(const CUtensorMap *mL, const CUtenso
         tma_load_2d(smem_addr(sL + sub * S::BL * 32), mL, smem_addr(&full[s]), ch * S::CH + 32 * sub, l0);
         tma_load_2d(smem_addr(sK + sub * S::BK * 32), mK, smem_addr(&full[s]), ch * S::CH + 32 * sub, k0);
     }
+}
+
+// The same, locating chunk c from its index (divisions: used for the first
+// ST chunks only).
+template <class S, int ST>
+__device__ __forceinline__ void issue_chunk(const CUtensorMap *mL, const CUtensorMap *mK,
+                                            const CtgArgs &a, float *ring, uint64_t *full,
+                                            int *last_issued, uint32_t c, int tiles_l, int tiles_k) {
+    const int ti = (int)(c / (uint32_t)a.n_chunks), ch = (int)(c % (uint32_t)a.n_chunks);
+    const int tile = blockIdx.x + ti * gridDim.x;
+    int l0, k0;
+    tile_origin(tile, tiles_l, tiles_k, S::BL, S::BK, l0, k0);
+    issue_chunk_at<S, ST>(mL, mK, ring, full, last_issued, c, l0, k0, ch);
 }
 
 // ---------------------------------------------------------------------------
@@ -261,7 +271,16 @@ __global__ void __launch_bounds__(WL * WK * 32, MINB)
                     const uint32_t nxt = it + ST;
                     if (nxt < total && !*abort_flag) {
                         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                        issue_chunk<S, ST>(&mL, &mK, a, ring, full, last_issued, nxt, tiles_l, tiles_k);
+                        // chunk ch + ST of this tile, or (rarely) of a later one:
+                        // the refilling warp is on the critical path of the
+                        // whole CTA, so it locates the chunk without divisions
+                        int nch = ch + ST, nl0 = l0, nk0 = k0;
+                        if (nch >= a.n_chunks) {
+                            const int ahead = nch / a.n_chunks;
+                            nch -= ahead * a.n_chunks;
+                            tile_origin(tile + ahead * (int)gridDim.x, tiles_l, tiles_k, S::BL, S::BK, nl0, nk0);
+                        }
+                        issue_chunk_at<S, ST>(&mL, &mK, ring, full, last_issued, nxt, nl0, nk0, nch);
                     }
                 }
             }
@@ -452,13 +471,12 @@ struct CasesPlan {
     __device__ const CtgArgs &case_args(int cid) const { return args[cid]; }
 };
 
-template <int ST, int BH, int ML, int MK, class Plan>
-__device__ __forceinline__ void issue_multi(const Plan &P, float *ring, uint64_t *full,
-                                            int *last_issued, uint32_t c, int i, int ch) {
+template <int ST, int BH, int ML, int MK>
+__device__ __forceinline__ void issue_multi_at(const MultiItemView &v, float *ring, uint64_t *full,
+                                               int *last_issued, uint32_t c, int ch) {
     using S = MultiShape<ST, BH, ML, MK>;
     constexpr uint32_t kBytes = (uint32_t)S::kStageFloats * sizeof(float);
     const int s = (int)(c % ST);
-    const MultiItemView v = P.item(i);
     float *sL = ring + (size_t)s * S::kStageFloats;
     float *sK = sL + S::BL * S::CH;
     float *sR = sK + S::BK * S::CH;
@@ -467,6 +485,12 @@ __device__ __forceinline__ void issue_multi(const Plan &P, float *ring, uint64_t
     tma_load_2d(smem_addr(sL), v.mL, smem_addr(&full[s]), ch * S::CH, v.l0);
     tma_load_2d(smem_addr(sK), v.mK, smem_addr(&full[s]), ch * S::CH, v.k0);
     tma_load_2d(smem_addr(sR), v.mR, smem_addr(&full[s]), v.b0, ch * S::CH);
+}
+
+template <int ST, int BH, int ML, int MK, class Plan>
+__device__ __forceinline__ void issue_multi(const Plan &P, float *ring, uint64_t *full,
+                                            int *last_issued, uint32_t c, int i, int ch) {
+    issue_multi_at<ST, BH, ML, MK>(P.item(i), ring, full, last_issued, c, ch);
 }
 
 // PK: accumulate box pairs with the packed two-lane FMA (same rounding per lane)
@@ -633,14 +657,24 @@ __device__ __forceinline__ void multi_body(const Plan &P, unsigned long long wai
                 if (old == (int)(it / ST) * S::kWarps + S::kWarps - 1) {
                     const uint32_t nxt = it + ST;
                     if (nxt < total && !*abort_flag) {
-                        // advance ST chunks from this warp's own position
-                        int i2 = ii, ch2 = ch + ST;
-                        while (ch2 >= P.item(i2).n_chunks) {
-                            ch2 -= P.item(i2).n_chunks;
-                            ++i2;
-                        }
+                        // advance ST chunks from this warp's own position; the
+                        // refilling warp is on the critical path of the whole
+                        // CTA, so within the item it reuses its own view (no
+                        // table loads or divisions)
                         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                        issue_multi<ST, BH, ML_, MK_>(P, ring, full, last_issued, nxt, i2, ch2);
+                        int ch2 = ch + ST;
+                        if (ch2 < v.n_chunks) {
+                            issue_multi_at<ST, BH, ML_, MK_>(v, ring, full, last_issued, nxt, ch2);
+                        } else {
+                            int i2 = ii;
+                            ch2 -= v.n_chunks;
+                            ++i2;
+                            while (ch2 >= P.item(i2).n_chunks) {
+                                ch2 -= P.item(i2).n_chunks;
+                                ++i2;
+                            }
+                            issue_multi<ST, BH, ML_, MK_>(P, ring, full, last_issued, nxt, i2, ch2);
+                        }
                     }
                 }
             }
