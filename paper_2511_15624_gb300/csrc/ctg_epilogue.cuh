@@ -150,8 +150,8 @@ __device__ __forceinline__ bool pair_epilogue(const CtgArgs &a, int box, int l, 
 // inlined raise the kernel's register pressure in the main loop (measured: the
 // contingency kernel takes 0.9% less time this way on mesh8316, while the
 // many-box kernel, at 255 registers, is 3.4% slower with the call).  The
-// caller loads every pair's inputs first (one round of independent loads per
-// tile instead of dependent loads in each call).
+// caller loads every pair's inputs first: two rounds of independent loads per
+// tile instead of two dependent loads in each call.
 static __device__ __noinline__ bool pair_epilogue_call(const CtgArgs &a, int box, int l, int k, float Lt,
                                                        float A, LineIn li, CtgIn ci,
                                                        float eta_r, float eta_c, float &slo_acc,
