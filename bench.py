@@ -39,7 +39,7 @@ FMA_LOOP_TFLOPS = 74.4
 # with the SHA-256 prefix of the kernel sources it was taken on
 # (KERNEL_SOURCES).  Other workloads or tile shapes report null; a kernel
 # build whose sources no longer match reports null with a note.
-MEASURED_TRAFFIC = {(3, 0, True, True): (0.93699e9, "721b303ee5e94fc0")}
+MEASURED_TRAFFIC = {(3, 0, True, True): (0.90089e9, "3f5249af420c2010")}
 KERNEL_SOURCES = ("kernel_ctg.cu", "ctg_epilogue.cuh", "refine.cuh", "common.cuh", "internal.h")
 
 

@@ -604,7 +604,7 @@ ibp_status set_error(ibp_status s, const char *msg) {
 // boxes, 8 warps in two box halves, 4 lines x 2 contingencies x 8 boxes per
 // thread, packed FMA, 6 stages
 constexpr int kDefaultOneBoxVariant = 16;
-constexpr int kDefaultMultiBoxVariant = 29;
+constexpr int kDefaultMultiBoxVariant = 30;
 
 static const CtgVariant *pick_variant(const ibp_case *c, int n_box) {
     if (c->variant > 0) {

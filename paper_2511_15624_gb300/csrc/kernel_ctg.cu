@@ -494,7 +494,8 @@ __device__ __forceinline__ void issue_multi(const Plan &P, float *ring, uint64_t
 }
 
 // PK: accumulate box pairs with the packed two-lane FMA (same rounding per lane)
-template <int ST, int BH, int ML_, class Plan, bool PK = false, int MK_ = 1>
+// GRP: wait for and release the stages of two chunks of an item together
+template <int ST, int BH, int ML_, class Plan, bool PK = false, int MK_ = 1, bool GRP = false>
 __device__ __forceinline__ void multi_body(const Plan &P, unsigned long long wait_ns, int *err) {
     using S = MultiShape<ST, BH, ML_, MK_>;
     constexpr int CH = S::CH, ML = S::ML, MK = S::MK, TL = S::TL, TK = S::TK, BL = S::BL,
@@ -590,15 +591,19 @@ __device__ __forceinline__ void multi_body(const Plan &P, unsigned long long wai
         for (int ch = 0; ch < v.n_chunks; ++ch, ++it) {
             const int s = (int)(it % ST);
             const uint32_t par = (it / ST) & 1u;
-            bool ok = mbar_wait(smem_addr(&full[s]), par, wait_ns);
-            ok = __all_sync(0xffffffffu, ok);
-            if (!ok || *abort_flag) {
-                if (!ok && lane == 0) {
-                    atomicOr(err, kErrTimeout);
-                    *abort_flag = 1;
+            if (!GRP || (ch & 1) == 0) {
+                bool ok = mbar_wait(smem_addr(&full[s]), par, wait_ns);
+                if (GRP && ok && ch + 1 < v.n_chunks)
+                    ok = mbar_wait(smem_addr(&full[(it + 1) % ST]), ((it + 1) / ST) & 1u, wait_ns);
+                ok = __all_sync(0xffffffffu, ok);
+                if (!ok || *abort_flag) {
+                    if (!ok && lane == 0) {
+                        atomicOr(err, kErrTimeout);
+                        *abort_flag = 1;
+                    }
+                    stop = true;
+                    break;
                 }
-                stop = true;
-                break;
             }
             const float *sL = ring + (size_t)s * S::kStageFloats;
             const float *sK = sL + BL * CH;
@@ -651,18 +656,18 @@ __device__ __forceinline__ void multi_body(const Plan &P, unsigned long long wai
                 }
             }
             __syncwarp();
-            if (lane == 0) {
-                __threadfence_block();
-                const int old = atomicAdd(&arrivals[s], 1);
-                if (old == (int)(it / ST) * S::kWarps + S::kWarps - 1) {
-                    const uint32_t nxt = it + ST;
+            // release chunk (itr, chr) of this item; the last of the warps refills it
+            auto release = [&](uint32_t itr, int chr) {
+                const int old = atomicAdd(&arrivals[itr % ST], 1);
+                if (old == (int)(itr / ST) * S::kWarps + S::kWarps - 1) {
+                    const uint32_t nxt = itr + ST;
                     if (nxt < total && !*abort_flag) {
                         // advance ST chunks from this warp's own position; the
                         // refilling warp is on the critical path of the whole
                         // CTA, so within the item it reuses its own view (no
                         // table loads or divisions)
                         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                        int ch2 = ch + ST;
+                        int ch2 = chr + ST;
                         if (ch2 < v.n_chunks) {
                             issue_multi_at<ST, BH, ML_, MK_>(v, ring, full, last_issued, nxt, ch2);
                         } else {
@@ -677,6 +682,11 @@ __device__ __forceinline__ void multi_body(const Plan &P, unsigned long long wai
                         }
                     }
                 }
+            };
+            if (lane == 0 && (!GRP || (ch & 1) || ch == v.n_chunks - 1)) {
+                __threadfence_block();
+                if (GRP && (ch & 1)) release(it - 1, ch - 1);
+                release(it, ch);
             }
 #pragma unroll
             for (int i = 0; i < ML; ++i)
@@ -788,7 +798,7 @@ __device__ __forceinline__ void multi_body(const Plan &P, unsigned long long wai
     }
 }
 
-template <int ST, int BH, int ML, bool PK, int MK>
+template <int ST, int BH, int ML, bool PK, int MK, bool GRP>
 __global__ void __launch_bounds__(MultiShape<ST, BH, ML, MK>::kThreads, 1)
     k_ctg_multi(const __grid_constant__ CUtensorMap mL, const __grid_constant__ CUtensorMap mK,
                 const __grid_constant__ CUtensorMap mR, const CtgArgs a) {
@@ -803,7 +813,7 @@ __global__ void __launch_bounds__(MultiShape<ST, BH, ML, MK>::kThreads, 1)
     const int tiles_l = a.n_live ? (n_ll + S::BL - 1) / S::BL : a.tiles_l;
     const int n_tiles = a.n_live ? tiles_l * tiles_k * box_tiles : a.n_tiles;
     const SinglePlan P{&a, &mL, &mK, &mR, tiles_l, tiles_k, box_tiles, S::BL, S::BK, n_tiles};
-    multi_body<ST, BH, ML, SinglePlan, PK, MK>(P, a.wait_ns, a.err);
+    multi_body<ST, BH, ML, SinglePlan, PK, MK, GRP>(P, a.wait_ns, a.err);
 }
 
 // Many cases in one persistent launch: CTA b walks items [start[b], start[b+1])
@@ -818,12 +828,12 @@ __global__ void __launch_bounds__(MultiShape<ST, BH, 4, MK>::kThreads, 1)
     multi_body<ST, BH, 4, CasesPlan, PK, MK>(P, wait_ns, err);
 }
 
-template <int ST, int BH, int ML = 4, bool PK = false, int MK = 1>
+template <int ST, int BH, int ML = 4, bool PK = false, int MK = 1, bool GRP = false>
 static cudaError_t launch_multi(const CUtensorMap &mL, const CUtensorMap &mK,
                                 const CUtensorMap &mR, const CtgArgs &a, int grid,
                                 cudaStream_t s) {
     using S = MultiShape<ST, BH, ML, MK>;
-    auto kern = k_ctg_multi<ST, BH, ML, PK, MK>;
+    auto kern = k_ctg_multi<ST, BH, ML, PK, MK, GRP>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)S::kBytes);
     if (e != cudaSuccess) return e;
@@ -846,6 +856,7 @@ cudaError_t launch_ctg_multi(const CtgVariant &v, const CUtensorMap &mL, const C
     case 27: return launch_multi<4, 2, 4, true>(mL, mK, mR, a, grid, s);
     case 28: return launch_multi<4, 2, 4, true, 2>(mL, mK, mR, a, grid, s);
     case 29: return launch_multi<6, 2, 4, true, 2>(mL, mK, mR, a, grid, s);
+    case 30: return launch_multi<6, 2, 4, true, 2, true>(mL, mK, mR, a, grid, s);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -883,7 +894,7 @@ static auto with_cases_body(int variant, F f) {
     case 26: return f(CasesBody<4, 1, true, 1>{});
     case 27: return f(CasesBody<4, 2, true, 1>{});
     case 28: return f(CasesBody<4, 2, true, 2>{});
-    default: return f(CasesBody<6, 2, true, 2>{});
+    default: return f(CasesBody<6, 2, true, 2>{});  // 29, and 30 (pairs: single-case calls only)
     }
 }
 
@@ -939,6 +950,7 @@ static const CtgVariant kVariants[] = {
     {27, 1, 64, 16, 32, 4, 8, -1, "multi-box 64x16x16, 16 warps, 4 lines x 8 boxes/thread, packed FMA"},
     {28, 1, 64, 16, 32, 4, 8, -1, "multi-box 64x16x16, 8 warps, 4 lines x 2 ctgs x 8 boxes/thread, packed FMA"},
     {29, 1, 64, 16, 32, 6, 8, -1, "multi-box 64x16x16, 8 warps, 4 lines x 2 ctgs x 8 boxes/thread, packed FMA, 6 stages"},
+    {30, 1, 64, 16, 32, 6, 8, -1, "multi-box as 29, stages waited for and released in pairs"},
 };
 
 const CtgVariant *ctg_variants(int *count) {
@@ -984,7 +996,7 @@ static cudaError_t launch_one(const CUtensorMap &mL, const CUtensorMap &mK, cons
 int ctg_warps(const CtgVariant &v) {
     switch (v.id) {
     case 3: case 8: case 9: case 12: case 13: case 24: case 25: return 16;
-    case 28: case 29: return MultiShape<6, 2, 4, 2>::kWarpsHalf;
+    case 28: case 29: case 30: return MultiShape<6, 2, 4, 2>::kWarpsHalf;
     default: return 8;
     }
 }
