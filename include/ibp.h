@@ -361,7 +361,10 @@ ibp_status ibp_case_info(const ibp_case *c, ibp_case_info_t *out);
  * IBP_EINVAL for an unknown variant.  A one-box variant applies to calls with
  * one box and a multi-box variant to calls with more (the other calls keep
  * the default).  ibp_bound_multi runs the multi-box body of the first case's
- * variant, or the default body for 0 or an id without a many-case form.
+ * variant, or variant 29's body for 0 or an id without a many-case form: the
+ * default multi-box variant of single-case calls, 30, is variant 29 with the
+ * ring's stages waited for and released in pairs, which the many-case launch
+ * does not use.
  */
 ibp_status ibp_case_set_variant(ibp_case *c, int32_t variant);
 int32_t ibp_kernel_variants(int32_t *ids, int32_t cap, int32_t batched);
